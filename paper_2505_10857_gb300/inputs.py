@@ -1,0 +1,325 @@
+"""Seeded synthetic workloads for the steady shallow-water NMGM.
+
+This module builds problem *inputs* only: bottom and width profiles, their
+samples at the points the library's interface asks for, boundary data, the
+coarse initial guess and the solver parameters. It holds none of the
+method's arithmetic (no reconstruction, flux, source, Jacobian or solver
+step), so it can feed both the CUDA library and the CPU oracle.
+
+Sampling contract (shared by both sides, 1D): on a grid of N cells over
+[x0, x1] with dx = (x1-x0)/N, cell j (0-based) has centre x_j = x0+(j+1/2)dx
+and the two Gauss points of Eq. 9, x_j -+ dx/(2 sqrt 3). The library takes
+  sigma_face[N+1]      width at the faces x0 + f dx,
+  gq[3][2][N]          (sigma, d sigma/dx, db/dx) at the two Gauss points,
+for every nested level l (N_l = N / 2^l).
+
+Workload families follow the paper's tests: Eq. 26 (smooth subcritical flow,
+Section 5.1.1), Eq. 28 with the contractions of Section 5.1.2, and the
+seeded channels of the benchmark (Gaussian hump, sinusoidal width).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Tuple
+
+import numpy as np
+
+BC_DISCHARGE, BC_DEPTH, BC_STATE, BC_EXTRAP = 1, 2, 3, 4
+
+G_PAPER = 9.812  # Section 2
+G_CONFIG = 9.81
+
+
+# --------------------------------------------------------------------------
+# Geometry families: each returns (f(x), f'(x)) as numpy functions.
+
+def bottom_eq26():
+    """b(x) of Eq. 26 on [-10, 10]."""
+    def b(x):
+        return 0.2 * np.exp(-0.5 * (x + 1.0) ** 2) + 0.3 * np.exp(-(x - 1.5) ** 2)
+
+    def bx(x):
+        return -0.2 * (x + 1.0) * np.exp(-0.5 * (x + 1.0) ** 2) - 0.6 * (x - 1.5) * np.exp(-(x - 1.5) ** 2)
+    return b, bx
+
+
+def bottom_eq28():
+    """b(x) of Eq. 28 on [0, 25] (parabolic bump on [8, 12])."""
+    def b(x):
+        x = np.asarray(x, dtype=np.float64)
+        return np.where((x >= 8.0) & (x <= 12.0), 0.2 - 0.05 * (x - 10.0) ** 2, 0.0)
+
+    def bx(x):
+        x = np.asarray(x, dtype=np.float64)
+        return np.where((x > 8.0) & (x < 12.0), -0.1 * (x - 10.0), 0.0)
+    return b, bx
+
+
+def bottom_gaussian(A, xc, w):
+    """b(x) = A exp(-((x-xc)/w)^2), the benchmark hump."""
+    def b(x):
+        return A * np.exp(-(((x - xc) / w) ** 2))
+
+    def bx(x):
+        return -2.0 * A * (x - xc) / (w * w) * np.exp(-(((x - xc) / w) ** 2))
+    return b, bx
+
+
+def bottom_linear(b0, slope):
+    def b(x):
+        return b0 + slope * np.asarray(x, dtype=np.float64)
+
+    def bx(x):
+        return np.full_like(np.asarray(x, dtype=np.float64), slope)
+    return b, bx
+
+
+def width_constant(s=1.0):
+    def s_(x):
+        return np.full_like(np.asarray(x, dtype=np.float64), s)
+
+    def sx(x):
+        return np.zeros_like(np.asarray(x, dtype=np.float64))
+    return s_, sx
+
+
+def width_sine(B0, k, Lc):
+    """sigma(x) = B0 (1 + 0.2 sin(2 pi k x / Lc)), the benchmark channel."""
+    def s_(x):
+        return B0 * (1.0 + 0.2 * np.sin(2.0 * np.pi * k * x / Lc))
+
+    def sx(x):
+        return B0 * 0.2 * (2.0 * np.pi * k / Lc) * np.cos(2.0 * np.pi * k * x / Lc)
+    return s_, sx
+
+
+def width_contraction(sigma0, xl, xr):
+    """Smooth contraction of Section 5.1.2 on [xl, xr], 1 elsewhere."""
+    xm, span = 0.5 * (xl + xr), xr - xl
+
+    def s_(x):
+        x = np.asarray(x, dtype=np.float64)
+        inside = (x >= xl) & (x <= xr)
+        return np.where(inside, 1.0 - sigma0 * (1.0 + np.cos(2.0 * np.pi * (x - xm) / span)), 1.0)
+
+    def sx(x):
+        x = np.asarray(x, dtype=np.float64)
+        inside = (x > xl) & (x < xr)
+        return np.where(inside, sigma0 * np.sin(2.0 * np.pi * (x - xm) / span) * 2.0 * np.pi / span, 0.0)
+    return s_, sx
+
+
+# --------------------------------------------------------------------------
+
+@dataclass
+class Problem1DInputs:
+    """All arrays a 1D nested solve needs (host, float64)."""
+    N: int
+    levels: int
+    x0: float
+    x1: float
+    g: float
+    sig_face: np.ndarray            # [N+1]
+    gq: List[np.ndarray]            # per level [3,2,N_l]
+    bcl: Tuple[int, float, float]   # (kind, h, q)
+    bcr: Tuple[int, float, float]
+    U0_start: np.ndarray            # [2, N_s] guess on the start level s
+    start_level: int = -1           # nested start level s (-1: coarsest)
+    omega: float = 1.0              # SOR relaxation suited to the family
+    b_fn: Callable = field(repr=False, default=None)
+    sig_fn: Callable = field(repr=False, default=None)
+    meta: dict = field(default_factory=dict)
+
+    def N_level(self, l):
+        return self.N >> l
+
+    def sig_face_level(self, l):
+        return np.ascontiguousarray(self.sig_face[:: 1 << l])
+
+    def centres(self, l=0):
+        n = self.N_level(l)
+        dx = (self.x1 - self.x0) / n
+        return self.x0 + (np.arange(n) + 0.5) * dx
+
+    def gq_all(self):
+        """Concatenation over levels of gq[l] (the library's layout)."""
+        return np.ascontiguousarray(np.concatenate([a.reshape(-1) for a in self.gq]))
+
+
+def gauss_points(x0, x1, n):
+    dx = (x1 - x0) / n
+    xc = x0 + (np.arange(n) + 0.5) * dx
+    d = dx / (2.0 * math.sqrt(3.0))
+    return xc - d, xc + d
+
+
+def sample_geometry(x0, x1, n, b_fn, sig_fn):
+    """gq[3,2,n] = (sigma, sigma_x, b_x) at the two Gauss points of each cell."""
+    (s, sx), (_, bx) = sig_fn, b_fn
+    out = np.empty((3, 2, n))
+    for q, xg in enumerate(gauss_points(x0, x1, n)):
+        out[0, q] = s(xg)
+        out[1, q] = sx(xg)
+        out[2, q] = bx(xg)
+    return out
+
+
+def make_problem_1d(N, levels, x0, x1, g, b_fns, sig_fns, bcl, bcr, init="lake", h_init=None, q_init=None,
+                    meta=None, start_level=-1, omega=1.0) -> Problem1DInputs:
+    """Samples geometry for every nested level and builds the start guess.
+
+    init = "lake": guess on the start level h = h_init - b(x_c), Q = q_init
+    (Section 5.1.2 uses h = 0.5 - b, u = 0; the benchmark uses h = h_out - b,
+    Q = q).
+    """
+    if N % (1 << (levels - 1)):
+        raise ValueError("N must be divisible by 2^(levels-1) for the nested solve")
+    b, _ = b_fns
+    s, _ = sig_fns
+    faces = x0 + np.arange(N + 1) * (x1 - x0) / N
+    sig_face = s(faces).astype(np.float64)
+    gq = [sample_geometry(x0, x1, N >> l, b_fns, sig_fns) for l in range(levels)]
+    sl = levels - 1 if start_level < 0 else start_level
+    NL = N >> sl
+    xc = x0 + (np.arange(NL) + 0.5) * (x1 - x0) / NL
+    if init == "lake":
+        h = h_init - b(xc)
+        U0 = np.stack([s(xc) * h, np.full(NL, q_init)])
+    else:
+        raise ValueError(init)
+    return Problem1DInputs(N, levels, x0, x1, g, sig_face, gq, tuple(bcl), tuple(bcr),
+                           np.ascontiguousarray(U0, dtype=np.float64), sl, omega, b, s, meta or {})
+
+
+# --------------------------------------------------------------------------
+# Solver parameters (Section 5).
+
+def eps_for_n(n, floor=0.05):
+    """FD perturbation: 0.2/0.15/0.1/0.05 at N=96/192/384/768 (Section 5.1);
+    in between, the same log2 progression, clipped to [floor, 0.2]. The paper
+    suggests 0.01 on finer grids; with the multicolour smoother that value
+    makes the FD Jacobian lose block-diagonal dominance on the N >= 2048
+    channels (the smoother diverges), so the default floor is 0.05, the value
+    the paper uses at N = 768."""
+    e = 0.2 - 0.05 * math.log2(n / 96.0)
+    return float(min(0.2, max(floor, e)))
+
+
+@dataclass
+class Params1D:
+    alpha: float = 3.0
+    tau: float = 0.6
+    omega: float = 1.0
+    tol: float = 1e-11
+    nu1: int = 2
+    nu2: int = 2
+    nu3: int = 2
+    levels: int = 4
+    n_max: int = 2000
+    nb: int = 3
+    eps: List[float] = field(default_factory=list)
+    nest_start: int = -1
+    lex: bool = False
+
+    @staticmethod
+    def for_problem(p: Problem1DInputs, **kw):
+        kw.setdefault("omega", p.omega)
+        kw.setdefault("nest_start", p.start_level)
+        prm = Params1D(levels=p.levels, **kw)
+        if not prm.eps:
+            prm.eps = [eps_for_n(p.N_level(l)) for l in range(p.levels)]
+        return prm
+
+
+# --------------------------------------------------------------------------
+# Paper workloads.
+
+def paper_smooth_subcritical(N, levels=4):
+    """Section 5.1.1: Eq. 26 on [-10, 10], sigma = 1, h = 1 and hu = 1 at both
+    ends, g = 9.812."""
+    return make_problem_1d(N, levels, -10.0, 10.0, G_PAPER, bottom_eq26(), width_constant(1.0),
+                           (BC_STATE, 1.0, 1.0), (BC_STATE, 1.0, 1.0), h_init=1.0, q_init=1.0,
+                           meta={"case": "eq26"})
+
+
+def paper_bump(N, levels=4, regime="sub", width="const"):
+    """Section 5.1.2 on [0, 25] (Eq. 28). regime sub: q=4.42, h_out=2,
+    sigma0=0.05; trans: q=1.53, h_out=0.66, sigma0=0.15. Coarsest guess
+    h = 0.5 - b, u = 0 as in the paper."""
+    q, hout, s0 = (4.42, 2.0, 0.05) if regime == "sub" else (1.53, 0.66, 0.15)
+    sig = {"const": width_constant(1.0), "left": width_contraction(s0, 3.75, 16.25),
+           "right": width_contraction(s0, 8.75, 21.25)}[width]
+    p = make_problem_1d(N, levels, 0.0, 25.0, G_PAPER, bottom_eq28(), sig,
+                        (BC_DISCHARGE, 0.0, q), (BC_DEPTH, hout, 0.0), h_init=0.5, q_init=0.0,
+                        meta={"case": f"eq28-{regime}-{width}"})
+    return p
+
+
+def _seeded_hump(rng):
+    A = float(rng.uniform(0.05, 0.2))
+    xc = float(rng.uniform(8.0, 12.0))
+    w = float(rng.uniform(1.0, 2.0))
+    return A, xc, w
+
+
+def channel_small(k, N=200, levels=4):
+    """Seeded 1D smooth subcritical channel, N=200 cells on [0, 25]: constant
+    width, Gaussian hump with A~U[0.05,0.2], xc~U[8,12], w~U[1,2], upstream
+    discharge 4.42, downstream depth 2.0, g=9.81. Seed 1000 + k."""
+    rng = np.random.default_rng(1000 + k)
+    A, xc, w = _seeded_hump(rng)
+    return make_problem_1d(N, levels, 0.0, 25.0, G_CONFIG, bottom_gaussian(A, xc, w), width_constant(1.0),
+                           (BC_DISCHARGE, 0.0, 4.42), (BC_DEPTH, 2.0, 0.0), h_init=2.0, q_init=4.42,
+                           meta={"A": A, "xc": xc, "w": w, "seed": 1000 + k}, omega=1.2)
+
+
+def critical_margin(q, hout, b_fn, sig_fn, g=G_CONFIG, x0=0.0, x1=25.0, n=4001):
+    """E - max_x E_c(x) for the downstream energy E (a positive margin means
+    the smooth subcritical steady state exists). Problem classification only."""
+    b, _ = b_fn
+    s, _ = sig_fn
+    x = np.linspace(x0, x1, n)
+    E = q * q / (2.0 * s(x1) ** 2 * hout * hout) + g * (hout + b(x1))
+    qx = q / s(x)
+    hc = (qx * qx / g) ** (1.0 / 3.0)
+    Ec = 1.5 * g * hc + g * b(x)
+    return float(E - Ec.max())
+
+
+def channel_irregular(k, N=4096, levels=8, regime="sub", min_margin=0.5, start_level=4):
+    """Seeded 1D channel with sinusoidal width B(x)=B0(1+0.2 sin(2 pi k' x/25)),
+    B0 = 1, k' ~ U{1..4}, Gaussian hump as in channel_small, N=4096 on [0,25],
+    8-level multigrid (4096 -> 32 cells).
+    regime "sub": q=4.42, h_out=2.0; seeds whose hump meets a narrow section
+    and would choke the subcritical flow are redrawn (deterministically, same
+    generator) until the energy margin exceeds min_margin. Seed 2000 + k.
+    The nested solve starts on level 4 (256 cells): coarser grids do not
+    resolve the width oscillation for k' >= 2. SOR relaxation 0.7."""
+    rng = np.random.default_rng(2000 + k)
+    q, hout = (4.42, 2.0) if regime == "sub" else (1.53, 0.66)
+    for draw in range(1000):
+        A, xc, w = _seeded_hump(rng)
+        kk = int(rng.integers(1, 5))
+        b_fns, s_fns = bottom_gaussian(A, xc, w), width_sine(1.0, kk, 25.0)
+        margin = critical_margin(q, hout, b_fns, s_fns)
+        if regime != "sub" or margin > min_margin:
+            break
+    return make_problem_1d(N, levels, 0.0, 25.0, G_CONFIG, b_fns, s_fns,
+                           (BC_DISCHARGE, 0.0, q), (BC_DEPTH, hout, 0.0), h_init=hout, q_init=q,
+                           meta={"A": A, "xc": xc, "w": w, "k": kk, "seed": 2000 + k, "draws": draw + 1,
+                                 "margin": margin, "regime": regime}, start_level=start_level, omega=0.7)
+
+
+def uniform_flow(N, levels, h, q, sigma=1.0, x0=0.0, x1=10.0, g=G_CONFIG, bc=BC_STATE):
+    """Flat bottom, constant width, uniform state (the residual is zero)."""
+    return make_problem_1d(N, levels, x0, x1, g, bottom_linear(0.0, 0.0), width_constant(sigma),
+                           (bc, h, q), (bc, h, q), h_init=h, q_init=q, meta={"case": "uniform"})
+
+
+def random_state(rng, N, H_range=(1.5, 2.5), Q_range=(3.5, 5.0)):
+    """A smooth-ish random state for operator tests (positive depth)."""
+    x = np.linspace(0, 1, N)
+    H = rng.uniform(*H_range) + 0.2 * np.sin(2 * np.pi * rng.uniform(1, 3) * x) + 0.02 * rng.standard_normal(N)
+    Q = rng.uniform(*Q_range) + 0.1 * np.cos(2 * np.pi * rng.uniform(1, 3) * x) + 0.02 * rng.standard_normal(N)
+    return np.ascontiguousarray(np.stack([H, Q]))

@@ -1,0 +1,543 @@
+"""Pins of the 1D CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed-form
+steady states, exactness properties, brute-force differentiation, dense
+linear algebra, and the values printed in the paper (tests/golden).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2505_10857_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- WENO3 (Eq. 7-8)
+
+def test_weno_linear_data_gives_quadratic_reconstruction(orc):
+    # On linear data beta0 == beta1, so the weights equal the linear weights
+    # and the result must be the 3-cell quadratic (third-order) formula.
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        a0, s = rng.uniform(-3, 3), rng.uniform(-1, 1)
+        a, b, c = a0, a0 + s, a0 + 2 * s
+        up, um = orc.weno3(a, b, c)
+        assert up == pytest.approx(a / 3 + 5 * b / 6 - c / 6, rel=1e-14, abs=1e-14)
+        assert um == pytest.approx(-a / 6 + 5 * b / 6 + c / 3, rel=1e-14, abs=1e-14)
+        # linear data: both are the exact interface values b -+ s/2
+        assert up == pytest.approx(b - s / 2, rel=1e-13, abs=1e-13)
+        assert um == pytest.approx(b + s / 2, rel=1e-13, abs=1e-13)
+
+
+def test_weno_mirror_symmetry(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        a, b, c = rng.uniform(0.5, 3, 3)
+        up, um = orc.weno3(a, b, c)
+        up2, um2 = orc.weno3(c, b, a)
+        assert up2 == pytest.approx(um, rel=1e-14)
+        assert um2 == pytest.approx(up, rel=1e-14)
+
+
+def test_weno_picks_smooth_side_at_a_jump(orc):
+    # Step between cells k and k+1: U^+_{k-1/2} uses T1 = {k-1,k} (flat),
+    # U^-_{k+1/2} must also come from T1 (the flat side): no overshoot.
+    up, um = orc.weno3(1.0, 1.0, 5.0)
+    assert up == pytest.approx(1.0, abs=1e-10)
+    assert um == pytest.approx(1.0, abs=1e-10)
+    # step between k-1 and k: T0 = {k,k+1} is flat
+    up, um = orc.weno3(5.0, 1.0, 1.0)
+    assert up == pytest.approx(1.0, abs=1e-10)
+    assert um == pytest.approx(1.0, abs=1e-10)
+
+
+def test_weno_third_order_interface_values(orc):
+    # Interface values from exact cell averages of a smooth function converge
+    # at third order (away from extrema, where the weights stay near linear).
+    f = lambda x: np.exp(0.3 * x) + 0.5 * x
+    F = lambda x: np.exp(0.3 * x) / 0.3 + 0.25 * x * x
+    errs = []
+    for n in [20, 40, 80, 160]:
+        h = 1.0 / n
+        x = 0.4 + h * np.arange(-1, 2)  # cells k-1, k, k+1 around 0.4+h/2
+        avg = (F(x + h) - F(x)) / h
+        up, um = orc.weno3(*avg)
+        errs.append(max(abs(up - f(x[1])), abs(um - f(x[1] + h))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert min(orders) > 2.6, orders
+
+
+# ---------------------------------------------------------------- HLL flux
+
+def test_hll_consistency_and_upwinding(orc):
+    g = 9.81
+    for H, Q, s in [(2.0, 4.42, 1.0), (1.3, -0.7, 0.8), (0.7, 0.2, 1.2)]:
+        F = orc.flux1d(H, Q, s, g)
+        assert np.allclose(orc.hll1d(H, Q, H, Q, s, g), F, rtol=1e-15, atol=0)
+        # closed form of the physical flux
+        assert F[0] == Q
+        assert F[1] == pytest.approx(Q * Q / H + 0.5 * g * H * H / s, rel=1e-15)
+    # supercritical to the right: all waves go right, flux = F(U_L)
+    HL, QL, HR, QR = 1.0, 8.0, 1.1, 8.2
+    assert np.array_equal(orc.hll1d(HL, QL, HR, QR, 1.0, g), orc.flux1d(HL, QL, 1.0, g))
+    # supercritical to the left: flux = F(U_R)
+    assert np.array_equal(orc.hll1d(HL, -QL, HR, -QR, 1.0, g), orc.flux1d(HR, -QR, 1.0, g))
+
+
+def test_hll_equals_intermediate_state_form(orc):
+    # The HLL flux equals F_L + S_L (U* - U_L) with the HLL intermediate state
+    # U* = (S_R U_R - S_L U_L - (F_R - F_L)) / (S_R - S_L).
+    g, s = 9.81, 0.9
+    rng = np.random.default_rng(3)
+    for _ in range(30):
+        HL, HR = rng.uniform(0.5, 2.5, 2)
+        QL, QR = rng.uniform(-2, 2, 2)
+        FL, FR = orc.flux1d(HL, QL, s, g), orc.flux1d(HR, QR, s, g)
+        uL, uR = QL / HL, QR / HR
+        cL, cR = math.sqrt(g * HL / s), math.sqrt(g * HR / s)
+        SL, SR = min(uL - cL, uR - cR), max(uL + cL, uR + cR)
+        assert SL < 0 < SR
+        UL, UR = np.array([HL, QL]), np.array([HR, QR])
+        Ustar = (SR * UR - SL * UL - (FR - FL)) / (SR - SL)
+        expect = FL + SL * (Ustar - UL)
+        assert np.allclose(orc.hll1d(HL, QL, HR, QR, s, g), expect, rtol=1e-12, atol=1e-12)
+
+
+def test_hll_mirror(orc):
+    # Reflecting x -> -x swaps the states and flips the velocity: the mass
+    # flux changes sign, the momentum flux does not.
+    g = 9.81
+    F = orc.hll1d(1.2, 0.9, 1.5, 0.4, 1.0, g)
+    Fm = orc.hll1d(1.5, -0.4, 1.2, -0.9, 1.0, g)
+    assert Fm[0] == pytest.approx(-F[0], rel=1e-14)
+    assert Fm[1] == pytest.approx(F[1], rel=1e-14)
+
+
+# ---------------------------------------------------------------- source quadrature (Eq. 9)
+
+def test_cubic_reproduces_cubics(orc):
+    rng = np.random.default_rng(4)
+    tk = np.array([-1.5, -0.5, 0.5, 1.5])
+    for _ in range(20):
+        c = rng.standard_normal(4)
+        poly = lambda t: c[0] + c[1] * t + c[2] * t * t + c[3] * t ** 3
+        for t in [-1 / (2 * math.sqrt(3)), 1 / (2 * math.sqrt(3)), 0.3, -1.1]:
+            assert orc.cubic4(poly(tk), t) == pytest.approx(poly(t), rel=1e-13, abs=1e-13)
+
+
+# ---------------------------------------------------------------- residual (Eq. 10)
+
+@pytest.mark.parametrize("bc", [I.BC_STATE, I.BC_EXTRAP])
+def test_uniform_state_has_zero_residual(orc, bc):
+    for h, q, s in [(2.0, 4.42, 1.0), (0.8, -1.3, 1.7)]:
+        p = I.uniform_flow(40, 1, h, q, sigma=s, bc=bc)
+        pr = orc.problem_levels(p)[0]
+        U = np.stack([np.full(40, s * h), np.full(40, q)])
+        R, res = orc.residual1d(pr, U)
+        scale = abs(orc.flux1d(s * h, q, s, p.g)).max()
+        assert np.abs(R).max() <= 1e-14 * scale
+
+
+def test_uniform_state_discharge_depth_bc(orc):
+    # Upstream discharge + downstream depth consistent with the interior state.
+    h, q = 2.0, 4.42
+    p = I.make_problem_1d(32, 1, 0.0, 25.0, 9.81, I.bottom_linear(0.0, 0.0), I.width_constant(1.0),
+                          (I.BC_DISCHARGE, 0.0, q), (I.BC_DEPTH, h, 0.0), h_init=h, q_init=q)
+    pr = orc.problem_levels(p)[0]
+    R, res = orc.residual1d(pr, np.stack([np.full(32, h), np.full(32, q)]))
+    assert np.abs(R).max() <= 1e-13
+
+
+def test_lake_at_rest_over_linear_bottom(orc):
+    # h + b = const, Q = 0, b linear, sigma constant: WENO3 and the cubic are
+    # exact on linear data and HLL is consistent, so interior R_j = 0 exactly
+    # up to rounding (flux difference g sigma h dh = -g sigma h b_x dx = S_j).
+    for N, slope, s in [(16, 0.02, 1.0), (50, -0.05, 2.5)]:
+        p = I.make_problem_1d(N, 1, 0.0, 25.0, 9.81, I.bottom_linear(0.1, slope), I.width_constant(s),
+                              (I.BC_EXTRAP, 0, 0), (I.BC_EXTRAP, 0, 0), h_init=3.0, q_init=0.0)
+        pr = orc.problem_levels(p)[0]
+        xc = p.centres(0)
+        H = s * (3.0 - (0.1 + slope * xc))  # averages of a linear function
+        R, res = orc.residual1d(pr, np.stack([H, np.zeros(N)]))
+        scale = 0.5 * 9.81 * H.max() ** 2 / s
+        assert np.abs(R[:, 2:-2]).max() <= 1e-13 * scale
+        # and the bottom source is really exercised
+        assert abs(slope * 9.81 * s * 3.0 * 25.0 / N) > 1e-3
+
+
+def test_lake_at_rest_varying_width_is_steady_in_the_limit(orc):
+    # With sigma(x) varying, the lake at rest is still a steady state of
+    # Eq. 3 (h_x = -b_x); the discrete residual must vanish as dx -> 0.
+    out = []
+    for N in [64, 128, 256]:
+        p = I.make_problem_1d(N, 1, 0.0, 25.0, 9.81, I.bottom_linear(0.0, 0.01), I.width_sine(1.0, 1, 25.0),
+                              (I.BC_EXTRAP, 0, 0), (I.BC_EXTRAP, 0, 0), h_init=2.0, q_init=0.0)
+        pr = orc.problem_levels(p)[0]
+        dx = 25.0 / N
+        t, w = np.polynomial.legendre.leggauss(8)
+        xc = p.centres(0)
+        H = sum(0.5 * wi * p.sig_fn(xc + 0.5 * dx * ti) * (2.0 - 0.01 * (xc + 0.5 * dx * ti)) for ti, wi in zip(t, w))
+        R, _ = orc.residual1d(pr, np.stack([H, np.zeros(N)]))
+        out.append(np.abs(R[:, 3:-3]).max())
+    assert out[0] / out[1] > 6 and out[1] / out[2] > 6, out
+
+
+# ---------------------------------------------------------------- Bernoulli / Table 1
+
+def _u_exact_eq27(x, g):
+    b, _ = I.bottom_eq26()
+    u = np.empty_like(x)
+    for i, xx in enumerate(x):
+        r = np.roots([1.0, 0.0, 2 * g * b(xx) - 2 * g - 1.0, 2 * g])
+        r = r[np.abs(r.imag) < 1e-10].real
+        u[i] = r[np.argmin(np.abs(r - 1.0))]
+    return u
+
+
+def _cell_avg(f, x0, x1, N, nq=8):
+    t, w = np.polynomial.legendre.leggauss(nq)
+    dx = (x1 - x0) / N
+    xc = x0 + (np.arange(N) + 0.5) * dx
+    return sum(0.5 * wi * f(xc + 0.5 * dx * ti) for ti, wi in zip(t, w))
+
+
+@pytest.mark.slow
+def test_smooth_subcritical_third_order_and_table1(orc):
+    """Section 5.1.1: discrete steady states converge to the exact solution of
+    Eq. 27 at third order, with errors of the magnitude printed in Table 1."""
+    gold = json.load(open(os.path.join(GOLDEN, "table1_smooth_subcritical.json")))
+    g = I.G_PAPER
+    eh, eq = [], []
+    for lev, N in enumerate(gold["N"]):
+        p = I.paper_smooth_subcritical(N, levels=lev + 1)
+        prm = I.Params1D.for_problem(p)
+        U, info = orc.solve_problem(p, prm)
+        assert info["status"] == 0 and info["res"][0] < 1e-11
+        h_ex = _cell_avg(lambda x: 1.0 / _u_exact_eq27(x, g), -10, 10, N)
+        # Bernoulli + constant discharge: hu = 1 exactly for the exact solution
+        eh.append(np.abs(U[0] - h_ex).mean())
+        eq.append(np.abs(U[1] - 1.0).mean())
+    for e, ref in [(eh, gold["h_l1"]), (eq, gold["hu_l1"])]:
+        orders = [math.log2(e[i] / e[i + 1]) for i in range(3)]
+        assert min(orders) > 2.3 and orders[-1] > 2.8, orders
+        for mine, paper in zip(e, ref):
+            assert paper / 3.0 < mine < paper * 3.0, (mine, paper)
+
+
+# ---------------------------------------------------------------- Jacobian (Eq. 12-13)
+
+def _random_problem(N=12, seed=5, bcl=(I.BC_DISCHARGE, 0.0, 4.42), bcr=(I.BC_DEPTH, 2.0, 0.0)):
+    rng = np.random.default_rng(seed)
+    p = I.make_problem_1d(N, 1, 0.0, 25.0, 9.81, I.bottom_gaussian(0.15, 12.0, 3.0), I.width_sine(1.0, 1, 25.0),
+                          bcl, bcr, h_init=2.0, q_init=4.42)
+    U = I.random_state(rng, N)
+    return p, U
+
+
+@pytest.mark.parametrize("bcs", [((I.BC_DISCHARGE, 0.0, 4.42), (I.BC_DEPTH, 2.0, 0.0)),
+                                 ((I.BC_STATE, 2.0, 4.0), (I.BC_EXTRAP, 0.0, 0.0))])
+def test_jacobian_equals_global_bruteforce_fd(orc, bcs):
+    """Local-stencil FD (Eq. 12) equals differencing the whole residual vector
+    after perturbing one unknown of the whole state: bit for bit inside the
+    5-cell stencil, exactly zero outside it (Fig. 1b)."""
+    p, U = _random_problem(bcl=bcs[0], bcr=bcs[1])
+    pr = orc.problem_levels(p)[0]
+    N, eps = p.N, 0.07
+    J5, R, res = orc.jacobian1d(pr, U, eps, 0.0, 5)
+    R0, _ = orc.residual1d(pr, U)
+    assert np.array_equal(R, R0)
+    for i in range(N):
+        for m in range(2):
+            Up = U.copy()
+            Up[m, i] += eps
+            Rp, _ = orc.residual1d(pr, Up)
+            col = (Rp - R0) / eps  # d R_j / d U_i[m] for all j
+            for j in range(N):
+                d = i - j
+                if abs(d) <= 2:
+                    for l in range(2):
+                        assert J5[d + 2, l * 2 + m, j] == col[l, j]
+                else:
+                    assert np.all(col[:, j] == 0.0)
+
+
+def test_j3_is_j5_without_outer_blocks(orc):
+    p, U = _random_problem()
+    pr = orc.problem_levels(p)[0]
+    J5, R5, _ = orc.jacobian1d(pr, U, 0.1, 3.0, 5)
+    J3, R3, _ = orc.jacobian1d(pr, U, 0.1, 3.0, 3)
+    assert np.array_equal(J3, J5[1:4]) and np.array_equal(R3, R5)
+    assert np.abs(J5[0]).max() > 0 and np.abs(J5[4]).max() > 0
+
+
+def test_regularization_on_diagonal_only(orc):
+    p, U = _random_problem()
+    pr = orc.problem_levels(p)[0]
+    J0, R, _ = orc.jacobian1d(pr, U, 0.1, 0.0, 3)
+    Ja, _, _ = orc.jacobian1d(pr, U, 0.1, 3.0, 3)
+    d = Ja - J0
+    reg = 3.0 * np.abs(R).sum(0)
+    assert np.allclose(d[1, 0], reg, rtol=1e-12) and np.allclose(d[1, 3], reg, rtol=1e-12)
+    d[1, 0] = 0
+    d[1, 3] = 0
+    assert np.all(d == 0)
+
+
+def test_fd_jacobian_first_order_in_eps(orc):
+    """J_FD(eps) -> dR/dU linearly in eps, against a central-difference
+    derivative of the whole residual vector (step 1e-6)."""
+    p, U = _random_problem(N=10, seed=7)
+    pr = orc.problem_levels(p)[0]
+    N = p.N
+    Jc = np.zeros((5, 4, N))
+    d = 1e-6
+    for i in range(N):
+        for m in range(2):
+            Up, Um = U.copy(), U.copy()
+            Up[m, i] += d
+            Um[m, i] -= d
+            col = (orc.residual1d(pr, Up)[0] - orc.residual1d(pr, Um)[0]) / (2 * d)
+            for j in range(max(0, i - 2), min(N, i + 3)):
+                for l in range(2):
+                    Jc[i - j + 2, l * 2 + m, j] = col[l, j]
+    errs = []
+    for eps in [4e-3, 2e-3, 1e-3]:
+        J, _, _ = orc.jacobian1d(pr, U, eps, 0.0, 5)
+        errs.append(np.abs(J - Jc).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.6 < r1 < 2.5 and 1.6 < r2 < 2.5, errs
+    assert errs[-1] < 1e-2 * np.abs(Jc).max()
+
+
+@pytest.mark.slow
+def test_block_magnitudes_section_3_3(orc):
+    """Section 3.3: for the N=96 smooth subcritical J5, the central tridiagonal
+    blocks exceed 1 and the outermost blocks fall below 1; a large share of
+    the outermost blocks is tiny (the paper reports 69% below 1e-4 at its
+    iterate; the iterate is unstated, so the share is a soft bound)."""
+    p = I.paper_smooth_subcritical(96, levels=1)
+    U, info = orc.solve_problem(p, I.Params1D.for_problem(p, nb=5))
+    pr = orc.problem_levels(p)[0]
+    J, _, _ = orc.jacobian1d(pr, U, 0.2, 3.0, 5)
+    mag = np.abs(J).sum(1)
+    central = np.concatenate([mag[1][1:], mag[2], mag[3][:-1]])
+    outer = np.concatenate([mag[0][2:], mag[4][:-2]])
+    assert central.min() > 1.0
+    assert outer.max() < 1.0
+    assert (outer < 1e-4).mean() > 0.3
+
+
+# ---------------------------------------------------------------- multigrid (Eq. 15-19)
+
+def _P(Nf):
+    Nc = (Nf + 1) // 2
+    P = np.zeros((2 * Nf, 2 * Nc))
+    for xi in range(Nf):
+        for m in range(2):
+            P[2 * xi + m, 2 * (xi // 2) + m] = 1.0
+    return P
+
+
+def _dense(J, nb):
+    N = J.shape[-1]
+    hw = (nb - 1) // 2
+    A = np.zeros((2 * N, 2 * N))
+    for j in range(N):
+        for k in range(nb):
+            i = j + k - hw
+            if 0 <= i < N:
+                A[2 * j:2 * j + 2, 2 * i:2 * i + 2] = J[k, :, j].reshape(2, 2)
+    return A
+
+
+def _vec(U):
+    return np.stack([U[0], U[1]], 1).reshape(-1)
+
+
+def _unvec(x):
+    return np.stack([x[0::2], x[1::2]])
+
+
+def _random_banded(N, nb, rng, dominant=True):
+    J = rng.standard_normal((nb, 4, N))
+    hw = (nb - 1) // 2
+    for k in range(nb):
+        i = np.arange(N) + k - hw
+        J[k, :, (i < 0) | (i >= N)] = 0.0
+    if dominant:
+        J[hw, 0] += 4.0 * nb
+        J[hw, 3] += 4.0 * nb
+    return J
+
+
+@pytest.mark.parametrize("Nf,nb", [(16, 3), (17, 3), (16, 5), (9, 5)])
+def test_coarse_operator_is_galerkin(orc, Nf, nb):
+    """Eq. 17 equals P^T J P with P the piecewise-constant aggregation (Eq. 15,
+    18), including an odd fine count (singleton last aggregate)."""
+    rng = np.random.default_rng(Nf + nb)
+    J = _random_banded(Nf, nb, rng)
+    Jc = orc.coarse_operator1d(J, nb)
+    P = _P(Nf)
+    assert np.allclose(_dense(Jc, 3), P.T @ _dense(J, nb) @ P, rtol=1e-14, atol=1e-13)
+
+
+@pytest.mark.parametrize("Nf,nb", [(16, 3), (17, 5)])
+def test_restriction_and_prolongation(orc, Nf, nb):
+    rng = np.random.default_rng(11)
+    J = _random_banded(Nf, nb, rng)
+    R = rng.standard_normal((2, Nf))
+    dU = rng.standard_normal((2, Nf))
+    Rc = orc.restrict1d(J, R, dU, nb)
+    P = _P(Nf)
+    assert np.allclose(_vec(Rc), P.T @ (_vec(R) + _dense(J, nb) @ _vec(dU)), rtol=1e-13, atol=1e-13)
+    dUc = rng.standard_normal((2, (Nf + 1) // 2))
+    assert np.allclose(_vec(orc.prolong1d(dU, dUc)), _vec(dU) + P @ _vec(dUc), rtol=1e-15, atol=1e-15)
+
+
+def test_dense_and_direct_solve(orc):
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((30, 30)) + 0.1 * np.eye(30)
+    b = rng.standard_normal(30)
+    x = orc.dense_solve(A, b)
+    assert np.allclose(A @ x, b, rtol=0, atol=1e-11 * np.abs(A).max() * np.abs(x).max())
+    J = _random_banded(20, 5, rng, dominant=False)
+    R = rng.standard_normal((2, 20))
+    dU = orc.direct_solve1d(J, R, 5)
+    assert np.abs(_dense(J, 5) @ _vec(dU) + _vec(R)).max() < 1e-12 * np.abs(R).max() * 100
+
+
+def test_sor_converges_to_direct_solution(orc):
+    rng = np.random.default_rng(13)
+    for nb in (3, 5):
+        J = _random_banded(25, nb, rng)
+        R = rng.standard_normal((2, 25))
+        D = orc.block_inverse1d(J, nb)
+        # the block inverse is the inverse of the diagonal blocks
+        hw = (nb - 1) // 2
+        for j in range(0, 25, 6):
+            assert np.allclose(D[:, j].reshape(2, 2) @ J[hw, :, j].reshape(2, 2), np.eye(2), atol=1e-13)
+        x = orc.direct_solve1d(J, R, nb)
+        dU = np.zeros((2, 25))
+        for _ in range(60):
+            dU = orc.sor_step1d(J, D, R, dU, 1.1, nb)
+        assert np.abs(dU - x).max() < 1e-11
+        # the exact solution is a fixed point of one step
+        assert np.abs(orc.sor_step1d(J, D, R, x, 1.1, nb) - x).max() < 1e-13
+
+
+def test_sor_colour_independence(orc):
+    """Cells of one colour do not couple, so the multicolour step does not
+    depend on the order within a colour: compare against a Jacobi-style update
+    per colour written with dense blocks."""
+    rng = np.random.default_rng(14)
+    for nb in (3, 5):
+        N = 13
+        J = _random_banded(N, nb, rng)
+        R = rng.standard_normal((2, N))
+        dU0 = rng.standard_normal((2, N))
+        D = orc.block_inverse1d(J, nb)
+        got = orc.sor_step1d(J, D, R, dU0, 0.9, nb)
+        C = (nb - 1) // 2 + 1
+        A = _dense(J, nb)
+        x = _vec(dU0).copy()
+        for col in list(range(C)) + list(range(C - 1, -1, -1)):
+            new = x.copy()
+            for j in range(col, N, C):
+                rows = slice(2 * j, 2 * j + 2)
+                off = A[rows] @ x - A[rows, rows] @ x[rows]
+                new[rows] = 0.1 * x[rows] - 0.9 * np.linalg.solve(A[rows, rows], _vec(R)[rows] + off)
+            x = new
+        assert np.allclose(_vec(got), x, rtol=1e-12, atol=1e-12)
+
+
+def test_two_level_vcycle_without_smoothing_is_coarse_correction(orc):
+    """Algorithm 2 with nu1 = nu2 = 0 and two levels from dU = 0 gives exactly
+    P (P^T J P)^{-1} P^T (-R)."""
+    rng = np.random.default_rng(15)
+    for Nf, nb in [(12, 3), (11, 5)]:
+        J = _random_banded(Nf, nb, rng)
+        R = rng.standard_normal((2, Nf))
+        dU = orc.vcycle1d(J, R, np.zeros((2, Nf)), nb, 2, 1.0, 0, 0)
+        P = _P(Nf)
+        A = _dense(J, nb)
+        expect = P @ np.linalg.solve(P.T @ A @ P, -(P.T @ _vec(R)))
+        assert np.allclose(_vec(dU), expect, rtol=1e-11, atol=1e-12)
+
+
+def test_vcycles_converge(orc):
+    rng = np.random.default_rng(16)
+    N = 64
+    J = _random_banded(N, 3, rng)
+    R = rng.standard_normal((2, N))
+    x = orc.direct_solve1d(J, R, 3)
+    dU = np.zeros((2, N))
+    errs = []
+    for _ in range(6):
+        dU = orc.vcycle1d(J, R, dU, 3, 4, 1.0, 2, 2)
+        errs.append(np.abs(dU - x).max())
+    assert errs[-1] < 1e-10 * np.abs(x).max() and errs[1] < errs[0]
+
+
+# ---------------------------------------------------------------- Appendix A
+
+def test_interp_conservative_and_exact_for_quadratics(orc):
+    Nc = 10
+    p = I.make_problem_1d(2 * Nc, 2, 0.0, 1.0, 9.81, I.bottom_linear(0, 0), I.width_constant(1.0),
+                          (I.BC_EXTRAP, 0, 0), (I.BC_EXTRAP, 0, 0), h_init=1.0, q_init=0.0)
+    pc = orc.problem_levels(p)[1]
+    a, b, c = 0.3, -1.2, 2.5
+    prim = lambda x: a * x + b * x * x / 2 + c * x ** 3 / 3
+    avg = lambda x0, x1, n: (prim(x0 + (np.arange(n) + 1) * (x1 - x0) / n) - prim(x0 + np.arange(n) * (x1 - x0) / n)) * n / (x1 - x0)
+    Uc = np.stack([avg(0, 1, Nc), 2 * avg(0, 1, Nc)])
+    Uf = orc.interp1d(pc, Uc)
+    # conservative: the two children average to the parent (all cells)
+    assert np.allclose(0.5 * (Uf[:, 0::2] + Uf[:, 1::2]), Uc, rtol=1e-15, atol=1e-15)
+    # exact for quadratics away from the ends
+    ex = avg(0, 1, 2 * Nc)
+    assert np.allclose(Uf[0, 2:-2], ex[2:-2], rtol=1e-13, atol=1e-13)
+    assert np.allclose(Uf[1, 2:-2], 2 * ex[2:-2], rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- Newton / NMGM (Alg. 1, 3)
+
+@pytest.mark.slow
+def test_nmgm_j3_j5_same_fixed_point_and_counts(orc):
+    """The converged state does not depend on J3 vs J5 (both solve R = 0), and
+    the Newton counts agree (Section 5.1.1 reports identical counts)."""
+    gold = json.load(open(os.path.join(GOLDEN, "table2_iterations.json")))
+    assert gold["nmgm3"] == gold["nmgm5"]
+    # the paper's setting: Eq. 26, omega = 1, nested 96 -> 768
+    p = I.paper_smooth_subcritical(768, levels=4)
+    _, e3 = orc.solve_problem(p, I.Params1D.for_problem(p, nb=3))
+    _, e5 = orc.solve_problem(p, I.Params1D.for_problem(p, nb=5))
+    assert e3["status"] == 0 and e5["status"] == 0
+    assert e3["iters"] == e5["iters"]
+    # benchmark channel: same fixed point
+    p = I.channel_small(0)
+    prm3 = I.Params1D.for_problem(p, tol=1e-11, nb=3)
+    prm5 = I.Params1D.for_problem(p, tol=1e-11, nb=5)
+    U3, i3 = orc.solve_problem(p, prm3)
+    U5, i5 = orc.solve_problem(p, prm5)
+    assert i3["status"] == 0 and i5["status"] == 0
+    assert np.abs(U3 - U5).max() <= 1e-10 * np.abs(U3).max()
+    # Bernoulli invariants for the smooth subcritical steady state: constant
+    # discharge and (to discretisation error) constant energy
+    q = p.bcl[2]
+    assert np.abs(U3[1] - q).max() < 1e-3 * q
+    xc = p.centres(0)
+    h = U3[0]
+    E = U3[1] ** 2 / (2 * h * h) + p.g * (h + p.b_fn(xc))
+    assert E.max() - E.min() < 5e-3 * E.mean()
+
+
+@pytest.mark.slow
+def test_nmgm_irregular_channel_converges(orc):
+    p = I.channel_irregular(3)
+    prm = I.Params1D.for_problem(p, tol=1e-10, n_max=400)
+    U, info = orc.solve_problem(p, prm)
+    assert info["status"] == 0 and info["res"][0] < 1e-10
+    assert np.all(U[0] > 0)
