@@ -1,0 +1,207 @@
+/*
+ * nswe.h - C ABI of the GB300 (sm_103a) library for the high-order Newton
+ * multigrid method (NMGM) with a simplified Jacobian for steady shallow water
+ * equations (Hu, Li, Wang, Wang, arXiv 2505.10857).
+ *
+ * Scope: the quasi-one-dimensional model of Section 2 (Eq. 3-4), discretised
+ * by the third-order finite-volume WENO scheme of Section 3.1, linearised by
+ * the regularized Newton iteration of Section 3.2 with the finite-difference
+ * Jacobian J5 or its simplified block-tridiagonal form J3 (Section 3.3), and
+ * solved by the geometric multigrid of Section 3.4 inside the nested NMGM of
+ * Algorithm 3. All arithmetic is FP64.
+ *
+ * Conventions
+ *   - Cells and faces are 0-based: cell j of a level with N cells spans faces
+ *     j and j+1; face f sits at x0 + f*dx, dx = (x1-x0)/N.
+ *   - A state (U, R, dU) is two planes of N doubles: H (wet cross-section
+ *     sigma*h) then Q (discharge).
+ *   - A banded block Jacobian with nb blocks per row (nb = 3: offsets -1..1;
+ *     nb = 5: offsets -2..2) is stored as
+ *         J[(k*4 + l*2 + m)*N + j] = (dR_j / dU_{j+k-(nb-1)/2})_{l,m},
+ *     2x2 blocks row-major, l = residual component, m = unknown component;
+ *     blocks reaching outside the grid are zero.
+ *   - Nested level l has N_l = N / 2^l cells (level 0 finest). The multigrid
+ *     hierarchy aggregates pairs of cells (Eq. 15).
+ *   - Unless stated otherwise, array arguments of compute calls are DEVICE
+ *     pointers owned by the caller; calls are asynchronous on the context's
+ *     stream. Problem-creation calls take HOST arrays and copy them.
+ *   - No call aborts, traps or exits. Bad arguments return NSWE_EINVAL; CUDA
+ *     failures return NSWE_ECUDA. Device-side conditions (NaN, non-positive
+ *     depth, non-convergence) are reported through nswe_info.
+ */
+#ifndef NSWE_H
+#define NSWE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NSWE_OK = 0,
+  NSWE_EINVAL = 1,    /* invalid argument (size, pointer, parameter)          */
+  NSWE_ENOMEM = 2,    /* device or host allocation failed                     */
+  NSWE_ECUDA = 3,     /* a CUDA runtime call failed                           */
+  NSWE_ENOTCONV = 4,  /* Newton stopped at n_max with res >= tol              */
+  NSWE_ENAN = 5,      /* NaN/Inf in the residual                              */
+  NSWE_ENEGDEPTH = 6, /* non-positive wet cross-section H in the state        */
+  NSWE_ESINGULAR = 7  /* exactly zero pivot in the coarsest direct solve      */
+} nswe_status;
+
+/* Boundary data (Section 5.1). The paper gives the data, not the discrete
+ * treatment: the library fills two ghost cells per side with one state built
+ * from the data and the adjacent interior cell (sigma_b = width at the
+ * boundary face):
+ *   DISCHARGE: (H, Q) = (H_edge, q)         e.g. upstream discharge
+ *   DEPTH:     (H, Q) = (sigma_b*h, Q_edge)  e.g. downstream depth
+ *   STATE:     (H, Q) = (sigma_b*h, q)       both given (Section 5.1.1)
+ *   EXTRAP:    (H, Q) = (H_edge, Q_edge)                                    */
+typedef enum {
+  NSWE_BC_DISCHARGE = 1,
+  NSWE_BC_DEPTH = 2,
+  NSWE_BC_STATE = 3,
+  NSWE_BC_EXTRAP = 4
+} nswe_bc_kind;
+
+typedef struct {
+  int kind;  /* nswe_bc_kind */
+  double h;  /* depth (DEPTH, STATE)    */
+  double q;  /* discharge (DISCHARGE, STATE) */
+} nswe_bc1d;
+
+#define NSWE_MAX_LEVELS 16
+#define NSWE_JAC_SIMPLIFIED 3 /* J3: block tridiagonal (Section 3.3) */
+#define NSWE_JAC_FULL 5       /* J5: block pentadiagonal             */
+
+/* Solver parameters (Section 5). nswe_params_default fills the paper's 1D
+ * values: alpha 3, tau 0.6, omega 1, nu1 = nu2 = nu3 = 2, tol 1e-11. */
+typedef struct {
+  double alpha;   /* regularization weight, Eq. 13                          */
+  double tau;     /* Newton damping, Eq. 14                                 */
+  double omega;   /* SOR relaxation, Eq. 19                                 */
+  double tol;     /* stop when res < tol (Algorithms 1, 3)                  */
+  int nu1, nu2;   /* pre/post smoothing steps per level (Algorithm 2)       */
+  int nu3;        /* V-cycles per Newton step (Algorithm 3)                 */
+  int n_max;      /* Newton iteration cap per nested level                  */
+  int jacobian;   /* NSWE_JAC_SIMPLIFIED (J3) or NSWE_JAC_FULL (J5)         */
+  int nest_start; /* nested level the solve starts on; <0: coarsest (Alg. 3)*/
+  double eps[NSWE_MAX_LEVELS]; /* FD perturbation per nested level, Eq. 12  */
+} nswe_params;
+
+/* Per-solve record filled by nswe_newton_solve*. */
+typedef struct {
+  int status;                        /* nswe_status of the finest level    */
+  int iters[NSWE_MAX_LEVELS];        /* Newton iterations per nested level */
+  double res[NSWE_MAX_LEVELS];       /* final res per nested level         */
+  int level_status[NSWE_MAX_LEVELS]; /* nswe_status per nested level       */
+  int total_iters;
+  int vcycles;
+} nswe_info;
+
+typedef struct nswe_ctx_s *nswe_ctx;
+typedef struct nswe_prob_s *nswe_prob;
+
+const char *nswe_status_str(int status);
+
+/* Fills p with the paper's one-dimensional defaults for a problem of N cells
+ * and `levels` multigrid levels; eps per level from the paper's values
+ * (0.2/0.15/0.1/0.05 at N = 96/192/384/768, log2 progression between,
+ * clipped to [0.05, 0.2]). */
+nswe_status nswe_params_default(nswe_params *p, int N, int levels);
+
+/* Context: binds a device and a CUDA stream (cudaStream_t passed as void*,
+ * may be NULL for the legacy default stream, or a stream owned by the
+ * caller, e.g. PyTorch's). Owns nothing the caller passes in. */
+nswe_status nswe_ctx_create(nswe_ctx *out, int device, void *stream);
+nswe_status nswe_ctx_set_stream(nswe_ctx ctx, void *stream);
+nswe_status nswe_ctx_destroy(nswe_ctx ctx);
+
+/* One-dimensional problem (Eq. 3-4) on [x0, x1] with N cells and `levels`
+ * nested/multigrid levels (N divisible by 2^(levels-1), every level >= 4
+ * cells, coarsest level at most 128 cells for the direct solve). HOST arrays,
+ * copied to device memory owned by the problem:
+ *   sigma_face[N+1]      channel width sigma at the finest faces;
+ *   gauss_geom           for l = 0..levels-1 in turn, [3][2][N_l]:
+ *                        sigma, d sigma/dx and db/dx at the two Gauss points
+ *                        x_j - dx_l/(2 sqrt 3) and x_j + dx_l/(2 sqrt 3)
+ *                        of each cell j of level l (Eq. 9);
+ *   left, right          boundary data (nswe_bc1d).
+ * The problem also owns the device workspace of the solver (Jacobians,
+ * multigrid hierarchy, coarsest factorisation). */
+nswe_status nswe_prob_create_1d(nswe_ctx ctx, nswe_prob *out, int N, int levels,
+                                double x0, double x1, double g,
+                                const double *sigma_face,
+                                const double *gauss_geom,
+                                const nswe_bc1d *left, const nswe_bc1d *right);
+/* Re-uploads geometry and boundary data of an existing problem (same N and
+ * levels) from HOST arrays, asynchronously on the context stream; the host
+ * arrays must stay valid until the stream reaches this point (pinned memory
+ * gives a true asynchronous copy). */
+nswe_status nswe_prob_set_geometry_1d(nswe_ctx ctx, nswe_prob prob,
+                                      const double *sigma_face,
+                                      const double *gauss_geom,
+                                      const nswe_bc1d *left,
+                                      const nswe_bc1d *right);
+nswe_status nswe_prob_destroy(nswe_prob prob);
+int nswe_prob_cells(nswe_prob prob, int level);
+
+/* Residual R_j = F_{j+1/2} - F_{j-1/2} - S_j (Eq. 10; not divided by dx)
+ * of state U on nested level `level`: WENO3 reconstruction (Eq. 7-8, with
+ * the linear weights that give third order), HLL flux, two-point Gauss
+ * source of the cubic through four interface values (Eq. 9).
+ *   U[2][N_l] in, R[2][N_l] out, res_l1 (device scalar, may be NULL) out =
+ *   (1/N_l) sum_j ||R_j||_1 (Algorithm 1, step 7). */
+nswe_status nswe_residual(nswe_ctx ctx, nswe_prob prob, int level,
+                          const double *U, double *R, double *res_l1);
+
+/* Regularized finite-difference Jacobian (Eq. 12-13) of the residual at U:
+ * one-sided differences of the local residual with U_i perturbed by eps in
+ * one component (ghost cells follow the perturbed interior cell), plus
+ * alpha*||R_j||_1 on the diagonal block. The simplified call keeps the three
+ * central blocks (J3, Section 3.3); the full call keeps all five (J5).
+ *   U[2][N_l] in; R[2][N_l] out (the residual at U); J[nb][4][N_l] out;
+ *   res_l1 (device scalar, may be NULL) out. */
+nswe_status nswe_jacobian_simplified(nswe_ctx ctx, nswe_prob prob, int level,
+                                     const double *U, double eps, double alpha,
+                                     double *R, double *J, double *res_l1);
+nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level,
+                               const double *U, double eps, double alpha,
+                               double *R, double *J, double *res_l1);
+
+/* One multigrid V-cycle (Algorithm 2) for J dU = -R on nested level `level`
+ * with the hierarchy level..levels-1: Galerkin coarse operators (Eq. 17),
+ * nu1/nu2 symmetric multicolour block-SOR steps (Eq. 19; colours j mod C,
+ * C = 2 for J3 and coarse levels, 3 for J5, visited 0..C-1 then C-1..0),
+ * defect restriction (Eq. 17), prolongation (Eq. 18), and an exact solve by
+ * LU with partial pivoting on the coarsest level.
+ *   nb = 3 or 5; J[nb][4][N_l], R[2][N_l] in; dU[2][N_l] in/out. */
+nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb,
+                           const double *J, const double *R, double *dU,
+                           const nswe_params *params);
+
+/* Nested NMGM (Algorithm 3). Starts on level s = params->nest_start (or the
+ * coarsest): Newton iterations with a direct solve on the coarsest level,
+ * with nu3 V-cycles from dU = 0 on other levels; damped update (Eq. 14);
+ * then App. A interpolation to the next finer level, until level 0.
+ *   U0[2][N_s] in (initial guess on level s), U[2][N_0] out.
+ *   info (HOST pointer, may be NULL) is filled; the call synchronises the
+ *   context stream when info != NULL. Returns the finest level's status. */
+nswe_status nswe_newton_solve(nswe_ctx ctx, nswe_prob prob, const double *U0,
+                              double *U, const nswe_params *params,
+                              nswe_info *info);
+
+/* Batched Algorithm 3: `count` independent problems solved by one launch
+ * (one thread block per problem). probs[], U0s[], Us[] are HOST arrays of
+ * count entries (U0s[i], Us[i] device pointers as in nswe_newton_solve);
+ * infos (HOST, may be NULL) receives count records and makes the call
+ * synchronous. */
+nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count,
+                                    const nswe_prob *probs,
+                                    const double *const *U0s,
+                                    double *const *Us,
+                                    const nswe_params *params,
+                                    nswe_info *infos);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,57 @@
+// Internal declarations shared by the host side of the library and its CUDA
+// kernels: the device-resident problem description and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/nswe.h"
+
+namespace nswe {
+
+constexpr int kThreads = 256;      // threads per block of every 1D kernel
+constexpr int kMaxCoarse = 128;    // max cells of the coarsest level (direct solve)
+constexpr int kMaxDense = 2 * kMaxCoarse;
+constexpr int kMaxKl = 5;          // scalar lower bandwidth of J5 (2*2+1)
+constexpr int kLdab = 3 * kMaxKl + 1;  // band storage rows for LU with pivoting
+
+// One nested / multigrid level of a 1D problem. Geometry is read-only input;
+// the rest is solver workspace owned by the problem.
+struct LevelDev {
+  int N;
+  double dx;
+  const double *sf;  // [N+1] width at faces
+  const double *gq;  // [3][2][N] sigma, sigma_x, b_x at the two Gauss points
+  double *U;         // [2][N] nested-level solution
+  double *R;         // [2][N] residual / multigrid right-hand side
+  double *J;         // [5][4][N] Jacobian (nb blocks used)
+  double *Dinv;      // [4][N] inverse diagonal blocks
+  double *dU;        // [2][N] multigrid correction
+};
+
+struct ProbDev {
+  int levels;
+  double g;
+  int bl, br;        // boundary kinds (nswe_bc_kind)
+  double blh, blq, brh, brq;
+  LevelDev lev[NSWE_MAX_LEVELS];
+};
+
+// One solve of a batch.
+struct SolveTask {
+  const ProbDev *prob;
+  const double *U0;
+  double *U;
+  nswe_info *info;   // device record
+};
+
+// Kernel launchers (stream-ordered, return cudaGetLastError()).
+cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U, double *R, double *res,
+                            double *partials, cudaStream_t s);
+cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
+                            double alpha, double *R, double *J, double *res, double *partials,
+                            cudaStream_t s);
+cudaError_t launch_vcycle(const ProbDev *p, int level, int nb, const double *J, const double *R, double *dU,
+                          const nswe_params &prm, int *status, cudaStream_t s);
+cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, cudaStream_t s);
+
+}  // namespace nswe

@@ -1,0 +1,752 @@
+// CUDA kernels (sm_103a) of the 1D NMGM: WENO3 finite-volume residual,
+// regularized FD Jacobian J3/J5, geometric multigrid V-cycle with
+// multicolour block SOR, and the nested Newton solve (Algorithm 3), all FP64.
+//
+// Execution model: every building block is a "CTA-level" routine that loops
+// over its work items with a block-wide stride, so the same code serves the
+// standalone grid kernels (residual, Jacobian: many blocks per problem) and
+// the persistent solve kernel, where one thread block runs a whole nested
+// solve of one problem with __syncthreads() between phases and no host
+// round trip. Problem data and workspace stay in device memory (L2 resident
+// for the 1D sizes); the coarsest factorisation lives in shared memory.
+#include <cmath>
+
+#include "nswe_internal.h"
+
+namespace nswe {
+namespace {
+
+constexpr double kZeta = 1e-6;  // WENO epsilon (Section 3.1)
+
+// Lagrange weights of the cubic through t = -3/2, -1/2, 1/2, 3/2 evaluated at
+// the Gauss points t = -/+ 1/(2 sqrt 3) (Eq. 9). With t^2 = 1/12 the basis
+// reduces to (t - 3/2)/36, -(13/12)(t - 1/2), (13/12)(t + 1/2), -(t + 3/2)/36.
+constexpr double kGs = 0.28867513459481288225;  // 1/(2 sqrt 3)
+__device__ constexpr double kLag[2][4] = {
+    {(-kGs - 1.5) / 36.0, -(13.0 / 12.0) * (-kGs - 0.5), (13.0 / 12.0) * (-kGs + 0.5), -(-kGs + 1.5) / 36.0},
+    {(kGs - 1.5) / 36.0, -(13.0 / 12.0) * (kGs - 0.5), (13.0 / 12.0) * (kGs + 0.5), -(kGs + 1.5) / 36.0}};
+
+struct Geo {
+  int N;
+  double dx, g;
+  const double *sf;
+  const double *gq;
+  int bl, br;
+  double blh, blq, brh, brq;
+};
+
+__device__ __forceinline__ Geo make_geo(const ProbDev &P, int l) {
+  Geo G;
+  G.N = P.lev[l].N;
+  G.dx = P.lev[l].dx;
+  G.g = P.g;
+  G.sf = P.lev[l].sf;
+  G.gq = P.lev[l].gq;
+  G.bl = P.bl;
+  G.br = P.br;
+  G.blh = P.blh;
+  G.blq = P.blq;
+  G.brh = P.brh;
+  G.brq = P.brq;
+  return G;
+}
+
+// Ghost state from the boundary data and the adjacent interior cell.
+__device__ __forceinline__ void ghost(int kind, double bh, double bq, double sb, double He, double Qe,
+                                      double &H, double &Q) {
+  if (kind == NSWE_BC_DISCHARGE) {
+    H = He;
+    Q = bq;
+  } else if (kind == NSWE_BC_DEPTH) {
+    H = sb * bh;
+    Q = Qe;
+  } else if (kind == NSWE_BC_STATE) {
+    H = sb * bh;
+    Q = bq;
+  } else {
+    H = He;
+    Q = Qe;
+  }
+}
+
+// WENO3 in one cell from averages a, b, c (cells k-1, k, k+1), Eq. 7-8 with
+// the linear weights (1/3, 2/3) for U^+_{k-1/2} and (2/3, 1/3) for
+// U^-_{k+1/2}. With s_r = (zeta + beta_r)^2 the normalised weights are
+// w0 = s1/(s1 + 2 s0), w1 = 2 s0/(s1 + 2 s0) and v0 = 2 s1/(2 s1 + s0),
+// v1 = s0/(2 s1 + s0): two divisions instead of eight.
+__device__ __forceinline__ void weno3(double a, double b, double c, double &up, double &um) {
+  double d0 = c - b, d1 = b - a;
+  double e0 = kZeta + d0 * d0, e1 = kZeta + d1 * d1;
+  double s0 = e0 * e0, s1 = e1 * e1;
+  double p0 = 1.5 * b - 0.5 * c, p1 = 0.5 * a + 0.5 * b;   // U^(0), U^(1) at k-1/2
+  double q0 = 0.5 * b + 0.5 * c, q1 = -0.5 * a + 1.5 * b;  // U^(0), U^(1) at k+1/2
+  up = (s1 * p0 + 2.0 * s0 * p1) / (s1 + 2.0 * s0);
+  um = (2.0 * s1 * q0 + s0 * q1) / (2.0 * s1 + s0);
+}
+
+// HLL flux at a face of width sig: S_L = min(u_L - c_L, u_R - c_R),
+// S_R = max(u_L + c_L, u_R + c_R), c = sqrt(g H / sig); physical flux
+// F = (Q, Q^2/H + g H^2/(2 sig)) (Eq. 4).
+__device__ __forceinline__ void hll(double HL, double QL, double HR, double QR, double sig, double g,
+                                    double &F0, double &F1) {
+  double isg = 1.0 / sig;
+  double iHL = 1.0 / HL, iHR = 1.0 / HR;
+  double uL = QL * iHL, uR = QR * iHR;
+  double hL = HL * isg, hR = HR * isg;
+  double cL = sqrt(g * hL), cR = sqrt(g * hR);
+  double FL1 = QL * uL + 0.5 * g * HL * hL;
+  double FR1 = QR * uR + 0.5 * g * HR * hR;
+  double SL = fmin(uL - cL, uR - cR);
+  double SR = fmax(uL + cL, uR + cR);
+  if (SL >= 0.0) {
+    F0 = QL;
+    F1 = FL1;
+  } else if (SR <= 0.0) {
+    F0 = QR;
+    F1 = FR1;
+  } else {
+    double iw = 1.0 / (SR - SL);
+    F0 = (SR * QL - SL * QR + SL * SR * (HR - HL)) * iw;
+    F1 = (SR * FL1 - SL * FR1 + SL * SR * (QR - QL)) * iw;
+  }
+}
+
+// Five-cell window j-2..j+2 of one residual evaluation.
+struct Win {
+  double H[5], Q[5];
+};
+
+__device__ __forceinline__ void load_win(const Geo &G, const double *H, const double *Q, int j, Win &w) {
+#pragma unroll
+  for (int p = 0; p < 5; ++p) {
+    int k = min(max(j - 2 + p, 0), G.N - 1);  // clamped: ghosts are filled later
+    w.H[p] = H[k];
+    w.Q[p] = Q[k];
+  }
+}
+
+// Ghost positions of the window take the boundary state built from the
+// window's (possibly perturbed) edge cell.
+__device__ __forceinline__ void fill_ghosts(const Geo &G, int j, Win &w) {
+  if (j < 2) {
+    double He = (j == 0) ? w.H[2] : w.H[1];
+    double Qe = (j == 0) ? w.Q[2] : w.Q[1];
+    double Hg, Qg;
+    ghost(G.bl, G.blh, G.blq, G.sf[0], He, Qe, Hg, Qg);
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+      if (j - 2 + p < 0) {
+        w.H[p] = Hg;
+        w.Q[p] = Qg;
+      }
+  }
+  if (j > G.N - 3) {
+    double He = (j == G.N - 1) ? w.H[2] : w.H[3];
+    double Qe = (j == G.N - 1) ? w.Q[2] : w.Q[3];
+    double Hg, Qg;
+    ghost(G.br, G.brh, G.brq, G.sf[G.N], He, Qe, Hg, Qg);
+#pragma unroll
+    for (int p = 3; p < 5; ++p)
+      if (j - 2 + p >= G.N) {
+        w.H[p] = Hg;
+        w.Q[p] = Qg;
+      }
+  }
+}
+
+// Local residual R_j (Eq. 10) from a filled window.
+__device__ __forceinline__ void local_residual(const Geo &G, int j, const Win &w, double &R0, double &R1) {
+  double upH[3], umH[3], upQ[3], umQ[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    weno3(w.H[p], w.H[p + 1], w.H[p + 2], upH[p], umH[p]);
+    weno3(w.Q[p], w.Q[p + 1], w.Q[p + 2], upQ[p], umQ[p]);
+  }
+  double Fr0, Fr1, Fl0, Fl1;
+  hll(umH[1], umQ[1], upH[2], upQ[2], G.sf[j + 1], G.g, Fr0, Fr1);
+  hll(umH[0], umQ[0], upH[1], upQ[1], G.sf[j], G.g, Fl0, Fl1);
+  double S = 0.0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    double Hh = kLag[q][0] * upH[0] + kLag[q][1] * upH[1] + kLag[q][2] * umH[1] + kLag[q][3] * umH[2];
+    double sig = G.gq[(0 * 2 + q) * G.N + j];
+    double sigx = G.gq[(1 * 2 + q) * G.N + j];
+    double bx = G.gq[(2 * 2 + q) * G.N + j];
+    double h = Hh / sig;
+    S += 0.5 * G.g * h * h * sigx - G.g * sig * h * bx;
+  }
+  S *= 0.5 * G.dx;
+  R0 = Fr0 - Fl0;
+  R1 = Fr1 - Fl1 - S;
+}
+
+// ----------------------------------------------------------------------------
+// Block-level helpers.
+
+// Fixed-order block sum (warp shuffles, then warps in index order).
+__device__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    red[32] = s;
+  }
+  __syncthreads();
+  double s = red[32];
+  __syncthreads();
+  return s;
+}
+
+// Residual of cells [first, N) with stride; returns sum_j ||R_j||_1.
+__device__ double residual_cells(const Geo &G, const double *U, double *R, int first, int stride) {
+  const double *H = U, *Q = U + G.N;
+  double acc = 0.0;
+  for (int j = first; j < G.N; j += stride) {
+    Win w;
+    load_win(G, H, Q, j, w);
+    fill_ghosts(G, j, w);
+    double R0, R1;
+    local_residual(G, j, w, R0, R1);
+    R[j] = R0;
+    R[G.N + j] = R1;
+    acc += fabs(R0) + fabs(R1);
+  }
+  return acc;
+}
+
+// One Jacobian work item: block k (offset k - hw) of row j, both columns
+// (Eq. 12), with the regularization on the diagonal block (Eq. 13).
+__device__ __forceinline__ void jacobian_item(const Geo &G, const double *U, int j, int k, int nb, double eps,
+                                              double alpha, const double *R, double *J) {
+  const int N = G.N, hw = (nb - 1) / 2, d = k - hw, i = j + d;
+  if (i < 0 || i >= N) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) J[(k * 4 + e) * N + j] = 0.0;
+    return;
+  }
+  Win w0;
+  load_win(G, U, U + N, j, w0);
+  const double R0 = R[j], R1 = R[N + j];
+  const double reg = (d == 0) ? alpha * (fabs(R0) + fabs(R1)) : 0.0;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    Win w = w0;
+#pragma unroll
+    for (int p = 0; p < 5; ++p)
+      if (p == 2 + d) {
+        if (m == 0) w.H[p] += eps;
+        else w.Q[p] += eps;
+      }
+    fill_ghosts(G, j, w);
+    double P0, P1;
+    local_residual(G, j, w, P0, P1);
+    double v0 = (P0 - R0) / eps, v1 = (P1 - R1) / eps;
+    if (m == 0) v0 += reg;
+    else v1 += reg;
+    J[(k * 4 + 0 * 2 + m) * N + j] = v0;
+    J[(k * 4 + 1 * 2 + m) * N + j] = v1;
+  }
+}
+
+__device__ void jacobian_cells(const Geo &G, const double *U, int nb, double eps, double alpha, const double *R,
+                               double *J, int first, int stride) {
+  const int items = G.N * nb;
+  for (int it = first; it < items; it += stride) jacobian_item(G, U, it / nb, it % nb, nb, eps, alpha, R, J);
+}
+
+// Inverse of the diagonal 2x2 blocks.
+__device__ void dinv_cells(int N, int nb, const double *J, double *Dinv, int first, int stride) {
+  const int hw = (nb - 1) / 2;
+  for (int j = first; j < N; j += stride) {
+    double a = J[(hw * 4 + 0) * N + j], b = J[(hw * 4 + 1) * N + j];
+    double c = J[(hw * 4 + 2) * N + j], d = J[(hw * 4 + 3) * N + j];
+    double det = a * d - b * c;
+    Dinv[0 * N + j] = d / det;
+    Dinv[1 * N + j] = -b / det;
+    Dinv[2 * N + j] = -c / det;
+    Dinv[3 * N + j] = a / det;
+  }
+}
+
+// Galerkin coarse operator (Eq. 17): sums of fine blocks over aggregate pairs.
+__device__ void coarse_op_cells(int Nf, int nbf, const double *Jf, int Nc, double *Jc, int first, int stride) {
+  const int hf = (nbf - 1) / 2;
+  for (int j = first; j < Nc; j += stride) {
+    double a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};
+    for (int a = 0; a < 2; ++a) {
+      int xi = 2 * j + a;
+      if (xi >= Nf) break;
+      for (int k = 0; k < nbf; ++k) {
+        int eta = xi + k - hf;
+        if (eta < 0 || eta >= Nf) continue;
+        int kc = eta / 2 - j + 1;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          double v = Jf[(k * 4 + e) * Nf + xi];
+          if (kc == 0) a0[e] += v;
+          else if (kc == 1) a1[e] += v;
+          else a2[e] += v;
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      Jc[(0 * 4 + e) * Nc + j] = a0[e];
+      Jc[(1 * 4 + e) * Nc + j] = a1[e];
+      Jc[(2 * 4 + e) * Nc + j] = a2[e];
+    }
+  }
+}
+
+// Block SOR update (Eq. 19) of the cells of one colour (j mod C == col).
+__device__ void sor_colour(int N, int nb, const double *J, const double *Dinv, const double *R, double *dU,
+                           double omega, int C, int col, int first, int stride) {
+  const int hw = (nb - 1) / 2;
+  for (int j = col + C * first; j < N; j += C * stride) {
+    double r0 = R[j], r1 = R[N + j];
+    for (int k = 0; k < nb; ++k) {
+      int i = j + k - hw;
+      if (k == hw || i < 0 || i >= N) continue;
+      double x0 = dU[i], x1 = dU[N + i];
+      r0 += J[(k * 4 + 0) * N + j] * x0 + J[(k * 4 + 1) * N + j] * x1;
+      r1 += J[(k * 4 + 2) * N + j] * x0 + J[(k * 4 + 3) * N + j] * x1;
+    }
+    double t0 = Dinv[0 * N + j] * r0 + Dinv[1 * N + j] * r1;
+    double t1 = Dinv[2 * N + j] * r0 + Dinv[3 * N + j] * r1;
+    dU[j] = (1.0 - omega) * dU[j] - omega * t0;
+    dU[N + j] = (1.0 - omega) * dU[N + j] - omega * t1;
+  }
+}
+
+// Defect restriction (Eq. 17) and zero coarse correction.
+__device__ void restrict_cells(int Nf, int nb, const double *J, const double *R, const double *dU, int Nc,
+                               double *Rc, double *dUc, int first, int stride) {
+  const int hw = (nb - 1) / 2;
+  for (int j = first; j < Nc; j += stride) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int a = 0; a < 2; ++a) {
+      int xi = 2 * j + a;
+      if (xi >= Nf) break;
+      double r0 = R[xi], r1 = R[Nf + xi];
+      for (int k = 0; k < nb; ++k) {
+        int eta = xi + k - hw;
+        if (eta < 0 || eta >= Nf) continue;
+        double x0 = dU[eta], x1 = dU[Nf + eta];
+        r0 += J[(k * 4 + 0) * Nf + xi] * x0 + J[(k * 4 + 1) * Nf + xi] * x1;
+        r1 += J[(k * 4 + 2) * Nf + xi] * x0 + J[(k * 4 + 3) * Nf + xi] * x1;
+      }
+      s0 += r0;
+      s1 += r1;
+    }
+    Rc[j] = s0;
+    Rc[Nc + j] = s1;
+    dUc[j] = 0.0;
+    dUc[Nc + j] = 0.0;
+  }
+}
+
+// Prolongation (Eq. 18).
+__device__ void prolong_cells(int Nf, double *dU, int Nc, const double *dUc, int first, int stride) {
+  for (int xi = first; xi < Nf; xi += stride) {
+    dU[xi] += dUc[xi / 2];
+    dU[Nf + xi] += dUc[Nc + xi / 2];
+  }
+}
+
+// App. A (Eq. A.2): fine averages from the coarse quadratic; the domain ends
+// use the coarse level's ghost states.
+__device__ void interp_cells(const Geo &Gc, const double *Uc, double *Uf, int first, int stride) {
+  const int Nc = Gc.N, Nf = 2 * Nc;
+  const double *Hc = Uc, *Qc = Uc + Nc;
+  for (int c = first; c < Nc; c += stride) {
+    double hm, qm, hp, qp;
+    double h0 = Hc[c], q0 = Qc[c];
+    if (c > 0) {
+      hm = Hc[c - 1];
+      qm = Qc[c - 1];
+    } else {
+      ghost(Gc.bl, Gc.blh, Gc.blq, Gc.sf[0], Hc[0], Qc[0], hm, qm);
+    }
+    if (c < Nc - 1) {
+      hp = Hc[c + 1];
+      qp = Qc[c + 1];
+    } else {
+      ghost(Gc.br, Gc.brh, Gc.brq, Gc.sf[Nc], Hc[Nc - 1], Qc[Nc - 1], hp, qp);
+    }
+    Uf[2 * c] = hm / 8.0 + h0 - hp / 8.0;
+    Uf[2 * c + 1] = -hm / 8.0 + h0 + hp / 8.0;
+    Uf[Nf + 2 * c] = qm / 8.0 + q0 - qp / 8.0;
+    Uf[Nf + 2 * c + 1] = -qm / 8.0 + q0 + qp / 8.0;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Coarsest direct solve: LU with partial pivoting (ties to the lowest row) of
+// the block-banded system in LAPACK-style band storage, by one warp. Unknown
+// u = 2j + m. A banded matrix keeps its zeros outside the band through the
+// elimination, so this performs the same pivots and updates as a dense LU.
+
+struct Band {
+  double *ab;  // [ldab][n]
+  int *piv;    // [n]
+  double *x;   // [n]
+  int n, kl, ldab;
+  __device__ __forceinline__ double &A(int r, int c) const { return ab[(2 * kl + r - c) * n + c]; }
+};
+
+// Assemble the band matrix from J (all threads), then factor (warp 0).
+// Returns true if a pivot was exactly zero (all threads).
+__device__ bool band_factor(Band &B, int N, int nb, const double *J) {
+  const int hw = (nb - 1) / 2;
+  B.n = 2 * N;
+  B.kl = 2 * hw + 1;
+  B.ldab = 3 * B.kl + 1;
+  const int n = B.n, kl = B.kl;
+  for (int t = threadIdx.x; t < B.ldab * n; t += blockDim.x) B.ab[t] = 0.0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * nb * 4; t += blockDim.x) {
+    int j = t % N, ke = t / N, k = ke / 4, e = ke % 4, l = e / 2, m = e % 2;
+    int i = j + k - hw;
+    if (i < 0 || i >= N) continue;
+    B.A(2 * j + l, 2 * i + m) = J[(k * 4 + e) * N + j];
+  }
+  __syncthreads();
+  __shared__ int s_sing;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int sing = 0;
+    for (int k = 0; k < n; ++k) {
+      const int imax = min(n - 1, k + kl), cmax = min(n - 1, k + 2 * kl);
+      double v = -1.0;
+      int idx = n;
+      if (k + lane <= imax) {
+        v = fabs(B.A(k + lane, k));
+        idx = k + lane;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, v, o);
+        int oi = __shfl_down_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) {
+          v = ov;
+          idx = oi;
+        }
+      }
+      const int p = __shfl_sync(0xffffffffu, idx, 0);
+      if (lane == 0) B.piv[k] = p;
+      if (p != k)
+        for (int c = k + lane; c <= cmax; c += 32) {
+          double t = B.A(k, c);
+          B.A(k, c) = B.A(p, c);
+          B.A(p, c) = t;
+        }
+      __syncwarp();
+      const double pv = B.A(k, k);
+      if (pv == 0.0) sing = 1;
+      for (int i = k + 1 + lane; i <= imax; i += 32) B.A(i, k) = B.A(i, k) / pv;
+      __syncwarp();
+      const int ni = imax - k, nc = cmax - k;
+      for (int t = lane; t < ni * nc; t += 32) {
+        int i = k + 1 + t / nc, c = k + 1 + t % nc;
+        B.A(i, c) -= B.A(i, k) * B.A(k, c);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) s_sing = sing;
+  }
+  __syncthreads();
+  return s_sing != 0;
+}
+
+// dU = -J^{-1} R with the stored factors (warp 0 works, all threads call).
+__device__ void band_solve(const Band &B, int N, const double *R, double *dU) {
+  const int n = B.n, kl = B.kl;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    B.x[2 * t] = -R[t];
+    B.x[2 * t + 1] = -R[N + t];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int k = 0; k < n; ++k) {
+      const int p = B.piv[k];
+      if (p != k && lane == 0) {
+        double t = B.x[k];
+        B.x[k] = B.x[p];
+        B.x[p] = t;
+      }
+      __syncwarp();
+      const double xk = B.x[k];
+      for (int i = k + 1 + lane; i <= min(n - 1, k + kl); i += 32) B.x[i] -= B.A(i, k) * xk;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      for (int i = n - 1; i >= 0; --i) {
+        double s = B.x[i];
+        for (int c = i + 1; c <= min(n - 1, i + 2 * kl); ++c) s -= B.A(i, c) * B.x[c];
+        B.x[i] = s / B.A(i, i);
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    dU[t] = B.x[2 * t];
+    dU[N + t] = B.x[2 * t + 1];
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// Multigrid hierarchy view: level l0 (the system being solved) uses the
+// caller's J/R/dU, levels l0+1..L the problem's workspace.
+struct MG {
+  int l0, L;
+  int N[NSWE_MAX_LEVELS], nb[NSWE_MAX_LEVELS];
+  double *J[NSWE_MAX_LEVELS], *Dinv[NSWE_MAX_LEVELS], *R[NSWE_MAX_LEVELS], *dU[NSWE_MAX_LEVELS];
+};
+
+__device__ void mg_bind(MG &mg, const ProbDev &P, int l0, int nb0, const double *J, const double *R, double *dU) {
+  mg.l0 = l0;
+  mg.L = P.levels - 1;
+  for (int l = l0; l <= mg.L; ++l) {
+    mg.N[l] = P.lev[l].N;
+    mg.nb[l] = (l == l0) ? nb0 : 3;
+    mg.J[l] = (l == l0) ? const_cast<double *>(J) : P.lev[l].J;
+    mg.R[l] = (l == l0) ? const_cast<double *>(R) : P.lev[l].R;
+    mg.dU[l] = (l == l0) ? dU : P.lev[l].dU;
+    mg.Dinv[l] = P.lev[l].Dinv;
+  }
+}
+
+// Coarse operators, diagonal inverses and the coarsest factorisation; done
+// once per Newton step since J is fixed during its V-cycles.
+__device__ bool mg_setup(const MG &mg, Band &B) {
+  for (int l = mg.l0 + 1; l <= mg.L; ++l) {
+    coarse_op_cells(mg.N[l - 1], mg.nb[l - 1], mg.J[l - 1], mg.N[l], mg.J[l], threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  for (int l = mg.l0; l < mg.L; ++l) dinv_cells(mg.N[l], mg.nb[l], mg.J[l], mg.Dinv[l], threadIdx.x, blockDim.x);
+  return band_factor(B, mg.N[mg.L], mg.nb[mg.L], mg.J[mg.L]);
+}
+
+__device__ void sor_step(const MG &mg, int l, double omega) {
+  const int nb = mg.nb[l], C = (nb - 1) / 2 + 1;
+  for (int pass = 0; pass < 2 * C; ++pass) {
+    int col = pass < C ? pass : 2 * C - 1 - pass;
+    sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, col, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+}
+
+// Algorithm 2 from level l0, unrolled over levels.
+__device__ void mg_vcycle(const MG &mg, const Band &B, const nswe_params &prm) {
+  for (int l = mg.l0; l < mg.L; ++l) {
+    for (int s = 0; s < prm.nu1; ++s) sor_step(mg, l, prm.omega);
+    restrict_cells(mg.N[l], mg.nb[l], mg.J[l], mg.R[l], mg.dU[l], mg.N[l + 1], mg.R[l + 1], mg.dU[l + 1],
+                   threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  band_solve(B, mg.N[mg.L], mg.R[mg.L], mg.dU[mg.L]);
+  for (int l = mg.L - 1; l >= mg.l0; --l) {
+    prolong_cells(mg.N[l], mg.dU[l], mg.N[l + 1], mg.dU[l + 1], threadIdx.x, blockDim.x);
+    __syncthreads();
+    for (int s = 0; s < prm.nu2; ++s) sor_step(mg, l, prm.omega);
+  }
+}
+
+struct SmemBand {
+  double ab[kLdab * kMaxDense];
+  int piv[kMaxDense];
+  double x[kMaxDense];
+};
+
+__device__ __forceinline__ Band band_view(SmemBand &s) {
+  Band B;
+  B.ab = s.ab;
+  B.piv = s.piv;
+  B.x = s.x;
+  B.n = B.kl = B.ldab = 0;
+  return B;
+}
+
+// ----------------------------------------------------------------------------
+// Kernels.
+
+__global__ void __launch_bounds__(kThreads) k_residual(const ProbDev *P, int level, const double *U, double *R,
+                                                       double *partials) {
+  __shared__ double red[33];
+  Geo G = make_geo(*P, level);
+  double acc = residual_cells(G, U, R, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_finish_res(const double *partials, int n, int N, double *res) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partials[i];
+    *res = s / N;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_jacobian(const ProbDev *P, int level, int nb, const double *U,
+                                                       double eps, double alpha, const double *R, double *J) {
+  Geo G = make_geo(*P, level);
+  jacobian_cells(G, U, nb, eps, alpha, R, J, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level, int nb, const double *J,
+                                                     const double *R, double *dU, nswe_params prm, int *status) {
+  __shared__ SmemBand sb;
+  MG mg;
+  mg_bind(mg, *P, level, nb, J, R, dU);
+  Band B = band_view(sb);
+  bool sing = mg_setup(mg, B);
+  __syncthreads();
+  mg_vcycle(mg, B, prm);
+  if (threadIdx.x == 0) *status = sing ? NSWE_ESINGULAR : NSWE_OK;
+}
+
+// Algorithm 3 for one problem per thread block.
+__global__ void __launch_bounds__(kThreads) k_solve(const SolveTask *tasks, nswe_params prm) {
+  __shared__ SmemBand sb;
+  __shared__ double red[33];
+  const SolveTask task = tasks[blockIdx.x];
+  const ProbDev &P = *task.prob;
+  const int L = P.levels - 1;
+  const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
+  const int nb = prm.jacobian == NSWE_JAC_FULL ? 5 : 3;
+  Band B = band_view(sb);
+
+  int iters[NSWE_MAX_LEVELS], lstat[NSWE_MAX_LEVELS];
+  double lres[NSWE_MAX_LEVELS];
+  for (int l = 0; l < NSWE_MAX_LEVELS; ++l) {
+    iters[l] = 0;
+    lstat[l] = NSWE_OK;
+    lres[l] = 0.0;
+  }
+  int vcycles = 0, total = 0, fatal = 0;
+
+  {
+    const int Ns = P.lev[s0].N;
+    for (int t = threadIdx.x; t < 2 * Ns; t += blockDim.x) P.lev[s0].U[t] = task.U0[t];
+    __syncthreads();
+  }
+
+  for (int l = s0; l >= 0 && !fatal; --l) {
+    const LevelDev &Lv = P.lev[l];
+    const Geo G = make_geo(P, l);
+    const int N = G.N;
+    if (l < s0) {
+      interp_cells(make_geo(P, l + 1), P.lev[l + 1].U, Lv.U, threadIdx.x, blockDim.x);
+      __syncthreads();
+    }
+    double res = block_sum(residual_cells(G, Lv.U, Lv.R, threadIdx.x, blockDim.x), red) / N;
+    int n = 0, st = NSWE_OK;
+    while (true) {
+      jacobian_cells(G, Lv.U, nb, prm.eps[l], prm.alpha, Lv.R, Lv.J, threadIdx.x, blockDim.x);
+      __syncthreads();
+      MG mg;
+      mg_bind(mg, P, l, nb, Lv.J, Lv.R, Lv.dU);
+      bool sing = mg_setup(mg, B);
+      __syncthreads();
+      if (sing) {
+        st = NSWE_ESINGULAR;
+        break;
+      }
+      if (l == L) {
+        band_solve(B, N, Lv.R, Lv.dU);
+      } else {
+        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) Lv.dU[t] = 0.0;
+        __syncthreads();
+        for (int m = 0; m < prm.nu3; ++m) {
+          mg_vcycle(mg, B, prm);
+          ++vcycles;
+        }
+      }
+      bool bad = false;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double h = Lv.U[j] + prm.tau * Lv.dU[j];
+        Lv.U[j] = h;
+        Lv.U[N + j] += prm.tau * Lv.dU[N + j];
+        if (!(h > 0.0)) bad = true;
+      }
+      bad = __syncthreads_or(bad);
+      res = block_sum(residual_cells(G, Lv.U, Lv.R, threadIdx.x, blockDim.x), red) / N;
+      ++n;
+      if (bad) {
+        st = NSWE_ENEGDEPTH;
+        break;
+      }
+      if (!(res == res) || isinf(res)) {
+        st = NSWE_ENAN;
+        break;
+      }
+      if (res < prm.tol) break;
+      if (n >= prm.n_max) {
+        st = NSWE_ENOTCONV;
+        break;
+      }
+    }
+    iters[l] = n;
+    lres[l] = res;
+    lstat[l] = st;
+    total += n;
+    if (st == NSWE_ENAN || st == NSWE_ENEGDEPTH || st == NSWE_ESINGULAR) fatal = st;
+  }
+
+  if (!fatal) {
+    const int N0 = P.lev[0].N;
+    for (int t = threadIdx.x; t < 2 * N0; t += blockDim.x) task.U[t] = P.lev[0].U[t];
+  }
+  if (threadIdx.x == 0 && task.info) {
+    nswe_info inf;
+    for (int l = 0; l < NSWE_MAX_LEVELS; ++l) {
+      inf.iters[l] = iters[l];
+      inf.res[l] = lres[l];
+      inf.level_status[l] = lstat[l];
+    }
+    inf.status = fatal ? fatal : lstat[0];
+    inf.total_iters = total;
+    inf.vcycles = vcycles;
+    *task.info = inf;
+  }
+}
+
+int grid_for(int items) {
+  int b = (items + kThreads - 1) / kThreads;
+  return b < 1 ? 1 : (b > 1024 ? 1024 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U, double *R, double *res,
+                            double *partials, cudaStream_t s) {
+  int grid = grid_for(N);
+  k_residual<<<grid, kThreads, 0, s>>>(p, level, U, R, partials);
+  if (res) k_finish_res<<<1, 32, 0, s>>>(partials, grid, N, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
+                            double alpha, double *R, double *J, double *res, double *partials, cudaStream_t s) {
+  cudaError_t e = launch_residual(p, level, N, U, R, res, partials, s);
+  if (e != cudaSuccess) return e;
+  k_jacobian<<<grid_for(N * nb), kThreads, 0, s>>>(p, level, nb, U, eps, alpha, R, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vcycle(const ProbDev *p, int level, int nb, const double *J, const double *R, double *dU,
+                          const nswe_params &prm, int *status, cudaStream_t s) {
+  k_vcycle<<<1, kThreads, 0, s>>>(p, level, nb, J, R, dU, prm, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, cudaStream_t s) {
+  k_solve<<<count, kThreads, 0, s>>>(tasks, prm);
+  return cudaGetLastError();
+}
+
+}  // namespace nswe

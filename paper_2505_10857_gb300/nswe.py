@@ -1,0 +1,264 @@
+"""Python binding of the C ABI in include/nswe.h (libnswe_gb300.so).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library. Device arrays are torch tensors (float64, CUDA, contiguous) whose
+pointers are passed through; PyTorch supplies device memory and the stream.
+There is no CPU fallback: if the library is missing or no GPU is present,
+loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+MAX_LEVELS = 16
+JAC_SIMPLIFIED, JAC_FULL = 3, 5
+BC_DISCHARGE, BC_DEPTH, BC_STATE, BC_EXTRAP = 1, 2, 3, 4
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENAN", 6: "ENEGDEPTH",
+          7: "ESINGULAR"}
+
+
+class BC1D(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("h", ctypes.c_double), ("q", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("omega", ctypes.c_double),
+                ("tol", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("nu3", ctypes.c_int),
+                ("n_max", ctypes.c_int), ("jacobian", ctypes.c_int), ("nest_start", ctypes.c_int),
+                ("eps", ctypes.c_double * MAX_LEVELS)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int * MAX_LEVELS),
+                ("res", ctypes.c_double * MAX_LEVELS), ("level_status", ctypes.c_int * MAX_LEVELS),
+                ("total_iters", ctypes.c_int), ("vcycles", ctypes.c_int)]
+
+    def as_dict(self, levels=MAX_LEVELS):
+        return {"status": self.status, "iters": list(self.iters)[:levels], "res": list(self.res)[:levels],
+                "level_status": list(self.level_status)[:levels], "total_iters": self.total_iters,
+                "vcycles": self.vcycles}
+
+
+class NsweError(RuntimeError):
+    def __init__(self, call, status):
+        super().__init__(f"{call} failed: {STATUS.get(status, status)} ({lib().nswe_status_str(status).decode()})")
+        self.status = status
+
+
+_lib = None
+_vp, _dp, _i, _d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+
+EXPORTS = {
+    "nswe_status_str": (ctypes.c_char_p, [_i]),
+    "nswe_params_default": (_i, [ctypes.POINTER(Params), _i, _i]),
+    "nswe_ctx_create": (_i, [ctypes.POINTER(_vp), _i, _vp]),
+    "nswe_ctx_set_stream": (_i, [_vp, _vp]),
+    "nswe_ctx_destroy": (_i, [_vp]),
+    "nswe_prob_create_1d": (_i, [_vp, ctypes.POINTER(_vp), _i, _i, _d, _d, _d, _dp, _dp,
+                                 ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
+    "nswe_prob_set_geometry_1d": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
+    "nswe_prob_destroy": (_i, [_vp]),
+    "nswe_prob_cells": (_i, [_vp, _i]),
+    "nswe_residual": (_i, [_vp, _vp, _i, _dp, _dp, _dp]),
+    "nswe_jacobian_simplified": (_i, [_vp, _vp, _i, _dp, _d, _d, _dp, _dp, _dp]),
+    "nswe_jacobian_full": (_i, [_vp, _vp, _i, _dp, _d, _d, _dp, _dp, _dp]),
+    "nswe_mg_vcycle": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
+    "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
+    "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                                     ctypes.POINTER(Params), ctypes.POINTER(Info)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libnswe_gb300.so (building it with nvcc if absent)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing; run paper_2505_10857_gb300.build.build()")
+            _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(call, rc):
+    if rc != 0:
+        raise NsweError(call, rc)
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a CUDA float64 contiguous tensor (or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def params(N, levels, **kw) -> Params:
+    """Paper defaults (nswe_params_default) with keyword overrides; eps may be
+    a sequence (per nested level) or a scalar."""
+    p = Params()
+    _check("nswe_params_default", lib().nswe_params_default(ctypes.byref(p), int(N), int(levels)))
+    for k, v in kw.items():
+        if k == "eps":
+            vals = list(v) if hasattr(v, "__len__") else [v] * MAX_LEVELS
+            for i in range(MAX_LEVELS):
+                p.eps[i] = float(vals[min(i, len(vals) - 1)])
+        elif k == "nb":
+            p.jacobian = int(v)
+        elif k == "lex":
+            if v:
+                raise ValueError("the CUDA path implements the multicolour smoother only")
+        elif k == "levels":
+            pass
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def params_from(prm) -> Params:
+    """From an inputs.Params1D (whose eps list is filled per nested level)."""
+    if not prm.eps:
+        raise ValueError("eps per level must be given")
+    return params(96, prm.levels, alpha=prm.alpha, tau=prm.tau, omega=prm.omega, tol=prm.tol, nu1=prm.nu1,
+                  nu2=prm.nu2, nu3=prm.nu3, n_max=prm.n_max, nb=prm.nb, nest_start=prm.nest_start, eps=prm.eps,
+                  lex=prm.lex)
+
+
+class Context:
+    """nswe_ctx bound to a device and (by default) torch's current stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the NMGM library runs on the GPU only")
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.device = device
+        self.h = _vp()
+        _check("nswe_ctx_create", lib().nswe_ctx_create(ctypes.byref(self.h), int(device), _vp(stream)))
+
+    def set_stream(self, stream):
+        _check("nswe_ctx_set_stream", lib().nswe_ctx_set_stream(self.h, _vp(stream)))
+
+    def close(self):
+        if self.h:
+            lib().nswe_ctx_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bc(b) -> BC1D:
+    return BC1D(int(b[0]), float(b[1]), float(b[2]))
+
+
+class Problem1D:
+    """nswe_prob of a 1D problem (host arrays copied to device)."""
+
+    def __init__(self, ctx: Context, N, levels, x0, x1, g, sigma_face, gauss_geom_all, bcl, bcr):
+        self.ctx = ctx
+        self.N, self.levels = int(N), int(levels)
+        sf = np.ascontiguousarray(sigma_face, dtype=np.float64)
+        gq = np.ascontiguousarray(gauss_geom_all, dtype=np.float64)
+        self.h = _vp()
+        _check("nswe_prob_create_1d", lib().nswe_prob_create_1d(
+            ctx.h, ctypes.byref(self.h), self.N, self.levels, float(x0), float(x1), float(g),
+            sf.ctypes.data, gq.ctypes.data, ctypes.byref(_bc(bcl)), ctypes.byref(_bc(bcr))))
+
+    @staticmethod
+    def from_inputs(ctx: Context, inp) -> "Problem1D":
+        return Problem1D(ctx, inp.N, inp.levels, inp.x0, inp.x1, inp.g, inp.sig_face, inp.gq_all(), inp.bcl, inp.bcr)
+
+    def set_geometry(self, sigma_face, gauss_geom_all, bcl, bcr):
+        """Arrays must stay alive until the stream has consumed them."""
+        _check("nswe_prob_set_geometry_1d", lib().nswe_prob_set_geometry_1d(
+            self.ctx.h, self.h, _host_ptr(sigma_face), _host_ptr(gauss_geom_all),
+            ctypes.byref(_bc(bcl)), ctypes.byref(_bc(bcr))))
+
+    def cells(self, level=0):
+        return lib().nswe_prob_cells(self.h, int(level))
+
+    def close(self):
+        if self.h:
+            lib().nswe_prob_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a) -> int:
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()  # pinned CPU torch tensor
+
+
+# ---------------------------------------------------------------- calls (same names as the C ABI)
+
+def nswe_residual(ctx: Context, prob: Problem1D, level, U, R, res=None):
+    _check("nswe_residual", lib().nswe_residual(ctx.h, prob.h, int(level), _ptr(U), _ptr(R), _ptr(res)))
+
+
+def nswe_jacobian_simplified(ctx, prob, level, U, eps, alpha, R, J, res=None):
+    _check("nswe_jacobian_simplified", lib().nswe_jacobian_simplified(
+        ctx.h, prob.h, int(level), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
+
+
+def nswe_jacobian_full(ctx, prob, level, U, eps, alpha, R, J, res=None):
+    _check("nswe_jacobian_full", lib().nswe_jacobian_full(
+        ctx.h, prob.h, int(level), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
+
+
+def nswe_mg_vcycle(ctx, prob, level, nb, J, R, dU, prm: Params):
+    _check("nswe_mg_vcycle", lib().nswe_mg_vcycle(ctx.h, prob.h, int(level), int(nb), _ptr(J), _ptr(R), _ptr(dU),
+                                                  ctypes.byref(prm)))
+
+
+def nswe_newton_solve(ctx, prob, U0, U, prm: Params, want_info=True, raise_on_status=False):
+    info = Info() if want_info else None
+    rc = lib().nswe_newton_solve(ctx.h, prob.h, _ptr(U0), _ptr(U), ctypes.byref(prm),
+                                 ctypes.byref(info) if info is not None else None)
+    if rc in (1, 2, 3) or (raise_on_status and rc):
+        raise NsweError("nswe_newton_solve", rc)
+    return info.as_dict(prob.levels) if info is not None else None
+
+
+def nswe_newton_solve_batch(ctx, probs: Sequence[Problem1D], U0s, Us, prm: Params, want_info=True):
+    n = len(probs)
+    ph = (_vp * n)(*[p.h.value for p in probs])
+    u0 = (_dp * n)(*[_ptr(u) for u in U0s])
+    uu = (_dp * n)(*[_ptr(u) for u in Us])
+    infos = (Info * n)() if want_info else None
+    rc = lib().nswe_newton_solve_batch(ctx.h, n, ph, u0, uu, ctypes.byref(prm), infos)
+    if rc in (1, 2, 3):
+        raise NsweError("nswe_newton_solve_batch", rc)
+    return [infos[i].as_dict(probs[i].levels) for i in range(n)] if infos is not None else None
