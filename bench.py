@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the 1D NMGM on GB300: steady solves/s and p99 latency at
+residual <= 1e-10 (FP64 Newton multigrid, nested Algorithm 3).
+
+Workload (one step = one batch of independent solves, inputs resident in HBM):
+1D irregular channel, N = 4096 cells on [0, 25], width
+B(x) = 1 + 0.2 sin(2 pi k x / 25), k ~ U{1..4}, Gaussian hump A ~ U[0.05, 0.2],
+xc ~ U[8, 12], w ~ U[1, 2], upstream discharge 4.42, downstream depth 2.0,
+WENO3 + HLL, simplified Jacobian J3, 8-level multigrid, seeded instances.
+
+Arms
+  default            CUDA library through its C ABI (device-timed value; e2e
+                     through the same API from pinned host buffers).
+  --impl reference   the CPU oracle on the host cores (the slow baseline).
+
+Multi-GPU: independent replicas (each rank solves its own instances; no
+collective on the data path), reported as weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "steady solves/s and p99 latency at residual <=1e-10 vs plain FP64 Newton-MG"
+UNIT = "solves/s"
+TOL = 1e-10
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x FP64 FMA/clk/SM x 2 flop x max SM GHz
+
+
+def workload_config(batch, nb):
+    return {"workload": "1D irregular channel, N=4096, 8-level MG, J%d, FP64, subcritical" % nb,
+            "N": 4096, "levels": 8, "nest_start_cells": 256, "instances_per_step_per_gpu": batch,
+            "jacobian": "J3 (simplified)" if nb == 3 else "J5 (full)", "tol": TOL,
+            "l2": "inputs + workspace per step (%.0f MB) exceed the 129 MB L2" % (batch * 2.4),
+            "seeds": "numpy default_rng(2000 + k)"}
+
+
+def make_instances(first, count, nb):
+    from paper_2505_10857_gb300 import inputs as I
+    inps = [I.channel_irregular(k) for k in range(first, first + count)]
+    prms = [I.Params1D.for_problem(p, tol=TOL, n_max=500, nb=nb) for p in inps]
+    return inps, prms
+
+
+# ------------------------------------------------------------------------------------------------
+# Algorithmic FP64 flop count of one solve (add/sub/mul = 1, fused multiply-add = 2, division = 1,
+# square root = 1), from the operation counts of each step of the method; per cell unless noted.
+F_RES = 331          # one local residual: 6 WENO3 (34), 2 HLL (43), Gauss source (36), R (3), |R|_1 (2)
+F_JAC_BLOCK = 668    # one Jacobian block: 2 perturbed local residuals (329+1) + 2 differences + 2 divisions
+F_UPDATE = 4         # damped Newton update of H and Q
+F_DINV = 9           # 2x2 inverse
+F_INTERP = 8         # App. A per fine cell
+
+
+def f_sor(nb):       # one block-SOR update of one cell
+    return 8 * (nb - 1) + 12
+
+
+def f_restrict(nb):  # per coarse cell
+    return 16 * nb + 2
+
+
+def lu_flops(n, kl):
+    return n * (kl + 4 * kl * kl), n * (6 * kl + 1)  # factor, solve
+
+
+def solve_flops(N, levels, start, iters, nb, nu1, nu2, nu3):
+    L = levels - 1
+    tot = 0.0
+    for l in range(start, -1, -1):
+        Nl = N >> l
+        if l < start:
+            tot += F_INTERP * Nl
+        tot += F_RES * Nl  # initial residual of the level
+        per = Nl * (nb * F_JAC_BLOCK + 2) + Nl * (F_RES + F_UPDATE)
+        nbl = [nb if k == l else 3 for k in range(L + 1)]
+        for k in range(l + 1, L + 1):
+            per += 8 * nbl[k - 1] * (N >> k)
+        for k in range(l, L):
+            per += F_DINV * (N >> k)
+        hw = (nbl[L] - 1) // 2
+        fac, sol = lu_flops(2 * (N >> L), 2 * hw + 1)
+        per += fac
+        if l == L:
+            per += sol
+        else:
+            vc = sol
+            for k in range(l, L):
+                Nk = N >> k
+                vc += (nu1 + nu2) * 2 * Nk * f_sor(nbl[k]) + (N >> (k + 1)) * f_restrict(nbl[k]) + 2 * Nk
+            per += nu3 * vc
+        tot += iters[l] * per
+    return tot
+
+
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------------------------------------------
+def _oracle_worker(args):
+    first, count, nb = args
+    import oracle
+    inps, prms = make_instances(first, count, nb)
+    out = []
+    for p, q in zip(inps, prms):
+        U, info = oracle.solve_problem(p, q)
+        out.append((U, info["status"]))
+    return out
+
+
+def oracle_sample(first, count, nb, workers):
+    """Solves `count` instances with the CPU oracle on `workers` processes
+    (spawn); returns (wall seconds, results)."""
+    import oracle
+    oracle.build()
+    chunks = [(first + i, 1, nb) for i in range(count)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_worker, [(first, 1, nb)] * workers)  # warm the workers
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, chunks)
+        wall = time.perf_counter() - t0
+    return wall, [r[0][0] for r in res]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = host_cores()
+    sample = cores
+    times = []
+    for s in range(args.warmup + args.steps):
+        wall, _ = oracle_sample((s * sample) % args.batch, sample, args.nb, cores)
+        if s >= args.warmup:
+            times.append(wall)
+    ms = 1000.0 * sum(times) / len(times)
+    value = sample / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sample, args.nb),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} solves per step, one per process (spawn pool)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_10857_gb300 import nswe
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B, nb = args.batch, args.nb
+    first = rank * B
+    inps, prms = make_instances(first, B, nb)
+    prm = nswe.params_from(prms[0])
+    for q in prms[1:]:
+        assert list(q.eps) == list(prms[0].eps) and q.omega == prms[0].omega
+
+    ctx = nswe.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    probs = [nswe.Problem1D.from_inputs(ctx, p) for p in inps]
+    U0s = [torch.from_numpy(p.U0_start).to(dev) for p in inps]
+    Us = [torch.zeros((2, p.N), dtype=torch.float64, device=dev) for p in inps]
+
+    def step(want_info=False):
+        return nswe.nswe_newton_solve_batch(ctx, probs, U0s, Us, prm, want_info=want_info)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed throughput (inputs resident in HBM)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for s in range(args.steps):
+        step()
+        ev[s + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    per_launch = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    ms = ev[0].elapsed_time(ev[-1]) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * B / (ms_max / 1000.0)
+
+    # ---- one more step with per-solve records (status, iterations, device timestamps)
+    infos = step(want_info=True)
+    torch.cuda.synchronize()
+    status = [i["status"] for i in infos]
+    res0 = [i["res"][0] for i in infos]
+    t0 = min(i["t_start_ns"] for i in infos)
+    lat = sorted((i["t_end_ns"] - t0) / 1e6 for i in infos)
+    dur = sorted((i["t_end_ns"] - i["t_start_ns"]) / 1e6 for i in infos)
+
+    def pct(a, p):
+        return a[min(len(a) - 1, int(math.ceil(p / 100.0 * len(a))) - 1)]
+
+    flops = sum(solve_flops(4096, 8, inps[k].start_level, infos[k]["iters"], nb, prm.nu1, prm.nu2, prm.nu3)
+                for k in range(B))
+    launch_ms = statistics.mean(per_launch)
+    achieved = flops / (launch_ms / 1000.0) / 1e12
+
+    # ---- single-solve latency (one instance alone on the GPU)
+    single = []
+    for s in range(3):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nswe.nswe_newton_solve(ctx, probs[s], U0s[s], Us[s], prm, want_info=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        single.append(e0.elapsed_time(e1))
+
+    # ---- end to end through the C ABI from pinned host buffers
+    pin = []
+    for p in inps:
+        sf = torch.from_numpy(p.sig_face).pin_memory()
+        gq = torch.from_numpy(p.gq_all()).pin_memory()
+        u0 = torch.from_numpy(p.U0_start).pin_memory()
+        pin.append((sf, gq, u0, torch.empty((2, p.N), dtype=torch.float64).pin_memory()))
+    h2d = sum(a.numel() * 8 for (sf, gq, u0, _) in pin for a in (sf, gq, u0))
+    d2h = sum(o.numel() * 8 for (_, _, _, o) in pin) + B * ctypes.sizeof(nswe.Info)
+    e2e_times = []
+    for s in range(args.warmup + args.steps):
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k, p in enumerate(inps):
+            sf, gq, u0, _ = pin[k]
+            probs[k].set_geometry(sf.numpy(), gq.numpy(), p.bcl, p.bcr)
+            U0s[k].copy_(u0, non_blocking=True)
+        infos_e = step(want_info=True)  # synchronous: includes the D2H of the per-solve records
+        for k in range(B):
+            pin[k][3].copy_(Us[k], non_blocking=True)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            e2e_times.append(time.perf_counter() - w0)
+        assert all(i["status"] == 0 for i in infos_e)
+    e2e_ms = 1000.0 * statistics.mean(e2e_times)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * B / (float(te.item()) / 1000.0)
+
+    out = None
+    if rank == 0:
+        cpu = None
+        parity = None
+        if world == 1 and not args.no_cpu:
+            cores = host_cores()
+            n = min(B, 2 * cores)
+            wall, refs = oracle_sample(first, n, nb, cores)
+            cpu = {"value": n / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"first {n} instances of the step, one solve per process (spawn pool), "
+                             f"{wall:.1f} s wall"}
+            errs = [float(np.abs(Us[k].cpu().numpy() - refs[k]).max() / np.abs(refs[k]).max()) for k in range(n)]
+            parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "bound": 1e-10}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(B, nb),
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
+                           "what": "per-solve completion time from the start of its batch (device timer)",
+                           "solve_p50": pct(dur, 50), "solve_p99": pct(dur, 99),
+                           "single_solve_alone": statistics.median(single)},
+            "converged": {"all_status_ok": all(s == 0 for s in status), "max_res": max(res0),
+                          "mean_newton_iters": statistics.mean(i["total_iters"] for i in infos)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": float(te.item())},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1000.0,
+                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1000.0), "traffic": None,
+                         "kernel": "k_solve (persistent nested NMGM, one block per instance)",
+                         "flops_per_launch": flops, "launch_ms": launch_ms,
+                         "peak_note": "FP64 derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"},
+            "clocks": clk,
+        }
+        if cpu:
+            out["cpu_baseline"] = cpu
+            out["parity"] = parity
+        print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--batch", type=int, default=608, help="instances per GPU per step")
+    ap.add_argument("--nb", type=int, default=3, choices=[3, 5], help="3: simplified J3, 5: full J5")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2505_10857_gb300 import build
+    build.build()
+    run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

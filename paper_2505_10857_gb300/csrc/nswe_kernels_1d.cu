@@ -574,6 +574,12 @@ __device__ __forceinline__ Band band_view(SmemBand &s) {
 // ----------------------------------------------------------------------------
 // Kernels.
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __global__ void __launch_bounds__(kThreads) k_residual(const ProbDev *P, int level, const double *U, double *R,
                                                        double *partials) {
   __shared__ double red[33];
@@ -613,6 +619,7 @@ __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level
 __global__ void __launch_bounds__(kThreads) k_solve(const SolveTask *tasks, nswe_params prm) {
   __shared__ SmemBand sb;
   __shared__ double red[33];
+  const unsigned long long t_start = global_ns();
   const SolveTask task = tasks[blockIdx.x];
   const ProbDev &P = *task.prob;
   const int L = P.levels - 1;
@@ -711,6 +718,8 @@ __global__ void __launch_bounds__(kThreads) k_solve(const SolveTask *tasks, nswe
     inf.status = fatal ? fatal : lstat[0];
     inf.total_iters = total;
     inf.vcycles = vcycles;
+    inf.t_start_ns = t_start;
+    inf.t_end_ns = global_ns();
     *task.info = inf;
   }
 }

@@ -127,6 +127,7 @@ class Problem1DInputs:
     U0_start: np.ndarray            # [2, N_s] guess on the start level s
     start_level: int = -1           # nested start level s (-1: coarsest)
     omega: float = 1.0              # SOR relaxation suited to the family
+    eps_levels: List[float] = field(default_factory=list)  # FD eps per nested level (empty: eps_for_n)
     b_fn: Callable = field(repr=False, default=None)
     sig_fn: Callable = field(repr=False, default=None)
     meta: dict = field(default_factory=dict)
@@ -166,7 +167,7 @@ def sample_geometry(x0, x1, n, b_fn, sig_fn):
 
 
 def make_problem_1d(N, levels, x0, x1, g, b_fns, sig_fns, bcl, bcr, init="lake", h_init=None, q_init=None,
-                    meta=None, start_level=-1, omega=1.0) -> Problem1DInputs:
+                    meta=None, start_level=-1, omega=1.0, eps_levels=None) -> Problem1DInputs:
     """Samples geometry for every nested level and builds the start guess.
 
     init = "lake": guess on the start level h = h_init - b(x_c), Q = q_init
@@ -189,7 +190,8 @@ def make_problem_1d(N, levels, x0, x1, g, b_fns, sig_fns, bcl, bcr, init="lake",
     else:
         raise ValueError(init)
     return Problem1DInputs(N, levels, x0, x1, g, sig_face, gq, tuple(bcl), tuple(bcr),
-                           np.ascontiguousarray(U0, dtype=np.float64), sl, omega, b, s, meta or {})
+                           np.ascontiguousarray(U0, dtype=np.float64), sl, omega, list(eps_levels or []), b, s,
+                           meta or {})
 
 
 # --------------------------------------------------------------------------
@@ -204,6 +206,12 @@ def eps_for_n(n, floor=0.05):
     the paper uses at N = 768."""
     e = 0.2 - 0.05 * math.log2(n / 96.0)
     return float(min(0.2, max(floor, e)))
+
+
+def eps_channel(n):
+    """FD perturbation for the sinusoidal-width channels: 0.2 up to 512 cells,
+    0.1 at 1024, 0.05 from 2048 cells."""
+    return 0.2 if n <= 512 else (0.1 if n <= 1024 else 0.05)
 
 
 @dataclass
@@ -228,7 +236,7 @@ class Params1D:
         kw.setdefault("nest_start", p.start_level)
         prm = Params1D(levels=p.levels, **kw)
         if not prm.eps:
-            prm.eps = [eps_for_n(p.N_level(l)) for l in range(p.levels)]
+            prm.eps = list(p.eps_levels) or [eps_for_n(p.N_level(l)) for l in range(p.levels)]
         return prm
 
 
@@ -287,7 +295,7 @@ def critical_margin(q, hout, b_fn, sig_fn, g=G_CONFIG, x0=0.0, x1=25.0, n=4001):
     return float(E - Ec.max())
 
 
-def channel_irregular(k, N=4096, levels=8, regime="sub", min_margin=0.5, start_level=4):
+def channel_irregular(k, N=4096, levels=8, regime="sub", min_margin=0.5, start_level=4, q_sub=4.42):
     """Seeded 1D channel with sinusoidal width B(x)=B0(1+0.2 sin(2 pi k' x/25)),
     B0 = 1, k' ~ U{1..4}, Gaussian hump as in channel_small, N=4096 on [0,25],
     8-level multigrid (4096 -> 32 cells).
@@ -295,9 +303,11 @@ def channel_irregular(k, N=4096, levels=8, regime="sub", min_margin=0.5, start_l
     and would choke the subcritical flow are redrawn (deterministically, same
     generator) until the energy margin exceeds min_margin. Seed 2000 + k.
     The nested solve starts on level 4 (256 cells): coarser grids do not
-    resolve the width oscillation for k' >= 2. SOR relaxation 0.7."""
+    resolve the width oscillation for k' >= 2. SOR relaxation 0.7. FD eps per
+    level (eps_channel): larger than the Section 5.1 progression below 2048
+    cells, without which the Newton iteration breaks down on k' = 4."""
     rng = np.random.default_rng(2000 + k)
-    q, hout = (4.42, 2.0) if regime == "sub" else (1.53, 0.66)
+    q, hout = (q_sub, 2.0) if regime == "sub" else (1.53, 0.66)
     for draw in range(1000):
         A, xc, w = _seeded_hump(rng)
         kk = int(rng.integers(1, 5))
@@ -308,7 +318,8 @@ def channel_irregular(k, N=4096, levels=8, regime="sub", min_margin=0.5, start_l
     return make_problem_1d(N, levels, 0.0, 25.0, G_CONFIG, b_fns, s_fns,
                            (BC_DISCHARGE, 0.0, q), (BC_DEPTH, hout, 0.0), h_init=hout, q_init=q,
                            meta={"A": A, "xc": xc, "w": w, "k": kk, "seed": 2000 + k, "draws": draw + 1,
-                                 "margin": margin, "regime": regime}, start_level=start_level, omega=0.7)
+                                 "margin": margin, "regime": regime}, start_level=start_level, omega=0.7,
+                           eps_levels=[eps_channel(N >> l) for l in range(levels)])
 
 
 def uniform_flow(N, levels, h, q, sigma=1.0, x0=0.0, x1=10.0, g=G_CONFIG, bc=BC_STATE):

@@ -37,12 +37,13 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int * MAX_LEVELS),
                 ("res", ctypes.c_double * MAX_LEVELS), ("level_status", ctypes.c_int * MAX_LEVELS),
-                ("total_iters", ctypes.c_int), ("vcycles", ctypes.c_int)]
+                ("total_iters", ctypes.c_int), ("vcycles", ctypes.c_int),
+                ("t_start_ns", ctypes.c_ulonglong), ("t_end_ns", ctypes.c_ulonglong)]
 
     def as_dict(self, levels=MAX_LEVELS):
         return {"status": self.status, "iters": list(self.iters)[:levels], "res": list(self.res)[:levels],
                 "level_status": list(self.level_status)[:levels], "total_iters": self.total_iters,
-                "vcycles": self.vcycles}
+                "vcycles": self.vcycles, "t_start_ns": self.t_start_ns, "t_end_ns": self.t_end_ns}
 
 
 class NsweError(RuntimeError):
