@@ -95,6 +95,8 @@ typedef struct {
   int level_status[NSWE_MAX_LEVELS]; /* nswe_status per nested level       */
   int total_iters;
   int vcycles;
+  unsigned long long t_start_ns;     /* device global timer at solve start */
+  unsigned long long t_end_ns;       /* device global timer at solve end   */
 } nswe_info;
 
 typedef struct nswe_ctx_s *nswe_ctx;
@@ -200,6 +202,40 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count,
                                     double *const *Us,
                                     const nswe_params *params,
                                     nswe_info *infos);
+
+/* Allocation-free nested solve. The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as code running
+ * after another allocator (e.g. a framework's caching allocator) has
+ * reserved the device memory it may use, or real-time loops that must not
+ * block on the device synchronisation cudaMalloc/cudaFree imply. It runs the
+ * same solve as nswe_newton_solve on one problem of at most
+ * NSWE_NOALLOC_MAX_CELLS cells, with the problem description and workspace
+ * in a fixed device array of the library (about 2 MB, held by every GPU that
+ * loads the library until the process exits); it allocates nothing.
+ *   device       CUDA device index; it is made current for the call.
+ *   stream       cudaStream_t as void* (NULL: legacy default stream).
+ *   N, levels, x0, x1, g, left, right: as in nswe_prob_create_1d, with
+ *                N <= NSWE_NOALLOC_MAX_CELLS (larger N returns NSWE_EINVAL).
+ *   sigma_face   DEVICE [N+1] width at the finest faces.
+ *   gauss_geom   DEVICE, the per-level Gauss-point geometry in the layout of
+ *                nswe_prob_create_1d; read in place.
+ *   U0, U        DEVICE, as in nswe_newton_solve.
+ *   info         DEVICE pointer to one nswe_info, or NULL.
+ * Asynchronous on `stream`. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls share the array, which keeps the last call's
+ * contents; calls that overlap on the GPU race and must be serialised by the
+ * caller. */
+#define NSWE_NOALLOC_MAX_CELLS 4096
+nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N,
+                                      int levels, double x0, double x1,
+                                      double g, const double *sigma_face,
+                                      const double *gauss_geom,
+                                      const nswe_bc1d *left,
+                                      const nswe_bc1d *right,
+                                      const double *U0, double *U,
+                                      const nswe_params *params,
+                                      nswe_info *info);
 
 #ifdef __cplusplus
 }

@@ -73,6 +73,8 @@ EXPORTS = {
     "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                      ctypes.POINTER(Params), ctypes.POINTER(Info)]),
+    "nswe_newton_solve_noalloc": (_i, [_i, _vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D),
+                                       ctypes.POINTER(BC1D), _dp, _dp, ctypes.POINTER(Params), _vp]),
 }
 
 
@@ -263,3 +265,23 @@ def nswe_newton_solve_batch(ctx, probs: Sequence[Problem1D], U0s, Us, prm: Param
     if rc in (1, 2, 3):
         raise NsweError("nswe_newton_solve_batch", rc)
     return [infos[i].as_dict(probs[i].levels) for i in range(n)] if infos is not None else None
+
+
+def nswe_newton_solve_noalloc(device, stream, N, levels, x0, x1, g, sigma_face, gauss_geom, bcl, bcr, U0, U,
+                              prm: Params, info=None):
+    """Allocation-free solve of one problem (see include/nswe.h): every array
+    is a device tensor; `info` is a device buffer of sizeof(Info) bytes (a
+    uint8 CUDA tensor) or None. Returns the status code of the call."""
+    rc = lib().nswe_newton_solve_noalloc(
+        int(device), _vp(stream), int(N), int(levels), float(x0), float(x1), float(g), _ptr(sigma_face),
+        _ptr(gauss_geom), ctypes.byref(_bc(bcl)), ctypes.byref(_bc(bcr)), _ptr(U0), _ptr(U), ctypes.byref(prm),
+        _vp(info.data_ptr()) if info is not None else None)
+    if rc:
+        raise NsweError("nswe_newton_solve_noalloc", rc)
+    return rc
+
+
+def info_from_bytes(raw: bytes, levels=MAX_LEVELS) -> dict:
+    """Decodes an nswe_info copied back from the device."""
+    inf = Info.from_buffer_copy(raw)
+    return inf.as_dict(levels)
