@@ -220,6 +220,7 @@ nswe_status nswe_prob_create_1d(nswe_ctx ctx, nswe_prob *out, int N, int levels,
     geo += round_up(Nl + 1) + round_up(6 * Nl);
     work += round_up(2 * Nl) * 3 + round_up(20 * Nl) + round_up(4 * Nl);
   }
+  work += round_up(jw_doubles((size_t)N));
   p->geo_doubles = geo;
   if (cudaMalloc(&p->arena, sizeof(double) * (geo + work)) != cudaSuccess) {
     delete p;
@@ -260,6 +261,8 @@ nswe_status nswe_prob_create_1d(nswe_ctx ctx, nswe_prob *out, int N, int levels,
     h.lev[l].Dinv = a;
     a += round_up(4 * Nl);
   }
+  h.jw = a;
+  a += round_up(jw_doubles((size_t)N));
   nswe_status st = upload_geometry(p, sigma_face, gauss_geom, left, right);
   if (st != NSWE_OK) {
     cudaStreamSynchronize(ctx->stream);

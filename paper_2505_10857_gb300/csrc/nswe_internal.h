@@ -33,8 +33,12 @@ struct ProbDev {
   double g;
   int bl, br;        // boundary kinds (nswe_bc_kind)
   double blh, blq, brh, brq;
+  double *jw;        // Jacobian workspace: 16*(N+2) + 18*(N+1) doubles, finest N
   LevelDev lev[NSWE_MAX_LEVELS];
 };
+
+// Doubles of Jacobian workspace for a level of N cells.
+inline size_t jw_doubles(size_t N) { return 16 * (N + 2) + 18 * (N + 1); }
 
 // One solve of a batch.
 struct SolveTask {

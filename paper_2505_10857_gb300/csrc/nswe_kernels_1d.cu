@@ -154,6 +154,23 @@ __device__ __forceinline__ void fill_ghosts(const Geo &G, int j, Win &w) {
   }
 }
 
+// Two-point Gauss source of cell j (Eq. 9): S = (dx/2) sum_q [g h^2 sigma_x/2
+// - g sigma h b_x] at the Gauss points, h = H_h/sigma, H_h the cubic through
+// the interface values p0..p3 of H at t = -3/2, -1/2, 1/2, 3/2.
+__device__ __forceinline__ double source_at(const Geo &G, int j, double p0, double p1, double p2, double p3) {
+  double S = 0.0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    double Hh = kLag[q][0] * p0 + kLag[q][1] * p1 + kLag[q][2] * p2 + kLag[q][3] * p3;
+    double sig = G.gq[(0 * 2 + q) * G.N + j];
+    double sigx = G.gq[(1 * 2 + q) * G.N + j];
+    double bx = G.gq[(2 * 2 + q) * G.N + j];
+    double h = Hh / sig;
+    S += 0.5 * G.g * h * h * sigx - G.g * sig * h * bx;
+  }
+  return S * (0.5 * G.dx);
+}
+
 // Local residual R_j (Eq. 10) from a filled window.
 __device__ __forceinline__ void local_residual(const Geo &G, int j, const Win &w, double &R0, double &R1) {
   double upH[3], umH[3], upQ[3], umQ[3];
@@ -165,17 +182,7 @@ __device__ __forceinline__ void local_residual(const Geo &G, int j, const Win &w
   double Fr0, Fr1, Fl0, Fl1;
   hll(umH[1], umQ[1], upH[2], upQ[2], G.sf[j + 1], G.g, Fr0, Fr1);
   hll(umH[0], umQ[0], upH[1], upQ[1], G.sf[j], G.g, Fl0, Fl1);
-  double S = 0.0;
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    double Hh = kLag[q][0] * upH[0] + kLag[q][1] * upH[1] + kLag[q][2] * umH[1] + kLag[q][3] * umH[2];
-    double sig = G.gq[(0 * 2 + q) * G.N + j];
-    double sigx = G.gq[(1 * 2 + q) * G.N + j];
-    double bx = G.gq[(2 * 2 + q) * G.N + j];
-    double h = Hh / sig;
-    S += 0.5 * G.g * h * h * sigx - G.g * sig * h * bx;
-  }
-  S *= 0.5 * G.dx;
+  double S = source_at(G, j, upH[0], upH[1], umH[1], umH[2]);
   R0 = Fr0 - Fl0;
   R1 = Fr1 - Fl1 - S;
 }
@@ -217,44 +224,155 @@ __device__ double residual_cells(const Geo &G, const double *U, double *R, int f
   return acc;
 }
 
-// One Jacobian work item: block k (offset k - hw) of row j, both columns
-// (Eq. 12), with the regularization on the diagonal block (Eq. 13).
-__device__ __forceinline__ void jacobian_item(const Geo &G, const double *U, int j, int k, int nb, double eps,
-                                              double alpha, const double *R, double *J) {
-  const int N = G.N, hw = (nb - 1) / 2, d = k - hw, i = j + d;
-  if (i < 0 || i >= N) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) J[(k * 4 + e) * N + j] = 0.0;
-    return;
+// ----------------------------------------------------------------------------
+// Regularized FD Jacobian (Eq. 12-13) in three passes that share work between
+// neighbouring cells. Perturbing U_i in component m changes only the
+// component-m reconstructions of cells i-1, i, i+1 (WENO3 is component-wise,
+// ghost states copy the same component of the edge cell), hence only the
+// fluxes of faces i-1..i+2 and the sources of cells i-1..i+1. So:
+//   A  per cell k = -1..N: reconstructions of the base state and of the
+//      three states with cell k-1, k or k+1 perturbed (same component);
+//   B  per face f = 0..N: the base flux and the 8 fluxes with one of cells
+//      f-2..f+1 perturbed in one component;
+//   C  per block (j, i): R_j of the perturbed state from two face fluxes and
+//      the Gauss source, minus the base R_j, over eps, plus alpha ||R_j||_1 I
+//      on the diagonal.
+// Each perturbed R_j is the same arithmetic on the same values as a full
+// re-evaluation of the local residual, at a fraction of the cost.
+
+struct JW {
+  double *rec;  // [2 comps][4 variants][2: up, um][N+2], cell k at k+1
+  double *flx;  // [9 variants][2 comps][N+1]
+  int N;
+  __device__ __forceinline__ double &r(int m, int v, int o, int k) const {
+    return rec[((m * 4 + v) * 2 + o) * (N + 2) + (k + 1)];
   }
-  Win w0;
-  load_win(G, U, U + N, j, w0);
-  const double R0 = R[j], R1 = R[N + j];
-  const double reg = (d == 0) ? alpha * (fabs(R0) + fabs(R1)) : 0.0;
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    Win w = w0;
-#pragma unroll
-    for (int p = 0; p < 5; ++p)
-      if (p == 2 + d) {
-        if (m == 0) w.H[p] += eps;
-        else w.Q[p] += eps;
-      }
-    fill_ghosts(G, j, w);
-    double P0, P1;
-    local_residual(G, j, w, P0, P1);
-    double v0 = (P0 - R0) / eps, v1 = (P1 - R1) / eps;
-    if (m == 0) v0 += reg;
-    else v1 += reg;
-    J[(k * 4 + 0 * 2 + m) * N + j] = v0;
-    J[(k * 4 + 1 * 2 + m) * N + j] = v1;
+  __device__ __forceinline__ double &f(int w, int l, int face) const { return flx[(w * 2 + l) * (N + 1) + face]; }
+};
+
+__device__ __forceinline__ JW jw_view(double *base, int N) {
+  JW W;
+  W.rec = base;
+  W.flx = base + 16 * (size_t)(N + 2);
+  W.N = N;
+  return W;
+}
+
+// Component m of cell kk (ghosts included) of the state with interior cell
+// ip perturbed by eps in component m (ip = -1: no perturbation).
+__device__ __forceinline__ double pval(const Geo &G, const double *U, int m, int kk, int ip, double eps) {
+  const int N = G.N;
+  if (kk >= 0 && kk < N) {
+    double x = U[m * N + kk];
+    return kk == ip ? x + eps : x;
+  }
+  const int e = kk < 0 ? 0 : N - 1;
+  double He = U[e], Qe = U[N + e];
+  if (e == ip) {
+    if (m == 0) He += eps;
+    else Qe += eps;
+  }
+  double Hg, Qg;
+  if (kk < 0) ghost(G.bl, G.blh, G.blq, G.sf[0], He, Qe, Hg, Qg);
+  else ghost(G.br, G.brh, G.brq, G.sf[N], He, Qe, Hg, Qg);
+  return m == 0 ? Hg : Qg;
+}
+
+// Pass A. Variant v = 0: base; v = 1, 2, 3: cell k + v - 2 perturbed.
+__device__ void jac_pass_a(const Geo &G, const double *U, double eps, const JW &W, int first, int stride) {
+  const int N = G.N, items = (N + 2) * 8;
+  for (int it = first; it < items; it += stride) {
+    const int k = it % (N + 2) - 1, mv = it / (N + 2), m = mv >> 2, v = mv & 3;
+    int ip = -1;
+    if (v > 0) {
+      ip = k + v - 2;
+      if (ip < 0 || ip >= N) continue;
+    }
+    double up, um;
+    weno3(pval(G, U, m, k - 1, ip, eps), pval(G, U, m, k, ip, eps), pval(G, U, m, k + 1, ip, eps), up, um);
+    W.r(m, v, 0, k) = up;
+    W.r(m, v, 1, k) = um;
   }
 }
 
-__device__ void jacobian_cells(const Geo &G, const double *U, int nb, double eps, double alpha, const double *R,
-                               double *J, int first, int stride) {
-  const int items = G.N * nb;
-  for (int it = first; it < items; it += stride) jacobian_item(G, U, it / nb, it % nb, nb, eps, alpha, R, J);
+// Reconstruction variant of cell kk under a perturbation of cell i.
+__device__ __forceinline__ int rec_variant(int i, int kk) {
+  int d = i - kk;
+  return (d >= -1 && d <= 1) ? d + 2 : 0;
+}
+
+// Pass B. Variant w = 0: base; w = 1 + 2p + m: cell f - 2 + p perturbed in
+// component m.
+__device__ void jac_pass_b(const Geo &G, const JW &W, int first, int stride) {
+  const int N = G.N, items = (N + 1) * 9;
+  for (int it = first; it < items; it += stride) {
+    const int f = it % (N + 1), w = it / (N + 1);
+    int vL0 = 0, vL1 = 0, vR0 = 0, vR1 = 0;
+    if (w > 0) {
+      const int p = (w - 1) >> 1, m = (w - 1) & 1, i = f - 2 + p;
+      if (i < 0 || i >= N) continue;
+      const int vL = rec_variant(i, f - 1), vR = rec_variant(i, f);
+      if (m == 0) {
+        vL0 = vL;
+        vR0 = vR;
+      } else {
+        vL1 = vL;
+        vR1 = vR;
+      }
+    }
+    double F0, F1;
+    hll(W.r(0, vL0, 1, f - 1), W.r(1, vL1, 1, f - 1), W.r(0, vR0, 0, f), W.r(1, vR1, 0, f), G.sf[f], G.g, F0, F1);
+    W.f(w, 0, f) = F0;
+    W.f(w, 1, f) = F1;
+  }
+}
+
+// Flux variant at face `face` for a perturbation of cell i, component m.
+__device__ __forceinline__ int flux_variant(int i, int m, int face) {
+  int p = i - face + 2;
+  return (p >= 0 && p <= 3) ? 1 + 2 * p + m : 0;
+}
+
+// Pass C over items (cell j, block k); writes R (from the k = hw items) and
+// J; returns the partial sum of ||R_j||_1 of the items it processed.
+__device__ double jac_pass_c(const Geo &G, int nb, double eps, double alpha, const JW &W, double *R, double *J,
+                             int first, int stride) {
+  const int N = G.N, hw = (nb - 1) / 2, items = N * nb;
+  double acc = 0.0;
+  for (int it = first; it < items; it += stride) {
+    const int j = it % N, k = it / N, d = k - hw, i = j + d;
+    const double Sb = source_at(G, j, W.r(0, 0, 0, j - 1), W.r(0, 0, 0, j), W.r(0, 0, 1, j), W.r(0, 0, 1, j + 1));
+    const double R0 = W.f(0, 0, j + 1) - W.f(0, 0, j);
+    const double R1 = W.f(0, 1, j + 1) - W.f(0, 1, j) - Sb;
+    if (d == 0) {
+      R[j] = R0;
+      R[N + j] = R1;
+      acc += fabs(R0) + fabs(R1);
+    }
+    if (i < 0 || i >= N) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) J[(k * 4 + e) * N + j] = 0.0;
+      continue;
+    }
+    const double reg = (d == 0) ? alpha * (fabs(R0) + fabs(R1)) : 0.0;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      double S = Sb;
+      if (m == 0) {
+        const int v0 = rec_variant(i, j - 1), v1 = rec_variant(i, j), v2 = rec_variant(i, j + 1);
+        S = source_at(G, j, W.r(0, v0, 0, j - 1), W.r(0, v1, 0, j), W.r(0, v1, 1, j), W.r(0, v2, 1, j + 1));
+      }
+      const int wr = flux_variant(i, m, j + 1), wl = flux_variant(i, m, j);
+      const double P0 = W.f(wr, 0, j + 1) - W.f(wl, 0, j);
+      const double P1 = W.f(wr, 1, j + 1) - W.f(wl, 1, j) - S;
+      double v0 = (P0 - R0) / eps, v1 = (P1 - R1) / eps;
+      if (m == 0) v0 += reg;
+      else v1 += reg;
+      J[(k * 4 + 0 * 2 + m) * N + j] = v0;
+      J[(k * 4 + 1 * 2 + m) * N + j] = v1;
+    }
+  }
+  return acc;
 }
 
 // Inverse of the diagonal 2x2 blocks.
@@ -597,10 +715,24 @@ __global__ void __launch_bounds__(kThreads) k_finish_res(const double *partials,
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_jacobian(const ProbDev *P, int level, int nb, const double *U,
-                                                       double eps, double alpha, const double *R, double *J) {
+__global__ void __launch_bounds__(kThreads) k_jac_a(const ProbDev *P, int level, const double *U, double eps) {
   Geo G = make_geo(*P, level);
-  jacobian_cells(G, U, nb, eps, alpha, R, J, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  jac_pass_a(G, U, eps, jw_view(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_jac_b(const ProbDev *P, int level) {
+  Geo G = make_geo(*P, level);
+  jac_pass_b(G, jw_view(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_jac_c(const ProbDev *P, int level, int nb, double eps, double alpha,
+                                                    double *R, double *J, double *partials) {
+  __shared__ double red[33];
+  Geo G = make_geo(*P, level);
+  double acc = jac_pass_c(G, nb, eps, alpha, jw_view(P->jw, G.N), R, J, blockIdx.x * blockDim.x + threadIdx.x,
+                          gridDim.x * blockDim.x);
+  double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level, int nb, const double *J,
@@ -650,11 +782,19 @@ __global__ void __launch_bounds__(kThreads) k_solve(const SolveTask *tasks, nswe
       interp_cells(make_geo(P, l + 1), P.lev[l + 1].U, Lv.U, threadIdx.x, blockDim.x);
       __syncthreads();
     }
-    double res = block_sum(residual_cells(G, Lv.U, Lv.R, threadIdx.x, blockDim.x), red) / N;
+    // R, J and res at the current state (Eq. 10, 12-13).
+    const JW W = jw_view(P.jw, N);
+    auto residual_jacobian = [&]() -> double {
+      jac_pass_a(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
+      __syncthreads();
+      jac_pass_b(G, W, threadIdx.x, blockDim.x);
+      __syncthreads();
+      double acc = jac_pass_c(G, nb, prm.eps[l], prm.alpha, W, Lv.R, Lv.J, threadIdx.x, blockDim.x);
+      return block_sum(acc, red) / N;
+    };
+    double res = residual_jacobian();
     int n = 0, st = NSWE_OK;
     while (true) {
-      jacobian_cells(G, Lv.U, nb, prm.eps[l], prm.alpha, Lv.R, Lv.J, threadIdx.x, blockDim.x);
-      __syncthreads();
       MG mg;
       mg_bind(mg, P, l, nb, Lv.J, Lv.R, Lv.dU);
       bool sing = mg_setup(mg, B);
@@ -681,12 +821,14 @@ __global__ void __launch_bounds__(kThreads) k_solve(const SolveTask *tasks, nswe
         if (!(h > 0.0)) bad = true;
       }
       bad = __syncthreads_or(bad);
-      res = block_sum(residual_cells(G, Lv.U, Lv.R, threadIdx.x, blockDim.x), red) / N;
       ++n;
       if (bad) {
         st = NSWE_ENEGDEPTH;
         break;
       }
+      // res of the new state; its Jacobian serves the next step (and is not
+      // needed once res < tol).
+      res = residual_jacobian();
       if (!(res == res) || isinf(res)) {
         st = NSWE_ENAN;
         break;
@@ -741,9 +883,11 @@ cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U,
 
 cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
                             double alpha, double *R, double *J, double *res, double *partials, cudaStream_t s) {
-  cudaError_t e = launch_residual(p, level, N, U, R, res, partials, s);
-  if (e != cudaSuccess) return e;
-  k_jacobian<<<grid_for(N * nb), kThreads, 0, s>>>(p, level, nb, U, eps, alpha, R, J);
+  k_jac_a<<<grid_for((N + 2) * 8), kThreads, 0, s>>>(p, level, U, eps);
+  k_jac_b<<<grid_for((N + 1) * 9), kThreads, 0, s>>>(p, level);
+  const int grid = grid_for(N * nb);
+  k_jac_c<<<grid, kThreads, 0, s>>>(p, level, nb, eps, alpha, R, J, partials);
+  if (res) k_finish_res<<<1, 32, 0, s>>>(partials, grid, N, res);
   return cudaGetLastError();
 }
 

@@ -30,9 +30,12 @@ namespace {
 
 // Workspace of a problem of up to NSWE_NOALLOC_MAX_CELLS cells: per level,
 // face widths (N_l+1), U, R, dU (2 N_l each), J (20 N_l), Dinv (4 N_l), each
-// slot rounded to 32 doubles; the sum over levels is below 31 * 2N + 64 * 16.
+// slot rounded to 32 doubles (below 31 * 2N + 6 * 32 * 16 over all levels),
+// plus the Jacobian workspace of the finest level (34 N + 50) and the
+// problem description and task (below 1024).
 constexpr size_t kSlot = 32;
-constexpr size_t kScratchDoubles = 31 * 2 * (size_t)NSWE_NOALLOC_MAX_CELLS + 6 * kSlot * NSWE_MAX_LEVELS + 1024;
+constexpr size_t kScratchDoubles =
+    (31 * 2 + 34) * (size_t)NSWE_NOALLOC_MAX_CELLS + 6 * kSlot * NSWE_MAX_LEVELS + 2 * kSlot + 1024;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -142,6 +145,8 @@ extern "C" nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N
       Lv.Dinv = a;
       a += slot(4 * Nl);
     }
+    P.jw = a;
+    a += slot(jw_doubles((size_t)N));
     if ((size_t)(a - base) > kScratchDoubles) {
       st = NSWE_EINVAL;  // cannot happen for N <= NSWE_NOALLOC_MAX_CELLS; kept as a guard
     } else {
