@@ -73,15 +73,17 @@ __device__ __forceinline__ void ghost(int kind, double bh, double bq, double sb,
 // the linear weights (1/3, 2/3) for U^+_{k-1/2} and (2/3, 1/3) for
 // U^-_{k+1/2}. With s_r = (zeta + beta_r)^2 the normalised weights are
 // w0 = s1/(s1 + 2 s0), w1 = 2 s0/(s1 + 2 s0) and v0 = 2 s1/(2 s1 + s0),
-// v1 = s0/(2 s1 + s0): two divisions instead of eight.
+// v1 = s0/(2 s1 + s0); both quotients share one reciprocal.
 __device__ __forceinline__ void weno3(double a, double b, double c, double &up, double &um) {
   double d0 = c - b, d1 = b - a;
   double e0 = kZeta + d0 * d0, e1 = kZeta + d1 * d1;
   double s0 = e0 * e0, s1 = e1 * e1;
   double p0 = 1.5 * b - 0.5 * c, p1 = 0.5 * a + 0.5 * b;   // U^(0), U^(1) at k-1/2
   double q0 = 0.5 * b + 0.5 * c, q1 = -0.5 * a + 1.5 * b;  // U^(0), U^(1) at k+1/2
-  up = (s1 * p0 + 2.0 * s0 * p1) / (s1 + 2.0 * s0);
-  um = (2.0 * s1 * q0 + s0 * q1) / (2.0 * s1 + s0);
+  double D1 = s1 + 2.0 * s0, D2 = 2.0 * s1 + s0;
+  double inv = 1.0 / (D1 * D2);
+  up = (s1 * p0 + 2.0 * s0 * p1) * (D2 * inv);
+  um = (2.0 * s1 * q0 + s0 * q1) * (D1 * inv);
 }
 
 // HLL flux at a face of width sig: S_L = min(u_L - c_L, u_R - c_R),
@@ -108,6 +110,40 @@ __device__ __forceinline__ void hll(double HL, double QL, double HR, double QR, 
     double iw = 1.0 / (SR - SL);
     F0 = (SR * QL - SL * QR + SL * SR * (HR - HL)) * iw;
     F1 = (SR * FL1 - SL * FR1 + SL * SR * (QR - QL)) * iw;
+  }
+}
+
+// Quantities of one interface state at a face of width 1/isg entering HLL.
+struct FState {
+  double H, Q, u, c, F1;
+};
+
+__device__ __forceinline__ FState fstate(double H, double Q, double isg, double g) {
+  FState s;
+  s.H = H;
+  s.Q = Q;
+  double iH = 1.0 / H;
+  s.u = Q * iH;
+  double h = H * isg;
+  s.c = sqrt(g * h);
+  s.F1 = Q * s.u + 0.5 * g * H * h;
+  return s;
+}
+
+// HLL combination of two interface states (same formula as hll()).
+__device__ __forceinline__ void hll_states(const FState &L, const FState &R, double &F0, double &F1) {
+  double SL = fmin(L.u - L.c, R.u - R.c);
+  double SR = fmax(L.u + L.c, R.u + R.c);
+  if (SL >= 0.0) {
+    F0 = L.Q;
+    F1 = L.F1;
+  } else if (SR <= 0.0) {
+    F0 = R.Q;
+    F1 = R.F1;
+  } else {
+    double iw = 1.0 / (SR - SL);
+    F0 = (SR * L.Q - SL * R.Q + SL * SR * (R.H - L.H)) * iw;
+    F1 = (SR * L.F1 - SL * R.F1 + SL * SR * (R.Q - L.Q)) * iw;
   }
 }
 
@@ -301,29 +337,37 @@ __device__ __forceinline__ int rec_variant(int i, int kk) {
   return (d >= -1 && d <= 1) ? d + 2 : 0;
 }
 
-// Pass B. Variant w = 0: base; w = 1 + 2p + m: cell f - 2 + p perturbed in
-// component m.
+// Pass B, one face per item. Variant w = 0: base; w = 1 + 2p + m: cell
+// f - 2 + p perturbed in component m. The left state comes from cell f-1
+// (perturbed for p = 0, 1, 2), the right state from cell f (p = 1, 2, 3);
+// the per-state HLL quantities of the base states serve all variants that do
+// not perturb that side.
 __device__ void jac_pass_b(const Geo &G, const JW &W, int first, int stride) {
-  const int N = G.N, items = (N + 1) * 9;
-  for (int it = first; it < items; it += stride) {
-    const int f = it % (N + 1), w = it / (N + 1);
-    int vL0 = 0, vL1 = 0, vR0 = 0, vR1 = 0;
-    if (w > 0) {
-      const int p = (w - 1) >> 1, m = (w - 1) & 1, i = f - 2 + p;
+  const int N = G.N;
+  for (int f = first; f <= N; f += stride) {
+    const double isg = 1.0 / G.sf[f];
+    const FState Lb = fstate(W.r(0, 0, 1, f - 1), W.r(1, 0, 1, f - 1), isg, G.g);
+    const FState Rb = fstate(W.r(0, 0, 0, f), W.r(1, 0, 0, f), isg, G.g);
+    double F0, F1;
+    hll_states(Lb, Rb, F0, F1);
+    W.f(0, 0, f) = F0;
+    W.f(0, 1, f) = F1;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int i = f - 2 + p;
       if (i < 0 || i >= N) continue;
-      const int vL = rec_variant(i, f - 1), vR = rec_variant(i, f);
-      if (m == 0) {
-        vL0 = vL;
-        vR0 = vR;
-      } else {
-        vL1 = vL;
-        vR1 = vR;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        FState Ls = Lb, Rs = Rb;
+        if (p <= 2)
+          Ls = fstate(W.r(0, m == 0 ? p + 1 : 0, 1, f - 1), W.r(1, m == 1 ? p + 1 : 0, 1, f - 1), isg, G.g);
+        if (p >= 1) Rs = fstate(W.r(0, m == 0 ? p : 0, 0, f), W.r(1, m == 1 ? p : 0, 0, f), isg, G.g);
+        hll_states(Ls, Rs, F0, F1);
+        const int w = 1 + 2 * p + m;
+        W.f(w, 0, f) = F0;
+        W.f(w, 1, f) = F1;
       }
     }
-    double F0, F1;
-    hll(W.r(0, vL0, 1, f - 1), W.r(1, vL1, 1, f - 1), W.r(0, vR0, 0, f), W.r(1, vR1, 0, f), G.sf[f], G.g, F0, F1);
-    W.f(w, 0, f) = F0;
-    W.f(w, 1, f) = F1;
   }
 }
 
@@ -355,6 +399,7 @@ __device__ double jac_pass_c(const Geo &G, int nb, double eps, double alpha, con
       continue;
     }
     const double reg = (d == 0) ? alpha * (fabs(R0) + fabs(R1)) : 0.0;
+    const double ieps = 1.0 / eps;
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
       double S = Sb;
@@ -365,7 +410,7 @@ __device__ double jac_pass_c(const Geo &G, int nb, double eps, double alpha, con
       const int wr = flux_variant(i, m, j + 1), wl = flux_variant(i, m, j);
       const double P0 = W.f(wr, 0, j + 1) - W.f(wl, 0, j);
       const double P1 = W.f(wr, 1, j + 1) - W.f(wl, 1, j) - S;
-      double v0 = (P0 - R0) / eps, v1 = (P1 - R1) / eps;
+      double v0 = (P0 - R0) * ieps, v1 = (P1 - R1) * ieps;
       if (m == 0) v0 += reg;
       else v1 += reg;
       J[(k * 4 + 0 * 2 + m) * N + j] = v0;
@@ -419,9 +464,13 @@ __device__ void coarse_op_cells(int Nf, int nbf, const double *Jf, int Nc, doubl
   }
 }
 
-// Block SOR update (Eq. 19) of the cells of one colour (j mod C == col).
+// Block SOR update (Eq. 19) of the cells of one colour (j mod C == col),
+// applied `reps` times in a row. Cells of one colour do not couple, so a
+// repeated visit of the same colour sees the same neighbour values: the
+// correction t is computed once and the relaxation applied reps times, which
+// is exactly the sequence of reps separate passes.
 __device__ void sor_colour(int N, int nb, const double *J, const double *Dinv, const double *R, double *dU,
-                           double omega, int C, int col, int first, int stride) {
+                           double omega, int C, int col, int reps, int first, int stride) {
   const int hw = (nb - 1) / 2;
   for (int j = col + C * first; j < N; j += C * stride) {
     double r0 = R[j], r1 = R[N + j];
@@ -434,8 +483,13 @@ __device__ void sor_colour(int N, int nb, const double *J, const double *Dinv, c
     }
     double t0 = Dinv[0 * N + j] * r0 + Dinv[1 * N + j] * r1;
     double t1 = Dinv[2 * N + j] * r0 + Dinv[3 * N + j] * r1;
-    dU[j] = (1.0 - omega) * dU[j] - omega * t0;
-    dU[N + j] = (1.0 - omega) * dU[N + j] - omega * t1;
+    double x0 = dU[j], x1 = dU[N + j];
+    for (int r = 0; r < reps; ++r) {
+      x0 = (1.0 - omega) * x0 - omega * t0;
+      x1 = (1.0 - omega) * x1 - omega * t1;
+    }
+    dU[j] = x0;
+    dU[N + j] = x1;
   }
 }
 
@@ -503,26 +557,159 @@ __device__ void interp_cells(const Geo &Gc, const double *Uc, double *Uf, int fi
 
 // ----------------------------------------------------------------------------
 // Coarsest direct solve: LU with partial pivoting (ties to the lowest row) of
-// the block-banded system in LAPACK-style band storage, by one warp. Unknown
-// u = 2j + m. A banded matrix keeps its zeros outside the band through the
-// elimination, so this performs the same pivots and updates as a dense LU.
+// the block-banded system, unknown u = 2j + m, in LAPACK-style band storage
+// (kl sub-diagonals, 2 kl super-diagonals after fill-in). A banded matrix
+// keeps its zeros outside the band through the elimination, so this performs
+// the same pivots and updates as a dense LU. The factorisation and the
+// triangular solves are sequential recurrences; one thread runs each with the
+// active rows in registers (a window of kl+1 rows), which keeps the latency
+// of every step to a few dependent FP64 operations.
 
 struct Band {
-  double *ab;  // [ldab][n]
-  int *piv;    // [n]
-  double *x;   // [n]
+  double *ab;    // [ldab][n]
+  int *piv;      // [n]
+  double *x;     // [n]
+  double *rinv;  // [n] reciprocals of the pivots
   int n, kl, ldab;
   __device__ __forceinline__ double &A(int r, int c) const { return ab[(2 * kl + r - c) * n + c]; }
 };
 
-// Assemble the band matrix from J (all threads), then factor (warp 0).
+template <int KL>
+__device__ bool band_lu_serial(const Band &B) {
+  constexpr int W = 2 * KL + 1;
+  const int n = B.n;
+  double w[KL + 1][W];
+#pragma unroll
+  for (int i = 0; i <= KL; ++i)
+#pragma unroll
+    for (int c = 0; c < W; ++c) w[i][c] = (i < n && c < n) ? B.A(i, c) : 0.0;
+  bool sing = false;
+  for (int k = 0; k < n; ++k) {
+    int p = 0;
+    double best = fabs(w[0][0]);
+#pragma unroll
+    for (int i = 1; i <= KL; ++i)
+      if (k + i < n && fabs(w[i][0]) > best) {
+        best = fabs(w[i][0]);
+        p = i;
+      }
+    B.piv[k] = k + p;
+#pragma unroll
+    for (int i = 1; i <= KL; ++i)
+      if (p == i)
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          double t = w[0][c];
+          w[0][c] = w[i][c];
+          w[i][c] = t;
+        }
+    const double d = w[0][0];
+    if (d == 0.0) sing = true;
+    B.rinv[k] = 1.0 / d;
+#pragma unroll
+    for (int i = 1; i <= KL; ++i)
+      if (k + i < n) {
+        const double l = w[i][0] / d;
+        B.A(k + i, k) = l;
+#pragma unroll
+        for (int c = 1; c < W; ++c) w[i][c] -= l * w[0][c];
+      }
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+      if (k + c < n) B.A(k, k + c) = w[0][c];
+    // Slide the window one row and one column.
+#pragma unroll
+    for (int i = 0; i < KL; ++i) {
+#pragma unroll
+      for (int c = 0; c < W - 1; ++c) w[i][c] = w[i + 1][c + 1];
+      w[i][W - 1] = 0.0;
+    }
+    const int r = k + KL + 1;
+#pragma unroll
+    for (int c = 0; c < W; ++c) w[KL][c] = (r < n && k + 1 + c < n) ? B.A(r, k + 1 + c) : 0.0;
+  }
+  return sing;
+}
+
+// The same factorisation working on the band storage in place (any kl); used
+// for the 5-block Jacobian of a direct solve on the coarsest nested level.
+__device__ bool band_lu_serial_smem(const Band &B) {
+  const int n = B.n, kl = B.kl;
+  bool sing = false;
+  for (int k = 0; k < n; ++k) {
+    const int imax = min(n - 1, k + kl), cmax = min(n - 1, k + 2 * kl);
+    int p = k;
+    for (int i = k + 1; i <= imax; ++i)
+      if (fabs(B.A(i, k)) > fabs(B.A(p, k))) p = i;
+    B.piv[k] = p;
+    if (p != k)
+      for (int c = k; c <= cmax; ++c) {
+        double t = B.A(k, c);
+        B.A(k, c) = B.A(p, c);
+        B.A(p, c) = t;
+      }
+    const double d = B.A(k, k);
+    if (d == 0.0) sing = true;
+    B.rinv[k] = 1.0 / d;
+    for (int i = k + 1; i <= imax; ++i) {
+      const double l = B.A(i, k) / d;
+      B.A(i, k) = l;
+      for (int c = k + 1; c <= cmax; ++c) B.A(i, c) -= l * B.A(k, c);
+    }
+  }
+  return sing;
+}
+
+// x (B.x, length n) := A^{-1} x with the stored factors (one thread).
+template <int KL>
+__device__ void band_lu_solve_serial(const Band &B) {
+  constexpr int W = 2 * KL + 1;
+  const int n = B.n;
+  double X[KL + 1];
+#pragma unroll
+  for (int i = 0; i <= KL; ++i) X[i] = i < n ? B.x[i] : 0.0;
+  for (int k = 0; k < n; ++k) {
+    const int p = B.piv[k] - k;
+#pragma unroll
+    for (int i = 1; i <= KL; ++i)
+      if (p == i) {
+        double t = X[0];
+        X[0] = X[i];
+        X[i] = t;
+      }
+#pragma unroll
+    for (int i = 1; i <= KL; ++i)
+      if (k + i < n) X[i] -= B.A(k + i, k) * X[0];
+    B.x[k] = X[0];
+#pragma unroll
+    for (int i = 0; i < KL; ++i) X[i] = X[i + 1];
+    X[KL] = (k + KL + 1 < n) ? B.x[k + KL + 1] : 0.0;
+  }
+  double Y[W - 1];  // Y[c] = x[i + 1 + c]
+#pragma unroll
+  for (int c = 0; c < W - 1; ++c) Y[c] = 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    double s = B.x[i];
+#pragma unroll
+    for (int c = W - 2; c >= 1; --c)
+      if (i + 1 + c < n) s -= B.A(i, i + 1 + c) * Y[c];
+    if (i + 1 < n) s -= B.A(i, i + 1) * Y[0];
+    const double xi = s * B.rinv[i];
+    B.x[i] = xi;
+#pragma unroll
+    for (int c = W - 2; c >= 1; --c) Y[c] = Y[c - 1];
+    Y[0] = xi;
+  }
+}
+
+// Assemble the band matrix from J (all threads), then factor (thread 0).
 // Returns true if a pivot was exactly zero (all threads).
 __device__ bool band_factor(Band &B, int N, int nb, const double *J) {
   const int hw = (nb - 1) / 2;
   B.n = 2 * N;
   B.kl = 2 * hw + 1;
   B.ldab = 3 * B.kl + 1;
-  const int n = B.n, kl = B.kl;
+  const int n = B.n;
   for (int t = threadIdx.x; t < B.ldab * n; t += blockDim.x) B.ab[t] = 0.0;
   __syncthreads();
   for (int t = threadIdx.x; t < N * nb * 4; t += blockDim.x) {
@@ -533,80 +720,21 @@ __device__ bool band_factor(Band &B, int N, int nb, const double *J) {
   }
   __syncthreads();
   __shared__ int s_sing;
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int sing = 0;
-    for (int k = 0; k < n; ++k) {
-      const int imax = min(n - 1, k + kl), cmax = min(n - 1, k + 2 * kl);
-      double v = -1.0;
-      int idx = n;
-      if (k + lane <= imax) {
-        v = fabs(B.A(k + lane, k));
-        idx = k + lane;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, v, o);
-        int oi = __shfl_down_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi < idx)) {
-          v = ov;
-          idx = oi;
-        }
-      }
-      const int p = __shfl_sync(0xffffffffu, idx, 0);
-      if (lane == 0) B.piv[k] = p;
-      if (p != k)
-        for (int c = k + lane; c <= cmax; c += 32) {
-          double t = B.A(k, c);
-          B.A(k, c) = B.A(p, c);
-          B.A(p, c) = t;
-        }
-      __syncwarp();
-      const double pv = B.A(k, k);
-      if (pv == 0.0) sing = 1;
-      for (int i = k + 1 + lane; i <= imax; i += 32) B.A(i, k) = B.A(i, k) / pv;
-      __syncwarp();
-      const int ni = imax - k, nc = cmax - k;
-      for (int t = lane; t < ni * nc; t += 32) {
-        int i = k + 1 + t / nc, c = k + 1 + t % nc;
-        B.A(i, c) -= B.A(i, k) * B.A(k, c);
-      }
-      __syncwarp();
-    }
-    if (lane == 0) s_sing = sing;
-  }
+  if (threadIdx.x == 0) s_sing = (B.kl == 3 ? band_lu_serial<3>(B) : band_lu_serial_smem(B)) ? 1 : 0;
   __syncthreads();
   return s_sing != 0;
 }
 
-// dU = -J^{-1} R with the stored factors (warp 0 works, all threads call).
+// dU = -J^{-1} R with the stored factors (thread 0 solves, all threads call).
 __device__ void band_solve(const Band &B, int N, const double *R, double *dU) {
-  const int n = B.n, kl = B.kl;
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     B.x[2 * t] = -R[t];
     B.x[2 * t + 1] = -R[N + t];
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int k = 0; k < n; ++k) {
-      const int p = B.piv[k];
-      if (p != k && lane == 0) {
-        double t = B.x[k];
-        B.x[k] = B.x[p];
-        B.x[p] = t;
-      }
-      __syncwarp();
-      const double xk = B.x[k];
-      for (int i = k + 1 + lane; i <= min(n - 1, k + kl); i += 32) B.x[i] -= B.A(i, k) * xk;
-      __syncwarp();
-    }
-    if (lane == 0) {
-      for (int i = n - 1; i >= 0; --i) {
-        double s = B.x[i];
-        for (int c = i + 1; c <= min(n - 1, i + 2 * kl); ++c) s -= B.A(i, c) * B.x[c];
-        B.x[i] = s / B.A(i, i);
-      }
-    }
+  if (threadIdx.x == 0) {
+    if (B.kl == 3) band_lu_solve_serial<3>(B);
+    else band_lu_solve_serial<5>(B);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -649,11 +777,28 @@ __device__ bool mg_setup(const MG &mg, Band &B) {
   return band_factor(B, mg.N[mg.L], mg.nb[mg.L], mg.J[mg.L]);
 }
 
-__device__ void sor_step(const MG &mg, int l, double omega) {
+// `steps` symmetric multicolour SOR steps (colours 0..C-1 then C-1..0 each);
+// consecutive visits of one colour run as one pass.
+__device__ void sor_smooth(const MG &mg, int l, int steps, double omega) {
   const int nb = mg.nb[l], C = (nb - 1) / 2 + 1;
-  for (int pass = 0; pass < 2 * C; ++pass) {
-    int col = pass < C ? pass : 2 * C - 1 - pass;
-    sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, col, threadIdx.x, blockDim.x);
+  int prev = -1, reps = 0;
+  for (int s = 0; s < steps; ++s)
+    for (int pass = 0; pass < 2 * C; ++pass) {
+      const int col = pass < C ? pass : 2 * C - 1 - pass;
+      if (col == prev) {
+        ++reps;
+        continue;
+      }
+      if (prev >= 0) {
+        sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, prev, reps, threadIdx.x,
+                   blockDim.x);
+        __syncthreads();
+      }
+      prev = col;
+      reps = 1;
+    }
+  if (prev >= 0) {
+    sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, prev, reps, threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
@@ -661,7 +806,7 @@ __device__ void sor_step(const MG &mg, int l, double omega) {
 // Algorithm 2 from level l0, unrolled over levels.
 __device__ void mg_vcycle(const MG &mg, const Band &B, const nswe_params &prm) {
   for (int l = mg.l0; l < mg.L; ++l) {
-    for (int s = 0; s < prm.nu1; ++s) sor_step(mg, l, prm.omega);
+    sor_smooth(mg, l, prm.nu1, prm.omega);
     restrict_cells(mg.N[l], mg.nb[l], mg.J[l], mg.R[l], mg.dU[l], mg.N[l + 1], mg.R[l + 1], mg.dU[l + 1],
                    threadIdx.x, blockDim.x);
     __syncthreads();
@@ -670,14 +815,15 @@ __device__ void mg_vcycle(const MG &mg, const Band &B, const nswe_params &prm) {
   for (int l = mg.L - 1; l >= mg.l0; --l) {
     prolong_cells(mg.N[l], mg.dU[l], mg.N[l + 1], mg.dU[l + 1], threadIdx.x, blockDim.x);
     __syncthreads();
-    for (int s = 0; s < prm.nu2; ++s) sor_step(mg, l, prm.omega);
+    sor_smooth(mg, l, prm.nu2, prm.omega);
   }
 }
 
 struct SmemBand {
   double ab[kLdab * kMaxDense];
-  int piv[kMaxDense];
   double x[kMaxDense];
+  double rinv[kMaxDense];
+  int piv[kMaxDense];
 };
 
 __device__ __forceinline__ Band band_view(SmemBand &s) {
@@ -685,6 +831,7 @@ __device__ __forceinline__ Band band_view(SmemBand &s) {
   B.ab = s.ab;
   B.piv = s.piv;
   B.x = s.x;
+  B.rinv = s.rinv;
   B.n = B.kl = B.ldab = 0;
   return B;
 }
@@ -884,7 +1031,7 @@ cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U,
 cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
                             double alpha, double *R, double *J, double *res, double *partials, cudaStream_t s) {
   k_jac_a<<<grid_for((N + 2) * 8), kThreads, 0, s>>>(p, level, U, eps);
-  k_jac_b<<<grid_for((N + 1) * 9), kThreads, 0, s>>>(p, level);
+  k_jac_b<<<grid_for(N + 1), kThreads, 0, s>>>(p, level);
   const int grid = grid_for(N * nb);
   k_jac_c<<<grid, kThreads, 0, s>>>(p, level, nb, eps, alpha, R, J, partials);
   if (res) k_finish_res<<<1, 32, 0, s>>>(partials, grid, N, res);
