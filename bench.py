@@ -57,16 +57,40 @@ def make_instances(first, count, nb):
 
 # ------------------------------------------------------------------------------------------------
 # Algorithmic FP64 flop count of one solve (add/sub/mul = 1, fused multiply-add = 2, division = 1,
-# square root = 1), from the operation counts of each step of the method; per cell unless noted.
-F_RES = 331          # one local residual: 6 WENO3 (34), 2 HLL (43), Gauss source (36), R (3), |R|_1 (2)
-F_JAC_BLOCK = 668    # one Jacobian block: 2 perturbed local residuals (329+1) + 2 differences + 2 divisions
+# square root = 1), following the steps the kernels execute; per cell unless noted.
+F_WENO = 38          # one component of one cell: smoothness, candidates, one reciprocal, two weights
+F_STATE = 10         # HLL quantities of one interface state (1/H, u, h, c, physical flux)
+F_HLL = 20           # HLL combination of two states
+F_SOURCE = 36        # two-point Gauss source of one cell (Eq. 9)
 F_UPDATE = 4         # damped Newton update of H and Q
 F_DINV = 9           # 2x2 inverse
 F_INTERP = 8         # App. A per fine cell
 
 
-def f_sor(nb):       # one block-SOR update of one cell
-    return 8 * (nb - 1) + 12
+def f_res_jac(nb):
+    """Residual + FD Jacobian per cell: 8 WENO variants (+6 perturbations),
+    per face 1 reciprocal + 14 states + 9 HLL combinations, per block two
+    sources, differences and scaling (+6 for the diagonal)."""
+    pass_a = 8 * F_WENO + 6
+    pass_b = 1 + 14 * F_STATE + 9 * F_HLL
+    pass_c = nb * (2 * F_SOURCE + 18) + 6
+    return pass_a + pass_b + pass_c
+
+
+def f_smooth(N, nb, steps):
+    """Fused multicolour SOR: per pass the neighbour sum and D^-1 product
+    once (8(nb-1)+6) and the relaxation per repeat (6), cells of one colour."""
+    C = (nb - 1) // 2 + 1
+    seq = [c for _ in range(steps) for c in list(range(C)) + list(range(C - 1, -1, -1))]
+    tot, i = 0, 0
+    while i < len(seq):
+        j = i
+        while j < len(seq) and seq[j] == seq[i]:
+            j += 1
+        ncell = len(range(seq[i], N, C))
+        tot += ncell * (8 * (nb - 1) + 6 + 6 * (j - i))
+        i = j
+    return tot
 
 
 def f_restrict(nb):  # per coarse cell
@@ -74,7 +98,7 @@ def f_restrict(nb):  # per coarse cell
 
 
 def lu_flops(n, kl):
-    return n * (kl + 4 * kl * kl), n * (6 * kl + 1)  # factor, solve
+    return n * (kl + 1 + 4 * kl * kl), n * (6 * kl + 1)  # factor, solve
 
 
 def solve_flops(N, levels, start, iters, nb, nu1, nu2, nu3):
@@ -84,8 +108,8 @@ def solve_flops(N, levels, start, iters, nb, nu1, nu2, nu3):
         Nl = N >> l
         if l < start:
             tot += F_INTERP * Nl
-        tot += F_RES * Nl  # initial residual of the level
-        per = Nl * (nb * F_JAC_BLOCK + 2) + Nl * (F_RES + F_UPDATE)
+        tot += f_res_jac(nb) * Nl  # R, J of the level's initial state
+        per = Nl * (f_res_jac(nb) + F_UPDATE)
         nbl = [nb if k == l else 3 for k in range(L + 1)]
         for k in range(l + 1, L + 1):
             per += 8 * nbl[k - 1] * (N >> k)
@@ -100,7 +124,8 @@ def solve_flops(N, levels, start, iters, nb, nu1, nu2, nu3):
             vc = sol
             for k in range(l, L):
                 Nk = N >> k
-                vc += (nu1 + nu2) * 2 * Nk * f_sor(nbl[k]) + (N >> (k + 1)) * f_restrict(nbl[k]) + 2 * Nk
+                vc += f_smooth(Nk, nbl[k], nu1) + f_smooth(Nk, nbl[k], nu2) + (N >> (k + 1)) * f_restrict(nbl[k]) \
+                    + 2 * Nk
             per += nu3 * vc
         tot += iters[l] * per
     return tot

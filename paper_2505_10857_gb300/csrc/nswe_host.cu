@@ -336,7 +336,10 @@ nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb, cons
   nswe_status st = check_params(params, nullptr, 0);
   if (st != NSWE_OK) return st;
   DeviceGuard dg(ctx->device);
-  return launch_vcycle(prob->dev, level, nb, J, R, dU, *params, ctx->status, ctx->stream) == cudaSuccess
+  const int coarse = prob->N >> (prob->levels - 1);
+  const int coarse_nb = (level == prob->levels - 1) ? nb : 3;
+  return launch_vcycle(prob->dev, level, nb, J, R, dU, *params, ctx->status, coarse, coarse_nb, ctx->stream) ==
+                 cudaSuccess
              ? NSWE_OK
              : NSWE_ECUDA;
 }
@@ -358,7 +361,10 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
   DeviceGuard dg(ctx->device);
   nswe_status st = ensure_cap(ctx, count);
   if (st != NSWE_OK) return st;
+  int max_coarse = 4;
   for (int i = 0; i < count; ++i) {
+    const int c = probs[i]->N >> (probs[i]->levels - 1);
+    if (c > max_coarse) max_coarse = c;
     tasks[i].prob = probs[i]->dev;
     tasks[i].U0 = U0s[i];
     tasks[i].U = Us[i];
@@ -368,7 +374,7 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
   if (cudaMemcpyAsync(ctx->tasks, tasks.data(), sizeof(SolveTask) * count, cudaMemcpyHostToDevice, s) !=
       cudaSuccess)
     return NSWE_ECUDA;
-  if (launch_solve(ctx->tasks, count, *params, s) != cudaSuccess) return NSWE_ECUDA;
+  if (launch_solve(ctx->tasks, count, *params, max_coarse, s) != cudaSuccess) return NSWE_ECUDA;
   if (infos) {
     if (cudaMemcpyAsync(infos, ctx->infos, sizeof(nswe_info) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return NSWE_ECUDA;

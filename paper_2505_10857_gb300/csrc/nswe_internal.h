@@ -8,11 +8,14 @@
 
 namespace nswe {
 
-constexpr int kThreads = 256;      // threads per block of every 1D kernel
+#ifndef NSWE_THREADS
+#define NSWE_THREADS 256           // threads per block of every 1D kernel
+#endif
+#ifndef NSWE_SOLVE_MIN_BLOCKS
+#define NSWE_SOLVE_MIN_BLOCKS 4    // resident blocks per SM the solve kernel is built for
+#endif
+constexpr int kThreads = NSWE_THREADS;
 constexpr int kMaxCoarse = 128;    // max cells of the coarsest level (direct solve)
-constexpr int kMaxDense = 2 * kMaxCoarse;
-constexpr int kMaxKl = 5;          // scalar lower bandwidth of J5 (2*2+1)
-constexpr int kLdab = 3 * kMaxKl + 1;  // band storage rows for LU with pivoting
 
 // One nested / multigrid level of a 1D problem. Geometry is read-only input;
 // the rest is solver workspace owned by the problem.
@@ -54,8 +57,11 @@ cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U,
 cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
                             double alpha, double *R, double *J, double *res, double *partials,
                             cudaStream_t s);
+// coarse_cells: cells of the coarsest level; coarse_nb: its block band (3 or 5).
 cudaError_t launch_vcycle(const ProbDev *p, int level, int nb, const double *J, const double *R, double *dU,
-                          const nswe_params &prm, int *status, cudaStream_t s);
-cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, cudaStream_t s);
+                          const nswe_params &prm, int *status, int coarse_cells, int coarse_nb, cudaStream_t s);
+// max_coarse_cells: largest coarsest level over the tasks.
+cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
+                         cudaStream_t s);
 
 }  // namespace nswe

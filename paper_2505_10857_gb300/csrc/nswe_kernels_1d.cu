@@ -819,19 +819,16 @@ __device__ void mg_vcycle(const MG &mg, const Band &B, const nswe_params &prm) {
   }
 }
 
-struct SmemBand {
-  double ab[kLdab * kMaxDense];
-  double x[kMaxDense];
-  double rinv[kMaxDense];
-  int piv[kMaxDense];
-};
+// Band storage in dynamic shared memory, sized by the host for the coarsest
+// level: ab [ldab_cap * n_cap], x [n_cap], rinv [n_cap], piv [n_cap].
+extern __shared__ double g_dyn_smem[];
 
-__device__ __forceinline__ Band band_view(SmemBand &s) {
+__device__ __forceinline__ Band band_view(int n_cap, int ldab_cap) {
   Band B;
-  B.ab = s.ab;
-  B.piv = s.piv;
-  B.x = s.x;
-  B.rinv = s.rinv;
+  B.ab = g_dyn_smem;
+  B.x = B.ab + (size_t)ldab_cap * n_cap;
+  B.rinv = B.x + n_cap;
+  B.piv = reinterpret_cast<int *>(B.rinv + n_cap);
   B.n = B.kl = B.ldab = 0;
   return B;
 }
@@ -883,11 +880,11 @@ __global__ void __launch_bounds__(kThreads) k_jac_c(const ProbDev *P, int level,
 }
 
 __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level, int nb, const double *J,
-                                                     const double *R, double *dU, nswe_params prm, int *status) {
-  __shared__ SmemBand sb;
+                                                     const double *R, double *dU, nswe_params prm, int *status,
+                                                     int n_cap, int ldab_cap) {
   MG mg;
   mg_bind(mg, *P, level, nb, J, R, dU);
-  Band B = band_view(sb);
+  Band B = band_view(n_cap, ldab_cap);
   bool sing = mg_setup(mg, B);
   __syncthreads();
   mg_vcycle(mg, B, prm);
@@ -895,8 +892,8 @@ __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level
 }
 
 // Algorithm 3 for one problem per thread block.
-__global__ void __launch_bounds__(kThreads) k_solve(const SolveTask *tasks, nswe_params prm) {
-  __shared__ SmemBand sb;
+__global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
+    k_solve(const SolveTask *tasks, nswe_params prm, int n_cap, int ldab_cap) {
   __shared__ double red[33];
   const unsigned long long t_start = global_ns();
   const SolveTask task = tasks[blockIdx.x];
@@ -904,7 +901,7 @@ __global__ void __launch_bounds__(kThreads) k_solve(const SolveTask *tasks, nswe
   const int L = P.levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
   const int nb = prm.jacobian == NSWE_JAC_FULL ? 5 : 3;
-  Band B = band_view(sb);
+  Band B = band_view(n_cap, ldab_cap);
 
   int iters[NSWE_MAX_LEVELS], lstat[NSWE_MAX_LEVELS];
   double lres[NSWE_MAX_LEVELS];
@@ -1038,14 +1035,22 @@ cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const do
   return cudaGetLastError();
 }
 
+size_t band_smem_bytes(int n_cap, int ldab_cap) {
+  return sizeof(double) * ((size_t)ldab_cap * n_cap + 2 * (size_t)n_cap) + sizeof(int) * (size_t)n_cap;
+}
+
 cudaError_t launch_vcycle(const ProbDev *p, int level, int nb, const double *J, const double *R, double *dU,
-                          const nswe_params &prm, int *status, cudaStream_t s) {
-  k_vcycle<<<1, kThreads, 0, s>>>(p, level, nb, J, R, dU, prm, status);
+                          const nswe_params &prm, int *status, int coarse_cells, int coarse_nb, cudaStream_t s) {
+  const int n_cap = 2 * coarse_cells, ldab_cap = 3 * (coarse_nb == 5 ? 5 : 3) + 1;
+  k_vcycle<<<1, kThreads, band_smem_bytes(n_cap, ldab_cap), s>>>(p, level, nb, J, R, dU, prm, status, n_cap,
+                                                                ldab_cap);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, cudaStream_t s) {
-  k_solve<<<count, kThreads, 0, s>>>(tasks, prm);
+cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
+                         cudaStream_t s) {
+  const int n_cap = 2 * max_coarse_cells, ldab_cap = 3 * (prm.jacobian == NSWE_JAC_FULL ? 5 : 3) + 1;
+  k_solve<<<count, kThreads, band_smem_bytes(n_cap, ldab_cap), s>>>(tasks, prm, n_cap, ldab_cap);
   return cudaGetLastError();
 }
 

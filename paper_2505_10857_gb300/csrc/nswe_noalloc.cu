@@ -157,7 +157,7 @@ extern "C" nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N
       T.info = info;
       cudaStream_t s = (cudaStream_t)stream;
       k_noalloc_setup<<<1, kThreads, 0, s>>>(P, T, prob_slot, task_slot, sigma_face);
-      if (cudaGetLastError() != cudaSuccess || launch_solve(task_slot, 1, p, s) != cudaSuccess) st = NSWE_ECUDA;
+      if (cudaGetLastError() != cudaSuccess || launch_solve(task_slot, 1, p, NL, s) != cudaSuccess) st = NSWE_ECUDA;
     }
   }
   if (prev != device) cudaSetDevice(prev);
