@@ -420,7 +420,7 @@ static void mg_free(or_mg1d *mg) {
 
 /* Build the coarse operators (Eq. 17) and diagonal inverses for all levels;
  * J is fixed during the V-cycles of one Newton step, so this is done once per
- * step (equivalent to line 6 of Algorithm 2). */
+ * step (equivalent to building them inside each V-cycle of Algorithm 2). */
 static void mg_setup(or_mg1d *mg) {
   for (int l = 1; l <= mg->L; ++l)
     or_coarse_operator1d(mg->N[l - 1], l == 1 ? mg->nb0 : 3, mg->J[l - 1], mg->J[l]);
