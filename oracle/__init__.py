@@ -26,7 +26,8 @@ _lock = threading.Lock()
 _lib = None
 
 BC_DISCHARGE, BC_DEPTH, BC_STATE, BC_EXTRAP = 1, 2, 3, 4
-BC_REFLECT, BC_INFLOW, BC_OUTFLOW = 5, 6, 7
+BC_REFLECT, BC_INFLOW, BC_OUTFLOW, BC2_DISCHARGE, BC2_DEPTH = 5, 6, 7, 8, 9
+ST_J9, ST_J21, ST_P5, ST_P9 = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +73,31 @@ class Info1D(ctypes.Structure):
     ]
 
 
+class Grid2D(ctypes.Structure):
+    _fields_ = [
+        ("Nx", ctypes.c_int), ("Ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("g", ctypes.c_double),
+        ("gq", ctypes.POINTER(ctypes.c_double)),
+        ("bc_kind", ctypes.POINTER(ctypes.c_int)),
+        ("bc_state", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class Params2D(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("omega", ctypes.c_double), ("tol", ctypes.c_double),
+        ("nu1", ctypes.c_int * 16), ("nu2", ctypes.c_int * 16),
+        ("nu3", ctypes.c_int), ("levels", ctypes.c_int), ("n_max", ctypes.c_int), ("st", ctypes.c_int),
+        ("nest_start", ctypes.c_int), ("eps", ctypes.c_double),
+    ]
+
+
+class Info2D(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int * 16), ("res", ctypes.c_double * 16),
+                ("total_iters", ctypes.c_int), ("vcycles", ctypes.c_int)]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 
 
@@ -103,6 +129,27 @@ def _lib_handle():
                 "or_nmgm1d": (i32, [P(Grid1D), _D, _D, P(Params1D), P(Info1D)]),
                 "or_newton1d": (i32, [P(Grid1D), _D, i32, dbl, P(Params1D), P(Info1D)]),
             }
+            G2 = P(Grid2D)
+            sig.update({
+                "or_llf2d": (None, [i32, _D, _D, dbl, _D]),
+                "or_residual_cell2d": (None, [G2, _D, i32, i32, _D]),
+                "or_residual2d": (dbl, [G2, _D, _D]),
+                "or_jacobian2d": (dbl, [G2, _D, dbl, dbl, i32, _D, _D]),
+                "or_stencil_size": (i32, [i32]),
+                "or_stencil_offset": (i32, [i32, i32, i32]),
+                "or_coarse_operator2d": (None, [i32, i32, i32, _D, _D]),
+                "or_block_inverse2d": (None, [i32, i32, _D, _D]),
+                "or_colours2d": (i32, [i32]),
+                "or_colour_of": (i32, [i32, i32, i32]),
+                "or_sor_step2d": (None, [i32, i32, i32, _D, _D, _D, _D, dbl]),
+                "or_restrict2d": (None, [i32, i32, i32, _D, _D, _D, _D]),
+                "or_prolong2d": (None, [i32, i32, _D, _D]),
+                "or_direct_solve2d": (i32, [i32, i32, i32, _D, _D, _D]),
+                "or_vcycle2d": (i32, [i32, i32, i32, i32, _D, _D, _D, dbl, i32, i32]),
+                "or_interp2d": (None, [G2, _D, _D]),
+                "or_nmgm2d": (i32, [G2, _D, _D, P(Params2D), P(Info2D)]),
+                "or_newton2d": (i32, [G2, _D, i32, P(Params2D), P(Info2D)]),
+            })
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
                 f.restype = res
@@ -327,3 +374,169 @@ def params_from(prm):
 def solve_problem(inp, prm):
     """Nested NMGM of an inputs.Problem1DInputs with inputs.Params1D."""
     return nmgm1d(problem_levels(inp), inp.U0_start, params_from(prm))
+
+
+# ------------------------------------------------------------------------------------------------
+# Two-dimensional oracle (Section 4).
+
+class Problem2D:
+    """One nested level of a 2D problem: gq [2,4,Ny*Nx] (b_x, b_y at the Gauss
+    points q = 2*beta + gamma), bc_kind [2*Ny + 2*Nx] (left, right, bottom,
+    top), bc_state [4,3] (per side (h, hu, hv) data)."""
+
+    def __init__(self, Nx, Ny, x0, x1, y0, y1, g, gq, bc_kind, bc_state):
+        self.Nx, self.Ny = int(Nx), int(Ny)
+        self.gq = _f64(gq).reshape(-1)
+        self.kind = np.ascontiguousarray(bc_kind, dtype=np.int32).reshape(-1)
+        self.state = _f64(bc_state).reshape(-1)
+        assert self.gq.size == 8 * Nx * Ny and self.kind.size == 2 * (Nx + Ny) and self.state.size == 12
+        self.s = Grid2D(self.Nx, self.Ny, float(x0), float(x1), float(y0), float(y1), (x1 - x0) / Nx,
+                        (y1 - y0) / Ny, float(g), ptr(self.gq),
+                        self.kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptr(self.state))
+
+    @property
+    def n(self):
+        return self.Nx * self.Ny
+
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def residual2d(prob: Problem2D, U):
+    U = _f64(U).reshape(3, prob.n).copy()
+    R = np.zeros((3, prob.n))
+    res = lib().or_residual2d(prob.ref(), ptr(U), ptr(R))
+    return R, res
+
+
+def residual_cell2d(prob: Problem2D, U, i, j):
+    U = _f64(U).reshape(3, prob.n).copy()
+    R = np.zeros(3)
+    lib().or_residual_cell2d(prob.ref(), ptr(U), int(i), int(j), ptr(R))
+    return R
+
+
+def llf2d(direction, UL, UR, g):
+    UL, UR, F = _f64(UL).copy(), _f64(UR).copy(), np.zeros(3)
+    lib().or_llf2d(int(direction), ptr(UL), ptr(UR), float(g), ptr(F))
+    return F
+
+
+def stencil2d(st):
+    K = lib().or_stencil_size(st)
+    return [(lib().or_stencil_offset(st, k, 0), lib().or_stencil_offset(st, k, 1)) for k in range(K)]
+
+
+def jacobian2d(prob: Problem2D, U, eps, alpha, st):
+    U = _f64(U).reshape(3, prob.n).copy()
+    K = lib().or_stencil_size(st)
+    R = np.zeros((3, prob.n))
+    J = np.zeros((K, 9, prob.n))
+    res = lib().or_jacobian2d(prob.ref(), ptr(U), float(eps), float(alpha), int(st), ptr(R), ptr(J))
+    return J, R, res
+
+
+def coarse_stencil(st):
+    return ST_P5 if st in (ST_J9, ST_P5) else ST_P9
+
+
+def coarse_operator2d(Jf, Nx, Ny, st):
+    Jf = _f64(Jf)
+    cs = coarse_stencil(st)
+    Jc = np.zeros((lib().or_stencil_size(cs), 9, (Nx // 2) * (Ny // 2)))
+    lib().or_coarse_operator2d(Nx, Ny, st, ptr(Jf), ptr(Jc))
+    return Jc
+
+
+def block_inverse2d(J, st):
+    J = _f64(J)
+    n = J.shape[-1]
+    D = np.zeros((9, n))
+    lib().or_block_inverse2d(n, st, ptr(J), ptr(D))
+    return D
+
+
+def sor_step2d(J, Dinv, R, dU, Nx, Ny, st, omega):
+    J, Dinv, R = _f64(J), _f64(Dinv), _f64(R)
+    dU = _f64(dU).copy()
+    lib().or_sor_step2d(Nx, Ny, st, ptr(J), ptr(Dinv), ptr(R), ptr(dU), float(omega))
+    return dU
+
+
+def restrict2d(J, R, dU, Nx, Ny, st):
+    J, R, dU = _f64(J), _f64(R), _f64(dU)
+    Rc = np.zeros((3, (Nx // 2) * (Ny // 2)))
+    lib().or_restrict2d(Nx, Ny, st, ptr(J), ptr(R), ptr(dU), ptr(Rc))
+    return Rc
+
+
+def prolong2d(dU, dUc, Nx, Ny):
+    dU = _f64(dU).copy()
+    lib().or_prolong2d(Nx, Ny, ptr(dU), ptr(_f64(dUc)))
+    return dU
+
+
+def direct_solve2d(J, R, Nx, Ny, st):
+    J, R = _f64(J), _f64(R)
+    dU = np.zeros((3, Nx * Ny))
+    if lib().or_direct_solve2d(Nx, Ny, st, ptr(J), ptr(R), ptr(dU)):
+        raise ZeroDivisionError("zero pivot")
+    return dU
+
+
+def vcycle2d(J, R, dU, Nx, Ny, st, nlev, omega, nu1, nu2):
+    J, R = _f64(J), _f64(R)
+    dU = _f64(dU).copy()
+    if lib().or_vcycle2d(Nx, Ny, st, nlev, ptr(J), ptr(R), ptr(dU), float(omega), int(nu1), int(nu2)):
+        raise ZeroDivisionError("zero pivot")
+    return dU
+
+
+def interp2d(prob_coarse: Problem2D, Uc):
+    Uc = _f64(Uc).reshape(3, prob_coarse.n)
+    Uf = np.zeros((3, 4 * prob_coarse.n))
+    lib().or_interp2d(prob_coarse.ref(), ptr(Uc), ptr(Uf))
+    return Uf
+
+
+def make_params2d(alpha, tau, omega, tol, nu1, nu2, nu3, levels, n_max, st, eps, nest_start=-1):
+    p = Params2D()
+    p.alpha, p.tau, p.omega, p.tol = alpha, tau, omega, tol
+    nu1 = list(nu1) if hasattr(nu1, "__len__") else [nu1] * 16
+    nu2 = list(nu2) if hasattr(nu2, "__len__") else [nu2] * 16
+    for i in range(16):
+        p.nu1[i] = int(nu1[min(i, len(nu1) - 1)])
+        p.nu2[i] = int(nu2[min(i, len(nu2) - 1)])
+    p.nu3, p.levels, p.n_max, p.st, p.nest_start, p.eps = nu3, levels, n_max, st, nest_start, eps
+    return p
+
+
+def problem_levels2d(inp):
+    return [Problem2D(inp.Nx >> l, inp.Ny >> l, inp.x0, inp.x1, inp.y0, inp.y1, inp.g, inp.gq[l], inp.bc_kind[l],
+                      inp.bc_state) for l in range(inp.levels)]
+
+
+def solve_problem2d(inp, prm):
+    """Nested NMGM (Algorithm 3) of an inputs.Problem2DInputs."""
+    probs = problem_levels2d(inp)
+    arr = (Grid2D * len(probs))(*[p.s for p in probs])
+    p = make_params2d(prm.alpha, prm.tau, prm.omega, prm.tol, prm.nu1, prm.nu2, prm.nu3, prm.levels, prm.n_max,
+                      prm.st, prm.eps, prm.nest_start)
+    U0 = _f64(inp.U0_start).reshape(-1)
+    U = np.zeros(3 * inp.Nx * inp.Ny)
+    info = Info2D()
+    lib().or_nmgm2d(arr, ptr(U0), ptr(U), ctypes.byref(p), ctypes.byref(info))
+    L = prm.levels
+    return U.reshape(3, -1), {"status": info.status, "iters": [info.iters[l] for l in range(L)],
+                              "res": [info.res[l] for l in range(L)], "total_iters": info.total_iters,
+                              "vcycles": info.vcycles}
+
+
+def newton2d(prob: Problem2D, U_init, nlev, prm):
+    p = make_params2d(prm.alpha, prm.tau, prm.omega, prm.tol, prm.nu1, prm.nu2, prm.nu3, nlev, prm.n_max,
+                      prm.st, prm.eps)
+    U = _f64(U_init).reshape(-1).copy()
+    info = Info2D()
+    lib().or_newton2d(prob.ref(), ptr(U), int(nlev), ctypes.byref(p), ctypes.byref(info))
+    return U.reshape(3, -1), {"status": info.status, "iters": info.iters[0], "res": info.res[0],
+                              "vcycles": info.vcycles}

@@ -334,3 +334,191 @@ def random_state(rng, N, H_range=(1.5, 2.5), Q_range=(3.5, 5.0)):
     H = rng.uniform(*H_range) + 0.2 * np.sin(2 * np.pi * rng.uniform(1, 3) * x) + 0.02 * rng.standard_normal(N)
     Q = rng.uniform(*Q_range) + 0.1 * np.cos(2 * np.pi * rng.uniform(1, 3) * x) + 0.02 * rng.standard_normal(N)
     return np.ascontiguousarray(np.stack([H, Q]))
+
+
+# ==========================================================================
+# Two-dimensional problems (Section 4; Section 5.2 workloads).
+#
+# Sampling contract (2D): cell (i, j) of an Nx x Ny grid over [x0,x1]x[y0,y1]
+# has centre (x_i, y_j) and Gauss points x_i^g = x_i -+ dx/(2 sqrt 3) (g = 0, 1),
+# y_j^b = y_j -+ dy/(2 sqrt 3) (b = 0, 1); gq[2][4][Ny*Nx] holds b_x and b_y at
+# point q = 2 b + g, cell index j*Nx + i. Boundary kinds per boundary cell:
+# [Ny left | Ny right | Nx bottom | Nx top]; bc_state[4][3] gives the (h, hu,
+# hv) data per side (left, right, bottom, top).
+
+BC2_REFLECT, BC2_INFLOW, BC2_OUTFLOW, BC2_DISCHARGE, BC2_DEPTH = 5, 6, 7, 8, 9
+ST_J9, ST_J21, ST_P5, ST_P9 = 0, 1, 2, 3
+
+
+def bottom2d_flat():
+    z = lambda x, y: np.zeros(np.broadcast(x, y).shape)
+    return z, z, z
+
+
+def bottom2d_linear(b0, sx, sy):
+    def b(x, y):
+        return b0 + sx * np.asarray(x, dtype=np.float64) + sy * np.asarray(y, dtype=np.float64)
+    return (b, lambda x, y: np.full(np.broadcast(x, y).shape, float(sx)),
+            lambda x, y: np.full(np.broadcast(x, y).shape, float(sy)))
+
+
+def bottom2d_eq29():
+    """Parabolic bump of Eq. 29 on [-4, 4] x [0, 4]."""
+    def r2(x, y):
+        return np.asarray(x, dtype=np.float64) ** 2 + (np.asarray(y, dtype=np.float64) - 2.0) ** 2
+
+    def b(x, y):
+        return np.where(r2(x, y) < 1.0, 0.4 - 0.4 * r2(x, y), 0.0)
+
+    def bx(x, y):
+        return np.where(r2(x, y) < 1.0, -0.8 * np.asarray(x, dtype=np.float64), 0.0)
+
+    def by(x, y):
+        return np.where(r2(x, y) < 1.0, -0.8 * (np.asarray(y, dtype=np.float64) - 2.0), 0.0)
+    return b, bx, by
+
+
+def bottom2d_gaussians(bumps):
+    """Sum of Gaussian bumps A exp(-((x-xc)^2 + (y-yc)^2)/w^2)."""
+    def b(x, y):
+        return sum(A * np.exp(-((x - xc) ** 2 + (y - yc) ** 2) / (w * w)) for A, xc, yc, w in bumps) + 0 * x
+
+    def bx(x, y):
+        return sum(-2 * A * (x - xc) / (w * w) * np.exp(-((x - xc) ** 2 + (y - yc) ** 2) / (w * w))
+                   for A, xc, yc, w in bumps) + 0 * x
+
+    def by(x, y):
+        return sum(-2 * A * (y - yc) / (w * w) * np.exp(-((x - xc) ** 2 + (y - yc) ** 2) / (w * w))
+                   for A, xc, yc, w in bumps) + 0 * y
+    return b, bx, by
+
+
+@dataclass
+class Problem2DInputs:
+    Nx: int
+    Ny: int
+    levels: int
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    g: float
+    gq: List[np.ndarray]          # per level [2,4,Ny_l*Nx_l]
+    bc_kind: List[np.ndarray]     # per level int32 [2*Ny_l + 2*Nx_l]
+    bc_state: np.ndarray          # [4,3]
+    U0_start: np.ndarray          # [3, n_s]
+    start_level: int = -1
+    b_fns: tuple = field(repr=False, default=None)
+    meta: dict = field(default_factory=dict)
+
+    def dims(self, l=0):
+        return self.Nx >> l, self.Ny >> l
+
+    def centres(self, l=0):
+        nx, ny = self.dims(l)
+        xc = self.x0 + (np.arange(nx) + 0.5) * (self.x1 - self.x0) / nx
+        yc = self.y0 + (np.arange(ny) + 0.5) * (self.y1 - self.y0) / ny
+        return np.meshgrid(xc, yc)  # [ny, nx] arrays
+
+    def gq_all(self):
+        return np.ascontiguousarray(np.concatenate([a.reshape(-1) for a in self.gq]))
+
+    def bc_kind_all(self):
+        return np.ascontiguousarray(np.concatenate([a.reshape(-1) for a in self.bc_kind]).astype(np.int32))
+
+
+def sample_geometry_2d(x0, x1, y0, y1, nx, ny, b_fns):
+    _, bx, by = b_fns
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+    xc = x0 + (np.arange(nx) + 0.5) * dx
+    yc = y0 + (np.arange(ny) + 0.5) * dy
+    ox, oy = dx / (2.0 * math.sqrt(3.0)), dy / (2.0 * math.sqrt(3.0))
+    out = np.empty((2, 4, ny * nx))
+    for b in range(2):
+        for gm in range(2):
+            X, Y = np.meshgrid(xc + (2 * gm - 1) * ox, yc + (2 * b - 1) * oy)
+            out[0, 2 * b + gm] = bx(X, Y).reshape(-1)
+            out[1, 2 * b + gm] = by(X, Y).reshape(-1)
+    return out
+
+
+def _kinds(spec, coords):
+    """spec: an int kind, or a callable coordinate -> kind."""
+    if callable(spec):
+        return np.array([spec(c) for c in coords], dtype=np.int32)
+    return np.full(len(coords), int(spec), dtype=np.int32)
+
+
+def make_problem_2d(Nx, Ny, levels, x0, x1, y0, y1, g, b_fns, sides, bc_state, U0_fn, start_level=-1, meta=None):
+    """sides = (left, right, bottom, top) kind specs; U0_fn(x, y) -> (h, hu, hv)
+    arrays evaluated at the start level's cell centres."""
+    if Nx % (1 << (levels - 1)) or Ny % (1 << (levels - 1)):
+        raise ValueError("grid sizes must be divisible by 2^(levels-1)")
+    gq, kinds = [], []
+    for l in range(levels):
+        nx, ny = Nx >> l, Ny >> l
+        gq.append(sample_geometry_2d(x0, x1, y0, y1, nx, ny, b_fns))
+        xc = x0 + (np.arange(nx) + 0.5) * (x1 - x0) / nx
+        yc = y0 + (np.arange(ny) + 0.5) * (y1 - y0) / ny
+        kinds.append(np.concatenate([_kinds(sides[0], yc), _kinds(sides[1], yc), _kinds(sides[2], xc),
+                                     _kinds(sides[3], xc)]))
+    sl = levels - 1 if start_level < 0 else start_level
+    nx, ny = Nx >> sl, Ny >> sl
+    X, Y = np.meshgrid(x0 + (np.arange(nx) + 0.5) * (x1 - x0) / nx, y0 + (np.arange(ny) + 0.5) * (y1 - y0) / ny)
+    h, hu, hv = U0_fn(X, Y)
+    U0 = np.stack([np.broadcast_to(h, X.shape).reshape(-1), np.broadcast_to(hu, X.shape).reshape(-1),
+                   np.broadcast_to(hv, X.shape).reshape(-1)]).astype(np.float64)
+    return Problem2DInputs(Nx, Ny, levels, x0, x1, y0, y1, g, gq, kinds, np.asarray(bc_state, dtype=np.float64),
+                           np.ascontiguousarray(U0), sl, b_fns, meta or {})
+
+
+def paper_parabolic_bump(Nx=16, Ny=8, levels=2):
+    """Section 5.2.1: Eq. 29 on [-4, 4] x [0, 4]; discharge hu = 1 at x = -4,
+    depth h = 1 at x = 4, reflective side walls; guess h = 1, hu = 1, hv = 0
+    (Eq. 30) on the start level; g = 9.812."""
+    st = np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0, 0, 0], [0, 0, 0]])
+    return make_problem_2d(Nx, Ny, levels, -4.0, 4.0, 0.0, 4.0, G_PAPER, bottom2d_eq29(),
+                           (BC2_DISCHARGE, BC2_DEPTH, BC2_REFLECT, BC2_REFLECT), st,
+                           lambda X, Y: (1.0, 1.0, 0.0), meta={"case": "eq29"})
+
+
+def wedge(Nx, Ny, levels, theta_deg=8.95, x1=5.0, y1=2.0, x_wall=1.0, speed=8.57, start_level=-1, meta=None):
+    """Hydraulic jump over a wedge in the rotated frame of Section 5.2.2:
+    inflow (h, u, v) = (1, speed cos(-theta), speed sin(-theta)) on the left
+    and top, extrapolated outflow on the right, bottom outflow for
+    x < x_wall / cos(theta) and reflective beyond; flat bottom; guess = the
+    inflow state (Eq. 31); g = 9.812."""
+    th = math.radians(theta_deg)
+    u, v = speed * math.cos(-th), speed * math.sin(-th)
+    xw = x_wall / math.cos(th)
+    st = np.array([[1.0, u, v], [1.0, u, v], [1.0, u, v], [1.0, u, v]])
+    bottom = lambda x: BC2_OUTFLOW if x < xw else BC2_REFLECT
+    return make_problem_2d(Nx, Ny, levels, 0.0, x1, 0.0, y1, G_PAPER, bottom2d_flat(),
+                           (BC2_INFLOW, BC2_OUTFLOW, bottom, BC2_INFLOW), st, lambda X, Y: (1.0, u, v),
+                           start_level=start_level,
+                           meta=dict(meta or {}, theta_deg=theta_deg, x_wall=xw, case="wedge"))
+
+
+def wedge_channel(k, Nx=512, Ny=256, levels=7):
+    """Seeded wedge channel: 512 x 256 cells on [0, 40] x [0, 30], deflection
+    theta ~ U[8, 15] degrees, inflow depth 1 and speed 8.57 (Froude 2.74), wall
+    from x = 8/cos(theta); seed 3000 + k."""
+    rng = np.random.default_rng(3000 + k)
+    th = float(rng.uniform(8.0, 15.0))
+    return wedge(Nx, Ny, levels, theta_deg=th, x1=40.0, y1=30.0, x_wall=8.0, meta={"seed": 3000 + k})
+
+
+@dataclass
+class Params2D:
+    alpha: float = 3.0
+    tau: float = 0.6
+    omega: float = 0.1
+    tol: float = 1e-11
+    nu1: List[int] = field(default_factory=lambda: [20])
+    nu2: List[int] = field(default_factory=lambda: [20])
+    nu3: int = 3
+    levels: int = 2
+    n_max: int = 2000
+    st: int = ST_J9
+    eps: float = 1e-6
+    nest_start: int = -1

@@ -1,0 +1,385 @@
+"""Pins of the 2D CPU oracle (Section 4) against facts fixed by the paper and
+by mathematics: exact steady states, symmetries of the equations, brute-force
+differentiation, dense linear algebra and convergence to an exact solution.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+from paper_2505_10857_gb300 import inputs as I
+
+G = 9.81
+
+
+def _problem(Nx, Ny, b_fns, sides, state, U0, x1=3.0, y1=2.0, levels=1):
+    return I.make_problem_2d(Nx, Ny, levels, 0.0, x1, 0.0, y1, G, b_fns, sides, state, U0)
+
+
+def _random_state(rng, Nx, Ny):
+    X, Y = np.meshgrid(np.linspace(0, 1, Nx), np.linspace(0, 1, Ny))
+    h = 1.5 + 0.2 * np.sin(2 * np.pi * X + 1.0) * np.cos(np.pi * Y) + 0.02 * rng.standard_normal(X.shape)
+    hu = 2.0 + 0.3 * np.cos(2 * np.pi * Y + X) + 0.05 * rng.standard_normal(X.shape)
+    hv = 0.4 * np.sin(np.pi * X) + 0.05 * rng.standard_normal(X.shape)
+    return np.stack([h.ravel(), hu.ravel(), hv.ravel()])
+
+
+BUMPS = I.bottom2d_gaussians([(0.1, 1.2, 0.8, 0.6), (-0.05, 2.0, 1.5, 0.4)])
+MIXED_SIDES = (I.BC2_INFLOW, I.BC2_OUTFLOW, lambda x: I.BC2_OUTFLOW if x < 1.5 else I.BC2_REFLECT, I.BC2_DEPTH)
+MIXED_STATE = np.array([[1.6, 2.2, 0.3], [0, 0, 0], [0, 0, 0], [1.4, 0.0, 0.0]])
+
+
+# ---------------------------------------------------------------- exact states
+
+def test_llf_consistency_and_mirror(orc):
+    for d in (0, 1):
+        U = np.array([1.3, 0.7, -0.4])
+        F = orc.llf2d(d, U, U, G)
+        h, u, v = U[0], U[1] / U[0], U[2] / U[0]
+        ref = [U[1], U[1] * u + 0.5 * G * h * h, U[1] * v] if d == 0 else [U[2], U[2] * u, U[2] * v + 0.5 * G * h * h]
+        assert np.allclose(F, ref, rtol=1e-15)
+    UL, UR = np.array([1.2, 0.9, 0.3]), np.array([1.5, 0.4, -0.2])
+    F = orc.llf2d(0, UL, UR, G)
+    Fm = orc.llf2d(0, UR * [1, -1, 1], UL * [1, -1, 1], G)  # x -> -x
+    assert np.allclose(Fm, F * [-1, 1, -1], rtol=1e-14)
+
+
+@pytest.mark.parametrize("sides", [(I.BC2_INFLOW, I.BC2_OUTFLOW, I.BC2_OUTFLOW, I.BC2_INFLOW),
+                                   (I.BC2_DISCHARGE, I.BC2_DEPTH, I.BC2_INFLOW, I.BC2_OUTFLOW)])
+def test_uniform_state_zero_residual(orc, sides):
+    s = np.array([1.3, 2.0, 0.5])
+    p = _problem(10, 8, I.bottom2d_flat(), sides, np.tile(s, (4, 1)), lambda X, Y: tuple(s))
+    R, _ = orc.residual2d(orc.problem_levels2d(p)[0], p.U0_start)
+    assert np.abs(R).max() <= 1e-13 * 0.5 * G * 1.3 ** 2
+
+
+def test_uniform_flow_along_walls(orc):
+    # reflective walls top and bottom, flow along x: the mirror ghosts equal the state
+    s = (1.1, 1.7, 0.0)
+    p = _problem(10, 6, I.bottom2d_flat(), (I.BC2_INFLOW, I.BC2_OUTFLOW, I.BC2_REFLECT, I.BC2_REFLECT),
+                 np.tile(s, (4, 1)), lambda X, Y: s)
+    R, _ = orc.residual2d(orc.problem_levels2d(p)[0], p.U0_start)
+    assert np.abs(R).max() <= 1e-13
+
+
+def test_lake_at_rest_linear_bottom(orc):
+    # h + b constant, u = v = 0, b linear in x and y: characteristic WENO3 and
+    # the transverse quadratic are exact on linear data, LLF is consistent and
+    # the Gauss quadratures are exact, so interior R = 0 to rounding.
+    b = I.bottom2d_linear(0.1, 0.03, -0.02)
+    p = _problem(12, 10, b, (I.BC2_REFLECT,) * 4, np.zeros((4, 3)), lambda X, Y: (2.0 - b[0](X, Y), 0.0, 0.0))
+    R, _ = orc.residual2d(orc.problem_levels2d(p)[0], p.U0_start)
+    R = R.reshape(3, 10, 12)
+    assert np.abs(R[:, 2:-2, 2:-2]).max() <= 1e-12
+    assert abs(0.03 * G * 2.0) > 0.1  # the source is exercised
+
+
+# ---------------------------------------------------------------- symmetries of the equations
+
+def test_transpose_symmetry(orc):
+    """Swapping x <-> y (and hu <-> hv, b_x <-> b_y, left <-> bottom, right <->
+    top) maps the residual onto itself with components 2 and 3 swapped."""
+    rng = np.random.default_rng(1)
+    Nx, Ny = 8, 6
+    b = I.bottom2d_gaussians([(0.1, 1.0, 0.9, 0.5)])
+    bt = I.bottom2d_gaussians([(0.1, 0.9, 1.0, 0.5)])
+    st = np.array([[1.5, 2.0, 0.2], [0, 0, 0], [1.2, 0.1, 1.0], [1.4, 0, 0]])
+    stT = np.array([[1.2, 1.0, 0.1], [1.4, 0, 0], [1.5, 0.2, 2.0], [0, 0, 0]])
+    p = I.make_problem_2d(Nx, Ny, 1, 0, 2.0, 0, 1.5, G, b, (I.BC2_INFLOW, I.BC2_OUTFLOW, I.BC2_INFLOW, I.BC2_DEPTH),
+                          st, lambda X, Y: (1.0, 0.0, 0.0))
+    pT = I.make_problem_2d(Ny, Nx, 1, 0, 1.5, 0, 2.0, G, bt, (I.BC2_INFLOW, I.BC2_DEPTH, I.BC2_INFLOW, I.BC2_OUTFLOW),
+                           stT, lambda X, Y: (1.0, 0.0, 0.0))
+    U = _random_state(rng, Nx, Ny)
+    UT = np.stack([U[m].reshape(Ny, Nx).T.ravel() for m in (0, 2, 1)])
+    R, _ = orc.residual2d(orc.problem_levels2d(p)[0], U)
+    RT, _ = orc.residual2d(orc.problem_levels2d(pT)[0], UT)
+    back = np.stack([RT[m].reshape(Nx, Ny).T.ravel() for m in (0, 2, 1)])
+    # corner ghosts apply the x rule before the y rule (a reading), which does
+    # not commute with the transposition: compare every cell but the 2x2
+    # blocks at the corners
+    keep = _off_corners(Nx, Ny)
+    assert np.allclose(back[:, keep], R[:, keep], rtol=1e-12, atol=1e-12 * np.abs(R).max())
+    assert np.array_equal(back[:, keep] == 0, R[:, keep] == 0)
+
+
+def _off_corners(Nx, Ny):
+    m = np.ones((Ny, Nx), dtype=bool)
+    for a in (0, 1, Ny - 2, Ny - 1):
+        for b in (0, 1, Nx - 2, Nx - 1):
+            if (a < 2 or a >= Ny - 2) and (b < 2 or b >= Nx - 2):
+                m[a, b] = False
+    return m.ravel()
+
+
+def test_mirror_symmetry(orc):
+    """x -> -x: reverse the cells, negate hu and b_x, swap left and right."""
+    rng = np.random.default_rng(2)
+    Nx, Ny = 9, 6
+    b = I.bottom2d_gaussians([(0.1, 1.1, 0.7, 0.5)])
+    bm = I.bottom2d_gaussians([(0.1, 3.0 - 1.1, 0.7, 0.5)])
+    st = np.array([[1.5, 2.0, 0.2], [1.3, 0, 0], [1.2, 0.3, 1.0], [0, 0, 0]])
+    stm = np.array([[1.3, 0, 0], [1.5, -2.0, 0.2], [1.2, -0.3, 1.0], [0, 0, 0]])
+    p = I.make_problem_2d(Nx, Ny, 1, 0, 3.0, 0, 2.0, G, b, (I.BC2_INFLOW, I.BC2_DEPTH, I.BC2_INFLOW, I.BC2_REFLECT),
+                          st, lambda X, Y: (1.0, 0, 0))
+    pm = I.make_problem_2d(Nx, Ny, 1, 0, 3.0, 0, 2.0, G, bm, (I.BC2_DEPTH, I.BC2_INFLOW, I.BC2_INFLOW, I.BC2_REFLECT),
+                           stm, lambda X, Y: (1.0, 0, 0))
+    U = _random_state(rng, Nx, Ny)
+    Um = np.stack([s * U[m].reshape(Ny, Nx)[:, ::-1].ravel() for m, s in ((0, 1), (1, -1), (2, 1))])
+    R, _ = orc.residual2d(orc.problem_levels2d(p)[0], U)
+    Rm, _ = orc.residual2d(orc.problem_levels2d(pm)[0], Um)
+    back = np.stack([s * Rm[m].reshape(Ny, Nx)[:, ::-1].ravel() for m, s in ((0, 1), (1, -1), (2, 1))])
+    assert np.allclose(back, R, rtol=1e-12, atol=1e-12 * np.abs(R).max())  # x rules commute with the mirror
+
+
+# ---------------------------------------------------------------- Jacobian
+
+def test_jacobian_equals_global_bruteforce_fd(orc):
+    rng = np.random.default_rng(3)
+    Nx, Ny = 7, 6
+    p = _problem(Nx, Ny, BUMPS, MIXED_SIDES, MIXED_STATE, lambda X, Y: (1.0, 0, 0))
+    pr = orc.problem_levels2d(p)[0]
+    U = _random_state(rng, Nx, Ny)
+    eps = 1e-6
+    J, R, _ = orc.jacobian2d(pr, U, eps, 0.0, orc.ST_J21)
+    off = orc.stencil2d(orc.ST_J21)
+    R0, _ = orc.residual2d(pr, U)
+    assert np.array_equal(R, R0)
+    n = Nx * Ny
+    for cp in range(n):
+        for m in range(3):
+            Up = U.copy()
+            Up[m, cp] += eps
+            col = (orc.residual2d(pr, Up)[0] - R0) / eps
+            pi, pj = cp % Nx, cp // Nx
+            for c in range(n):
+                i, j = c % Nx, c // Nx
+                d = (pi - i, pj - j)
+                if d in off:
+                    k = off.index(d)
+                    for l in range(3):
+                        assert J[k, l * 3 + m, c] == col[l, c]
+                else:
+                    assert np.all(col[:, c] == 0.0), (d, c)
+
+
+def test_j9_is_j21_restricted_to_the_cross(orc):
+    rng = np.random.default_rng(4)
+    p = _problem(6, 5, BUMPS, MIXED_SIDES, MIXED_STATE, lambda X, Y: (1.0, 0, 0))
+    pr = orc.problem_levels2d(p)[0]
+    U = _random_state(rng, 6, 5)
+    J21, R21, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, orc.ST_J21)
+    J9, R9, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, orc.ST_J9)
+    o21, o9 = orc.stencil2d(orc.ST_J21), orc.stencil2d(orc.ST_J9)
+    assert len(o21) == 21 and len(o9) == 9 and set(o9) <= set(o21)
+    for k, d in enumerate(o9):
+        assert np.array_equal(J9[k], J21[o21.index(d)])
+    assert np.array_equal(R9, R21)
+
+
+# ---------------------------------------------------------------- multigrid
+
+def _dense(J, Nx, Ny, st, orc):
+    off = orc.stencil2d(st)
+    n = Nx * Ny
+    A = np.zeros((3 * n, 3 * n))
+    for c in range(n):
+        i, j = c % Nx, c // Nx
+        for k, (dx, dy) in enumerate(off):
+            p, q = i + dx, j + dy
+            if 0 <= p < Nx and 0 <= q < Ny:
+                A[3 * c:3 * c + 3, 3 * (q * Nx + p):3 * (q * Nx + p) + 3] = J[k, :, c].reshape(3, 3)
+    return A
+
+
+def _P(Nx, Ny):
+    n, nc = Nx * Ny, (Nx // 2) * (Ny // 2)
+    P = np.zeros((3 * n, 3 * nc))
+    for c in range(n):
+        cc = (c // Nx // 2) * (Nx // 2) + (c % Nx) // 2
+        for m in range(3):
+            P[3 * c + m, 3 * cc + m] = 1.0
+    return P
+
+
+def _vec(U):
+    return np.stack(list(U), 1).reshape(-1)
+
+
+def _random_op(orc, st, Nx, Ny, rng, dominant=True):
+    off = orc.stencil2d(st)
+    J = rng.standard_normal((len(off), 9, Nx * Ny))
+    for k, (dx, dy) in enumerate(off):
+        for c in range(Nx * Ny):
+            i, j = c % Nx, c // Nx
+            if not (0 <= i + dx < Nx and 0 <= j + dy < Ny):
+                J[k, :, c] = 0.0
+    if dominant:
+        kc = off.index((0, 0))
+        for l in range(3):
+            J[kc, l * 4] += 5.0 * len(off)
+    return J
+
+
+@pytest.mark.parametrize("st", [0, 1, 2, 3])
+def test_coarse_operator_is_galerkin(orc, st):
+    rng = np.random.default_rng(10 + st)
+    Nx, Ny = 8, 6
+    J = _random_op(orc, st, Nx, Ny, rng)
+    Jc = orc.coarse_operator2d(J, Nx, Ny, st)
+    P = _P(Nx, Ny)
+    Ac = _dense(Jc, Nx // 2, Ny // 2, orc.coarse_stencil(st), orc)
+    assert np.allclose(Ac, P.T @ _dense(J, Nx, Ny, st, orc) @ P, rtol=1e-14, atol=1e-12)
+
+
+@pytest.mark.parametrize("st", [0, 1, 2, 3])
+def test_restriction_prolongation_and_colours(orc, st):
+    rng = np.random.default_rng(20 + st)
+    Nx, Ny = 8, 6
+    J = _random_op(orc, st, Nx, Ny, rng)
+    R = rng.standard_normal((3, Nx * Ny))
+    dU = rng.standard_normal((3, Nx * Ny))
+    P = _P(Nx, Ny)
+    Rc = orc.restrict2d(J, R, dU, Nx, Ny, st)
+    assert np.allclose(_vec(Rc), P.T @ (_vec(R) + _dense(J, Nx, Ny, st, orc) @ _vec(dU)), rtol=1e-13, atol=1e-12)
+    dUc = rng.standard_normal((3, (Nx // 2) * (Ny // 2)))
+    assert np.allclose(_vec(orc.prolong2d(dU, dUc, Nx, Ny)), _vec(dU) + P @ _vec(dUc), rtol=1e-15)
+    # no two cells of one colour are coupled by the stencil
+    for (dx, dy) in orc.stencil2d(st):
+        if (dx, dy) == (0, 0):
+            continue
+        for j in range(6):
+            for i in range(6):
+                assert orc.lib().or_colour_of(st, i, j) != orc.lib().or_colour_of(st, i + dx + 6, j + dy + 6)
+
+
+def test_sor_direct_and_two_level_cycle(orc):
+    rng = np.random.default_rng(30)
+    Nx, Ny = 8, 4
+    for st in (0, 2):
+        J = _random_op(orc, st, Nx, Ny, rng)
+        R = rng.standard_normal((3, Nx * Ny))
+        A = _dense(J, Nx, Ny, st, orc)
+        x = orc.direct_solve2d(J, R, Nx, Ny, st)
+        assert np.abs(A @ _vec(x) + _vec(R)).max() < 1e-11
+        D = orc.block_inverse2d(J, st)
+        dU = np.zeros_like(R)
+        for _ in range(40):
+            dU = orc.sor_step2d(J, D, R, dU, Nx, Ny, st, 1.0)
+        assert np.abs(dU - x).max() < 1e-10
+        # two levels, no smoothing: exactly the coarse correction
+        P = _P(Nx, Ny)
+        got = orc.vcycle2d(J, R, np.zeros_like(R), Nx, Ny, st, 2, 1.0, 0, 0)
+        ref = P @ np.linalg.solve(P.T @ A @ P, -(P.T @ _vec(R)))
+        assert np.allclose(_vec(got), ref, rtol=1e-11, atol=1e-12)
+
+
+def test_interp2d_conservative_and_exact_for_quadratics(orc):
+    Ncx, Ncy = 6, 5
+    p = I.make_problem_2d(2 * Ncx, 2 * Ncy, 2, 0.0, 1.2, 0.0, 1.0, G, I.bottom2d_flat(), (I.BC2_OUTFLOW,) * 4,
+                          np.zeros((4, 3)), lambda X, Y: (1.0, 0, 0))
+    pc = orc.problem_levels2d(p)[1]
+    # cell averages of q(x, y) = 1 + x + 2y + 3x^2 - xy + 2y^2 by exact integration
+    Fx = lambda a, b: (b - a, (b * b - a * a) / 2, (b ** 3 - a ** 3) / 3)
+
+    def avg(nx, ny):
+        xs, ys = np.linspace(0, 1.2, nx + 1), np.linspace(0, 1.0, ny + 1)
+        out = np.zeros((ny, nx))
+        for j in range(ny):
+            for i in range(nx):
+                X0, X1, X2 = Fx(xs[i], xs[i + 1])
+                Y0, Y1, Y2 = Fx(ys[j], ys[j + 1])
+                out[j, i] = (X0 * Y0 + X1 * Y0 + 2 * X0 * Y1 + 3 * X2 * Y0 - X1 * Y1 + 2 * X0 * Y2) / (X0 * Y0)
+        return out.ravel()
+    Uc = np.stack([avg(Ncx, Ncy), 2 * avg(Ncx, Ncy), -avg(Ncx, Ncy)])
+    Uf = orc.interp2d(pc, Uc)
+    f4 = Uf.reshape(3, 2 * Ncy, 2 * Ncx)
+    parent = 0.25 * (f4[:, 0::2, 0::2] + f4[:, 0::2, 1::2] + f4[:, 1::2, 0::2] + f4[:, 1::2, 1::2])
+    assert np.allclose(parent.reshape(3, -1), Uc, rtol=1e-14, atol=1e-14)
+    ex = avg(2 * Ncx, 2 * Ncy).reshape(2 * Ncy, 2 * Ncx)
+    assert np.allclose(f4[0, 2:-2, 2:-2], ex[2:-2, 2:-2], rtol=1e-13)
+    assert np.allclose(f4[2, 2:-2, 2:-2], -ex[2:-2, 2:-2], rtol=1e-13)
+
+
+# ---------------------------------------------------------------- accuracy
+
+def _sparse(J, Nx, Ny, st, orc):
+    off = orc.stencil2d(st)
+    rows, cols, vals = [], [], []
+    for k, (dx, dy) in enumerate(off):
+        for c in range(Nx * Ny):
+            i, j = c % Nx, c // Nx
+            p, q = i + dx, j + dy
+            if 0 <= p < Nx and 0 <= q < Ny:
+                for l in range(3):
+                    for m in range(3):
+                        rows.append(3 * c + l)
+                        cols.append(3 * (q * Nx + p) + m)
+                        vals.append(J[k, l * 3 + m, c])
+    n = 3 * Nx * Ny
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n)).tocsc()
+
+
+@pytest.mark.slow
+def test_channel_flow_converges_to_the_1d_exact_solution(orc):
+    """The 2D scheme on a narrow channel with reflective side walls over the
+    bottom of Eq. 26 has y-invariant discrete steady states that converge to
+    the exact solution of Eq. 27 at third order as dx -> 0 (the discrete
+    steady state is found with Newton steps and exact sparse solves)."""
+    g = I.G_PAPER
+    b1, bx1 = I.bottom_eq26()
+    b_fns = (lambda x, y: b1(x) + 0 * y, lambda x, y: bx1(x) + 0 * y, lambda x, y: 0 * x + 0 * y)
+
+    def u_exact(x):
+        out = np.empty_like(x)
+        for i, xx in enumerate(x):
+            r = np.roots([1.0, 0.0, 2 * g * b1(xx) - 2 * g - 1.0, 2 * g])
+            r = r[np.abs(r.imag) < 1e-10].real
+            out[i] = r[np.argmin(np.abs(r - 1.0))]
+        return out
+    errs, U, ny = [], None, 2
+    for nx in (64, 128, 256):
+        st = np.array([[1.0, 1.0, 0.0], [1.0, 1.0, 0.0], [0, 0, 0], [0, 0, 0]])
+        p = I.make_problem_2d(nx, ny, 1, -10, 10, 0, 20.0 / nx * ny, g, b_fns,
+                              (I.BC2_INFLOW, I.BC2_INFLOW, I.BC2_REFLECT, I.BC2_REFLECT), st,
+                              lambda X, Y: (1.0 - b1(X), 1.0, 0.0))
+        pr = orc.problem_levels2d(p)[0]
+        if U is None:
+            U = p.U0_start.copy()
+        else:
+            Uc = orc.interp2d(orc.problem_levels2d(I.make_problem_2d(
+                nx // 2, ny // 2, 1, -10, 10, 0, 20.0 / nx * ny, g, b_fns,
+                (I.BC2_INFLOW, I.BC2_INFLOW, I.BC2_REFLECT, I.BC2_REFLECT), st, lambda X, Y: (1.0, 1.0, 0.0)))[0],
+                U.reshape(3, ny, nx // 2)[:, ::2, :].reshape(3, -1))
+            U = Uc
+        for _ in range(80):
+            J, R, res = orc.jacobian2d(pr, U, 1e-7, 3.0, orc.ST_J21)
+            if res < 1e-12:
+                break
+            x = spl.spsolve(_sparse(J, nx, ny, orc.ST_J21, orc), -_vec(R))
+            U = U + 0.6 * np.stack([x[0::3], x[1::3], x[2::3]])
+        assert res < 1e-12
+        dx = 20.0 / nx
+        xc = -10 + (np.arange(nx) + 0.5) * dx
+        t, w = np.polynomial.legendre.leggauss(8)
+        he = sum(0.5 * wi * (1.0 / u_exact(xc + 0.5 * dx * ti)) for ti, wi in zip(t, w))
+        errs.append(np.abs(U[0].reshape(ny, nx) - he[None]).mean())
+        assert np.abs(U[2]).max() < 1e-12  # stays y-invariant
+    assert math.log2(errs[0] / errs[1]) > 1.5 and math.log2(errs[1] / errs[2]) > 2.5, errs
+
+
+@pytest.mark.slow
+def test_j9_and_j21_reach_the_same_steady_state(orc):
+    """NMGM-9 and NMGM-21 solve the same R = 0 (Section 5.2.1): same fixed
+    point, nearly the same Newton counts."""
+    p = I.paper_parabolic_bump(16, 8, 2)
+    out = {}
+    for st in (I.ST_J9, I.ST_J21):
+        prm = I.Params2D(levels=2, nu1=[15], nu2=[15], tol=1e-11, n_max=400, st=st)
+        U, info = orc.solve_problem2d(p, prm)
+        out[st] = (U, info)
+    (U9, i9), (U21, i21) = out[I.ST_J9], out[I.ST_J21]
+    assert i9["res"][0] < 1e-11 and i21["res"][0] < 1e-11
+    assert np.abs(U9 - U21).max() <= 1e-9 * np.abs(U9).max()
+    assert abs(i9["iters"][0] - i21["iters"][0]) <= max(3, 0.2 * i21["iters"][0])
