@@ -68,9 +68,21 @@ typedef struct {
   double q;  /* discharge (DISCHARGE, STATE) */
 } nswe_bc1d;
 
+/* Two-dimensional boundary kinds (Section 5.2), one per boundary cell. The
+ * library fills two ghost layers: REFLECT mirrors the interior with the
+ * normal momentum negated (slip wall), INFLOW takes the given (h, hu, hv),
+ * OUTFLOW copies the edge cell, DISCHARGE takes the given momenta and the
+ * edge depth, DEPTH the given depth and the edge momenta. Corner ghosts apply
+ * the x rule, then the y rule. */
+#define NSWE_BC2_REFLECT 5
+#define NSWE_BC2_INFLOW 6
+#define NSWE_BC2_OUTFLOW 7
+#define NSWE_BC2_DISCHARGE 8
+#define NSWE_BC2_DEPTH 9
+
 #define NSWE_MAX_LEVELS 16
-#define NSWE_JAC_SIMPLIFIED 3 /* J3: block tridiagonal (Section 3.3) */
-#define NSWE_JAC_FULL 5       /* J5: block pentadiagonal             */
+#define NSWE_JAC_SIMPLIFIED 3 /* 1D J3: block tridiagonal (Section 3.3); 2D J9 */
+#define NSWE_JAC_FULL 5       /* 1D J5: block pentadiagonal; 2D J21          */
 
 /* Solver parameters (Section 5). nswe_params_default fills the paper's 1D
  * values: alpha 3, tau 0.6, omega 1, nu1 = nu2 = nu3 = 2, tol 1e-11. */
@@ -143,8 +155,29 @@ nswe_status nswe_prob_set_geometry_1d(nswe_ctx ctx, nswe_prob prob,
                                       const double *gauss_geom,
                                       const nswe_bc1d *left,
                                       const nswe_bc1d *right);
+/* Two-dimensional problem (Eq. 1-2, Section 4) on [x0,x1] x [y0,y1] with
+ * Nx x Ny cells and `levels` nested/multigrid levels (Nx, Ny divisible by
+ * 2^(levels-1); every level at least 4 x 4 cells; coarsest level at most 512
+ * cells for the dense direct solve). Cell (i, j) has index c = j*Nx + i; a 2D
+ * state is three planes h, hu, hv of Nx*Ny doubles. HOST arrays, copied:
+ *   gauss_geom   for l = 0..levels-1 in turn, [2][4][Ny_l*Nx_l]: db/dx and
+ *                db/dy at the Gauss points (x_i -+ dx/(2 sqrt 3), y_j -+
+ *                dy/(2 sqrt 3)), point q = 2*beta + gamma (beta: y, gamma: x);
+ *   bc_kind      for l = 0..levels-1 in turn, [Ny_l left | Ny_l right |
+ *                Nx_l bottom | Nx_l top] NSWE_BC2_* kinds;
+ *   bc_state     [4][3] (h, hu, hv) data of the left, right, bottom, top sides.
+ * 2D block operators use 3x3 blocks: J[(k*9 + l*3 + m)*n + c] =
+ * (dR_c/dU_{c + off(k)})_{lm}, with the offset lists (dx, dy) sorted by dy then
+ * dx: J9 (the cross of Eq. 21) (0,-2) (0,-1) (-2,0) (-1,0) (0,0) (1,0) (2,0)
+ * (0,1) (0,2); J21 (the 21-cell stencil of Section 4.1): |dx| <= 2, |dy| <= 1
+ * or |dx| <= 1, |dy| <= 2. */
+nswe_status nswe_prob_create_2d(nswe_ctx ctx, nswe_prob *out, int Nx, int Ny,
+                                int levels, double x0, double x1, double y0,
+                                double y1, double g, const double *gauss_geom,
+                                const int *bc_kind, const double *bc_state);
 nswe_status nswe_prob_destroy(nswe_prob prob);
 int nswe_prob_cells(nswe_prob prob, int level);
+int nswe_prob_dim(nswe_prob prob);
 
 /* Residual R_j = F_{j+1/2} - F_{j-1/2} - S_j (Eq. 10; not divided by dx)
  * of state U on nested level `level`: WENO3 reconstruction (Eq. 7-8, with

@@ -22,12 +22,24 @@ struct nswe_ctx_s {
 
 struct nswe_prob_s {
   nswe_ctx ctx;
-  int N, levels;
+  int dim;               // 1 or 2
+  int N, levels;         // 1D: cells of the finest level
   double x0, x1, g;
   ProbDev host;          // device pointers, host copy
   ProbDev *dev;          // device copy
   double *arena;
   size_t geo_doubles;    // geometry region at the front of the arena
+  // 2D
+  int Nx, Ny;
+  ProbDev2 host2;
+  ProbDev2 *dev2;
+  double *dense;         // coarsest dense LU factors [N3][N3]
+  int *piv;              // [N3]
+  double *xbuf;          // [N3]
+  int *flag;             // device flag (zero pivot / non-positive depth)
+  double *res_dev;       // device scalar
+  double *res_host;      // pinned host scalar
+  int *flag_host;        // pinned host flag
 };
 
 namespace {
@@ -116,6 +128,154 @@ nswe_status upload_geometry(nswe_prob p, const double *sigma_face, const double 
   if (cudaMemcpyAsync(p->dev, &p->host, sizeof(ProbDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return NSWE_ECUDA;
   return NSWE_OK;
+}
+
+// ---------------------------------------------------------------- 2D host side
+
+int coarse_cells2(const nswe_prob_s *p) { return (p->Nx >> (p->levels - 1)) * (p->Ny >> (p->levels - 1)); }
+
+// Symmetric multicolour smoothing of 2D level l: one step = colours 0..C-1,
+// C-1..0, twice; consecutive visits of a colour run as one pass.
+cudaError_t smooth2(const Level2Dev &Lv, int st, int steps, double omega, cudaStream_t s) {
+  const int C = st_colours_host(st);
+  int prev = -1, reps = 0;
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < steps; ++t)
+    for (int pass = 0; pass < 4 * C; ++pass) {
+      const int q = pass % (2 * C), col = q < C ? q : 2 * C - 1 - q;
+      if (col == prev) {
+        ++reps;
+        continue;
+      }
+      if (prev >= 0 && (e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, prev, reps, s)))
+        return e;
+      prev = col;
+      reps = 1;
+    }
+  if (prev >= 0) e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, prev, reps, s);
+  return e;
+}
+
+// Multigrid hierarchy from level l0 (stencil st0) to the coarsest: the
+// level-l0 arrays are J, R, dU given by the caller.
+struct MG2 {
+  int l0, L;
+  int st[NSWE_MAX_LEVELS];
+  Level2Dev lv[NSWE_MAX_LEVELS];
+};
+
+MG2 mg2_bind(const nswe_prob_s *p, int l0, int st0, const double *J, const double *R, double *dU) {
+  MG2 m;
+  m.l0 = l0;
+  m.L = p->levels - 1;
+  for (int l = l0; l <= m.L; ++l) {
+    m.lv[l] = p->host2.lev[l];
+    m.st[l] = l == l0 ? st0 : st_coarse_host(m.st[l - 1]);
+  }
+  m.lv[l0].J = const_cast<double *>(J);
+  m.lv[l0].R = const_cast<double *>(R);
+  m.lv[l0].dU = dU;
+  return m;
+}
+
+cudaError_t mg2_setup(nswe_prob_s *p, const MG2 &m, cudaStream_t s) {
+  cudaError_t e;
+  for (int l = m.l0 + 1; l <= m.L; ++l)
+    if ((e = launch2_coarse_op(m.lv[l - 1].Nx, m.lv[l - 1].Ny, m.st[l - 1], m.lv[l - 1].J, m.lv[l].J, s))) return e;
+  for (int l = m.l0; l < m.L; ++l)
+    if ((e = launch2_dinv(m.lv[l].Nx * m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].Dinv, s))) return e;
+  return launch2_dense_factor(m.lv[m.L].Nx, m.lv[m.L].Ny, m.st[m.L], m.lv[m.L].J, p->dense, p->piv, p->flag, s);
+}
+
+cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2 &m, const nswe_params &prm, cudaStream_t s) {
+  cudaError_t e;
+  for (int l = m.l0; l < m.L; ++l) {
+    if ((e = smooth2(m.lv[l], m.st[l], prm.nu1, prm.omega, s))) return e;
+    if ((e = launch2_restrict(m.lv[l].Nx, m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].R, m.lv[l].dU, m.lv[l + 1].R,
+                              m.lv[l + 1].dU, s)))
+      return e;
+  }
+  const int nL = m.lv[m.L].Nx * m.lv[m.L].Ny;
+  if ((e = launch2_dense_solve(nL, p->dense, p->piv, m.lv[m.L].R, p->xbuf, m.lv[m.L].dU, s))) return e;
+  for (int l = m.L - 1; l >= m.l0; --l) {
+    if ((e = launch2_prolong(m.lv[l].Nx, m.lv[l].Ny, m.lv[l].dU, m.lv[l + 1].dU, s))) return e;
+    if ((e = smooth2(m.lv[l], m.st[l], prm.nu2, prm.omega, s))) return e;
+  }
+  return cudaSuccess;
+}
+
+// Algorithm 3 for one 2D problem, sequenced from the host (one synchronisation
+// per Newton step for the convergence test).
+nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm,
+                    nswe_info *info) {
+  cudaStream_t s = ctx->stream;
+  const int L = p->levels - 1;
+  const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
+  const int st0 = prm.jacobian == NSWE_JAC_FULL ? ST_J21 : ST_J9;
+  nswe_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  const int ns = p->host2.lev[s0].Nx * p->host2.lev[s0].Ny;
+  if (cudaMemcpyAsync(p->host2.lev[s0].U, U0, sizeof(double) * 3 * ns, cudaMemcpyDeviceToDevice, s)) return NSWE_ECUDA;
+  int fatal = 0;
+  for (int l = s0; l >= 0 && !fatal; --l) {
+    const Level2Dev &Lv = p->host2.lev[l];
+    const int n = Lv.Nx * Lv.Ny;
+    if (l < s0 && launch2_interp(p->dev2, l + 1, p->host2.lev[l + 1].Nx * p->host2.lev[l + 1].Ny,
+                                 p->host2.lev[l + 1].U, Lv.U, s))
+      return NSWE_ECUDA;
+    if (launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, s)) return NSWE_ECUDA;
+    int it = 0, st = NSWE_OK;
+    double res = 0.0;
+    while (true) {
+      if (launch2_jacobian(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, Lv.J, s)) return NSWE_ECUDA;
+      cudaMemsetAsync(p->flag, 0, sizeof(int), s);
+      MG2 m = mg2_bind(p, l, st0, Lv.J, Lv.R, Lv.dU);
+      if (l == L) {
+        if (launch2_dense_factor(Lv.Nx, Lv.Ny, st0, Lv.J, p->dense, p->piv, p->flag, s) ||
+            launch2_dense_solve(n, p->dense, p->piv, Lv.R, p->xbuf, Lv.dU, s))
+          return NSWE_ECUDA;
+      } else {
+        if (mg2_setup(p, m, s)) return NSWE_ECUDA;
+        cudaMemsetAsync(Lv.dU, 0, sizeof(double) * 3 * n, s);
+        for (int v = 0; v < prm.nu3; ++v) {
+          if (mg2_vcycle(p, m, prm, s)) return NSWE_ECUDA;
+          ++inf.vcycles;
+        }
+      }
+      if (launch2_update(n, Lv.U, Lv.dU, prm.tau, p->flag, s)) return NSWE_ECUDA;
+      if (launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, s)) return NSWE_ECUDA;
+      cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(p->flag_host, p->flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return NSWE_ECUDA;
+      res = *p->res_host;
+      ++it;
+      if (*p->flag_host) {
+        st = NSWE_ENEGDEPTH;  // non-positive depth or an exact zero pivot
+        break;
+      }
+      if (!(res == res) || std::isinf(res)) {
+        st = NSWE_ENAN;
+        break;
+      }
+      if (res < prm.tol) break;
+      if (it >= prm.n_max) {
+        st = NSWE_ENOTCONV;
+        break;
+      }
+    }
+    inf.iters[l] = it;
+    inf.res[l] = res;
+    inf.level_status[l] = st;
+    inf.total_iters += it;
+    if (st == NSWE_ENAN || st == NSWE_ENEGDEPTH) fatal = st;
+  }
+  if (!fatal) {
+    const int n0 = p->Nx * p->Ny;
+    if (cudaMemcpyAsync(U, p->host2.lev[0].U, sizeof(double) * 3 * n0, cudaMemcpyDeviceToDevice, s)) return NSWE_ECUDA;
+  }
+  inf.status = fatal ? fatal : inf.level_status[0];
+  if (info) *info = inf;
+  return (nswe_status)inf.status;
 }
 
 }  // namespace
@@ -209,6 +369,7 @@ nswe_status nswe_prob_create_1d(nswe_ctx ctx, nswe_prob *out, int N, int levels,
   nswe_prob p = new (std::nothrow) nswe_prob_s();
   if (!p) return NSWE_ENOMEM;
   p->ctx = ctx;
+  p->dim = 1;
   p->N = N;
   p->levels = levels;
   p->x0 = x0;
@@ -289,18 +450,141 @@ nswe_status nswe_prob_destroy(nswe_prob prob) {
   cudaStreamSynchronize(prob->ctx->stream);
   cudaFree(prob->arena);
   cudaFree(prob->dev);
+  cudaFree(prob->dev2);
+  cudaFree(prob->piv);
+  cudaFree(prob->flag);
+  cudaFree(prob->res_dev);
+  cudaFreeHost(prob->res_host);
+  cudaFreeHost(prob->flag_host);
   delete prob;
   return NSWE_OK;
 }
 
 int nswe_prob_cells(nswe_prob prob, int level) {
   if (!prob || level < 0 || level >= prob->levels) return -1;
+  if (prob->dim == 2) return (prob->Nx >> level) * (prob->Ny >> level);
   return prob->N >> level;
+}
+
+int nswe_prob_dim(nswe_prob prob) { return prob ? prob->dim : 0; }
+
+nswe_status nswe_prob_create_2d(nswe_ctx ctx, nswe_prob *out, int Nx, int Ny, int levels, double x0, double x1,
+                                double y0, double y1, double g, const double *gauss_geom, const int *bc_kind,
+                                const double *bc_state) {
+  if (!out) return NSWE_EINVAL;
+  *out = nullptr;
+  if (!ctx || !gauss_geom || !bc_kind || !bc_state) return NSWE_EINVAL;
+  if (levels < 1 || levels > NSWE_MAX_LEVELS || Nx < 4 || Ny < 4 || (long)Nx * Ny > (1L << 26)) return NSWE_EINVAL;
+  if (Nx % (1 << (levels - 1)) || Ny % (1 << (levels - 1))) return NSWE_EINVAL;
+  const int NLx = Nx >> (levels - 1), NLy = Ny >> (levels - 1);
+  if (NLx < 4 || NLy < 4 || NLx * NLy > 512) return NSWE_EINVAL;
+  if (!(x1 > x0) || !(y1 > y0) || !(g > 0.0) || !std::isfinite(x0) || !std::isfinite(x1) || !std::isfinite(y0) ||
+      !std::isfinite(y1) || !std::isfinite(g))
+    return NSWE_EINVAL;
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(bc_state[i])) return NSWE_EINVAL;
+  size_t nk = 0, ng = 0;
+  for (int l = 0; l < levels; ++l) {
+    nk += 2 * (size_t)((Nx >> l) + (Ny >> l));
+    ng += 8 * (size_t)(Nx >> l) * (Ny >> l);
+  }
+  for (size_t i = 0; i < nk; ++i)
+    if (bc_kind[i] < NSWE_BC2_REFLECT || bc_kind[i] > NSWE_BC2_DEPTH) return NSWE_EINVAL;
+  for (size_t i = 0; i < ng; ++i)
+    if (!std::isfinite(gauss_geom[i])) return NSWE_EINVAL;
+  DeviceGuard dg(ctx->device);
+  nswe_prob p = new (std::nothrow) nswe_prob_s();
+  if (!p) return NSWE_ENOMEM;
+  p->ctx = ctx;
+  p->dim = 2;
+  p->Nx = Nx;
+  p->Ny = Ny;
+  p->levels = levels;
+  p->x0 = x0;
+  p->x1 = x1;
+  p->g = g;
+  size_t doubles = 0;
+  for (int l = 0; l < levels; ++l) {
+    size_t n = (size_t)(Nx >> l) * (Ny >> l);
+    doubles += round_up(8 * n) + 3 * round_up(3 * n) + round_up(189 * n) + round_up(9 * n);
+  }
+  const size_t N3 = 3 * (size_t)NLx * NLy;
+  doubles += round_up(N3 * N3) + round_up(N3) + 2 * round_up(nk);
+  bool ok = cudaMalloc(&p->arena, sizeof(double) * doubles) == cudaSuccess &&
+            cudaMalloc(&p->dev2, sizeof(ProbDev2)) == cudaSuccess &&
+            cudaMalloc(&p->piv, sizeof(int) * (N3 + 64)) == cudaSuccess &&
+            cudaMalloc(&p->flag, sizeof(int) * 4) == cudaSuccess &&
+            cudaMalloc(&p->res_dev, sizeof(double) * 4) == cudaSuccess &&
+            cudaMallocHost(&p->res_host, sizeof(double) * 4) == cudaSuccess &&
+            cudaMallocHost(&p->flag_host, sizeof(int) * 4) == cudaSuccess;
+  if (!ok) {
+    cudaFree(p->arena);
+    cudaFree(p->dev2);
+    cudaFree(p->piv);
+    cudaFree(p->flag);
+    cudaFree(p->res_dev);
+    cudaFreeHost(p->res_host);
+    cudaFreeHost(p->flag_host);
+    delete p;
+    return NSWE_ENOMEM;
+  }
+  ProbDev2 &h = p->host2;
+  std::memset(&h, 0, sizeof(h));
+  h.levels = levels;
+  h.g = g;
+  for (int i = 0; i < 12; ++i) h.bcs[i] = bc_state[i];
+  double *a = p->arena;
+  std::vector<double> geo;
+  std::vector<int> kinds(bc_kind, bc_kind + nk);
+  size_t gsrc = 0, ksrc = 0;
+  int *kind_dev = reinterpret_cast<int *>(a);
+  a += 2 * round_up(nk);
+  for (int l = 0; l < levels; ++l) {
+    Level2Dev &Lv = h.lev[l];
+    Lv.Nx = Nx >> l;
+    Lv.Ny = Ny >> l;
+    Lv.dx = (x1 - x0) / Lv.Nx;
+    Lv.dy = (y1 - y0) / Lv.Ny;
+    const size_t n = (size_t)Lv.Nx * Lv.Ny;
+    Lv.gq = a;
+    if (cudaMemcpyAsync(a, gauss_geom + gsrc, sizeof(double) * 8 * n, cudaMemcpyHostToDevice, ctx->stream)) ok = false;
+    gsrc += 8 * n;
+    a += round_up(8 * n);
+    Lv.bck = kind_dev + ksrc;
+    ksrc += 2 * (size_t)(Lv.Nx + Lv.Ny);
+    Lv.U = a;
+    a += round_up(3 * n);
+    Lv.R = a;
+    a += round_up(3 * n);
+    Lv.dU = a;
+    a += round_up(3 * n);
+    Lv.J = a;
+    a += round_up(189 * n);
+    Lv.Dinv = a;
+    a += round_up(9 * n);
+  }
+  p->dense = a;
+  a += round_up(N3 * N3);
+  p->xbuf = a;
+  a += round_up(N3);
+  if (cudaMemcpyAsync(kind_dev, kinds.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, ctx->stream)) ok = false;
+  if (cudaMemcpyAsync(p->dev2, &p->host2, sizeof(ProbDev2), cudaMemcpyHostToDevice, ctx->stream)) ok = false;
+  if (!ok || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    nswe_prob_destroy(p);
+    return NSWE_ECUDA;
+  }
+  *out = p;
+  return NSWE_OK;
 }
 
 nswe_status nswe_residual(nswe_ctx ctx, nswe_prob prob, int level, const double *U, double *R, double *res_l1) {
   if (!ctx || !prob || prob->ctx != ctx || !U || !R || level < 0 || level >= prob->levels) return NSWE_EINVAL;
   DeviceGuard dg(ctx->device);
+  if (prob->dim == 2)
+    return launch2_residual(prob->dev2, level, nswe_prob_cells(prob, level), U, R, res_l1, ctx->partials,
+                            ctx->stream) == cudaSuccess
+               ? NSWE_OK
+               : NSWE_ECUDA;
   int N = prob->N >> level;
   return launch_residual(prob->dev, level, N, U, R, res_l1, ctx->partials, ctx->stream) == cudaSuccess
              ? NSWE_OK
@@ -312,6 +596,13 @@ static nswe_status jacobian_common(nswe_ctx ctx, nswe_prob prob, int level, int 
   if (!ctx || !prob || prob->ctx != ctx || !U || !R || !J || level < 0 || level >= prob->levels) return NSWE_EINVAL;
   if (!(eps > 0.0) || !std::isfinite(eps) || !(alpha >= 0.0) || !std::isfinite(alpha)) return NSWE_EINVAL;
   DeviceGuard dg(ctx->device);
+  if (prob->dim == 2) {
+    const int n = nswe_prob_cells(prob, level);
+    if (launch2_residual(prob->dev2, level, n, U, R, res, ctx->partials, ctx->stream) ||
+        launch2_jacobian(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, ctx->stream))
+      return NSWE_ECUDA;
+    return NSWE_OK;
+  }
   int N = prob->N >> level;
   return launch_jacobian(prob->dev, level, N, nb, U, eps, alpha, R, J, res, ctx->partials, ctx->stream) ==
                  cudaSuccess
@@ -332,10 +623,24 @@ nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level, const do
 nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *J, const double *R,
                            double *dU, const nswe_params *params) {
   if (!ctx || !prob || prob->ctx != ctx || !J || !R || !dU || level < 0 || level >= prob->levels) return NSWE_EINVAL;
-  if (nb != 3 && nb != 5) return NSWE_EINVAL;
   nswe_status st = check_params(params, nullptr, 0);
   if (st != NSWE_OK) return st;
   DeviceGuard dg(ctx->device);
+  if (prob->dim == 2) {
+    if (nb != 9 && nb != 21) return NSWE_EINVAL;
+    MG2 m = mg2_bind(prob, level, nb == 21 ? ST_J21 : ST_J9, J, R, dU);
+    cudaMemsetAsync(prob->flag, 0, sizeof(int), ctx->stream);
+    if (level == prob->levels - 1) {
+      const int n = nswe_prob_cells(prob, level);
+      return (launch2_dense_factor(m.lv[level].Nx, m.lv[level].Ny, m.st[level], J, prob->dense, prob->piv,
+                                   prob->flag, ctx->stream) ||
+              launch2_dense_solve(n, prob->dense, prob->piv, R, prob->xbuf, dU, ctx->stream))
+                 ? NSWE_ECUDA
+                 : NSWE_OK;
+    }
+    return (mg2_setup(prob, m, ctx->stream) || mg2_vcycle(prob, m, *params, ctx->stream)) ? NSWE_ECUDA : NSWE_OK;
+  }
+  if (nb != 3 && nb != 5) return NSWE_EINVAL;
   const int coarse = prob->N >> (prob->levels - 1);
   const int coarse_nb = (level == prob->levels - 1) ? nb : 3;
   return launch_vcycle(prob->dev, level, nb, J, R, dU, *params, ctx->status, coarse, coarse_nb, ctx->stream) ==
@@ -353,12 +658,24 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
   for (int i = 0; i < count; ++i) {
     nswe_prob p = probs[i];
     if (!p || p->ctx != ctx || !U0s[i] || !Us[i]) return NSWE_EINVAL;
+    if (p->dim != probs[0]->dim) return NSWE_EINVAL;
     int s0 = (params && params->nest_start >= 0 && params->nest_start < p->levels) ? params->nest_start
                                                                                      : p->levels - 1;
     nswe_status st = check_params(params, p, s0);
     if (st != NSWE_OK) return st;
   }
   DeviceGuard dg(ctx->device);
+  if (probs[0]->dim == 2) {
+    int worst = NSWE_OK;
+    for (int i = 0; i < count; ++i) {
+      nswe_info inf;
+      nswe_status st = solve2d(ctx, probs[i], U0s[i], Us[i], *params, &inf);
+      if (st == NSWE_ECUDA) return st;
+      if (infos) infos[i] = inf;
+      if (st != NSWE_OK && worst == NSWE_OK) worst = st;
+    }
+    return (nswe_status)worst;
+  }
   nswe_status st = ensure_cap(ctx, count);
   if (st != NSWE_OK) return st;
   int max_coarse = 4;

@@ -43,6 +43,49 @@ struct ProbDev {
 // Doubles of Jacobian workspace for a level of N cells.
 inline size_t jw_doubles(size_t N) { return 16 * (N + 2) + 18 * (N + 1); }
 
+// ---------------------------------------------------------------- 2D
+// Block stencils of 2D operators (offset tables in nswe_kernels_2d.cu).
+constexpr int ST_J9 = 0, ST_J21 = 1, ST_P5 = 2, ST_P9 = 3;
+inline int st_size_host(int st) { return st == ST_J9 ? 9 : st == ST_J21 ? 21 : st == ST_P5 ? 5 : 9; }
+inline int st_coarse_host(int st) { return (st == ST_J9 || st == ST_P5) ? ST_P5 : ST_P9; }
+inline int st_colours_host(int st) { return st == ST_J9 ? 3 : st == ST_J21 ? 9 : st == ST_P5 ? 2 : 4; }
+
+struct Level2Dev {
+  int Nx, Ny;
+  double dx, dy;
+  const double *gq;  // [2][4][n]: b_x, b_y at the Gauss points q = 2*beta + gamma
+  const int *bck;    // [2*Ny + 2*Nx] boundary kinds: left, right, bottom, top
+  double *U, *R, *dU;  // [3][n]
+  double *J;           // [21][9][n]
+  double *Dinv;        // [9][n]
+};
+
+struct ProbDev2 {
+  int levels;
+  double g;
+  double bcs[12];    // (h, hu, hv) data per side
+  Level2Dev lev[NSWE_MAX_LEVELS];
+};
+
+cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *U, double *R, double *res,
+                             double *partials, cudaStream_t s);
+cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
+                             const double *R, double *J, cudaStream_t s);
+cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const double *Jf, double *Jc, cudaStream_t s);
+cudaError_t launch2_dinv(int n, int st, const double *J, double *Dinv, cudaStream_t s);
+cudaError_t launch2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
+                        double omega, int col, int reps, cudaStream_t s);
+cudaError_t launch2_restrict(int Nx, int Ny, int st, const double *J, const double *R, const double *dU, double *Rc,
+                             double *dUc, cudaStream_t s);
+cudaError_t launch2_prolong(int Nx, int Ny, double *dU, const double *dUc, cudaStream_t s);
+cudaError_t launch2_dense_factor(int Nx, int Ny, int st, const double *J, double *A, int *piv, int *flag,
+                                 cudaStream_t s);
+cudaError_t launch2_dense_solve(int n, const double *A, const int *piv, const double *R, double *x, double *dU,
+                                cudaStream_t s);
+cudaError_t launch2_update(int n, double *U, const double *dU, double tau, int *flag, cudaStream_t s);
+cudaError_t launch2_interp(const ProbDev2 *p, int coarse_level, int nc, const double *Uc, double *Uf,
+                           cudaStream_t s);
+
 // One solve of a batch.
 struct SolveTask {
   const ProbDev *prob;

@@ -1,0 +1,663 @@
+// CUDA kernels (sm_103a) of the 2D NMGM (Section 4), FP64: the residual of
+// Eq. 20 with dimension-by-dimension characteristic WENO3, LLF fluxes at the
+// two Gauss points of each edge and the S2/S3 source quadratures; the FD
+// Jacobians J21 and J9 (Eq. 21); Galerkin coarse operators by 2x2
+// aggregation (Eq. 24); multicolour 3x3 block SOR (Eq. 22); restriction and
+// prolongation (Eq. 24-25); a dense LU with partial pivoting on the coarsest
+// grid; the App. A interpolation in tensor form (Eq. A.3).
+//
+// A 2D problem is large (512 x 256 cells = 131k cells, 85-200 MB of Jacobian),
+// so every phase is a grid-wide kernel over cells; the host sequences them.
+#include <cmath>
+
+#include "nswe_internal.h"
+
+namespace nswe {
+
+// Stencil offset tables (dx, dy), sorted by dy then dx; index = position in
+// the block storage J[(k*9 + l*3 + m)*n + c].
+__constant__ int c_off_j9[9][2] = {{0, -2}, {0, -1}, {-2, 0}, {-1, 0}, {0, 0}, {1, 0}, {2, 0}, {0, 1}, {0, 2}};
+__constant__ int c_off_j21[21][2] = {{-1, -2}, {0, -2}, {1, -2}, {-2, -1}, {-1, -1}, {0, -1}, {1, -1},
+                                     {2, -1},  {-2, 0}, {-1, 0}, {0, 0},   {1, 0},   {2, 0},   {-2, 1},
+                                     {-1, 1},  {0, 1},  {1, 1},  {2, 1},   {-1, 2},  {0, 2},   {1, 2}};
+__constant__ int c_off_p5[5][2] = {{0, -1}, {-1, 0}, {0, 0}, {1, 0}, {0, 1}};
+__constant__ int c_off_p9[9][2] = {{-1, -1}, {0, -1}, {1, -1}, {-1, 0}, {0, 0}, {1, 0}, {-1, 1}, {0, 1}, {1, 1}};
+
+namespace {
+
+constexpr double kZeta2 = 1e-6;
+constexpr double kGs2 = 0.28867513459481288225;   // 1/(2 sqrt 3)
+constexpr double kTq = 0.14433756729740644113;    // 1/(4 sqrt 3)
+__device__ constexpr double kLag2[2][4] = {
+    {(-kGs2 - 1.5) / 36.0, -(13.0 / 12.0) * (-kGs2 - 0.5), (13.0 / 12.0) * (-kGs2 + 0.5), -(-kGs2 + 1.5) / 36.0},
+    {(kGs2 - 1.5) / 36.0, -(13.0 / 12.0) * (kGs2 - 0.5), (13.0 / 12.0) * (kGs2 + 0.5), -(kGs2 + 1.5) / 36.0}};
+
+__device__ __forceinline__ int st_size(int st) { return st == ST_J9 ? 9 : st == ST_J21 ? 21 : st == ST_P5 ? 5 : 9; }
+__device__ __forceinline__ int st_off(int st, int k, int d) {
+  return st == ST_J9 ? c_off_j9[k][d] : st == ST_J21 ? c_off_j21[k][d] : st == ST_P5 ? c_off_p5[k][d] : c_off_p9[k][d];
+}
+__device__ __forceinline__ int st_center(int st) { return st == ST_J9 ? 4 : st == ST_J21 ? 10 : st == ST_P5 ? 2 : 4; }
+__device__ __forceinline__ int st_coarse(int st) { return (st == ST_J9 || st == ST_P5) ? ST_P5 : ST_P9; }
+__device__ __forceinline__ int st_colour(int st, int i, int j) {
+  return st == ST_J9 ? (i + j) % 3 : st == ST_J21 ? (i % 3) + 3 * (j % 3) : st == ST_P5 ? (i + j) % 2 : (i % 2) + 2 * (j % 2);
+}
+
+struct Geo2 {
+  int Nx, Ny;
+  double dx, dy, g;
+  const double *gq;
+  const int *bck;
+  const double *bcs;
+};
+
+__device__ __forceinline__ Geo2 make_geo2(const ProbDev2 &P, int l) {
+  Geo2 G;
+  G.Nx = P.lev[l].Nx;
+  G.Ny = P.lev[l].Ny;
+  G.dx = P.lev[l].dx;
+  G.dy = P.lev[l].dy;
+  G.g = P.g;
+  G.gq = P.lev[l].gq;
+  G.bck = P.lev[l].bck;
+  G.bcs = P.bcs;
+  return G;
+}
+
+// Perturbation of one interior cell in one component (cp < 0: none).
+struct Pert {
+  int cp, m;
+  double eps;
+};
+
+__device__ __forceinline__ void bc_post(int kind, const double *st, double o[3], int normal) {
+  if (kind == NSWE_BC2_REFLECT) {
+    o[normal] = -o[normal];
+  } else if (kind == NSWE_BC2_DISCHARGE) {
+    o[1] = st[1];
+    o[2] = st[2];
+  } else if (kind == NSWE_BC2_DEPTH) {
+    o[0] = st[0];
+  }
+}
+
+// Cell value with two ghost layers (x rule, then y rule at corners).
+__device__ __forceinline__ void cellv(const Geo2 &G, const double *U, int i, int j, const Pert &p, double o[3]) {
+  const int Nx = G.Nx, Ny = G.Ny, n = Nx * Ny;
+  int xk = 0, xs = 0;
+  if (i < 0 || i >= Nx) {
+    xs = i < 0 ? 0 : 1;
+    xk = G.bck[xs * Ny + min(max(j, 0), Ny - 1)];
+    if (xk == NSWE_BC2_INFLOW) {
+      o[0] = G.bcs[xs * 3];
+      o[1] = G.bcs[xs * 3 + 1];
+      o[2] = G.bcs[xs * 3 + 2];
+      return;
+    }
+    i = (xk == NSWE_BC2_REFLECT) ? (i < 0 ? -1 - i : 2 * Nx - 1 - i) : (i < 0 ? 0 : Nx - 1);
+  }
+  if (j < 0 || j >= Ny) {
+    const int ys = j < 0 ? 2 : 3;
+    const int yk = G.bck[2 * Ny + (ys - 2) * Nx + i];
+    if (yk == NSWE_BC2_INFLOW) {
+      o[0] = G.bcs[ys * 3];
+      o[1] = G.bcs[ys * 3 + 1];
+      o[2] = G.bcs[ys * 3 + 2];
+    } else {
+      const int jj = (yk == NSWE_BC2_REFLECT) ? (j < 0 ? -1 - j : 2 * Ny - 1 - j) : (j < 0 ? 0 : Ny - 1);
+      const int c = jj * Nx + i;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) o[m] = (c == p.cp && m == p.m) ? U[m * n + c] + p.eps : U[m * n + c];
+      bc_post(yk, G.bcs + ys * 3, o, 2);
+    }
+  } else {
+    const int c = j * Nx + i;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) o[m] = (c == p.cp && m == p.m) ? U[m * n + c] + p.eps : U[m * n + c];
+  }
+  if (xk) bc_post(xk, G.bcs + xs * 3, o, 1);
+}
+
+__device__ __forceinline__ void weno3_both(double a, double b, double c, double &up, double &um) {
+  double d0 = c - b, d1 = b - a;
+  double e0 = kZeta2 + d0 * d0, e1 = kZeta2 + d1 * d1;
+  double s0 = e0 * e0, s1 = e1 * e1;
+  double p0 = 1.5 * b - 0.5 * c, p1 = 0.5 * a + 0.5 * b;
+  double q0 = 0.5 * b + 0.5 * c, q1 = -0.5 * a + 1.5 * b;
+  double D1 = s1 + 2.0 * s0, D2 = 2.0 * s1 + s0;
+  double inv = 1.0 / (D1 * D2);
+  up = (s1 * p0 + 2.0 * s0 * p1) * (D2 * inv);
+  um = (2.0 * s1 * q0 + s0 * q1) * (D1 * inv);
+}
+
+// One-sided characteristic WENO3 at the interface between line cells a and
+// a+1; v[0..3] = cells a-1..a+2; side 0: U^-, side 1: U^+.
+__device__ __forceinline__ void char_rec(int dir, const double v[4][3], double g, int side, double out[3]) {
+  const int in = dir == 0 ? 1 : 2, it = dir == 0 ? 2 : 1;
+  const double h = 0.5 * (v[1][0] + v[2][0]);
+  const double ih = 1.0 / h;
+  const double un = 0.5 * (v[1][in] + v[2][in]) * ih, ut = 0.5 * (v[1][it] + v[2][it]) * ih;
+  const double c = sqrt(g * h), i2c = 0.5 / c;
+  double W[3][3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const double *u = v[side + s];
+    W[s][0] = (un + c) * i2c * u[0] - i2c * u[in];
+    W[s][1] = -ut * u[0] + u[it];
+    W[s][2] = -(un - c) * i2c * u[0] + i2c * u[in];
+  }
+  double Wr[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    double up, um;
+    weno3_both(W[0][f], W[1][f], W[2][f], up, um);
+    Wr[f] = side == 0 ? um : up;
+  }
+  out[0] = Wr[0] + Wr[2];
+  out[in] = (un - c) * Wr[0] + (un + c) * Wr[2];
+  out[it] = ut * Wr[0] + Wr[1] + ut * Wr[2];
+}
+
+__device__ __forceinline__ void llf(int dir, const double L[3], const double R[3], double g, double F[3]) {
+  const int in = dir == 0 ? 1 : 2;
+  const double iL = 1.0 / L[0], iR = 1.0 / R[0];
+  const double uL = L[1] * iL, vL = L[2] * iL, uR = R[1] * iR, vR = R[2] * iR;
+  const double pL = 0.5 * g * L[0] * L[0], pR = 0.5 * g * R[0] * R[0];
+  double FL[3], FR[3];
+  if (dir == 0) {
+    FL[0] = L[1]; FL[1] = L[1] * uL + pL; FL[2] = L[1] * vL;
+    FR[0] = R[1]; FR[1] = R[1] * uR + pR; FR[2] = R[1] * vR;
+  } else {
+    FL[0] = L[2]; FL[1] = L[2] * uL; FL[2] = L[2] * vL + pL;
+    FR[0] = R[2]; FR[1] = R[2] * uR; FR[2] = R[2] * vR + pR;
+  }
+  const double a = fmax(fabs(L[in] * iL) + sqrt(g * L[0]), fabs(R[in] * iR) + sqrt(g * R[0]));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) F[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * a * (R[m] - L[m]);
+}
+
+// Local residual R_ij (Eq. 20) of the (possibly perturbed) state.
+__device__ void local_residual2(const Geo2 &G, const double *U, int i, int j, const Pert &p, double R[3]) {
+  const int n = G.Nx * G.Ny, c = j * G.Nx + i;
+  double flux[2][3], S[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    const int a = dir == 0 ? i : j, r0 = dir == 0 ? j : i;
+    // gv[q][f][side][m]: values at the two Gauss lines q of the interfaces
+    // f = a-3/2, a-1/2, a+1/2, a+3/2 (f = 0..3)
+    double ifv[3][4][2][3];
+#pragma unroll 1
+    for (int t = 0; t < 3; ++t) {
+      double v[7][3];  // line cells a-3 .. a+3
+#pragma unroll
+      for (int s = 0; s < 7; ++s) {
+        if (dir == 0) cellv(G, U, a - 3 + s, r0 - 1 + t, p, v[s]);
+        else cellv(G, U, r0 - 1 + t, a - 3 + s, p, v[s]);
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        // interface between cells k = a-2+f and k+1: v index of cell k-1 is f
+        const double(*w)[3] = &v[f];
+        if (f > 0) char_rec(dir, w, G.g, 0, ifv[t][f][0]);
+        if (f < 3) char_rec(dir, w, G.g, 1, ifv[t][f][1]);
+      }
+    }
+    double fl[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    double hq[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double sg = q == 0 ? -kTq : kTq;
+      double gv[4][2][3];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          if ((f == 0 && sd == 0) || (f == 3 && sd == 1)) continue;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) gv[f][sd][m] = ifv[1][f][sd][m] + sg * (ifv[2][f][sd][m] - ifv[0][f][sd][m]);
+        }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        double F[3];
+        llf(dir, gv[1 + e][0], gv[1 + e][1], G.g, F);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) fl[e][m] += 0.5 * F[m];
+      }
+      hq[q][0] = gv[0][1][0];
+      hq[q][1] = gv[1][1][0];
+      hq[q][2] = gv[2][0][0];
+      hq[q][3] = gv[3][0][0];
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) flux[dir][m] = fl[1][m] - fl[0][m];
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int pp = 0; pp < 2; ++pp) {
+        const double hv = kLag2[pp][0] * hq[q][0] + kLag2[pp][1] * hq[q][1] + kLag2[pp][2] * hq[q][2] +
+                          kLag2[pp][3] * hq[q][3];
+        const int beta = dir == 0 ? q : pp, gamma = dir == 0 ? pp : q;
+        acc += G.g * hv * G.gq[(dir * 4 + 2 * beta + gamma) * n + c];
+      }
+    S[1 + dir] = -0.25 * acc;
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) R[m] = flux[0][m] / G.dx + flux[1][m] / G.dy - S[m];
+}
+
+__device__ double block_sum2(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// ---------------------------------------------------------------------------- kernels
+
+__global__ void __launch_bounds__(kThreads) k2_residual(const ProbDev2 *P, int level, const double *U, double *R,
+                                                        double *partials) {
+  __shared__ double red[33];
+  const Geo2 G = make_geo2(*P, level);
+  const int n = G.Nx * G.Ny;
+  const Pert np{-1, 0, 0.0};
+  double acc = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    double r[3];
+    local_residual2(G, U, c % G.Nx, c / G.Nx, np, r);
+    R[c] = r[0];
+    R[n + c] = r[1];
+    R[2 * n + c] = r[2];
+    acc += fabs(r[0]) + fabs(r[1]) + fabs(r[2]);
+  }
+  const double s = block_sum2(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k2_finish(const double *partials, int nparts, int n, double *res) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += partials[i];
+    *res = s / n;
+  }
+}
+
+// One item = (cell, stencil block k): three perturbed local residuals.
+__global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int level, int st, const double *U,
+                                                        double eps, double alpha, const double *R, double *J) {
+  const Geo2 G = make_geo2(*P, level);
+  const int n = G.Nx * G.Ny, K = st_size(st), kc = st_center(st);
+  const double ieps = 1.0 / eps;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n * K; it += gridDim.x * blockDim.x) {
+    const int c = it % n, k = it / n, i = c % G.Nx, j = c / G.Nx;
+    const int pi = i + st_off(st, k, 0), pj = j + st_off(st, k, 1);
+    if (pi < 0 || pi >= G.Nx || pj < 0 || pj >= G.Ny) {
+      for (int e = 0; e < 9; ++e) J[(size_t)(k * 9 + e) * n + c] = 0.0;
+      continue;
+    }
+    const double R0[3] = {R[c], R[n + c], R[2 * n + c]};
+    const double reg = (k == kc) ? alpha * (fabs(R0[0]) + fabs(R0[1]) + fabs(R0[2])) : 0.0;
+    for (int m = 0; m < 3; ++m) {
+      const Pert p{pj * G.Nx + pi, m, eps};
+      double Rp[3];
+      local_residual2(G, U, i, j, p, Rp);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        double v = (Rp[l] - R0[l]) * ieps;
+        if (l == m) v += reg;
+        J[(size_t)(k * 9 + l * 3 + m) * n + c] = v;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st, const double *Jf, double *Jc) {
+  const int n = Nx * Ny, Ncx = Nx / 2, Ncy = Ny / 2, nc = Ncx * Ncy, K = st_size(st), cs = st_coarse(st),
+            Kc = st_size(cs);
+  for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += gridDim.x * blockDim.x) {
+    const int I = cc % Ncx, Jy = cc / Ncx;
+    double acc[9][9];
+    for (int t = 0; t < Kc; ++t)
+      for (int e = 0; e < 9; ++e) acc[t][e] = 0.0;
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int xi = 2 * I + a, yi = 2 * Jy + b, c = yi * Nx + xi;
+        for (int k = 0; k < K; ++k) {
+          const int ex = xi + st_off(st, k, 0), ey = yi + st_off(st, k, 1);
+          if (ex < 0 || ex >= Nx || ey < 0 || ey >= Ny) continue;
+          const int ox = ex / 2 - I, oy = ey / 2 - Jy;
+          int kk = -1;
+          for (int t = 0; t < Kc; ++t)
+            if (st_off(cs, t, 0) == ox && st_off(cs, t, 1) == oy) kk = t;
+          if (kk < 0) continue;
+          for (int e = 0; e < 9; ++e) acc[kk][e] += Jf[(size_t)(k * 9 + e) * n + c];
+        }
+      }
+    for (int t = 0; t < Kc; ++t)
+      for (int e = 0; e < 9; ++e) Jc[(size_t)(t * 9 + e) * nc + cc] = acc[t][e];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k2_dinv(int n, int st, const double *J, double *Dinv) {
+  const int kc = st_center(st);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    double a[9];
+    for (int e = 0; e < 9; ++e) a[e] = J[(size_t)(kc * 9 + e) * n + c];
+    const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    Dinv[0 * (size_t)n + c] = c00 / det;
+    Dinv[1 * (size_t)n + c] = (a[2] * a[7] - a[1] * a[8]) / det;
+    Dinv[2 * (size_t)n + c] = (a[1] * a[5] - a[2] * a[4]) / det;
+    Dinv[3 * (size_t)n + c] = c01 / det;
+    Dinv[4 * (size_t)n + c] = (a[0] * a[8] - a[2] * a[6]) / det;
+    Dinv[5 * (size_t)n + c] = (a[2] * a[3] - a[0] * a[5]) / det;
+    Dinv[6 * (size_t)n + c] = c02 / det;
+    Dinv[7 * (size_t)n + c] = (a[1] * a[6] - a[0] * a[7]) / det;
+    Dinv[8 * (size_t)n + c] = (a[0] * a[4] - a[1] * a[3]) / det;
+  }
+}
+
+// Block SOR (Eq. 22) on the cells of one colour, relaxation applied reps
+// times (consecutive visits of a colour see the same neighbours).
+__global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv,
+                                                   const double *R, double *dU, double omega, int col, int reps) {
+  const int n = Nx * Ny, K = st_size(st), kc = st_center(st);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const int i = c % Nx, j = c / Nx;
+    if (st_colour(st, i, j) != col) continue;
+    double r[3] = {R[c], R[n + c], R[2 * n + c]};
+    for (int k = 0; k < K; ++k) {
+      if (k == kc) continue;
+      const int p = i + st_off(st, k, 0), q = j + st_off(st, k, 1);
+      if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
+      const int cp = q * Nx + p;
+      const double x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
+                J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
+    }
+    double t[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      t[l] = Dinv[(size_t)(l * 3 + 0) * n + c] * r[0] + Dinv[(size_t)(l * 3 + 1) * n + c] * r[1] +
+             Dinv[(size_t)(l * 3 + 2) * n + c] * r[2];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double x = dU[l * n + c];
+      for (int s = 0; s < reps; ++s) x = (1.0 - omega) * x - omega * t[l];
+      dU[l * n + c] = x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, const double *J, const double *R,
+                                                        const double *dU, double *Rc, double *dUc) {
+  const int n = Nx * Ny, Ncx = Nx / 2, nc = Ncx * (Ny / 2), K = st_size(st);
+  for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += gridDim.x * blockDim.x) {
+    const int I = cc % Ncx, Jy = cc / Ncx;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int xi = 2 * I + a, yi = 2 * Jy + b, c = yi * Nx + xi;
+        double r[3] = {R[c], R[n + c], R[2 * n + c]};
+        for (int k = 0; k < K; ++k) {
+          const int p = xi + st_off(st, k, 0), q = yi + st_off(st, k, 1);
+          if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
+          const int cp = q * Nx + p;
+          const double x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
+                    J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
+        }
+        s[0] += r[0];
+        s[1] += r[1];
+        s[2] += r[2];
+      }
+    // the oracle accumulates the four children in row-major fine order
+    for (int l = 0; l < 3; ++l) {
+      Rc[l * nc + cc] = s[l];
+      dUc[l * nc + cc] = 0.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k2_prolong(int Nx, int Ny, double *dU, const double *dUc) {
+  const int n = Nx * Ny, Ncx = Nx / 2, nc = Ncx * (Ny / 2);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const int cc = (c / Nx / 2) * Ncx + (c % Nx) / 2;
+    for (int l = 0; l < 3; ++l) dU[l * n + c] += dUc[l * nc + cc];
+  }
+}
+
+// Dense system A (row-major, unknown 3c+m) assembled from a block operator:
+// zero it, then scatter the blocks.
+__global__ void __launch_bounds__(kThreads) k2_zero(long count, double *A) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) A[t] = 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) k2_scatter(int Nx, int Ny, int st, const double *J, double *A) {
+  const int n = Nx * Ny, N3 = 3 * n, K = st_size(st);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * K; t += gridDim.x * blockDim.x) {
+    const int c = t % n, k = t / n, i = c % Nx, j = c / Nx;
+    const int p = i + st_off(st, k, 0), q = j + st_off(st, k, 1);
+    if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
+    const int cp = q * Nx + p;
+    for (int l = 0; l < 3; ++l)
+      for (int m = 0; m < 3; ++m) A[(size_t)(3 * c + l) * N3 + 3 * cp + m] = J[(size_t)(k * 9 + l * 3 + m) * n + c];
+  }
+}
+
+// LU with partial pivoting (ties to the lowest row) of A (n x n, global
+// memory), one thread block. piv[k] = pivot row; flag = 1 on an exact zero pivot.
+__global__ void __launch_bounds__(kThreads) k2_lu(int N3, double *A, int *piv, int *flag) {
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_p;
+  for (int k = 0; k < N3; ++k) {
+    double best = -1.0;
+    int bi = N3;
+    for (int i = k + threadIdx.x; i < N3; i += blockDim.x) {
+      const double v = fabs(A[(size_t)i * N3 + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sv[threadIdx.x >> 5] = best;
+      si[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = sv[0];
+      int p = si[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (sv[w] > b || (sv[w] == b && si[w] < p)) {
+          b = sv[w];
+          p = si[w];
+        }
+      s_p = p;
+      piv[k] = p;
+      if (A[(size_t)p * N3 + k] == 0.0) *flag = 1;
+    }
+    __syncthreads();
+    const int p = s_p;
+    // Swap only the active columns: earlier multipliers stay where they were
+    // computed, which is what the interleaved forward solve expects.
+    if (p != k)
+      for (int c = k + threadIdx.x; c < N3; c += blockDim.x) {
+        const double t = A[(size_t)k * N3 + c];
+        A[(size_t)k * N3 + c] = A[(size_t)p * N3 + c];
+        A[(size_t)p * N3 + c] = t;
+      }
+    __syncthreads();
+    const double d = A[(size_t)k * N3 + k];
+    for (int i = k + 1 + threadIdx.x; i < N3; i += blockDim.x) A[(size_t)i * N3 + k] = A[(size_t)i * N3 + k] / d;
+    __syncthreads();
+    const int rows = N3 - k - 1;
+    for (int t = threadIdx.x; t < rows * rows; t += blockDim.x) {
+      const int i = k + 1 + t / rows, c = k + 1 + t % rows;
+      A[(size_t)i * N3 + c] -= A[(size_t)i * N3 + k] * A[(size_t)k * N3 + c];
+    }
+    __syncthreads();
+  }
+}
+
+// dU = -A^{-1} R with the factors (one warp; unknown 3c+m).
+__global__ void k2_lu_solve(int n, const double *A, const int *piv, const double *R, double *x, double *dU) {
+  const int N3 = 3 * n, lane = threadIdx.x;
+  if (threadIdx.x >= 32) return;
+  for (int t = lane; t < n; t += 32)
+    for (int m = 0; m < 3; ++m) x[3 * t + m] = -R[m * n + t];
+  __syncwarp();
+  for (int k = 0; k < N3; ++k) {
+    const int p = piv[k];
+    if (lane == 0 && p != k) {
+      const double t = x[k];
+      x[k] = x[p];
+      x[p] = t;
+    }
+    __syncwarp();
+    const double xk = x[k];
+    for (int i = k + 1 + lane; i < N3; i += 32) x[i] -= A[(size_t)i * N3 + k] * xk;
+    __syncwarp();
+  }
+  for (int i = N3 - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int c = i + 1 + lane; c < N3; c += 32) s += A[(size_t)i * N3 + c] * x[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[i] = (x[i] - s) / A[(size_t)i * N3 + i];
+    __syncwarp();
+  }
+  for (int t = lane; t < n; t += 32)
+    for (int m = 0; m < 3; ++m) dU[m * n + t] = x[3 * t + m];
+}
+
+__global__ void __launch_bounds__(kThreads) k2_update(int n, double *U, const double *dU, double tau, int *flag) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const double h = U[c] + tau * dU[c];
+    U[c] = h;
+    U[n + c] += tau * dU[n + c];
+    U[2 * n + c] += tau * dU[2 * n + c];
+    if (!(h > 0.0)) atomicOr(flag, 1);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k2_interp(const ProbDev2 *P, int coarse_level, const double *Uc,
+                                                      double *Uf) {
+  const Geo2 Gc = make_geo2(*P, coarse_level);
+  const int Ncx = Gc.Nx, Ncy = Gc.Ny, Nfx = 2 * Ncx, nf = 4 * Ncx * Ncy;
+  const double w[2][3] = {{0.125, 1.0, -0.125}, {-0.125, 1.0, 0.125}};
+  const Pert np{-1, 0, 0.0};
+  for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < Ncx * Ncy; cc += gridDim.x * blockDim.x) {
+    const int I = cc % Ncx, Jc = cc / Ncx;
+    double nb[3][3][3];
+    for (int q = -1; q <= 1; ++q)
+      for (int p = -1; p <= 1; ++p) cellv(Gc, Uc, I + p, Jc + q, np, nb[q + 1][p + 1]);
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int cf = (2 * Jc + b) * Nfx + 2 * I + a;
+        for (int m = 0; m < 3; ++m) {
+          double s = 0.0;
+          for (int q = 0; q < 3; ++q) {
+            double row = 0.0;
+            for (int p = 0; p < 3; ++p) row += w[a][p] * nb[q][p][m];
+            s += w[b][q] * row;
+          }
+          Uf[m * nf + cf] = s;
+        }
+      }
+  }
+}
+
+int grid2(long items) {
+  long b = (items + kThreads - 1) / kThreads;
+  return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+}  // namespace
+
+cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *U, double *R, double *res,
+                             double *partials, cudaStream_t s) {
+  const int grid = grid2(n) > 1024 ? 1024 : grid2(n);
+  k2_residual<<<grid, kThreads, 0, s>>>(p, level, U, R, partials);
+  if (res) k2_finish<<<1, 32, 0, s>>>(partials, grid, n, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
+                             const double *R, double *J, cudaStream_t s) {
+  k2_jacobian<<<grid2((long)n * (st == ST_J21 ? 21 : 9)), kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const double *Jf, double *Jc, cudaStream_t s) {
+  k2_coarse_op<<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, Jf, Jc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_dinv(int n, int st, const double *J, double *Dinv, cudaStream_t s) {
+  k2_dinv<<<grid2(n), kThreads, 0, s>>>(n, st, J, Dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
+                        double omega, int col, int reps, cudaStream_t s) {
+  k2_sor<<<grid2((long)Nx * Ny), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, col, reps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_restrict(int Nx, int Ny, int st, const double *J, const double *R, const double *dU, double *Rc,
+                             double *dUc, cudaStream_t s) {
+  k2_restrict<<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, J, R, dU, Rc, dUc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_prolong(int Nx, int Ny, double *dU, const double *dUc, cudaStream_t s) {
+  k2_prolong<<<grid2((long)Nx * Ny), kThreads, 0, s>>>(Nx, Ny, dU, dUc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_dense_factor(int Nx, int Ny, int st, const double *J, double *A, int *piv, int *flag,
+                                 cudaStream_t s) {
+  const long N3 = 3L * Nx * Ny;
+  k2_zero<<<grid2(N3 * N3), kThreads, 0, s>>>(N3 * N3, A);
+  k2_scatter<<<grid2((long)Nx * Ny * (st == ST_J21 ? 21 : 9)), kThreads, 0, s>>>(Nx, Ny, st, J, A);
+  k2_lu<<<1, kThreads, 0, s>>>((int)N3, A, piv, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_dense_solve(int n, const double *A, const int *piv, const double *R, double *x, double *dU,
+                                cudaStream_t s) {
+  k2_lu_solve<<<1, 32, 0, s>>>(n, A, piv, R, x, dU);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_update(int n, double *U, const double *dU, double tau, int *flag, cudaStream_t s) {
+  k2_update<<<grid2(n), kThreads, 0, s>>>(n, U, dU, tau, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch2_interp(const ProbDev2 *p, int coarse_level, int nc, const double *Uc, double *Uf,
+                           cudaStream_t s) {
+  k2_interp<<<grid2(nc), kThreads, 0, s>>>(p, coarse_level, Uc, Uf);
+  return cudaGetLastError();
+}
+
+}  // namespace nswe

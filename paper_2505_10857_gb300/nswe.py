@@ -64,8 +64,10 @@ EXPORTS = {
     "nswe_prob_create_1d": (_i, [_vp, ctypes.POINTER(_vp), _i, _i, _d, _d, _d, _dp, _dp,
                                  ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
     "nswe_prob_set_geometry_1d": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
+    "nswe_prob_create_2d": (_i, [_vp, ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _d, _d, _d, _dp, _dp, _dp]),
     "nswe_prob_destroy": (_i, [_vp]),
     "nswe_prob_cells": (_i, [_vp, _i]),
+    "nswe_prob_dim": (_i, [_vp]),
     "nswe_residual": (_i, [_vp, _vp, _i, _dp, _dp, _dp]),
     "nswe_jacobian_simplified": (_i, [_vp, _vp, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_jacobian_full": (_i, [_vp, _vp, _i, _dp, _d, _d, _dp, _dp, _dp]),
@@ -216,6 +218,49 @@ class Problem1D:
             self.close()
         except Exception:
             pass
+
+
+class Problem2D:
+    """nswe_prob of a 2D problem (host arrays copied to device)."""
+
+    def __init__(self, ctx: Context, Nx, Ny, levels, x0, x1, y0, y1, g, gauss_geom_all, bc_kind_all, bc_state):
+        self.ctx = ctx
+        self.Nx, self.Ny, self.levels = int(Nx), int(Ny), int(levels)
+        gq = np.ascontiguousarray(gauss_geom_all, dtype=np.float64)
+        kinds = np.ascontiguousarray(bc_kind_all, dtype=np.int32)
+        st = np.ascontiguousarray(bc_state, dtype=np.float64).reshape(-1)
+        self.h = _vp()
+        _check("nswe_prob_create_2d", lib().nswe_prob_create_2d(
+            ctx.h, ctypes.byref(self.h), self.Nx, self.Ny, self.levels, float(x0), float(x1), float(y0), float(y1),
+            float(g), gq.ctypes.data, kinds.ctypes.data, st.ctypes.data))
+
+    @staticmethod
+    def from_inputs(ctx: Context, inp) -> "Problem2D":
+        return Problem2D(ctx, inp.Nx, inp.Ny, inp.levels, inp.x0, inp.x1, inp.y0, inp.y1, inp.g, inp.gq_all(),
+                         inp.bc_kind_all(), inp.bc_state)
+
+    def cells(self, level=0):
+        return lib().nswe_prob_cells(self.h, int(level))
+
+    def close(self):
+        if self.h:
+            lib().nswe_prob_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def params2d_from(prm, levels=None) -> Params:
+    """From an inputs.Params2D (one eps for every level, scalar smoothing counts)."""
+    nu1 = prm.nu1[0] if hasattr(prm.nu1, "__len__") else prm.nu1
+    nu2 = prm.nu2[0] if hasattr(prm.nu2, "__len__") else prm.nu2
+    return params(96, levels or prm.levels, alpha=prm.alpha, tau=prm.tau, omega=prm.omega, tol=prm.tol, nu1=nu1,
+                  nu2=nu2, nu3=prm.nu3, n_max=prm.n_max, nb=JAC_FULL if prm.st == 1 else JAC_SIMPLIFIED,
+                  nest_start=prm.nest_start, eps=prm.eps)
 
 
 def _host_ptr(a) -> int:

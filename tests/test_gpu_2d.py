@@ -1,0 +1,146 @@
+"""GPU parity of the 2D CUDA path (through the C ABI) against the 2D oracle.
+
+Tolerances: residual 1e-12 of the flux scale (fluxes over the cell size);
+Jacobian 1e-12 of the block scale plus 8u*scale/eps for FD cancellation
+(eps = 1e-6 in 2D, Section 5.2); V-cycles 1e-12 relative; converged Newton
+solutions 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_2505_10857_gb300 import inputs as I
+from gpu_util import EPS64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nswe():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2505_10857_gb300 import nswe as N
+    N.lib()
+    return N
+
+
+@pytest.fixture(scope="module")
+def ctx(nswe):
+    return nswe.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def problems():
+    bumps = I.bottom2d_gaussians([(0.1, 1.2, 0.8, 0.6), (-0.05, 2.0, 1.5, 0.4)])
+    mixed = I.make_problem_2d(12, 8, 2, 0.0, 3.0, 0.0, 2.0, 9.81, bumps,
+                              (I.BC2_INFLOW, I.BC2_OUTFLOW, lambda x: I.BC2_OUTFLOW if x < 1.5 else I.BC2_REFLECT,
+                               I.BC2_DEPTH), np.array([[1.6, 2.2, 0.3], [0, 0, 0], [0, 0, 0], [1.4, 0.0, 0.0]]),
+                              lambda X, Y: (1.5, 2.0, 0.1))
+    return {"mixed": mixed, "wedge": I.wedge(32, 16, 2), "bump": I.paper_parabolic_bump(32, 16, 3)}
+
+
+def state_for(inp, level, seed):
+    rng = np.random.default_rng(seed)
+    nx, ny = inp.dims(level)
+    X, Y = inp.centres(level)
+    s = inp.bc_state[0]
+    h = 1.2 + 0.2 * np.sin(X) * np.cos(Y) + 0.01 * rng.standard_normal(X.shape)
+    hu = (s[1] if s[1] else 1.0) * (1 + 0.05 * np.cos(Y + X)) + 0.02 * rng.standard_normal(X.shape)
+    hv = 0.1 * np.sin(X) + 0.02 * rng.standard_normal(X.shape)
+    return np.ascontiguousarray(np.stack([h.ravel(), hu.ravel(), hv.ravel()]))
+
+
+def flux_scale2(U, g, dx):
+    h = np.abs(U[0]).max()
+    m = np.abs(U[1:]).max()
+    return (m * m / np.abs(U[0]).min() + 0.5 * g * h * h + m) / dx
+
+
+@pytest.mark.parametrize("name", ["mixed", "wedge", "bump"])
+def test_residual_parity_2d(nswe, ctx, orc, name):
+    inp = problems()[name]
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    for level in range(inp.levels):
+        pr = orc.problem_levels2d(inp)[level]
+        U = state_for(inp, level, 10 + level)
+        Rref, resref = orc.residual2d(pr, U)
+        dR = torch.zeros_like(dev(U))
+        dres = torch.zeros(1, dtype=torch.float64, device="cuda")
+        nswe.nswe_residual(ctx, prob, level, dev(U), dR, dres)
+        sc = flux_scale2(U, inp.g, min(pr.s.dx, pr.s.dy))
+        assert np.abs(host(dR) - Rref).max() <= 1e-12 * sc
+        assert abs(host(dres)[0] - resref) <= 1e-12 * sc
+
+
+@pytest.mark.parametrize("name", ["mixed", "wedge"])
+@pytest.mark.parametrize("full", [False, True])
+def test_jacobian_parity_2d(nswe, ctx, orc, name, full):
+    inp = problems()[name]
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    level = inp.levels - 1
+    pr = orc.problem_levels2d(inp)[level]
+    U = state_for(inp, level, 20)
+    st = orc.ST_J21 if full else orc.ST_J9
+    eps = 1e-6
+    Jref, Rref, _ = orc.jacobian2d(pr, U, eps, 3.0, st)
+    K = Jref.shape[0]
+    dR = torch.zeros((3, pr.n), dtype=torch.float64, device="cuda")
+    dJ = torch.full((K, 9, pr.n), float("nan"), dtype=torch.float64, device="cuda")
+    f = nswe.nswe_jacobian_full if full else nswe.nswe_jacobian_simplified
+    f(ctx, prob, level, dev(U), eps, 3.0, dR, dJ)
+    J = host(dJ)
+    sc = flux_scale2(U, inp.g, min(pr.s.dx, pr.s.dy))
+    assert np.isfinite(J).all()
+    tol = 1e-12 * np.abs(Jref).max() + 8.0 * EPS64 * sc / eps
+    assert np.abs(J - Jref).max() <= tol, (np.abs(J - Jref).max(), tol)
+    assert np.abs(host(dR) - Rref).max() <= 1e-12 * sc
+
+
+@pytest.mark.parametrize("name,level,full", [("bump", 0, False), ("bump", 1, False), ("bump", 0, True),
+                                             ("wedge", 0, False), ("mixed", 0, False)])
+def test_vcycle_parity_2d(nswe, ctx, orc, name, level, full):
+    inp = problems()[name]
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    pr = orc.problem_levels2d(inp)[level]
+    U = state_for(inp, level, 30)
+    st = orc.ST_J21 if full else orc.ST_J9
+    J, R, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, st)
+    nx, ny = inp.dims(level)
+    rng = np.random.default_rng(31)
+    dU0 = 1e-3 * rng.standard_normal((3, nx * ny))
+    nlev = inp.levels - level
+    ref = orc.vcycle2d(J, R, dU0, nx, ny, st, nlev, 0.1, 3, 3)
+    prm = nswe.params(96, inp.levels, omega=0.1, nu1=3, nu2=3)
+    ddU = dev(dU0)
+    nswe.nswe_mg_vcycle(ctx, prob, level, 21 if full else 9, dev(J), dev(R), ddU, prm)
+    got = host(ddU)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", ["bump_j9", "bump_j21", "wedge_direct"])
+def test_newton_solve_parity_2d(nswe, ctx, orc, case):
+    if case.startswith("bump"):
+        inp = I.paper_parabolic_bump(32, 16, 3)
+        prm = I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400, st=orc.ST_J21 if "j21" in case else 0)
+    else:
+        inp = I.wedge(16, 8, 1)
+        prm = I.Params2D(levels=1, nu1=[10], nu2=[10], tol=1e-11, n_max=400)
+    Uref, iref = orc.solve_problem2d(inp, prm)
+    assert iref["status"] == 0
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    U = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
+    info = nswe.nswe_newton_solve(ctx, prob, dev(inp.U0_start), U, nswe.params2d_from(prm))
+    assert info["status"] == 0, info
+    got = host(U)
+    assert np.abs(got - Uref).max() <= 1e-10 * np.abs(Uref).max(), np.abs(got - Uref).max()
+    for l in range(inp.levels):
+        assert abs(info["iters"][l] - iref["iters"][l]) <= 2, (info["iters"], iref["iters"])
