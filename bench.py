@@ -398,6 +398,73 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
+def run_wedge2d(args):
+    """2D measurement (not the default line): a nested solve of the seeded
+    wedge channel at the size given by --nx/--ny, plus the time of each
+    phase of one Newton step at 512 x 256 (Section 4 kernels, FP64)."""
+    import numpy as np
+    import torch
+
+    from paper_2505_10857_gb300 import inputs as I
+    from paper_2505_10857_gb300 import nswe
+
+    ctx = nswe.Context(0)
+    stream = torch.cuda.current_stream()
+
+    def timed(f, reps):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            f()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    big = I.wedge_channel(0)
+    pb = nswe.Problem2D.from_inputs(ctx, big)
+    n = big.Nx * big.Ny
+    X, _ = big.centres(0)
+    s0 = big.bc_state[0]
+    U = torch.tensor(np.stack([s0[0] * (1 + 0.01 * np.sin(X.ravel())), np.full(n, s0[1]), np.full(n, s0[2])]),
+                     dtype=torch.float64, device="cuda")
+    R, res = torch.zeros_like(U), torch.zeros(1, dtype=torch.float64, device="cuda")
+    J9 = torch.zeros((9, 9, n), dtype=torch.float64, device="cuda")
+    J21 = torch.zeros((21, 9, n), dtype=torch.float64, device="cuda")
+    dU = torch.zeros_like(U)
+    prm = nswe.params(96, big.levels, omega=args.omega2d, nu1=20, nu2=20, nu3=3)
+    kern = {"residual_ms": timed(lambda: nswe.nswe_residual(ctx, pb, 0, U, R, res), 10),
+            "jacobian_j9_ms": timed(lambda: nswe.nswe_jacobian_simplified(ctx, pb, 0, U, 1e-6, 3.0, R, J9, res), 3),
+            "jacobian_j21_ms": timed(lambda: nswe.nswe_jacobian_full(ctx, pb, 0, U, 1e-6, 3.0, R, J21, res), 2),
+            "vcycle_j9_nu20_ms": timed(lambda: nswe.nswe_mg_vcycle(ctx, pb, 0, 9, J9, R, dU, prm), 2),
+            "grid": "512x256, 7 levels"}
+    w = I.wedge(args.nx, args.ny, args.levels2d, x1=40.0, y1=30.0, x_wall=8.0, theta_deg=big.meta["theta_deg"])
+    pw = nswe.Problem2D.from_inputs(ctx, w)
+    p2 = nswe.params2d_from(I.Params2D(levels=args.levels2d, nu1=[20], nu2=[20], omega=args.omega2d, tol=TOL,
+                                       n_max=3000))
+    U0 = torch.from_numpy(w.U0_start).cuda()
+    Uo = torch.zeros((3, args.nx * args.ny), dtype=torch.float64, device="cuda")
+    times, info = [], None
+    for s in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = nswe.nswe_newton_solve(ctx, pw, U0, Uo, p2)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1000.0 * statistics.mean(times)
+    print(json.dumps({
+        "metric": METRIC, "value": 1000.0 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2D wedge channel {args.nx}x{args.ny} on [0,40]x[0,30], J9, {args.levels2d} levels, "
+                               f"omega {args.omega2d}, nu 20, nu3 3, eps 1e-6",
+                   "theta_deg": big.meta["theta_deg"]},
+        "converged": {"status": info["status"], "iters": info["iters"][:args.levels2d], "res": info["res"][0]},
+        "kernels_512x256": kern}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,7 +474,17 @@ def main():
     ap.add_argument("--batch", type=int, default=608, help="instances per GPU per step")
     ap.add_argument("--nb", type=int, default=3, choices=[3, 5], help="3: simplified J3, 5: full J5")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d"])
+    ap.add_argument("--nx", type=int, default=128)
+    ap.add_argument("--ny", type=int, default=64)
+    ap.add_argument("--levels2d", type=int, default=5)
+    ap.add_argument("--omega2d", type=float, default=0.01)
     args = ap.parse_args()
+    if args.workload == "wedge2d":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        run_wedge2d(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

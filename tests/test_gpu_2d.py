@@ -144,3 +144,41 @@ def test_newton_solve_parity_2d(nswe, ctx, orc, case):
     assert np.abs(got - Uref).max() <= 1e-10 * np.abs(Uref).max(), np.abs(got - Uref).max()
     for l in range(inp.levels):
         assert abs(info["iters"][l] - iref["iters"][l]) <= 2, (info["iters"], iref["iters"])
+
+
+def test_full_size_residual_and_jacobian_sampled(nswe, ctx, orc):
+    """At the benchmark size (512 x 256 wedge channel) the GPU residual and J9
+    blocks match the oracle on sampled cells (boundary cells included); the
+    oracle evaluates each sampled cell on its own."""
+    inp = I.wedge_channel(0)
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    pr = orc.problem_levels2d(inp)[0]
+    n = inp.Nx * inp.Ny
+    U = state_for(inp, 0, 40)
+    dU = dev(U)
+    dR = torch.zeros_like(dU)
+    dJ = torch.zeros((9, 9, n), dtype=torch.float64, device="cuda")
+    eps = 1e-6
+    nswe.nswe_jacobian_simplified(ctx, prob, 0, dU, eps, 3.0, dR, dJ)
+    R, J = host(dR), host(dJ)
+    rng = np.random.default_rng(41)
+    cells = list(rng.integers(0, n, 24)) + [0, inp.Nx - 1, n - 1, n - inp.Nx, 5 * inp.Nx + 1, 2 * inp.Nx - 2]
+    sc = flux_scale2(U, inp.g, min(pr.s.dx, pr.s.dy))
+    off = orc.stencil2d(orc.ST_J9)
+    for c in cells:
+        i, j = int(c) % inp.Nx, int(c) // inp.Nx
+        r0 = orc.residual_cell2d(pr, U, i, j)
+        assert np.abs(R[:, c] - r0).max() <= 1e-12 * sc
+        for k in (0, 3, 4, 6):  # (0,-2), (-1,0), centre, (2,0)
+            p, q = i + off[k][0], j + off[k][1]
+            if not (0 <= p < inp.Nx and 0 <= q < inp.Ny):
+                assert np.all(J[k, :, c] == 0.0)
+                continue
+            for m in range(3):
+                Up = U.copy()
+                Up[m, q * inp.Nx + p] += eps
+                col = (orc.residual_cell2d(pr, Up, i, j) - r0) / eps
+                if k == 4:
+                    col[m] += 3.0 * np.abs(r0).sum()
+                for l in range(3):
+                    assert abs(J[k, l * 3 + m, c] - col[l]) <= 1e-12 * abs(col[l]) + 8 * EPS64 * sc / eps
