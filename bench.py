@@ -37,11 +37,15 @@ if ROOT not in sys.path:
 METRIC = "steady solves/s and p99 latency at residual <=1e-10 vs plain FP64 Newton-MG"
 UNIT = "solves/s"
 TOL = 1e-10
+MIXED_BOUND = 1e-8  # solution distance of two solves that both reach res < TOL by different paths
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x FP64 FMA/clk/SM x 2 flop x max SM GHz
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM GHz
 
 
-def workload_config(batch, nb):
-    return {"workload": "1D irregular channel, N=4096, 8-level MG, J%d, FP64, subcritical" % nb,
+def workload_config(batch, nb, precision="fp64"):
+    prec = "FP64" if precision == "fp64" else "mixed FP64 residual/update + FP32 Jacobian/MG"
+    return {"workload": "1D irregular channel, N=4096, 8-level MG, J%d, %s, subcritical" % (nb, prec),
+            "precision": precision,
             "N": 4096, "levels": 8, "nest_start_cells": 256, "instances_per_step_per_gpu": batch,
             "jacobian": "J3 (simplified)" if nb == 3 else "J5 (full)", "tol": TOL,
             "l2": "inputs + workspace per step (%.0f MB) exceed the 129 MB L2" % (batch * 2.4),
@@ -65,6 +69,13 @@ F_SOURCE = 36        # two-point Gauss source of one cell (Eq. 9)
 F_UPDATE = 4         # damped Newton update of H and Q
 F_DINV = 9           # 2x2 inverse
 F_INTERP = 8         # App. A per fine cell
+
+
+def f_res():
+    """Residual alone per cell (Eq. 10): WENO of both components of the
+    cells j-1, j, j+1, two faces of 1 reciprocal + 2 states + HLL, the
+    source and the differences."""
+    return 6 * F_WENO + 2 * (1 + 2 * F_STATE + F_HLL) + F_SOURCE + 4
 
 
 def f_res_jac(nb):
@@ -101,34 +112,40 @@ def lu_flops(n, kl):
     return n * (kl + 1 + 4 * kl * kl), n * (6 * kl + 1)  # factor, solve
 
 
-def solve_flops(N, levels, start, iters, nb, nu1, nu2, nu3):
+def solve_flops(N, levels, start, iters, nb, nu1, nu2, nu3, mixed=False):
+    """(FP64 flops, FP32 flops) of one nested solve. FP64 path: R and J
+    together at each state. Mixed path: the FP64 residual at each state, the
+    FP32 Jacobian (which also forms R) and linear solve at each step."""
     L = levels - 1
-    tot = 0.0
+    f64 = f32 = 0.0
     for l in range(start, -1, -1):
         Nl = N >> l
         if l < start:
-            tot += F_INTERP * Nl
-        tot += f_res_jac(nb) * Nl  # R, J of the level's initial state
-        per = Nl * (f_res_jac(nb) + F_UPDATE)
+            f64 += F_INTERP * Nl
+        lin = 0.0
         nbl = [nb if k == l else 3 for k in range(L + 1)]
         for k in range(l + 1, L + 1):
-            per += 8 * nbl[k - 1] * (N >> k)
+            lin += 8 * nbl[k - 1] * (N >> k)
         for k in range(l, L):
-            per += F_DINV * (N >> k)
+            lin += F_DINV * (N >> k)
         hw = (nbl[L] - 1) // 2
         fac, sol = lu_flops(2 * (N >> L), 2 * hw + 1)
-        per += fac
+        lin += fac
         if l == L:
-            per += sol
+            lin += sol
         else:
             vc = sol
             for k in range(l, L):
                 Nk = N >> k
                 vc += f_smooth(Nk, nbl[k], nu1) + f_smooth(Nk, nbl[k], nu2) + (N >> (k + 1)) * f_restrict(nbl[k]) \
                     + 2 * Nk
-            per += nu3 * vc
-        tot += iters[l] * per
-    return tot
+            lin += nu3 * vc
+        if mixed:
+            f64 += f_res() * Nl + iters[l] * Nl * (f_res() + F_UPDATE)
+            f32 += iters[l] * (Nl * (f_res_jac(nb) + 1) + lin)
+        else:
+            f64 += f_res_jac(nb) * Nl + iters[l] * (Nl * (f_res_jac(nb) + F_UPDATE) + lin)
+    return f64, f32
 
 
 # ------------------------------------------------------------------------------------------------
@@ -253,9 +270,11 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     B, nb = args.batch, args.nb
+    mixed = args.precision == "mixed"
     first = rank * B
     inps, prms = make_instances(first, B, nb)
     prm = nswe.params_from(prms[0])
+    prm.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
     for q in prms[1:]:
         assert list(q.eps) == list(prms[0].eps) and q.omega == prms[0].omega
 
@@ -310,9 +329,13 @@ def run_gpu(args, rank, world, local_rank):
     def pct(a, p):
         return a[min(len(a) - 1, int(math.ceil(p / 100.0 * len(a))) - 1)]
 
-    flops = sum(solve_flops(4096, 8, inps[k].start_level, infos[k]["iters"], nb, prm.nu1, prm.nu2, prm.nu3)
-                for k in range(B))
+    fl = [solve_flops(4096, 8, inps[k].start_level, infos[k]["iters"], nb, prm.nu1, prm.nu2, prm.nu3, mixed)
+          for k in range(B)]
+    f64, f32 = sum(a for a, _ in fl), sum(b for _, b in fl)
     launch_ms = statistics.mean(per_launch)
+    # FP64-equivalent rate: FP32 flops weighted by the FP64:FP32 peak ratio, so
+    # that achieved / FP64 peak is the fraction of the time at both peaks.
+    flops = f64 + f32 * FP64_PEAK_GFLOPS / FP32_PEAK_GFLOPS
     achieved = flops / (launch_ms / 1000.0) / 1e12
 
     # ---- single-solve latency (one instance alone on the GPU)
@@ -369,12 +392,12 @@ def run_gpu(args, rank, world, local_rank):
                    "sample": f"first {n} instances of the step, one solve per process (spawn pool), "
                              f"{wall:.1f} s wall"}
             errs = [float(np.abs(Us[k].cpu().numpy() - refs[k]).max() / np.abs(refs[k]).max()) for k in range(n)]
-            parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "bound": 1e-10}
+            parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "bound": MIXED_BOUND if mixed else 1e-10}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(B, nb),
+            "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
+            "config": workload_config(B, nb, args.precision),
             "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
                            "what": "per-solve completion time from the start of its batch (device timer)",
                            "solve_p50": pct(dur, 50), "solve_p99": pct(dur, 99),
@@ -387,8 +410,10 @@ def run_gpu(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1000.0,
                          "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1000.0), "traffic": None,
                          "kernel": "k_solve (persistent nested NMGM, one block per instance)",
-                         "flops_per_launch": flops, "launch_ms": launch_ms,
-                         "peak_note": "FP64 derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"},
+                         "flops_per_launch": flops, "fp64_flops": f64, "fp32_flops": f32, "launch_ms": launch_ms,
+                         "peak_note": "FP64 derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"
+                                      + ("; FP32 flops counted at FP64/FP32 peak ratio (FP32 peak 152 x 128 lanes x "
+                                         "2 x 2.07 GHz)" if mixed else "")},
             "clocks": clk,
         }
         if cpu:
@@ -474,6 +499,8 @@ def main():
     ap.add_argument("--batch", type=int, default=608, help="instances per GPU per step")
     ap.add_argument("--nb", type=int, default=3, choices=[3, 5], help="3: simplified J3, 5: full J5")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d"])
     ap.add_argument("--nx", type=int, default=128)
     ap.add_argument("--ny", type=int, default=64)

@@ -84,6 +84,16 @@ typedef struct {
 #define NSWE_JAC_SIMPLIFIED 3 /* 1D J3: block tridiagonal (Section 3.3); 2D J9 */
 #define NSWE_JAC_FULL 5       /* 1D J5: block pentadiagonal; 2D J21          */
 
+/* Arithmetic of a Newton step. The paper computes in double precision
+ * (NSWE_PREC_FP64). NSWE_PREC_MIXED is this library's addition, for 1D
+ * problems: the residual (Eq. 10), res, the stopping test and the update
+ * (Eq. 14) stay FP64, while the FD Jacobian (Eq. 12-13), the coarse
+ * operators, the smoother and the coarsest LU run in FP32. The Jacobian is an
+ * approximation of the true derivative either way, so the Newton fixed point
+ * R(U) = 0 is the FP64 one; only the convergence path changes. */
+#define NSWE_PREC_FP64 0
+#define NSWE_PREC_MIXED 1
+
 /* Solver parameters (Section 5). nswe_params_default fills the paper's 1D
  * values: alpha 3, tau 0.6, omega 1, nu1 = nu2 = nu3 = 2, tol 1e-11. */
 typedef struct {
@@ -96,6 +106,7 @@ typedef struct {
   int n_max;      /* Newton iteration cap per nested level                  */
   int jacobian;   /* NSWE_JAC_SIMPLIFIED (J3) or NSWE_JAC_FULL (J5)         */
   int nest_start; /* nested level the solve starts on; <0: coarsest (Alg. 3)*/
+  int precision;  /* NSWE_PREC_FP64 or NSWE_PREC_MIXED (1D problems only)   */
   double eps[NSWE_MAX_LEVELS]; /* FD perturbation per nested level, Eq. 12  */
 } nswe_params;
 
@@ -202,6 +213,17 @@ nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level,
                                const double *U, double eps, double alpha,
                                double *R, double *J, double *res_l1);
 
+/* The Jacobian of a NSWE_PREC_MIXED Newton step (1D problems only): R and
+ * res_l1 as in nswe_residual (FP64); J the Jacobian of Eq. 12-13 with the
+ * perturbed residuals evaluated in FP32 from the FP64 state, and the
+ * regularization alpha*||R_j||_1 taken from the FP64 R.
+ *   nb = 3 (J3) or 5 (J5); U[2][N_l] (double) in; R[2][N_l] (double) out;
+ *   J[nb][4][N_l] (float) out; res_l1 (device scalar, may be NULL) out.
+ *   2D problems return NSWE_EINVAL. */
+nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb,
+                              const double *U, double eps, double alpha,
+                              double *R, float *J, double *res_l1);
+
 /* One multigrid V-cycle (Algorithm 2) for J dU = -R on nested level `level`
  * with the hierarchy level..levels-1: Galerkin coarse operators (Eq. 17),
  * nu1/nu2 symmetric multicolour block-SOR steps (Eq. 19; colours j mod C,
@@ -212,6 +234,14 @@ nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level,
 nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb,
                            const double *J, const double *R, double *dU,
                            const nswe_params *params);
+
+/* nswe_mg_vcycle in FP32, the linear solve of a NSWE_PREC_MIXED step (1D
+ * problems only; 2D returns NSWE_EINVAL): J[nb][4][N_l], R[2][N_l] (float)
+ * in; dU[2][N_l] (float) in/out. The coarse levels reuse the problem's
+ * workspace, which this call overwrites. */
+nswe_status nswe_mg_vcycle_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb,
+                               const float *J, const float *R, float *dU,
+                               const nswe_params *params);
 
 /* Nested NMGM (Algorithm 3). Starts on level s = params->nest_start (or the
  * coarsest): Newton iterations with a direct solve on the coarsest level,

@@ -71,6 +71,8 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
       p->nu3 > 1000)
     return NSWE_EINVAL;
   if (p->jacobian != NSWE_JAC_SIMPLIFIED && p->jacobian != NSWE_JAC_FULL) return NSWE_EINVAL;
+  if (p->precision != NSWE_PREC_FP64 && p->precision != NSWE_PREC_MIXED) return NSWE_EINVAL;
+  if (pr && pr->dim == 2 && p->precision != NSWE_PREC_FP64) return NSWE_EINVAL;
   if (pr) {
     for (int l = 0; l <= first_level && l < pr->levels; ++l)
       if (!(p->eps[l] > 0.0) || !std::isfinite(p->eps[l])) return NSWE_EINVAL;
@@ -618,6 +620,34 @@ nswe_status nswe_jacobian_simplified(nswe_ctx ctx, nswe_prob prob, int level, co
 nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level, const double *U, double eps,
                                double alpha, double *R, double *J, double *res_l1) {
   return jacobian_common(ctx, prob, level, 5, U, eps, alpha, R, J, res_l1);
+}
+
+nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *U, double eps,
+                              double alpha, double *R, float *J, double *res_l1) {
+  if (!ctx || !prob || prob->ctx != ctx || !U || !R || !J || level < 0 || level >= prob->levels) return NSWE_EINVAL;
+  if (prob->dim != 1 || (nb != 3 && nb != 5)) return NSWE_EINVAL;
+  if (!(eps > 0.0) || !std::isfinite(eps) || !(alpha >= 0.0) || !std::isfinite(alpha)) return NSWE_EINVAL;
+  DeviceGuard dg(ctx->device);
+  const int N = prob->N >> level;
+  return launch_jacobian_f32(prob->dev, level, N, nb, U, eps, alpha, R, J, res_l1, ctx->partials, ctx->stream) ==
+                 cudaSuccess
+             ? NSWE_OK
+             : NSWE_ECUDA;
+}
+
+nswe_status nswe_mg_vcycle_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, const float *J, const float *R,
+                               float *dU, const nswe_params *params) {
+  if (!ctx || !prob || prob->ctx != ctx || !J || !R || !dU || level < 0 || level >= prob->levels) return NSWE_EINVAL;
+  if (prob->dim != 1 || (nb != 3 && nb != 5)) return NSWE_EINVAL;
+  nswe_status st = check_params(params, nullptr, 0);
+  if (st != NSWE_OK) return st;
+  DeviceGuard dg(ctx->device);
+  const int coarse = prob->N >> (prob->levels - 1);
+  const int coarse_nb = (level == prob->levels - 1) ? nb : 3;
+  return launch_vcycle_f32(prob->dev, level, nb, J, R, dU, *params, ctx->status, coarse, coarse_nb, ctx->stream) ==
+                 cudaSuccess
+             ? NSWE_OK
+             : NSWE_ECUDA;
 }
 
 nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *J, const double *R,

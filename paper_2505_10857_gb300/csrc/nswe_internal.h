@@ -100,10 +100,17 @@ cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U,
 cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
                             double alpha, double *R, double *J, double *res, double *partials,
                             cudaStream_t s);
+// FP64 residual (R, res) then the FP32 Jacobian regularised with that R.
+cudaError_t launch_jacobian_f32(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
+                                double alpha, double *R, float *J, double *res, double *partials,
+                                cudaStream_t s);
 // coarse_cells: cells of the coarsest level; coarse_nb: its block band (3 or 5).
 cudaError_t launch_vcycle(const ProbDev *p, int level, int nb, const double *J, const double *R, double *dU,
                           const nswe_params &prm, int *status, int coarse_cells, int coarse_nb, cudaStream_t s);
-// max_coarse_cells: largest coarsest level over the tasks.
+cudaError_t launch_vcycle_f32(const ProbDev *p, int level, int nb, const float *J, const float *R, float *dU,
+                              const nswe_params &prm, int *status, int coarse_cells, int coarse_nb, cudaStream_t s);
+// max_coarse_cells: largest coarsest level over the tasks; prm.precision
+// selects the FP64 or the mixed-precision solve kernel.
 cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                          cudaStream_t s);
 

@@ -10,6 +10,7 @@
 // round trip. Problem data and workspace stay in device memory (L2 resident
 // for the 1D sizes); the coarsest factorisation lives in shared memory.
 #include <cmath>
+#include <type_traits>
 
 #include "nswe_internal.h"
 
@@ -74,16 +75,17 @@ __device__ __forceinline__ void ghost(int kind, double bh, double bq, double sb,
 // U^-_{k+1/2}. With s_r = (zeta + beta_r)^2 the normalised weights are
 // w0 = s1/(s1 + 2 s0), w1 = 2 s0/(s1 + 2 s0) and v0 = 2 s1/(2 s1 + s0),
 // v1 = s0/(2 s1 + s0); both quotients share one reciprocal.
-__device__ __forceinline__ void weno3(double a, double b, double c, double &up, double &um) {
-  double d0 = c - b, d1 = b - a;
-  double e0 = kZeta + d0 * d0, e1 = kZeta + d1 * d1;
-  double s0 = e0 * e0, s1 = e1 * e1;
-  double p0 = 1.5 * b - 0.5 * c, p1 = 0.5 * a + 0.5 * b;   // U^(0), U^(1) at k-1/2
-  double q0 = 0.5 * b + 0.5 * c, q1 = -0.5 * a + 1.5 * b;  // U^(0), U^(1) at k+1/2
-  double D1 = s1 + 2.0 * s0, D2 = 2.0 * s1 + s0;
-  double inv = 1.0 / (D1 * D2);
-  up = (s1 * p0 + 2.0 * s0 * p1) * (D2 * inv);
-  um = (2.0 * s1 * q0 + s0 * q1) * (D1 * inv);
+template <typename T>
+__device__ __forceinline__ void weno3(T a, T b, T c, T &up, T &um) {
+  T d0 = c - b, d1 = b - a;
+  T e0 = T(kZeta) + d0 * d0, e1 = T(kZeta) + d1 * d1;
+  T s0 = e0 * e0, s1 = e1 * e1;
+  T p0 = T(1.5) * b - T(0.5) * c, p1 = T(0.5) * a + T(0.5) * b;   // U^(0), U^(1) at k-1/2
+  T q0 = T(0.5) * b + T(0.5) * c, q1 = T(-0.5) * a + T(1.5) * b;  // U^(0), U^(1) at k+1/2
+  T D1 = s1 + T(2.0) * s0, D2 = T(2.0) * s1 + s0;
+  T inv = T(1.0) / (D1 * D2);
+  up = (s1 * p0 + T(2.0) * s0 * p1) * (D2 * inv);
+  um = (T(2.0) * s1 * q0 + s0 * q1) * (D1 * inv);
 }
 
 // HLL flux at a face of width sig: S_L = min(u_L - c_L, u_R - c_R),
@@ -114,34 +116,37 @@ __device__ __forceinline__ void hll(double HL, double QL, double HR, double QR, 
 }
 
 // Quantities of one interface state at a face of width 1/isg entering HLL.
+template <typename T>
 struct FState {
-  double H, Q, u, c, F1;
+  T H, Q, u, c, F1;
 };
 
-__device__ __forceinline__ FState fstate(double H, double Q, double isg, double g) {
-  FState s;
+template <typename T>
+__device__ __forceinline__ FState<T> fstate(T H, T Q, T isg, T g) {
+  FState<T> s;
   s.H = H;
   s.Q = Q;
-  double iH = 1.0 / H;
+  T iH = T(1.0) / H;
   s.u = Q * iH;
-  double h = H * isg;
+  T h = H * isg;
   s.c = sqrt(g * h);
-  s.F1 = Q * s.u + 0.5 * g * H * h;
+  s.F1 = Q * s.u + T(0.5) * g * H * h;
   return s;
 }
 
 // HLL combination of two interface states (same formula as hll()).
-__device__ __forceinline__ void hll_states(const FState &L, const FState &R, double &F0, double &F1) {
-  double SL = fmin(L.u - L.c, R.u - R.c);
-  double SR = fmax(L.u + L.c, R.u + R.c);
-  if (SL >= 0.0) {
+template <typename T>
+__device__ __forceinline__ void hll_states(const FState<T> &L, const FState<T> &R, T &F0, T &F1) {
+  T SL = fmin(L.u - L.c, R.u - R.c);
+  T SR = fmax(L.u + L.c, R.u + R.c);
+  if (SL >= T(0.0)) {
     F0 = L.Q;
     F1 = L.F1;
-  } else if (SR <= 0.0) {
+  } else if (SR <= T(0.0)) {
     F0 = R.Q;
     F1 = R.F1;
   } else {
-    double iw = 1.0 / (SR - SL);
+    T iw = T(1.0) / (SR - SL);
     F0 = (SR * L.Q - SL * R.Q + SL * SR * (R.H - L.H)) * iw;
     F1 = (SR * L.F1 - SL * R.F1 + SL * SR * (R.Q - L.Q)) * iw;
   }
@@ -193,18 +198,20 @@ __device__ __forceinline__ void fill_ghosts(const Geo &G, int j, Win &w) {
 // Two-point Gauss source of cell j (Eq. 9): S = (dx/2) sum_q [g h^2 sigma_x/2
 // - g sigma h b_x] at the Gauss points, h = H_h/sigma, H_h the cubic through
 // the interface values p0..p3 of H at t = -3/2, -1/2, 1/2, 3/2.
-__device__ __forceinline__ double source_at(const Geo &G, int j, double p0, double p1, double p2, double p3) {
-  double S = 0.0;
+template <typename T>
+__device__ __forceinline__ T source_at(const Geo &G, int j, T p0, T p1, T p2, T p3) {
+  T S = T(0.0);
+  const T g = T(G.g);
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    double Hh = kLag[q][0] * p0 + kLag[q][1] * p1 + kLag[q][2] * p2 + kLag[q][3] * p3;
-    double sig = G.gq[(0 * 2 + q) * G.N + j];
-    double sigx = G.gq[(1 * 2 + q) * G.N + j];
-    double bx = G.gq[(2 * 2 + q) * G.N + j];
-    double h = Hh / sig;
-    S += 0.5 * G.g * h * h * sigx - G.g * sig * h * bx;
+    T Hh = T(kLag[q][0]) * p0 + T(kLag[q][1]) * p1 + T(kLag[q][2]) * p2 + T(kLag[q][3]) * p3;
+    T sig = T(G.gq[(0 * 2 + q) * G.N + j]);
+    T sigx = T(G.gq[(1 * 2 + q) * G.N + j]);
+    T bx = T(G.gq[(2 * 2 + q) * G.N + j]);
+    T h = Hh / sig;
+    S += T(0.5) * g * h * h * sigx - g * sig * h * bx;
   }
-  return S * (0.5 * G.dx);
+  return S * (T(0.5) * T(G.dx));
 }
 
 // Local residual R_j (Eq. 10) from a filled window.
@@ -276,31 +283,34 @@ __device__ double residual_cells(const Geo &G, const double *U, double *R, int f
 // Each perturbed R_j is the same arithmetic on the same values as a full
 // re-evaluation of the local residual, at a fraction of the cost.
 
+template <typename T>
 struct JW {
-  double *rec;  // [2 comps][4 variants][2: up, um][N+2], cell k at k+1
-  double *flx;  // [9 variants][2 comps][N+1]
+  T *rec;  // [2 comps][4 variants][2: up, um][N+2], cell k at k+1
+  T *flx;  // [9 variants][2 comps][N+1]
   int N;
-  __device__ __forceinline__ double &r(int m, int v, int o, int k) const {
+  __device__ __forceinline__ T &r(int m, int v, int o, int k) const {
     return rec[((m * 4 + v) * 2 + o) * (N + 2) + (k + 1)];
   }
-  __device__ __forceinline__ double &f(int w, int l, int face) const { return flx[(w * 2 + l) * (N + 1) + face]; }
+  __device__ __forceinline__ T &f(int w, int l, int face) const { return flx[(w * 2 + l) * (N + 1) + face]; }
 };
 
-__device__ __forceinline__ JW jw_view(double *base, int N) {
-  JW W;
-  W.rec = base;
-  W.flx = base + 16 * (size_t)(N + 2);
+template <typename T>
+__device__ __forceinline__ JW<T> jw_view(double *base, int N) {
+  JW<T> W;
+  W.rec = reinterpret_cast<T *>(base);
+  W.flx = W.rec + 16 * (size_t)(N + 2);
   W.N = N;
   return W;
 }
 
 // Component m of cell kk (ghosts included) of the state with interior cell
 // ip perturbed by eps in component m (ip = -1: no perturbation).
-__device__ __forceinline__ double pval(const Geo &G, const double *U, int m, int kk, int ip, double eps) {
+template <typename T>
+__device__ __forceinline__ T pval(const Geo &G, const double *U, int m, int kk, int ip, double eps) {
   const int N = G.N;
   if (kk >= 0 && kk < N) {
-    double x = U[m * N + kk];
-    return kk == ip ? x + eps : x;
+    T x = T(U[m * N + kk]);
+    return kk == ip ? x + T(eps) : x;
   }
   const int e = kk < 0 ? 0 : N - 1;
   double He = U[e], Qe = U[N + e];
@@ -311,11 +321,12 @@ __device__ __forceinline__ double pval(const Geo &G, const double *U, int m, int
   double Hg, Qg;
   if (kk < 0) ghost(G.bl, G.blh, G.blq, G.sf[0], He, Qe, Hg, Qg);
   else ghost(G.br, G.brh, G.brq, G.sf[N], He, Qe, Hg, Qg);
-  return m == 0 ? Hg : Qg;
+  return T(m == 0 ? Hg : Qg);
 }
 
 // Pass A. Variant v = 0: base; v = 1, 2, 3: cell k + v - 2 perturbed.
-__device__ void jac_pass_a(const Geo &G, const double *U, double eps, const JW &W, int first, int stride) {
+template <typename T>
+__device__ void jac_pass_a(const Geo &G, const double *U, double eps, const JW<T> &W, int first, int stride) {
   const int N = G.N, items = (N + 2) * 8;
   for (int it = first; it < items; it += stride) {
     const int k = it % (N + 2) - 1, mv = it / (N + 2), m = mv >> 2, v = mv & 3;
@@ -324,8 +335,8 @@ __device__ void jac_pass_a(const Geo &G, const double *U, double eps, const JW &
       ip = k + v - 2;
       if (ip < 0 || ip >= N) continue;
     }
-    double up, um;
-    weno3(pval(G, U, m, k - 1, ip, eps), pval(G, U, m, k, ip, eps), pval(G, U, m, k + 1, ip, eps), up, um);
+    T up, um;
+    weno3<T>(pval<T>(G, U, m, k - 1, ip, eps), pval<T>(G, U, m, k, ip, eps), pval<T>(G, U, m, k + 1, ip, eps), up, um);
     W.r(m, v, 0, k) = up;
     W.r(m, v, 1, k) = um;
   }
@@ -342,13 +353,15 @@ __device__ __forceinline__ int rec_variant(int i, int kk) {
 // (perturbed for p = 0, 1, 2), the right state from cell f (p = 1, 2, 3);
 // the per-state HLL quantities of the base states serve all variants that do
 // not perturb that side.
-__device__ void jac_pass_b(const Geo &G, const JW &W, int first, int stride) {
+template <typename T>
+__device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) {
   const int N = G.N;
+  const T g = T(G.g);
   for (int f = first; f <= N; f += stride) {
-    const double isg = 1.0 / G.sf[f];
-    const FState Lb = fstate(W.r(0, 0, 1, f - 1), W.r(1, 0, 1, f - 1), isg, G.g);
-    const FState Rb = fstate(W.r(0, 0, 0, f), W.r(1, 0, 0, f), isg, G.g);
-    double F0, F1;
+    const T isg = T(1.0) / T(G.sf[f]);
+    const FState<T> Lb = fstate<T>(W.r(0, 0, 1, f - 1), W.r(1, 0, 1, f - 1), isg, g);
+    const FState<T> Rb = fstate<T>(W.r(0, 0, 0, f), W.r(1, 0, 0, f), isg, g);
+    T F0, F1;
     hll_states(Lb, Rb, F0, F1);
     W.f(0, 0, f) = F0;
     W.f(0, 1, f) = F1;
@@ -358,10 +371,10 @@ __device__ void jac_pass_b(const Geo &G, const JW &W, int first, int stride) {
       if (i < 0 || i >= N) continue;
 #pragma unroll
       for (int m = 0; m < 2; ++m) {
-        FState Ls = Lb, Rs = Rb;
+        FState<T> Ls = Lb, Rs = Rb;
         if (p <= 2)
-          Ls = fstate(W.r(0, m == 0 ? p + 1 : 0, 1, f - 1), W.r(1, m == 1 ? p + 1 : 0, 1, f - 1), isg, G.g);
-        if (p >= 1) Rs = fstate(W.r(0, m == 0 ? p : 0, 0, f), W.r(1, m == 1 ? p : 0, 0, f), isg, G.g);
+          Ls = fstate<T>(W.r(0, m == 0 ? p + 1 : 0, 1, f - 1), W.r(1, m == 1 ? p + 1 : 0, 1, f - 1), isg, g);
+        if (p >= 1) Rs = fstate<T>(W.r(0, m == 0 ? p : 0, 0, f), W.r(1, m == 1 ? p : 0, 0, f), isg, g);
         hll_states(Ls, Rs, F0, F1);
         const int w = 1 + 2 * p + m;
         W.f(w, 0, f) = F0;
@@ -377,40 +390,44 @@ __device__ __forceinline__ int flux_variant(int i, int m, int face) {
   return (p >= 0 && p <= 3) ? 1 + 2 * p + m : 0;
 }
 
-// Pass C over items (cell j, block k); writes R (from the k = hw items) and
-// J; returns the partial sum of ||R_j||_1 of the items it processed.
-__device__ double jac_pass_c(const Geo &G, int nb, double eps, double alpha, const JW &W, double *R, double *J,
-                             int first, int stride) {
+// Pass C over items (cell j, block k); writes J and, when Rout is given, R
+// (from the k = hw items). The regularisation uses Rreg when given (the FP64
+// residual of a mixed-precision step), else the pass's own base residual.
+// Returns the partial sum of ||R_j||_1 of the items that wrote R.
+template <typename T>
+__device__ double jac_pass_c(const Geo &G, int nb, double eps, double alpha, const JW<T> &W, const double *Rreg,
+                             double *Rout, T *J, int first, int stride) {
   const int N = G.N, hw = (nb - 1) / 2, items = N * nb;
   double acc = 0.0;
   for (int it = first; it < items; it += stride) {
     const int j = it % N, k = it / N, d = k - hw, i = j + d;
-    const double Sb = source_at(G, j, W.r(0, 0, 0, j - 1), W.r(0, 0, 0, j), W.r(0, 0, 1, j), W.r(0, 0, 1, j + 1));
-    const double R0 = W.f(0, 0, j + 1) - W.f(0, 0, j);
-    const double R1 = W.f(0, 1, j + 1) - W.f(0, 1, j) - Sb;
-    if (d == 0) {
-      R[j] = R0;
-      R[N + j] = R1;
-      acc += fabs(R0) + fabs(R1);
+    const T Sb = source_at<T>(G, j, W.r(0, 0, 0, j - 1), W.r(0, 0, 0, j), W.r(0, 0, 1, j), W.r(0, 0, 1, j + 1));
+    const T R0 = W.f(0, 0, j + 1) - W.f(0, 0, j);
+    const T R1 = W.f(0, 1, j + 1) - W.f(0, 1, j) - Sb;
+    if (d == 0 && Rout) {
+      Rout[j] = double(R0);
+      Rout[N + j] = double(R1);
+      acc += fabs(double(R0)) + fabs(double(R1));
     }
     if (i < 0 || i >= N) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) J[(k * 4 + e) * N + j] = 0.0;
+      for (int e = 0; e < 4; ++e) J[(k * 4 + e) * N + j] = T(0.0);
       continue;
     }
-    const double reg = (d == 0) ? alpha * (fabs(R0) + fabs(R1)) : 0.0;
-    const double ieps = 1.0 / eps;
+    T reg = T(0.0);
+    if (d == 0) reg = Rreg ? T(alpha * (fabs(Rreg[j]) + fabs(Rreg[N + j]))) : T(alpha) * (fabs(R0) + fabs(R1));
+    const T ieps = T(1.0) / T(eps);
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-      double S = Sb;
+      T S = Sb;
       if (m == 0) {
         const int v0 = rec_variant(i, j - 1), v1 = rec_variant(i, j), v2 = rec_variant(i, j + 1);
-        S = source_at(G, j, W.r(0, v0, 0, j - 1), W.r(0, v1, 0, j), W.r(0, v1, 1, j), W.r(0, v2, 1, j + 1));
+        S = source_at<T>(G, j, W.r(0, v0, 0, j - 1), W.r(0, v1, 0, j), W.r(0, v1, 1, j), W.r(0, v2, 1, j + 1));
       }
       const int wr = flux_variant(i, m, j + 1), wl = flux_variant(i, m, j);
-      const double P0 = W.f(wr, 0, j + 1) - W.f(wl, 0, j);
-      const double P1 = W.f(wr, 1, j + 1) - W.f(wl, 1, j) - S;
-      double v0 = (P0 - R0) * ieps, v1 = (P1 - R1) * ieps;
+      const T P0 = W.f(wr, 0, j + 1) - W.f(wl, 0, j);
+      const T P1 = W.f(wr, 1, j + 1) - W.f(wl, 1, j) - S;
+      T v0 = (P0 - R0) * ieps, v1 = (P1 - R1) * ieps;
       if (m == 0) v0 += reg;
       else v1 += reg;
       J[(k * 4 + 0 * 2 + m) * N + j] = v0;
@@ -421,12 +438,13 @@ __device__ double jac_pass_c(const Geo &G, int nb, double eps, double alpha, con
 }
 
 // Inverse of the diagonal 2x2 blocks.
-__device__ void dinv_cells(int N, int nb, const double *J, double *Dinv, int first, int stride) {
+template <typename T>
+__device__ void dinv_cells(int N, int nb, const T *J, T *Dinv, int first, int stride) {
   const int hw = (nb - 1) / 2;
   for (int j = first; j < N; j += stride) {
-    double a = J[(hw * 4 + 0) * N + j], b = J[(hw * 4 + 1) * N + j];
-    double c = J[(hw * 4 + 2) * N + j], d = J[(hw * 4 + 3) * N + j];
-    double det = a * d - b * c;
+    T a = J[(hw * 4 + 0) * N + j], b = J[(hw * 4 + 1) * N + j];
+    T c = J[(hw * 4 + 2) * N + j], d = J[(hw * 4 + 3) * N + j];
+    T det = a * d - b * c;
     Dinv[0 * N + j] = d / det;
     Dinv[1 * N + j] = -b / det;
     Dinv[2 * N + j] = -c / det;
@@ -435,10 +453,11 @@ __device__ void dinv_cells(int N, int nb, const double *J, double *Dinv, int fir
 }
 
 // Galerkin coarse operator (Eq. 17): sums of fine blocks over aggregate pairs.
-__device__ void coarse_op_cells(int Nf, int nbf, const double *Jf, int Nc, double *Jc, int first, int stride) {
+template <typename T>
+__device__ void coarse_op_cells(int Nf, int nbf, const T *Jf, int Nc, T *Jc, int first, int stride) {
   const int hf = (nbf - 1) / 2;
   for (int j = first; j < Nc; j += stride) {
-    double a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};
+    T a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};
     for (int a = 0; a < 2; ++a) {
       int xi = 2 * j + a;
       if (xi >= Nf) break;
@@ -448,7 +467,7 @@ __device__ void coarse_op_cells(int Nf, int nbf, const double *Jf, int Nc, doubl
         int kc = eta / 2 - j + 1;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          double v = Jf[(k * 4 + e) * Nf + xi];
+          T v = Jf[(k * 4 + e) * Nf + xi];
           if (kc == 0) a0[e] += v;
           else if (kc == 1) a1[e] += v;
           else a2[e] += v;
@@ -469,24 +488,26 @@ __device__ void coarse_op_cells(int Nf, int nbf, const double *Jf, int Nc, doubl
 // repeated visit of the same colour sees the same neighbour values: the
 // correction t is computed once and the relaxation applied reps times, which
 // is exactly the sequence of reps separate passes.
-__device__ void sor_colour(int N, int nb, const double *J, const double *Dinv, const double *R, double *dU,
-                           double omega, int C, int col, int reps, int first, int stride) {
+template <typename T>
+__device__ void sor_colour(int N, int nb, const T *J, const T *Dinv, const T *R, T *dU, double omega_d, int C,
+                           int col, int reps, int first, int stride) {
+  const T omega = T(omega_d);
   const int hw = (nb - 1) / 2;
   for (int j = col + C * first; j < N; j += C * stride) {
-    double r0 = R[j], r1 = R[N + j];
+    T r0 = R[j], r1 = R[N + j];
     for (int k = 0; k < nb; ++k) {
       int i = j + k - hw;
       if (k == hw || i < 0 || i >= N) continue;
-      double x0 = dU[i], x1 = dU[N + i];
+      T x0 = dU[i], x1 = dU[N + i];
       r0 += J[(k * 4 + 0) * N + j] * x0 + J[(k * 4 + 1) * N + j] * x1;
       r1 += J[(k * 4 + 2) * N + j] * x0 + J[(k * 4 + 3) * N + j] * x1;
     }
-    double t0 = Dinv[0 * N + j] * r0 + Dinv[1 * N + j] * r1;
-    double t1 = Dinv[2 * N + j] * r0 + Dinv[3 * N + j] * r1;
-    double x0 = dU[j], x1 = dU[N + j];
+    T t0 = Dinv[0 * N + j] * r0 + Dinv[1 * N + j] * r1;
+    T t1 = Dinv[2 * N + j] * r0 + Dinv[3 * N + j] * r1;
+    T x0 = dU[j], x1 = dU[N + j];
     for (int r = 0; r < reps; ++r) {
-      x0 = (1.0 - omega) * x0 - omega * t0;
-      x1 = (1.0 - omega) * x1 - omega * t1;
+      x0 = (T(1.0) - omega) * x0 - omega * t0;
+      x1 = (T(1.0) - omega) * x1 - omega * t1;
     }
     dU[j] = x0;
     dU[N + j] = x1;
@@ -494,19 +515,20 @@ __device__ void sor_colour(int N, int nb, const double *J, const double *Dinv, c
 }
 
 // Defect restriction (Eq. 17) and zero coarse correction.
-__device__ void restrict_cells(int Nf, int nb, const double *J, const double *R, const double *dU, int Nc,
-                               double *Rc, double *dUc, int first, int stride) {
+template <typename T>
+__device__ void restrict_cells(int Nf, int nb, const T *J, const T *R, const T *dU, int Nc, T *Rc, T *dUc,
+                               int first, int stride) {
   const int hw = (nb - 1) / 2;
   for (int j = first; j < Nc; j += stride) {
-    double s0 = 0.0, s1 = 0.0;
+    T s0 = T(0.0), s1 = T(0.0);
     for (int a = 0; a < 2; ++a) {
       int xi = 2 * j + a;
       if (xi >= Nf) break;
-      double r0 = R[xi], r1 = R[Nf + xi];
+      T r0 = R[xi], r1 = R[Nf + xi];
       for (int k = 0; k < nb; ++k) {
         int eta = xi + k - hw;
         if (eta < 0 || eta >= Nf) continue;
-        double x0 = dU[eta], x1 = dU[Nf + eta];
+        T x0 = dU[eta], x1 = dU[Nf + eta];
         r0 += J[(k * 4 + 0) * Nf + xi] * x0 + J[(k * 4 + 1) * Nf + xi] * x1;
         r1 += J[(k * 4 + 2) * Nf + xi] * x0 + J[(k * 4 + 3) * Nf + xi] * x1;
       }
@@ -515,13 +537,14 @@ __device__ void restrict_cells(int Nf, int nb, const double *J, const double *R,
     }
     Rc[j] = s0;
     Rc[Nc + j] = s1;
-    dUc[j] = 0.0;
-    dUc[Nc + j] = 0.0;
+    dUc[j] = T(0.0);
+    dUc[Nc + j] = T(0.0);
   }
 }
 
 // Prolongation (Eq. 18).
-__device__ void prolong_cells(int Nf, double *dU, int Nc, const double *dUc, int first, int stride) {
+template <typename T>
+__device__ void prolong_cells(int Nf, T *dU, int Nc, const T *dUc, int first, int stride) {
   for (int xi = first; xi < Nf; xi += stride) {
     dU[xi] += dUc[xi / 2];
     dU[Nf + xi] += dUc[Nc + xi / 2];
@@ -565,28 +588,29 @@ __device__ void interp_cells(const Geo &Gc, const double *Uc, double *Uf, int fi
 // active rows in registers (a window of kl+1 rows), which keeps the latency
 // of every step to a few dependent FP64 operations.
 
+template <typename T>
 struct Band {
-  double *ab;    // [ldab][n]
+  T *ab;    // [ldab][n]
   int *piv;      // [n]
-  double *x;     // [n]
-  double *rinv;  // [n] reciprocals of the pivots
+  T *x;     // [n]
+  T *rinv;  // [n] reciprocals of the pivots
   int n, kl, ldab;
-  __device__ __forceinline__ double &A(int r, int c) const { return ab[(2 * kl + r - c) * n + c]; }
+  __device__ __forceinline__ T &A(int r, int c) const { return ab[(2 * kl + r - c) * n + c]; }
 };
 
-template <int KL>
-__device__ bool band_lu_serial(const Band &B) {
+template <int KL, typename T>
+__device__ bool band_lu_serial(const Band<T> &B) {
   constexpr int W = 2 * KL + 1;
   const int n = B.n;
-  double w[KL + 1][W];
+  T w[KL + 1][W];
 #pragma unroll
   for (int i = 0; i <= KL; ++i)
 #pragma unroll
-    for (int c = 0; c < W; ++c) w[i][c] = (i < n && c < n) ? B.A(i, c) : 0.0;
+    for (int c = 0; c < W; ++c) w[i][c] = (i < n && c < n) ? B.A(i, c) : T(0.0);
   bool sing = false;
   for (int k = 0; k < n; ++k) {
     int p = 0;
-    double best = fabs(w[0][0]);
+    T best = fabs(w[0][0]);
 #pragma unroll
     for (int i = 1; i <= KL; ++i)
       if (k + i < n && fabs(w[i][0]) > best) {
@@ -599,17 +623,17 @@ __device__ bool band_lu_serial(const Band &B) {
       if (p == i)
 #pragma unroll
         for (int c = 0; c < W; ++c) {
-          double t = w[0][c];
+          T t = w[0][c];
           w[0][c] = w[i][c];
           w[i][c] = t;
         }
-    const double d = w[0][0];
-    if (d == 0.0) sing = true;
-    B.rinv[k] = 1.0 / d;
+    const T d = w[0][0];
+    if (d == T(0.0)) sing = true;
+    B.rinv[k] = T(1.0) / d;
 #pragma unroll
     for (int i = 1; i <= KL; ++i)
       if (k + i < n) {
-        const double l = w[i][0] / d;
+        const T l = w[i][0] / d;
         B.A(k + i, k) = l;
 #pragma unroll
         for (int c = 1; c < W; ++c) w[i][c] -= l * w[0][c];
@@ -622,18 +646,19 @@ __device__ bool band_lu_serial(const Band &B) {
     for (int i = 0; i < KL; ++i) {
 #pragma unroll
       for (int c = 0; c < W - 1; ++c) w[i][c] = w[i + 1][c + 1];
-      w[i][W - 1] = 0.0;
+      w[i][W - 1] = T(0.0);
     }
     const int r = k + KL + 1;
 #pragma unroll
-    for (int c = 0; c < W; ++c) w[KL][c] = (r < n && k + 1 + c < n) ? B.A(r, k + 1 + c) : 0.0;
+    for (int c = 0; c < W; ++c) w[KL][c] = (r < n && k + 1 + c < n) ? B.A(r, k + 1 + c) : T(0.0);
   }
   return sing;
 }
 
 // The same factorisation working on the band storage in place (any kl); used
 // for the 5-block Jacobian of a direct solve on the coarsest nested level.
-__device__ bool band_lu_serial_smem(const Band &B) {
+template <typename T>
+__device__ bool band_lu_serial_smem(const Band<T> &B) {
   const int n = B.n, kl = B.kl;
   bool sing = false;
   for (int k = 0; k < n; ++k) {
@@ -644,15 +669,15 @@ __device__ bool band_lu_serial_smem(const Band &B) {
     B.piv[k] = p;
     if (p != k)
       for (int c = k; c <= cmax; ++c) {
-        double t = B.A(k, c);
+        T t = B.A(k, c);
         B.A(k, c) = B.A(p, c);
         B.A(p, c) = t;
       }
-    const double d = B.A(k, k);
-    if (d == 0.0) sing = true;
-    B.rinv[k] = 1.0 / d;
+    const T d = B.A(k, k);
+    if (d == T(0.0)) sing = true;
+    B.rinv[k] = T(1.0) / d;
     for (int i = k + 1; i <= imax; ++i) {
-      const double l = B.A(i, k) / d;
+      const T l = B.A(i, k) / d;
       B.A(i, k) = l;
       for (int c = k + 1; c <= cmax; ++c) B.A(i, c) -= l * B.A(k, c);
     }
@@ -661,19 +686,19 @@ __device__ bool band_lu_serial_smem(const Band &B) {
 }
 
 // x (B.x, length n) := A^{-1} x with the stored factors (one thread).
-template <int KL>
-__device__ void band_lu_solve_serial(const Band &B) {
+template <int KL, typename T>
+__device__ void band_lu_solve_serial(const Band<T> &B) {
   constexpr int W = 2 * KL + 1;
   const int n = B.n;
-  double X[KL + 1];
+  T X[KL + 1];
 #pragma unroll
-  for (int i = 0; i <= KL; ++i) X[i] = i < n ? B.x[i] : 0.0;
+  for (int i = 0; i <= KL; ++i) X[i] = i < n ? B.x[i] : T(0.0);
   for (int k = 0; k < n; ++k) {
     const int p = B.piv[k] - k;
 #pragma unroll
     for (int i = 1; i <= KL; ++i)
       if (p == i) {
-        double t = X[0];
+        T t = X[0];
         X[0] = X[i];
         X[i] = t;
       }
@@ -683,18 +708,18 @@ __device__ void band_lu_solve_serial(const Band &B) {
     B.x[k] = X[0];
 #pragma unroll
     for (int i = 0; i < KL; ++i) X[i] = X[i + 1];
-    X[KL] = (k + KL + 1 < n) ? B.x[k + KL + 1] : 0.0;
+    X[KL] = (k + KL + 1 < n) ? B.x[k + KL + 1] : T(0.0);
   }
-  double Y[W - 1];  // Y[c] = x[i + 1 + c]
+  T Y[W - 1];  // Y[c] = x[i + 1 + c]
 #pragma unroll
-  for (int c = 0; c < W - 1; ++c) Y[c] = 0.0;
+  for (int c = 0; c < W - 1; ++c) Y[c] = T(0.0);
   for (int i = n - 1; i >= 0; --i) {
-    double s = B.x[i];
+    T s = B.x[i];
 #pragma unroll
     for (int c = W - 2; c >= 1; --c)
       if (i + 1 + c < n) s -= B.A(i, i + 1 + c) * Y[c];
     if (i + 1 < n) s -= B.A(i, i + 1) * Y[0];
-    const double xi = s * B.rinv[i];
+    const T xi = s * B.rinv[i];
     B.x[i] = xi;
 #pragma unroll
     for (int c = W - 2; c >= 1; --c) Y[c] = Y[c - 1];
@@ -704,13 +729,14 @@ __device__ void band_lu_solve_serial(const Band &B) {
 
 // Assemble the band matrix from J (all threads), then factor (thread 0).
 // Returns true if a pivot was exactly zero (all threads).
-__device__ bool band_factor(Band &B, int N, int nb, const double *J) {
+template <typename T>
+__device__ bool band_factor(Band<T> &B, int N, int nb, const T *J) {
   const int hw = (nb - 1) / 2;
   B.n = 2 * N;
   B.kl = 2 * hw + 1;
   B.ldab = 3 * B.kl + 1;
   const int n = B.n;
-  for (int t = threadIdx.x; t < B.ldab * n; t += blockDim.x) B.ab[t] = 0.0;
+  for (int t = threadIdx.x; t < B.ldab * n; t += blockDim.x) B.ab[t] = T(0.0);
   __syncthreads();
   for (int t = threadIdx.x; t < N * nb * 4; t += blockDim.x) {
     int j = t % N, ke = t / N, k = ke / 4, e = ke % 4, l = e / 2, m = e % 2;
@@ -720,21 +746,22 @@ __device__ bool band_factor(Band &B, int N, int nb, const double *J) {
   }
   __syncthreads();
   __shared__ int s_sing;
-  if (threadIdx.x == 0) s_sing = (B.kl == 3 ? band_lu_serial<3>(B) : band_lu_serial_smem(B)) ? 1 : 0;
+  if (threadIdx.x == 0) s_sing = (B.kl == 3 ? band_lu_serial<3, T>(B) : band_lu_serial_smem<T>(B)) ? 1 : 0;
   __syncthreads();
   return s_sing != 0;
 }
 
 // dU = -J^{-1} R with the stored factors (thread 0 solves, all threads call).
-__device__ void band_solve(const Band &B, int N, const double *R, double *dU) {
+template <typename T>
+__device__ void band_solve(const Band<T> &B, int N, const T *R, T *dU) {
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     B.x[2 * t] = -R[t];
     B.x[2 * t + 1] = -R[N + t];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (B.kl == 3) band_lu_solve_serial<3>(B);
-    else band_lu_solve_serial<5>(B);
+    if (B.kl == 3) band_lu_solve_serial<3, T>(B);
+    else band_lu_solve_serial<5, T>(B);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -747,28 +774,33 @@ __device__ void band_solve(const Band &B, int N, const double *R, double *dU) {
 // ----------------------------------------------------------------------------
 // Multigrid hierarchy view: level l0 (the system being solved) uses the
 // caller's J/R/dU, levels l0+1..L the problem's workspace.
+// In the FP32 instantiation the workspace arrays (sized for FP64) hold FP32
+// values.
+template <typename T>
 struct MG {
   int l0, L;
   int N[NSWE_MAX_LEVELS], nb[NSWE_MAX_LEVELS];
-  double *J[NSWE_MAX_LEVELS], *Dinv[NSWE_MAX_LEVELS], *R[NSWE_MAX_LEVELS], *dU[NSWE_MAX_LEVELS];
+  T *J[NSWE_MAX_LEVELS], *Dinv[NSWE_MAX_LEVELS], *R[NSWE_MAX_LEVELS], *dU[NSWE_MAX_LEVELS];
 };
 
-__device__ void mg_bind(MG &mg, const ProbDev &P, int l0, int nb0, const double *J, const double *R, double *dU) {
+template <typename T>
+__device__ void mg_bind(MG<T> &mg, const ProbDev &P, int l0, int nb0, const T *J, const T *R, T *dU) {
   mg.l0 = l0;
   mg.L = P.levels - 1;
   for (int l = l0; l <= mg.L; ++l) {
     mg.N[l] = P.lev[l].N;
     mg.nb[l] = (l == l0) ? nb0 : 3;
-    mg.J[l] = (l == l0) ? const_cast<double *>(J) : P.lev[l].J;
-    mg.R[l] = (l == l0) ? const_cast<double *>(R) : P.lev[l].R;
-    mg.dU[l] = (l == l0) ? dU : P.lev[l].dU;
-    mg.Dinv[l] = P.lev[l].Dinv;
+    mg.J[l] = (l == l0) ? const_cast<T *>(J) : reinterpret_cast<T *>(P.lev[l].J);
+    mg.R[l] = (l == l0) ? const_cast<T *>(R) : reinterpret_cast<T *>(P.lev[l].R);
+    mg.dU[l] = (l == l0) ? dU : reinterpret_cast<T *>(P.lev[l].dU);
+    mg.Dinv[l] = reinterpret_cast<T *>(P.lev[l].Dinv);
   }
 }
 
 // Coarse operators, diagonal inverses and the coarsest factorisation; done
 // once per Newton step since J is fixed during its V-cycles.
-__device__ bool mg_setup(const MG &mg, Band &B) {
+template <typename T>
+__device__ bool mg_setup(const MG<T> &mg, Band<T> &B) {
   for (int l = mg.l0 + 1; l <= mg.L; ++l) {
     coarse_op_cells(mg.N[l - 1], mg.nb[l - 1], mg.J[l - 1], mg.N[l], mg.J[l], threadIdx.x, blockDim.x);
     __syncthreads();
@@ -779,7 +811,8 @@ __device__ bool mg_setup(const MG &mg, Band &B) {
 
 // `steps` symmetric multicolour SOR steps (colours 0..C-1 then C-1..0 each);
 // consecutive visits of one colour run as one pass.
-__device__ void sor_smooth(const MG &mg, int l, int steps, double omega) {
+template <typename T>
+__device__ void sor_smooth(const MG<T> &mg, int l, int steps, double omega) {
   const int nb = mg.nb[l], C = (nb - 1) / 2 + 1;
   int prev = -1, reps = 0;
   for (int s = 0; s < steps; ++s)
@@ -804,7 +837,8 @@ __device__ void sor_smooth(const MG &mg, int l, int steps, double omega) {
 }
 
 // Algorithm 2 from level l0, unrolled over levels.
-__device__ void mg_vcycle(const MG &mg, const Band &B, const nswe_params &prm) {
+template <typename T>
+__device__ void mg_vcycle(const MG<T> &mg, const Band<T> &B, const nswe_params &prm) {
   for (int l = mg.l0; l < mg.L; ++l) {
     sor_smooth(mg, l, prm.nu1, prm.omega);
     restrict_cells(mg.N[l], mg.nb[l], mg.J[l], mg.R[l], mg.dU[l], mg.N[l + 1], mg.R[l + 1], mg.dU[l + 1],
@@ -823,9 +857,10 @@ __device__ void mg_vcycle(const MG &mg, const Band &B, const nswe_params &prm) {
 // level: ab [ldab_cap * n_cap], x [n_cap], rinv [n_cap], piv [n_cap].
 extern __shared__ double g_dyn_smem[];
 
-__device__ __forceinline__ Band band_view(int n_cap, int ldab_cap) {
-  Band B;
-  B.ab = g_dyn_smem;
+template <typename T>
+__device__ __forceinline__ Band<T> band_view(int n_cap, int ldab_cap) {
+  Band<T> B;
+  B.ab = reinterpret_cast<T *>(g_dyn_smem);
   B.x = B.ab + (size_t)ldab_cap * n_cap;
   B.rinv = B.x + n_cap;
   B.piv = reinterpret_cast<int *>(B.rinv + n_cap);
@@ -859,41 +894,50 @@ __global__ void __launch_bounds__(kThreads) k_finish_res(const double *partials,
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jac_a(const ProbDev *P, int level, const double *U, double eps) {
   Geo G = make_geo(*P, level);
-  jac_pass_a(G, U, eps, jw_view(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  jac_pass_a<T>(G, U, eps, jw_view<T>(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jac_b(const ProbDev *P, int level) {
   Geo G = make_geo(*P, level);
-  jac_pass_b(G, jw_view(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  jac_pass_b<T>(G, jw_view<T>(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jac_c(const ProbDev *P, int level, int nb, double eps, double alpha,
-                                                    double *R, double *J, double *partials) {
+                                                    const double *Rreg, double *R, T *J, double *partials) {
   __shared__ double red[33];
   Geo G = make_geo(*P, level);
-  double acc = jac_pass_c(G, nb, eps, alpha, jw_view(P->jw, G.N), R, J, blockIdx.x * blockDim.x + threadIdx.x,
-                          gridDim.x * blockDim.x);
+  double acc = jac_pass_c<T>(G, nb, eps, alpha, jw_view<T>(P->jw, G.N), Rreg, R, J,
+                             blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   double s = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level, int nb, const double *J,
-                                                     const double *R, double *dU, nswe_params prm, int *status,
-                                                     int n_cap, int ldab_cap) {
-  MG mg;
-  mg_bind(mg, *P, level, nb, J, R, dU);
-  Band B = band_view(n_cap, ldab_cap);
-  bool sing = mg_setup(mg, B);
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level, int nb, const T *J, const T *R,
+                                                     T *dU, nswe_params prm, int *status, int n_cap, int ldab_cap) {
+  MG<T> mg;
+  mg_bind<T>(mg, *P, level, nb, J, R, dU);
+  Band<T> B = band_view<T>(n_cap, ldab_cap);
+  bool sing = mg_setup<T>(mg, B);
   __syncthreads();
-  mg_vcycle(mg, B, prm);
+  mg_vcycle<T>(mg, B, prm);
   if (threadIdx.x == 0) *status = sing ? NSWE_ESINGULAR : NSWE_OK;
 }
 
-// Algorithm 3 for one problem per thread block.
+// Algorithm 3 for one problem per thread block. T is the precision of the
+// Jacobian and the multigrid solve of each Newton step: with T = double the
+// whole step is FP64; with T = float the residual, the convergence test and
+// the update U += tau dU stay FP64 while the FD Jacobian (Eq. 12-13), the
+// coarse operators, the smoother and the coarsest LU run in FP32.
+template <typename T>
 __global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
     k_solve(const SolveTask *tasks, nswe_params prm, int n_cap, int ldab_cap) {
+  constexpr bool kMixed = std::is_same<T, float>::value;
   __shared__ double red[33];
   const unsigned long long t_start = global_ns();
   const SolveTask task = tasks[blockIdx.x];
@@ -901,7 +945,7 @@ __global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
   const int L = P.levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
   const int nb = prm.jacobian == NSWE_JAC_FULL ? 5 : 3;
-  Band B = band_view(n_cap, ldab_cap);
+  Band<T> B = band_view<T>(n_cap, ldab_cap);
 
   int iters[NSWE_MAX_LEVELS], lstat[NSWE_MAX_LEVELS];
   double lres[NSWE_MAX_LEVELS];
@@ -926,42 +970,64 @@ __global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
       interp_cells(make_geo(P, l + 1), P.lev[l + 1].U, Lv.U, threadIdx.x, blockDim.x);
       __syncthreads();
     }
-    // R, J and res at the current state (Eq. 10, 12-13).
-    const JW W = jw_view(P.jw, N);
-    auto residual_jacobian = [&]() -> double {
-      jac_pass_a(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
-      __syncthreads();
-      jac_pass_b(G, W, threadIdx.x, blockDim.x);
-      __syncthreads();
-      double acc = jac_pass_c(G, nb, prm.eps[l], prm.alpha, W, Lv.R, Lv.J, threadIdx.x, blockDim.x);
+    const JW<T> W = jw_view<T>(P.jw, N);
+    T *const J = reinterpret_cast<T *>(Lv.J);
+    T *const dU = reinterpret_cast<T *>(Lv.dU);
+    // Right-hand side of the linear solve: the FP64 residual itself, or its
+    // FP32 copy in the unused upper part of J's storage (J takes 4 nb N of
+    // the 40 N floats there).
+    T *const Rs = kMixed ? J + (size_t)4 * nb * N : reinterpret_cast<T *>(Lv.R);
+    // FP64 path: R, J and res at the current state in one pass (Eq. 10,
+    // 12-13). Mixed path: only the FP64 residual and res here.
+    auto residual_step = [&]() -> double {
+      double acc;
+      if constexpr (kMixed) {
+        acc = residual_cells(G, Lv.U, Lv.R, threadIdx.x, blockDim.x);
+      } else {
+        jac_pass_a<T>(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
+        __syncthreads();
+        jac_pass_b<T>(G, W, threadIdx.x, blockDim.x);
+        __syncthreads();
+        acc = jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, nullptr, Lv.R, J, threadIdx.x, blockDim.x);
+      }
       return block_sum(acc, red) / N;
     };
-    double res = residual_jacobian();
+    double res = residual_step();
     int n = 0, st = NSWE_OK;
     while (true) {
-      MG mg;
-      mg_bind(mg, P, l, nb, Lv.J, Lv.R, Lv.dU);
-      bool sing = mg_setup(mg, B);
+      if constexpr (kMixed) {
+        // FP32 Jacobian at the current state, regularised with the FP64 R.
+        jac_pass_a<T>(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
+        __syncthreads();
+        jac_pass_b<T>(G, W, threadIdx.x, blockDim.x);
+        __syncthreads();
+        jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, Lv.R, nullptr, J, threadIdx.x, blockDim.x);
+        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) Rs[t] = T(Lv.R[t]);
+        __syncthreads();
+      }
+      MG<T> mg;
+      mg_bind<T>(mg, P, l, nb, J, Rs, dU);
+      bool sing = mg_setup<T>(mg, B);
       __syncthreads();
       if (sing) {
         st = NSWE_ESINGULAR;
         break;
       }
       if (l == L) {
-        band_solve(B, N, Lv.R, Lv.dU);
+        band_solve<T>(B, N, Rs, dU);
       } else {
-        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) Lv.dU[t] = 0.0;
+        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) dU[t] = T(0.0);
         __syncthreads();
         for (int m = 0; m < prm.nu3; ++m) {
-          mg_vcycle(mg, B, prm);
+          mg_vcycle<T>(mg, B, prm);
           ++vcycles;
         }
       }
       bool bad = false;
       for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double h = Lv.U[j] + prm.tau * Lv.dU[j];
+        double h = Lv.U[j] + prm.tau * double(dU[j]);
         Lv.U[j] = h;
-        Lv.U[N + j] += prm.tau * Lv.dU[N + j];
+        Lv.U[N + j] += prm.tau * double(dU[N + j]);
         if (!(h > 0.0)) bad = true;
       }
       bad = __syncthreads_or(bad);
@@ -970,9 +1036,9 @@ __global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
         st = NSWE_ENEGDEPTH;
         break;
       }
-      // res of the new state; its Jacobian serves the next step (and is not
-      // needed once res < tol).
-      res = residual_jacobian();
+      // res of the new state (on the FP64 path its Jacobian serves the next
+      // step and is not needed once res < tol).
+      res = residual_step();
       if (!(res == res) || isinf(res)) {
         st = NSWE_ENAN;
         break;
@@ -1027,11 +1093,23 @@ cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U,
 
 cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
                             double alpha, double *R, double *J, double *res, double *partials, cudaStream_t s) {
-  k_jac_a<<<grid_for((N + 2) * 8), kThreads, 0, s>>>(p, level, U, eps);
-  k_jac_b<<<grid_for(N + 1), kThreads, 0, s>>>(p, level);
+  k_jac_a<double><<<grid_for((N + 2) * 8), kThreads, 0, s>>>(p, level, U, eps);
+  k_jac_b<double><<<grid_for(N + 1), kThreads, 0, s>>>(p, level);
   const int grid = grid_for(N * nb);
-  k_jac_c<<<grid, kThreads, 0, s>>>(p, level, nb, eps, alpha, R, J, partials);
+  k_jac_c<double><<<grid, kThreads, 0, s>>>(p, level, nb, eps, alpha, nullptr, R, J, partials);
   if (res) k_finish_res<<<1, 32, 0, s>>>(partials, grid, N, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian_f32(const ProbDev *p, int level, int N, int nb, const double *U, double eps,
+                                double alpha, double *R, float *J, double *res, double *partials, cudaStream_t s) {
+  // The residual's reduction has consumed `partials` (stream order) before
+  // the FP32 pass C reuses it (it writes zeros there).
+  cudaError_t e = launch_residual(p, level, N, U, R, res, partials, s);
+  if (e != cudaSuccess) return e;
+  k_jac_a<float><<<grid_for((N + 2) * 8), kThreads, 0, s>>>(p, level, U, eps);
+  k_jac_b<float><<<grid_for(N + 1), kThreads, 0, s>>>(p, level);
+  k_jac_c<float><<<grid_for(N * nb), kThreads, 0, s>>>(p, level, nb, eps, alpha, R, nullptr, J, partials);
   return cudaGetLastError();
 }
 
@@ -1042,15 +1120,25 @@ size_t band_smem_bytes(int n_cap, int ldab_cap) {
 cudaError_t launch_vcycle(const ProbDev *p, int level, int nb, const double *J, const double *R, double *dU,
                           const nswe_params &prm, int *status, int coarse_cells, int coarse_nb, cudaStream_t s) {
   const int n_cap = 2 * coarse_cells, ldab_cap = 3 * (coarse_nb == 5 ? 5 : 3) + 1;
-  k_vcycle<<<1, kThreads, band_smem_bytes(n_cap, ldab_cap), s>>>(p, level, nb, J, R, dU, prm, status, n_cap,
-                                                                ldab_cap);
+  k_vcycle<double><<<1, kThreads, band_smem_bytes(n_cap, ldab_cap), s>>>(p, level, nb, J, R, dU, prm, status,
+                                                                        n_cap, ldab_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vcycle_f32(const ProbDev *p, int level, int nb, const float *J, const float *R, float *dU,
+                              const nswe_params &prm, int *status, int coarse_cells, int coarse_nb, cudaStream_t s) {
+  const int n_cap = 2 * coarse_cells, ldab_cap = 3 * (coarse_nb == 5 ? 5 : 3) + 1;
+  k_vcycle<float><<<1, kThreads, band_smem_bytes(n_cap, ldab_cap), s>>>(p, level, nb, J, R, dU, prm, status,
+                                                                       n_cap, ldab_cap);
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                          cudaStream_t s) {
   const int n_cap = 2 * max_coarse_cells, ldab_cap = 3 * (prm.jacobian == NSWE_JAC_FULL ? 5 : 3) + 1;
-  k_solve<<<count, kThreads, band_smem_bytes(n_cap, ldab_cap), s>>>(tasks, prm, n_cap, ldab_cap);
+  const size_t smem = band_smem_bytes(n_cap, ldab_cap);
+  if (prm.precision == NSWE_PREC_MIXED) k_solve<float><<<count, kThreads, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+  else k_solve<double><<<count, kThreads, smem, s>>>(tasks, prm, n_cap, ldab_cap);
   return cudaGetLastError();
 }
 

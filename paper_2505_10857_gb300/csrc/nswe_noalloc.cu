@@ -93,7 +93,8 @@ extern "C" nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N
   const nswe_params &p = *params;
   if (!(p.tau > 0.0 && p.tau <= 1.0) || !(p.alpha >= 0.0) || !(p.omega > 0.0 && p.omega < 2.0) ||
       !(p.tol > 0.0) || p.nu1 < 0 || p.nu2 < 0 || p.nu3 < 1 || p.n_max < 1 || p.nu1 > 1000 || p.nu2 > 1000 ||
-      p.nu3 > 1000 || (p.jacobian != NSWE_JAC_SIMPLIFIED && p.jacobian != NSWE_JAC_FULL))
+      p.nu3 > 1000 || (p.jacobian != NSWE_JAC_SIMPLIFIED && p.jacobian != NSWE_JAC_FULL) ||
+      (p.precision != NSWE_PREC_FP64 && p.precision != NSWE_PREC_MIXED))
     return NSWE_EINVAL;
   const int s0 = (p.nest_start >= 0 && p.nest_start < levels) ? p.nest_start : levels - 1;
   for (int l = 0; l <= s0; ++l)

@@ -18,6 +18,7 @@ from . import build as _build
 
 MAX_LEVELS = 16
 JAC_SIMPLIFIED, JAC_FULL = 3, 5
+PREC_FP64, PREC_MIXED = 0, 1
 BC_DISCHARGE, BC_DEPTH, BC_STATE, BC_EXTRAP = 1, 2, 3, 4
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENAN", 6: "ENEGDEPTH",
           7: "ESINGULAR"}
@@ -31,7 +32,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("omega", ctypes.c_double),
                 ("tol", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("nu3", ctypes.c_int),
                 ("n_max", ctypes.c_int), ("jacobian", ctypes.c_int), ("nest_start", ctypes.c_int),
-                ("eps", ctypes.c_double * MAX_LEVELS)]
+                ("precision", ctypes.c_int), ("eps", ctypes.c_double * MAX_LEVELS)]
 
 
 class Info(ctypes.Structure):
@@ -72,6 +73,8 @@ EXPORTS = {
     "nswe_jacobian_simplified": (_i, [_vp, _vp, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_jacobian_full": (_i, [_vp, _vp, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_mg_vcycle": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
+    "nswe_jacobian_f32": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
+    "nswe_mg_vcycle_f32": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
     "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                      ctypes.POINTER(Params), ctypes.POINTER(Info)]),
@@ -107,15 +110,17 @@ def _check(call, rc):
         raise NsweError(call, rc)
 
 
-def _ptr(t) -> Optional[int]:
-    """Device pointer of a CUDA float64 contiguous tensor (or None)."""
+def _ptr(t, f32=False) -> Optional[int]:
+    """Device pointer of a contiguous CUDA float64 (float32 with f32) tensor,
+    or None."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
     import torch
-    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise ValueError("expected a contiguous float64 CUDA tensor")
+    dt = torch.float32 if f32 else torch.float64
+    if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous {dt} CUDA tensor")
     return t.data_ptr()
 
 
@@ -289,6 +294,17 @@ def nswe_jacobian_full(ctx, prob, level, U, eps, alpha, R, J, res=None):
 def nswe_mg_vcycle(ctx, prob, level, nb, J, R, dU, prm: Params):
     _check("nswe_mg_vcycle", lib().nswe_mg_vcycle(ctx.h, prob.h, int(level), int(nb), _ptr(J), _ptr(R), _ptr(dU),
                                                   ctypes.byref(prm)))
+
+
+def nswe_jacobian_f32(ctx, prob, level, nb, U, eps, alpha, R, J, res=None):
+    """R (float64) and the FP32 Jacobian J (float32) of a mixed-precision step."""
+    _check("nswe_jacobian_f32", lib().nswe_jacobian_f32(
+        ctx.h, prob.h, int(level), int(nb), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J, True), _ptr(res)))
+
+
+def nswe_mg_vcycle_f32(ctx, prob, level, nb, J, R, dU, prm: Params):
+    _check("nswe_mg_vcycle_f32", lib().nswe_mg_vcycle_f32(ctx.h, prob.h, int(level), int(nb), _ptr(J, True),
+                                                          _ptr(R, True), _ptr(dU, True), ctypes.byref(prm)))
 
 
 def nswe_newton_solve(ctx, prob, U0, U, prm: Params, want_info=True, raise_on_status=False):

@@ -44,3 +44,27 @@ def test_product_path_does_not_import_the_oracle():
             if fn.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "nswe_oracle" not in src, fn
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Field offsets and sizes of nswe_params / nswe_info / nswe_bc1d as the
+    C compiler lays them out agree with the ctypes mirrors."""
+    import subprocess
+    from paper_2505_10857_gb300 import nswe
+    structs = {"nswe_params": nswe.Params, "nswe_info": nswe.Info, "nswe_bc1d": nswe.BC1D}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nswe.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
