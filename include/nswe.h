@@ -273,7 +273,7 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count,
  * block on the device synchronisation cudaMalloc/cudaFree imply. It runs the
  * same solve as nswe_newton_solve on one problem of at most
  * NSWE_NOALLOC_MAX_CELLS cells, with the problem description and workspace
- * in a fixed device array of the library (about 3.2 MB, held by every GPU that
+ * in a fixed device array of the library (about 3.4 MB, held by every GPU that
  * loads the library until the process exits); it allocates nothing.
  *   device       CUDA device index; it is made current for the call.
  *   stream       cudaStream_t as void* (NULL: legacy default stream).

@@ -129,12 +129,11 @@ nswe_status upload_geometry(nswe_prob p, const double *sigma_face, const double 
     return NSWE_ECUDA;
   if (cudaMemcpyAsync(p->dev, &p->host, sizeof(ProbDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return NSWE_ECUDA;
+  if (launch_geom_derive(p->dev, p->N, s) != cudaSuccess) return NSWE_ECUDA;
   return NSWE_OK;
 }
 
 // ---------------------------------------------------------------- 2D host side
-
-int coarse_cells2(const nswe_prob_s *p) { return (p->Nx >> (p->levels - 1)) * (p->Ny >> (p->levels - 1)); }
 
 // Symmetric multicolour smoothing of 2D level l: one step = colours 0..C-1,
 // C-1..0, twice; consecutive visits of a colour run as one pass.
@@ -381,7 +380,7 @@ nswe_status nswe_prob_create_1d(nswe_ctx ctx, nswe_prob *out, int N, int levels,
   for (int l = 0; l < levels; ++l) {
     size_t Nl = (size_t)(N >> l);
     geo += round_up(Nl + 1) + round_up(6 * Nl);
-    work += round_up(2 * Nl) * 3 + round_up(20 * Nl) + round_up(4 * Nl);
+    work += round_up(2 * Nl) * 3 + round_up(20 * Nl) + round_up(4 * Nl) + round_up(gd_doubles(Nl));
   }
   work += round_up(jw_doubles((size_t)N));
   p->geo_doubles = geo;
@@ -423,6 +422,8 @@ nswe_status nswe_prob_create_1d(nswe_ctx ctx, nswe_prob *out, int N, int levels,
     a += round_up(20 * Nl);
     h.lev[l].Dinv = a;
     a += round_up(4 * Nl);
+    h.lev[l].gd = a;
+    a += round_up(gd_doubles(Nl));
   }
   h.jw = a;
   a += round_up(jw_doubles((size_t)N));

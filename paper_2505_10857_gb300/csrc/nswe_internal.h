@@ -29,6 +29,9 @@ struct LevelDev {
   double *J;         // [5][4][N] Jacobian (nb blocks used)
   double *Dinv;      // [4][N] inverse diagonal blocks
   double *dU;        // [2][N] multigrid correction
+  double *gd;        // [4N+2] derived from the geometry by launch_geom_derive:
+                     // 1/sigma at faces [N+1], sqrt(g/sigma) at faces [N+1],
+                     // 1/sigma at the Gauss points [2][N]
 };
 
 struct ProbDev {
@@ -41,7 +44,9 @@ struct ProbDev {
 };
 
 // Doubles of Jacobian workspace for a level of N cells.
-inline size_t jw_doubles(size_t N) { return 16 * (N + 2) + 18 * (N + 1); }
+__host__ __device__ inline size_t jw_doubles(size_t N) { return 16 * (N + 2) + 18 * (N + 1); }
+// Doubles of derived geometry per level of N cells.
+inline size_t gd_doubles(size_t N) { return 4 * N + 2; }
 
 // ---------------------------------------------------------------- 2D
 // Block stencils of 2D operators (offset tables in nswe_kernels_2d.cu).
@@ -95,6 +100,8 @@ struct SolveTask {
 };
 
 // Kernel launchers (stream-ordered, return cudaGetLastError()).
+// Fills every level's gd from its sf and gq (after each geometry upload).
+cudaError_t launch_geom_derive(const ProbDev *p, int finest_cells, cudaStream_t s);
 cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U, double *R, double *res,
                             double *partials, cudaStream_t s);
 cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,

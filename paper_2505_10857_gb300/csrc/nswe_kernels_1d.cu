@@ -30,8 +30,11 @@ __device__ constexpr double kLag[2][4] = {
 struct Geo {
   int N;
   double dx, g;
-  const double *sf;
-  const double *gq;
+  const double *sf;   // [N+1] width at faces
+  const double *gq;   // [3][2][N] sigma, sigma_x, b_x at the Gauss points
+  const double *isf;  // [N+1] 1/sigma at faces
+  const double *cgf;  // [N+1] sqrt(g/sigma) at faces
+  const double *igq;  // [2][N] 1/sigma at the Gauss points
   int bl, br;
   double blh, blq, brh, brq;
 };
@@ -43,6 +46,9 @@ __device__ __forceinline__ Geo make_geo(const ProbDev &P, int l) {
   G.g = P.g;
   G.sf = P.lev[l].sf;
   G.gq = P.lev[l].gq;
+  G.isf = P.lev[l].gd;
+  G.cgf = G.isf + G.N + 1;
+  G.igq = G.cgf + G.N + 1;
   G.bl = P.bl;
   G.br = P.br;
   G.blh = P.blh;
@@ -88,53 +94,35 @@ __device__ __forceinline__ void weno3(T a, T b, T c, T &up, T &um) {
   um = (T(2.0) * s1 * q0 + s0 * q1) * (D1 * inv);
 }
 
-// HLL flux at a face of width sig: S_L = min(u_L - c_L, u_R - c_R),
-// S_R = max(u_L + c_L, u_R + c_R), c = sqrt(g H / sig); physical flux
-// F = (Q, Q^2/H + g H^2/(2 sig)) (Eq. 4).
-__device__ __forceinline__ void hll(double HL, double QL, double HR, double QR, double sig, double g,
-                                    double &F0, double &F1) {
-  double isg = 1.0 / sig;
-  double iHL = 1.0 / HL, iHR = 1.0 / HR;
-  double uL = QL * iHL, uR = QR * iHR;
-  double hL = HL * isg, hR = HR * isg;
-  double cL = sqrt(g * hL), cR = sqrt(g * hR);
-  double FL1 = QL * uL + 0.5 * g * HL * hL;
-  double FR1 = QR * uR + 0.5 * g * HR * hR;
-  double SL = fmin(uL - cL, uR - cR);
-  double SR = fmax(uL + cL, uR + cR);
-  if (SL >= 0.0) {
-    F0 = QL;
-    F1 = FL1;
-  } else if (SR <= 0.0) {
-    F0 = QR;
-    F1 = FR1;
-  } else {
-    double iw = 1.0 / (SR - SL);
-    F0 = (SR * QL - SL * QR + SL * SR * (HR - HL)) * iw;
-    F1 = (SR * FL1 - SL * FR1 + SL * SR * (QR - QL)) * iw;
-  }
-}
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
-// Quantities of one interface state at a face of width 1/isg entering HLL.
+// Quantities of one interface state entering the HLL flux at a face of width
+// sigma: velocity u = Q/H, celerity c = sqrt(g H/sigma) and physical flux
+// F = (Q, Q^2/H + g H^2/(2 sigma)) (Eq. 4). One reciprocal square root
+// r = H^(-1/2) gives both 1/H = r^2 and c = sqrt(g/sigma) H r; isg = 1/sigma
+// and cg = sqrt(g/sigma) are per-face geometry.
 template <typename T>
 struct FState {
   T H, Q, u, c, F1;
 };
 
 template <typename T>
-__device__ __forceinline__ FState<T> fstate(T H, T Q, T isg, T g) {
+__device__ __forceinline__ FState<T> fstate(T H, T Q, T isg, T cg, T g) {
   FState<T> s;
   s.H = H;
   s.Q = Q;
-  T iH = T(1.0) / H;
-  s.u = Q * iH;
-  T h = H * isg;
-  s.c = sqrt(g * h);
+  const T r = rsq(H);
+  s.u = Q * (r * r);
+  const T h = H * isg;
+  s.c = cg * (H * r);
   s.F1 = Q * s.u + T(0.5) * g * H * h;
   return s;
 }
 
-// HLL combination of two interface states (same formula as hll()).
+// HLL flux of two interface states: S_L = min(u_L - c_L, u_R - c_R),
+// S_R = max(u_L + c_L, u_R + c_R), upwind fluxes outside the fan, the HLL
+// average inside.
 template <typename T>
 __device__ __forceinline__ void hll_states(const FState<T> &L, const FState<T> &R, T &F0, T &F1) {
   T SL = fmin(L.u - L.c, R.u - R.c);
@@ -198,6 +186,8 @@ __device__ __forceinline__ void fill_ghosts(const Geo &G, int j, Win &w) {
 // Two-point Gauss source of cell j (Eq. 9): S = (dx/2) sum_q [g h^2 sigma_x/2
 // - g sigma h b_x] at the Gauss points, h = H_h/sigma, H_h the cubic through
 // the interface values p0..p3 of H at t = -3/2, -1/2, 1/2, 3/2.
+// With H_h = sigma h the second term is g H_h b_x; 1/sigma is per-cell
+// geometry.
 template <typename T>
 __device__ __forceinline__ T source_at(const Geo &G, int j, T p0, T p1, T p2, T p3) {
   T S = T(0.0);
@@ -205,11 +195,10 @@ __device__ __forceinline__ T source_at(const Geo &G, int j, T p0, T p1, T p2, T 
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     T Hh = T(kLag[q][0]) * p0 + T(kLag[q][1]) * p1 + T(kLag[q][2]) * p2 + T(kLag[q][3]) * p3;
-    T sig = T(G.gq[(0 * 2 + q) * G.N + j]);
     T sigx = T(G.gq[(1 * 2 + q) * G.N + j]);
     T bx = T(G.gq[(2 * 2 + q) * G.N + j]);
-    T h = Hh / sig;
-    S += T(0.5) * g * h * h * sigx - g * sig * h * bx;
+    T h = Hh * T(G.igq[q * G.N + j]);
+    S += T(0.5) * g * h * h * sigx - g * Hh * bx;
   }
   return S * (T(0.5) * T(G.dx));
 }
@@ -223,8 +212,10 @@ __device__ __forceinline__ void local_residual(const Geo &G, int j, const Win &w
     weno3(w.Q[p], w.Q[p + 1], w.Q[p + 2], upQ[p], umQ[p]);
   }
   double Fr0, Fr1, Fl0, Fl1;
-  hll(umH[1], umQ[1], upH[2], upQ[2], G.sf[j + 1], G.g, Fr0, Fr1);
-  hll(umH[0], umQ[0], upH[1], upQ[1], G.sf[j], G.g, Fl0, Fl1);
+  hll_states(fstate(umH[1], umQ[1], G.isf[j + 1], G.cgf[j + 1], G.g),
+             fstate(upH[2], upQ[2], G.isf[j + 1], G.cgf[j + 1], G.g), Fr0, Fr1);
+  hll_states(fstate(umH[0], umQ[0], G.isf[j], G.cgf[j], G.g), fstate(upH[1], upQ[1], G.isf[j], G.cgf[j], G.g),
+             Fl0, Fl1);
   double S = source_at(G, j, upH[0], upH[1], umH[1], umH[2]);
   R0 = Fr0 - Fl0;
   R1 = Fr1 - Fl1 - S;
@@ -358,9 +349,9 @@ __device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) 
   const int N = G.N;
   const T g = T(G.g);
   for (int f = first; f <= N; f += stride) {
-    const T isg = T(1.0) / T(G.sf[f]);
-    const FState<T> Lb = fstate<T>(W.r(0, 0, 1, f - 1), W.r(1, 0, 1, f - 1), isg, g);
-    const FState<T> Rb = fstate<T>(W.r(0, 0, 0, f), W.r(1, 0, 0, f), isg, g);
+    const T isg = T(G.isf[f]), cg = T(G.cgf[f]);
+    const FState<T> Lb = fstate<T>(W.r(0, 0, 1, f - 1), W.r(1, 0, 1, f - 1), isg, cg, g);
+    const FState<T> Rb = fstate<T>(W.r(0, 0, 0, f), W.r(1, 0, 0, f), isg, cg, g);
     T F0, F1;
     hll_states(Lb, Rb, F0, F1);
     W.f(0, 0, f) = F0;
@@ -373,8 +364,8 @@ __device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) 
       for (int m = 0; m < 2; ++m) {
         FState<T> Ls = Lb, Rs = Rb;
         if (p <= 2)
-          Ls = fstate<T>(W.r(0, m == 0 ? p + 1 : 0, 1, f - 1), W.r(1, m == 1 ? p + 1 : 0, 1, f - 1), isg, g);
-        if (p >= 1) Rs = fstate<T>(W.r(0, m == 0 ? p : 0, 0, f), W.r(1, m == 1 ? p : 0, 0, f), isg, g);
+          Ls = fstate<T>(W.r(0, m == 0 ? p + 1 : 0, 1, f - 1), W.r(1, m == 1 ? p + 1 : 0, 1, f - 1), isg, cg, g);
+        if (p >= 1) Rs = fstate<T>(W.r(0, m == 0 ? p : 0, 0, f), W.r(1, m == 1 ? p : 0, 0, f), isg, cg, g);
         hll_states(Ls, Rs, F0, F1);
         const int w = 1 + 2 * p + m;
         W.f(w, 0, f) = F0;
@@ -390,51 +381,133 @@ __device__ __forceinline__ int flux_variant(int i, int m, int face) {
   return (p >= 0 && p <= 3) ? 1 + 2 * p + m : 0;
 }
 
-// Pass C over items (cell j, block k); writes J and, when Rout is given, R
-// (from the k = hw items). The regularisation uses Rreg when given (the FP64
-// residual of a mixed-precision step), else the pass's own base residual.
-// Returns the partial sum of ||R_j||_1 of the items that wrote R.
+// Pass C, one cell j per item: the base R_j (written when Rout is given),
+// then for each block k (cell i = j + k - hw) R_j of the state with U_i
+// perturbed, from two face fluxes and the Gauss source, minus the base R_j,
+// over eps, plus alpha ||R_j||_1 I on the diagonal. The regularisation uses
+// Rreg when given (the FP64 residual of a mixed-precision step), else the
+// pass's own base residual. Returns the partial sum of ||R_j||_1 of the
+// cells that wrote R.
 template <typename T>
 __device__ double jac_pass_c(const Geo &G, int nb, double eps, double alpha, const JW<T> &W, const double *Rreg,
                              double *Rout, T *J, int first, int stride) {
-  const int N = G.N, hw = (nb - 1) / 2, items = N * nb;
+  const int N = G.N, hw = (nb - 1) / 2;
+  const T ieps = T(1.0) / T(eps);
   double acc = 0.0;
-  for (int it = first; it < items; it += stride) {
-    const int j = it % N, k = it / N, d = k - hw, i = j + d;
+  for (int j = first; j < N; j += stride) {
     const T Sb = source_at<T>(G, j, W.r(0, 0, 0, j - 1), W.r(0, 0, 0, j), W.r(0, 0, 1, j), W.r(0, 0, 1, j + 1));
     const T R0 = W.f(0, 0, j + 1) - W.f(0, 0, j);
     const T R1 = W.f(0, 1, j + 1) - W.f(0, 1, j) - Sb;
-    if (d == 0 && Rout) {
+    if (Rout) {
       Rout[j] = double(R0);
       Rout[N + j] = double(R1);
       acc += fabs(double(R0)) + fabs(double(R1));
     }
-    if (i < 0 || i >= N) {
+    const T reg = Rreg ? T(alpha * (fabs(Rreg[j]) + fabs(Rreg[N + j]))) : T(alpha) * (fabs(R0) + fabs(R1));
+    for (int k = 0; k < nb; ++k) {
+      const int i = j + k - hw;
+      if (i < 0 || i >= N) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) J[(k * 4 + e) * N + j] = T(0.0);
-      continue;
-    }
-    T reg = T(0.0);
-    if (d == 0) reg = Rreg ? T(alpha * (fabs(Rreg[j]) + fabs(Rreg[N + j]))) : T(alpha) * (fabs(R0) + fabs(R1));
-    const T ieps = T(1.0) / T(eps);
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      T S = Sb;
-      if (m == 0) {
-        const int v0 = rec_variant(i, j - 1), v1 = rec_variant(i, j), v2 = rec_variant(i, j + 1);
-        S = source_at<T>(G, j, W.r(0, v0, 0, j - 1), W.r(0, v1, 0, j), W.r(0, v1, 1, j), W.r(0, v2, 1, j + 1));
+        for (int e = 0; e < 4; ++e) J[(k * 4 + e) * N + j] = T(0.0);
+        continue;
       }
-      const int wr = flux_variant(i, m, j + 1), wl = flux_variant(i, m, j);
-      const T P0 = W.f(wr, 0, j + 1) - W.f(wl, 0, j);
-      const T P1 = W.f(wr, 1, j + 1) - W.f(wl, 1, j) - S;
-      T v0 = (P0 - R0) * ieps, v1 = (P1 - R1) * ieps;
-      if (m == 0) v0 += reg;
-      else v1 += reg;
-      J[(k * 4 + 0 * 2 + m) * N + j] = v0;
-      J[(k * 4 + 1 * 2 + m) * N + j] = v1;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        T S = Sb;
+        if (m == 0) {
+          const int v0 = rec_variant(i, j - 1), v1 = rec_variant(i, j), v2 = rec_variant(i, j + 1);
+          S = source_at<T>(G, j, W.r(0, v0, 0, j - 1), W.r(0, v1, 0, j), W.r(0, v1, 1, j), W.r(0, v2, 1, j + 1));
+        }
+        const int wr = flux_variant(i, m, j + 1), wl = flux_variant(i, m, j);
+        const T P0 = W.f(wr, 0, j + 1) - W.f(wl, 0, j);
+        const T P1 = W.f(wr, 1, j + 1) - W.f(wl, 1, j) - S;
+        T v0 = (P0 - R0) * ieps, v1 = (P1 - R1) * ieps;
+        if (i == j) {
+          if (m == 0) v0 += reg;
+          else v1 += reg;
+        }
+        J[(k * 4 + 0 * 2 + m) * N + j] = v0;
+        J[(k * 4 + 1 * 2 + m) * N + j] = v1;
+      }
     }
   }
   return acc;
+}
+
+// ----------------------------------------------------------------------------
+// FP64 residual in three passes over a compact workspace (the residual of a
+// mixed-precision Newton step): reconstructions once per cell, fluxes once
+// per face, then sources and differences per cell. Same arithmetic as the
+// base variant of the Jacobian passes.
+struct RW {
+  double *rec;  // [2 comps][2: up, um][N+2], cell k at k+1
+  double *flx;  // [2 comps][N+1]
+  int N;
+  __device__ __forceinline__ double &r(int m, int o, int k) const { return rec[(m * 2 + o) * (N + 2) + (k + 1)]; }
+  __device__ __forceinline__ double &f(int l, int face) const { return flx[l * (N + 1) + face]; }
+};
+
+// Placed after the FP32 Jacobian workspace of the same level.
+__device__ __forceinline__ RW rw_view(double *jw, int N) {
+  RW W;
+  W.rec = jw + (jw_doubles((size_t)N) / 2 + 2) / 2 * 2;
+  W.flx = W.rec + 4 * (size_t)(N + 2);
+  W.N = N;
+  return W;
+}
+
+__device__ void res_pass_a(const Geo &G, const double *U, const RW &W, int first, int stride) {
+  const int N = G.N, items = (N + 2) * 2;
+  for (int it = first; it < items; it += stride) {
+    const int k = it % (N + 2) - 1, m = it / (N + 2);
+    double up, um;
+    weno3<double>(pval<double>(G, U, m, k - 1, -1, 0.0), pval<double>(G, U, m, k, -1, 0.0),
+                  pval<double>(G, U, m, k + 1, -1, 0.0), up, um);
+    W.r(m, 0, k) = up;
+    W.r(m, 1, k) = um;
+  }
+}
+
+__device__ void res_pass_b(const Geo &G, const RW &W, int first, int stride) {
+  for (int f = first; f <= G.N; f += stride) {
+    double F0, F1;
+    hll_states(fstate(W.r(0, 1, f - 1), W.r(1, 1, f - 1), G.isf[f], G.cgf[f], G.g),
+               fstate(W.r(0, 0, f), W.r(1, 0, f), G.isf[f], G.cgf[f], G.g), F0, F1);
+    W.f(0, f) = F0;
+    W.f(1, f) = F1;
+  }
+}
+
+__device__ double res_pass_c(const Geo &G, const RW &W, double *R, int first, int stride) {
+  const int N = G.N;
+  double acc = 0.0;
+  for (int j = first; j < N; j += stride) {
+    const double S = source_at<double>(G, j, W.r(0, 0, j - 1), W.r(0, 0, j), W.r(0, 1, j), W.r(0, 1, j + 1));
+    const double R0 = W.f(0, j + 1) - W.f(0, j);
+    const double R1 = W.f(1, j + 1) - W.f(1, j) - S;
+    R[j] = R0;
+    R[N + j] = R1;
+    acc += fabs(R0) + fabs(R1);
+  }
+  return acc;
+}
+
+// Derived geometry of every level (1/sigma and sqrt(g/sigma) at faces, 1/sigma
+// at the Gauss points), items strided over the finest level's faces.
+__device__ void geom_derive_items(const ProbDev &P, int first, int stride) {
+  for (int l = 0; l < P.levels; ++l) {
+    const LevelDev &Lv = P.lev[l];
+    const int N = Lv.N;
+    double *isf = Lv.gd, *cgf = isf + N + 1, *igq = cgf + N + 1;
+    for (int t = first; t <= N; t += stride) {
+      isf[t] = 1.0 / Lv.sf[t];
+      cgf[t] = sqrt(P.g * isf[t]);
+    }
+    for (int t = first; t < 2 * N; t += stride) {
+      const int q = t / N, j = t % N;
+      igq[t] = 1.0 / Lv.gq[(0 * 2 + q) * N + j];
+    }
+  }
 }
 
 // Inverse of the diagonal 2x2 blocks.
@@ -894,6 +967,10 @@ __global__ void __launch_bounds__(kThreads) k_finish_res(const double *partials,
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_geom_derive(const ProbDev *P) {
+  geom_derive_items(*P, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jac_a(const ProbDev *P, int level, const double *U, double eps) {
   Geo G = make_geo(*P, level);
@@ -982,7 +1059,12 @@ __global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
     auto residual_step = [&]() -> double {
       double acc;
       if constexpr (kMixed) {
-        acc = residual_cells(G, Lv.U, Lv.R, threadIdx.x, blockDim.x);
+        const RW RWv = rw_view(P.jw, N);
+        res_pass_a(G, Lv.U, RWv, threadIdx.x, blockDim.x);
+        __syncthreads();
+        res_pass_b(G, RWv, threadIdx.x, blockDim.x);
+        __syncthreads();
+        acc = res_pass_c(G, RWv, Lv.R, threadIdx.x, blockDim.x);
       } else {
         jac_pass_a<T>(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
         __syncthreads();
@@ -1082,6 +1164,11 @@ int grid_for(int items) {
 }
 
 }  // namespace
+
+cudaError_t launch_geom_derive(const ProbDev *p, int finest_cells, cudaStream_t s) {
+  k_geom_derive<<<grid_for(2 * finest_cells + 1), kThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U, double *R, double *res,
                             double *partials, cudaStream_t s) {

@@ -29,13 +29,14 @@ using namespace nswe;
 namespace {
 
 // Workspace of a problem of up to NSWE_NOALLOC_MAX_CELLS cells: per level,
-// face widths (N_l+1), U, R, dU (2 N_l each), J (20 N_l), Dinv (4 N_l), each
-// slot rounded to 32 doubles (below 31 * 2N + 6 * 32 * 16 over all levels),
-// plus the Jacobian workspace of the finest level (34 N + 50) and the
-// problem description and task (below 1024).
+// face widths (N_l+1), U, R, dU (2 N_l each), J (20 N_l), Dinv (4 N_l),
+// derived geometry (4 N_l + 2), each slot rounded to 32 doubles (below
+// 35 * 2N + 7 * 32 * 16 over all levels), plus the Jacobian workspace of the
+// finest level (34 N + 50) and the problem description and task (below
+// 1024).
 constexpr size_t kSlot = 32;
 constexpr size_t kScratchDoubles =
-    (31 * 2 + 34) * (size_t)NSWE_NOALLOC_MAX_CELLS + 6 * kSlot * NSWE_MAX_LEVELS + 2 * kSlot + 1024;
+    (35 * 2 + 34) * (size_t)NSWE_NOALLOC_MAX_CELLS + 7 * kSlot * NSWE_MAX_LEVELS + 2 * kSlot + 1024;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -145,6 +146,8 @@ extern "C" nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N
       a += slot(20 * Nl);
       Lv.Dinv = a;
       a += slot(4 * Nl);
+      Lv.gd = a;
+      a += slot(gd_doubles(Nl));
     }
     P.jw = a;
     a += slot(jw_doubles((size_t)N));
@@ -158,7 +161,9 @@ extern "C" nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N
       T.info = info;
       cudaStream_t s = (cudaStream_t)stream;
       k_noalloc_setup<<<1, kThreads, 0, s>>>(P, T, prob_slot, task_slot, sigma_face);
-      if (cudaGetLastError() != cudaSuccess || launch_solve(task_slot, 1, p, NL, s) != cudaSuccess) st = NSWE_ECUDA;
+      if (cudaGetLastError() != cudaSuccess || launch_geom_derive(prob_slot, N, s) != cudaSuccess ||
+          launch_solve(task_slot, 1, p, NL, s) != cudaSuccess)
+        st = NSWE_ECUDA;
     }
   }
   if (prev != device) cudaSetDevice(prev);
