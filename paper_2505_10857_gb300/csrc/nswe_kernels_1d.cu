@@ -517,11 +517,11 @@ __device__ void dinv_cells(int N, int nb, const T *J, T *Dinv, int first, int st
   for (int j = first; j < N; j += stride) {
     T a = J[(hw * 4 + 0) * N + j], b = J[(hw * 4 + 1) * N + j];
     T c = J[(hw * 4 + 2) * N + j], d = J[(hw * 4 + 3) * N + j];
-    T det = a * d - b * c;
-    Dinv[0 * N + j] = d / det;
-    Dinv[1 * N + j] = -b / det;
-    Dinv[2 * N + j] = -c / det;
-    Dinv[3 * N + j] = a / det;
+    T idet = T(1.0) / (a * d - b * c);
+    Dinv[0 * N + j] = d * idet;
+    Dinv[1 * N + j] = -b * idet;
+    Dinv[2 * N + j] = -c * idet;
+    Dinv[3 * N + j] = a * idet;
   }
 }
 
@@ -656,10 +656,14 @@ __device__ void interp_cells(const Geo &Gc, const double *Uc, double *Uf, int fi
 // the block-banded system, unknown u = 2j + m, in LAPACK-style band storage
 // (kl sub-diagonals, 2 kl super-diagonals after fill-in). A banded matrix
 // keeps its zeros outside the band through the elimination, so this performs
-// the same pivots and updates as a dense LU. The factorisation and the
-// triangular solves are sequential recurrences; one thread runs each with the
-// active rows in registers (a window of kl+1 rows), which keeps the latency
-// of every step to a few dependent FP64 operations.
+// the same pivots and updates as a dense LU. The elimination is a sequence of
+// n pivot steps; one warp runs it, its lanes covering the entries of a step
+// (the kl multipliers, the kl x 2kl updated entries, the 2kl back-substitution
+// updates). GB300 issues an FP64 warp instruction at the same cost whatever
+// its active lanes, so spreading each step over lanes, rather than running it
+// on one thread, divides the FP64 work of the solve by about the band width.
+// Every entry sees the same operations in the same order as in a serial
+// elimination.
 
 template <typename T>
 struct Band {
@@ -671,6 +675,109 @@ struct Band {
   __device__ __forceinline__ T &A(int r, int c) const { return ab[(2 * kl + r - c) * n + c]; }
 };
 
+// Order key of |a|: for non-negative floating-point values the bit patterns,
+// read as unsigned integers, are ordered as the values (NaN keys are dropped
+// to 0, so a NaN never wins a pivot search).
+__device__ __forceinline__ unsigned long long abs_key(double a) {
+  return a == a ? (unsigned long long)(__double_as_longlong(a) & 0x7fffffffffffffffLL) : 0ull;
+}
+__device__ __forceinline__ unsigned long long abs_key(float a) {
+  return a == a ? (unsigned long long)(__float_as_uint(a) & 0x7fffffffu) : 0ull;
+}
+
+// Factorisation by warp 0 (lanes 0..31, all of them calling). Returns true if
+// a pivot was exactly zero.
+template <typename T>
+__device__ bool band_lu_warp(const Band<T> &B) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int n = B.n, kl = B.kl, w2 = 2 * kl, upd = kl * w2;
+  bool sing = false;
+  for (int k = 0; k < n; ++k) {
+    const int imax = min(n - 1, k + kl), cmax = min(n - 1, k + w2);
+    // Pivot: the first row of largest |A(i, k)|, i = k..imax (kl <= 7).
+    unsigned long long key = 0;
+    int p = 0x7fffffff;
+    if (lane <= kl && k + lane <= imax) {
+      key = abs_key(B.A(k + lane, k));
+      p = k + lane;
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(FULL, key, o);
+      const int op = __shfl_xor_sync(FULL, p, o);
+      if (ok > key || (ok == key && op < p)) {
+        key = ok;
+        p = op;
+      }
+    }
+    p = __shfl_sync(FULL, p, 0);
+    if (lane == 0) B.piv[k] = p;
+    if (p != k)
+      for (int c = k + lane; c <= cmax; c += 32) {
+        const T t = B.A(k, c);
+        B.A(k, c) = B.A(p, c);
+        B.A(p, c) = t;
+      }
+    __syncwarp();
+    // One division for 1/d (lane 0) and the multipliers A(k+i, k)/d (lane i).
+    const T d = B.A(k, k);
+    const bool mrow = lane >= 1 && lane <= kl && k + lane <= imax;
+    const T q = (lane == 0 ? T(1.0) : (mrow ? B.A(k + lane, k) : T(0.0))) / d;
+    if (lane == 0) {
+      B.rinv[k] = q;
+      if (d == T(0.0)) sing = true;
+    }
+    if (mrow) B.A(k + lane, k) = q;
+    // A(k+i, k+c) -= l_i A(k, k+c), i = 1..kl, c = 1..2kl.
+    for (int e0 = 0; e0 < upd; e0 += 32) {
+      const int e = e0 + lane, i = 1 + e / w2, c = 1 + e % w2;
+      const T l = __shfl_sync(FULL, q, min(i, 31));
+      if (e < upd && k + i <= imax && k + c <= cmax) B.A(k + i, k + c) -= l * B.A(k, k + c);
+    }
+    __syncwarp();
+  }
+  return __shfl_sync(FULL, sing, 0);
+}
+
+// x (B.x, length n) := A^{-1} x with the stored factors, by warp 0. The back
+// substitution is column oriented: once x_i is known, the rows above it take
+// their A(r, i) x_i terms, so each row subtracts its terms from the farthest
+// column to the nearest, the order of the row-oriented loop.
+template <typename T>
+__device__ void band_lu_solve_warp(const Band<T> &B) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int n = B.n, kl = B.kl;
+  for (int k = 0; k < n; ++k) {
+    const int p = B.piv[k];
+    if (p != k && lane == 0) {
+      const T t = B.x[k];
+      B.x[k] = B.x[p];
+      B.x[p] = t;
+    }
+    __syncwarp();
+    const T xk = B.x[k];
+    if (lane >= 1 && lane <= kl && k + lane < n) B.x[k + lane] -= B.A(k + lane, k) * xk;
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    T xi = T(0.0);
+    if (lane == 0) {
+      xi = B.x[i] * B.rinv[i];
+      B.x[i] = xi;
+    }
+    xi = __shfl_sync(FULL, xi, 0);
+    const int r = i - lane;
+    if (lane >= 1 && lane <= 2 * kl && r >= 0) B.x[r] -= B.A(r, i) * xi;
+    __syncwarp();
+  }
+}
+
+// FP32 instantiation: one thread runs the elimination with the active rows in
+// registers (a window of kl+1 rows). FP32 instructions issue at full rate, so
+// the serial recurrence is shorter than its warp-parallel form, whose
+// shuffles and warp barriers then dominate.
 template <int KL, typename T>
 __device__ bool band_lu_serial(const Band<T> &B) {
   constexpr int W = 2 * KL + 1;
@@ -728,8 +835,8 @@ __device__ bool band_lu_serial(const Band<T> &B) {
   return sing;
 }
 
-// The same factorisation working on the band storage in place (any kl); used
-// for the 5-block Jacobian of a direct solve on the coarsest nested level.
+// The same serial factorisation working on the band storage in place (any
+// kl); used for the 5-block Jacobian of a direct solve on the coarsest level.
 template <typename T>
 __device__ bool band_lu_serial_smem(const Band<T> &B) {
   const int n = B.n, kl = B.kl;
@@ -800,8 +907,9 @@ __device__ void band_lu_solve_serial(const Band<T> &B) {
   }
 }
 
-// Assemble the band matrix from J (all threads), then factor (thread 0).
-// Returns true if a pivot was exactly zero (all threads).
+// Assemble the band matrix from J (all threads), then factor (warp 0 in
+// FP64, thread 0 in FP32). Returns true if a pivot was exactly zero (all
+// threads).
 template <typename T>
 __device__ bool band_factor(Band<T> &B, int N, int nb, const T *J) {
   const int hw = (nb - 1) / 2;
@@ -819,12 +927,20 @@ __device__ bool band_factor(Band<T> &B, int N, int nb, const T *J) {
   }
   __syncthreads();
   __shared__ int s_sing;
-  if (threadIdx.x == 0) s_sing = (B.kl == 3 ? band_lu_serial<3, T>(B) : band_lu_serial_smem<T>(B)) ? 1 : 0;
+  if constexpr (std::is_same<T, double>::value) {
+    if (threadIdx.x < 32) {
+      const bool sing = band_lu_warp<T>(B);
+      if (threadIdx.x == 0) s_sing = sing ? 1 : 0;
+    }
+  } else {
+    if (threadIdx.x == 0) s_sing = (B.kl == 3 ? band_lu_serial<3, T>(B) : band_lu_serial_smem<T>(B)) ? 1 : 0;
+  }
   __syncthreads();
   return s_sing != 0;
 }
 
-// dU = -J^{-1} R with the stored factors (thread 0 solves, all threads call).
+// dU = -J^{-1} R with the stored factors (warp 0 solves in FP64, thread 0 in
+// FP32; all threads call).
 template <typename T>
 __device__ void band_solve(const Band<T> &B, int N, const T *R, T *dU) {
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -832,7 +948,9 @@ __device__ void band_solve(const Band<T> &B, int N, const T *R, T *dU) {
     B.x[2 * t + 1] = -R[N + t];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (threadIdx.x < 32) band_lu_solve_warp<T>(B);
+  } else if (threadIdx.x == 0) {
     if (B.kl == 3) band_lu_solve_serial<3, T>(B);
     else band_lu_solve_serial<5, T>(B);
   }
