@@ -490,6 +490,130 @@ def run_wedge2d(args):
         "kernels_512x256": kern}), flush=True)
 
 
+def _serve_oracle_worker(k):
+    import oracle
+    from paper_2505_10857_gb300 import inputs as I
+    inp = I.serving_instance(k)
+    U, info = oracle.solve_problem(inp, I.Params1D.for_problem(inp, tol=TOL, n_max=500))
+    return U, info["status"]
+
+
+def run_serve1d(args):
+    """Serving measurement (not the default line): `--requests` seeded 1D
+    requests (N log-uniform in [256, 16384], q ~ U[1, 6]) arriving as a
+    seeded Poisson process at `--rate` per second into the continuous-batching
+    server, mixed precision by default. Throughput counts the solves that
+    reached res < tol over the span from the first submission to the last
+    completion; latency is completion minus submission, host clock, per
+    request."""
+    import numpy as np
+    import torch
+
+    from paper_2505_10857_gb300 import inputs as I
+    from paper_2505_10857_gb300 import nswe
+
+    mixed = args.precision != "fp64"
+    M = args.requests
+    inps = [I.serving_instance(k) for k in range(M)]
+    prms = []
+    for p in inps:
+        q = nswe.params_from(I.Params1D.for_problem(p, tol=TOL, n_max=500))
+        q.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
+        prms.append(q)
+    foot = [nswe.Server.footprint(p.N, p.levels, p.start_level) for p in inps]
+    torch.cuda.init()
+    sv = nswe.Server(0, device_bytes=args.serve_mem_gb << 30, host_bytes=1 << 30, streams=args.streams,
+                     max_batch=args.max_batch)
+    results = {}
+
+    def drain(block_until=None):
+        while True:
+            for t in sv.poll():
+                results[t] = sv.take(t)
+            if block_until is None or len(results) >= block_until:
+                return
+            sv.wait(1, 1.0)
+
+    # warm-up: a burst of the first requests, discarded
+    warm = min(M, 64 * max(1, args.warmup))
+    for k in range(warm):
+        sv.submit(inps[k], prms[k])
+    drain(warm)
+    results.clear()
+    st0 = sv.stats()
+    clocks = ClockSampler(0)
+    clocks.start()
+    rng = np.random.default_rng(4999)
+    gaps = rng.exponential(1.0 / args.rate, size=M)
+    arrive = np.cumsum(gaps) - gaps[0]
+    tickets = []
+    t0 = time.perf_counter()
+    for k in range(M):
+        while True:
+            dt = t0 + arrive[k] - time.perf_counter()
+            if dt <= 0:
+                break
+            if dt > 0.002:
+                for t in sv.poll():
+                    results[t] = sv.take(t)
+            time.sleep(min(dt, 0.001))
+        tickets.append(sv.submit(inps[k], prms[k]))
+    drain(M)
+    clk = clocks.stop()
+    st1 = sv.stats()
+    sv.close()
+    tim = [results[t][2] for t in tickets]
+    infos = [results[t][1] for t in tickets]
+    lat = sorted((x["t_done_ns"] - x["t_submit_ns"]) / 1e6 for x in tim)
+    queue = sorted((x["t_launch_ns"] - x["t_submit_ns"]) / 1e6 for x in tim)
+    span = (max(x["t_done_ns"] for x in tim) - min(x["t_submit_ns"] for x in tim)) / 1e9
+    ok = [k for k in range(M) if infos[k]["status"] == 0]
+    value = len(ok) / span  # solves that reached res < tol
+
+    def pct(a, q):
+        return a[min(len(a) - 1, int(math.ceil(q / 100.0 * len(a))) - 1)]
+
+    parity = None
+    if not args.no_cpu:
+        cores = host_cores()
+        n = min(M, 2 * cores)
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            refs = pool.map(_serve_oracle_worker, range(n))
+        errs = [float(np.abs(results[tickets[k]][0] - refs[k][0]).max() / np.abs(refs[k][0]).max())
+                for k in range(n) if infos[k]["status"] == 0 and refs[k][1] == 0]
+        parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "bound": MIXED_BOUND if mixed else 1e-10}
+    h2d = sum(p.sig_face.nbytes + p.gq_all().nbytes + p.U0_start.nbytes for p in inps) / M
+    d2h = sum(2 * p.N * 8 for p in inps) / M + ctypes.sizeof(nswe.Info)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"1D serving: {M} requests, N log-uniform [256,16384] (mean {np.mean([p.N for p in inps]):.0f}"
+                               f" cells), q~U[1,6], Poisson arrivals at {args.rate}/s, "
+                               + ("mixed FP64/FP32" if mixed else "FP64"),
+                   "offered_rate": args.rate, "streams": args.streams, "max_batch": args.max_batch,
+                   "device_arena_gb": args.serve_mem_gb, "seeds": "numpy default_rng(4000 + k); arrivals 4999",
+                   "l2": "resident workspace of the requests in flight exceeds the 129 MB L2"},
+        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": lat[-1],
+                       "what": "completion minus submission per request (host clock)",
+                       "queue_p50": pct(queue, 50), "queue_p99": pct(queue, 99)},
+        "converged": {"all_status_ok": len(ok) == M, "converged": len(ok), "of": M,
+                      "not_converged_seeds": [4000 + k for k in range(M) if infos[k]["status"] != 0],
+                      "max_res": max(infos[k]["res"][0] for k in ok),
+                      "mean_newton_iters": statistics.mean(infos[k]["total_iters"] for k in ok)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d * M, "d2h_bytes_per_step": d2h * M,
+                "what": "the serving throughput is end to end: host arrays in, host results out"},
+        "gpu_launches": st1["launches"] - st0["launches"],
+        "serving": {"device_bytes_peak": st1["device_bytes_peak"], "mean_footprint_mb": float(np.mean(foot)) / 2**20,
+                    "launches": st1["launches"] - st0["launches"]},
+        "clocks": clk,
+    }
+    if parity:
+        line["parity"] = parity
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,7 +625,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
-    ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d"])
+    ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d", "serve1d"])
+    ap.add_argument("--requests", type=int, default=1024, help="serve1d: requests in the arrival schedule")
+    ap.add_argument("--rate", type=float, default=1500.0, help="serve1d: Poisson arrival rate (requests/s)")
+    ap.add_argument("--streams", type=int, default=8, help="serve1d: concurrent launches")
+    ap.add_argument("--max-batch", type=int, default=512, help="serve1d: solves per launch")
+    ap.add_argument("--serve-mem-gb", type=int, default=16, help="serve1d: device arena (GB)")
     ap.add_argument("--nx", type=int, default=128)
     ap.add_argument("--ny", type=int, default=64)
     ap.add_argument("--levels2d", type=int, default=5)
@@ -511,6 +640,13 @@ def main():
         from paper_2505_10857_gb300 import build
         build.build()
         run_wedge2d(args)
+        return
+    if args.workload == "serve1d":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        if args.precision == "fp64" and "--precision" not in sys.argv:
+            args.precision = "mixed"  # the serving workload is specified in mixed precision
+        run_serve1d(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

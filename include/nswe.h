@@ -8,7 +8,10 @@
  * the regularized Newton iteration of Section 3.2 with the finite-difference
  * Jacobian J5 or its simplified block-tridiagonal form J3 (Section 3.3), and
  * solved by the geometric multigrid of Section 3.4 inside the nested NMGM of
- * Algorithm 3. All arithmetic is FP64.
+ * Algorithm 3; the two-dimensional model of Section 4 (J21 / J9) through the
+ * same calls. Arithmetic is FP64, with an optional mixed-precision 1D solve
+ * (NSWE_PREC_MIXED). A continuous-batching server for streams of 1D solves
+ * sits at the end of this header.
  *
  * Conventions
  *   - Cells and faces are 0-based: cell j of a level with N cells spans faces
@@ -32,6 +35,8 @@
 #ifndef NSWE_H
 #define NSWE_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -44,7 +49,8 @@ typedef enum {
   NSWE_ENOTCONV = 4,  /* Newton stopped at n_max with res >= tol              */
   NSWE_ENAN = 5,      /* NaN/Inf in the residual                              */
   NSWE_ENEGDEPTH = 6, /* non-positive wet cross-section H in the state        */
-  NSWE_ESINGULAR = 7  /* exactly zero pivot in the coarsest direct solve      */
+  NSWE_ESINGULAR = 7, /* exactly zero pivot in the coarsest direct solve     */
+  NSWE_ETIMEOUT = 8    /* a wait ended before the awaited event              */
 } nswe_status;
 
 /* Boundary data (Section 5.1). The paper gives the data, not the discrete
@@ -299,6 +305,101 @@ nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N,
                                       const double *U0, double *U,
                                       const nswe_params *params,
                                       nswe_info *info);
+
+/* ------------------------------------------------------------------------
+ * Continuous-batching solve server (1D). The paper has no counterpart: this
+ * is the serving form of nswe_newton_solve_batch for a stream of requests of
+ * different sizes. Each request is one nested solve (Algorithm 3) described
+ * by host arrays, copied at submission. The server owns one device arena of
+ * device_bytes and one pinned host arena of host_bytes; a request is
+ * admitted, in submission order, once its footprint
+ * (nswe_server_footprint_1d) fits, and its problem data and Newton /
+ * multigrid workspace stay resident in its block until it completes.
+ * Admitted requests are launched together, one thread block each, on an
+ * idle stream among `streams`, at most max_batch per launch and one
+ * precision per launch; launches on different streams overlap on the GPU.
+ * A scheduler thread owned by the server issues all of its CUDA work; the
+ * calls below are thread-safe. A solve's result does not depend on the
+ * other requests it is launched with.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  size_t device_bytes; /* device arena for resident solves (>= 1 MiB)        */
+  size_t host_bytes;   /* pinned staging arena (>= 1 MiB)                    */
+  int streams;         /* concurrent launches, 1..16                         */
+  int max_batch;       /* solves per launch, 1..65536                        */
+  double batch_window_s; /* a launch that is not full waits until its oldest
+                            request has waited this long (0: launch at once) */
+} nswe_server_config;
+
+typedef struct { /* host steady-clock nanoseconds */
+  unsigned long long t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns;
+} nswe_server_times;
+
+typedef struct {
+  long long submitted, completed, launches;
+  int waiting, running;
+  size_t device_bytes_used, device_bytes_peak;
+} nswe_server_stats;
+
+typedef struct nswe_server_s *nswe_server;
+
+/* Device bytes a request of N cells, `levels` levels and nested start level
+ * nest_start (<0: coarsest) occupies in the arena; 0 for invalid sizes. */
+size_t nswe_server_footprint_1d(int N, int levels, int nest_start);
+
+/* Allocates the arenas, streams and the scheduler thread on `device`.
+ * EINVAL for a bad config, ENOMEM if an arena cannot be allocated. */
+nswe_status nswe_server_create(nswe_server *out, int device,
+                               const nswe_server_config *cfg);
+
+/* Queues one solve. Arguments as nswe_prob_create_1d (HOST arrays) plus
+ * U0 (HOST [2][N_s], N_s the cells of the nested start level) and params
+ * (copied; eps per level, precision and jacobian per request). Returns a
+ * ticket. EINVAL for invalid input, ENOMEM if the footprint exceeds an
+ * arena (it could never be admitted), the server's error after a CUDA
+ * failure. */
+nswe_status nswe_server_submit_1d(nswe_server s, int N, int levels, double x0,
+                                  double x1, double g,
+                                  const double *sigma_face,
+                                  const double *gauss_geom,
+                                  const nswe_bc1d *left,
+                                  const nswe_bc1d *right, const double *U0,
+                                  const nswe_params *params,
+                                  unsigned long long *ticket);
+
+/* Tickets completed since the last poll (up to max, in completion order). */
+nswe_status nswe_server_poll(nswe_server s, unsigned long long *tickets,
+                             int max, int *count);
+
+/* Blocks until at least min_completed tickets await polling, or timeout_s
+ * seconds pass (NSWE_ETIMEOUT). */
+nswe_status nswe_server_wait(nswe_server s, int min_completed,
+                             double timeout_s);
+
+/* Result of a completed ticket: U (HOST [2][N], may be NULL), the solve
+ * record and the host timestamps; the ticket is released. EINVAL for a
+ * ticket that is not (or no longer) complete. */
+nswe_status nswe_server_take(nswe_server s, unsigned long long ticket,
+                             double *U, nswe_info *info,
+                             nswe_server_times *times);
+
+nswe_status nswe_server_query(nswe_server s, nswe_server_stats *out);
+
+/* Stops the scheduler after the launched work finishes, frees everything;
+ * requests not yet launched are dropped. */
+nswe_status nswe_server_destroy(nswe_server s);
+
+/* The server's arena allocator, exposed for tests and for callers that
+ * manage their own device pools: first fit over [0, bytes), offsets and
+ * lengths rounded up to `align` (a power of two), freed blocks coalesced
+ * with free neighbours. No device memory is involved. */
+typedef struct nswe_arena_s *nswe_arena;
+nswe_status nswe_arena_create(nswe_arena *out, size_t bytes, size_t align);
+nswe_status nswe_arena_alloc(nswe_arena a, size_t bytes, size_t *offset);
+nswe_status nswe_arena_free(nswe_arena a, size_t offset);
+nswe_status nswe_arena_query(nswe_arena a, size_t *used, size_t *peak,
+                             size_t *largest_free);
+nswe_status nswe_arena_destroy(nswe_arena a);
 
 #ifdef __cplusplus
 }

@@ -80,6 +80,18 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
   return NSWE_OK;
 }
 
+}  // namespace
+
+nswe_status nswe::check_params_1d(const nswe_params *p, int levels, int first_level) {
+  nswe_status st = check_params(p, nullptr, 0);
+  if (st != NSWE_OK) return st;
+  for (int l = 0; l <= first_level && l < levels; ++l)
+    if (!(p->eps[l] > 0.0) || !std::isfinite(p->eps[l])) return NSWE_EINVAL;
+  return NSWE_OK;
+}
+
+namespace {
+
 nswe_status ensure_cap(nswe_ctx ctx, int count) {
   if (count <= ctx->cap) return NSWE_OK;
   int cap = count < 64 ? 64 : count;
@@ -293,6 +305,7 @@ const char *nswe_status_str(int s) {
   case NSWE_ENAN: return "NaN or Inf in the residual";
   case NSWE_ENEGDEPTH: return "non-positive wet cross-section";
   case NSWE_ESINGULAR: return "singular coarsest system";
+  case NSWE_ETIMEOUT: return "wait timed out";
   default: return "unknown status";
   }
 }
@@ -717,6 +730,9 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
     tasks[i].U0 = U0s[i];
     tasks[i].U = Us[i];
     tasks[i].info = ctx->infos + i;
+    tasks[i].prm = nullptr;
+    tasks[i].derive = 0;
+    tasks[i].done = nullptr;
   }
   cudaStream_t s = ctx->stream;
   if (cudaMemcpyAsync(ctx->tasks, tasks.data(), sizeof(SolveTask) * count, cudaMemcpyHostToDevice, s) !=

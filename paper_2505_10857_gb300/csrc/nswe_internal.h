@@ -96,7 +96,13 @@ struct SolveTask {
   const ProbDev *prob;
   const double *U0;
   double *U;
-  nswe_info *info;   // device record
+  nswe_info *info;           // device record
+  const nswe_params *prm;    // device copy of this solve's parameters, or
+                             // null for the launch's parameters
+  int derive;                // 1: fill prob's derived geometry first
+  int *done;                 // null, or a flag set to 1 (system scope) once
+                             // U and info are written: lets the host see
+                             // each solve of a launch complete on its own
 };
 
 // Kernel launchers (stream-ordered, return cudaGetLastError()).
@@ -120,5 +126,11 @@ cudaError_t launch_vcycle_f32(const ProbDev *p, int level, int nb, const float *
 // selects the FP64 or the mixed-precision solve kernel.
 cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                          cudaStream_t s);
+// The same with the coarsest band sized for max_nb (3 or 5) whatever prm
+// says: for batches whose tasks carry their own parameters.
+cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
+                               int max_nb, cudaStream_t s);
+// Parameter checks shared by the entry points (eps of levels 0..first_level).
+nswe_status check_params_1d(const nswe_params *p, int levels, int first_level);
 
 }  // namespace nswe

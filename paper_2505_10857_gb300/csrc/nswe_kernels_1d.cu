@@ -1131,12 +1131,17 @@ __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level
 // coarse operators, the smoother and the coarsest LU run in FP32.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
-    k_solve(const SolveTask *tasks, nswe_params prm, int n_cap, int ldab_cap) {
+    k_solve(const SolveTask *tasks, nswe_params launch_prm, int n_cap, int ldab_cap) {
   constexpr bool kMixed = std::is_same<T, float>::value;
   __shared__ double red[33];
+  __shared__ nswe_params s_prm;
   const unsigned long long t_start = global_ns();
   const SolveTask task = tasks[blockIdx.x];
   const ProbDev &P = *task.prob;
+  if (threadIdx.x == 0) s_prm = task.prm ? *task.prm : launch_prm;
+  if (task.derive) geom_derive_items(P, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const nswe_params &prm = s_prm;
   const int L = P.levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
   const int nb = prm.jacobian == NSWE_JAC_FULL ? 5 : 3;
@@ -1274,6 +1279,12 @@ __global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
     inf.t_end_ns = global_ns();
     *task.info = inf;
   }
+  if (task.done) {
+    // Every thread's result writes are visible system-wide before the flag.
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) *reinterpret_cast<volatile int *>(task.done) = 1;
+  }
 }
 
 int grid_for(int items) {
@@ -1340,7 +1351,12 @@ cudaError_t launch_vcycle_f32(const ProbDev *p, int level, int nb, const float *
 
 cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                          cudaStream_t s) {
-  const int n_cap = 2 * max_coarse_cells, ldab_cap = 3 * (prm.jacobian == NSWE_JAC_FULL ? 5 : 3) + 1;
+  return launch_solve_sized(tasks, count, prm, max_coarse_cells, prm.jacobian == NSWE_JAC_FULL ? 5 : 3, s);
+}
+
+cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
+                               int max_nb, cudaStream_t s) {
+  const int n_cap = 2 * max_coarse_cells, ldab_cap = 3 * (max_nb == 5 ? 5 : 3) + 1;
   const size_t smem = band_smem_bytes(n_cap, ldab_cap);
   if (prm.precision == NSWE_PREC_MIXED) k_solve<float><<<count, kThreads, smem, s>>>(tasks, prm, n_cap, ldab_cap);
   else k_solve<double><<<count, kThreads, smem, s>>>(tasks, prm, n_cap, ldab_cap);

@@ -159,6 +159,9 @@ extern "C" nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N
       T.U0 = U0;
       T.U = U;
       T.info = info;
+      T.prm = nullptr;
+      T.derive = 0;
+      T.done = nullptr;
       cudaStream_t s = (cudaStream_t)stream;
       k_noalloc_setup<<<1, kThreads, 0, s>>>(P, T, prob_slot, task_slot, sigma_face);
       if (cudaGetLastError() != cudaSuccess || launch_geom_derive(prob_slot, N, s) != cudaSuccess ||

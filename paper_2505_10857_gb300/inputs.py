@@ -210,8 +210,8 @@ def eps_for_n(n, floor=0.05):
 
 def eps_channel(n):
     """FD perturbation for the sinusoidal-width channels: 0.2 up to 512 cells,
-    0.1 at 1024, 0.05 from 2048 cells."""
-    return 0.2 if n <= 512 else (0.1 if n <= 1024 else 0.05)
+    0.1 below 2048, 0.05 from 2048 cells."""
+    return 0.2 if n <= 512 else (0.1 if n < 2048 else 0.05)
 
 
 @dataclass
@@ -319,6 +319,38 @@ def channel_irregular(k, N=4096, levels=8, regime="sub", min_margin=0.5, start_l
                            (BC_DISCHARGE, 0.0, q), (BC_DEPTH, hout, 0.0), h_init=hout, q_init=q,
                            meta={"A": A, "xc": xc, "w": w, "k": kk, "seed": 2000 + k, "draws": draw + 1,
                                  "margin": margin, "regime": regime}, start_level=start_level, omega=0.7,
+                           eps_levels=[eps_channel(N >> l) for l in range(levels)])
+
+
+def serving_instance(k, n_min=256, n_max=16384, min_margin=0.5):
+    """Seeded request of the 1D serving workload (seed 4000 + k): N drawn
+    log-uniform in [n_min, n_max], then rounded to a multiple of 2^(L-1) with
+    L the number of levels that brings the coarsest grid into [32, 64) cells
+    (the nested solve needs N divisible by 2^(L-1)); discharge q ~ U[1, 6];
+    width B(x) = 1 + 0.2 sin(2 pi k' x/25), k' ~ U{1..4};
+    Gaussian hump as in channel_small; downstream depth 2.0, raised in steps
+    of 0.25 until the subcritical energy margin exceeds min_margin (q up to 6
+    chokes at depth 2 where the width narrows). The nested solve starts on the
+    level of [256, 512) cells (level 0 for N < 512); SOR relaxation 0.7; eps
+    per level as for the sinusoidal channels."""
+    rng = np.random.default_rng(4000 + k)
+    n_raw = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+    levels = max(1, int(math.floor(math.log2(n_raw / 32.0))) + 1)
+    m = 1 << (levels - 1)
+    N = max(m * 32, int(round(n_raw / m)) * m)
+    q = float(rng.uniform(1.0, 6.0))
+    A, xc, w = _seeded_hump(rng)
+    kk = int(rng.integers(1, 5))
+    b_fns, s_fns = bottom_gaussian(A, xc, w), width_sine(1.0, kk, 25.0)
+    hout = 2.0
+    while critical_margin(q, hout, b_fns, s_fns) <= min_margin:
+        hout += 0.25
+    margin = critical_margin(q, hout, b_fns, s_fns)
+    start = max(0, levels - 4)
+    return make_problem_1d(N, levels, 0.0, 25.0, G_CONFIG, b_fns, s_fns,
+                           (BC_DISCHARGE, 0.0, q), (BC_DEPTH, hout, 0.0), h_init=hout, q_init=q,
+                           meta={"A": A, "xc": xc, "w": w, "k": kk, "q": q, "h_out": hout, "seed": 4000 + k,
+                                 "margin": margin, "N_raw": n_raw}, start_level=start, omega=0.7,
                            eps_levels=[eps_channel(N >> l) for l in range(levels)])
 
 

@@ -53,6 +53,22 @@ class NsweError(RuntimeError):
         self.status = status
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_size_t), ("host_bytes", ctypes.c_size_t), ("streams", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("batch_window_s", ctypes.c_double)]
+
+
+class ServerTimes(ctypes.Structure):
+    _fields_ = [("t_submit_ns", ctypes.c_ulonglong), ("t_admit_ns", ctypes.c_ulonglong),
+                ("t_launch_ns", ctypes.c_ulonglong), ("t_done_ns", ctypes.c_ulonglong)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("launches", ctypes.c_longlong),
+                ("waiting", ctypes.c_int), ("running", ctypes.c_int), ("device_bytes_used", ctypes.c_size_t),
+                ("device_bytes_peak", ctypes.c_size_t)]
+
+
 _lib = None
 _vp, _dp, _i, _d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 
@@ -80,6 +96,21 @@ EXPORTS = {
                                      ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_noalloc": (_i, [_i, _vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D),
                                        ctypes.POINTER(BC1D), _dp, _dp, ctypes.POINTER(Params), _vp]),
+    "nswe_server_footprint_1d": (ctypes.c_size_t, [_i, _i, _i]),
+    "nswe_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(ServerConfig)]),
+    "nswe_server_submit_1d": (_i, [_vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D), ctypes.POINTER(BC1D),
+                                   _dp, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "nswe_server_poll": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong), _i, ctypes.POINTER(_i)]),
+    "nswe_server_wait": (_i, [_vp, _i, _d]),
+    "nswe_server_take": (_i, [_vp, ctypes.c_ulonglong, _dp, ctypes.POINTER(Info), ctypes.POINTER(ServerTimes)]),
+    "nswe_server_query": (_i, [_vp, ctypes.POINTER(ServerStats)]),
+    "nswe_server_destroy": (_i, [_vp]),
+    "nswe_arena_create": (_i, [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_size_t]),
+    "nswe_arena_alloc": (_i, [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "nswe_arena_free": (_i, [_vp, ctypes.c_size_t]),
+    "nswe_arena_query": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                              ctypes.POINTER(ctypes.c_size_t)]),
+    "nswe_arena_destroy": (_i, [_vp]),
 }
 
 
@@ -346,3 +377,95 @@ def info_from_bytes(raw: bytes, levels=MAX_LEVELS) -> dict:
     """Decodes an nswe_info copied back from the device."""
     inf = Info.from_buffer_copy(raw)
     return inf.as_dict(levels)
+
+
+# ---------------------------------------------------------------- continuous-batching server (1D)
+
+class Server:
+    """nswe_server: requests are Problem1DInputs-like objects (N, levels, x0,
+    x1, g, sig_face, gq_all(), bcl, bcr, U0_start) with their Params."""
+
+    def __init__(self, device=0, device_bytes=1 << 30, host_bytes=256 << 20, streams=4, max_batch=1024,
+                 batch_window_s=0.0):
+        cfg = ServerConfig(int(device_bytes), int(host_bytes), int(streams), int(max_batch), float(batch_window_s))
+        self.h = _vp()
+        _check("nswe_server_create", lib().nswe_server_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)))
+        self.N = {}
+
+    @staticmethod
+    def footprint(N, levels, nest_start=-1) -> int:
+        return int(lib().nswe_server_footprint_1d(int(N), int(levels), int(nest_start)))
+
+    def submit(self, inp, prm: Params) -> int:
+        sf = np.ascontiguousarray(inp.sig_face, dtype=np.float64)
+        gq = np.ascontiguousarray(inp.gq_all(), dtype=np.float64)
+        u0 = np.ascontiguousarray(inp.U0_start, dtype=np.float64)
+        t = ctypes.c_ulonglong()
+        _check("nswe_server_submit_1d", lib().nswe_server_submit_1d(
+            self.h, int(inp.N), int(inp.levels), float(inp.x0), float(inp.x1), float(inp.g), sf.ctypes.data,
+            gq.ctypes.data, ctypes.byref(_bc(inp.bcl)), ctypes.byref(_bc(inp.bcr)), u0.ctypes.data,
+            ctypes.byref(prm), ctypes.byref(t)))
+        self.N[t.value] = int(inp.N)
+        return t.value
+
+    def poll(self, max_n=4096):
+        buf = (ctypes.c_ulonglong * max_n)()
+        n = _i()
+        _check("nswe_server_poll", lib().nswe_server_poll(self.h, buf, max_n, ctypes.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
+    def wait(self, min_completed=1, timeout_s=60.0) -> bool:
+        rc = lib().nswe_server_wait(self.h, int(min_completed), float(timeout_s))
+        if rc == 8:
+            return False
+        _check("nswe_server_wait", rc)
+        return True
+
+    def take(self, ticket):
+        U = np.empty((2, self.N.pop(ticket)), dtype=np.float64)
+        info, times = Info(), ServerTimes()
+        _check("nswe_server_take", lib().nswe_server_take(self.h, ctypes.c_ulonglong(ticket), U.ctypes.data,
+                                                          ctypes.byref(info), ctypes.byref(times)))
+        return U, info.as_dict(MAX_LEVELS), {f: getattr(times, f) for f, _ in ServerTimes._fields_}
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check("nswe_server_query", lib().nswe_server_query(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            lib().nswe_server_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Arena:
+    """nswe_arena: the server's first-fit allocator (host logic only)."""
+
+    def __init__(self, nbytes, align=256):
+        self.h = _vp()
+        _check("nswe_arena_create", lib().nswe_arena_create(ctypes.byref(self.h), int(nbytes), int(align)))
+
+    def alloc(self, nbytes):
+        off = ctypes.c_size_t()
+        rc = lib().nswe_arena_alloc(self.h, int(nbytes), ctypes.byref(off))
+        return off.value if rc == 0 else None
+
+    def free(self, off) -> bool:
+        return lib().nswe_arena_free(self.h, int(off)) == 0
+
+    def query(self):
+        u, p, l = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+        _check("nswe_arena_query", lib().nswe_arena_query(self.h, ctypes.byref(u), ctypes.byref(p), ctypes.byref(l)))
+        return u.value, p.value, l.value
+
+    def close(self):
+        if self.h:
+            lib().nswe_arena_destroy(self.h)
+            self.h = _vp()

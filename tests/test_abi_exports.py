@@ -51,7 +51,9 @@ def test_binding_structs_match_the_header(tmp_path):
     C compiler lays them out agree with the ctypes mirrors."""
     import subprocess
     from paper_2505_10857_gb300 import nswe
-    structs = {"nswe_params": nswe.Params, "nswe_info": nswe.Info, "nswe_bc1d": nswe.BC1D}
+    structs = {"nswe_params": nswe.Params, "nswe_info": nswe.Info, "nswe_bc1d": nswe.BC1D,
+               "nswe_server_config": nswe.ServerConfig, "nswe_server_times": nswe.ServerTimes,
+               "nswe_server_stats": nswe.ServerStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nswe.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

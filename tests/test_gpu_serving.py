@@ -1,0 +1,119 @@
+"""GPU tests of the continuous-batching server: every result in a mix of
+requests of different sizes, arriving at different times, equals (bitwise)
+the same solve run alone through nswe_newton_solve; admission respects the
+device budget; a request that can never fit is refused at submission."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2505_10857_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+KS = [1, 3, 9, 10, 11, 0, 6, 8]  # serving instances of 280..1696 cells
+
+
+@pytest.fixture(scope="module")
+def nswe():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2505_10857_gb300 import nswe as N
+    N.lib()
+    return N
+
+
+def alone(nswe, ctx, inp, prm):
+    prob = nswe.Problem1D.from_inputs(ctx, inp)
+    U = torch.zeros((2, inp.N), dtype=torch.float64, device="cuda")
+    info = nswe.nswe_newton_solve(ctx, prob, torch.from_numpy(inp.U0_start).cuda(), U, prm)
+    torch.cuda.synchronize()
+    return U.cpu().numpy(), info
+
+
+def params(nswe, inp, precision):
+    p = nswe.params_from(I.Params1D.for_problem(inp, tol=1e-10, n_max=500))
+    p.precision = precision
+    return p
+
+
+def collect(sv, n, timeout=120.0):
+    out, t0 = {}, time.time()
+    while len(out) < n:
+        assert time.time() - t0 < timeout, "server did not complete"
+        sv.wait(1, 1.0)
+        for t in sv.poll():
+            out[t] = sv.take(t)
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mix_equals_alone(nswe, precision):
+    ctx = nswe.Context(0)
+    inps = [I.serving_instance(k) for k in KS]
+    prms = [params(nswe, p, precision) for p in inps]
+    ref = [alone(nswe, ctx, p, q) for p, q in zip(inps, prms)]
+    sv = nswe.Server(0, device_bytes=256 << 20, host_bytes=64 << 20, streams=3, max_batch=4)
+    rng = np.random.default_rng(5)
+    tickets = []
+    for p, q in zip(inps, prms):
+        tickets.append(sv.submit(p, q))
+        time.sleep(float(rng.exponential(0.01)))  # Poisson arrivals
+    res = collect(sv, len(inps))
+    st = sv.stats()
+    sv.close()
+    levels = dict(zip(tickets, [p.levels for p in inps]))
+
+    def inp_levels(t):
+        return levels[t]
+
+    assert st["completed"] == len(inps) and st["launches"] >= 2
+    for t, (Uref, iref) in zip(tickets, ref):
+        U, info, times = res[t]
+        assert info["status"] == 0 and iref["status"] == 0
+        assert np.array_equal(U, Uref)
+        assert info["iters"][:inp_levels(t)] == iref["iters"][:inp_levels(t)]
+        assert times["t_submit_ns"] <= times["t_admit_ns"] <= times["t_launch_ns"] <= times["t_done_ns"]
+
+
+def test_admission_by_footprint(nswe):
+    inps = [I.serving_instance(k) for k in KS]
+    prms = [params(nswe, p, 1) for p in inps]
+    biggest = max(nswe.Server.footprint(p.N, p.levels, p.start_level) for p in inps)
+    budget = int(2.2 * biggest)  # at most two of the largest at a time
+    sv = nswe.Server(0, device_bytes=budget, host_bytes=32 << 20, streams=4, max_batch=8)
+    tickets = [sv.submit(p, q) for p, q in zip(inps, prms)]
+    res = collect(sv, len(inps))
+    st = sv.stats()
+    sv.close()
+    assert st["device_bytes_peak"] <= budget
+    assert st["completed"] == len(inps)
+    assert all(res[t][1]["status"] == 0 for t in tickets)
+
+
+def test_oversized_request_refused(nswe):
+    inp = I.serving_instance(4)  # 7168 cells, about 6.8 MB resident
+    assert nswe.Server.footprint(inp.N, inp.levels, inp.start_level) > 2 << 20
+    sv = nswe.Server(0, device_bytes=2 << 20, host_bytes=8 << 20, streams=1, max_batch=4)
+    with pytest.raises(nswe.NsweError):
+        sv.submit(inp, params(nswe, inp, 1))
+    sv.close()
+
+
+def test_requests_complete_individually(nswe):
+    """A small solve launched together with a large one completes (and is
+    taken) before the large one ends: completion is per request."""
+    small, big = I.serving_instance(11), I.serving_instance(5)  # 280 and 12032 cells
+    sv = nswe.Server(0, device_bytes=256 << 20, host_bytes=64 << 20, streams=1, max_batch=8,
+                     batch_window_s=0.5)
+    tb = sv.submit(big, params(nswe, big, 0))
+    ts = sv.submit(small, params(nswe, small, 0))
+    res = collect(sv, 2)
+    st = sv.stats()
+    sv.close()
+    assert st["launches"] == 1
+    assert res[ts][2]["t_launch_ns"] == res[tb][2]["t_launch_ns"]
+    assert res[ts][2]["t_done_ns"] < res[tb][2]["t_done_ns"]
+    assert res[ts][1]["status"] == 0 and res[tb][1]["status"] == 0
