@@ -113,6 +113,13 @@ typedef struct {
   int jacobian;   /* NSWE_JAC_SIMPLIFIED (J3) or NSWE_JAC_FULL (J5)         */
   int nest_start; /* nested level the solve starts on; <0: coarsest (Alg. 3)*/
   int precision;  /* NSWE_PREC_FP64 or NSWE_PREC_MIXED (1D problems only)   */
+  int colours2d;  /* 2D smoothing of the cross stencils (J9, coarse 5-point):
+                     0 = two symmetric passes of the stencil colouring;
+                     K >= 3 = the directional schedule, the multicolour
+                     analogue of the sweeps D1-D4 of Eq. 22: diagonal colours
+                     (i + j) mod K ascending, (j - i + Nx - 1) mod K
+                     ascending, both descending; K >= Nx + Ny - 1 is the
+                     lexicographic sweep itself                          */
   double eps[NSWE_MAX_LEVELS]; /* FD perturbation per nested level, Eq. 12  */
 } nswe_params;
 

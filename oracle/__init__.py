@@ -89,7 +89,7 @@ class Params2D(ctypes.Structure):
         ("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("omega", ctypes.c_double), ("tol", ctypes.c_double),
         ("nu1", ctypes.c_int * 16), ("nu2", ctypes.c_int * 16),
         ("nu3", ctypes.c_int), ("levels", ctypes.c_int), ("n_max", ctypes.c_int), ("st", ctypes.c_int),
-        ("nest_start", ctypes.c_int), ("eps", ctypes.c_double),
+        ("nest_start", ctypes.c_int), ("eps", ctypes.c_double), ("colours", ctypes.c_int),
     ]
 
 
@@ -141,11 +141,12 @@ def _lib_handle():
                 "or_block_inverse2d": (None, [i32, i32, _D, _D]),
                 "or_colours2d": (i32, [i32]),
                 "or_colour_of": (i32, [i32, i32, i32]),
-                "or_sor_step2d": (None, [i32, i32, i32, _D, _D, _D, _D, dbl]),
+                "or_sor_step2d": (None, [i32, i32, i32, _D, _D, _D, _D, dbl, i32]),
+                "or_diag_colour": (i32, [i32, i32, i32, i32, i32]),
                 "or_restrict2d": (None, [i32, i32, i32, _D, _D, _D, _D]),
                 "or_prolong2d": (None, [i32, i32, _D, _D]),
                 "or_direct_solve2d": (i32, [i32, i32, i32, _D, _D, _D]),
-                "or_vcycle2d": (i32, [i32, i32, i32, i32, _D, _D, _D, dbl, i32, i32]),
+                "or_vcycle2d": (i32, [i32, i32, i32, i32, _D, _D, _D, dbl, i32, i32, i32]),
                 "or_interp2d": (None, [G2, _D, _D]),
                 "or_nmgm2d": (i32, [G2, _D, _D, P(Params2D), P(Info2D)]),
                 "or_newton2d": (i32, [G2, _D, i32, P(Params2D), P(Info2D)]),
@@ -456,10 +457,10 @@ def block_inverse2d(J, st):
     return D
 
 
-def sor_step2d(J, Dinv, R, dU, Nx, Ny, st, omega):
+def sor_step2d(J, Dinv, R, dU, Nx, Ny, st, omega, colours=0):
     J, Dinv, R = _f64(J), _f64(Dinv), _f64(R)
     dU = _f64(dU).copy()
-    lib().or_sor_step2d(Nx, Ny, st, ptr(J), ptr(Dinv), ptr(R), ptr(dU), float(omega))
+    lib().or_sor_step2d(Nx, Ny, st, ptr(J), ptr(Dinv), ptr(R), ptr(dU), float(omega), int(colours))
     return dU
 
 
@@ -484,10 +485,11 @@ def direct_solve2d(J, R, Nx, Ny, st):
     return dU
 
 
-def vcycle2d(J, R, dU, Nx, Ny, st, nlev, omega, nu1, nu2):
+def vcycle2d(J, R, dU, Nx, Ny, st, nlev, omega, nu1, nu2, colours=0):
     J, R = _f64(J), _f64(R)
     dU = _f64(dU).copy()
-    if lib().or_vcycle2d(Nx, Ny, st, nlev, ptr(J), ptr(R), ptr(dU), float(omega), int(nu1), int(nu2)):
+    if lib().or_vcycle2d(Nx, Ny, st, nlev, ptr(J), ptr(R), ptr(dU), float(omega), int(nu1), int(nu2),
+                         int(colours)):
         raise ZeroDivisionError("zero pivot")
     return dU
 
@@ -499,7 +501,7 @@ def interp2d(prob_coarse: Problem2D, Uc):
     return Uf
 
 
-def make_params2d(alpha, tau, omega, tol, nu1, nu2, nu3, levels, n_max, st, eps, nest_start=-1):
+def make_params2d(alpha, tau, omega, tol, nu1, nu2, nu3, levels, n_max, st, eps, nest_start=-1, colours=0):
     p = Params2D()
     p.alpha, p.tau, p.omega, p.tol = alpha, tau, omega, tol
     nu1 = list(nu1) if hasattr(nu1, "__len__") else [nu1] * 16
@@ -508,6 +510,7 @@ def make_params2d(alpha, tau, omega, tol, nu1, nu2, nu3, levels, n_max, st, eps,
         p.nu1[i] = int(nu1[min(i, len(nu1) - 1)])
         p.nu2[i] = int(nu2[min(i, len(nu2) - 1)])
     p.nu3, p.levels, p.n_max, p.st, p.nest_start, p.eps = nu3, levels, n_max, st, nest_start, eps
+    p.colours = colours
     return p
 
 
@@ -521,7 +524,7 @@ def solve_problem2d(inp, prm):
     probs = problem_levels2d(inp)
     arr = (Grid2D * len(probs))(*[p.s for p in probs])
     p = make_params2d(prm.alpha, prm.tau, prm.omega, prm.tol, prm.nu1, prm.nu2, prm.nu3, prm.levels, prm.n_max,
-                      prm.st, prm.eps, prm.nest_start)
+                      prm.st, prm.eps, prm.nest_start, getattr(prm, "colours", 0))
     U0 = _f64(inp.U0_start).reshape(-1)
     U = np.zeros(3 * inp.Nx * inp.Ny)
     info = Info2D()
@@ -534,7 +537,7 @@ def solve_problem2d(inp, prm):
 
 def newton2d(prob: Problem2D, U_init, nlev, prm):
     p = make_params2d(prm.alpha, prm.tau, prm.omega, prm.tol, prm.nu1, prm.nu2, prm.nu3, nlev, prm.n_max,
-                      prm.st, prm.eps)
+                      prm.st, prm.eps, colours=getattr(prm, "colours", 0))
     U = _f64(U_init).reshape(-1).copy()
     info = Info2D()
     lib().or_newton2d(prob.ref(), ptr(U), int(nlev), ctypes.byref(p), ctypes.byref(info))

@@ -354,13 +354,25 @@ int or_colour_of(int st, int i, int j) {
   }
 }
 
-/* Block SOR update (Eq. 22) of every cell of one colour. */
+/* Diagonal colourings of the cross stencils (J9, coarse 5-point) of a grid
+ * Nx wide, K colours: mode 1: (i + j) mod K, mode 2: (j - i + Nx - 1) mod K
+ * (the offset makes the diagonal index non-negative, so that ascending
+ * colours are ascending diagonals when K covers them all). Cells of one
+ * colour do not couple for K >= 3 (J9: offsets up to 2 along an axis) or
+ * K >= 2 (5-point). */
+int or_diag_colour(int mode, int K, int i, int j, int Nx) {
+  return (mode == 1 ? i + j : j - i + Nx - 1) % K;
+}
+
+/* Block SOR update (Eq. 22) of every cell of one colour: mode 0 uses the
+ * stencil's own colouring (or_colour_of), modes 1 and 2 the diagonal ones. */
 static void sor_colour2d(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
-                         double omega, int col) {
+                         double omega, int mode, int Kc, int col) {
   const int n = Nx * Ny, K = or_stencil_size(st), kc = stencil_center(st);
   for (int j = 0; j < Ny; ++j)
     for (int i = 0; i < Nx; ++i) {
-      if (or_colour_of(st, i, j) != col) continue;
+      const int colour = mode == 0 ? or_colour_of(st, i, j) : or_diag_colour(mode, Kc, i, j, Nx);
+      if (colour != col) continue;
       int c = j * Nx + i;
       double r[3] = {R[c], R[n + c], R[2 * n + c]};
       for (int k = 0; k < K; ++k) {
@@ -380,13 +392,28 @@ static void sor_colour2d(int Nx, int Ny, int st, const double *J, const double *
     }
 }
 
-/* One smoothing step: two symmetric multicolour passes. */
+/* One smoothing step, the multicolour analogue of the four sweeps D1-D4 of
+ * Eq. 22. Cross stencils (J9, coarse 5-point) with K >= 3 colours: the
+ * colours of (i + j) mod K ascending (D1: towards +x, +y), of
+ * (j - i + Nx - 1) mod K ascending (D2: -x, +y), of (i + j) mod K descending
+ * (D3: -x, -y), of (j - i + Nx - 1) mod K descending (D4: +x, -y). Within each, a cell sees the new
+ * values of its upstream neighbours up to K - 1 diagonals back; for
+ * K >= Nx + Ny - 1 this is exactly the lexicographic sweep D1..D4. Other
+ * stencils (J21, coarse 9-point), or K = 0: two symmetric passes of the
+ * stencil's own colouring (0..C-1, C-1..0, twice). */
 void or_sor_step2d(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
-                   double omega) {
+                   double omega, int K) {
+  if (K >= 3 && (st == ST_J9 || st == ST_P5)) {
+    for (int c = 0; c < K; ++c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, 1, K, c);
+    for (int c = 0; c < K; ++c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, 2, K, c);
+    for (int c = K - 1; c >= 0; --c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, 1, K, c);
+    for (int c = K - 1; c >= 0; --c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, 2, K, c);
+    return;
+  }
   int C = or_colours2d(st);
   for (int rep = 0; rep < 2; ++rep) {
-    for (int c = 0; c < C; ++c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, c);
-    for (int c = C - 1; c >= 0; --c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, c);
+    for (int c = 0; c < C; ++c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, 0, 0, c);
+    for (int c = C - 1; c >= 0; --c) sor_colour2d(Nx, Ny, st, J, Dinv, R, dU, omega, 0, 0, c);
   }
 }
 
@@ -487,27 +514,27 @@ static void mg2_setup(or_mg2d *mg) {
   for (int l = 0; l <= mg->L; ++l) or_block_inverse2d(mg->Nx[l] * mg->Ny[l], mg->st[l], mg->J[l], mg->Dinv[l]);
 }
 
-static int mg2_vcycle(or_mg2d *mg, int l, double omega, int nu1, int nu2) {
+static int mg2_vcycle(or_mg2d *mg, int l, double omega, int nu1, int nu2, int K) {
   int Nx = mg->Nx[l], Ny = mg->Ny[l], st = mg->st[l];
   if (l == mg->L) return or_direct_solve2d(Nx, Ny, st, mg->J[l], mg->R[l], mg->dU[l]);
-  for (int s = 0; s < nu1; ++s) or_sor_step2d(Nx, Ny, st, mg->J[l], mg->Dinv[l], mg->R[l], mg->dU[l], omega);
+  for (int s = 0; s < nu1; ++s) or_sor_step2d(Nx, Ny, st, mg->J[l], mg->Dinv[l], mg->R[l], mg->dU[l], omega, K);
   or_restrict2d(Nx, Ny, st, mg->J[l], mg->R[l], mg->dU[l], mg->R[l + 1]);
   memset(mg->dU[l + 1], 0, sizeof(double) * 3 * (size_t)mg->Nx[l + 1] * mg->Ny[l + 1]);
-  int rc = mg2_vcycle(mg, l + 1, omega, nu1, nu2);
+  int rc = mg2_vcycle(mg, l + 1, omega, nu1, nu2, K);
   or_prolong2d(Nx, Ny, mg->dU[l], mg->dU[l + 1]);
-  for (int s = 0; s < nu2; ++s) or_sor_step2d(Nx, Ny, st, mg->J[l], mg->Dinv[l], mg->R[l], mg->dU[l], omega);
+  for (int s = 0; s < nu2; ++s) or_sor_step2d(Nx, Ny, st, mg->J[l], mg->Dinv[l], mg->R[l], mg->dU[l], omega, K);
   return rc;
 }
 
 int or_vcycle2d(int Nx, int Ny, int st, int nlev, const double *J, const double *R, double *dU, double omega,
-                int nu1, int nu2) {
+                int nu1, int nu2, int K) {
   or_mg2d mg;
   mg2_alloc(&mg, Nx, Ny, nlev, st);
   mg.J[0] = (double *)J;
   mg.R[0] = (double *)R;
   mg.dU[0] = dU;
   mg2_setup(&mg);
-  int rc = mg2_vcycle(&mg, 0, omega, nu1, nu2);
+  int rc = mg2_vcycle(&mg, 0, omega, nu1, nu2, K);
   mg2_free(&mg);
   return rc;
 }
@@ -544,6 +571,7 @@ typedef struct {
   int nu1[16], nu2[16]; /* smoothing steps per nested level (Section 5.2: grid dependent) */
   int nu3, levels, n_max, st, nest_start;
   double eps;
+  int colours; /* K of the diagonal smoothing schedule (cross stencils); 0: stencil colourings */
 } or_params2d;
 
 typedef struct {
@@ -574,7 +602,7 @@ static int newton_level2d(const or_grid2d *G, double *U, int nlev, const or_para
     } else {
       mg2_setup(&mg);
       for (int m = 0; m < p->nu3; ++m) {
-        if (mg2_vcycle(&mg, 0, p->omega, nu1, nu2)) { *status = 3; break; }
+        if (mg2_vcycle(&mg, 0, p->omega, nu1, nu2, p->colours)) { *status = 3; break; }
         (*vcycles)++;
       }
       if (*status) break;

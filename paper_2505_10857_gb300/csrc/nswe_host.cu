@@ -72,6 +72,7 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
     return NSWE_EINVAL;
   if (p->jacobian != NSWE_JAC_SIMPLIFIED && p->jacobian != NSWE_JAC_FULL) return NSWE_EINVAL;
   if (p->precision != NSWE_PREC_FP64 && p->precision != NSWE_PREC_MIXED) return NSWE_EINVAL;
+  if (p->colours2d != 0 && (p->colours2d < 3 || p->colours2d > 4096)) return NSWE_EINVAL;
   if (pr && pr->dim == 2 && p->precision != NSWE_PREC_FP64) return NSWE_EINVAL;
   if (pr) {
     for (int l = 0; l <= first_level && l < pr->levels; ++l)
@@ -149,10 +150,23 @@ nswe_status upload_geometry(nswe_prob p, const double *sigma_face, const double 
 
 // Symmetric multicolour smoothing of 2D level l: one step = colours 0..C-1,
 // C-1..0, twice; consecutive visits of a colour run as one pass.
-cudaError_t smooth2(const Level2Dev &Lv, int st, int steps, double omega, cudaStream_t s) {
+cudaError_t smooth2(const Level2Dev &Lv, int st, int steps, double omega, int Kc, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (Kc >= 3 && (st == ST_J9 || st == ST_P5)) {
+    // Directional schedule (the multicolour analogue of D1-D4): diagonal
+    // colourings (i + j) mod Kc ascending, (j - i + Nx - 1) mod Kc ascending,
+    // then both descending.
+    for (int t = 0; t < steps; ++t)
+      for (int d = 0; d < 4; ++d)
+        for (int q = 0; q < Kc; ++q) {
+          const int mode = (d % 2) + 1, col = d < 2 ? q : Kc - 1 - q;
+          if ((e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, mode, Kc, col, 1, s)))
+            return e;
+        }
+    return e;
+  }
   const int C = st_colours_host(st);
   int prev = -1, reps = 0;
-  cudaError_t e = cudaSuccess;
   for (int t = 0; t < steps; ++t)
     for (int pass = 0; pass < 4 * C; ++pass) {
       const int q = pass % (2 * C), col = q < C ? q : 2 * C - 1 - q;
@@ -160,12 +174,12 @@ cudaError_t smooth2(const Level2Dev &Lv, int st, int steps, double omega, cudaSt
         ++reps;
         continue;
       }
-      if (prev >= 0 && (e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, prev, reps, s)))
+      if (prev >= 0 && (e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s)))
         return e;
       prev = col;
       reps = 1;
     }
-  if (prev >= 0) e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, prev, reps, s);
+  if (prev >= 0) e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s);
   return e;
 }
 
@@ -203,7 +217,7 @@ cudaError_t mg2_setup(nswe_prob_s *p, const MG2 &m, cudaStream_t s) {
 cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2 &m, const nswe_params &prm, cudaStream_t s) {
   cudaError_t e;
   for (int l = m.l0; l < m.L; ++l) {
-    if ((e = smooth2(m.lv[l], m.st[l], prm.nu1, prm.omega, s))) return e;
+    if ((e = smooth2(m.lv[l], m.st[l], prm.nu1, prm.omega, prm.colours2d, s))) return e;
     if ((e = launch2_restrict(m.lv[l].Nx, m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].R, m.lv[l].dU, m.lv[l + 1].R,
                               m.lv[l + 1].dU, s)))
       return e;
@@ -212,7 +226,7 @@ cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2 &m, const nswe_params &prm, cud
   if ((e = launch2_dense_solve(nL, p->dense, p->piv, m.lv[m.L].R, p->xbuf, m.lv[m.L].dU, s))) return e;
   for (int l = m.L - 1; l >= m.l0; --l) {
     if ((e = launch2_prolong(m.lv[l].Nx, m.lv[l].Ny, m.lv[l].dU, m.lv[l + 1].dU, s))) return e;
-    if ((e = smooth2(m.lv[l], m.st[l], prm.nu2, prm.omega, s))) return e;
+    if ((e = smooth2(m.lv[l], m.st[l], prm.nu2, prm.omega, prm.colours2d, s))) return e;
   }
   return cudaSuccess;
 }

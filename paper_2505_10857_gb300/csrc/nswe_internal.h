@@ -78,8 +78,10 @@ cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const 
                              const double *R, double *J, cudaStream_t s);
 cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const double *Jf, double *Jc, cudaStream_t s);
 cudaError_t launch2_dinv(int n, int st, const double *J, double *Dinv, cudaStream_t s);
+// mode 0: cells of colour col of the stencil's colouring; mode 1 / 2: of the
+// diagonal colourings (i + j) mod Kc / (j - i + Nx - 1) mod Kc.
 cudaError_t launch2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
-                        double omega, int col, int reps, cudaStream_t s);
+                        double omega, int mode, int Kc, int col, int reps, cudaStream_t s);
 cudaError_t launch2_restrict(int Nx, int Ny, int st, const double *J, const double *R, const double *dU, double *Rc,
                              double *dUc, cudaStream_t s);
 cudaError_t launch2_prolong(int Nx, int Ny, double *dU, const double *dUc, cudaStream_t s);

@@ -363,37 +363,57 @@ __global__ void __launch_bounds__(kThreads) k2_dinv(int n, int st, const double 
   }
 }
 
-// Block SOR (Eq. 22) on the cells of one colour, relaxation applied reps
-// times (consecutive visits of a colour see the same neighbours).
-__global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv,
-                                                   const double *R, double *dU, double omega, int col, int reps) {
-  const int n = Nx * Ny, K = st_size(st), kc = st_center(st);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    const int i = c % Nx, j = c / Nx;
-    if (st_colour(st, i, j) != col) continue;
-    double r[3] = {R[c], R[n + c], R[2 * n + c]};
-    for (int k = 0; k < K; ++k) {
-      if (k == kc) continue;
-      const int p = i + st_off(st, k, 0), q = j + st_off(st, k, 1);
-      if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
-      const int cp = q * Nx + p;
-      const double x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
-#pragma unroll
-      for (int l = 0; l < 3; ++l)
-        r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
-                J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
-    }
-    double t[3];
+// Block SOR update (Eq. 22) of cell (i, j), relaxation applied reps times
+// (consecutive visits of a colour see the same neighbours).
+__device__ __forceinline__ void sor_cell2(int Nx, int Ny, int st, const double *J, const double *Dinv,
+                                          const double *R, double *dU, double omega, int reps, int i, int j) {
+  const int n = Nx * Ny, K = st_size(st), kc = st_center(st), c = j * Nx + i;
+  double r[3] = {R[c], R[n + c], R[2 * n + c]};
+  for (int k = 0; k < K; ++k) {
+    if (k == kc) continue;
+    const int p = i + st_off(st, k, 0), q = j + st_off(st, k, 1);
+    if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
+    const int cp = q * Nx + p;
+    const double x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      t[l] = Dinv[(size_t)(l * 3 + 0) * n + c] * r[0] + Dinv[(size_t)(l * 3 + 1) * n + c] * r[1] +
-             Dinv[(size_t)(l * 3 + 2) * n + c] * r[2];
+      r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
+              J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
+  }
+  double t[3];
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      double x = dU[l * n + c];
-      for (int s = 0; s < reps; ++s) x = (1.0 - omega) * x - omega * t[l];
-      dU[l * n + c] = x;
+  for (int l = 0; l < 3; ++l)
+    t[l] = Dinv[(size_t)(l * 3 + 0) * n + c] * r[0] + Dinv[(size_t)(l * 3 + 1) * n + c] * r[1] +
+           Dinv[(size_t)(l * 3 + 2) * n + c] * r[2];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    double x = dU[l * n + c];
+    for (int s = 0; s < reps; ++s) x = (1.0 - omega) * x - omega * t[l];
+    dU[l * n + c] = x;
+  }
+}
+
+// The cells of colour col: mode 0, the stencil's own colouring (every cell
+// tested); mode 1, (i + j) mod Kc; mode 2, (j - i + Nx - 1) mod Kc. In the
+// diagonal modes row j holds the cells i = r0 + m Kc, enumerated directly.
+__global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv,
+                                                   const double *R, double *dU, double omega, int mode, int Kc,
+                                                   int col, int reps) {
+  const int stride = gridDim.x * blockDim.x;
+  if (mode == 0) {
+    const int n = Nx * Ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+      const int i = c % Nx, j = c / Nx;
+      if (st_colour(st, i, j) == col) sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, i, j);
     }
+    return;
+  }
+  const int W = (Nx + Kc - 1) / Kc, items = W * Ny;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < items; t += stride) {
+    const int j = t / W, m = t % W;
+    const int a = mode == 1 ? col - j : j + Nx - 1 - col;
+    const int i = ((a % Kc) + Kc) % Kc + m * Kc;
+    if (i < Nx) sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, i, j);
   }
 }
 
@@ -618,8 +638,9 @@ cudaError_t launch2_dinv(int n, int st, const double *J, double *Dinv, cudaStrea
 }
 
 cudaError_t launch2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
-                        double omega, int col, int reps, cudaStream_t s) {
-  k2_sor<<<grid2((long)Nx * Ny), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, col, reps);
+                        double omega, int mode, int Kc, int col, int reps, cudaStream_t s) {
+  const long items = mode == 0 ? (long)Nx * Ny : (long)((Nx + Kc - 1) / Kc) * Ny;
+  k2_sor<<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
   return cudaGetLastError();
 }
 

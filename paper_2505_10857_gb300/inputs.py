@@ -554,3 +554,4 @@ class Params2D:
     st: int = ST_J9
     eps: float = 1e-6
     nest_start: int = -1
+    colours: int = 0  # K of the diagonal smoothing schedule for cross stencils (0: stencil colourings)

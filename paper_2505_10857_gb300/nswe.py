@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("omega", ctypes.c_double),
                 ("tol", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("nu3", ctypes.c_int),
                 ("n_max", ctypes.c_int), ("jacobian", ctypes.c_int), ("nest_start", ctypes.c_int),
-                ("precision", ctypes.c_int), ("eps", ctypes.c_double * MAX_LEVELS)]
+                ("precision", ctypes.c_int), ("colours2d", ctypes.c_int), ("eps", ctypes.c_double * MAX_LEVELS)]
 
 
 class Info(ctypes.Structure):
@@ -296,7 +296,7 @@ def params2d_from(prm, levels=None) -> Params:
     nu2 = prm.nu2[0] if hasattr(prm.nu2, "__len__") else prm.nu2
     return params(96, levels or prm.levels, alpha=prm.alpha, tau=prm.tau, omega=prm.omega, tol=prm.tol, nu1=nu1,
                   nu2=nu2, nu3=prm.nu3, n_max=prm.n_max, nb=JAC_FULL if prm.st == 1 else JAC_SIMPLIFIED,
-                  nest_start=prm.nest_start, eps=prm.eps)
+                  nest_start=prm.nest_start, eps=prm.eps, colours2d=getattr(prm, "colours", 0))
 
 
 def _host_ptr(a) -> int:

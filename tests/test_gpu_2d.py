@@ -105,9 +105,12 @@ def test_jacobian_parity_2d(nswe, ctx, orc, name, full):
     assert np.abs(host(dR) - Rref).max() <= 1e-12 * sc
 
 
-@pytest.mark.parametrize("name,level,full", [("bump", 0, False), ("bump", 1, False), ("bump", 0, True),
-                                             ("wedge", 0, False), ("mixed", 0, False)])
-def test_vcycle_parity_2d(nswe, ctx, orc, name, level, full):
+@pytest.mark.parametrize("name,level,full,colours", [("bump", 0, False, 0), ("bump", 1, False, 0),
+                                                     ("bump", 0, True, 0), ("wedge", 0, False, 0),
+                                                     ("mixed", 0, False, 0), ("bump", 0, False, 3),
+                                                     ("wedge", 0, False, 5), ("mixed", 0, False, 19),
+                                                     ("bump", 0, True, 3)])
+def test_vcycle_parity_2d(nswe, ctx, orc, name, level, full, colours):
     inp = problems()[name]
     prob = nswe.Problem2D.from_inputs(ctx, inp)
     pr = orc.problem_levels2d(inp)[level]
@@ -118,19 +121,20 @@ def test_vcycle_parity_2d(nswe, ctx, orc, name, level, full):
     rng = np.random.default_rng(31)
     dU0 = 1e-3 * rng.standard_normal((3, nx * ny))
     nlev = inp.levels - level
-    ref = orc.vcycle2d(J, R, dU0, nx, ny, st, nlev, 0.1, 3, 3)
-    prm = nswe.params(96, inp.levels, omega=0.1, nu1=3, nu2=3)
+    ref = orc.vcycle2d(J, R, dU0, nx, ny, st, nlev, 0.1, 3, 3, colours)
+    prm = nswe.params(96, inp.levels, omega=0.1, nu1=3, nu2=3, colours2d=colours)
     ddU = dev(dU0)
     nswe.nswe_mg_vcycle(ctx, prob, level, 21 if full else 9, dev(J), dev(R), ddU, prm)
     got = host(ddU)
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
 
 
-@pytest.mark.parametrize("case", ["bump_j9", "bump_j21", "wedge_direct"])
+@pytest.mark.parametrize("case", ["bump_j9", "bump_j21", "wedge_direct", "bump_j9_directional"])
 def test_newton_solve_parity_2d(nswe, ctx, orc, case):
     if case.startswith("bump"):
         inp = I.paper_parabolic_bump(32, 16, 3)
-        prm = I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400, st=orc.ST_J21 if "j21" in case else 0)
+        prm = I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400, st=orc.ST_J21 if "j21" in case else 0,
+                         colours=3 if "directional" in case else 0)
     else:
         inp = I.wedge(16, 8, 1)
         prm = I.Params2D(levels=1, nu1=[10], nu2=[10], tol=1e-11, n_max=400)

@@ -275,6 +275,55 @@ def test_sor_direct_and_two_level_cycle(orc):
         assert np.allclose(_vec(got), ref, rtol=1e-11, atol=1e-12)
 
 
+def _lexicographic_d1_d4(J, D, R, dU, Nx, Ny, st, omega, orc):
+    """The four sweeps D1-D4 of Eq. 22 written out literally: block SOR in
+    lexicographic order, i the outer loop, with the directions of the paper."""
+    off = orc.stencil2d(st)
+    dU = dU.copy()
+    order = [(range(Nx), range(Ny)), (range(Nx - 1, -1, -1), range(Ny)),
+             (range(Nx - 1, -1, -1), range(Ny - 1, -1, -1)), (range(Nx), range(Ny - 1, -1, -1))]
+    for irange, jrange in order:
+        for i in irange:
+            for j in jrange:
+                c = j * Nx + i
+                r = R[:, c].copy()
+                for k, (dx, dy) in enumerate(off):
+                    p, q = i + dx, j + dy
+                    if (dx, dy) == (0, 0) or not (0 <= p < Nx and 0 <= q < Ny):
+                        continue
+                    r += J[k, :, c].reshape(3, 3) @ dU[:, q * Nx + p]
+                dU[:, c] = (1.0 - omega) * dU[:, c] - omega * (D[:, c].reshape(3, 3) @ r)
+    return dU
+
+
+@pytest.mark.parametrize("st", [0, 2])
+def test_directional_schedule_reduces_to_the_lexicographic_sweeps(orc, st):
+    """The multicolour analogue of D1-D4 with K >= Nx + Ny - 1 diagonal colours
+    performs exactly the paper's lexicographic sweeps on the cross stencils
+    (J9 and the coarse 5-point operator); with fewer colours it still couples
+    no two cells of one colour."""
+    rng = np.random.default_rng(31 + st)
+    Nx, Ny = 7, 5
+    J = _random_op(orc, st, Nx, Ny, rng)
+    D = orc.block_inverse2d(J, st)
+    R = rng.standard_normal((3, Nx * Ny))
+    dU0 = rng.standard_normal((3, Nx * Ny))
+    ref = _lexicographic_d1_d4(J, D, R, dU0, Nx, Ny, st, 0.7, orc)
+    got = orc.sor_step2d(J, D, R, dU0, Nx, Ny, st, 0.7, colours=Nx + Ny - 1)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    few = orc.sor_step2d(J, D, R, dU0, Nx, Ny, st, 0.7, colours=3)
+    assert np.abs(few - ref).max() > 1e-8  # a different (multicolour) sequence
+    for K in (3, 4, 7):
+        for mode in (1, 2):
+            for (dx, dy) in orc.stencil2d(st):
+                if (dx, dy) == (0, 0):
+                    continue
+                for j in range(5):
+                    for i in range(5):
+                        assert orc.lib().or_diag_colour(mode, K, i + 2, j + 2, 9) != \
+                            orc.lib().or_diag_colour(mode, K, i + 2 + dx, j + 2 + dy, 9)
+
+
 def test_interp2d_conservative_and_exact_for_quadratics(orc):
     Ncx, Ncy = 6, 5
     p = I.make_problem_2d(2 * Ncx, 2 * Ncy, 2, 0.0, 1.2, 0.0, 1.0, G, I.bottom2d_flat(), (I.BC2_OUTFLOW,) * 4,
