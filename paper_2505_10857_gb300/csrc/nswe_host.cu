@@ -40,6 +40,7 @@ struct nswe_prob_s {
   double *res_dev;       // device scalar
   double *res_host;      // pinned host scalar
   int *flag_host;        // pinned host flag
+  cudaStream_t cap;      // 2D: stream on which a Newton step is captured
 };
 
 namespace {
@@ -251,29 +252,48 @@ nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, c
                                  p->host2.lev[l + 1].U, Lv.U, s))
       return NSWE_ECUDA;
     if (launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, s)) return NSWE_ECUDA;
+    // One Newton step of this level (Eq. 12-14 with Algorithm 2): the same
+    // launches every iteration, so they are captured once into a CUDA graph
+    // and replayed; the host only waits for the residual and the flag.
+    auto step = [&](cudaStream_t q) -> cudaError_t {
+      cudaError_t e;
+      if ((e = launch2_jacobian(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, Lv.J, q))) return e;
+      if ((e = cudaMemsetAsync(p->flag, 0, sizeof(int), q))) return e;
+      MG2 m = mg2_bind(p, l, st0, Lv.J, Lv.R, Lv.dU);
+      if (l == L) {
+        if ((e = launch2_dense_factor(Lv.Nx, Lv.Ny, st0, Lv.J, p->dense, p->piv, p->flag, q)) ||
+            (e = launch2_dense_solve(n, p->dense, p->piv, Lv.R, p->xbuf, Lv.dU, q)))
+          return e;
+      } else {
+        if ((e = mg2_setup(p, m, q))) return e;
+        if ((e = cudaMemsetAsync(Lv.dU, 0, sizeof(double) * 3 * n, q))) return e;
+        for (int v = 0; v < prm.nu3; ++v)
+          if ((e = mg2_vcycle(p, m, prm, q))) return e;
+      }
+      if ((e = launch2_update(n, Lv.U, Lv.dU, prm.tau, p->flag, q))) return e;
+      if ((e = launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, q))) return e;
+      if ((e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(double), cudaMemcpyDeviceToHost, q))) return e;
+      return cudaMemcpyAsync(p->flag_host, p->flag, sizeof(int), cudaMemcpyDeviceToHost, q);
+    };
+    if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) return NSWE_ECUDA;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NSWE_ECUDA;
+    const cudaError_t ce = step(p->cap);
+    if (cudaStreamEndCapture(p->cap, &graph) != cudaSuccess || ce != cudaSuccess ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return NSWE_ECUDA;
+    }
+    cudaGraphDestroy(graph);
     int it = 0, st = NSWE_OK;
     double res = 0.0;
     while (true) {
-      if (launch2_jacobian(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, Lv.J, s)) return NSWE_ECUDA;
-      cudaMemsetAsync(p->flag, 0, sizeof(int), s);
-      MG2 m = mg2_bind(p, l, st0, Lv.J, Lv.R, Lv.dU);
-      if (l == L) {
-        if (launch2_dense_factor(Lv.Nx, Lv.Ny, st0, Lv.J, p->dense, p->piv, p->flag, s) ||
-            launch2_dense_solve(n, p->dense, p->piv, Lv.R, p->xbuf, Lv.dU, s))
-          return NSWE_ECUDA;
-      } else {
-        if (mg2_setup(p, m, s)) return NSWE_ECUDA;
-        cudaMemsetAsync(Lv.dU, 0, sizeof(double) * 3 * n, s);
-        for (int v = 0; v < prm.nu3; ++v) {
-          if (mg2_vcycle(p, m, prm, s)) return NSWE_ECUDA;
-          ++inf.vcycles;
-        }
+      if (cudaGraphLaunch(exec, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return NSWE_ECUDA;
       }
-      if (launch2_update(n, Lv.U, Lv.dU, prm.tau, p->flag, s)) return NSWE_ECUDA;
-      if (launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, s)) return NSWE_ECUDA;
-      cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(p->flag_host, p->flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-      if (cudaStreamSynchronize(s) != cudaSuccess) return NSWE_ECUDA;
+      if (l != L) inf.vcycles += prm.nu3;
       res = *p->res_host;
       ++it;
       if (*p->flag_host) {
@@ -290,6 +310,7 @@ nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, c
         break;
       }
     }
+    cudaGraphExecDestroy(exec);
     inf.iters[l] = it;
     inf.res[l] = res;
     inf.level_status[l] = st;
@@ -486,6 +507,7 @@ nswe_status nswe_prob_destroy(nswe_prob prob) {
   cudaFree(prob->res_dev);
   cudaFreeHost(prob->res_host);
   cudaFreeHost(prob->flag_host);
+  if (prob->cap) cudaStreamDestroy(prob->cap);
   delete prob;
   return NSWE_OK;
 }
