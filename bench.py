@@ -464,6 +464,9 @@ def run_wedge2d(args):
             "jacobian_j21_ms": timed(lambda: nswe.nswe_jacobian_full(ctx, pb, 0, U, 1e-6, 3.0, R, J21, res), 2),
             "vcycle_j9_nu20_ms": timed(lambda: nswe.nswe_mg_vcycle(ctx, pb, 0, 9, J9, R, dU, prm), 2),
             "grid": "512x256, 7 levels"}
+    if args.phases_only:
+        print(json.dumps({"metric": "2D phase times at 512x256 (ms)", "kernels_512x256": kern}), flush=True)
+        return
     w = I.wedge(args.nx, args.ny, args.levels2d, x1=40.0, y1=30.0, x_wall=8.0, theta_deg=big.meta["theta_deg"])
     pw = nswe.Problem2D.from_inputs(ctx, w)
     p2 = nswe.params2d_from(I.Params2D(levels=args.levels2d, nu1=[20], nu2=[20], omega=args.omega2d, tol=TOL,
@@ -635,6 +638,7 @@ def main():
     ap.add_argument("--ny", type=int, default=64)
     ap.add_argument("--levels2d", type=int, default=5)
     ap.add_argument("--omega2d", type=float, default=0.01)
+    ap.add_argument("--phases-only", action="store_true", help="wedge2d: only the 512x256 phase times")
     args = ap.parse_args()
     if args.workload == "wedge2d":
         from paper_2505_10857_gb300 import build

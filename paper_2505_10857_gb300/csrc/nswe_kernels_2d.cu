@@ -393,22 +393,43 @@ __device__ __forceinline__ void sor_cell2(int Nx, int Ny, int st, const double *
   }
 }
 
-// The cells of colour col: mode 0, the stencil's own colouring (every cell
-// tested); mode 1, (i + j) mod Kc; mode 2, (j - i + Nx - 1) mod Kc. In the
-// diagonal modes row j holds the cells i = r0 + m Kc, enumerated directly.
+// The cells of colour col, enumerated directly so that every lane of a warp
+// updates a cell (an FP64 warp instruction costs the same whatever its
+// active lanes): mode 0, the stencil's own colouring; mode 1, (i + j) mod Kc;
+// mode 2, (j - i + Nx - 1) mod Kc. The J9 and 5-point colourings are mode 1
+// with Kc = 3 and 2; the J21 and 9-point colourings are tensor products of
+// residues, (i mod P) + P (j mod P) with P = 3 and 2.
+__device__ __forceinline__ void sor_items(int Nx, int Ny, int st, int &mode, int &Kc, int col, int &P, int &W,
+                                          int &items) {
+  if (mode == 0 && (st == ST_J9 || st == ST_P5)) {
+    mode = 1;
+    Kc = st == ST_J9 ? 3 : 2;
+  }
+  if (mode == 0) {
+    P = st == ST_J21 ? 3 : 2;
+    const int a = col % P, b = col / P;
+    W = Nx > a ? (Nx - a + P - 1) / P : 0;
+    const int H = Ny > b ? (Ny - b + P - 1) / P : 0;
+    items = W * H;
+  } else {
+    P = 0;
+    W = (Nx + Kc - 1) / Kc;
+    items = W * Ny;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv,
                                                    const double *R, double *dU, double omega, int mode, int Kc,
                                                    int col, int reps) {
   const int stride = gridDim.x * blockDim.x;
+  int P, W, items;
+  sor_items(Nx, Ny, st, mode, Kc, col, P, W, items);
   if (mode == 0) {
-    const int n = Nx * Ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
-      const int i = c % Nx, j = c / Nx;
-      if (st_colour(st, i, j) == col) sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, i, j);
-    }
+    const int a = col % P, b = col / P;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < items; t += stride)
+      sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, a + (t % W) * P, b + (t / W) * P);
     return;
   }
-  const int W = (Nx + Kc - 1) / Kc, items = W * Ny;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < items; t += stride) {
     const int j = t / W, m = t % W;
     const int a = mode == 1 ? col - j : j + Nx - 1 - col;
@@ -639,7 +660,11 @@ cudaError_t launch2_dinv(int n, int st, const double *J, double *Dinv, cudaStrea
 
 cudaError_t launch2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
                         double omega, int mode, int Kc, int col, int reps, cudaStream_t s) {
-  const long items = mode == 0 ? (long)Nx * Ny : (long)((Nx + Kc - 1) / Kc) * Ny;
+  // Items of the pass as the kernel enumerates them (see sor_items).
+  long items;
+  if (mode == 0 && (st == ST_J9 || st == ST_P5)) items = (long)((Nx + (st == ST_J9 ? 3 : 2) - 1) / (st == ST_J9 ? 3 : 2)) * Ny;
+  else if (mode == 0) items = (long)((Nx + 2) / (st == ST_J21 ? 3 : 2) + 1) * ((Ny + 2) / (st == ST_J21 ? 3 : 2) + 1);
+  else items = (long)((Nx + Kc - 1) / Kc) * Ny;
   k2_sor<<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
   return cudaGetLastError();
 }
