@@ -287,6 +287,14 @@ def run_gpu(args, rank, world, local_rank):
     def step(want_info=False):
         return nswe.nswe_newton_solve_batch(ctx, probs, U0s, Us, prm, want_info=want_info)
 
+    # Launch-shape autotuning on this batch (before the warm-up; not timed).
+    tune = None
+    if not args.no_autotune:
+        ms_shapes, best = nswe.nswe_autotune_solve_batch(ctx, probs, U0s, Us, prm, reps=1)
+        tune = {"shapes": ["%dx%d" % tb for tb in nswe.solve_shapes()], "ms_per_batch": ms_shapes,
+                "chosen": "%dx%d" % nswe.solve_shapes()[best],
+                "what": "threads per block x resident blocks per SM of k_solve, one timed batch each"}
+
     def barrier():
         if world > 1:
             dist.barrier()
@@ -416,6 +424,8 @@ def run_gpu(args, rank, world, local_rank):
                                          "2 x 2.07 GHz)" if mixed else "")},
             "clocks": clk,
         }
+        if tune:
+            out["autotune"] = tune
         if cpu:
             out["cpu_baseline"] = cpu
             out["parity"] = parity
@@ -626,6 +636,7 @@ def main():
     ap.add_argument("--batch", type=int, default=608, help="instances per GPU per step")
     ap.add_argument("--nb", type=int, default=3, choices=[3, 5], help="3: simplified J3, 5: full J5")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of k_solve")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d", "serve1d"])

@@ -279,6 +279,31 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count,
                                     const nswe_params *params,
                                     nswe_info *infos);
 
+/* Launch shapes of the batched 1D solve kernel (one thread block per
+ * problem): shape i has nswe_solve_shape_info(i) threads per block and is
+ * built for that many resident blocks per SM. Which shape is fastest depends
+ * on the precision, the problem sizes and the batch size; the context keeps
+ * one shape per precision (shape 0 until changed), used by
+ * nswe_newton_solve and nswe_newton_solve_batch on 1D problems. */
+int nswe_solve_shape_count(void);
+nswe_status nswe_solve_shape_info(int shape, int *threads, int *blocks_per_sm);
+nswe_status nswe_ctx_set_solve_shape(nswe_ctx ctx, int precision, int shape);
+nswe_status nswe_ctx_get_solve_shape(nswe_ctx ctx, int precision, int *shape);
+
+/* Autotuner of the launch shape (the paper has no counterpart): solves the
+ * given 1D batch once untimed and `reps` times timed (CUDA events on the
+ * context stream) in every shape, records the fastest for params->precision
+ * in the context, writes the mean milliseconds per batch of each shape to
+ * ms[nswe_solve_shape_count()] (may be NULL) and the chosen shape to *best
+ * (may be NULL). Arguments as nswe_newton_solve_batch; the solutions in Us
+ * are overwritten. Synchronises the context stream. */
+nswe_status nswe_autotune_solve_batch(nswe_ctx ctx, int count,
+                                      const nswe_prob *probs,
+                                      const double *const *U0s,
+                                      double *const *Us,
+                                      const nswe_params *params, int reps,
+                                      double *ms, int *best);
+
 /* Allocation-free nested solve. The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc, such as code running
  * after another allocator (e.g. a framework's caching allocator) has

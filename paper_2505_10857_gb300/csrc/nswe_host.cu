@@ -18,6 +18,7 @@ struct nswe_ctx_s {
   SolveTask *tasks;      // device task array
   nswe_info *infos;      // device info records
   int cap;               // capacity of tasks / infos
+  int solve_shape[2];    // launch shape of the 1D solve kernel per precision
 };
 
 struct nswe_prob_s {
@@ -774,7 +775,10 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
   if (cudaMemcpyAsync(ctx->tasks, tasks.data(), sizeof(SolveTask) * count, cudaMemcpyHostToDevice, s) !=
       cudaSuccess)
     return NSWE_ECUDA;
-  if (launch_solve(ctx->tasks, count, *params, max_coarse, s) != cudaSuccess) return NSWE_ECUDA;
+  const int shape = ctx->solve_shape[params->precision == NSWE_PREC_MIXED ? 1 : 0];
+  if (launch_solve_sized(ctx->tasks, count, *params, max_coarse, params->jacobian == NSWE_JAC_FULL ? 5 : 3, shape,
+                         s) != cudaSuccess)
+    return NSWE_ECUDA;
   if (infos) {
     if (cudaMemcpyAsync(infos, ctx->infos, sizeof(nswe_info) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return NSWE_ECUDA;
@@ -790,6 +794,69 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
 nswe_status nswe_newton_solve(nswe_ctx ctx, nswe_prob prob, const double *U0, double *U, const nswe_params *params,
                               nswe_info *info) {
   return nswe_newton_solve_batch(ctx, 1, &prob, &U0, &U, params, info);
+}
+
+int nswe_solve_shape_count(void) { return kSolveShapes; }
+
+nswe_status nswe_solve_shape_info(int shape, int *threads, int *blocks_per_sm) {
+  if (shape < 0 || shape >= kSolveShapes) return NSWE_EINVAL;
+  if (threads) *threads = kSolveShapeThreads[shape];
+  if (blocks_per_sm) *blocks_per_sm = kSolveShapeBlocks[shape];
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_set_solve_shape(nswe_ctx ctx, int precision, int shape) {
+  if (!ctx || (precision != NSWE_PREC_FP64 && precision != NSWE_PREC_MIXED) || shape < 0 || shape >= kSolveShapes)
+    return NSWE_EINVAL;
+  ctx->solve_shape[precision == NSWE_PREC_MIXED ? 1 : 0] = shape;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_get_solve_shape(nswe_ctx ctx, int precision, int *shape) {
+  if (!ctx || !shape || (precision != NSWE_PREC_FP64 && precision != NSWE_PREC_MIXED)) return NSWE_EINVAL;
+  *shape = ctx->solve_shape[precision == NSWE_PREC_MIXED ? 1 : 0];
+  return NSWE_OK;
+}
+
+nswe_status nswe_autotune_solve_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
+                                      double *const *Us, const nswe_params *params, int reps, double *ms,
+                                      int *best) {
+  if (!ctx || !params || count < 1 || reps < 1 || reps > 100) return NSWE_EINVAL;
+  if (probs[0] == nullptr || probs[0]->dim != 1) return NSWE_EINVAL;
+  const int prec = params->precision == NSWE_PREC_MIXED ? 1 : 0;
+  const int keep = ctx->solve_shape[prec];
+  DeviceGuard dg(ctx->device);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return NSWE_ECUDA;
+  }
+  nswe_status st = NSWE_OK;
+  int arg = 0;
+  double tbest = 0.0;
+  for (int shape = 0; shape < kSolveShapes && st == NSWE_OK; ++shape) {
+    ctx->solve_shape[prec] = shape;
+    st = nswe_newton_solve_batch(ctx, count, probs, U0s, Us, params, nullptr);  // untimed first run
+    if (st != NSWE_OK) break;
+    if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) st = NSWE_ECUDA;
+    for (int r = 0; r < reps && st == NSWE_OK; ++r) st = nswe_newton_solve_batch(ctx, count, probs, U0s, Us, params, nullptr);
+    float t = 0.f;
+    if (st == NSWE_OK && (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+      st = NSWE_ECUDA;
+    if (st != NSWE_OK) break;
+    const double per = (double)t / reps;
+    if (ms) ms[shape] = per;
+    if (shape == 0 || per < tbest) {
+      tbest = per;
+      arg = shape;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->solve_shape[prec] = st == NSWE_OK ? arg : keep;
+  if (st == NSWE_OK && best) *best = arg;
+  return st;
 }
 
 }  // extern "C"

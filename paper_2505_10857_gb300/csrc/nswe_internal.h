@@ -11,10 +11,14 @@ namespace nswe {
 #ifndef NSWE_THREADS
 #define NSWE_THREADS 256           // threads per block of every 1D kernel
 #endif
-#ifndef NSWE_SOLVE_MIN_BLOCKS
-#define NSWE_SOLVE_MIN_BLOCKS 4    // resident blocks per SM the solve kernel is built for
-#endif
 constexpr int kThreads = NSWE_THREADS;
+
+// Launch shapes of the persistent solve kernel, (threads per block, resident
+// blocks per SM it is built for): the register budget per thread follows
+// from the pair (65536 registers per SM). Shape 0 is the default.
+constexpr int kSolveShapes = 3;
+constexpr int kSolveShapeThreads[kSolveShapes] = {256, 128, 256};
+constexpr int kSolveShapeBlocks[kSolveShapes] = {4, 8, 2};
 constexpr int kMaxCoarse = 128;    // max cells of the coarsest level (direct solve)
 
 // One nested / multigrid level of a 1D problem. Geometry is read-only input;
@@ -129,9 +133,10 @@ cudaError_t launch_vcycle_f32(const ProbDev *p, int level, int nb, const float *
 cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                          cudaStream_t s);
 // The same with the coarsest band sized for max_nb (3 or 5) whatever prm
-// says: for batches whose tasks carry their own parameters.
+// says (for batches whose tasks carry their own parameters), in launch shape
+// `shape` (0 .. kSolveShapes-1).
 cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
-                               int max_nb, cudaStream_t s);
+                               int max_nb, int shape, cudaStream_t s);
 // Parameter checks shared by the entry points (eps of levels 0..first_level).
 nswe_status check_params_1d(const nswe_params *p, int levels, int first_level);
 

@@ -1129,8 +1129,8 @@ __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level
 // whole step is FP64; with T = float the residual, the convergence test and
 // the update U += tau dU stay FP64 while the FD Jacobian (Eq. 12-13), the
 // coarse operators, the smoother and the coarsest LU run in FP32.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, NSWE_SOLVE_MIN_BLOCKS)
+template <typename T, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_solve(const SolveTask *tasks, nswe_params launch_prm, int n_cap, int ldab_cap) {
   constexpr bool kMixed = std::is_same<T, float>::value;
   __shared__ double red[33];
@@ -1351,15 +1351,28 @@ cudaError_t launch_vcycle_f32(const ProbDev *p, int level, int nb, const float *
 
 cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                          cudaStream_t s) {
-  return launch_solve_sized(tasks, count, prm, max_coarse_cells, prm.jacobian == NSWE_JAC_FULL ? 5 : 3, s);
+  return launch_solve_sized(tasks, count, prm, max_coarse_cells, prm.jacobian == NSWE_JAC_FULL ? 5 : 3, 0, s);
 }
 
+namespace {
+template <int SHAPE>
+void launch_shape(const SolveTask *tasks, int count, const nswe_params &prm, int n_cap, int ldab_cap, size_t smem,
+                  cudaStream_t s) {
+  constexpr int TH = kSolveShapeThreads[SHAPE], MB = kSolveShapeBlocks[SHAPE];
+  if (prm.precision == NSWE_PREC_MIXED) k_solve<float, TH, MB><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+  else k_solve<double, TH, MB><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+}
+}  // namespace
+
 cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
-                               int max_nb, cudaStream_t s) {
+                               int max_nb, int shape, cudaStream_t s) {
   const int n_cap = 2 * max_coarse_cells, ldab_cap = 3 * (max_nb == 5 ? 5 : 3) + 1;
   const size_t smem = band_smem_bytes(n_cap, ldab_cap);
-  if (prm.precision == NSWE_PREC_MIXED) k_solve<float><<<count, kThreads, smem, s>>>(tasks, prm, n_cap, ldab_cap);
-  else k_solve<double><<<count, kThreads, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+  switch (shape) {
+  case 1: launch_shape<1>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
+  case 2: launch_shape<2>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
+  default: launch_shape<0>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
+  }
   return cudaGetLastError();
 }
 

@@ -337,7 +337,7 @@ bool nswe_server_s::admit_and_launch(int s) {
   const uint64_t tl = now_ns();
   if (cudaMemcpyAsync(task_dev[s], task_host[s], sizeof(SolveTask) * n, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
-      launch_solve_sized(task_dev[s], n, launch, max_coarse, max_nb, st) != cudaSuccess) {
+      launch_solve_sized(task_dev[s], n, launch, max_coarse, max_nb, 0, st) != cudaSuccess) {
     error = NSWE_ECUDA;
     return false;
   }

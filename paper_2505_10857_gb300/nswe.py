@@ -96,6 +96,12 @@ EXPORTS = {
                                      ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_noalloc": (_i, [_i, _vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D),
                                        ctypes.POINTER(BC1D), _dp, _dp, ctypes.POINTER(Params), _vp]),
+    "nswe_solve_shape_count": (_i, []),
+    "nswe_solve_shape_info": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "nswe_ctx_set_solve_shape": (_i, [_vp, _i, _i]),
+    "nswe_ctx_get_solve_shape": (_i, [_vp, _i, ctypes.POINTER(_i)]),
+    "nswe_autotune_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                                       ctypes.POINTER(Params), _i, ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "nswe_server_footprint_1d": (ctypes.c_size_t, [_i, _i, _i]),
     "nswe_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(ServerConfig)]),
     "nswe_server_submit_1d": (_i, [_vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D), ctypes.POINTER(BC1D),
@@ -357,6 +363,40 @@ def nswe_newton_solve_batch(ctx, probs: Sequence[Problem1D], U0s, Us, prm: Param
     if rc in (1, 2, 3):
         raise NsweError("nswe_newton_solve_batch", rc)
     return [infos[i].as_dict(probs[i].levels) for i in range(n)] if infos is not None else None
+
+
+def solve_shapes():
+    """[(threads per block, blocks per SM)] of the batched 1D solve kernel."""
+    out = []
+    for i in range(lib().nswe_solve_shape_count()):
+        t, b = _i(), _i()
+        _check("nswe_solve_shape_info", lib().nswe_solve_shape_info(i, ctypes.byref(t), ctypes.byref(b)))
+        out.append((t.value, b.value))
+    return out
+
+
+def nswe_ctx_set_solve_shape(ctx, precision, shape):
+    _check("nswe_ctx_set_solve_shape", lib().nswe_ctx_set_solve_shape(ctx.h, int(precision), int(shape)))
+
+
+def nswe_ctx_get_solve_shape(ctx, precision):
+    v = _i()
+    _check("nswe_ctx_get_solve_shape", lib().nswe_ctx_get_solve_shape(ctx.h, int(precision), ctypes.byref(v)))
+    return v.value
+
+
+def nswe_autotune_solve_batch(ctx, probs, U0s, Us, prm: Params, reps=2):
+    """Times every launch shape on the batch; returns (ms per shape, chosen shape)."""
+    n = len(probs)
+    ph = (_vp * n)(*[p.h.value for p in probs])
+    u0 = (_dp * n)(*[_ptr(u) for u in U0s])
+    uu = (_dp * n)(*[_ptr(u) for u in Us])
+    k = lib().nswe_solve_shape_count()
+    ms = (_d * k)()
+    best = _i()
+    _check("nswe_autotune_solve_batch", lib().nswe_autotune_solve_batch(ctx.h, n, ph, u0, uu, ctypes.byref(prm),
+                                                                        int(reps), ms, ctypes.byref(best)))
+    return [ms[i] for i in range(k)], best.value
 
 
 def nswe_newton_solve_noalloc(device, stream, N, levels, x0, x1, g, sigma_face, gauss_geom, bcl, bcr, U0, U,

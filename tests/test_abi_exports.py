@@ -70,3 +70,11 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_solve_shapes_listed():
+    from paper_2505_10857_gb300 import nswe
+    shapes = nswe.solve_shapes()
+    assert shapes[0] == (256, 4) and len(shapes) >= 2
+    for t, b in shapes:
+        assert t % 32 == 0 and t * b <= 2048 and t * b * 64 <= 65536 * 2
