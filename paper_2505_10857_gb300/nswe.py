@@ -8,8 +8,10 @@ loading raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -70,6 +72,20 @@ class ServerStats(ctypes.Structure):
 
 
 _lib = None
+
+# Live handles, closed at interpreter exit in dependency order (servers and
+# problems before the contexts they use), before CUDA is torn down.
+_live = {"server": weakref.WeakSet(), "prob": weakref.WeakSet(), "ctx": weakref.WeakSet()}
+
+
+@atexit.register
+def _close_all():
+    for kind in ("server", "prob", "ctx"):
+        for obj in list(_live[kind]):
+            try:
+                obj.close()
+            except Exception:
+                pass
 _vp, _dp, _i, _d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 
 EXPORTS = {
@@ -204,6 +220,7 @@ class Context:
         self.device = device
         self.h = _vp()
         _check("nswe_ctx_create", lib().nswe_ctx_create(ctypes.byref(self.h), int(device), _vp(stream)))
+        _live["ctx"].add(self)
 
     def set_stream(self, stream):
         _check("nswe_ctx_set_stream", lib().nswe_ctx_set_stream(self.h, _vp(stream)))
@@ -236,6 +253,7 @@ class Problem1D:
         _check("nswe_prob_create_1d", lib().nswe_prob_create_1d(
             ctx.h, ctypes.byref(self.h), self.N, self.levels, float(x0), float(x1), float(g),
             sf.ctypes.data, gq.ctypes.data, ctypes.byref(_bc(bcl)), ctypes.byref(_bc(bcr))))
+        _live["prob"].add(self)
 
     @staticmethod
     def from_inputs(ctx: Context, inp) -> "Problem1D":
@@ -275,6 +293,7 @@ class Problem2D:
         _check("nswe_prob_create_2d", lib().nswe_prob_create_2d(
             ctx.h, ctypes.byref(self.h), self.Nx, self.Ny, self.levels, float(x0), float(x1), float(y0), float(y1),
             float(g), gq.ctypes.data, kinds.ctypes.data, st.ctypes.data))
+        _live["prob"].add(self)
 
     @staticmethod
     def from_inputs(ctx: Context, inp) -> "Problem2D":
@@ -431,6 +450,7 @@ class Server:
         self.h = _vp()
         _check("nswe_server_create", lib().nswe_server_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)))
         self.N = {}
+        _live["server"].add(self)
 
     @staticmethod
     def footprint(N, levels, nest_start=-1) -> int:
