@@ -1,8 +1,8 @@
 """Launch shapes of the batched 1D solve kernel and the autotuner. Every
 shape runs the same per-cell arithmetic; the shapes are compiled with
 different register budgets, so the compiler's fused multiply-adds may differ
-and the solutions agree to a few ulps (bound 1e-13 relative), with the same
-Newton counts."""
+and FP64 solutions agree to a few ulps (bound 1e-13 relative) with the same
+Newton counts; mixed-precision solutions agree within the mixed bound."""
 import numpy as np
 import pytest
 
@@ -55,12 +55,17 @@ def test_all_shapes_agree(nswe, ctx, precision):
     finally:
         nswe.nswe_ctx_set_solve_shape(ctx, precision, 0)
         b.close()
+    # FP64: the same iterates up to those ulps. Mixed: FP32 rounding of the
+    # Jacobian and multigrid moves the Newton path, and both solves stop at
+    # res < tol, so they agree as any two converged mixed solves do.
+    bound, slack = (1e-13, 0) if precision == 0 else (1e-8, 2)
     for shape, (U, status, iters) in enumerate(results):
         assert status == [0, 0, 0], (shape, status, iters)
-        assert iters == results[0][2], (shape, iters, results[0][2])
+        for a, b in zip(iters, results[0][2]):
+            assert all(abs(x - y) <= slack for x, y in zip(a, b)), (shape, iters, results[0][2])
         for k in range(3):
             err = np.abs(U[k] - results[0][0][k]).max() / np.abs(results[0][0][k]).max()
-            assert err <= 1e-13, (shape, k, err)
+            assert err <= bound, (shape, k, err)
 
 
 def test_autotuner_picks_and_records_a_shape(nswe, ctx):
