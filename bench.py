@@ -260,6 +260,32 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------------
+# Replicas across ranks (one process per GPU): each rank solves its own instances, no collective on
+# the data path; only the timing is reduced.
+
+def replica_instances(rank, world, per_rank):
+    """Instance indices of `rank`: a disjoint block of per_rank seeds per rank."""
+    assert 0 <= rank < world and per_rank > 0
+    return rank * per_rank, per_rank
+
+
+def max_over_ranks(x, world, device=None):
+    """Max of a float over all ranks (identity for one process)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, per_rank, ms_max):
+    """Solves per second of the whole job: all ranks' instances over the slowest rank's time."""
+    return world * per_rank / (ms_max / 1000.0)
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -271,7 +297,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     B, nb = args.batch, args.nb
     mixed = args.precision == "mixed"
-    first = rank * B
+    first, _ = replica_instances(rank, world, B)
     inps, prms = make_instances(first, B, nb)
     prm = nswe.params_from(prms[0])
     prm.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
@@ -319,11 +345,8 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     per_launch = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     ms = ev[0].elapsed_time(ev[-1]) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * B / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(world, B, ms_max)
 
     # ---- one more step with per-solve records (status, iterations, device timestamps)
     infos = step(want_info=True)
@@ -382,11 +405,8 @@ def run_gpu(args, rank, world, local_rank):
         if s >= args.warmup:
             e2e_times.append(time.perf_counter() - w0)
         assert all(i["status"] == 0 for i in infos_e)
-    e2e_ms = 1000.0 * statistics.mean(e2e_times)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * B / (float(te.item()) / 1000.0)
+    e2e_ms = max_over_ranks(1000.0 * statistics.mean(e2e_times), world, dev)
+    e2e_value = whole_job_rate(world, B, e2e_ms)
 
     out = None
     if rank == 0:
@@ -413,7 +433,7 @@ def run_gpu(args, rank, world, local_rank):
             "converged": {"all_status_ok": all(s == 0 for s in status), "max_res": max(res0),
                           "mean_newton_iters": statistics.mean(i["total_iters"] for i in infos)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": float(te.item())},
+                    "ms_per_step": e2e_ms},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1000.0,
                          "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1000.0), "traffic": None,
