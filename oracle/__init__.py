@@ -377,6 +377,52 @@ def solve_problem(inp, prm):
     return nmgm1d(problem_levels(inp), inp.U0_start, params_from(prm))
 
 
+def newton_sor1d(inp, prm, max_sweeps=10, var_tol=1e-7):
+    """The Newton-SOR reference solver of Section 5.1.1 (Table 2): the nested
+    iteration of Algorithm 3 in which each regularized linear system (Eq. 13)
+    is solved on its own grid by symmetric block SOR steps (Eq. 19) from
+    dU = 0, without coarse grids; the steps stop once the l1 norm of the change
+    between two successive iterates (mean over cells, the convention of res)
+    falls below var_tol, or after max_sweeps. Returns (U, info) like
+    solve_problem."""
+    probs = problem_levels(inp)
+    L = inp.levels - 1
+    s0 = L if prm.nest_start < 0 or prm.nest_start > L else prm.nest_start
+    U = _f64(inp.U0_start).reshape(2, -1).copy()
+    info = {"status": 0, "iters": [0] * inp.levels, "res": [0.0] * inp.levels, "sweeps": 0}
+    for l in range(s0, -1, -1):
+        pr = probs[l]
+        if l < s0:
+            U = interp1d(probs[l + 1], U)
+        n, res = 0, 0.0
+        while True:
+            J, R, _ = jacobian1d(pr, U, prm.eps[l], prm.alpha, prm.nb)
+            D = block_inverse1d(J, prm.nb)
+            dU = np.zeros_like(R)
+            for _ in range(max_sweeps):
+                new = sor_step1d(J, D, R, dU, prm.omega, prm.nb, lex=getattr(prm, "lex", False))
+                var = np.abs(new - dU).sum() / pr.N
+                dU = new
+                info["sweeps"] += 1
+                if var < var_tol:
+                    break
+            U = U + prm.tau * dU
+            n += 1
+            _, res = residual1d(pr, U)
+            if not np.isfinite(res) or not (U[0] > 0).all():
+                info["status"] = 2
+                break
+            if res < prm.tol:
+                break
+            if n >= prm.n_max:
+                info["status"] = 1
+                break
+        info["iters"][l], info["res"][l] = n, res
+        if info["status"] == 2:
+            break
+    return U, info
+
+
 # ------------------------------------------------------------------------------------------------
 # Two-dimensional oracle (Section 4).
 

@@ -541,3 +541,28 @@ def test_nmgm_irregular_channel_converges(orc):
     U, info = orc.solve_problem(p, prm)
     assert info["status"] == 0 and info["res"][0] < 1e-10
     assert np.all(U[0] > 0)
+
+
+# ---------------------------------------------------------------- paper comparisons (Section 5.1.1, Table 2)
+
+@pytest.mark.slow
+def test_newton_sor_reference_and_nmgm(orc):
+    """Table 2 compares NMGM with a Newton-SOR solver (the same nested Newton
+    iteration with each linear system solved by at most 10 symmetric block SOR
+    steps on its own grid). Pins: with the paper's lexicographic sweeps both
+    reach the same fixed point and NMGM needs no more Newton iterations than
+    Newton-SOR on any grid (the paper's finding); with the data-parallel
+    multicolour ordering, single-level SOR does not solve the linear systems
+    well enough for Newton to converge on the finer grids, while NMGM does."""
+    p = I.paper_smooth_subcritical(768, levels=4)
+    prm = I.Params1D.for_problem(p, nb=3, lex=True)
+    U_mg, i_mg = orc.solve_problem(p, prm)
+    U_sor, i_sor = orc.newton_sor1d(p, prm)
+    assert i_mg["status"] == 0 and i_sor["status"] == 0
+    assert np.abs(U_mg - U_sor).max() <= 1e-9 * np.abs(U_mg).max()
+    assert all(a <= b for a, b in zip(i_mg["iters"][:4], i_sor["iters"][:4])), (i_mg["iters"], i_sor["iters"])
+    prm_mc = I.Params1D.for_problem(p, nb=3, n_max=300)
+    _, i_mc = orc.solve_problem(p, prm_mc)
+    _, i_sor_mc = orc.newton_sor1d(p, prm_mc)
+    assert i_mc["status"] == 0
+    assert i_sor_mc["status"] != 0
