@@ -143,11 +143,15 @@ def _solve_gpu(nswe, ctx, inp, prm_inputs):
     return host(U), info
 
 
-@pytest.mark.parametrize("case", ["small0", "small1", "irregular3", "eq26", "small0_j5"])
+@pytest.mark.parametrize("case", ["small0", "small1", "irregular3", "eq26", "small0_j5", "eq28_trans_const",
+                                  "eq28_trans_left", "eq28_trans_right"])
 def test_newton_solve_parity(nswe, ctx, orc, case):
     inp = {"small0": lambda: I.channel_small(0), "small1": lambda: I.channel_small(1),
            "irregular3": lambda: I.channel_irregular(3), "eq26": lambda: I.paper_smooth_subcritical(384, 3),
-           "small0_j5": lambda: I.channel_small(0)}[case]()
+           "small0_j5": lambda: I.channel_small(0),
+           "eq28_trans_const": lambda: I.paper_bump(192, levels=2, regime="trans", width="const"),
+           "eq28_trans_left": lambda: I.paper_bump(192, levels=2, regime="trans", width="left"),
+           "eq28_trans_right": lambda: I.paper_bump(192, levels=2, regime="trans", width="right")}[case]()
     prm = I.Params1D.for_problem(inp, tol=1e-10 if case != "eq26" else 1e-11, n_max=500,
                                  nb=5 if case.endswith("j5") else 3)
     Uref, iref = orc.solve_problem(inp, prm)

@@ -566,3 +566,50 @@ def test_newton_sor_reference_and_nmgm(orc):
     _, i_sor_mc = orc.newton_sor1d(p, prm_mc)
     assert i_mc["status"] == 0
     assert i_sor_mc["status"] != 0
+
+
+def _transcritical_exact_h(x, Q, g, b, sigma):
+    """Exact smooth transcritical steady state (Section 5.1.2, Table 4 setting):
+    constant discharge Q, Bernoulli u^2/2 + g (h + b) = E along the channel,
+    E fixed by critical flow at the control section where
+    E_c(x) = 1.5 (g Q / sigma)^(2/3) + g b is largest; subcritical branch
+    upstream of it, supercritical downstream. The downstream depth condition
+    acts only at the outflow boundary (no stationary jump exists for these data:
+    the supercritical branch carries more momentum than any subcritical state)."""
+    from scipy.optimize import brentq
+    xs = np.linspace(0.0, 25.0, 20001)
+    Ec = 1.5 * (g * Q / sigma(xs)) ** (2.0 / 3.0) + g * b(xs)
+    k = int(np.argmax(Ec))
+    xcrit, E = xs[k], Ec[k]
+    out = np.empty_like(x)
+    for i, xi in enumerate(x):
+        qs = Q / float(sigma(xi))
+        hc = (qs * qs / g) ** (1.0 / 3.0)
+        f = lambda h: qs * qs / (2.0 * h * h) + g * (h + float(b(xi))) - E
+        if f(hc) >= 0.0:
+            out[i] = hc
+        else:
+            out[i] = brentq(f, hc, 50.0) if xi <= xcrit else brentq(f, 1e-4, hc)
+    return out, xcrit
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("width", ["const", "left", "right"])
+def test_transcritical_flow_matches_the_exact_solution(orc, width):
+    """P9: NMGM-3 on the transcritical bump (q = 1.53, h_out = 0.66, nested from
+    96 cells as in the paper) reproduces the exact subcritical-critical-
+    supercritical profile away from the outflow boundary layer; the critical
+    point sits at the bump crest (constant width, left contraction) or at the
+    narrowest section (right contraction)."""
+    p = I.paper_bump(768, levels=4, regime="trans", width=width)
+    U, info = orc.solve_problem(p, I.Params1D.for_problem(p, tol=1e-10, n_max=800))
+    assert info["status"] == 0
+    x = p.centres(0)
+    h = U[0] / p.sig_fn(x)
+    he, xcrit = _transcritical_exact_h(x, 1.53, p.g, p.b_fn, p.sig_fn)
+    assert abs(xcrit - (15.0 if width == "right" else 10.0)) < 0.01
+    m = x < 20.0
+    assert np.abs(h - he)[m].mean() < 3e-3
+    assert np.abs(h - he)[m].max() < 1e-2
+    # constant discharge to discretisation accuracy
+    assert np.abs(U[1] - 1.53)[m].max() < 2e-2
