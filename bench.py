@@ -495,6 +495,13 @@ def run_wedge2d(args):
             "jacobian_j21_ms": timed(lambda: nswe.nswe_jacobian_full(ctx, pb, 0, U, 1e-6, 3.0, R, J21, res), 2),
             "vcycle_j9_nu20_ms": timed(lambda: nswe.nswe_mg_vcycle(ctx, pb, 0, 9, J9, R, dU, prm), 2),
             "grid": "512x256, 7 levels"}
+    # mixed precision: FP64-evaluated J9 stored in FP32, FP32 V-cycle
+    J32 = torch.zeros((9, 9, n), dtype=torch.float32, device="cuda")
+    R32, dU32 = torch.zeros((3, n), dtype=torch.float32, device="cuda"), torch.zeros((3, n), dtype=torch.float32,
+                                                                                        device="cuda")
+    kern["jacobian_j9_f32_ms"] = timed(lambda: nswe.nswe_jacobian_f32(ctx, pb, 0, 9, U, 1e-6, 3.0, R, J32, res), 3)
+    R32.copy_(R.float())
+    kern["vcycle_j9_nu20_f32_ms"] = timed(lambda: nswe.nswe_mg_vcycle_f32(ctx, pb, 0, 9, J32, R32, dU32, prm), 2)
     if args.phases_only:
         print(json.dumps({"metric": "2D phase times at 512x256 (ms)", "kernels_512x256": kern}), flush=True)
         return

@@ -91,12 +91,15 @@ typedef struct {
 #define NSWE_JAC_FULL 5       /* 1D J5: block pentadiagonal; 2D J21          */
 
 /* Arithmetic of a Newton step. The paper computes in double precision
- * (NSWE_PREC_FP64). NSWE_PREC_MIXED is this library's addition, for 1D
- * problems: the residual (Eq. 10), res, the stopping test and the update
- * (Eq. 14) stay FP64, while the FD Jacobian (Eq. 12-13), the coarse
- * operators, the smoother and the coarsest LU run in FP32. The Jacobian is an
- * approximation of the true derivative either way, so the Newton fixed point
- * R(U) = 0 is the FP64 one; only the convergence path changes. */
+ * (NSWE_PREC_FP64). NSWE_PREC_MIXED is this library's addition: the residual
+ * (Eq. 10 / Eq. 20), res, the stopping test and the update (Eq. 14) stay
+ * FP64, while the coarse operators, the smoother and the coarsest LU run in
+ * FP32. The FD Jacobian (Eq. 12-13) is evaluated in FP32 in 1D and, since
+ * the 2D perturbation eps = 1e-6 (Section 5.2) leaves no significant digits
+ * in an FP32 difference, evaluated in FP64 and stored in FP32 in 2D. The
+ * Jacobian is an approximation of the true derivative either way, so the
+ * Newton fixed point R(U) = 0 is the FP64 one; only the convergence path
+ * changes. */
 #define NSWE_PREC_FP64 0
 #define NSWE_PREC_MIXED 1
 
@@ -112,7 +115,7 @@ typedef struct {
   int n_max;      /* Newton iteration cap per nested level                  */
   int jacobian;   /* NSWE_JAC_SIMPLIFIED (J3) or NSWE_JAC_FULL (J5)         */
   int nest_start; /* nested level the solve starts on; <0: coarsest (Alg. 3)*/
-  int precision;  /* NSWE_PREC_FP64 or NSWE_PREC_MIXED (1D problems only)   */
+  int precision;  /* NSWE_PREC_FP64 or NSWE_PREC_MIXED                      */
   int colours2d;  /* 2D smoothing of the cross stencils (J9, coarse 5-point):
                      0 = two symmetric passes of the stencil colouring;
                      K >= 3 = the directional schedule, the multicolour
@@ -226,13 +229,13 @@ nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level,
                                const double *U, double eps, double alpha,
                                double *R, double *J, double *res_l1);
 
-/* The Jacobian of a NSWE_PREC_MIXED Newton step (1D problems only): R and
- * res_l1 as in nswe_residual (FP64); J the Jacobian of Eq. 12-13 with the
- * perturbed residuals evaluated in FP32 from the FP64 state, and the
- * regularization alpha*||R_j||_1 taken from the FP64 R.
- *   nb = 3 (J3) or 5 (J5); U[2][N_l] (double) in; R[2][N_l] (double) out;
- *   J[nb][4][N_l] (float) out; res_l1 (device scalar, may be NULL) out.
- *   2D problems return NSWE_EINVAL. */
+/* The Jacobian of a NSWE_PREC_MIXED Newton step: R and res_l1 as in
+ * nswe_residual (FP64); J the Jacobian of Eq. 12-13 stored in FP32, with the
+ * regularization alpha*||R_j||_1 taken from the FP64 R. 1D: the perturbed
+ * residuals are evaluated in FP32 from the FP64 state; nb = 3 (J3) or 5 (J5),
+ * U, R [2][N_l] (double), J [nb][4][N_l] (float). 2D: evaluated in FP64,
+ * rounded to FP32; nb = 9 (J9) or 21 (J21), U, R [3][n_l] (double),
+ * J [nb][9][n_l] (float). res_l1 (device scalar, may be NULL) out. */
 nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb,
                               const double *U, double eps, double alpha,
                               double *R, float *J, double *res_l1);
@@ -248,9 +251,9 @@ nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb,
                            const double *J, const double *R, double *dU,
                            const nswe_params *params);
 
-/* nswe_mg_vcycle in FP32, the linear solve of a NSWE_PREC_MIXED step (1D
- * problems only; 2D returns NSWE_EINVAL): J[nb][4][N_l], R[2][N_l] (float)
- * in; dU[2][N_l] (float) in/out. The coarse levels reuse the problem's
+/* nswe_mg_vcycle in FP32, the linear solve of a NSWE_PREC_MIXED step: J, R
+ * (float) in and dU (float) in/out in the layouts of nswe_mg_vcycle (nb = 3
+ * or 5 in 1D, 9 or 21 in 2D). The coarse levels reuse the problem's
  * workspace, which this call overwrites. */
 nswe_status nswe_mg_vcycle_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb,
                                const float *J, const float *R, float *dU,

@@ -75,7 +75,6 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
   if (p->jacobian != NSWE_JAC_SIMPLIFIED && p->jacobian != NSWE_JAC_FULL) return NSWE_EINVAL;
   if (p->precision != NSWE_PREC_FP64 && p->precision != NSWE_PREC_MIXED) return NSWE_EINVAL;
   if (p->colours2d != 0 && (p->colours2d < 3 || p->colours2d > 4096)) return NSWE_EINVAL;
-  if (pr && pr->dim == 2 && p->precision != NSWE_PREC_FP64) return NSWE_EINVAL;
   if (pr) {
     for (int l = 0; l <= first_level && l < pr->levels; ++l)
       if (!(p->eps[l] > 0.0) || !std::isfinite(p->eps[l])) return NSWE_EINVAL;
@@ -152,7 +151,23 @@ nswe_status upload_geometry(nswe_prob p, const double *sigma_face, const double 
 
 // Symmetric multicolour smoothing of 2D level l: one step = colours 0..C-1,
 // C-1..0, twice; consecutive visits of a colour run as one pass.
-cudaError_t smooth2(const Level2Dev &Lv, int st, int steps, double omega, int Kc, cudaStream_t s) {
+// One level of a 2D multigrid hierarchy in arithmetic T: in the FP32
+// instantiation (the multigrid of a mixed-precision step) the level's FP64
+// workspace arrays hold FP32 values.
+template <typename T>
+struct Lev2 {
+  int Nx, Ny;
+  T *J, *Dinv, *R, *dU;
+};
+
+template <typename T>
+Lev2<T> lev2_view(const Level2Dev &L) {
+  return Lev2<T>{L.Nx, L.Ny, reinterpret_cast<T *>(L.J), reinterpret_cast<T *>(L.Dinv), reinterpret_cast<T *>(L.R),
+                 reinterpret_cast<T *>(L.dU)};
+}
+
+template <typename T>
+cudaError_t smooth2(const Lev2<T> &Lv, int st, int steps, double omega, int Kc, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (Kc >= 3 && (st == ST_J9 || st == ST_P5)) {
     // Directional schedule (the multicolour analogue of D1-D4): diagonal
@@ -162,7 +177,7 @@ cudaError_t smooth2(const Level2Dev &Lv, int st, int steps, double omega, int Kc
       for (int d = 0; d < 4; ++d)
         for (int q = 0; q < Kc; ++q) {
           const int mode = (d % 2) + 1, col = d < 2 ? q : Kc - 1 - q;
-          if ((e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, mode, Kc, col, 1, s)))
+          if ((e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, mode, Kc, col, 1, s)))
             return e;
         }
     return e;
@@ -176,67 +191,81 @@ cudaError_t smooth2(const Level2Dev &Lv, int st, int steps, double omega, int Kc
         ++reps;
         continue;
       }
-      if (prev >= 0 && (e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s)))
+      if (prev >= 0 &&
+          (e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s)))
         return e;
       prev = col;
       reps = 1;
     }
-  if (prev >= 0) e = launch2_sor(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s);
+  if (prev >= 0) e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s);
   return e;
 }
 
 // Multigrid hierarchy from level l0 (stencil st0) to the coarsest: the
 // level-l0 arrays are J, R, dU given by the caller.
+template <typename T>
 struct MG2 {
   int l0, L;
   int st[NSWE_MAX_LEVELS];
-  Level2Dev lv[NSWE_MAX_LEVELS];
+  Lev2<T> lv[NSWE_MAX_LEVELS];
 };
 
-MG2 mg2_bind(const nswe_prob_s *p, int l0, int st0, const double *J, const double *R, double *dU) {
-  MG2 m;
+template <typename T>
+MG2<T> mg2_bind(const nswe_prob_s *p, int l0, int st0, const T *J, const T *R, T *dU) {
+  MG2<T> m;
   m.l0 = l0;
   m.L = p->levels - 1;
   for (int l = l0; l <= m.L; ++l) {
-    m.lv[l] = p->host2.lev[l];
+    m.lv[l] = lev2_view<T>(p->host2.lev[l]);
     m.st[l] = l == l0 ? st0 : st_coarse_host(m.st[l - 1]);
   }
-  m.lv[l0].J = const_cast<double *>(J);
-  m.lv[l0].R = const_cast<double *>(R);
+  m.lv[l0].J = const_cast<T *>(J);
+  m.lv[l0].R = const_cast<T *>(R);
   m.lv[l0].dU = dU;
   return m;
 }
 
-cudaError_t mg2_setup(nswe_prob_s *p, const MG2 &m, cudaStream_t s) {
+template <typename T>
+cudaError_t mg2_setup(nswe_prob_s *p, const MG2<T> &m, cudaStream_t s) {
   cudaError_t e;
   for (int l = m.l0 + 1; l <= m.L; ++l)
-    if ((e = launch2_coarse_op(m.lv[l - 1].Nx, m.lv[l - 1].Ny, m.st[l - 1], m.lv[l - 1].J, m.lv[l].J, s))) return e;
+    if ((e = launch2_coarse_op<T>(m.lv[l - 1].Nx, m.lv[l - 1].Ny, m.st[l - 1], m.lv[l - 1].J, m.lv[l].J, s)))
+      return e;
   for (int l = m.l0; l < m.L; ++l)
-    if ((e = launch2_dinv(m.lv[l].Nx * m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].Dinv, s))) return e;
-  return launch2_dense_factor(m.lv[m.L].Nx, m.lv[m.L].Ny, m.st[m.L], m.lv[m.L].J, p->dense, p->piv, p->flag, s);
+    if ((e = launch2_dinv<T>(m.lv[l].Nx * m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].Dinv, s))) return e;
+  return launch2_dense_factor<T>(m.lv[m.L].Nx, m.lv[m.L].Ny, m.st[m.L], m.lv[m.L].J,
+                                 reinterpret_cast<T *>(p->dense), p->piv, p->flag, s);
 }
 
-cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2 &m, const nswe_params &prm, cudaStream_t s) {
+template <typename T>
+cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2<T> &m, const nswe_params &prm, cudaStream_t s) {
   cudaError_t e;
   for (int l = m.l0; l < m.L; ++l) {
-    if ((e = smooth2(m.lv[l], m.st[l], prm.nu1, prm.omega, prm.colours2d, s))) return e;
-    if ((e = launch2_restrict(m.lv[l].Nx, m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].R, m.lv[l].dU, m.lv[l + 1].R,
-                              m.lv[l + 1].dU, s)))
+    if ((e = smooth2<T>(m.lv[l], m.st[l], prm.nu1, prm.omega, prm.colours2d, s))) return e;
+    if ((e = launch2_restrict<T>(m.lv[l].Nx, m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].R, m.lv[l].dU, m.lv[l + 1].R,
+                                 m.lv[l + 1].dU, s)))
       return e;
   }
   const int nL = m.lv[m.L].Nx * m.lv[m.L].Ny;
-  if ((e = launch2_dense_solve(nL, p->dense, p->piv, m.lv[m.L].R, p->xbuf, m.lv[m.L].dU, s))) return e;
+  if ((e = launch2_dense_solve<T>(nL, reinterpret_cast<const T *>(p->dense), p->piv, m.lv[m.L].R,
+                                  reinterpret_cast<T *>(p->xbuf), m.lv[m.L].dU, s)))
+    return e;
   for (int l = m.L - 1; l >= m.l0; --l) {
-    if ((e = launch2_prolong(m.lv[l].Nx, m.lv[l].Ny, m.lv[l].dU, m.lv[l + 1].dU, s))) return e;
-    if ((e = smooth2(m.lv[l], m.st[l], prm.nu2, prm.omega, prm.colours2d, s))) return e;
+    if ((e = launch2_prolong<T>(m.lv[l].Nx, m.lv[l].Ny, m.lv[l].dU, m.lv[l + 1].dU, s))) return e;
+    if ((e = smooth2<T>(m.lv[l], m.st[l], prm.nu2, prm.omega, prm.colours2d, s))) return e;
   }
   return cudaSuccess;
 }
 
 // Algorithm 3 for one 2D problem, sequenced from the host (one synchronisation
 // per Newton step for the convergence test).
-nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm,
-                    nswe_info *info) {
+// T = double: the FP64 path; T = float: mixed precision (FP64 residual,
+// stopping test and update; the FD Jacobian evaluated in FP64 and stored in
+// FP32, FP32 multigrid with the FP32 right-hand side in the upper half of
+// J's storage).
+template <typename T>
+nswe_status solve2d_t(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm,
+                      nswe_info *info) {
   cudaStream_t s = ctx->stream;
   const int L = p->levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
@@ -256,22 +285,31 @@ nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, c
     // One Newton step of this level (Eq. 12-14 with Algorithm 2): the same
     // launches every iteration, so they are captured once into a CUDA graph
     // and replayed; the host only waits for the residual and the flag.
+    constexpr bool kMixed = std::is_same<T, float>::value;
+    const int K = st0 == ST_J21 ? 21 : 9;
+    T *const J = reinterpret_cast<T *>(Lv.J);
+    T *const dU = reinterpret_cast<T *>(Lv.dU);
+    T *const Rs = kMixed ? J + (size_t)K * 9 * n : reinterpret_cast<T *>(Lv.R);
     auto step = [&](cudaStream_t q) -> cudaError_t {
       cudaError_t e;
-      if ((e = launch2_jacobian(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, Lv.J, q))) return e;
+      if ((e = launch2_jacobian<T>(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, J, q))) return e;
+      if constexpr (kMixed) {
+        if ((e = launch2_to_f32(3L * n, Lv.R, reinterpret_cast<float *>(Rs), q))) return e;
+      }
       if ((e = cudaMemsetAsync(p->flag, 0, sizeof(int), q))) return e;
-      MG2 m = mg2_bind(p, l, st0, Lv.J, Lv.R, Lv.dU);
+      MG2<T> m = mg2_bind<T>(p, l, st0, J, Rs, dU);
       if (l == L) {
-        if ((e = launch2_dense_factor(Lv.Nx, Lv.Ny, st0, Lv.J, p->dense, p->piv, p->flag, q)) ||
-            (e = launch2_dense_solve(n, p->dense, p->piv, Lv.R, p->xbuf, Lv.dU, q)))
+        if ((e = launch2_dense_factor<T>(Lv.Nx, Lv.Ny, st0, J, reinterpret_cast<T *>(p->dense), p->piv, p->flag, q)) ||
+            (e = launch2_dense_solve<T>(n, reinterpret_cast<const T *>(p->dense), p->piv, Rs,
+                                        reinterpret_cast<T *>(p->xbuf), dU, q)))
           return e;
       } else {
-        if ((e = mg2_setup(p, m, q))) return e;
-        if ((e = cudaMemsetAsync(Lv.dU, 0, sizeof(double) * 3 * n, q))) return e;
+        if ((e = mg2_setup<T>(p, m, q))) return e;
+        if ((e = cudaMemsetAsync(dU, 0, sizeof(T) * 3 * n, q))) return e;
         for (int v = 0; v < prm.nu3; ++v)
-          if ((e = mg2_vcycle(p, m, prm, q))) return e;
+          if ((e = mg2_vcycle<T>(p, m, prm, q))) return e;
       }
-      if ((e = launch2_update(n, Lv.U, Lv.dU, prm.tau, p->flag, q))) return e;
+      if ((e = launch2_update<T>(n, Lv.U, dU, prm.tau, p->flag, q))) return e;
       if ((e = launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, q))) return e;
       if ((e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(double), cudaMemcpyDeviceToHost, q))) return e;
       return cudaMemcpyAsync(p->flag_host, p->flag, sizeof(int), cudaMemcpyDeviceToHost, q);
@@ -325,6 +363,32 @@ nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, c
   inf.status = fatal ? fatal : inf.level_status[0];
   if (info) *info = inf;
   return (nswe_status)inf.status;
+}
+
+nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm,
+                    nswe_info *info) {
+  return prm.precision == NSWE_PREC_MIXED ? solve2d_t<float>(ctx, p, U0, U, prm, info)
+                                          : solve2d_t<double>(ctx, p, U0, U, prm, info);
+}
+
+// One 2D V-cycle from `level` in arithmetic T (a direct solve when `level`
+// is the coarsest).
+template <typename T>
+nswe_status vcycle2d_entry(nswe_ctx ctx, nswe_prob prob, int level, int nb, const T *J, const T *R, T *dU,
+                           const nswe_params &prm) {
+  if (nb != 9 && nb != 21) return NSWE_EINVAL;
+  MG2<T> m = mg2_bind<T>(prob, level, nb == 21 ? ST_J21 : ST_J9, J, R, dU);
+  cudaMemsetAsync(prob->flag, 0, sizeof(int), ctx->stream);
+  if (level == prob->levels - 1) {
+    const int n = nswe_prob_cells(prob, level);
+    return (launch2_dense_factor<T>(m.lv[level].Nx, m.lv[level].Ny, m.st[level], J,
+                                    reinterpret_cast<T *>(prob->dense), prob->piv, prob->flag, ctx->stream) ||
+            launch2_dense_solve<T>(n, reinterpret_cast<const T *>(prob->dense), prob->piv, R,
+                                   reinterpret_cast<T *>(prob->xbuf), dU, ctx->stream))
+               ? NSWE_ECUDA
+               : NSWE_OK;
+  }
+  return (mg2_setup<T>(prob, m, ctx->stream) || mg2_vcycle<T>(prob, m, prm, ctx->stream)) ? NSWE_ECUDA : NSWE_OK;
 }
 
 }  // namespace
@@ -652,7 +716,7 @@ static nswe_status jacobian_common(nswe_ctx ctx, nswe_prob prob, int level, int 
   if (prob->dim == 2) {
     const int n = nswe_prob_cells(prob, level);
     if (launch2_residual(prob->dev2, level, n, U, R, res, ctx->partials, ctx->stream) ||
-        launch2_jacobian(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, ctx->stream))
+        launch2_jacobian<double>(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, ctx->stream))
       return NSWE_ECUDA;
     return NSWE_OK;
   }
@@ -676,9 +740,18 @@ nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level, const do
 nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *U, double eps,
                               double alpha, double *R, float *J, double *res_l1) {
   if (!ctx || !prob || prob->ctx != ctx || !U || !R || !J || level < 0 || level >= prob->levels) return NSWE_EINVAL;
-  if (prob->dim != 1 || (nb != 3 && nb != 5)) return NSWE_EINVAL;
   if (!(eps > 0.0) || !std::isfinite(eps) || !(alpha >= 0.0) || !std::isfinite(alpha)) return NSWE_EINVAL;
   DeviceGuard dg(ctx->device);
+  if (prob->dim == 2) {
+    if (nb != 9 && nb != 21) return NSWE_EINVAL;
+    const int n = nswe_prob_cells(prob, level);
+    return (launch2_residual(prob->dev2, level, n, U, R, res_l1, ctx->partials, ctx->stream) ||
+            launch2_jacobian<float>(prob->dev2, level, n, nb == 21 ? ST_J21 : ST_J9, U, eps, alpha, R, J,
+                                    ctx->stream))
+               ? NSWE_ECUDA
+               : NSWE_OK;
+  }
+  if (nb != 3 && nb != 5) return NSWE_EINVAL;
   const int N = prob->N >> level;
   return launch_jacobian_f32(prob->dev, level, N, nb, U, eps, alpha, R, J, res_l1, ctx->partials, ctx->stream) ==
                  cudaSuccess
@@ -689,10 +762,11 @@ nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, c
 nswe_status nswe_mg_vcycle_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, const float *J, const float *R,
                                float *dU, const nswe_params *params) {
   if (!ctx || !prob || prob->ctx != ctx || !J || !R || !dU || level < 0 || level >= prob->levels) return NSWE_EINVAL;
-  if (prob->dim != 1 || (nb != 3 && nb != 5)) return NSWE_EINVAL;
   nswe_status st = check_params(params, nullptr, 0);
   if (st != NSWE_OK) return st;
   DeviceGuard dg(ctx->device);
+  if (prob->dim == 2) return vcycle2d_entry<float>(ctx, prob, level, nb, J, R, dU, *params);
+  if (nb != 3 && nb != 5) return NSWE_EINVAL;
   const int coarse = prob->N >> (prob->levels - 1);
   const int coarse_nb = (level == prob->levels - 1) ? nb : 3;
   return launch_vcycle_f32(prob->dev, level, nb, J, R, dU, *params, ctx->status, coarse, coarse_nb, ctx->stream) ==
@@ -707,20 +781,7 @@ nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb, cons
   nswe_status st = check_params(params, nullptr, 0);
   if (st != NSWE_OK) return st;
   DeviceGuard dg(ctx->device);
-  if (prob->dim == 2) {
-    if (nb != 9 && nb != 21) return NSWE_EINVAL;
-    MG2 m = mg2_bind(prob, level, nb == 21 ? ST_J21 : ST_J9, J, R, dU);
-    cudaMemsetAsync(prob->flag, 0, sizeof(int), ctx->stream);
-    if (level == prob->levels - 1) {
-      const int n = nswe_prob_cells(prob, level);
-      return (launch2_dense_factor(m.lv[level].Nx, m.lv[level].Ny, m.st[level], J, prob->dense, prob->piv,
-                                   prob->flag, ctx->stream) ||
-              launch2_dense_solve(n, prob->dense, prob->piv, R, prob->xbuf, dU, ctx->stream))
-                 ? NSWE_ECUDA
-                 : NSWE_OK;
-    }
-    return (mg2_setup(prob, m, ctx->stream) || mg2_vcycle(prob, m, *params, ctx->stream)) ? NSWE_ECUDA : NSWE_OK;
-  }
+  if (prob->dim == 2) return vcycle2d_entry<double>(ctx, prob, level, nb, J, R, dU, *params);
   if (nb != 3 && nb != 5) return NSWE_EINVAL;
   const int coarse = prob->N >> (prob->levels - 1);
   const int coarse_nb = (level == prob->levels - 1) ? nb : 3;

@@ -78,22 +78,32 @@ struct ProbDev2 {
 
 cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *U, double *R, double *res,
                              double *partials, cudaStream_t s);
+// Multigrid launchers for T = double (FP64 path) and T = float (the multigrid
+// of a mixed-precision step); the Jacobian may be stored in either.
+template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, double *J, cudaStream_t s);
-cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const double *Jf, double *Jc, cudaStream_t s);
-cudaError_t launch2_dinv(int n, int st, const double *J, double *Dinv, cudaStream_t s);
+                             const double *R, TJ *J, cudaStream_t s);
+template <typename T>
+cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, cudaStream_t s);
+template <typename T>
+cudaError_t launch2_dinv(int n, int st, const T *J, T *Dinv, cudaStream_t s);
 // mode 0: cells of colour col of the stencil's colouring; mode 1 / 2: of the
 // diagonal colourings (i + j) mod Kc / (j - i + Nx - 1) mod Kc.
-cudaError_t launch2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
-                        double omega, int mode, int Kc, int col, int reps, cudaStream_t s);
-cudaError_t launch2_restrict(int Nx, int Ny, int st, const double *J, const double *R, const double *dU, double *Rc,
-                             double *dUc, cudaStream_t s);
-cudaError_t launch2_prolong(int Nx, int Ny, double *dU, const double *dUc, cudaStream_t s);
-cudaError_t launch2_dense_factor(int Nx, int Ny, int st, const double *J, double *A, int *piv, int *flag,
-                                 cudaStream_t s);
-cudaError_t launch2_dense_solve(int n, const double *A, const int *piv, const double *R, double *x, double *dU,
-                                cudaStream_t s);
-cudaError_t launch2_update(int n, double *U, const double *dU, double tau, int *flag, cudaStream_t s);
+template <typename T>
+cudaError_t launch2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU, double omega, int mode,
+                        int Kc, int col, int reps, cudaStream_t s);
+template <typename T>
+cudaError_t launch2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch2_prolong(int Nx, int Ny, T *dU, const T *dUc, cudaStream_t s);
+template <typename T>
+cudaError_t launch2_dense_factor(int Nx, int Ny, int st, const T *J, T *A, int *piv, int *flag, cudaStream_t s);
+template <typename T>
+cudaError_t launch2_dense_solve(int n, const T *A, const int *piv, const T *R, T *x, T *dU, cudaStream_t s);
+template <typename T>
+cudaError_t launch2_update(int n, double *U, const T *dU, double tau, int *flag, cudaStream_t s);
+cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream_t s);
 cudaError_t launch2_interp(const ProbDev2 *p, int coarse_level, int nc, const double *Uc, double *Uf,
                            cudaStream_t s);
 

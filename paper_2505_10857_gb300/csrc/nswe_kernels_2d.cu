@@ -289,8 +289,9 @@ __global__ void k2_finish(const double *partials, int nparts, int n, double *res
 }
 
 // One item = (cell, stencil block k): three perturbed local residuals.
+template <typename TJ>
 __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int level, int st, const double *U,
-                                                        double eps, double alpha, const double *R, double *J) {
+                                                        double eps, double alpha, const double *R, TJ *J) {
   const Geo2 G = make_geo2(*P, level);
   const int n = G.Nx * G.Ny, K = st_size(st), kc = st_center(st);
   const double ieps = 1.0 / eps;
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
     const int c = it % n, k = it / n, i = c % G.Nx, j = c / G.Nx;
     const int pi = i + st_off(st, k, 0), pj = j + st_off(st, k, 1);
     if (pi < 0 || pi >= G.Nx || pj < 0 || pj >= G.Ny) {
-      for (int e = 0; e < 9; ++e) J[(size_t)(k * 9 + e) * n + c] = 0.0;
+      for (int e = 0; e < 9; ++e) J[(size_t)(k * 9 + e) * n + c] = TJ(0.0);
       continue;
     }
     const double R0[3] = {R[c], R[n + c], R[2 * n + c]};
@@ -311,20 +312,21 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
       for (int l = 0; l < 3; ++l) {
         double v = (Rp[l] - R0[l]) * ieps;
         if (l == m) v += reg;
-        J[(size_t)(k * 9 + l * 3 + m) * n + c] = v;
+        J[(size_t)(k * 9 + l * 3 + m) * n + c] = TJ(v);
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st, const double *Jf, double *Jc) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc) {
   const int n = Nx * Ny, Ncx = Nx / 2, Ncy = Ny / 2, nc = Ncx * Ncy, K = st_size(st), cs = st_coarse(st),
             Kc = st_size(cs);
   for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += gridDim.x * blockDim.x) {
     const int I = cc % Ncx, Jy = cc / Ncx;
-    double acc[9][9];
+    T acc[9][9];
     for (int t = 0; t < Kc; ++t)
-      for (int e = 0; e < 9; ++e) acc[t][e] = 0.0;
+      for (int e = 0; e < 9; ++e) acc[t][e] = T(0.0);
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         const int xi = 2 * I + a, yi = 2 * Jy + b, c = yi * Nx + xi;
@@ -344,13 +346,14 @@ __global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st,
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k2_dinv(int n, int st, const double *J, double *Dinv) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_dinv(int n, int st, const T *J, T *Dinv) {
   const int kc = st_center(st);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    double a[9];
+    T a[9];
     for (int e = 0; e < 9; ++e) a[e] = J[(size_t)(kc * 9 + e) * n + c];
-    const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
-    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    const T c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    const T det = a[0] * c00 + a[1] * c01 + a[2] * c02;
     Dinv[0 * (size_t)n + c] = c00 / det;
     Dinv[1 * (size_t)n + c] = (a[2] * a[7] - a[1] * a[8]) / det;
     Dinv[2 * (size_t)n + c] = (a[1] * a[5] - a[2] * a[4]) / det;
@@ -365,30 +368,32 @@ __global__ void __launch_bounds__(kThreads) k2_dinv(int n, int st, const double 
 
 // Block SOR update (Eq. 22) of cell (i, j), relaxation applied reps times
 // (consecutive visits of a colour see the same neighbours).
-__device__ __forceinline__ void sor_cell2(int Nx, int Ny, int st, const double *J, const double *Dinv,
-                                          const double *R, double *dU, double omega, int reps, int i, int j) {
+template <typename T>
+__device__ __forceinline__ void sor_cell2(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU,
+                                          double omega_d, int reps, int i, int j) {
+  const T omega = T(omega_d);
   const int n = Nx * Ny, K = st_size(st), kc = st_center(st), c = j * Nx + i;
-  double r[3] = {R[c], R[n + c], R[2 * n + c]};
+  T r[3] = {R[c], R[n + c], R[2 * n + c]};
   for (int k = 0; k < K; ++k) {
     if (k == kc) continue;
     const int p = i + st_off(st, k, 0), q = j + st_off(st, k, 1);
     if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
     const int cp = q * Nx + p;
-    const double x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
+    const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
       r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
               J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
   }
-  double t[3];
+  T t[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l)
     t[l] = Dinv[(size_t)(l * 3 + 0) * n + c] * r[0] + Dinv[(size_t)(l * 3 + 1) * n + c] * r[1] +
            Dinv[(size_t)(l * 3 + 2) * n + c] * r[2];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    double x = dU[l * n + c];
-    for (int s = 0; s < reps; ++s) x = (1.0 - omega) * x - omega * t[l];
+    T x = dU[l * n + c];
+    for (int s = 0; s < reps; ++s) x = (T(1.0) - omega) * x - omega * t[l];
     dU[l * n + c] = x;
   }
 }
@@ -418,9 +423,9 @@ __device__ __forceinline__ void sor_items(int Nx, int Ny, int st, int &mode, int
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv,
-                                                   const double *R, double *dU, double omega, int mode, int Kc,
-                                                   int col, int reps) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R,
+                                                   T *dU, double omega, int mode, int Kc, int col, int reps) {
   const int stride = gridDim.x * blockDim.x;
   int P, W, items;
   sor_items(Nx, Ny, st, mode, Kc, col, P, W, items);
@@ -438,21 +443,22 @@ __global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, const double *J, const double *R,
-                                                        const double *dU, double *Rc, double *dUc) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU,
+                                                        T *Rc, T *dUc) {
   const int n = Nx * Ny, Ncx = Nx / 2, nc = Ncx * (Ny / 2), K = st_size(st);
   for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += gridDim.x * blockDim.x) {
     const int I = cc % Ncx, Jy = cc / Ncx;
-    double s[3] = {0.0, 0.0, 0.0};
+    T s[3] = {T(0.0), T(0.0), T(0.0)};
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         const int xi = 2 * I + a, yi = 2 * Jy + b, c = yi * Nx + xi;
-        double r[3] = {R[c], R[n + c], R[2 * n + c]};
+        T r[3] = {R[c], R[n + c], R[2 * n + c]};
         for (int k = 0; k < K; ++k) {
           const int p = xi + st_off(st, k, 0), q = yi + st_off(st, k, 1);
           if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
           const int cp = q * Nx + p;
-          const double x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
+          const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
 #pragma unroll
           for (int l = 0; l < 3; ++l)
             r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
@@ -465,12 +471,13 @@ __global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, 
     // the oracle accumulates the four children in row-major fine order
     for (int l = 0; l < 3; ++l) {
       Rc[l * nc + cc] = s[l];
-      dUc[l * nc + cc] = 0.0;
+      dUc[l * nc + cc] = T(0.0);
     }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k2_prolong(int Nx, int Ny, double *dU, const double *dUc) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_prolong(int Nx, int Ny, T *dU, const T *dUc) {
   const int n = Nx * Ny, Ncx = Nx / 2, nc = Ncx * (Ny / 2);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
     const int cc = (c / Nx / 2) * Ncx + (c % Nx) / 2;
@@ -480,11 +487,13 @@ __global__ void __launch_bounds__(kThreads) k2_prolong(int Nx, int Ny, double *d
 
 // Dense system A (row-major, unknown 3c+m) assembled from a block operator:
 // zero it, then scatter the blocks.
-__global__ void __launch_bounds__(kThreads) k2_zero(long count, double *A) {
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) A[t] = 0.0;
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_zero(long count, T *A) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) A[t] = T(0.0);
 }
 
-__global__ void __launch_bounds__(kThreads) k2_scatter(int Nx, int Ny, int st, const double *J, double *A) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_scatter(int Nx, int Ny, int st, const T *J, T *A) {
   const int n = Nx * Ny, N3 = 3 * n, K = st_size(st);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * K; t += gridDim.x * blockDim.x) {
     const int c = t % n, k = t / n, i = c % Nx, j = c / Nx;
@@ -498,22 +507,23 @@ __global__ void __launch_bounds__(kThreads) k2_scatter(int Nx, int Ny, int st, c
 
 // LU with partial pivoting (ties to the lowest row) of A (n x n, global
 // memory), one thread block. piv[k] = pivot row; flag = 1 on an exact zero pivot.
-__global__ void __launch_bounds__(kThreads) k2_lu(int N3, double *A, int *piv, int *flag) {
-  __shared__ double sv[32];
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_lu(int N3, T *A, int *piv, int *flag) {
+  __shared__ T sv[32];
   __shared__ int si[32];
   __shared__ int s_p;
   for (int k = 0; k < N3; ++k) {
-    double best = -1.0;
+    T best = T(-1.0);
     int bi = N3;
     for (int i = k + threadIdx.x; i < N3; i += blockDim.x) {
-      const double v = fabs(A[(size_t)i * N3 + k]);
+      const T v = fabs(A[(size_t)i * N3 + k]);
       if (v > best) {
         best = v;
         bi = i;
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const T ov = __shfl_down_sync(0xffffffffu, best, o);
       const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) {
         best = ov;
@@ -526,7 +536,7 @@ __global__ void __launch_bounds__(kThreads) k2_lu(int N3, double *A, int *piv, i
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double b = sv[0];
+      T b = sv[0];
       int p = si[0];
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
         if (sv[w] > b || (sv[w] == b && si[w] < p)) {
@@ -535,7 +545,7 @@ __global__ void __launch_bounds__(kThreads) k2_lu(int N3, double *A, int *piv, i
         }
       s_p = p;
       piv[k] = p;
-      if (A[(size_t)p * N3 + k] == 0.0) *flag = 1;
+      if (A[(size_t)p * N3 + k] == T(0.0)) *flag = 1;
     }
     __syncthreads();
     const int p = s_p;
@@ -543,12 +553,12 @@ __global__ void __launch_bounds__(kThreads) k2_lu(int N3, double *A, int *piv, i
     // computed, which is what the interleaved forward solve expects.
     if (p != k)
       for (int c = k + threadIdx.x; c < N3; c += blockDim.x) {
-        const double t = A[(size_t)k * N3 + c];
+        const T t = A[(size_t)k * N3 + c];
         A[(size_t)k * N3 + c] = A[(size_t)p * N3 + c];
         A[(size_t)p * N3 + c] = t;
       }
     __syncthreads();
-    const double d = A[(size_t)k * N3 + k];
+    const T d = A[(size_t)k * N3 + k];
     for (int i = k + 1 + threadIdx.x; i < N3; i += blockDim.x) A[(size_t)i * N3 + k] = A[(size_t)i * N3 + k] / d;
     __syncthreads();
     const int rows = N3 - k - 1;
@@ -561,7 +571,8 @@ __global__ void __launch_bounds__(kThreads) k2_lu(int N3, double *A, int *piv, i
 }
 
 // dU = -A^{-1} R with the factors (one warp; unknown 3c+m).
-__global__ void k2_lu_solve(int n, const double *A, const int *piv, const double *R, double *x, double *dU) {
+template <typename T>
+__global__ void k2_lu_solve(int n, const T *A, const int *piv, const T *R, T *x, T *dU) {
   const int N3 = 3 * n, lane = threadIdx.x;
   if (threadIdx.x >= 32) return;
   for (int t = lane; t < n; t += 32)
@@ -570,17 +581,17 @@ __global__ void k2_lu_solve(int n, const double *A, const int *piv, const double
   for (int k = 0; k < N3; ++k) {
     const int p = piv[k];
     if (lane == 0 && p != k) {
-      const double t = x[k];
+      const T t = x[k];
       x[k] = x[p];
       x[p] = t;
     }
     __syncwarp();
-    const double xk = x[k];
+    const T xk = x[k];
     for (int i = k + 1 + lane; i < N3; i += 32) x[i] -= A[(size_t)i * N3 + k] * xk;
     __syncwarp();
   }
   for (int i = N3 - 1; i >= 0; --i) {
-    double s = 0.0;
+    T s = T(0.0);
     for (int c = i + 1 + lane; c < N3; c += 32) s += A[(size_t)i * N3 + c] * x[c];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) x[i] = (x[i] - s) / A[(size_t)i * N3 + i];
@@ -590,12 +601,18 @@ __global__ void k2_lu_solve(int n, const double *A, const int *piv, const double
     for (int m = 0; m < 3; ++m) dU[m * n + t] = x[3 * t + m];
 }
 
-__global__ void __launch_bounds__(kThreads) k2_update(int n, double *U, const double *dU, double tau, int *flag) {
+__global__ void __launch_bounds__(kThreads) k2_to_f32(long count, const double *src, float *dst) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x)
+    dst[t] = float(src[t]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_update(int n, double *U, const T *dU, double tau, int *flag) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    const double h = U[c] + tau * dU[c];
+    const double h = U[c] + tau * double(dU[c]);
     U[c] = h;
-    U[n + c] += tau * dU[n + c];
-    U[2 * n + c] += tau * dU[2 * n + c];
+    U[n + c] += tau * double(dU[n + c]);
+    U[2 * n + c] += tau * double(dU[2 * n + c]);
     if (!(h > 0.0)) atomicOr(flag, 1);
   }
 }
@@ -642,63 +659,92 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
   return cudaGetLastError();
 }
 
+template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, double *J, cudaStream_t s) {
-  k2_jacobian<<<grid2((long)n * (st == ST_J21 ? 21 : 9)), kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
+                             const double *R, TJ *J, cudaStream_t s) {
+  k2_jacobian<TJ><<<grid2((long)n * (st == ST_J21 ? 21 : 9)), kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const double *Jf, double *Jc, cudaStream_t s) {
-  k2_coarse_op<<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, Jf, Jc);
+template <typename T>
+cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, cudaStream_t s) {
+  k2_coarse_op<T><<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, Jf, Jc);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_dinv(int n, int st, const double *J, double *Dinv, cudaStream_t s) {
-  k2_dinv<<<grid2(n), kThreads, 0, s>>>(n, st, J, Dinv);
+template <typename T>
+cudaError_t launch2_dinv(int n, int st, const T *J, T *Dinv, cudaStream_t s) {
+  k2_dinv<T><<<grid2(n), kThreads, 0, s>>>(n, st, J, Dinv);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_sor(int Nx, int Ny, int st, const double *J, const double *Dinv, const double *R, double *dU,
-                        double omega, int mode, int Kc, int col, int reps, cudaStream_t s) {
+template <typename T>
+cudaError_t launch2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU, double omega, int mode,
+                        int Kc, int col, int reps, cudaStream_t s) {
   // Items of the pass as the kernel enumerates them (see sor_items).
   long items;
   if (mode == 0 && (st == ST_J9 || st == ST_P5)) items = (long)((Nx + (st == ST_J9 ? 3 : 2) - 1) / (st == ST_J9 ? 3 : 2)) * Ny;
   else if (mode == 0) items = (long)((Nx + 2) / (st == ST_J21 ? 3 : 2) + 1) * ((Ny + 2) / (st == ST_J21 ? 3 : 2) + 1);
   else items = (long)((Nx + Kc - 1) / Kc) * Ny;
-  k2_sor<<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+  k2_sor<T><<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_restrict(int Nx, int Ny, int st, const double *J, const double *R, const double *dU, double *Rc,
-                             double *dUc, cudaStream_t s) {
-  k2_restrict<<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, J, R, dU, Rc, dUc);
+template <typename T>
+cudaError_t launch2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc,
+                             cudaStream_t s) {
+  k2_restrict<T><<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, J, R, dU, Rc, dUc);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_prolong(int Nx, int Ny, double *dU, const double *dUc, cudaStream_t s) {
-  k2_prolong<<<grid2((long)Nx * Ny), kThreads, 0, s>>>(Nx, Ny, dU, dUc);
+template <typename T>
+cudaError_t launch2_prolong(int Nx, int Ny, T *dU, const T *dUc, cudaStream_t s) {
+  k2_prolong<T><<<grid2((long)Nx * Ny), kThreads, 0, s>>>(Nx, Ny, dU, dUc);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_dense_factor(int Nx, int Ny, int st, const double *J, double *A, int *piv, int *flag,
-                                 cudaStream_t s) {
+template <typename T>
+cudaError_t launch2_dense_factor(int Nx, int Ny, int st, const T *J, T *A, int *piv, int *flag, cudaStream_t s) {
   const long N3 = 3L * Nx * Ny;
-  k2_zero<<<grid2(N3 * N3), kThreads, 0, s>>>(N3 * N3, A);
-  k2_scatter<<<grid2((long)Nx * Ny * (st == ST_J21 ? 21 : 9)), kThreads, 0, s>>>(Nx, Ny, st, J, A);
-  k2_lu<<<1, kThreads, 0, s>>>((int)N3, A, piv, flag);
+  k2_zero<T><<<grid2(N3 * N3), kThreads, 0, s>>>(N3 * N3, A);
+  k2_scatter<T><<<grid2((long)Nx * Ny * (st == ST_J21 ? 21 : 9)), kThreads, 0, s>>>(Nx, Ny, st, J, A);
+  k2_lu<T><<<1, kThreads, 0, s>>>((int)N3, A, piv, flag);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_dense_solve(int n, const double *A, const int *piv, const double *R, double *x, double *dU,
-                                cudaStream_t s) {
-  k2_lu_solve<<<1, 32, 0, s>>>(n, A, piv, R, x, dU);
+template <typename T>
+cudaError_t launch2_dense_solve(int n, const T *A, const int *piv, const T *R, T *x, T *dU, cudaStream_t s) {
+  k2_lu_solve<T><<<1, 32, 0, s>>>(n, A, piv, R, x, dU);
   return cudaGetLastError();
 }
 
-cudaError_t launch2_update(int n, double *U, const double *dU, double tau, int *flag, cudaStream_t s) {
-  k2_update<<<grid2(n), kThreads, 0, s>>>(n, U, dU, tau, flag);
+template <typename T>
+cudaError_t launch2_update(int n, double *U, const T *dU, double tau, int *flag, cudaStream_t s) {
+  k2_update<T><<<grid2(n), kThreads, 0, s>>>(n, U, dU, tau, flag);
   return cudaGetLastError();
 }
+
+cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream_t s) {
+  k2_to_f32<<<grid2(count), kThreads, 0, s>>>(count, src, dst);
+  return cudaGetLastError();
+}
+
+#define NSWE_2D_INSTANTIATE(T)                                                                                    \
+  template cudaError_t launch2_jacobian<T>(const ProbDev2 *, int, int, int, const double *, double, double,      \
+                                           const double *, T *, cudaStream_t);                                   \
+  template cudaError_t launch2_coarse_op<T>(int, int, int, const T *, T *, cudaStream_t);                        \
+  template cudaError_t launch2_dinv<T>(int, int, const T *, T *, cudaStream_t);                                  \
+  template cudaError_t launch2_sor<T>(int, int, int, const T *, const T *, const T *, T *, double, int, int, int, \
+                                      int, cudaStream_t);                                                        \
+  template cudaError_t launch2_restrict<T>(int, int, int, const T *, const T *, const T *, T *, T *,             \
+                                           cudaStream_t);                                                        \
+  template cudaError_t launch2_prolong<T>(int, int, T *, const T *, cudaStream_t);                               \
+  template cudaError_t launch2_dense_factor<T>(int, int, int, const T *, T *, int *, int *, cudaStream_t);       \
+  template cudaError_t launch2_dense_solve<T>(int, const T *, const int *, const T *, T *, T *, cudaStream_t);    \
+  template cudaError_t launch2_update<T>(int, double *, const T *, double, int *, cudaStream_t);
+NSWE_2D_INSTANTIATE(double)
+NSWE_2D_INSTANTIATE(float)
+#undef NSWE_2D_INSTANTIATE
 
 cudaError_t launch2_interp(const ProbDev2 *p, int coarse_level, int nc, const double *Uc, double *Uf,
                            cudaStream_t s) {

@@ -58,7 +58,7 @@ nswe_status scratch_address(int device, double **out) {
   return NSWE_OK;
 }
 
-// Writes the problem description and the task into the scratch array and
+// Writes the problem description and its SolveTask record into the scratch array and
 // gathers the face widths of every level from the finest ones.
 __global__ void k_noalloc_setup(ProbDev P, SolveTask T, ProbDev *prob_slot, SolveTask *task_slot,
                                 const double *sigma_face) {

@@ -175,15 +175,77 @@ def test_mixed_batch_equals_single(nswe, ctx):
         assert np.array_equal(host(Us[k]), singles[k])
 
 
-def test_mixed_rejected_for_2d(nswe, ctx):
-    inp = I.paper_parabolic_bump(16, 8, 2)
+# ---------------------------------------------------------------- 2D
+
+def _state2d(inp, level, seed):
+    rng = np.random.default_rng(seed)
+    X, Y = inp.centres(level)
+    s0 = inp.bc_state[0]
+    h = 1.2 + 0.2 * np.sin(X) * np.cos(Y) + 0.01 * rng.standard_normal(X.shape)
+    hu = (s0[1] if s0[1] else 1.0) * (1 + 0.05 * np.cos(Y + X)) + 0.02 * rng.standard_normal(X.shape)
+    hv = 0.1 * np.sin(X) + 0.02 * rng.standard_normal(X.shape)
+    return np.ascontiguousarray(np.stack([h.ravel(), hu.ravel(), hv.ravel()]))
+
+
+def _flux_scale2(U, g, d):
+    h, m = np.abs(U[0]).max(), np.abs(U[1:]).max()
+    return (m * m / np.abs(U[0]).min() + 0.5 * g * h * h + m) / d
+
+
+@pytest.mark.parametrize("nb", [9, 21])
+def test_jacobian_f32_parity_2d(nswe, ctx, orc, nb):
+    """2D: the FD Jacobian is evaluated in FP64 (eps = 1e-6 leaves nothing to
+    difference in FP32) and rounded to FP32: the FP64 bound plus one FP32
+    rounding (2^-24 relative) per entry."""
+    inp = I.wedge(32, 16, 2)
     prob = nswe.Problem2D.from_inputs(ctx, inp)
-    p = nswe.params2d_from(I.Params2D(levels=2))
+    pr = orc.problem_levels2d(inp)[0]
+    U = _state2d(inp, 0, 20)
+    Jref, Rref, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, orc.ST_J21 if nb == 21 else orc.ST_J9)
+    dR = torch.zeros((3, pr.n), dtype=torch.float64, device="cuda")
+    dJ = torch.full((nb, 9, pr.n), float("nan"), dtype=torch.float32, device="cuda")
+    nswe.nswe_jacobian_f32(ctx, prob, 0, nb, dev(U), 1e-6, 3.0, dR, dJ)
+    J = host(dJ)
+    sc = _flux_scale2(U, inp.g, min(pr.s.dx, pr.s.dy))
+    assert np.abs(host(dR) - Rref).max() <= 1e-12 * sc
+    tol = 1e-12 * np.abs(Jref).max() + 8.0 * 2.0 ** -52 * sc / 1e-6 + EPS32 * np.abs(Jref)
+    assert np.isfinite(J).all()
+    assert (np.abs(J - Jref) <= tol).all(), np.abs(J - Jref).max()
+
+
+@pytest.mark.parametrize("name,colours", [("bump", 0), ("wedge", 0), ("bump", 3)])
+def test_vcycle_f32_parity_2d(nswe, ctx, orc, name, colours):
+    inp = {"bump": I.paper_parabolic_bump(32, 16, 3), "wedge": I.wedge(32, 16, 2)}[name]
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    pr = orc.problem_levels2d(inp)[0]
+    J, R, _ = orc.jacobian2d(pr, _state2d(inp, 0, 30), 1e-6, 3.0, orc.ST_J9)
+    J = J.astype(np.float32).astype(np.float64)
+    R = R.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(31)
+    dU0 = (1e-3 * rng.standard_normal((3, pr.n))).astype(np.float32).astype(np.float64)
+    nx, ny = inp.dims(0)
+    ref = orc.vcycle2d(J, R, dU0, nx, ny, orc.ST_J9, inp.levels, 0.1, 3, 3, colours)
+    prm = nswe.params(96, inp.levels, omega=0.1, nu1=3, nu2=3, colours2d=colours)
+    ddU = dev(dU0, torch.float32)
+    nswe.nswe_mg_vcycle_f32(ctx, prob, 0, 9, dev(J, torch.float32), dev(R, torch.float32), ddU, prm)
+    err = np.abs(host(ddU) - ref).max() / np.abs(ref).max()
+    assert err <= 2.0 ** -16, err
+
+
+def test_mixed_newton_solve_2d(nswe, ctx, orc):
+    inp = I.paper_parabolic_bump(32, 16, 3)
+    prm = I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400)
+    Uref, iref = orc.solve_problem2d(inp, prm)
+    assert iref["status"] == 0
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    p = nswe.params2d_from(prm)
     p.precision = nswe.PREC_MIXED
-    U = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
-    with pytest.raises(nswe.NsweError):
-        nswe.nswe_newton_solve(ctx, prob, dev(inp.U0_start), U, p, raise_on_status=True)
-    J = torch.zeros((3, 4, 16), dtype=torch.float32, device="cuda")
-    with pytest.raises(nswe.NsweError):
-        nswe.nswe_mg_vcycle_f32(ctx, prob, 0, 3, J, J[0, :2].contiguous(), J[1, :2].contiguous(),
-                                nswe.params(96, 2))
+    dU = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
+    info = nswe.nswe_newton_solve(ctx, prob, dev(inp.U0_start), dU, p)
+    U = host(dU)
+    assert info["status"] == 0, info
+    _, res = orc.residual2d(orc.problem_levels2d(inp)[0], U)
+    assert res < prm.tol, res
+    assert np.abs(U - Uref).max() / np.abs(Uref).max() <= MIXED_BOUND
+    for l in range(inp.levels):
+        assert abs(info["iters"][l] - iref["iters"][l]) <= 2 + iref["iters"][l] // 10, (info["iters"], iref["iters"])
