@@ -40,6 +40,10 @@ TOL = 1e-10
 MIXED_BOUND = 1e-8  # solution distance of two solves that both reach res < TOL by different paths
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x FP64 FMA/clk/SM x 2 flop x max SM GHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM GHz
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_solve launch of the default step
+# (608 channel solves, J3, shape 256x4), from a one-pass ncu capture of `bench.py --steps 1 --warmup 3
+# --no-cpu --no-autotune [--precision mixed]`; summarised in profiles/k_solve_channel_n4096_ncu_full.md.
+TRAFFIC_608 = {"fp64": 186.17e9 + 104.77e9, "mixed": 99.28e9 + 64.18e9}
 
 
 def workload_config(batch, nb, precision="fp64"):
@@ -437,7 +441,10 @@ def run_gpu(args, rank, world, local_rank):
                     "ms_per_step": e2e_ms},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1000.0,
-                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1000.0), "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1000.0),
+                         "traffic": TRAFFIC_608[args.precision] if (B == 608 and nb == 3) else None,
+                         "traffic_note": "DRAM bytes per launch from one ncu capture of this workload; "
+                                         "8-16 % of the HBM copy rate over the launch, far from bound",
                          "kernel": "k_solve (persistent nested NMGM, one block per instance)",
                          "flops_per_launch": flops, "fp64_flops": f64, "fp32_flops": f32, "launch_ms": launch_ms,
                          "peak_note": "FP64 derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"
