@@ -237,20 +237,40 @@ cudaError_t mg2_setup(nswe_prob_s *p, const MG2<T> &m, cudaStream_t s) {
                                  reinterpret_cast<T *>(p->dense), p->piv, p->flag, s);
 }
 
+// Algorithm 2 from level l0: grid-wide kernels on the large levels; from the
+// first level of at most tail2_cells<T>() cells down to the coarsest and back
+// up, one block-persistent launch.
 template <typename T>
 cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2<T> &m, const nswe_params &prm, cudaStream_t s) {
   cudaError_t e;
+  int ls = m.L;  // first level handled by the tail launch
   for (int l = m.l0; l < m.L; ++l) {
+    if (m.lv[l].Nx * m.lv[l].Ny <= tail2_cells<T>()) {
+      ls = l;
+      break;
+    }
     if ((e = smooth2<T>(m.lv[l], m.st[l], prm.nu1, prm.omega, prm.colours2d, s))) return e;
     if ((e = launch2_restrict<T>(m.lv[l].Nx, m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].R, m.lv[l].dU, m.lv[l + 1].R,
                                  m.lv[l + 1].dU, s)))
       return e;
   }
-  const int nL = m.lv[m.L].Nx * m.lv[m.L].Ny;
-  if ((e = launch2_dense_solve<T>(nL, reinterpret_cast<const T *>(p->dense), p->piv, m.lv[m.L].R,
-                                  reinterpret_cast<T *>(p->xbuf), m.lv[m.L].dU, s)))
-    return e;
-  for (int l = m.L - 1; l >= m.l0; --l) {
+  Tail2<T> t;
+  t.ls = ls;
+  t.L = m.L;
+  for (int l = ls; l <= m.L; ++l) {
+    t.Nx[l] = m.lv[l].Nx;
+    t.Ny[l] = m.lv[l].Ny;
+    t.st[l] = m.st[l];
+    t.J[l] = m.lv[l].J;
+    t.Dinv[l] = m.lv[l].Dinv;
+    t.R[l] = m.lv[l].R;
+    t.dU[l] = m.lv[l].dU;
+  }
+  t.A = reinterpret_cast<const T *>(p->dense);
+  t.piv = p->piv;
+  t.x = reinterpret_cast<T *>(p->xbuf);
+  if ((e = launch2_vcycle_tail<T>(t, prm.nu1, prm.nu2, prm.omega, prm.colours2d, s))) return e;
+  for (int l = ls - 1; l >= m.l0; --l) {
     if ((e = launch2_prolong<T>(m.lv[l].Nx, m.lv[l].Ny, m.lv[l].dU, m.lv[l + 1].dU, s))) return e;
     if ((e = smooth2<T>(m.lv[l], m.st[l], prm.nu2, prm.omega, prm.colours2d, s))) return e;
   }

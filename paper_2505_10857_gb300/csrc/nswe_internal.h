@@ -104,6 +104,26 @@ cudaError_t launch2_dense_solve(int n, const T *A, const int *piv, const T *R, T
 template <typename T>
 cudaError_t launch2_update(int n, double *U, const T *dU, double tau, int *flag, cudaStream_t s);
 cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream_t s);
+
+// The levels ls..L of a 2D V-cycle (down-leg, coarsest solve with the dense
+// factors A/piv, up-leg) run by one thread block: the levels of at most
+// tail2_cells<T>() cells, where one launch per colour pass would cost
+// more than the pass. One SM issues FP32 at 64x its FP64 rate, so the FP64
+// tail stops at far smaller levels.
+template <typename T>
+constexpr int tail2_cells() { return sizeof(T) == 4 ? 4096 : 256; }
+constexpr int kTail2Threads = 1024;
+template <typename T>
+struct Tail2 {
+  int ls, L;
+  int Nx[NSWE_MAX_LEVELS], Ny[NSWE_MAX_LEVELS], st[NSWE_MAX_LEVELS];
+  T *J[NSWE_MAX_LEVELS], *Dinv[NSWE_MAX_LEVELS], *R[NSWE_MAX_LEVELS], *dU[NSWE_MAX_LEVELS];
+  const T *A;
+  const int *piv;
+  T *x;
+};
+template <typename T>
+cudaError_t launch2_vcycle_tail(const Tail2<T> &t, int nu1, int nu2, double omega, int Kc, cudaStream_t s);
 cudaError_t launch2_interp(const ProbDev2 *p, int coarse_level, int nc, const double *Uc, double *Uf,
                            cudaStream_t s);
 

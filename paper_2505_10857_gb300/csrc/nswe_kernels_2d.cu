@@ -423,19 +423,20 @@ __device__ __forceinline__ void sor_items(int Nx, int Ny, int st, int &mode, int
   }
 }
 
+// One colour pass over the items first, first + stride, ... (a grid-wide or a
+// block-wide stride).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R,
-                                                   T *dU, double omega, int mode, int Kc, int col, int reps) {
-  const int stride = gridDim.x * blockDim.x;
+__device__ void sor_pass(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU, double omega,
+                         int mode, int Kc, int col, int reps, int first, int stride) {
   int P, W, items;
   sor_items(Nx, Ny, st, mode, Kc, col, P, W, items);
   if (mode == 0) {
     const int a = col % P, b = col / P;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < items; t += stride)
+    for (int t = first; t < items; t += stride)
       sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, a + (t % W) * P, b + (t / W) * P);
     return;
   }
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < items; t += stride) {
+  for (int t = first; t < items; t += stride) {
     const int j = t / W, m = t % W;
     const int a = mode == 1 ? col - j : j + Nx - 1 - col;
     const int i = ((a % Kc) + Kc) % Kc + m * Kc;
@@ -444,10 +445,17 @@ __global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU,
-                                                        T *Rc, T *dUc) {
+__global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R,
+                                                   T *dU, double omega, int mode, int Kc, int col, int reps) {
+  sor_pass<T>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, blockIdx.x * blockDim.x + threadIdx.x,
+              gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__device__ void restrict_cells2(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc, int first,
+                                int stride) {
   const int n = Nx * Ny, Ncx = Nx / 2, nc = Ncx * (Ny / 2), K = st_size(st);
-  for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += gridDim.x * blockDim.x) {
+  for (int cc = first; cc < nc; cc += stride) {
     const int I = cc % Ncx, Jy = cc / Ncx;
     T s[3] = {T(0.0), T(0.0), T(0.0)};
     for (int b = 0; b < 2; ++b)
@@ -477,12 +485,23 @@ __global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_prolong(int Nx, int Ny, T *dU, const T *dUc) {
+__global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU,
+                                                        T *Rc, T *dUc) {
+  restrict_cells2<T>(Nx, Ny, st, J, R, dU, Rc, dUc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__device__ void prolong_cells2(int Nx, int Ny, T *dU, const T *dUc, int first, int stride) {
   const int n = Nx * Ny, Ncx = Nx / 2, nc = Ncx * (Ny / 2);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+  for (int c = first; c < n; c += stride) {
     const int cc = (c / Nx / 2) * Ncx + (c % Nx) / 2;
     for (int l = 0; l < 3; ++l) dU[l * n + c] += dUc[l * nc + cc];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_prolong(int Nx, int Ny, T *dU, const T *dUc) {
+  prolong_cells2<T>(Nx, Ny, dU, dUc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Dense system A (row-major, unknown 3c+m) assembled from a block operator:
@@ -571,10 +590,10 @@ __global__ void __launch_bounds__(kThreads) k2_lu(int N3, T *A, int *piv, int *f
 }
 
 // dU = -A^{-1} R with the factors (one warp; unknown 3c+m).
+// Called by the 32 lanes of one warp (lane = threadIdx.x & 31).
 template <typename T>
-__global__ void k2_lu_solve(int n, const T *A, const int *piv, const T *R, T *x, T *dU) {
-  const int N3 = 3 * n, lane = threadIdx.x;
-  if (threadIdx.x >= 32) return;
+__device__ void lu_solve_warp(int n, const T *A, const int *piv, const T *R, T *x, T *dU) {
+  const int N3 = 3 * n, lane = threadIdx.x & 31;
   for (int t = lane; t < n; t += 32)
     for (int m = 0; m < 3; ++m) x[3 * t + m] = -R[m * n + t];
   __syncwarp();
@@ -599,6 +618,72 @@ __global__ void k2_lu_solve(int n, const T *A, const int *piv, const T *R, T *x,
   }
   for (int t = lane; t < n; t += 32)
     for (int m = 0; m < 3; ++m) dU[m * n + t] = x[3 * t + m];
+}
+
+template <typename T>
+__global__ void k2_lu_solve(int n, const T *A, const int *piv, const T *R, T *x, T *dU) {
+  if (threadIdx.x < 32) lu_solve_warp<T>(n, A, piv, R, x, dU);
+}
+
+// Smoothing of level l by the calling block, the same sequence of colour
+// passes as the host's schedule (directional: four diagonal sweeps per step;
+// otherwise two symmetric passes of the stencil colouring with consecutive
+// visits of a colour fused).
+__device__ __forceinline__ int st_ncolours(int st) { return st == ST_J9 ? 3 : st == ST_J21 ? 9 : st == ST_P5 ? 2 : 4; }
+
+template <typename T>
+__device__ void smooth_block(const Tail2<T> &t, int l, int steps, double omega, int Kc) {
+  const int Nx = t.Nx[l], Ny = t.Ny[l], st = t.st[l];
+  if (Kc >= 3 && (st == ST_J9 || st == ST_P5)) {
+    for (int s = 0; s < steps; ++s)
+      for (int d = 0; d < 4; ++d)
+        for (int q = 0; q < Kc; ++q) {
+          const int mode = (d % 2) + 1, col = d < 2 ? q : Kc - 1 - q;
+          sor_pass<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, mode, Kc, col, 1, threadIdx.x,
+                      blockDim.x);
+          __syncthreads();
+        }
+    return;
+  }
+  const int C = st_ncolours(st);
+  int prev = -1, reps = 0;
+  for (int s = 0; s < steps; ++s)
+    for (int pass = 0; pass < 4 * C; ++pass) {
+      const int q = pass % (2 * C), col = q < C ? q : 2 * C - 1 - q;
+      if (col == prev) {
+        ++reps;
+        continue;
+      }
+      if (prev >= 0) {
+        sor_pass<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, 0, 0, prev, reps, threadIdx.x,
+                    blockDim.x);
+        __syncthreads();
+      }
+      prev = col;
+      reps = 1;
+    }
+  if (prev >= 0) {
+    sor_pass<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, 0, 0, prev, reps, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTail2Threads, 1) k2_vcycle_tail(Tail2<T> t, int nu1, int nu2, double omega,
+                                                                  int Kc) {
+  for (int l = t.ls; l < t.L; ++l) {
+    smooth_block<T>(t, l, nu1, omega, Kc);
+    restrict_cells2<T>(t.Nx[l], t.Ny[l], t.st[l], t.J[l], t.R[l], t.dU[l], t.R[l + 1], t.dU[l + 1], threadIdx.x,
+                       blockDim.x);
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) lu_solve_warp<T>(t.Nx[t.L] * t.Ny[t.L], t.A, t.piv, t.R[t.L], t.x, t.dU[t.L]);
+  __syncthreads();
+  for (int l = t.L - 1; l >= t.ls; --l) {
+    prolong_cells2<T>(t.Nx[l], t.Ny[l], t.dU[l], t.dU[l + 1], threadIdx.x, blockDim.x);
+    __syncthreads();
+    smooth_block<T>(t, l, nu2, omega, Kc);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k2_to_f32(long count, const double *src, float *dst) {
@@ -724,6 +809,12 @@ cudaError_t launch2_update(int n, double *U, const T *dU, double tau, int *flag,
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch2_vcycle_tail(const Tail2<T> &t, int nu1, int nu2, double omega, int Kc, cudaStream_t s) {
+  k2_vcycle_tail<T><<<1, kTail2Threads, 0, s>>>(t, nu1, nu2, omega, Kc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream_t s) {
   k2_to_f32<<<grid2(count), kThreads, 0, s>>>(count, src, dst);
   return cudaGetLastError();
@@ -741,7 +832,8 @@ cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream
   template cudaError_t launch2_prolong<T>(int, int, T *, const T *, cudaStream_t);                               \
   template cudaError_t launch2_dense_factor<T>(int, int, int, const T *, T *, int *, int *, cudaStream_t);       \
   template cudaError_t launch2_dense_solve<T>(int, const T *, const int *, const T *, T *, T *, cudaStream_t);    \
-  template cudaError_t launch2_update<T>(int, double *, const T *, double, int *, cudaStream_t);
+  template cudaError_t launch2_update<T>(int, double *, const T *, double, int *, cudaStream_t);                 \
+  template cudaError_t launch2_vcycle_tail<T>(const Tail2<T> &, int, int, double, int, cudaStream_t);
 NSWE_2D_INSTANTIATE(double)
 NSWE_2D_INSTANTIATE(float)
 #undef NSWE_2D_INSTANTIATE
