@@ -270,10 +270,14 @@ nswe_status nswe_newton_solve(nswe_ctx ctx, nswe_prob prob, const double *U0,
                               double *U, const nswe_params *params,
                               nswe_info *info);
 
-/* Batched Algorithm 3: `count` independent problems solved by one launch
- * (one thread block per problem). probs[], U0s[], Us[] are HOST arrays of
- * count entries (U0s[i], Us[i] device pointers as in nswe_newton_solve);
- * infos (HOST, may be NULL) receives count records and makes the call
+/* Batched Algorithm 3: `count` independent problems of one dimension. 1D:
+ * one launch, one thread block per problem. 2D: the solves run concurrently,
+ * each sequenced by a host worker thread on its own stream (up to 8 at a
+ * time) after the work already queued on the context stream; the call
+ * returns when all have finished. A problem may appear once per batch
+ * (NSWE_EINVAL otherwise, 2D). probs[], U0s[], Us[] are HOST arrays of count
+ * entries (U0s[i], Us[i] device pointers as in nswe_newton_solve); infos
+ * (HOST, may be NULL) receives count records and makes the 1D call
  * synchronous. */
 nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count,
                                     const nswe_prob *probs,

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "nswe_internal.h"
@@ -42,6 +44,8 @@ struct nswe_prob_s {
   double *res_host;      // pinned host scalar
   int *flag_host;        // pinned host flag
   cudaStream_t cap;      // 2D: stream on which a Newton step is captured
+  double *partials2;     // 2D: [1024] per-block partial sums of res (per problem, so
+                         // that several 2D solves can run concurrently)
 };
 
 namespace {
@@ -284,9 +288,8 @@ cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2<T> &m, const nswe_params &prm, 
 // FP32, FP32 multigrid with the FP32 right-hand side in the upper half of
 // J's storage).
 template <typename T>
-nswe_status solve2d_t(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm,
-                      nswe_info *info) {
-  cudaStream_t s = ctx->stream;
+nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm, nswe_info *info,
+                      cudaStream_t s) {
   const int L = p->levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
   const int st0 = prm.jacobian == NSWE_JAC_FULL ? ST_J21 : ST_J9;
@@ -301,7 +304,7 @@ nswe_status solve2d_t(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U,
     if (l < s0 && launch2_interp(p->dev2, l + 1, p->host2.lev[l + 1].Nx * p->host2.lev[l + 1].Ny,
                                  p->host2.lev[l + 1].U, Lv.U, s))
       return NSWE_ECUDA;
-    if (launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, s)) return NSWE_ECUDA;
+    if (launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, p->partials2, s)) return NSWE_ECUDA;
     // One Newton step of this level (Eq. 12-14 with Algorithm 2): the same
     // launches every iteration, so they are captured once into a CUDA graph
     // and replayed; the host only waits for the residual and the flag.
@@ -330,7 +333,7 @@ nswe_status solve2d_t(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U,
           if ((e = mg2_vcycle<T>(p, m, prm, q))) return e;
       }
       if ((e = launch2_update<T>(n, Lv.U, dU, prm.tau, p->flag, q))) return e;
-      if ((e = launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, ctx->partials, q))) return e;
+      if ((e = launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, p->partials2, q))) return e;
       if ((e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(double), cudaMemcpyDeviceToHost, q))) return e;
       return cudaMemcpyAsync(p->flag_host, p->flag, sizeof(int), cudaMemcpyDeviceToHost, q);
     };
@@ -385,10 +388,67 @@ nswe_status solve2d_t(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U,
   return (nswe_status)inf.status;
 }
 
-nswe_status solve2d(nswe_ctx ctx, nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm,
-                    nswe_info *info) {
-  return prm.precision == NSWE_PREC_MIXED ? solve2d_t<float>(ctx, p, U0, U, prm, info)
-                                          : solve2d_t<double>(ctx, p, U0, U, prm, info);
+nswe_status solve2d(nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm, nswe_info *info,
+                    cudaStream_t s) {
+  return prm.precision == NSWE_PREC_MIXED ? solve2d_t<float>(p, U0, U, prm, info, s)
+                                          : solve2d_t<double>(p, U0, U, prm, info, s);
+}
+
+// A batch of 2D solves. Each 2D solve is sequenced from the host with one
+// synchronisation per Newton step and mostly small kernels, so the solves of
+// a batch run concurrently: up to kSolve2DWorkers host threads, each with its
+// own stream, take the problems in turn. The workers' streams first wait for
+// the work already queued on the context stream; the call returns once every
+// solve has finished.
+constexpr int kSolve2DWorkers = 8;
+
+nswe_status solve2d_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
+                          double *const *Us, const nswe_params &prm, nswe_info *infos) {
+  if (count == 1) {
+    nswe_info inf;
+    nswe_status st = solve2d(probs[0], U0s[0], Us[0], prm, &inf, ctx->stream);
+    if (infos) infos[0] = inf;
+    return st;
+  }
+  cudaEvent_t ready = nullptr;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(ready, ctx->stream) != cudaSuccess) {
+    if (ready) cudaEventDestroy(ready);
+    return NSWE_ECUDA;
+  }
+  std::vector<nswe_status> status(count, NSWE_OK);
+  std::vector<nswe_info> rec(count);
+  std::atomic<int> next{0};
+  std::atomic<bool> cuda_error{false};
+  const int workers = count < kSolve2DWorkers ? count : kSolve2DWorkers;
+  std::vector<std::thread> pool;
+  for (int w = 0; w < workers; ++w)
+    pool.emplace_back([&] {
+      cudaStream_t s = nullptr;
+      if (cudaSetDevice(ctx->device) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamWaitEvent(s, ready, 0) != cudaSuccess) {
+        cuda_error = true;
+        if (s) cudaStreamDestroy(s);
+        return;
+      }
+      for (int i = next++; i < count; i = next++) {
+        std::memset(&rec[i], 0, sizeof(nswe_info));
+        status[i] = solve2d(probs[i], U0s[i], Us[i], prm, &rec[i], s);
+        if (status[i] == NSWE_ECUDA) cuda_error = true;
+      }
+      if (cudaStreamSynchronize(s) != cudaSuccess) cuda_error = true;
+      cudaStreamDestroy(s);
+    });
+  for (auto &t : pool) t.join();
+  cudaEventDestroy(ready);
+  if (cuda_error) return NSWE_ECUDA;
+  int worst = NSWE_OK;
+  for (int i = 0; i < count; ++i) {
+    if (infos) infos[i] = rec[i];
+    if (status[i] != NSWE_OK && worst == NSWE_OK) worst = status[i];
+  }
+  return (nswe_status)worst;
 }
 
 // One 2D V-cycle from `level` in arithmetic T (a direct solve when `level`
@@ -592,6 +652,7 @@ nswe_status nswe_prob_destroy(nswe_prob prob) {
   cudaFree(prob->res_dev);
   cudaFreeHost(prob->res_host);
   cudaFreeHost(prob->flag_host);
+  cudaFree(prob->partials2);
   if (prob->cap) cudaStreamDestroy(prob->cap);
   delete prob;
   return NSWE_OK;
@@ -652,6 +713,7 @@ nswe_status nswe_prob_create_2d(nswe_ctx ctx, nswe_prob *out, int Nx, int Ny, in
             cudaMalloc(&p->piv, sizeof(int) * (N3 + 64)) == cudaSuccess &&
             cudaMalloc(&p->flag, sizeof(int) * 4) == cudaSuccess &&
             cudaMalloc(&p->res_dev, sizeof(double) * 4) == cudaSuccess &&
+            cudaMalloc(&p->partials2, sizeof(double) * 1024) == cudaSuccess &&
             cudaMallocHost(&p->res_host, sizeof(double) * 4) == cudaSuccess &&
             cudaMallocHost(&p->flag_host, sizeof(int) * 4) == cudaSuccess;
   if (!ok) {
@@ -828,15 +890,10 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
   }
   DeviceGuard dg(ctx->device);
   if (probs[0]->dim == 2) {
-    int worst = NSWE_OK;
-    for (int i = 0; i < count; ++i) {
-      nswe_info inf;
-      nswe_status st = solve2d(ctx, probs[i], U0s[i], Us[i], *params, &inf);
-      if (st == NSWE_ECUDA) return st;
-      if (infos) infos[i] = inf;
-      if (st != NSWE_OK && worst == NSWE_OK) worst = st;
-    }
-    return (nswe_status)worst;
+    for (int i = 1; i < count; ++i)
+      for (int k = 0; k < i; ++k)
+        if (probs[k] == probs[i]) return NSWE_EINVAL;  // one problem's workspace cannot serve two solves at once
+    return solve2d_batch(ctx, count, probs, U0s, Us, *params, infos);
   }
   nswe_status st = ensure_cap(ctx, count);
   if (st != NSWE_OK) return st;

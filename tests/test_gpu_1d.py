@@ -41,6 +41,7 @@ def host(t):
 def problems():
     return {
         "small": I.channel_small(0),
+        "small512": I.channel_small(0, N=512, levels=3),  # coarsest level of 128 cells
         "irregular": I.channel_irregular(3),
         "eq26": I.paper_smooth_subcritical(192, levels=2),
         "eq28_right": I.paper_bump(96, levels=2, regime="sub", width="right"),
@@ -112,7 +113,8 @@ def _random_system(orc, inp, level, nb, seed):
 
 @pytest.mark.parametrize("name,level,nb", [("small", 0, 3), ("small", 0, 5), ("small", 2, 3), ("small", 3, 3),
                                            ("small", 3, 5), ("irregular", 0, 3), ("irregular", 4, 3),
-                                           ("irregular", 0, 5), ("eq26", 0, 3)])
+                                           ("irregular", 0, 5), ("eq26", 0, 3), ("small512", 0, 3),
+                                           ("small512", 2, 5)])
 def test_vcycle_parity(nswe, ctx, orc, name, level, nb):
     inp = problems()[name]
     prob = nswe.Problem1D.from_inputs(ctx, inp)
@@ -144,14 +146,19 @@ def _solve_gpu(nswe, ctx, inp, prm_inputs):
 
 
 @pytest.mark.parametrize("case", ["small0", "small1", "irregular3", "eq26", "small0_j5", "eq28_trans_const",
-                                  "eq28_trans_left", "eq28_trans_right"])
+                                  "eq28_trans_left", "eq28_trans_right", "max_coarse_j3", "direct128_j3",
+                                  "direct128_j5"])
 def test_newton_solve_parity(nswe, ctx, orc, case):
     inp = {"small0": lambda: I.channel_small(0), "small1": lambda: I.channel_small(1),
            "irregular3": lambda: I.channel_irregular(3), "eq26": lambda: I.paper_smooth_subcritical(384, 3),
            "small0_j5": lambda: I.channel_small(0),
            "eq28_trans_const": lambda: I.paper_bump(192, levels=2, regime="trans", width="const"),
            "eq28_trans_left": lambda: I.paper_bump(192, levels=2, regime="trans", width="left"),
-           "eq28_trans_right": lambda: I.paper_bump(192, levels=2, regime="trans", width="right")}[case]()
+           "eq28_trans_right": lambda: I.paper_bump(192, levels=2, regime="trans", width="right"),
+           # the largest coarsest level the library takes (128 cells): band LU of 256 unknowns
+           "max_coarse_j3": lambda: I.channel_small(0, N=512, levels=3),
+           "direct128_j3": lambda: I.channel_small(0, N=128, levels=1),
+           "direct128_j5": lambda: I.channel_small(0, N=128, levels=1)}[case]()
     prm = I.Params1D.for_problem(inp, tol=1e-10 if case != "eq26" else 1e-11, n_max=500,
                                  nb=5 if case.endswith("j5") else 3)
     Uref, iref = orc.solve_problem(inp, prm)

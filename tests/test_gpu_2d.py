@@ -186,3 +186,31 @@ def test_full_size_residual_and_jacobian_sampled(nswe, ctx, orc):
                     col[m] += 3.0 * np.abs(r0).sum()
                 for l in range(3):
                     assert abs(J[k, l * 3 + m, c] - col[l]) <= 1e-12 * abs(col[l]) + 8 * EPS64 * sc / eps
+
+
+def test_2d_batch_runs_concurrently_and_equals_single(nswe, ctx):
+    """A batch of 2D problems is solved concurrently (one worker stream each);
+    every result equals, bit for bit, the same problem solved alone."""
+    inps = [I.paper_parabolic_bump(32, 16, 3), I.wedge(16, 8, 1), I.paper_parabolic_bump(16, 8, 2),
+            I.make_problem_2d(12, 8, 2, 0.0, 3.0, 0.0, 2.0, 9.81, I.bottom2d_linear(0.0, 0.01, 0.0),
+                              (I.BC2_INFLOW, I.BC2_OUTFLOW, I.BC2_REFLECT, I.BC2_REFLECT),
+                              np.array([[1.5, 1.0, 0.0], [0, 0, 0], [0, 0, 0], [0, 0, 0]]),
+                              lambda X, Y: (1.5, 1.0, 0.0))]
+    prms = [I.Params2D(levels=p.levels, nu1=[15], nu2=[15], tol=1e-11, n_max=400) for p in inps]
+    prm = nswe.params2d_from(prms[0], levels=3)
+    probs = [nswe.Problem2D.from_inputs(ctx, p) for p in inps]
+    U0s = [dev(p.U0_start) for p in inps]
+    alone = []
+    for pr, u0, p in zip(probs, U0s, inps):
+        U = torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda")
+        info = nswe.nswe_newton_solve(ctx, pr, u0, U, prm)
+        alone.append((host(U), info))
+    Us = [torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda") for p in inps]
+    infos = nswe.nswe_newton_solve_batch(ctx, probs, U0s, Us, prm)
+    assert alone[0][1]["status"] == alone[2][1]["status"] == 0  # the bumps converge
+    for k in range(len(inps)):
+        assert infos[k]["status"] == alone[k][1]["status"], (k, infos[k], alone[k][1])
+        assert np.array_equal(host(Us[k]), alone[k][0])
+        assert infos[k]["iters"] == alone[k][1]["iters"]
+    with pytest.raises(nswe.NsweError):
+        nswe.nswe_newton_solve_batch(ctx, [probs[0], probs[0]], U0s[:2], Us[:2], prm)
