@@ -662,6 +662,79 @@ def run_serve1d(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch2d(args):
+    """Batched 2D measurement (not the default line): `--batch2d` seeded
+    subcritical parabolic-bump channels (around Section 5.2.1, half 64 x 32
+    and half 128 x 64, J9, 20 smoothing steps, nested from 8 x 4), solved by batched
+    calls whose solves run concurrently, against the same solves one after
+    another. Host-timed (the solves run on several streams); the value counts
+    the solves that reached res < tol."""
+    import torch
+
+    from paper_2505_10857_gb300 import inputs as I
+    from paper_2505_10857_gb300 import nswe
+
+    mixed = args.precision != "fp64"
+    B = args.batch2d
+    inps = [I.bump_channel_2d(k, *((64, 32, 4) if k % 2 == 0 else (128, 64, 5))) for k in range(B)]
+    ctx = nswe.Context(0)
+    groups = {}
+    for k, p in enumerate(inps):
+        groups.setdefault(p.levels, []).append(k)
+    probs = [nswe.Problem2D.from_inputs(ctx, p) for p in inps]
+    U0s = [torch.from_numpy(p.U0_start).cuda() for p in inps]
+    Us = [torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda") for p in inps]
+    prms = {}
+    for lev in groups:
+        q = nswe.params2d_from(I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=TOL, n_max=400))
+        q.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
+        prms[lev] = q
+
+    def batched():
+        out = [None] * B
+        for lev, ks in groups.items():  # one batched call per level count (the parameters differ)
+            res = nswe.nswe_newton_solve_batch(ctx, [probs[k] for k in ks], [U0s[k] for k in ks],
+                                               [Us[k] for k in ks], prms[lev])
+            for k, r in zip(ks, res):
+                out[k] = r
+        return out
+
+    def one_by_one():
+        return [nswe.nswe_newton_solve(ctx, probs[k], U0s[k], Us[k], prms[inps[k].levels]) for k in range(B)]
+
+    for _ in range(max(1, args.warmup)):
+        batched()
+    times = []
+    infos = None
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = batched()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    one_by_one()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    ms = 1000.0 * statistics.mean(times)
+    ok = [k for k in range(B) if infos[k]["status"] == 0]
+    print(json.dumps({
+        "metric": METRIC, "value": len(ok) / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"2D batched: {B} seeded parabolic-bump channels (half 64x32, half 128x64), J9, nu 20, "
+                               + ("mixed FP64/FP32" if mixed else "FP64"), "seeds": "default_rng(5000 + k)"},
+        "converged": {"all_status_ok": len(ok) == B, "converged": len(ok), "of": B,
+                      "by_grid": {f"{inps[k].Nx}x{inps[k].Ny}": sum(1 for j in ok if inps[j].Nx == inps[k].Nx)
+                                  for k in range(min(B, 2))},
+                      "failed": [(5000 + k, infos[k]["status"], infos[k]["iters"][:inps[k].levels]) for k in range(B)
+                                 if infos[k]["status"] != 0][:8],
+                      "max_res": max((infos[k]["res"][0] for k in ok), default=None)},
+        "one_by_one": {"solves_per_s": B / t_seq, "ms": 1000.0 * t_seq},
+        "what": "host-timed: the batched call runs the solves concurrently on worker streams"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -674,7 +747,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of k_solve")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
-    ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d", "serve1d"])
+    ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d", "serve1d", "batch2d"])
+    ap.add_argument("--batch2d", type=int, default=32, help="batch2d: 2D problems per batch")
     ap.add_argument("--requests", type=int, default=1024, help="serve1d: requests in the arrival schedule")
     ap.add_argument("--rate", type=float, default=1500.0, help="serve1d: Poisson arrival rate (requests/s)")
     ap.add_argument("--streams", type=int, default=8, help="serve1d: concurrent launches")
@@ -690,6 +764,11 @@ def main():
         from paper_2505_10857_gb300 import build
         build.build()
         run_wedge2d(args)
+        return
+    if args.workload == "batch2d":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        run_batch2d(args)
         return
     if args.workload == "serve1d":
         from paper_2505_10857_gb300 import build

@@ -410,6 +410,25 @@ def bottom2d_eq29():
     return b, bx, by
 
 
+def bottom2d_parabolic(A, R, xc, yc):
+    """Parabolic bump of height A and radius R centred at (xc, yc): the
+    shape of Eq. 29 (A = 0.4, R = 1, centre (0, 2)) moved and scaled."""
+    c = A / (R * R)
+
+    def r2(x, y):
+        return (np.asarray(x, dtype=np.float64) - xc) ** 2 + (np.asarray(y, dtype=np.float64) - yc) ** 2
+
+    def b(x, y):
+        return np.where(r2(x, y) < R * R, A - c * r2(x, y), 0.0)
+
+    def bx(x, y):
+        return np.where(r2(x, y) < R * R, -2.0 * c * (np.asarray(x, dtype=np.float64) - xc), 0.0)
+
+    def by(x, y):
+        return np.where(r2(x, y) < R * R, -2.0 * c * (np.asarray(y, dtype=np.float64) - yc), 0.0)
+    return b, bx, by
+
+
 def bottom2d_gaussians(bumps):
     """Sum of Gaussian bumps A exp(-((x-xc)^2 + (y-yc)^2)/w^2)."""
     def b(x, y):
@@ -512,6 +531,24 @@ def paper_parabolic_bump(Nx=16, Ny=8, levels=2):
     return make_problem_2d(Nx, Ny, levels, -4.0, 4.0, 0.0, 4.0, G_PAPER, bottom2d_eq29(),
                            (BC2_DISCHARGE, BC2_DEPTH, BC2_REFLECT, BC2_REFLECT), st,
                            lambda X, Y: (1.0, 1.0, 0.0), meta={"case": "eq29"})
+
+
+def bump_channel_2d(k, Nx=64, Ny=32, levels=4, start_level=-1):
+    """Seeded subcritical 2D channel around Section 5.2.1 (seed 5000 + k):
+    [-4, 4] x [0, 4] with one parabolic bump shaped as Eq. 29, height
+    ~U[0.2, 0.4], radius ~U[0.75, 1.25], centre ~U([-1.5, 1.5] x [1.5, 2.5]);
+    inflow discharge hu ~U[0.75, 1.25] at x = -4, depth 1 at x = 4,
+    reflective side walls; guess h = 1, hu = the inflow discharge, hv = 0
+    (as Eq. 30) on start_level (the coarsest for -1); g = 9.812."""
+    rng = np.random.default_rng(5000 + k)
+    A, R = float(rng.uniform(0.2, 0.4)), float(rng.uniform(0.75, 1.25))
+    xc, yc = float(rng.uniform(-1.5, 1.5)), float(rng.uniform(1.5, 2.5))
+    q = float(rng.uniform(0.75, 1.25))
+    st = np.array([[0.0, q, 0.0], [1.0, 0.0, 0.0], [0, 0, 0], [0, 0, 0]])
+    return make_problem_2d(Nx, Ny, levels, -4.0, 4.0, 0.0, 4.0, G_PAPER, bottom2d_parabolic(A, R, xc, yc),
+                           (BC2_DISCHARGE, BC2_DEPTH, BC2_REFLECT, BC2_REFLECT), st,
+                           lambda X, Y: (1.0, q, 0.0), start_level=start_level,
+                           meta={"case": "bump-channel", "seed": 5000 + k, "bump": (A, R, xc, yc), "q": q})
 
 
 def wedge(Nx, Ny, levels, theta_deg=8.95, x1=5.0, y1=2.0, x_wall=1.0, speed=8.57, start_level=-1, meta=None):

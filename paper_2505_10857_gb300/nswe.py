@@ -363,7 +363,21 @@ def nswe_mg_vcycle_f32(ctx, prob, level, nb, J, R, dU, prm: Params):
                                                           _ptr(R, True), _ptr(dU, True), ctypes.byref(prm)))
 
 
+def _check_solve_sizes(prob, U0, U, prm: Params):
+    """The guess must hold the start level's state and U the finest level's
+    (the C entry points take bare pointers and cannot check this)."""
+    s = prm.nest_start if 0 <= prm.nest_start < prob.levels else prob.levels - 1
+    comps = 3 if isinstance(prob, Problem2D) else 2
+    for name, t, lev in (("U0", U0, s), ("U", U, 0)):
+        if t is None or isinstance(t, int):
+            continue
+        need = comps * prob.cells(lev)
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} values; level {lev} needs {comps} x {need // comps}")
+
+
 def nswe_newton_solve(ctx, prob, U0, U, prm: Params, want_info=True, raise_on_status=False):
+    _check_solve_sizes(prob, U0, U, prm)
     info = Info() if want_info else None
     rc = lib().nswe_newton_solve(ctx.h, prob.h, _ptr(U0), _ptr(U), ctypes.byref(prm),
                                  ctypes.byref(info) if info is not None else None)
@@ -374,6 +388,8 @@ def nswe_newton_solve(ctx, prob, U0, U, prm: Params, want_info=True, raise_on_st
 
 def nswe_newton_solve_batch(ctx, probs: Sequence[Problem1D], U0s, Us, prm: Params, want_info=True):
     n = len(probs)
+    for p, u0, u in zip(probs, U0s, Us):
+        _check_solve_sizes(p, u0, u, prm)
     ph = (_vp * n)(*[p.h.value for p in probs])
     u0 = (_dp * n)(*[_ptr(u) for u in U0s])
     uu = (_dp * n)(*[_ptr(u) for u in Us])

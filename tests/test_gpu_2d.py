@@ -214,3 +214,26 @@ def test_2d_batch_runs_concurrently_and_equals_single(nswe, ctx):
         assert infos[k]["iters"] == alone[k][1]["iters"]
     with pytest.raises(nswe.NsweError):
         nswe.nswe_newton_solve_batch(ctx, [probs[0], probs[0]], U0s[:2], Us[:2], prm)
+
+
+def test_guess_sized_for_another_level_is_refused(nswe, ctx):
+    """The guess must hold the start level's state: one built for the 8 x 4
+    grid, given with a nested start on 16 x 8, is refused before any launch
+    (the C entry points take bare pointers), as is a result buffer smaller
+    than the finest grid."""
+    p = I.bump_channel_2d(0, 32, 16, 3)
+    pr = nswe.Problem2D.from_inputs(ctx, p)
+    U = torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda")
+    u0 = dev(p.U0_start)
+    assert u0.numel() == 3 * 8 * 4
+    prm = nswe.params2d_from(I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400, nest_start=1))
+    with pytest.raises(ValueError):
+        nswe.nswe_newton_solve(ctx, pr, u0, U, prm)
+    with pytest.raises(ValueError):
+        nswe.nswe_newton_solve_batch(ctx, [pr], [u0], [U], prm)
+    prm0 = nswe.params2d_from(I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400))
+    with pytest.raises(ValueError):
+        nswe.nswe_newton_solve(ctx, pr, u0, U[:, : p.Nx * p.Ny // 2].contiguous(), prm0)
+    p1 = I.bump_channel_2d(0, 32, 16, 3, start_level=1)
+    info = nswe.nswe_newton_solve(ctx, pr, dev(p1.U0_start), U, prm)
+    assert info["status"] == 0 and info["res"][0] < 1e-10

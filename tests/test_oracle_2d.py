@@ -432,3 +432,28 @@ def test_j9_and_j21_reach_the_same_steady_state(orc):
     assert i9["res"][0] < 1e-11 and i21["res"][0] < 1e-11
     assert np.abs(U9 - U21).max() <= 1e-9 * np.abs(U9).max()
     assert abs(i9["iters"][0] - i21["iters"][0]) <= max(3, 0.2 * i21["iters"][0])
+
+
+def test_parabolic_family_contains_eq29():
+    """The seeded workload's bump family, at the parameters of Eq. 29
+    (height 0.4, radius 1, centre (0, 2)), is Eq. 29 with its gradient."""
+    rng = np.random.default_rng(7)
+    x, y = rng.uniform(-4, 4, 4000), rng.uniform(0, 4, 4000)
+    for f, g in zip(I.bottom2d_parabolic(0.4, 1.0, 0.0, 2.0), I.bottom2d_eq29()):
+        assert np.array_equal(f(x, y), g(x, y))
+    b, bx, by = I.bottom2d_parabolic(0.3, 0.8, 1.0, 2.5)
+    assert b(1.0, 2.5) == 0.3 and b(1.0, 3.31) == 0.0 and b(-2.0, 1.0) == 0.0
+    h = 1e-6
+    for px, py in ((1.2, 2.3), (0.6, 2.9)):
+        assert abs((b(px + h, py) - b(px - h, py)) / (2 * h) - bx(px, py)) < 1e-7
+        assert abs((b(px, py + h) - b(px, py - h)) / (2 * h) - by(px, py)) < 1e-7
+
+
+def test_seeded_bump_channels_converge(orc):
+    """The seeded subcritical 2D channels of the batched workload converge to
+    res < tol and keep a positive depth (coarse grids, FP64 oracle)."""
+    for k in range(3):
+        p = I.bump_channel_2d(k, 16, 8, 2)
+        U, info = orc.solve_problem2d(p, I.Params2D(levels=2, nu1=[20], nu2=[20], tol=1e-10, n_max=400))
+        assert info["status"] == 0 and info["res"][0] < 1e-10, (k, info)
+        assert (U[0] > 0).all()
