@@ -213,7 +213,7 @@ def test_2d_batch_runs_concurrently_and_equals_single(nswe, ctx):
         assert np.array_equal(host(Us[k]), alone[k][0])
         assert infos[k]["iters"] == alone[k][1]["iters"]
     with pytest.raises(nswe.NsweError):
-        nswe.nswe_newton_solve_batch(ctx, [probs[0], probs[0]], U0s[:2], Us[:2], prm)
+        nswe.nswe_newton_solve_batch(ctx, [probs[0], probs[0]], [U0s[0], U0s[0]], [Us[0], Us[0]], prm)
 
 
 def test_guess_sized_for_another_level_is_refused(nswe, ctx):
