@@ -90,6 +90,7 @@ class Params2D(ctypes.Structure):
         ("nu1", ctypes.c_int * 16), ("nu2", ctypes.c_int * 16),
         ("nu3", ctypes.c_int), ("levels", ctypes.c_int), ("n_max", ctypes.c_int), ("st", ctypes.c_int),
         ("nest_start", ctypes.c_int), ("eps", ctypes.c_double), ("colours", ctypes.c_int),
+        ("frozen", ctypes.c_int),
     ]
 
 
@@ -135,6 +136,7 @@ def _lib_handle():
                 "or_residual_cell2d": (None, [G2, _D, i32, i32, _D]),
                 "or_residual2d": (dbl, [G2, _D, _D]),
                 "or_jacobian2d": (dbl, [G2, _D, dbl, dbl, i32, _D, _D]),
+                "or_jacobian2d_frozen": (dbl, [G2, _D, dbl, dbl, i32, _D, _D]),
                 "or_stencil_size": (i32, [i32]),
                 "or_stencil_offset": (i32, [i32, i32, i32]),
                 "or_coarse_operator2d": (None, [i32, i32, i32, _D, _D]),
@@ -474,12 +476,15 @@ def stencil2d(st):
     return [(lib().or_stencil_offset(st, k, 0), lib().or_stencil_offset(st, k, 1)) for k in range(K)]
 
 
-def jacobian2d(prob: Problem2D, U, eps, alpha, st):
+def jacobian2d(prob: Problem2D, U, eps, alpha, st, frozen=False):
+    """Eq. 12-13; frozen=True: the frozen linearisation (WENO weights and
+    characteristic eigenvectors from U, an option beside the paper)."""
     U = _f64(U).reshape(3, prob.n).copy()
     K = lib().or_stencil_size(st)
     R = np.zeros((3, prob.n))
     J = np.zeros((K, 9, prob.n))
-    res = lib().or_jacobian2d(prob.ref(), ptr(U), float(eps), float(alpha), int(st), ptr(R), ptr(J))
+    f = lib().or_jacobian2d_frozen if frozen else lib().or_jacobian2d
+    res = f(prob.ref(), ptr(U), float(eps), float(alpha), int(st), ptr(R), ptr(J))
     return J, R, res
 
 
@@ -547,7 +552,8 @@ def interp2d(prob_coarse: Problem2D, Uc):
     return Uf
 
 
-def make_params2d(alpha, tau, omega, tol, nu1, nu2, nu3, levels, n_max, st, eps, nest_start=-1, colours=0):
+def make_params2d(alpha, tau, omega, tol, nu1, nu2, nu3, levels, n_max, st, eps, nest_start=-1, colours=0,
+                  frozen=False):
     p = Params2D()
     p.alpha, p.tau, p.omega, p.tol = alpha, tau, omega, tol
     nu1 = list(nu1) if hasattr(nu1, "__len__") else [nu1] * 16
@@ -557,6 +563,7 @@ def make_params2d(alpha, tau, omega, tol, nu1, nu2, nu3, levels, n_max, st, eps,
         p.nu2[i] = int(nu2[min(i, len(nu2) - 1)])
     p.nu3, p.levels, p.n_max, p.st, p.nest_start, p.eps = nu3, levels, n_max, st, nest_start, eps
     p.colours = colours
+    p.frozen = int(bool(frozen))
     return p
 
 
@@ -570,7 +577,7 @@ def solve_problem2d(inp, prm):
     probs = problem_levels2d(inp)
     arr = (Grid2D * len(probs))(*[p.s for p in probs])
     p = make_params2d(prm.alpha, prm.tau, prm.omega, prm.tol, prm.nu1, prm.nu2, prm.nu3, prm.levels, prm.n_max,
-                      prm.st, prm.eps, prm.nest_start, getattr(prm, "colours", 0))
+                      prm.st, prm.eps, prm.nest_start, getattr(prm, "colours", 0), getattr(prm, "frozen", False))
     U0 = _f64(inp.U0_start).reshape(-1)
     U = np.zeros(3 * inp.Nx * inp.Ny)
     info = Info2D()
@@ -583,7 +590,7 @@ def solve_problem2d(inp, prm):
 
 def newton2d(prob: Problem2D, U_init, nlev, prm):
     p = make_params2d(prm.alpha, prm.tau, prm.omega, prm.tol, prm.nu1, prm.nu2, prm.nu3, nlev, prm.n_max,
-                      prm.st, prm.eps, colours=getattr(prm, "colours", 0))
+                      prm.st, prm.eps, colours=getattr(prm, "colours", 0), frozen=getattr(prm, "frozen", False))
     U = _f64(U_init).reshape(-1).copy()
     info = Info2D()
     lib().or_newton2d(prob.ref(), ptr(U), int(nlev), ctypes.byref(p), ctypes.byref(info))

@@ -35,6 +35,16 @@
  *    smoothing step = two symmetric passes (colours 0..C-1, C-1..0, twice),
  *    the multicolour analogue of the four sweeps D1-D4 of Eq. 22;
  *  - App. A in 2D: tensor product of the one-dimensional weights (A.2).
+ *
+ * Frozen linearisation (an option beside Eq. 12, not in the paper): the
+ * perturbed local residuals take the WENO nonlinear weights and the
+ * characteristic eigenvectors of every reconstruction from the current,
+ * unperturbed iterate, so that only the candidate polynomials, the LLF
+ * fluxes and the sources see the perturbation. With Eq. 12 as printed, the
+ * derivatives of the nonlinear weights where the wedge's oblique jump meets
+ * the wall (Section 5.2.2) give a Jacobian on which block SOR diverges for
+ * every relaxation factor tried; with the weights frozen the paper's
+ * omega = 0.1 contracts. The residual, and so the fixed point, are unchanged.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -97,6 +107,20 @@ static void value2d(const or_grid2d *G, const double *U, int i, int j, double ou
 /* WENO3 of Section 3.1 (same weights as the 1D oracle, see or_weno3). */
 void or_weno3(double a, double b, double c, double *up, double *um);
 
+/* WENO3 of the values (a, b, c) with the nonlinear weights of the values
+ * (a0, b0, c0): the weights of Eq. 8 with zeta = 1e-6 and the linear weights
+ * 1/3, 2/3 (U^+) and 2/3, 1/3 (U^-) of or_weno3, the candidates of Eq. 7. */
+static void weno3_fixed(double a0, double b0, double c0, double a, double b, double c, double *up,
+                        double *um) {
+  double beta0 = (c0 - b0) * (c0 - b0), beta1 = (b0 - a0) * (b0 - a0);
+  double s0 = (1e-6 + beta0) * (1e-6 + beta0), s1 = (1e-6 + beta1) * (1e-6 + beta1);
+  double a0w = (1.0 / 3.0) / s0, a1w = (2.0 / 3.0) / s1; /* alpha_r  */
+  double t0w = (2.0 / 3.0) / s0, t1w = (1.0 / 3.0) / s1; /* alpha~_r */
+  double p0 = 1.5 * b - 0.5 * c, p1 = 0.5 * a + 0.5 * b, q0 = 0.5 * b + 0.5 * c, q1 = -0.5 * a + 1.5 * b;
+  *up = (a0w / (a0w + a1w)) * p0 + (a1w / (a0w + a1w)) * p1;
+  *um = (t0w / (t0w + t1w)) * q0 + (t1w / (t0w + t1w)) * q1;
+}
+
 /* Eigenvectors of n.dF/dU for n = x (dir 0) or y (dir 1) at state V:
  * eigenvalues u_n - c, u_t (shear), u_n + c (Section 2). Rows of Lm are left
  * eigenvectors, columns of Rm right eigenvectors. */
@@ -119,19 +143,28 @@ static void eigen2d(int dir, const double V[3], double g, double Lm[3][3], doubl
 /* One-sided characteristic WENO3 value at the interface between cells a and
  * a+1 of a line. vals[0..3] = U of cells a-1, a, a+1, a+2 along the line.
  * side 0: U^- (from the stencil a-1, a, a+1), side 1: U^+ (a, a+1, a+2). */
-static void char_rec(int dir, const double vals[4][3], double g, int side, double out[3]) {
+static void char_rec(int dir, const double vals[4][3], const double (*base)[3], double g, int side,
+                     double out[3]) {
+  /* base: NULL, or the unperturbed values of the same cells (frozen linearisation) */
+  const double(*ref)[3] = base ? base : vals;
   double V[3], Lm[3][3], Rm[3][3];
-  for (int m = 0; m < 3; ++m) V[m] = 0.5 * (vals[1][m] + vals[2][m]);
+  for (int m = 0; m < 3; ++m) V[m] = 0.5 * (ref[1][m] + ref[2][m]);
   eigen2d(dir, V, g, Lm, Rm);
-  double W[3][3]; /* [cell][field] */
+  double W[3][3], Wb[3][3]; /* [cell][field] */
   for (int s = 0; s < 3; ++s) {
-    const double *Uc = vals[side + s];
-    for (int f = 0; f < 3; ++f) W[s][f] = Lm[f][0] * Uc[0] + Lm[f][1] * Uc[1] + Lm[f][2] * Uc[2];
+    const double *Uc = vals[side + s], *Ub = ref[side + s];
+    for (int f = 0; f < 3; ++f) {
+      W[s][f] = Lm[f][0] * Uc[0] + Lm[f][1] * Uc[1] + Lm[f][2] * Uc[2];
+      Wb[s][f] = Lm[f][0] * Ub[0] + Lm[f][1] * Ub[1] + Lm[f][2] * Ub[2];
+    }
   }
   double Wr[3];
   for (int f = 0; f < 3; ++f) {
     double up, um;
-    or_weno3(W[0][f], W[1][f], W[2][f], &up, &um);
+    if (base)
+      weno3_fixed(Wb[0][f], Wb[1][f], Wb[2][f], W[0][f], W[1][f], W[2][f], &up, &um);
+    else
+      or_weno3(W[0][f], W[1][f], W[2][f], &up, &um);
     Wr[f] = side == 0 ? um : up;
   }
   for (int m = 0; m < 3; ++m) out[m] = Rm[m][0] * Wr[0] + Rm[m][1] * Wr[1] + Rm[m][2] * Wr[2];
@@ -170,14 +203,18 @@ static void line_value(const or_grid2d *G, const double *U, int dir, int r, int 
 }
 
 /* Reconstructed values at the interface k+1/2 of line r, side 0 (U^-) or 1. */
-static void iface_value(const or_grid2d *G, const double *U, int dir, int r, int k, int side, double out[3]) {
-  double vals[4][3];
+static void iface_value(const or_grid2d *G, const double *U, const double *U0, int dir, int r, int k, int side,
+                        double out[3]) {
+  double vals[4][3], base[4][3];
   for (int s = 0; s < 4; ++s) line_value(G, U, dir, r, k - 1 + s, vals[s]);
-  char_rec(dir, vals, G->g, side, out);
+  if (U0)
+    for (int s = 0; s < 4; ++s) line_value(G, U0, dir, r, k - 1 + s, base[s]);
+  char_rec(dir, vals, U0 ? (const double(*)[3])base : NULL, G->g, side, out);
 }
 
-/* Local residual R_ij (Eq. 20), three components. */
-void or_residual_cell2d(const or_grid2d *G, const double *U, int i, int j, double R[3]) {
+/* Local residual R_ij (Eq. 20), three components; with U0 != NULL the
+ * reconstructions take their weights and eigenvectors from U0. */
+static void residual_cell2d(const or_grid2d *G, const double *U, const double *U0, int i, int j, double R[3]) {
   const int n = G->Nx * G->Ny, c = j * G->Nx + i;
   const double s3 = 1.0 / (4.0 * sqrt(3.0)), tg = 1.0 / (2.0 * sqrt(3.0));
   double flux[2][3] = {{0}}, S[3] = {0, 0, 0};
@@ -194,7 +231,7 @@ void or_residual_cell2d(const or_grid2d *G, const double *U, int i, int j, doubl
         for (int side = 0; side < 2; ++side) {
           int k = a - 2 + f;
           if ((f == 0 && side == 0) || (f == 3 && side == 1)) continue; /* not needed */
-          iface_value(G, U, dir, r0 - 1 + t, k, side, ifv[t][f][side]);
+          iface_value(G, U, U0, dir, r0 - 1 + t, k, side, ifv[t][f][side]);
         }
     double fl[2][3] = {{0}};
     double hq[2][4]; /* h at the two Gauss lines, interfaces f = 0..3 (side used by the cubic) */
@@ -230,6 +267,10 @@ void or_residual_cell2d(const or_grid2d *G, const double *U, int i, int j, doubl
     S[1 + dir] = -0.25 * acc; /* S / (dx dy) */
   }
   for (int m = 0; m < 3; ++m) R[m] = flux[0][m] / G->dx + flux[1][m] / G->dy - S[m];
+}
+
+void or_residual_cell2d(const or_grid2d *G, const double *U, int i, int j, double R[3]) {
+  residual_cell2d(G, U, NULL, i, j, R);
 }
 
 double or_residual2d(const or_grid2d *G, const double *U, double *R) {
@@ -269,10 +310,16 @@ static int stencil_center(int st) { int K = or_stencil_size(st); for (int k = 0;
 static int coarse_stencil(int st) { return (st == ST_J9 || st == ST_P5) ? ST_P5 : ST_P9; }
 
 /* FD Jacobian (Eq. 12-13 in 2D; J21: full stencil, J9: cross, Eq. 21). */
-double or_jacobian2d(const or_grid2d *G, double *U, double eps, double alpha, int st, double *R, double *J) {
+static double jacobian2d(const or_grid2d *G, double *U, double eps, double alpha, int st, int frozen, double *R,
+                         double *J) {
   const int Nx = G->Nx, Ny = G->Ny, n = Nx * Ny, K = or_stencil_size(st), kc = stencil_center(st);
   double res = or_residual2d(G, U, R);
   memset(J, 0, sizeof(double) * (size_t)K * 9 * n);
+  double *U0 = NULL;
+  if (frozen) {
+    U0 = malloc(sizeof(double) * 3 * n);
+    memcpy(U0, U, sizeof(double) * 3 * n);
+  }
   for (int j = 0; j < Ny; ++j)
     for (int i = 0; i < Nx; ++i) {
       int c = j * Nx + i;
@@ -285,7 +332,7 @@ double or_jacobian2d(const or_grid2d *G, double *U, double eps, double alpha, in
           double save = U[m * n + cp];
           U[m * n + cp] = save + eps;
           double Rp[3];
-          or_residual_cell2d(G, U, i, j, Rp);
+          residual_cell2d(G, U, U0, i, j, Rp);
           U[m * n + cp] = save;
           for (int l = 0; l < 3; ++l) J[(size_t)(k * 9 + l * 3 + m) * n + c] = (Rp[l] - R0[l]) / eps;
         }
@@ -293,7 +340,19 @@ double or_jacobian2d(const or_grid2d *G, double *U, double eps, double alpha, in
       double reg = alpha * (fabs(R0[0]) + fabs(R0[1]) + fabs(R0[2]));
       for (int l = 0; l < 3; ++l) J[(size_t)(kc * 9 + l * 3 + l) * n + c] += reg;
     }
+  free(U0);
   return res;
+}
+
+/* Eq. 12-13 on the stencil st. */
+double or_jacobian2d(const or_grid2d *G, double *U, double eps, double alpha, int st, double *R, double *J) {
+  return jacobian2d(G, U, eps, alpha, st, 0, R, J);
+}
+
+/* Eq. 12-13 with the frozen linearisation (weights and eigenvectors of the
+ * reconstructions from U, see the header). */
+double or_jacobian2d_frozen(const or_grid2d *G, double *U, double eps, double alpha, int st, double *R, double *J) {
+  return jacobian2d(G, U, eps, alpha, st, 1, R, J);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -572,6 +631,7 @@ typedef struct {
   int nu3, levels, n_max, st, nest_start;
   double eps;
   int colours; /* K of the diagonal smoothing schedule (cross stencils); 0: stencil colourings */
+  int frozen;  /* 1: the frozen linearisation of the Jacobian */
 } or_params2d;
 
 typedef struct {
@@ -595,7 +655,7 @@ static int newton_level2d(const or_grid2d *G, double *U, int nlev, const or_para
   double res = 0.0;
   *status = 0;
   do {
-    or_jacobian2d(G, U, p->eps, p->alpha, p->st, R, J);
+    jacobian2d(G, U, p->eps, p->alpha, p->st, p->frozen, R, J);
     memset(dU, 0, sizeof(double) * 3 * n);
     if (nlev == 1) {
       if (or_direct_solve2d(G->Nx, G->Ny, p->st, J, R, dU)) { *status = 3; break; }

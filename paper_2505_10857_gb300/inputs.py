@@ -592,3 +592,4 @@ class Params2D:
     eps: float = 1e-6
     nest_start: int = -1
     colours: int = 0  # K of the diagonal smoothing schedule for cross stencils (0: stencil colourings)
+    frozen: bool = False  # frozen linearisation of the 2D Jacobian (weights and eigenvectors from the iterate)

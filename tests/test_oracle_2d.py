@@ -457,3 +457,82 @@ def test_seeded_bump_channels_converge(orc):
         U, info = orc.solve_problem2d(p, I.Params2D(levels=2, nu1=[20], nu2=[20], tol=1e-10, n_max=400))
         assert info["status"] == 0 and info["res"][0] < 1e-10, (k, info)
         assert (U[0] > 0).all()
+
+
+def _oblique_jump(F1, theta):
+    """Oblique hydraulic jump of a wedge of deflection theta (radians) in a
+    stream of Froude number F1 (the shallow-water analogue of the oblique
+    shock relations, weak branch): returns (jump angle beta to the upstream
+    flow, depth ratio h2/h1)."""
+    from scipy.optimize import brentq
+
+    def f(b):
+        s = math.sqrt(1.0 + 8.0 * F1 * F1 * math.sin(b) ** 2)
+        return math.tan(b) * (s - 3.0) / (2.0 * math.tan(b) ** 2 + s - 1.0) - math.tan(theta)
+    b = brentq(f, math.asin(1.0 / F1) + 1e-9, math.radians(60.0))
+    return b, 0.5 * (math.sqrt(1.0 + 8.0 * F1 * F1 * math.sin(b) ** 2) - 1.0)
+
+
+def test_frozen_linearisation_is_eq12_at_a_uniform_state(orc):
+    """With linear WENO weights the characteristic basis cancels, so at a
+    uniform state the frozen Jacobian and Eq. 12 differ only by the weights'
+    response to the perturbation itself, of relative size about eps/zeta * eps;
+    the residuals are the same bits."""
+    p = I.make_problem_2d(8, 8, 1, 0, 2.0, 0, 2.0, 9.81, I.bottom2d_flat(),
+                          (I.BC2_INFLOW, I.BC2_OUTFLOW, I.BC2_REFLECT, I.BC2_REFLECT),
+                          np.array([[1.0, 2.0, 0.1], [0, 0, 0], [0, 0, 0], [0, 0, 0]]), lambda X, Y: (1.0, 2.0, 0.1))
+    pr = orc.problem_levels2d(p)[0]
+    U = np.array([1.0, 2.0, 0.1])[:, None] * np.ones((3, 64))
+    Ja, Ra, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, I.ST_J21)
+    Jb, Rb, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, I.ST_J21, frozen=True)
+    assert np.array_equal(Ra, Rb)
+    assert np.abs(Ja - Jb).max() <= 2e-5 * np.abs(Ja).max()
+
+
+def test_frozen_linearisation_freezes_the_weights(orc):
+    """Near-uniform data whose differences (1e-3) make the smoothness
+    indicators comparable to zeta: the Eq. 12 quotient moves by percents
+    between eps = 1e-4 and 1e-6 (the weights react to the perturbation), the
+    frozen one only by the flux curvature, O(eps)."""
+    rng = np.random.default_rng(3)
+    p = I.make_problem_2d(8, 8, 1, 0, 2.0, 0, 2.0, 9.81, I.bottom2d_flat(),
+                          (I.BC2_INFLOW, I.BC2_OUTFLOW, I.BC2_REFLECT, I.BC2_REFLECT),
+                          np.array([[1.0, 2.0, 0.1], [0, 0, 0], [0, 0, 0], [0, 0, 0]]), lambda X, Y: (1.0, 2.0, 0.1))
+    pr = orc.problem_levels2d(p)[0]
+    U = np.array([1.0, 2.0, 0.1])[:, None] + 1e-3 * rng.standard_normal((3, 64))
+    moved = {}
+    for frozen in (False, True):
+        Ja, _, _ = orc.jacobian2d(pr, U, 1e-4, 3.0, I.ST_J21, frozen=frozen)
+        Jb, _, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, I.ST_J21, frozen=frozen)
+        moved[frozen] = np.abs(Ja - Jb).max() / np.abs(Jb).max()
+    assert moved[True] < 5e-4 and moved[False] > 1e-2, moved
+
+
+def test_wedge_reaches_the_oblique_jump_with_the_frozen_linearisation(orc):
+    """Section 5.2.2 with the paper's parameters (omega = 0.1, nu3 = 3, nested
+    from 16 x 8 with nu = 10, 15 on 16 x 8, 32 x 16) and the frozen
+    linearisation: the solve converges, and the steady state is the oblique
+    jump of the wedge: upstream depth 1, downstream depth h2 and jump angle
+    beta - theta to the wall from the oblique jump relations at
+    F1 = 8.57 / sqrt(g)."""
+    Nx, Ny = 32, 16
+    inp = I.wedge(Nx, Ny, 3, start_level=1)
+    U, info = orc.solve_problem2d(inp, I.Params2D(levels=3, nu1=[15, 10, 10], nu2=[15, 10, 10], tol=1e-11,
+                                                  n_max=400, nest_start=1, omega=0.1, frozen=True))
+    assert info["status"] == 0 and info["res"][0] < 1e-11, info
+    th = math.radians(8.95)
+    beta, ratio = _oblique_jump(8.57 / math.sqrt(I.G_PAPER), th)
+    assert abs(ratio - 1.5) < 1e-3  # the wedge of Section 5.2.2 is designed for h2 = 1.5
+    h = U[0].reshape(Ny, Nx)
+    dx, dy = 5.0 / Nx, 2.0 / Ny
+    assert np.abs(h[:, :4] - 1.0).max() < 1e-3          # undisturbed inflow
+    assert np.abs(h[:3, -8:] / ratio - 1.0).max() < 2e-3  # behind the jump, along the wall
+    mid, pts = 0.5 * (1.0 + ratio), []
+    for j in range(Ny):
+        k = int(np.argmax(h[j] > mid))
+        if k > 0:
+            pts.append(((j + 0.5) * dy, (k - 0.5 + (mid - h[j, k - 1]) / (h[j, k] - h[j, k - 1])) * dx))
+    pts = np.array(pts)
+    slope, icpt = np.polyfit(pts[:, 1], pts[:, 0], 1)
+    assert abs(math.degrees(math.atan(slope)) - math.degrees(beta - th)) < 1.0
+    assert abs(-icpt / slope - 1.0 / math.cos(th)) < dx  # the jump starts where the wall does
