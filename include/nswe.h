@@ -89,6 +89,18 @@ typedef struct {
 #define NSWE_MAX_LEVELS 16
 #define NSWE_JAC_SIMPLIFIED 3 /* 1D J3: block tridiagonal (Section 3.3); 2D J9 */
 #define NSWE_JAC_FULL 5       /* 1D J5: block pentadiagonal; 2D J21          */
+/* 2D only, OR'd into nswe_params.jacobian (J9 or J21): the frozen
+ * linearisation, an option beside Eq. 12 that the paper does not have. The
+ * perturbed local residuals take the WENO nonlinear weights (Eq. 8) and the
+ * characteristic eigenvectors of every reconstruction from the current
+ * iterate, so only the candidate polynomials, the fluxes and the sources see
+ * the perturbation. The residual and its steady state are unchanged; Newton
+ * becomes a quasi-Newton iteration. Where a discontinuity meets a wall (the
+ * wedge of Section 5.2.2) the derivatives of the nonlinear weights make the
+ * Jacobian of Eq. 12 one on which block SOR diverges; with the weights
+ * frozen it contracts at the paper's omega = 0.1. 1D calls refuse it
+ * (NSWE_EINVAL). */
+#define NSWE_JAC_FROZEN 0x100
 
 /* Arithmetic of a Newton step. The paper computes in double precision
  * (NSWE_PREC_FP64). NSWE_PREC_MIXED is this library's addition: the residual
@@ -113,7 +125,8 @@ typedef struct {
   int nu1, nu2;   /* pre/post smoothing steps per level (Algorithm 2)       */
   int nu3;        /* V-cycles per Newton step (Algorithm 3)                 */
   int n_max;      /* Newton iteration cap per nested level                  */
-  int jacobian;   /* NSWE_JAC_SIMPLIFIED (J3) or NSWE_JAC_FULL (J5)         */
+  int jacobian;   /* NSWE_JAC_SIMPLIFIED (J3/J9) or NSWE_JAC_FULL (J5/J21);
+                     2D: optionally | NSWE_JAC_FROZEN                        */
   int nest_start; /* nested level the solve starts on; <0: coarsest (Alg. 3)*/
   int precision;  /* NSWE_PREC_FP64 or NSWE_PREC_MIXED                      */
   int colours2d;  /* 2D smoothing of the cross stencils (J9, coarse 5-point):
@@ -228,6 +241,14 @@ nswe_status nswe_jacobian_simplified(nswe_ctx ctx, nswe_prob prob, int level,
 nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level,
                                const double *U, double eps, double alpha,
                                double *R, double *J, double *res_l1);
+
+/* 2D Jacobian of Eq. 12-13 under the frozen linearisation (NSWE_JAC_FROZEN;
+ * not in the paper): nb = 9 (J9) or 21 (J21); U, R [3][n_l], J [nb][9][n_l],
+ * res_l1 (device scalar, may be NULL) as in nswe_jacobian_simplified. A 1D
+ * problem or another nb: NSWE_EINVAL. */
+nswe_status nswe_jacobian_frozen(nswe_ctx ctx, nswe_prob prob, int level, int nb,
+                                 const double *U, double eps, double alpha,
+                                 double *R, double *J, double *res_l1);
 
 /* The Jacobian of a NSWE_PREC_MIXED Newton step: R and res_l1 as in
  * nswe_residual (FP64); J the Jacobian of Eq. 12-13 stored in FP32, with the

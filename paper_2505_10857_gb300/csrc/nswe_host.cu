@@ -76,7 +76,9 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu3 < 1 || p->n_max < 1 || p->nu1 > 1000 || p->nu2 > 1000 ||
       p->nu3 > 1000)
     return NSWE_EINVAL;
-  if (p->jacobian != NSWE_JAC_SIMPLIFIED && p->jacobian != NSWE_JAC_FULL) return NSWE_EINVAL;
+  const int jb = p->jacobian & ~NSWE_JAC_FROZEN;
+  if (jb != NSWE_JAC_SIMPLIFIED && jb != NSWE_JAC_FULL) return NSWE_EINVAL;
+  if ((p->jacobian & NSWE_JAC_FROZEN) && pr && pr->dim != 2) return NSWE_EINVAL;  // 2D only
   if (p->precision != NSWE_PREC_FP64 && p->precision != NSWE_PREC_MIXED) return NSWE_EINVAL;
   if (p->colours2d != 0 && (p->colours2d < 3 || p->colours2d > 4096)) return NSWE_EINVAL;
   if (pr) {
@@ -91,6 +93,7 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
 nswe_status nswe::check_params_1d(const nswe_params *p, int levels, int first_level) {
   nswe_status st = check_params(p, nullptr, 0);
   if (st != NSWE_OK) return st;
+  if (p->jacobian & NSWE_JAC_FROZEN) return NSWE_EINVAL;  // 2D only
   for (int l = 0; l <= first_level && l < levels; ++l)
     if (!(p->eps[l] > 0.0) || !std::isfinite(p->eps[l])) return NSWE_EINVAL;
   return NSWE_OK;
@@ -292,7 +295,8 @@ nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_pa
                       cudaStream_t s) {
   const int L = p->levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
-  const int st0 = prm.jacobian == NSWE_JAC_FULL ? ST_J21 : ST_J9;
+  const int st0 = (prm.jacobian & ~NSWE_JAC_FROZEN) == NSWE_JAC_FULL ? ST_J21 : ST_J9;
+  const bool frozen = (prm.jacobian & NSWE_JAC_FROZEN) != 0;
   nswe_info inf;
   std::memset(&inf, 0, sizeof(inf));
   const int ns = p->host2.lev[s0].Nx * p->host2.lev[s0].Ny;
@@ -315,7 +319,7 @@ nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_pa
     T *const Rs = kMixed ? J + (size_t)K * 9 * n : reinterpret_cast<T *>(Lv.R);
     auto step = [&](cudaStream_t q) -> cudaError_t {
       cudaError_t e;
-      if ((e = launch2_jacobian<T>(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, J, q))) return e;
+      if ((e = launch2_jacobian<T>(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, J, frozen, q))) return e;
       if constexpr (kMixed) {
         if ((e = launch2_to_f32(3L * n, Lv.R, reinterpret_cast<float *>(Rs), q))) return e;
       }
@@ -791,14 +795,15 @@ nswe_status nswe_residual(nswe_ctx ctx, nswe_prob prob, int level, const double 
 }
 
 static nswe_status jacobian_common(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *U, double eps,
-                                   double alpha, double *R, double *J, double *res) {
+                                   double alpha, double *R, double *J, double *res, bool frozen = false) {
   if (!ctx || !prob || prob->ctx != ctx || !U || !R || !J || level < 0 || level >= prob->levels) return NSWE_EINVAL;
   if (!(eps > 0.0) || !std::isfinite(eps) || !(alpha >= 0.0) || !std::isfinite(alpha)) return NSWE_EINVAL;
   DeviceGuard dg(ctx->device);
   if (prob->dim == 2) {
     const int n = nswe_prob_cells(prob, level);
     if (launch2_residual(prob->dev2, level, n, U, R, res, ctx->partials, ctx->stream) ||
-        launch2_jacobian<double>(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, ctx->stream))
+        launch2_jacobian<double>(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, frozen,
+                                 ctx->stream))
       return NSWE_ECUDA;
     return NSWE_OK;
   }
@@ -819,6 +824,12 @@ nswe_status nswe_jacobian_full(nswe_ctx ctx, nswe_prob prob, int level, const do
   return jacobian_common(ctx, prob, level, 5, U, eps, alpha, R, J, res_l1);
 }
 
+nswe_status nswe_jacobian_frozen(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *U, double eps,
+                                 double alpha, double *R, double *J, double *res_l1) {
+  if (!prob || prob->dim != 2 || (nb != 9 && nb != 21)) return NSWE_EINVAL;
+  return jacobian_common(ctx, prob, level, nb == 21 ? 5 : 3, U, eps, alpha, R, J, res_l1, true);
+}
+
 nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *U, double eps,
                               double alpha, double *R, float *J, double *res_l1) {
   if (!ctx || !prob || prob->ctx != ctx || !U || !R || !J || level < 0 || level >= prob->levels) return NSWE_EINVAL;
@@ -828,7 +839,7 @@ nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, c
     if (nb != 9 && nb != 21) return NSWE_EINVAL;
     const int n = nswe_prob_cells(prob, level);
     return (launch2_residual(prob->dev2, level, n, U, R, res_l1, ctx->partials, ctx->stream) ||
-            launch2_jacobian<float>(prob->dev2, level, n, nb == 21 ? ST_J21 : ST_J9, U, eps, alpha, R, J,
+            launch2_jacobian<float>(prob->dev2, level, n, nb == 21 ? ST_J21 : ST_J9, U, eps, alpha, R, J, false,
                                     ctx->stream))
                ? NSWE_ECUDA
                : NSWE_OK;

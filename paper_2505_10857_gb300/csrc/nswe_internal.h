@@ -80,9 +80,10 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
                              double *partials, cudaStream_t s);
 // Multigrid launchers for T = double (FP64 path) and T = float (the multigrid
 // of a mixed-precision step); the Jacobian may be stored in either.
+// frozen: the frozen linearisation (weights and eigenvectors from U).
 template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, TJ *J, cudaStream_t s);
+                             const double *R, TJ *J, bool frozen, cudaStream_t s);
 template <typename T>
 cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, cudaStream_t s);
 template <typename T>

@@ -129,27 +129,56 @@ __device__ __forceinline__ void weno3_both(double a, double b, double c, double 
   um = (2.0 * s1 * q0 + s0 * q1) * (D1 * inv);
 }
 
+// WENO3 of the values (a, b, c) with the nonlinear weights of (a0, b0, c0):
+// the frozen linearisation's reconstruction (weights as in weno3_both).
+__device__ __forceinline__ void weno3_fixed(double a0, double b0, double c0, double a, double b, double c,
+                                            double &up, double &um) {
+  double d0 = c0 - b0, d1 = b0 - a0;
+  double e0 = kZeta2 + d0 * d0, e1 = kZeta2 + d1 * d1;
+  double s0 = e0 * e0, s1 = e1 * e1;
+  double p0 = 1.5 * b - 0.5 * c, p1 = 0.5 * a + 0.5 * b;
+  double q0 = 0.5 * b + 0.5 * c, q1 = -0.5 * a + 1.5 * b;
+  double D1 = s1 + 2.0 * s0, D2 = 2.0 * s1 + s0;
+  double inv = 1.0 / (D1 * D2);
+  up = (s1 * p0 + 2.0 * s0 * p1) * (D2 * inv);
+  um = (2.0 * s1 * q0 + s0 * q1) * (D1 * inv);
+}
+
 // One-sided characteristic WENO3 at the interface between line cells a and
-// a+1; v[0..3] = cells a-1..a+2; side 0: U^-, side 1: U^+.
-__device__ __forceinline__ void char_rec(int dir, const double v[4][3], double g, int side, double out[3]) {
+// a+1; v[0..3] = cells a-1..a+2; side 0: U^-, side 1: U^+. FROZEN: the
+// eigenvectors and the nonlinear weights come from b, the unperturbed values
+// of the same cells (b is not read otherwise).
+template <bool FROZEN>
+__device__ __forceinline__ void char_rec(int dir, const double v[4][3], const double b[4][3], double g, int side,
+                                         double out[3]) {
   const int in = dir == 0 ? 1 : 2, it = dir == 0 ? 2 : 1;
-  const double h = 0.5 * (v[1][0] + v[2][0]);
+  const double(*r)[3] = FROZEN ? b : v;
+  const double h = 0.5 * (r[1][0] + r[2][0]);
   const double ih = 1.0 / h;
-  const double un = 0.5 * (v[1][in] + v[2][in]) * ih, ut = 0.5 * (v[1][it] + v[2][it]) * ih;
+  const double un = 0.5 * (r[1][in] + r[2][in]) * ih, ut = 0.5 * (r[1][it] + r[2][it]) * ih;
   const double c = sqrt(g * h), i2c = 0.5 / c;
-  double W[3][3];
+  double W[3][3], Wb[3][3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const double *u = v[side + s];
     W[s][0] = (un + c) * i2c * u[0] - i2c * u[in];
     W[s][1] = -ut * u[0] + u[it];
     W[s][2] = -(un - c) * i2c * u[0] + i2c * u[in];
+    if (FROZEN) {
+      const double *w = b[side + s];
+      Wb[s][0] = (un + c) * i2c * w[0] - i2c * w[in];
+      Wb[s][1] = -ut * w[0] + w[it];
+      Wb[s][2] = -(un - c) * i2c * w[0] + i2c * w[in];
+    }
   }
   double Wr[3];
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     double up, um;
-    weno3_both(W[0][f], W[1][f], W[2][f], up, um);
+    if (FROZEN)
+      weno3_fixed(Wb[0][f], Wb[1][f], Wb[2][f], W[0][f], W[1][f], W[2][f], up, um);
+    else
+      weno3_both(W[0][f], W[1][f], W[2][f], up, um);
     Wr[f] = side == 0 ? um : up;
   }
   out[0] = Wr[0] + Wr[2];
@@ -175,7 +204,9 @@ __device__ __forceinline__ void llf(int dir, const double L[3], const double R[3
   for (int m = 0; m < 3; ++m) F[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * a * (R[m] - L[m]);
 }
 
-// Local residual R_ij (Eq. 20) of the (possibly perturbed) state.
+// Local residual R_ij (Eq. 20) of the (possibly perturbed) state; FROZEN:
+// the reconstructions take their weights and eigenvectors from U itself.
+template <bool FROZEN>
 __device__ void local_residual2(const Geo2 &G, const double *U, int i, int j, const Pert &p, double R[3]) {
   const int n = G.Nx * G.Ny, c = j * G.Nx + i;
   double flux[2][3], S[3] = {0.0, 0.0, 0.0};
@@ -187,18 +218,28 @@ __device__ void local_residual2(const Geo2 &G, const double *U, int i, int j, co
     double ifv[3][4][2][3];
 #pragma unroll 1
     for (int t = 0; t < 3; ++t) {
-      double v[7][3];  // line cells a-3 .. a+3
+      double v[7][3];                 // line cells a-3 .. a+3
+      double v0[FROZEN ? 7 : 1][3];   // the same cells unperturbed (FROZEN)
 #pragma unroll
       for (int s = 0; s < 7; ++s) {
         if (dir == 0) cellv(G, U, a - 3 + s, r0 - 1 + t, p, v[s]);
         else cellv(G, U, r0 - 1 + t, a - 3 + s, p, v[s]);
       }
+      if (FROZEN) {
+        const Pert none{-1, 0, 0.0};
+#pragma unroll
+        for (int s = 0; s < 7; ++s) {
+          if (dir == 0) cellv(G, U, a - 3 + s, r0 - 1 + t, none, v0[FROZEN ? s : 0]);
+          else cellv(G, U, r0 - 1 + t, a - 3 + s, none, v0[FROZEN ? s : 0]);
+        }
+      }
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         // interface between cells k = a-2+f and k+1: v index of cell k-1 is f
         const double(*w)[3] = &v[f];
-        if (f > 0) char_rec(dir, w, G.g, 0, ifv[t][f][0]);
-        if (f < 3) char_rec(dir, w, G.g, 1, ifv[t][f][1]);
+        const double(*w0)[3] = FROZEN ? &v0[FROZEN ? f : 0] : w;
+        if (f > 0) char_rec<FROZEN>(dir, w, w0, G.g, 0, ifv[t][f][0]);
+        if (f < 3) char_rec<FROZEN>(dir, w, w0, G.g, 1, ifv[t][f][1]);
       }
     }
     double fl[2][3] = {{0, 0, 0}, {0, 0, 0}};
@@ -270,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) k2_residual(const ProbDev2 *P, int l
   double acc = 0.0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
     double r[3];
-    local_residual2(G, U, c % G.Nx, c / G.Nx, np, r);
+    local_residual2<false>(G, U, c % G.Nx, c / G.Nx, np, r);
     R[c] = r[0];
     R[n + c] = r[1];
     R[2 * n + c] = r[2];
@@ -288,8 +329,9 @@ __global__ void k2_finish(const double *partials, int nparts, int n, double *res
   }
 }
 
-// One item = (cell, stencil block k): three perturbed local residuals.
-template <typename TJ>
+// One item = (cell, stencil block k): three perturbed local residuals
+// (FROZEN: the frozen linearisation).
+template <typename TJ, bool FROZEN>
 __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int level, int st, const double *U,
                                                         double eps, double alpha, const double *R, TJ *J) {
   const Geo2 G = make_geo2(*P, level);
@@ -307,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
     for (int m = 0; m < 3; ++m) {
       const Pert p{pj * G.Nx + pi, m, eps};
       double Rp[3];
-      local_residual2(G, U, i, j, p, Rp);
+      local_residual2<FROZEN>(G, U, i, j, p, Rp);
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
         double v = (Rp[l] - R0[l]) * ieps;
@@ -746,8 +788,12 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
 
 template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, TJ *J, cudaStream_t s) {
-  k2_jacobian<TJ><<<grid2((long)n * (st == ST_J21 ? 21 : 9)), kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
+                             const double *R, TJ *J, bool frozen, cudaStream_t s) {
+  const int grid = grid2((long)n * (st == ST_J21 ? 21 : 9));
+  if (frozen)
+    k2_jacobian<TJ, true><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
+  else
+    k2_jacobian<TJ, false><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
   return cudaGetLastError();
 }
 
@@ -822,7 +868,7 @@ cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream
 
 #define NSWE_2D_INSTANTIATE(T)                                                                                    \
   template cudaError_t launch2_jacobian<T>(const ProbDev2 *, int, int, int, const double *, double, double,      \
-                                           const double *, T *, cudaStream_t);                                   \
+                                           const double *, T *, bool, cudaStream_t);                             \
   template cudaError_t launch2_coarse_op<T>(int, int, int, const T *, T *, cudaStream_t);                        \
   template cudaError_t launch2_dinv<T>(int, int, const T *, T *, cudaStream_t);                                  \
   template cudaError_t launch2_sor<T>(int, int, int, const T *, const T *, const T *, T *, double, int, int, int, \

@@ -20,6 +20,7 @@ from . import build as _build
 
 MAX_LEVELS = 16
 JAC_SIMPLIFIED, JAC_FULL = 3, 5
+JAC_FROZEN = 0x100  # 2D: OR'd into the Jacobian choice, the frozen linearisation
 PREC_FP64, PREC_MIXED = 0, 1
 BC_DISCHARGE, BC_DEPTH, BC_STATE, BC_EXTRAP = 1, 2, 3, 4
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENAN", 6: "ENEGDEPTH",
@@ -106,6 +107,7 @@ EXPORTS = {
     "nswe_jacobian_full": (_i, [_vp, _vp, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_mg_vcycle": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
     "nswe_jacobian_f32": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
+    "nswe_jacobian_frozen": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_mg_vcycle_f32": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
     "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
@@ -320,7 +322,8 @@ def params2d_from(prm, levels=None) -> Params:
     nu1 = prm.nu1[0] if hasattr(prm.nu1, "__len__") else prm.nu1
     nu2 = prm.nu2[0] if hasattr(prm.nu2, "__len__") else prm.nu2
     return params(96, levels or prm.levels, alpha=prm.alpha, tau=prm.tau, omega=prm.omega, tol=prm.tol, nu1=nu1,
-                  nu2=nu2, nu3=prm.nu3, n_max=prm.n_max, nb=JAC_FULL if prm.st == 1 else JAC_SIMPLIFIED,
+                  nu2=nu2, nu3=prm.nu3, n_max=prm.n_max,
+                  nb=(JAC_FULL if prm.st == 1 else JAC_SIMPLIFIED) | (JAC_FROZEN if getattr(prm, "frozen", False) else 0),
                   nest_start=prm.nest_start, eps=prm.eps, colours2d=getattr(prm, "colours", 0))
 
 
@@ -345,6 +348,12 @@ def nswe_jacobian_simplified(ctx, prob, level, U, eps, alpha, R, J, res=None):
 def nswe_jacobian_full(ctx, prob, level, U, eps, alpha, R, J, res=None):
     _check("nswe_jacobian_full", lib().nswe_jacobian_full(
         ctx.h, prob.h, int(level), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
+
+
+def nswe_jacobian_frozen(ctx, prob, level, nb, U, eps, alpha, R, J, res=None):
+    """2D Jacobian (nb 9 or 21) under the frozen linearisation."""
+    _check("nswe_jacobian_frozen", lib().nswe_jacobian_frozen(
+        ctx.h, prob.h, int(level), int(nb), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
 
 
 def nswe_mg_vcycle(ctx, prob, level, nb, J, R, dU, prm: Params):
