@@ -521,6 +521,8 @@ def run_wedge2d(args):
     pw = nswe.Problem2D.from_inputs(ctx, w)
     p2 = nswe.params2d_from(I.Params2D(levels=args.levels2d, nu1=[20], nu2=[20], omega=args.omega2d, tol=TOL,
                                        n_max=3000, nest_start=args.levels2d - 2, frozen=frozen))
+    mixed = args.precision == "mixed"
+    p2.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
     U0 = torch.from_numpy(w.U0_start).cuda()
     Uo = torch.zeros((3, args.nx * args.ny), dtype=torch.float64, device="cuda")
     times, info = [], None
@@ -535,10 +537,11 @@ def run_wedge2d(args):
     print(json.dumps({
         "metric": METRIC, "value": 1000.0 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
         "config": {"workload": f"2D wedge channel {args.nx}x{args.ny} on [0,40]x[0,30], J9"
                                + (" (frozen linearisation)" if frozen else "") + f", {args.levels2d} levels, "
-                               f"nested from 16x8, omega {args.omega2d}, nu 20, nu3 3, eps 1e-6",
+                               f"nested from 16x8, omega {args.omega2d}, nu 20, nu3 3, eps 1e-6, "
+                               + ("mixed FP64/FP32" if mixed else "FP64"),
                    "theta_deg": big.meta["theta_deg"]},
         "converged": {"status": info["status"], "iters": info["iters"][:args.levels2d], "res": info["res"][0]},
         "kernels_512x256": kern}), flush=True)
@@ -668,45 +671,59 @@ def run_serve1d(args):
     print(json.dumps(line), flush=True)
 
 
+def batch2d_instances(B, family):
+    """The batched 2D workload: instance k is a wedge (even k, or all with
+    family "wedge") or a bump channel (odd k, or all with family "bump"), on
+    128 x 64 (5 levels) or 256 x 128 (6 levels) alternating in pairs. Wedges:
+    `wedge_serving_2d` under the frozen linearisation, omega 0.1, nested from
+    16 x 8; bumps: `bump_channel_2d` with Eq. 12, nested from 8 x 4 (Eq. 30);
+    both J9, nu1 = nu2 = 20, nu3 = 3, eps 1e-6."""
+    from paper_2505_10857_gb300 import inputs as I
+    inps, prms = [], []
+    for k in range(B):
+        fam = family if family != "mix" else ("wedge" if k % 2 == 0 else "bump")
+        Nx, Ny, lev = (256, 128, 6) if (k // 2) % 2 == 1 else (128, 64, 5)
+        if fam == "wedge":
+            inps.append(I.wedge_serving_2d(k, Nx, Ny, lev))
+            prms.append(I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=TOL, n_max=400, nest_start=lev - 2,
+                                   omega=0.1, frozen=True))
+        else:
+            inps.append(I.bump_channel_2d(k, Nx, Ny, lev))
+            prms.append(I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=TOL, n_max=400))
+    return inps, prms
+
+
 def run_batch2d(args):
-    """Batched 2D measurement (not the default line): `--batch2d` seeded
-    subcritical parabolic-bump channels (around Section 5.2.1, half 64 x 32
-    and half 128 x 64, J9, 20 smoothing steps, nested from 8 x 4), solved by batched
-    calls whose solves run concurrently, against the same solves one after
-    another. Host-timed (the solves run on several streams); the value counts
-    the solves that reached res < tol."""
+    """Batched 2D measurement (not the default line), shaped like the batched
+    2D serving configuration: `--batch2d` seeded supercritical wedge channels
+    (Froude 2-4, deflection 5-15 degrees) and subcritical parabolic-bump
+    channels (around Section 5.2.1) on 128 x 64 and 256 x 128 grids, each with
+    its own parameters, solved by one batched call whose solves run
+    concurrently, against the same solves one after another. Host-timed (the
+    solves run on several streams); the value counts the solves that reached
+    res < tol; latencies are per solve from the start of the batch."""
     import torch
 
-    from paper_2505_10857_gb300 import inputs as I
     from paper_2505_10857_gb300 import nswe
 
     mixed = args.precision != "fp64"
     B = args.batch2d
-    inps = [I.bump_channel_2d(k, *((64, 32, 4) if k % 2 == 0 else (128, 64, 5))) for k in range(B)]
+    inps, prms_in = batch2d_instances(B, args.family2d)
     ctx = nswe.Context(0)
-    groups = {}
-    for k, p in enumerate(inps):
-        groups.setdefault(p.levels, []).append(k)
     probs = [nswe.Problem2D.from_inputs(ctx, p) for p in inps]
     U0s = [torch.from_numpy(p.U0_start).cuda() for p in inps]
     Us = [torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda") for p in inps]
-    prms = {}
-    for lev in groups:
-        q = nswe.params2d_from(I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=TOL, n_max=400))
-        q.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
-        prms[lev] = q
+    prms = []
+    for q in prms_in:
+        c = nswe.params2d_from(q)
+        c.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
+        prms.append(c)
 
     def batched():
-        out = [None] * B
-        for lev, ks in groups.items():  # one batched call per level count (the parameters differ)
-            res = nswe.nswe_newton_solve_batch(ctx, [probs[k] for k in ks], [U0s[k] for k in ks],
-                                               [Us[k] for k in ks], prms[lev])
-            for k, r in zip(ks, res):
-                out[k] = r
-        return out
+        return nswe.nswe_newton_solve_batch_each(ctx, probs, U0s, Us, prms)
 
     def one_by_one():
-        return [nswe.nswe_newton_solve(ctx, probs[k], U0s[k], Us[k], prms[inps[k].levels]) for k in range(B)]
+        return [nswe.nswe_newton_solve(ctx, probs[k], U0s[k], Us[k], prms[k]) for k in range(B)]
 
     for _ in range(max(1, args.warmup)):
         batched()
@@ -720,24 +737,37 @@ def run_batch2d(args):
         times.append(time.perf_counter() - t0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    one_by_one()
+    seq = one_by_one()
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     ms = 1000.0 * statistics.mean(times)
     ok = [k for k in range(B) if infos[k]["status"] == 0]
+    # per-solve latency from the batch start, from the device timestamps of each solve
+    t0s = min(i["t_start_ns"] for i in infos)
+    lat = sorted((i["t_end_ns"] - t0s) / 1e6 for i in infos)
+    pick = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
+    kinds = {}
+    for k, p in enumerate(inps):
+        key = f"{'wedge' if 'froude' in p.meta else 'bump'} {p.Nx}x{p.Ny}"
+        kinds.setdefault(key, [0, 0])
+        kinds[key][0] += 1
+        kinds[key][1] += int(infos[k]["status"] == 0)
     print(json.dumps({
         "metric": METRIC, "value": len(ok) / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": f"2D batched: {B} seeded parabolic-bump channels (half 64x32, half 128x64), J9, nu 20, "
-                               + ("mixed FP64/FP32" if mixed else "FP64"), "seeds": "default_rng(5000 + k)"},
+        "config": {"workload": f"2D batched: {B} seeded channels ({args.family2d}: wedges Froude 2-4, 5-15 deg, "
+                               "frozen linearisation; parabolic bumps, Eq. 12), 128x64 and 256x128, J9, nu 20, "
+                               + ("mixed FP64/FP32" if mixed else "FP64"),
+                   "seeds": "wedges default_rng(7000 + k), bumps default_rng(5000 + k)"},
+        "latency_ms": {"p50": pick(0.5), "p99": pick(0.99), "what": "per-solve completion from the batch start"},
         "converged": {"all_status_ok": len(ok) == B, "converged": len(ok), "of": B,
-                      "by_grid": {f"{inps[k].Nx}x{inps[k].Ny}": sum(1 for j in ok if inps[j].Nx == inps[k].Nx)
-                                  for k in range(min(B, 2))},
-                      "failed": [(5000 + k, infos[k]["status"], infos[k]["iters"][:inps[k].levels]) for k in range(B)
-                                 if infos[k]["status"] != 0][:8],
-                      "max_res": max((infos[k]["res"][0] for k in ok), default=None)},
-        "one_by_one": {"solves_per_s": B / t_seq, "ms": 1000.0 * t_seq},
+                      "by_kind": {k: {"n": v[0], "converged": v[1]} for k, v in kinds.items()},
+                      "failed": [(inps[k].meta.get("seed"), infos[k]["status"], infos[k]["iters"][:inps[k].levels])
+                                 for k in range(B) if infos[k]["status"] != 0][:8],
+                      "max_res": max((infos[k]["res"][0] for k in ok), default=None),
+                      "one_by_one_equal_iters": all(seq[k]["iters"] == infos[k]["iters"] for k in range(B))},
+        "one_by_one": {"solves_per_s": sum(1 for i in seq if i["status"] == 0) / t_seq, "ms": 1000.0 * t_seq},
         "what": "host-timed: the batched call runs the solves concurrently on worker streams"}), flush=True)
 
 
@@ -754,7 +784,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d", "serve1d", "batch2d"])
-    ap.add_argument("--batch2d", type=int, default=32, help="batch2d: 2D problems per batch")
+    ap.add_argument("--batch2d", type=int, default=16, help="batch2d: 2D problems per batch")
+    ap.add_argument("--family2d", choices=["mix", "wedge", "bump"], default="mix",
+                    help="batch2d: wedge and bump channels, or one family")
     ap.add_argument("--requests", type=int, default=1024, help="serve1d: requests in the arrival schedule")
     ap.add_argument("--rate", type=float, default=1500.0, help="serve1d: Poisson arrival rate (requests/s)")
     ap.add_argument("--streams", type=int, default=8, help="serve1d: concurrent launches")

@@ -147,8 +147,9 @@ typedef struct {
   int level_status[NSWE_MAX_LEVELS]; /* nswe_status per nested level       */
   int total_iters;
   int vcycles;
-  unsigned long long t_start_ns;     /* device global timer at solve start */
-  unsigned long long t_end_ns;       /* device global timer at solve end   */
+  unsigned long long t_start_ns;     /* solve start: 1D the device global
+                                        timer, 2D the host steady clock   */
+  unsigned long long t_end_ns;       /* solve end, on the same clock       */
 } nswe_info;
 
 typedef struct nswe_ctx_s *nswe_ctx;
@@ -306,6 +307,21 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count,
                                     double *const *Us,
                                     const nswe_params *params,
                                     nswe_info *infos);
+
+/* Batched Algorithm 3 with parameters per problem (uneven instances sharing
+ * one batch): params is a HOST array of `count` records, params[i] for
+ * problem i, each checked as in nswe_newton_solve; everything else as in
+ * nswe_newton_solve_batch. A 1D batch is one launch, which computes in one
+ * arithmetic type: all records must then share `precision` (NSWE_EINVAL
+ * otherwise), while J3 and J5 tasks, relaxation factors, smoothing counts,
+ * tolerances and nested start levels may differ. In 2D each record may also
+ * choose its own Jacobian (J9, J21, | NSWE_JAC_FROZEN). */
+nswe_status nswe_newton_solve_batch_each(nswe_ctx ctx, int count,
+                                         const nswe_prob *probs,
+                                         const double *const *U0s,
+                                         double *const *Us,
+                                         const nswe_params *params,
+                                         nswe_info *infos);
 
 /* Launch shapes of the batched 1D solve kernel (one thread block per
  * problem): shape i has nswe_solve_shape_info(i) threads per block and is

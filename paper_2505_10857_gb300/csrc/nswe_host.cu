@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <atomic>
+#include <chrono>
 #include <thread>
 #include <vector>
 
@@ -19,7 +20,8 @@ struct nswe_ctx_s {
   int *status;           // device status word of standalone V-cycles
   SolveTask *tasks;      // device task array
   nswe_info *infos;      // device info records
-  int cap;               // capacity of tasks / infos
+  nswe_params *prms;     // device per-task parameters (nswe_newton_solve_batch_each)
+  int cap;               // capacity of tasks / infos / prms
   int solve_shape[2];    // launch shape of the 1D solve kernel per precision
 };
 
@@ -106,17 +108,21 @@ nswe_status ensure_cap(nswe_ctx ctx, int count) {
   int cap = count < 64 ? 64 : count;
   SolveTask *t = nullptr;
   nswe_info *i = nullptr;
+  nswe_params *q = nullptr;
   if (cudaMalloc(&t, sizeof(SolveTask) * cap) != cudaSuccess) return NSWE_ENOMEM;
-  if (cudaMalloc(&i, sizeof(nswe_info) * cap) != cudaSuccess) {
+  if (cudaMalloc(&i, sizeof(nswe_info) * cap) != cudaSuccess || cudaMalloc(&q, sizeof(nswe_params) * cap) != cudaSuccess) {
     cudaFree(t);
+    cudaFree(i);
     return NSWE_ENOMEM;
   }
   // Buffers may still be read by queued work on the context stream.
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->tasks);
   cudaFree(ctx->infos);
+  cudaFree(ctx->prms);
   ctx->tasks = t;
   ctx->infos = i;
+  ctx->prms = q;
   ctx->cap = cap;
   return NSWE_OK;
 }
@@ -406,12 +412,26 @@ nswe_status solve2d(nswe_prob_s *p, const double *U0, double *U, const nswe_para
 // solve has finished.
 constexpr int kSolve2DWorkers = 8;
 
+// Host steady clock in ns: the time stamps of 2D solves, which the host sequences.
+unsigned long long host_ns() {
+  return (unsigned long long)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// prms[each ? i : 0] are problem i's parameters.
 nswe_status solve2d_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
-                          double *const *Us, const nswe_params &prm, nswe_info *infos) {
+                          double *const *Us, const nswe_params *prms, bool each, nswe_info *infos) {
   if (count == 1) {
     nswe_info inf;
-    nswe_status st = solve2d(probs[0], U0s[0], Us[0], prm, &inf, ctx->stream);
-    if (infos) infos[0] = inf;
+    const unsigned long long t0 = host_ns();
+    nswe_status st = solve2d(probs[0], U0s[0], Us[0], prms[0], &inf, ctx->stream);
+    if (infos) {
+      if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NSWE_ECUDA;
+      inf.t_start_ns = t0;
+      inf.t_end_ns = host_ns();
+      infos[0] = inf;
+    }
     return st;
   }
   cudaEvent_t ready = nullptr;
@@ -438,8 +458,11 @@ nswe_status solve2d_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const
       }
       for (int i = next++; i < count; i = next++) {
         std::memset(&rec[i], 0, sizeof(nswe_info));
-        status[i] = solve2d(probs[i], U0s[i], Us[i], prm, &rec[i], s);
-        if (status[i] == NSWE_ECUDA) cuda_error = true;
+        const unsigned long long t0 = host_ns();
+        status[i] = solve2d(probs[i], U0s[i], Us[i], prms[each ? i : 0], &rec[i], s);
+        if (status[i] == NSWE_ECUDA || cudaStreamSynchronize(s) != cudaSuccess) cuda_error = true;
+        rec[i].t_start_ns = t0;
+        rec[i].t_end_ns = host_ns();
       }
       if (cudaStreamSynchronize(s) != cudaSuccess) cuda_error = true;
       cudaStreamDestroy(s);
@@ -547,6 +570,7 @@ nswe_status nswe_ctx_destroy(nswe_ctx ctx) {
   cudaFree(ctx->status);
   cudaFree(ctx->tasks);
   cudaFree(ctx->infos);
+  cudaFree(ctx->prms);
   delete ctx;
   return NSWE_OK;
 }
@@ -884,30 +908,39 @@ nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb, cons
              : NSWE_ECUDA;
 }
 
-nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
-                                    double *const *Us, const nswe_params *params, nswe_info *infos) {
-  if (!ctx || count < 0 || (count > 0 && (!probs || !U0s || !Us))) return NSWE_EINVAL;
+// Batched Algorithm 3; params[each ? i : 0] are problem i's parameters.
+static nswe_status solve_batch_common(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
+                                      double *const *Us, const nswe_params *params, bool each, nswe_info *infos) {
+  if (!ctx || count < 0 || (count > 0 && (!probs || !U0s || !Us || !params))) return NSWE_EINVAL;
   if (count == 0) return NSWE_OK;
   if (count > (1 << 20)) return NSWE_EINVAL;
   std::vector<SolveTask> tasks(count);
+  int nb = 3;
   for (int i = 0; i < count; ++i) {
     nswe_prob p = probs[i];
+    const nswe_params *q = params + (each ? i : 0);
     if (!p || p->ctx != ctx || !U0s[i] || !Us[i]) return NSWE_EINVAL;
     if (p->dim != probs[0]->dim) return NSWE_EINVAL;
-    int s0 = (params && params->nest_start >= 0 && params->nest_start < p->levels) ? params->nest_start
-                                                                                     : p->levels - 1;
-    nswe_status st = check_params(params, p, s0);
+    int s0 = (q->nest_start >= 0 && q->nest_start < p->levels) ? q->nest_start : p->levels - 1;
+    nswe_status st = check_params(q, p, s0);
     if (st != NSWE_OK) return st;
+    // one 1D launch computes in one arithmetic type
+    if (q->precision != params[0].precision) return NSWE_EINVAL;
+    if ((q->jacobian & ~NSWE_JAC_FROZEN) == NSWE_JAC_FULL) nb = 5;
   }
   DeviceGuard dg(ctx->device);
   if (probs[0]->dim == 2) {
     for (int i = 1; i < count; ++i)
       for (int k = 0; k < i; ++k)
         if (probs[k] == probs[i]) return NSWE_EINVAL;  // one problem's workspace cannot serve two solves at once
-    return solve2d_batch(ctx, count, probs, U0s, Us, *params, infos);
+    return solve2d_batch(ctx, count, probs, U0s, Us, params, each, infos);
   }
   nswe_status st = ensure_cap(ctx, count);
   if (st != NSWE_OK) return st;
+  cudaStream_t s = ctx->stream;
+  if (each && cudaMemcpyAsync(ctx->prms, params, sizeof(nswe_params) * count, cudaMemcpyHostToDevice, s) !=
+                  cudaSuccess)
+    return NSWE_ECUDA;
   int max_coarse = 4;
   for (int i = 0; i < count; ++i) {
     const int c = probs[i]->N >> (probs[i]->levels - 1);
@@ -916,18 +949,15 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
     tasks[i].U0 = U0s[i];
     tasks[i].U = Us[i];
     tasks[i].info = ctx->infos + i;
-    tasks[i].prm = nullptr;
+    tasks[i].prm = each ? ctx->prms + i : nullptr;
     tasks[i].derive = 0;
     tasks[i].done = nullptr;
   }
-  cudaStream_t s = ctx->stream;
   if (cudaMemcpyAsync(ctx->tasks, tasks.data(), sizeof(SolveTask) * count, cudaMemcpyHostToDevice, s) !=
       cudaSuccess)
     return NSWE_ECUDA;
   const int shape = ctx->solve_shape[params->precision == NSWE_PREC_MIXED ? 1 : 0];
-  if (launch_solve_sized(ctx->tasks, count, *params, max_coarse, params->jacobian == NSWE_JAC_FULL ? 5 : 3, shape,
-                         s) != cudaSuccess)
-    return NSWE_ECUDA;
+  if (launch_solve_sized(ctx->tasks, count, *params, max_coarse, nb, shape, s) != cudaSuccess) return NSWE_ECUDA;
   if (infos) {
     if (cudaMemcpyAsync(infos, ctx->infos, sizeof(nswe_info) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return NSWE_ECUDA;
@@ -938,6 +968,16 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *pr
     return (nswe_status)worst;
   }
   return NSWE_OK;
+}
+
+nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
+                                    double *const *Us, const nswe_params *params, nswe_info *infos) {
+  return solve_batch_common(ctx, count, probs, U0s, Us, params, false, infos);
+}
+
+nswe_status nswe_newton_solve_batch_each(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
+                                         double *const *Us, const nswe_params *params, nswe_info *infos) {
+  return solve_batch_common(ctx, count, probs, U0s, Us, params, true, infos);
 }
 
 nswe_status nswe_newton_solve(nswe_ctx ctx, nswe_prob prob, const double *U0, double *U, const nswe_params *params,

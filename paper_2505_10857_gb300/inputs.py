@@ -568,6 +568,22 @@ def wedge(Nx, Ny, levels, theta_deg=8.95, x1=5.0, y1=2.0, x_wall=1.0, speed=8.57
                            meta=dict(meta or {}, theta_deg=theta_deg, x_wall=xw, case="wedge"))
 
 
+def wedge_serving_2d(k, Nx=128, Ny=64, levels=5, start_level=None):
+    """Seeded supercritical wedge channel of the batched 2D workload (seed
+    7000 + k): the rotated-frame wedge of Section 5.2.2 on [0, 40] x [0, 30]
+    with the wall from x = 8 / cos(theta), deflection theta ~ U[5, 15] degrees,
+    inflow depth 1 and Froude number F ~ U[2, 4] (speed F sqrt(g)); every draw
+    lies below the largest deflection of an attached oblique jump (19.6
+    degrees at F = 2). Guess Eq. 31 on start_level (default: the 16 x 8 grid
+    of a grid whose coarsest level is 8 x 4, as in Section 5.2.2)."""
+    rng = np.random.default_rng(7000 + k)
+    th = float(rng.uniform(5.0, 15.0))
+    F = float(rng.uniform(2.0, 4.0))
+    sl = levels - 2 if start_level is None else start_level
+    return wedge(Nx, Ny, levels, theta_deg=th, x1=40.0, y1=30.0, x_wall=8.0, speed=F * math.sqrt(G_PAPER),
+                 start_level=sl, meta={"seed": 7000 + k, "froude": F})
+
+
 def wedge_channel(k, Nx=512, Ny=256, levels=7):
     """Seeded wedge channel: 512 x 256 cells on [0, 40] x [0, 30], deflection
     theta ~ U[8, 15] degrees, inflow depth 1 and speed 8.57 (Froude 2.74), wall

@@ -112,6 +112,8 @@ EXPORTS = {
     "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                      ctypes.POINTER(Params), ctypes.POINTER(Info)]),
+    "nswe_newton_solve_batch_each": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                                     ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_noalloc": (_i, [_i, _vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D),
                                        ctypes.POINTER(BC1D), _dp, _dp, ctypes.POINTER(Params), _vp]),
     "nswe_solve_shape_count": (_i, []),
@@ -406,6 +408,24 @@ def nswe_newton_solve_batch(ctx, probs: Sequence[Problem1D], U0s, Us, prm: Param
     rc = lib().nswe_newton_solve_batch(ctx.h, n, ph, u0, uu, ctypes.byref(prm), infos)
     if rc in (1, 2, 3):
         raise NsweError("nswe_newton_solve_batch", rc)
+    return [infos[i].as_dict(probs[i].levels) for i in range(n)] if infos is not None else None
+
+
+def nswe_newton_solve_batch_each(ctx, probs, U0s, Us, prms: Sequence[Params], want_info=True):
+    """Batched solve with one parameter record per problem."""
+    n = len(probs)
+    if len(prms) != n:
+        raise ValueError("one parameter record per problem")
+    for p, u0, u, q in zip(probs, U0s, Us, prms):
+        _check_solve_sizes(p, u0, u, q)
+    ph = (_vp * n)(*[p.h.value for p in probs])
+    u0 = (_dp * n)(*[_ptr(u) for u in U0s])
+    uu = (_dp * n)(*[_ptr(u) for u in Us])
+    pa = (Params * n)(*prms)
+    infos = (Info * n)() if want_info else None
+    rc = lib().nswe_newton_solve_batch_each(ctx.h, n, ph, u0, uu, pa, infos)
+    if rc in (1, 2, 3):
+        raise NsweError("nswe_newton_solve_batch_each", rc)
     return [infos[i].as_dict(probs[i].levels) for i in range(n)] if infos is not None else None
 
 

@@ -190,6 +190,31 @@ def test_batch_equals_single(nswe, ctx):
         assert np.array_equal(host(Us[k]), singles[k])
 
 
+def test_batch_with_parameters_per_problem(nswe, ctx):
+    """Uneven 1D instances in one launch, each with its own parameters (J3 and
+    J5, relaxation, smoothing, sizes and nested starts): every result equals,
+    bit for bit, the same problem solved alone with its parameters; a batch
+    that mixes arithmetic types is refused."""
+    inps = [I.channel_small(0), I.channel_small(1), I.channel_small(5, N=400, levels=5), I.paper_smooth_subcritical(384, 3)]
+    prms = [I.Params1D.for_problem(inps[0], tol=1e-10, n_max=500),
+            I.Params1D.for_problem(inps[1], tol=1e-10, n_max=500, nb=5),
+            I.Params1D.for_problem(inps[2], tol=1e-10, n_max=500, omega=1.0, nu1=3, nu2=3),
+            I.Params1D.for_problem(inps[3], tol=1e-11, n_max=500)]
+    singles = [_solve_gpu(nswe, ctx, p, q) for p, q in zip(inps, prms)]
+    probs = [nswe.Problem1D.from_inputs(ctx, p) for p in inps]
+    U0s = [dev(p.U0_start) for p in inps]
+    Us = [torch.zeros((2, p.N), dtype=torch.float64, device="cuda") for p in inps]
+    cp = [nswe.params_from(q) for q in prms]
+    infos = nswe.nswe_newton_solve_batch_each(ctx, probs, U0s, Us, cp)
+    for k in range(len(inps)):
+        assert infos[k]["status"] == 0 == singles[k][1]["status"], (k, infos[k])
+        assert infos[k]["iters"] == singles[k][1]["iters"]
+        assert np.array_equal(host(Us[k]), singles[k][0])
+    cp[1].precision = nswe.PREC_MIXED
+    with pytest.raises(nswe.NsweError):
+        nswe.nswe_newton_solve_batch_each(ctx, probs, U0s, Us, cp)
+
+
 def test_invalid_arguments_rejected(nswe, ctx):
     inp = I.channel_small(0)
     with pytest.raises(nswe.NsweError):

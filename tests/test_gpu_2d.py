@@ -242,6 +242,34 @@ def test_2d_batch_runs_concurrently_and_equals_single(nswe, ctx):
         nswe.nswe_newton_solve_batch(ctx, [probs[0], probs[0]], [U0s[0], U0s[0]], [Us[0], Us[0]], prm)
 
 
+def test_2d_batch_with_parameters_per_problem(nswe, ctx):
+    """Wedges under the frozen linearisation (omega 0.1, nested from 16 x 8)
+    and bumps with Eq. 12 (nested from 8 x 4, J9 and J21) in one batched
+    call, each with its own parameters: every result equals, bit for bit,
+    the problem solved alone with its parameters."""
+    g = I.G_PAPER
+    inps = [I.wedge(32, 16, 3, theta_deg=12.0, speed=3.0 * np.sqrt(g), x1=40.0, y1=30.0, x_wall=8.0, start_level=1),
+            I.bump_channel_2d(1, 32, 16, 3), I.wedge(16, 8, 2, start_level=1), I.bump_channel_2d(2, 32, 16, 3)]
+    prms = [I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400, nest_start=1, omega=0.1, frozen=True),
+            I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400),
+            I.Params2D(levels=2, nu1=[15], nu2=[15], tol=1e-10, n_max=400, nest_start=1, omega=0.1, frozen=True),
+            I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-10, n_max=400, st=1)]
+    cp = [nswe.params2d_from(q) for q in prms]
+    probs = [nswe.Problem2D.from_inputs(ctx, p) for p in inps]
+    U0s = [dev(p.U0_start) for p in inps]
+    alone = []
+    for pr, u0, p, q in zip(probs, U0s, inps, cp):
+        U = torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda")
+        info = nswe.nswe_newton_solve(ctx, pr, u0, U, q)
+        alone.append((host(U), info))
+    Us = [torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda") for p in inps]
+    infos = nswe.nswe_newton_solve_batch_each(ctx, probs, U0s, Us, cp)
+    for k in range(len(inps)):
+        assert infos[k]["status"] == 0 == alone[k][1]["status"], (k, infos[k], alone[k][1])
+        assert infos[k]["iters"] == alone[k][1]["iters"]
+        assert np.array_equal(host(Us[k]), alone[k][0])
+
+
 def test_guess_sized_for_another_level_is_refused(nswe, ctx):
     """The guess must hold the start level's state: one built for the 8 x 4
     grid, given with a nested start on 16 x 8, is refused before any launch
