@@ -112,8 +112,17 @@ cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream
 // more than the pass. One SM issues FP32 at 64x its FP64 rate, so the FP64
 // tail stops at far smaller levels.
 template <typename T>
-constexpr int tail2_cells() { return sizeof(T) == 4 ? 4096 : 256; }
-constexpr int kTail2Threads = 1024;
+#ifndef NSWE_TAIL_F64
+#define NSWE_TAIL_F64 256
+#endif
+#ifndef NSWE_TAIL_F32
+#define NSWE_TAIL_F32 4096
+#endif
+constexpr int tail2_cells() { return sizeof(T) == 4 ? NSWE_TAIL_F32 : NSWE_TAIL_F64; }
+#ifndef NSWE_TAIL_THREADS
+#define NSWE_TAIL_THREADS 1024
+#endif
+constexpr int kTail2Threads = NSWE_TAIL_THREADS;
 template <typename T>
 struct Tail2 {
   int ls, L;

@@ -8,6 +8,7 @@
 //
 // A 2D problem is large (512 x 256 cells = 131k cells, 85-200 MB of Jacobian),
 // so every phase is a grid-wide kernel over cells; the host sequences them.
+#include <type_traits>
 #include <cmath>
 
 #include "nswe_internal.h"
@@ -64,6 +65,18 @@ __device__ __forceinline__ Geo2 make_geo2(const ProbDev2 &P, int l) {
 }
 
 // Perturbation of one interior cell in one component (cp < 0: none).
+// Largest colour pass (cells) that runs as k2_sor_split, per precision.
+#ifndef NSWE_SOR_SPLIT_F64
+#define NSWE_SOR_SPLIT_F64 (1L << 40)
+#endif
+#ifndef NSWE_SOR_SPLIT_F32
+#define NSWE_SOR_SPLIT_F32 (1L << 40)
+#endif
+#ifndef NSWE_SOR_UNROLL
+#define NSWE_SOR_UNROLL 1
+#endif
+constexpr long kSorSplitF64 = NSWE_SOR_SPLIT_F64, kSorSplitF32 = NSWE_SOR_SPLIT_F32;
+
 struct Pert {
   int cp, m;
   double eps;
@@ -493,6 +506,97 @@ __global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const
               gridDim.x * blockDim.x);
 }
 
+// Cell (i, j) of item t of a colour pass (the enumeration of sor_pass);
+// false if the item lies beyond the grid.
+__device__ __forceinline__ bool sor_item_cell(int Nx, int mode, int Kc, int col, int P, int W, int t, int &i, int &j) {
+  if (mode == 0) {
+    i = col % P + (t % W) * P;
+    j = col / P + (t / W) * P;
+    return true;
+  }
+  j = t / W;
+  const int a = mode == 1 ? col - j : j + Nx - 1 - col;
+  i = ((a % Kc) + Kc) % Kc + (t % W) * Kc;
+  return i < Nx;
+}
+
+// The same colour pass with three lanes per cell: lane l of a cell's group
+// forms component l of r = R + sum_k J_k dU_k (the expression of sor_cell2,
+// so the results are the same bits), the group exchanges r by shuffles, and
+// lane l updates dU component l. Ten cells per warp (lanes 30, 31 idle). On
+// small grids this spreads a pass over three times as many warps, each with a
+// third of the dependent FP64 instructions: an FP64 warp instruction holds
+// its SMSP's FP64 unit for tens of cycles, so the length of one thread's
+// chain, not the total work, bounds such a pass.
+// STC >= 0: the stencil fixed at compile time (the neighbour loop unrolls
+// and its loads issue together); -1: the stencil st of the call.
+template <typename T, int STC>
+__device__ __forceinline__ void sor_pass_split(int Nx, int Ny, int st_arg, const T *J, const T *Dinv, const T *R,
+                                               T *dU, double omega_d, int mode, int Kc, int col, int reps,
+                                               int warp0, int warps) {
+  const int st = STC >= 0 ? STC : st_arg;
+  int P, W, items;
+  sor_items(Nx, Ny, st, mode, Kc, col, P, W, items);
+  const T omega = T(omega_d);
+  const int lane = threadIdx.x & 31, g = lane / 3, l = lane - 3 * g, src = 3 * g;
+  const int n = Nx * Ny, K = st_size(st), kc = st_center(st);
+  for (int w = warp0; w * 10 < items; w += warps) {  // warp-uniform
+    const int t = w * 10 + g;
+    int i = 0, j = 0;
+    const bool on = lane < 30 && t < items && sor_item_cell(Nx, mode, Kc, col, P, W, t, i, j);
+    const int c = j * Nx + i;
+    T r = on ? R[l * n + c] : T(0.0);
+    if (on)
+#pragma unroll
+      for (int k = 0; k < (STC >= 0 ? (STC == ST_J9 ? 9 : STC == ST_P5 ? 5 : 21) : K); ++k) {
+        if (k == kc) continue;
+        const int p = i + st_off(st, k, 0), q = j + st_off(st, k, 1);
+        if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
+        const int cp = q * Nx + p;
+        const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
+        r += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
+             J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
+      }
+    const T r0 = __shfl_sync(0xffffffffu, r, min(src, 31));
+    const T r1 = __shfl_sync(0xffffffffu, r, min(src + 1, 31));
+    const T r2 = __shfl_sync(0xffffffffu, r, min(src + 2, 31));
+    if (on) {
+      const T tl = Dinv[(size_t)(l * 3 + 0) * n + c] * r0 + Dinv[(size_t)(l * 3 + 1) * n + c] * r1 +
+                   Dinv[(size_t)(l * 3 + 2) * n + c] * r2;
+      T x = dU[l * n + c];
+      for (int s = 0; s < reps; ++s) x = (T(1.0) - omega) * x - omega * tl;
+      dU[l * n + c] = x;
+    }
+  }
+}
+
+template <typename T, int STC>
+__global__ void __launch_bounds__(kThreads) k2_sor_split(int Nx, int Ny, int st, const T *J, const T *Dinv,
+                                                         const T *R, T *dU, double omega, int mode, int Kc, int col,
+                                                         int reps) {
+  sor_pass_split<T, STC>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps,
+                         (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
+// A colour pass by the threads of one block (the tail kernel): in FP64 split
+// as above; in FP32, where the dependent chains are short, one thread per
+// cell measured faster.
+template <typename T>
+__device__ void sor_pass_block_split(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU,
+                                     double omega, int mode, int Kc, int col, int reps) {
+  if (!std::is_same<T, double>::value) {
+    sor_pass<T>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, threadIdx.x, blockDim.x);
+    return;
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (st == ST_J9)
+    sor_pass_split<T, ST_J9>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw);
+  else if (st == ST_P5)
+    sor_pass_split<T, ST_P5>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw);
+  else
+    sor_pass_split<T, -1>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw);
+}
+
 template <typename T>
 __device__ void restrict_cells2(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc, int first,
                                 int stride) {
@@ -681,8 +785,7 @@ __device__ void smooth_block(const Tail2<T> &t, int l, int steps, double omega, 
       for (int d = 0; d < 4; ++d)
         for (int q = 0; q < Kc; ++q) {
           const int mode = (d % 2) + 1, col = d < 2 ? q : Kc - 1 - q;
-          sor_pass<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, mode, Kc, col, 1, threadIdx.x,
-                      blockDim.x);
+          sor_pass_block_split<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, mode, Kc, col, 1);
           __syncthreads();
         }
     return;
@@ -697,15 +800,14 @@ __device__ void smooth_block(const Tail2<T> &t, int l, int steps, double omega, 
         continue;
       }
       if (prev >= 0) {
-        sor_pass<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, 0, 0, prev, reps, threadIdx.x,
-                    blockDim.x);
+        sor_pass_block_split<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, 0, 0, prev, reps);
         __syncthreads();
       }
       prev = col;
       reps = 1;
     }
   if (prev >= 0) {
-    sor_pass<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, 0, 0, prev, reps, threadIdx.x, blockDim.x);
+    sor_pass_block_split<T>(Nx, Ny, st, t.J[l], t.Dinv[l], t.R[l], t.dU[l], omega, 0, 0, prev, reps);
     __syncthreads();
   }
 }
@@ -817,7 +919,21 @@ cudaError_t launch2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const
   if (mode == 0 && (st == ST_J9 || st == ST_P5)) items = (long)((Nx + (st == ST_J9 ? 3 : 2) - 1) / (st == ST_J9 ? 3 : 2)) * Ny;
   else if (mode == 0) items = (long)((Nx + 2) / (st == ST_J21 ? 3 : 2) + 1) * ((Ny + 2) / (st == ST_J21 ? 3 : 2) + 1);
   else items = (long)((Nx + Kc - 1) / Kc) * Ny;
-  k2_sor<T><<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+  if (items <= (std::is_same<T, double>::value ? kSorSplitF64 : kSorSplitF32)) {
+    // three lanes per cell; one warp per block on small passes so that the
+    // block scheduler spreads the warps over the SMs
+    const long warps = (items + 9) / 10;
+    const int bs = warps <= 4L * 152 ? 32 : 128;
+    const unsigned grid = (unsigned)((warps * 32 + bs - 1) / bs);
+    if (NSWE_SOR_UNROLL && st == ST_J9)
+      k2_sor_split<T, ST_J9><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+    else if (NSWE_SOR_UNROLL && st == ST_P5)
+      k2_sor_split<T, ST_P5><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+    else
+      k2_sor_split<T, -1><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+  } else {
+    k2_sor<T><<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+  }
   return cudaGetLastError();
 }
 
