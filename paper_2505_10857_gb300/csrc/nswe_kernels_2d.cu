@@ -64,7 +64,6 @@ __device__ __forceinline__ Geo2 make_geo2(const ProbDev2 &P, int l) {
   return G;
 }
 
-// Perturbation of one interior cell in one component (cp < 0: none).
 // Largest colour pass (cells) that runs as k2_sor_split, per precision.
 #ifndef NSWE_SOR_SPLIT_F64
 #define NSWE_SOR_SPLIT_F64 (1L << 40)
@@ -77,6 +76,7 @@ __device__ __forceinline__ Geo2 make_geo2(const ProbDev2 &P, int l) {
 #endif
 constexpr long kSorSplitF64 = NSWE_SOR_SPLIT_F64, kSorSplitF32 = NSWE_SOR_SPLIT_F32;
 
+// Perturbation of one interior cell in one component (cp < 0: none).
 struct Pert {
   int cp, m;
   double eps;
@@ -217,88 +217,130 @@ __device__ __forceinline__ void llf(int dir, const double L[3], const double R[3
   for (int m = 0; m < 3; ++m) F[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * a * (R[m] - L[m]);
 }
 
+// Interface values of one line of direction dir (dir 0: row r, positions
+// a-3..a+3 along x; dir 1: column r, positions a-3..a+3 along y) at the
+// interfaces a-3/2 .. a+3/2 (f = 0..3), sides U^- (0) and U^+ (1), of the
+// (possibly perturbed) state; FROZEN: weights and eigenvectors from U itself.
+template <bool FROZEN>
+__device__ __forceinline__ void line_values2(const Geo2 &G, const double *U, int dir, int a, int r, const Pert &p,
+                                             double out[4][2][3]) {
+  double v[7][3];                 // line cells a-3 .. a+3
+  double v0[FROZEN ? 7 : 1][3];   // the same cells unperturbed (FROZEN)
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    if (dir == 0) cellv(G, U, a - 3 + s, r, p, v[s]);
+    else cellv(G, U, r, a - 3 + s, p, v[s]);
+  }
+  if (FROZEN) {
+    const Pert none{-1, 0, 0.0};
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      if (dir == 0) cellv(G, U, a - 3 + s, r, none, v0[FROZEN ? s : 0]);
+      else cellv(G, U, r, a - 3 + s, none, v0[FROZEN ? s : 0]);
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    // interface between cells k = a-2+f and k+1: v index of cell k-1 is f
+    const double(*w)[3] = &v[f];
+    const double(*w0)[3] = FROZEN ? &v0[FROZEN ? f : 0] : w;
+    if (f > 0) char_rec<FROZEN>(dir, w, w0, G.g, 0, out[f][0]);
+    if (f < 3) char_rec<FROZEN>(dir, w, w0, G.g, 1, out[f][1]);
+  }
+}
+
+// The direction-dir part of R_ij from the interface values of its three
+// lines (transverse positions r0-1, r0, r0+1): the edge fluxes at the two
+// Gauss points of the faces a-1/2, a+1/2 (flux = right minus left) and the
+// source component 1 + dir, -(1/4) sum g h b_dir (S / (dx dy)).
+__device__ __forceinline__ void dir_part2(const Geo2 &G, int dir, int c, const double ifv[3][4][2][3],
+                                          double flux[3], double &S) {
+  const int n = G.Nx * G.Ny;
+  double fl[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  double hq[2][4];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double sg = q == 0 ? -kTq : kTq;
+    double gv[4][2][3];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        if ((f == 0 && sd == 0) || (f == 3 && sd == 1)) continue;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) gv[f][sd][m] = ifv[1][f][sd][m] + sg * (ifv[2][f][sd][m] - ifv[0][f][sd][m]);
+      }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      double F[3];
+      llf(dir, gv[1 + e][0], gv[1 + e][1], G.g, F);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) fl[e][m] += 0.5 * F[m];
+    }
+    hq[q][0] = gv[0][1][0];
+    hq[q][1] = gv[1][1][0];
+    hq[q][2] = gv[2][0][0];
+    hq[q][3] = gv[3][0][0];
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) flux[m] = fl[1][m] - fl[0][m];
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp) {
+      const double hv = kLag2[pp][0] * hq[q][0] + kLag2[pp][1] * hq[q][1] + kLag2[pp][2] * hq[q][2] +
+                        kLag2[pp][3] * hq[q][3];
+      const int beta = dir == 0 ? q : pp, gamma = dir == 0 ? pp : q;
+      acc += G.g * hv * G.gq[(dir * 4 + 2 * beta + gamma) * n + c];
+    }
+  S = -0.25 * acc;
+}
+
 // Local residual R_ij (Eq. 20) of the (possibly perturbed) state; FROZEN:
 // the reconstructions take their weights and eigenvectors from U itself.
 template <bool FROZEN>
 __device__ void local_residual2(const Geo2 &G, const double *U, int i, int j, const Pert &p, double R[3]) {
-  const int n = G.Nx * G.Ny, c = j * G.Nx + i;
+  const int c = j * G.Nx + i;
   double flux[2][3], S[3] = {0.0, 0.0, 0.0};
 #pragma unroll 1
   for (int dir = 0; dir < 2; ++dir) {
     const int a = dir == 0 ? i : j, r0 = dir == 0 ? j : i;
-    // gv[q][f][side][m]: values at the two Gauss lines q of the interfaces
-    // f = a-3/2, a-1/2, a+1/2, a+3/2 (f = 0..3)
     double ifv[3][4][2][3];
 #pragma unroll 1
-    for (int t = 0; t < 3; ++t) {
-      double v[7][3];                 // line cells a-3 .. a+3
-      double v0[FROZEN ? 7 : 1][3];   // the same cells unperturbed (FROZEN)
-#pragma unroll
-      for (int s = 0; s < 7; ++s) {
-        if (dir == 0) cellv(G, U, a - 3 + s, r0 - 1 + t, p, v[s]);
-        else cellv(G, U, r0 - 1 + t, a - 3 + s, p, v[s]);
-      }
-      if (FROZEN) {
-        const Pert none{-1, 0, 0.0};
-#pragma unroll
-        for (int s = 0; s < 7; ++s) {
-          if (dir == 0) cellv(G, U, a - 3 + s, r0 - 1 + t, none, v0[FROZEN ? s : 0]);
-          else cellv(G, U, r0 - 1 + t, a - 3 + s, none, v0[FROZEN ? s : 0]);
-        }
-      }
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        // interface between cells k = a-2+f and k+1: v index of cell k-1 is f
-        const double(*w)[3] = &v[f];
-        const double(*w0)[3] = FROZEN ? &v0[FROZEN ? f : 0] : w;
-        if (f > 0) char_rec<FROZEN>(dir, w, w0, G.g, 0, ifv[t][f][0]);
-        if (f < 3) char_rec<FROZEN>(dir, w, w0, G.g, 1, ifv[t][f][1]);
-      }
-    }
-    double fl[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    double hq[2][4];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const double sg = q == 0 ? -kTq : kTq;
-      double gv[4][2][3];
-#pragma unroll
-      for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-          if ((f == 0 && sd == 0) || (f == 3 && sd == 1)) continue;
-#pragma unroll
-          for (int m = 0; m < 3; ++m) gv[f][sd][m] = ifv[1][f][sd][m] + sg * (ifv[2][f][sd][m] - ifv[0][f][sd][m]);
-        }
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        double F[3];
-        llf(dir, gv[1 + e][0], gv[1 + e][1], G.g, F);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) fl[e][m] += 0.5 * F[m];
-      }
-      hq[q][0] = gv[0][1][0];
-      hq[q][1] = gv[1][1][0];
-      hq[q][2] = gv[2][0][0];
-      hq[q][3] = gv[3][0][0];
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) flux[dir][m] = fl[1][m] - fl[0][m];
-    double acc = 0.0;
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int pp = 0; pp < 2; ++pp) {
-        const double hv = kLag2[pp][0] * hq[q][0] + kLag2[pp][1] * hq[q][1] + kLag2[pp][2] * hq[q][2] +
-                          kLag2[pp][3] * hq[q][3];
-        const int beta = dir == 0 ? q : pp, gamma = dir == 0 ? pp : q;
-        acc += G.g * hv * G.gq[(dir * 4 + 2 * beta + gamma) * n + c];
-      }
-    S[1 + dir] = -0.25 * acc;
+    for (int t = 0; t < 3; ++t) line_values2<FROZEN>(G, U, dir, a, r0 - 1 + t, p, ifv[t]);
+    dir_part2(G, dir, c, ifv, flux[dir], S[1 + dir]);
   }
 #pragma unroll
   for (int m = 0; m < 3; ++m) R[m] = flux[0][m] / G.dx + flux[1][m] / G.dy - S[m];
 }
 
+// Interior cell whose state the (possibly ghost) position (i, j) reads, as in
+// cellv, or -1 where it reads boundary data only (inflow ghosts).
+__device__ __forceinline__ int cell_src(const Geo2 &G, int i, int j) {
+  const int Nx = G.Nx, Ny = G.Ny;
+  if (i < 0 || i >= Nx) {
+    const int xs = i < 0 ? 0 : 1;
+    const int xk = G.bck[xs * Ny + min(max(j, 0), Ny - 1)];
+    if (xk == NSWE_BC2_INFLOW) return -1;
+    i = (xk == NSWE_BC2_REFLECT) ? (i < 0 ? -1 - i : 2 * Nx - 1 - i) : (i < 0 ? 0 : Nx - 1);
+  }
+  if (j < 0 || j >= Ny) {
+    const int ys = j < 0 ? 2 : 3;
+    const int yk = G.bck[2 * Ny + (ys - 2) * Nx + i];
+    if (yk == NSWE_BC2_INFLOW) return -1;
+    j = (yk == NSWE_BC2_REFLECT) ? (j < 0 ? -1 - j : 2 * Ny - 1 - j) : (j < 0 ? 0 : Ny - 1);
+  }
+  return j * Nx + i;
+}
+
+// Whether the line (dir, a, r) of line_values2 reads interior cell cp.
+__device__ __forceinline__ bool line_reads(const Geo2 &G, int dir, int a, int r, int cp) {
+  bool hit = false;
+#pragma unroll
+  for (int s = 0; s < 7; ++s) hit |= (dir == 0 ? cell_src(G, a - 3 + s, r) : cell_src(G, r, a - 3 + s)) == cp;
+  return hit;
+}
 __device__ double block_sum2(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -359,13 +401,51 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
     }
     const double R0[3] = {R[c], R[n + c], R[2 * n + c]};
     const double reg = (k == kc) ? alpha * (fabs(R0[0]) + fabs(R0[1]) + fabs(R0[2])) : 0.0;
+    // The perturbed local residuals of Eq. 12, built line by line: a line
+    // that does not read cell cp has the same interface values for the three
+    // perturbations and is reconstructed once; a direction none of whose
+    // lines read cp contributes the same flux and source to all three.
+    const int cp = pj * G.Nx + pi;
+    const Pert none{-1, 0, 0.0};
+    double fd[2][3][3], sd[2][3];  // [dir][m][component], [dir][m]
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      const int a = dir == 0 ? i : j, r0 = dir == 0 ? j : i;
+      double ifv[3][4][2][3];
+      int reads = 0;
+#pragma unroll 1
+      for (int t = 0; t < 3; ++t) {
+        if (line_reads(G, dir, a, r0 - 1 + t, cp)) reads |= 1 << t;
+        else line_values2<FROZEN>(G, U, dir, a, r0 - 1 + t, none, ifv[t]);
+      }
+      if (!reads) {
+        double f[3], sv;
+        dir_part2(G, dir, c, ifv, f, sv);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          fd[dir][m][0] = f[0];
+          fd[dir][m][1] = f[1];
+          fd[dir][m][2] = f[2];
+          sd[dir][m] = sv;
+        }
+        continue;
+      }
+#pragma unroll 1
+      for (int m = 0; m < 3; ++m) {
+        const Pert p{cp, m, eps};
+#pragma unroll 1
+        for (int t = 0; t < 3; ++t)
+          if (reads & (1 << t)) line_values2<FROZEN>(G, U, dir, a, r0 - 1 + t, p, ifv[t]);
+        dir_part2(G, dir, c, ifv, fd[dir][m], sd[dir][m]);
+      }
+    }
+#pragma unroll
     for (int m = 0; m < 3; ++m) {
-      const Pert p{pj * G.Nx + pi, m, eps};
-      double Rp[3];
-      local_residual2<FROZEN>(G, U, i, j, p, Rp);
+      const double S[3] = {0.0, sd[0][m], sd[1][m]};
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
-        double v = (Rp[l] - R0[l]) * ieps;
+        const double Rp = fd[0][m][l] / G.dx + fd[1][m][l] / G.dy - S[l];
+        double v = (Rp - R0[l]) * ieps;
         if (l == m) v += reg;
         J[(size_t)(k * 9 + l * 3 + m) * n + c] = TJ(v);
       }
