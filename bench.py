@@ -771,6 +771,90 @@ def run_batch2d(args):
         "what": "host-timed: the batched call runs the solves concurrently on worker streams"}), flush=True)
 
 
+def run_serve2d(args):
+    """2D serving measurement (not the default line): the `--batch2d` seeded
+    channels of the batched 2D workload (`batch2d_instances`) arriving as a
+    seeded Poisson process at `--rate2d` per second into the server's 2D
+    worker pool (`--streams` workers, a 2D device budget of `--serve-mem-gb`
+    GB). Throughput counts the solves that reached res < tol over the span
+    from the first submission to the last completion; latency is completion
+    minus submission per request (host clock)."""
+    import numpy as np
+    import torch
+
+    from paper_2505_10857_gb300 import nswe
+
+    mixed = args.precision != "fp64"
+    B = args.batch2d
+    inps, prms_in = batch2d_instances(B, args.family2d)
+    prms = []
+    for q in prms_in:
+        c = nswe.params2d_from(q)
+        c.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
+        prms.append(c)
+    torch.cuda.init()
+    sv = nswe.Server(0, device_bytes=64 << 20, host_bytes=64 << 20, streams=args.streams, max_batch=4,
+                     device_bytes_2d=args.serve_mem_gb << 30)
+    results = {}
+
+    def drain(block_until):
+        while len(results) < block_until:
+            for t in sv.poll():
+                results[t] = sv.take(t)
+            if len(results) < block_until:
+                sv.wait(1, 1.0)
+
+    warm = min(B, max(1, args.warmup))  # first requests once, discarded
+    for k in range(warm):
+        sv.submit2d(inps[k], prms[k])
+    drain(warm)
+    results.clear()
+    clocks = ClockSampler(0)
+    clocks.start()
+    rng = np.random.default_rng(6999)
+    gaps = rng.exponential(1.0 / args.rate2d, size=B)
+    arrive = np.cumsum(gaps) - gaps[0]
+    tickets = []
+    t0 = time.perf_counter()
+    for k in range(B):
+        while True:
+            dt = t0 + arrive[k] - time.perf_counter()
+            if dt <= 0:
+                break
+            for t in sv.poll():
+                results[t] = sv.take(t)
+            time.sleep(min(dt, 0.005))
+        tickets.append(sv.submit2d(inps[k], prms[k]))
+    drain(B)
+    clk = clocks.stop()
+    st = sv.stats()
+    sv.close()
+    tim = [results[t][2] for t in tickets]
+    infos = [results[t][1] for t in tickets]
+    lat = sorted((x["t_done_ns"] - x["t_submit_ns"]) / 1e6 for x in tim)
+    queue = sorted((x["t_launch_ns"] - x["t_submit_ns"]) / 1e6 for x in tim)
+    span = (max(x["t_done_ns"] for x in tim) - min(x["t_submit_ns"] for x in tim)) / 1e9
+    ok = [k for k in range(B) if infos[k]["status"] == 0]
+
+    def pct(a, q):
+        return a[min(len(a) - 1, int(math.ceil(q / 100.0 * len(a))) - 1)]
+
+    print(json.dumps({
+        "metric": METRIC, "value": len(ok) / span, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"2D serving: {B} requests ({args.family2d}: wedges Froude 2-4, 5-15 deg, frozen "
+                               "linearisation; parabolic bumps, Eq. 12), 128x64 and 256x128, J9, nu 20, Poisson "
+                               f"arrivals at {args.rate2d}/s, " + ("mixed FP64/FP32" if mixed else "FP64"),
+                   "offered_rate": args.rate2d, "workers": args.streams, "device_budget_2d_gb": args.serve_mem_gb,
+                   "seeds": "wedges default_rng(7000 + k), bumps default_rng(5000 + k); arrivals 6999"},
+        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "queue_p50": pct(queue, 50),
+                       "queue_p99": pct(queue, 99), "what": "completion minus submission per request (host clock)"},
+        "converged": {"converged": len(ok), "of": B, "max_res": max((infos[k]["res"][0] for k in ok), default=None)},
+        "server": {"completed": st["completed"], "submitted": st["submitted"]},
+        "clocks": clk}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -783,8 +867,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of k_solve")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
-    ap.add_argument("--workload", default="channel1d", choices=["channel1d", "wedge2d", "serve1d", "batch2d"])
+    ap.add_argument("--workload", default="channel1d",
+                    choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d"])
     ap.add_argument("--batch2d", type=int, default=16, help="batch2d: 2D problems per batch")
+    ap.add_argument("--rate2d", type=float, default=1.0, help="serve2d: Poisson arrival rate (requests/s)")
     ap.add_argument("--family2d", choices=["mix", "wedge", "bump"], default="mix",
                     help="batch2d: wedge and bump channels, or one family")
     ap.add_argument("--requests", type=int, default=1024, help="serve1d: requests in the arrival schedule")
@@ -809,6 +895,13 @@ def main():
         from paper_2505_10857_gb300 import build
         build.build()
         run_batch2d(args)
+        return
+    if args.workload == "serve2d":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        if args.precision == "fp64" and "--precision" not in sys.argv:
+            args.precision = "mixed"  # the batched 2D serving workload is specified in mixed precision
+        run_serve2d(args)
         return
     if args.workload == "serve1d":
         from paper_2505_10857_gb300 import build

@@ -397,6 +397,15 @@ nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N,
  * A scheduler thread owned by the server issues all of its CUDA work; the
  * calls below are thread-safe. A solve's result does not depend on the
  * other requests it is launched with.
+ *
+ * 2D requests (nswe_server_submit_2d, when device_bytes_2d > 0) are served
+ * by `streams` worker threads, each with its own stream: a request is
+ * admitted, in submission order, once its footprint
+ * (nswe_server_footprint_2d) fits in device_bytes_2d besides the 2D solves
+ * running; its worker then builds the problem, runs the nested solve (the
+ * host sequences each 2D Newton step) and copies the result back, and the
+ * solves of different workers overlap on the GPU. Tickets, polling,
+ * waiting and results are shared with the 1D requests.
  * ------------------------------------------------------------------------ */
 typedef struct {
   size_t device_bytes; /* device arena for resident solves (>= 1 MiB)        */
@@ -405,6 +414,8 @@ typedef struct {
   int max_batch;       /* solves per launch, 1..65536                        */
   double batch_window_s; /* a launch that is not full waits until its oldest
                             request has waited this long (0: launch at once) */
+  size_t device_bytes_2d; /* device bytes for 2D solves in flight (0: the
+                             server refuses 2D requests)                  */
 } nswe_server_config;
 
 typedef struct { /* host steady-clock nanoseconds */
@@ -422,6 +433,11 @@ typedef struct nswe_server_s *nswe_server;
 /* Device bytes a request of N cells, `levels` levels and nested start level
  * nest_start (<0: coarsest) occupies in the arena; 0 for invalid sizes. */
 size_t nswe_server_footprint_1d(int N, int levels, int nest_start);
+
+/* Device bytes a 2D request of Nx x Ny cells and `levels` levels asks of the
+ * device allocator while it runs (problem, workspace, guess on the nested
+ * start level nest_start (<0: coarsest) and result); 0 for invalid sizes. */
+size_t nswe_server_footprint_2d(int Nx, int Ny, int levels, int nest_start);
 
 /* Allocates the arenas, streams and the scheduler thread on `device`.
  * EINVAL for a bad config, ENOMEM if an arena cannot be allocated. */
@@ -443,6 +459,19 @@ nswe_status nswe_server_submit_1d(nswe_server s, int N, int levels, double x0,
                                   const nswe_params *params,
                                   unsigned long long *ticket);
 
+/* Queues one 2D solve. Arguments as nswe_prob_create_2d (HOST arrays) plus
+ * U0 (HOST [3][n_s], n_s the cells of the nested start level) and params
+ * (copied; the Jacobian choice, NSWE_JAC_FROZEN included, and precision per
+ * request). Returns a ticket. EINVAL for invalid input or when the server
+ * takes no 2D requests, ENOMEM if the footprint exceeds device_bytes_2d (it
+ * could never be admitted), the server's error after a CUDA failure. */
+nswe_status nswe_server_submit_2d(nswe_server s, int Nx, int Ny, int levels,
+                                  double x0, double x1, double y0, double y1,
+                                  double g, const double *gauss_geom,
+                                  const int *bc_kind, const double *bc_state,
+                                  const double *U0, const nswe_params *params,
+                                  unsigned long long *ticket);
+
 /* Tickets completed since the last poll (up to max, in completion order). */
 nswe_status nswe_server_poll(nswe_server s, unsigned long long *tickets,
                              int max, int *count);
@@ -452,9 +481,9 @@ nswe_status nswe_server_poll(nswe_server s, unsigned long long *tickets,
 nswe_status nswe_server_wait(nswe_server s, int min_completed,
                              double timeout_s);
 
-/* Result of a completed ticket: U (HOST [2][N], may be NULL), the solve
- * record and the host timestamps; the ticket is released. EINVAL for a
- * ticket that is not (or no longer) complete. */
+/* Result of a completed ticket: U (HOST [2][N] in 1D, [3][Nx Ny] in 2D,
+ * may be NULL), the solve record and the host timestamps; the ticket is
+ * released. EINVAL for a ticket that is not (or no longer) complete. */
 nswe_status nswe_server_take(nswe_server s, unsigned long long ticket,
                              double *U, nswe_info *info,
                              nswe_server_times *times);

@@ -92,6 +92,34 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
 
 }  // namespace
 
+// Doubles of a 2D problem's device arena (geometry, boundary kinds, state,
+// Jacobian and multigrid workspace of every level, coarsest dense LU).
+size_t nswe::prob2d_arena_doubles(int Nx, int Ny, int levels) {
+  size_t doubles = 0, nk = 0;
+  for (int l = 0; l < levels; ++l) {
+    const size_t n = (size_t)(Nx >> l) * (Ny >> l);
+    doubles += round_up(8 * n) + 3 * round_up(3 * n) + round_up(189 * n) + round_up(9 * n);
+    nk += 2 * (size_t)((Nx >> l) + (Ny >> l));
+  }
+  const size_t N3 = 3 * (size_t)(Nx >> (levels - 1)) * (Ny >> (levels - 1));
+  return doubles + round_up(N3 * N3) + round_up(N3) + 2 * round_up(nk);
+}
+
+// All device bytes nswe_prob_create_2d requests for such a problem.
+size_t nswe::prob2d_device_bytes(int Nx, int Ny, int levels) {
+  const size_t N3 = 3 * (size_t)(Nx >> (levels - 1)) * (Ny >> (levels - 1));
+  return sizeof(double) * prob2d_arena_doubles(Nx, Ny, levels) + sizeof(ProbDev2) + sizeof(int) * (N3 + 64) +
+         sizeof(int) * 4 + sizeof(double) * 4 + sizeof(double) * 1024;
+}
+
+nswe_status nswe::check_params_2d(const nswe_params *p, int levels, int first_level) {
+  nswe_status st = check_params(p, nullptr, 0);
+  if (st != NSWE_OK) return st;
+  for (int l = 0; l <= first_level && l < levels; ++l)
+    if (!(p->eps[l] > 0.0) || !std::isfinite(p->eps[l])) return NSWE_EINVAL;
+  return NSWE_OK;
+}
+
 nswe_status nswe::check_params_1d(const nswe_params *p, int levels, int first_level) {
   nswe_status st = check_params(p, nullptr, 0);
   if (st != NSWE_OK) return st;
@@ -729,13 +757,8 @@ nswe_status nswe_prob_create_2d(nswe_ctx ctx, nswe_prob *out, int Nx, int Ny, in
   p->x0 = x0;
   p->x1 = x1;
   p->g = g;
-  size_t doubles = 0;
-  for (int l = 0; l < levels; ++l) {
-    size_t n = (size_t)(Nx >> l) * (Ny >> l);
-    doubles += round_up(8 * n) + 3 * round_up(3 * n) + round_up(189 * n) + round_up(9 * n);
-  }
+  const size_t doubles = prob2d_arena_doubles(Nx, Ny, levels);
   const size_t N3 = 3 * (size_t)NLx * NLy;
-  doubles += round_up(N3 * N3) + round_up(N3) + 2 * round_up(nk);
   bool ok = cudaMalloc(&p->arena, sizeof(double) * doubles) == cudaSuccess &&
             cudaMalloc(&p->dev2, sizeof(ProbDev2)) == cudaSuccess &&
             cudaMalloc(&p->piv, sizeof(int) * (N3 + 64)) == cudaSuccess &&

@@ -179,5 +179,10 @@ cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_par
                                int max_nb, int shape, cudaStream_t s);
 // Parameter checks shared by the entry points (eps of levels 0..first_level).
 nswe_status check_params_1d(const nswe_params *p, int levels, int first_level);
+// Parameter checks of a 2D solve (the frozen linearisation allowed).
+nswe_status check_params_2d(const nswe_params *p, int levels, int first_level);
+// 2D problem sizes (nswe_prob_create_2d): arena doubles and all device bytes.
+size_t prob2d_arena_doubles(int Nx, int Ny, int levels);
+size_t prob2d_device_bytes(int Nx, int Ny, int levels);
 
 }  // namespace nswe

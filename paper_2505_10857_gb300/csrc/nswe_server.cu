@@ -11,8 +11,15 @@
 // for them. Results come back through pinned host memory, with host
 // timestamps of submission, admission, launch and completion.
 //
-// One scheduler thread per server issues every CUDA call of the server; the
-// public calls only exchange requests and results with it under a mutex.
+// One scheduler thread per server issues every CUDA call of the server's 1D
+// work; the public calls only exchange requests and results with it under a
+// mutex.
+//
+// 2D requests go to a pool of worker threads instead, each with its own
+// stream and context: a 2D Newton step is sequenced from the host, so one
+// solve keeps one host thread. A worker takes the oldest 2D request once its
+// footprint fits in the 2D budget beside the solves in flight, builds the
+// problem, solves it and files the result with the same tickets.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -144,7 +151,14 @@ Layout layout_1d(int N, int levels, int s0) {
 
 struct Request {
   unsigned long long ticket = 0;
+  int dim = 1;
   int N = 0, levels = 0, s0 = 0;
+  // 2D: grid, domain, boundary kinds and states, footprint
+  int Nx = 0, Ny = 0;
+  double y0 = 0, y1 = 0;
+  std::vector<int> kinds;
+  double bcs[12] = {};
+  size_t foot2d = 0;
   double x0 = 0, x1 = 0, g = 0;
   nswe_bc1d left{}, right{};
   nswe_params prm{};
@@ -193,7 +207,14 @@ struct nswe_server_s {
 
   std::vector<Request *> running;  // launched, not yet finished
 
+  // 2D requests
+  std::deque<Request *> waiting2d;
+  size_t used2d = 0;  // footprints of the 2D solves in flight
+  std::condition_variable cv2;
+  std::vector<std::thread> workers2d;
+
   void run();
+  void run2d();
   bool admit_and_launch(int s);
   bool finish_requests();
   bool release_stream(int s);
@@ -444,6 +465,90 @@ void nswe_server_s::run() {
 
 extern "C" {
 
+namespace {
+
+// Builds request r's 2D problem on ctx (stream s), runs its nested solve and
+// copies the result into r->U; the problem and the buffers are freed before
+// returning. Returns the solve's status.
+nswe_status solve2d_request(nswe_ctx ctx, cudaStream_t s, Request *r) {
+  nswe_prob p = nullptr;
+  nswe_status st = nswe_prob_create_2d(ctx, &p, r->Nx, r->Ny, r->levels, r->x0, r->x1, r->y0, r->y1, r->g,
+                                       r->gq.data(), r->kinds.data(), r->bcs);
+  if (st != NSWE_OK) return st;
+  const size_t n = (size_t)r->Nx * r->Ny;
+  double *dU0 = nullptr, *dU = nullptr;
+  if (cudaMalloc(&dU0, sizeof(double) * r->u0.size()) != cudaSuccess ||
+      cudaMalloc(&dU, sizeof(double) * 3 * n) != cudaSuccess)
+    st = NSWE_ENOMEM;
+  if (st == NSWE_OK &&
+      cudaMemcpyAsync(dU0, r->u0.data(), sizeof(double) * r->u0.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    st = NSWE_ECUDA;
+  if (st == NSWE_OK) st = nswe_newton_solve(ctx, p, dU0, dU, &r->prm, &r->info);
+  if (st != NSWE_EINVAL && st != NSWE_ENOMEM && st != NSWE_ECUDA) {  // a solve outcome: the state is valid
+    r->U.resize(3 * n);
+    if (cudaMemcpyAsync(r->U.data(), dU, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = NSWE_ECUDA;
+  }
+  cudaFree(dU0);
+  cudaFree(dU);
+  nswe_prob_destroy(p);
+  return st;
+}
+
+}  // namespace
+
+// One 2D worker (see the top of the file).
+void nswe_server_s::run2d() {
+  cudaStream_t s = nullptr;
+  nswe_ctx ctx = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      nswe_ctx_create(&ctx, device, s) != NSWE_OK) {
+    int ok = NSWE_OK;
+    error.compare_exchange_strong(ok, NSWE_ECUDA);
+    cv.notify_all();
+    if (s) cudaStreamDestroy(s);
+    return;
+  }
+  for (;;) {
+    Request *r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv2.wait(lk, [&] {
+        return stop.load() || error.load() != NSWE_OK ||
+               (!waiting2d.empty() && used2d + waiting2d.front()->foot2d <= cfg.device_bytes_2d);
+      });
+      if (stop.load() || error.load() != NSWE_OK) break;
+      r = waiting2d.front();
+      waiting2d.pop_front();
+      used2d += r->foot2d;
+      stats.running += 1;
+      r->times.t_admit_ns = now_ns();
+    }
+    cv2.notify_all();  // the next request may fit as well
+    r->times.t_launch_ns = now_ns();
+    const nswe_status st = solve2d_request(ctx, s, r);
+    r->status = st;
+    r->times.t_done_ns = now_ns();
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      used2d -= r->foot2d;
+      stats.running -= 1;
+      stats.completed += 1;
+      if (st == NSWE_ECUDA || st == NSWE_ENOMEM) {
+        int ok = NSWE_OK;
+        error.compare_exchange_strong(ok, (int)st);
+      }
+      done[r->ticket] = r;
+      completed.push_back(r->ticket);
+    }
+    cv.notify_all();
+    cv2.notify_all();
+  }
+  nswe_ctx_destroy(ctx);
+  cudaStreamDestroy(s);
+}
+
 nswe_status nswe_arena_create(nswe_arena *out, size_t bytes, size_t align) {
   if (!out || bytes == 0 || align == 0 || (align & (align - 1)) != 0) return NSWE_EINVAL;
   nswe_arena_s *a = new (std::nothrow) nswe_arena_s;
@@ -529,8 +634,83 @@ nswe_status nswe_server_create(nswe_server *out, int device, const nswe_server_c
     return st;
   }
   sv->worker = std::thread([sv] { sv->run(); });
+  if (cfg->device_bytes_2d > 0)
+    for (int w = 0; w < cfg->streams; ++w) sv->workers2d.emplace_back([sv] { sv->run2d(); });
   cudaSetDevice(prev);
   *out = sv;
+  return NSWE_OK;
+}
+
+size_t nswe_server_footprint_2d(int Nx, int Ny, int levels, int nest_start) {
+  if (levels < 1 || levels > NSWE_MAX_LEVELS || Nx < 4 || Ny < 4 || (long)Nx * Ny > (1L << 26)) return 0;
+  if (Nx % (1 << (levels - 1)) || Ny % (1 << (levels - 1))) return 0;
+  const int NLx = Nx >> (levels - 1), NLy = Ny >> (levels - 1);
+  if (NLx < 4 || NLy < 4 || NLx * NLy > 512) return 0;
+  const int s0 = (nest_start >= 0 && nest_start < levels) ? nest_start : levels - 1;
+  const size_t n = (size_t)Nx * Ny, ns = (size_t)(Nx >> s0) * (Ny >> s0);
+  return prob2d_device_bytes(Nx, Ny, levels) + sizeof(double) * 3 * (n + ns);
+}
+
+nswe_status nswe_server_submit_2d(nswe_server sv, int Nx, int Ny, int levels, double x0, double x1, double y0,
+                                  double y1, double g, const double *gauss_geom, const int *bc_kind,
+                                  const double *bc_state, const double *U0, const nswe_params *params,
+                                  unsigned long long *ticket) {
+  if (!sv || !gauss_geom || !bc_kind || !bc_state || !U0 || !params || !ticket) return NSWE_EINVAL;
+  if (sv->cfg.device_bytes_2d == 0) return NSWE_EINVAL;
+  if (sv->error.load() != NSWE_OK) return (nswe_status)sv->error.load();
+  const size_t foot = nswe_server_footprint_2d(Nx, Ny, levels, params->nest_start);
+  if (foot == 0) return NSWE_EINVAL;
+  if (!(x1 > x0) || !(y1 > y0) || !(g > 0.0) || !std::isfinite(x0) || !std::isfinite(x1) || !std::isfinite(y0) ||
+      !std::isfinite(y1) || !std::isfinite(g))
+    return NSWE_EINVAL;
+  const int s0 = (params->nest_start >= 0 && params->nest_start < levels) ? params->nest_start : levels - 1;
+  nswe_status st = check_params_2d(params, levels, s0);
+  if (st != NSWE_OK) return st;
+  if (foot > sv->cfg.device_bytes_2d) return NSWE_ENOMEM;  // can never be admitted
+  size_t nk = 0, ng = 0;
+  for (int l = 0; l < levels; ++l) {
+    nk += 2 * (size_t)((Nx >> l) + (Ny >> l));
+    ng += 8 * (size_t)(Nx >> l) * (Ny >> l);
+  }
+  for (size_t i = 0; i < nk; ++i)
+    if (bc_kind[i] < NSWE_BC2_REFLECT || bc_kind[i] > NSWE_BC2_DEPTH) return NSWE_EINVAL;
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(bc_state[i])) return NSWE_EINVAL;
+  Request *r = new (std::nothrow) Request;
+  if (!r) return NSWE_ENOMEM;
+  r->dim = 2;
+  r->Nx = Nx;
+  r->Ny = Ny;
+  r->levels = levels;
+  r->s0 = s0;
+  r->x0 = x0;
+  r->x1 = x1;
+  r->y0 = y0;
+  r->y1 = y1;
+  r->g = g;
+  r->prm = *params;
+  r->foot2d = foot;
+  r->gq.assign(gauss_geom, gauss_geom + ng);
+  r->kinds.assign(bc_kind, bc_kind + nk);
+  std::memcpy(r->bcs, bc_state, sizeof(r->bcs));
+  r->u0.assign(U0, U0 + 3 * (size_t)(Nx >> s0) * (Ny >> s0));
+  for (double v : r->gq)
+    if (!std::isfinite(v)) st = NSWE_EINVAL;
+  for (double v : r->u0)
+    if (!std::isfinite(v)) st = NSWE_EINVAL;
+  if (st != NSWE_OK) {
+    delete r;
+    return st;
+  }
+  r->times.t_submit_ns = now_ns();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->ticket = sv->next_ticket++;
+    sv->waiting2d.push_back(r);
+    sv->stats.submitted += 1;
+  }
+  sv->cv2.notify_all();
+  *ticket = r->ticket;
   return NSWE_OK;
 }
 
@@ -636,15 +816,21 @@ nswe_status nswe_server_query(nswe_server sv, nswe_server_stats *out) {
   if (!sv || !out) return NSWE_EINVAL;
   std::lock_guard<std::mutex> lk(sv->mu);
   *out = sv->stats;
-  out->waiting = (int)(sv->waiting.size() + sv->submitted.size());
+  out->waiting = (int)(sv->waiting.size() + sv->submitted.size() + sv->waiting2d.size());
   return (nswe_status)sv->error.load();
 }
 
 nswe_status nswe_server_destroy(nswe_server sv) {
   if (!sv) return NSWE_EINVAL;
-  sv->stop = true;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);  // a worker between its test and its wait sees stop
+    sv->stop = true;
+  }
   sv->cv.notify_all();
+  sv->cv2.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
+  for (auto &t : sv->workers2d)  // each finishes the solve it holds
+    if (t.joinable()) t.join();
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(sv->device);
@@ -659,6 +845,7 @@ nswe_status nswe_server_destroy(nswe_server sv) {
   if (sv->host_base) cudaFreeHost(sv->host_base);
   for (Request *r : sv->submitted) delete r;
   for (Request *r : sv->waiting) delete r;
+  for (Request *r : sv->waiting2d) delete r;
   for (Request *r : sv->running) delete r;
   for (auto &kv : sv->done) delete kv.second;
   delete sv;

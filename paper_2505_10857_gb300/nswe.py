@@ -58,7 +58,7 @@ class NsweError(RuntimeError):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("host_bytes", ctypes.c_size_t), ("streams", ctypes.c_int),
-                ("max_batch", ctypes.c_int), ("batch_window_s", ctypes.c_double)]
+                ("max_batch", ctypes.c_int), ("batch_window_s", ctypes.c_double), ("device_bytes_2d", ctypes.c_size_t)]
 
 
 class ServerTimes(ctypes.Structure):
@@ -123,6 +123,9 @@ EXPORTS = {
     "nswe_autotune_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                        ctypes.POINTER(Params), _i, ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "nswe_server_footprint_1d": (ctypes.c_size_t, [_i, _i, _i]),
+    "nswe_server_footprint_2d": (ctypes.c_size_t, [_i, _i, _i, _i]),
+    "nswe_server_submit_2d": (_i, [_vp, _i, _i, _i, _d, _d, _d, _d, _d, _dp, ctypes.POINTER(ctypes.c_int), _dp, _dp,
+                                   ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_ulonglong)]),
     "nswe_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(ServerConfig)]),
     "nswe_server_submit_1d": (_i, [_vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D), ctypes.POINTER(BC1D),
                                    _dp, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -486,12 +489,14 @@ def info_from_bytes(raw: bytes, levels=MAX_LEVELS) -> dict:
 # ---------------------------------------------------------------- continuous-batching server (1D)
 
 class Server:
-    """nswe_server: requests are Problem1DInputs-like objects (N, levels, x0,
-    x1, g, sig_face, gq_all(), bcl, bcr, U0_start) with their Params."""
+    """nswe_server: 1D requests are Problem1DInputs-like objects (N, levels,
+    x0, x1, g, sig_face, gq_all(), bcl, bcr, U0_start), 2D requests
+    Problem2DInputs-like ones (submit2d), each with its Params."""
 
     def __init__(self, device=0, device_bytes=1 << 30, host_bytes=256 << 20, streams=4, max_batch=1024,
-                 batch_window_s=0.0):
-        cfg = ServerConfig(int(device_bytes), int(host_bytes), int(streams), int(max_batch), float(batch_window_s))
+                 batch_window_s=0.0, device_bytes_2d=0):
+        cfg = ServerConfig(int(device_bytes), int(host_bytes), int(streams), int(max_batch), float(batch_window_s),
+                           int(device_bytes_2d))
         self.h = _vp()
         _check("nswe_server_create", lib().nswe_server_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)))
         self.N = {}
@@ -513,6 +518,23 @@ class Server:
         self.N[t.value] = int(inp.N)
         return t.value
 
+    @staticmethod
+    def footprint2d(Nx, Ny, levels, nest_start=-1) -> int:
+        return int(lib().nswe_server_footprint_2d(int(Nx), int(Ny), int(levels), int(nest_start)))
+
+    def submit2d(self, inp, prm: Params) -> int:
+        gq = np.ascontiguousarray(inp.gq_all(), dtype=np.float64)
+        kinds = np.ascontiguousarray(inp.bc_kind_all(), dtype=np.int32)
+        st = np.ascontiguousarray(inp.bc_state, dtype=np.float64).reshape(-1)
+        u0 = np.ascontiguousarray(inp.U0_start, dtype=np.float64)
+        t = ctypes.c_ulonglong()
+        _check("nswe_server_submit_2d", lib().nswe_server_submit_2d(
+            self.h, int(inp.Nx), int(inp.Ny), int(inp.levels), float(inp.x0), float(inp.x1), float(inp.y0),
+            float(inp.y1), float(inp.g), gq.ctypes.data, kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            st.ctypes.data, u0.ctypes.data, ctypes.byref(prm), ctypes.byref(t)))
+        self.N[t.value] = (3, int(inp.Nx) * int(inp.Ny))
+        return t.value
+
     def poll(self, max_n=4096):
         buf = (ctypes.c_ulonglong * max_n)()
         n = _i()
@@ -527,7 +549,8 @@ class Server:
         return True
 
     def take(self, ticket):
-        U = np.empty((2, self.N.pop(ticket)), dtype=np.float64)
+        shape = self.N.pop(ticket)
+        U = np.empty(shape if isinstance(shape, tuple) else (2, shape), dtype=np.float64)
         info, times = Info(), ServerTimes()
         _check("nswe_server_take", lib().nswe_server_take(self.h, ctypes.c_ulonglong(ticket), U.ctypes.data,
                                                           ctypes.byref(info), ctypes.byref(times)))

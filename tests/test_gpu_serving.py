@@ -117,3 +117,87 @@ def test_requests_complete_individually(nswe):
     assert res[ts][2]["t_launch_ns"] == res[tb][2]["t_launch_ns"]
     assert res[ts][2]["t_done_ns"] < res[tb][2]["t_done_ns"]
     assert res[ts][1]["status"] == 0 and res[tb][1]["status"] == 0
+
+
+def alone2d(nswe, ctx, inp, prm):
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    U = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
+    info = nswe.nswe_newton_solve(ctx, prob, torch.from_numpy(inp.U0_start).cuda(), U, prm)
+    torch.cuda.synchronize()
+    return U.cpu().numpy(), info
+
+
+def requests2d(nswe):
+    """Seeded wedges (frozen linearisation, omega 0.1, nested from 16 x 8) and
+    bump channels (Eq. 12, nested from 8 x 4), two sizes, both precisions."""
+    out = []
+    for k, (Nx, Ny, lev) in enumerate([(32, 16, 3), (64, 32, 4), (32, 16, 3), (64, 32, 4)]):
+        if k % 2 == 0:
+            inp = I.wedge_serving_2d(k, Nx, Ny, lev)
+            q = I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=1e-10, n_max=400, nest_start=lev - 2, omega=0.1,
+                           frozen=True)
+        else:
+            inp = I.bump_channel_2d(k, Nx, Ny, lev)
+            q = I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=1e-10, n_max=400)
+        p = nswe.params2d_from(q)
+        p.precision = k // 2  # FP64 for the first pair, mixed for the second
+        out.append((inp, p))
+    return out
+
+
+def test_2d_requests_equal_alone_beside_1d(nswe):
+    """2D requests served by the worker pool, interleaved with 1D requests on
+    the same server: every result equals, bit for bit, its solve alone."""
+    ctx = nswe.Context(0)
+    reqs = requests2d(nswe)
+    ref2 = [alone2d(nswe, ctx, inp, p) for inp, p in reqs]
+    one = [I.serving_instance(k) for k in (11, 9)]
+    p1 = [params(nswe, p, 0) for p in one]
+    ref1 = [alone(nswe, ctx, p, q) for p, q in zip(one, p1)]
+    sv = nswe.Server(0, device_bytes=64 << 20, host_bytes=16 << 20, streams=3, max_batch=4, device_bytes_2d=1 << 30)
+    t2, t1 = [], []
+    for k, (inp, p) in enumerate(reqs):
+        t2.append(sv.submit2d(inp, p))
+        if k < len(one):
+            t1.append(sv.submit(one[k], p1[k]))
+    res = collect(sv, len(reqs) + len(one))
+    st = sv.stats()
+    sv.close()
+    assert st["completed"] == len(reqs) + len(one)
+    for t, (Uref, iref), (inp, _) in zip(t2, ref2, reqs):
+        U, info, times = res[t]
+        assert info["status"] == 0 == iref["status"], (info, iref)
+        assert np.array_equal(U, Uref)
+        assert info["iters"][:inp.levels] == iref["iters"][:inp.levels]
+        assert times["t_submit_ns"] <= times["t_admit_ns"] <= times["t_launch_ns"] <= times["t_done_ns"]
+    for t, (Uref, iref) in zip(t1, ref1):
+        assert res[t][1]["status"] == 0 and np.array_equal(res[t][0], Uref)
+
+
+def test_2d_admission_by_footprint(nswe):
+    """With a 2D budget of the largest footprint, the footprints of the 2D
+    solves in flight never add up beyond it; all complete."""
+    reqs = requests2d(nswe)
+    foot = [nswe.Server.footprint2d(inp.Nx, inp.Ny, inp.levels, p.nest_start) for inp, p in reqs]
+    budget = max(foot)
+    sv = nswe.Server(0, device_bytes=8 << 20, host_bytes=8 << 20, streams=4, max_batch=4, device_bytes_2d=budget)
+    tickets = [sv.submit2d(inp, p) for inp, p in reqs]
+    res = collect(sv, len(reqs))
+    sv.close()
+    assert all(res[t][1]["status"] == 0 for t in tickets)
+    spans = [(res[t][2]["t_admit_ns"], res[t][2]["t_done_ns"], f) for t, f in zip(tickets, foot)]
+    for a, _, _ in spans:  # footprints in flight at every admission
+        assert sum(f for s, e, f in spans if s <= a < e) <= budget
+
+
+def test_2d_requests_refused(nswe):
+    inp, p = requests2d(nswe)[1]
+    sv = nswe.Server(0, device_bytes=8 << 20, host_bytes=8 << 20, streams=1, max_batch=4)  # no 2D budget
+    with pytest.raises(nswe.NsweError):
+        sv.submit2d(inp, p)
+    sv.close()
+    sv = nswe.Server(0, device_bytes=8 << 20, host_bytes=8 << 20, streams=1, max_batch=4, device_bytes_2d=1 << 20)
+    assert nswe.Server.footprint2d(inp.Nx, inp.Ny, inp.levels, p.nest_start) > 1 << 20
+    with pytest.raises(nswe.NsweError):  # can never fit
+        sv.submit2d(inp, p)
+    sv.close()

@@ -91,3 +91,15 @@ def test_footprint():
     # workspace (x2 over the levels), the Jacobian workspace (34 doubles),
     # geometry and the result
     assert 800 * 4096 < f(4096, 8, 4) < 1100 * 4096
+
+
+def test_footprint_2d():
+    f = nswe.Server.footprint2d
+    assert f(512, 256, 7, -1) > f(256, 128, 6, -1) > f(64, 32, 4, -1) > 0
+    assert f(512, 256, 7, 5) > f(512, 256, 7, -1)  # a finer start level holds a larger guess
+    # invalid: too small, not divisible, coarsest grid below 4 x 4 or above 512 cells
+    assert f(2, 2, 1, -1) == 0 and f(100, 64, 4, -1) == 0 and f(64, 32, 5, -1) == 0 and f(512, 256, 2, -1) == 0
+    # about 2.3 KB per finest cell: 215 doubles per cell and level (state, residual, update, Gauss-point
+    # geometry, 21 Jacobian blocks and the diagonal inverses), x 4/3 over the levels, and the result
+    n = 512 * 256
+    assert 2200 * n < f(512, 256, 7, -1) < 2400 * n
