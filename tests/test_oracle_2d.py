@@ -536,3 +536,20 @@ def test_wedge_reaches_the_oblique_jump_with_the_frozen_linearisation(orc):
     slope, icpt = np.polyfit(pts[:, 1], pts[:, 0], 1)
     assert abs(math.degrees(math.atan(slope)) - math.degrees(beta - th)) < 1.0
     assert abs(-icpt / slope - 1.0 / math.cos(th)) < dx  # the jump starts where the wall does
+
+
+@pytest.mark.parametrize("k", [0, 2, 4])
+def test_seeded_wedges_reach_their_oblique_jump(orc, k):
+    """The seeded wedges of the batched 2D workload (Froude ~U[2, 4],
+    deflection ~U[5, 15] degrees, [0, 40] x [0, 30]) converge under the frozen
+    linearisation with the paper's omega = 0.1, and the depth along the wall
+    behind the jump is the oblique-jump value h2 / h1 for that seed's Froude
+    number and deflection."""
+    inp = I.wedge_serving_2d(k, 32, 16, 3)
+    U, info = orc.solve_problem2d(inp, I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400, nest_start=1,
+                                                  omega=0.1, frozen=True))
+    assert info["status"] == 0 and info["res"][0] < 1e-10, info
+    _, ratio = _oblique_jump(inp.meta["froude"], math.radians(inp.meta["theta_deg"]))
+    h = U[0].reshape(16, 32)
+    assert abs(h[0, -3:].mean() / ratio - 1.0) < 2e-3, (h[0, -3:], ratio)
+    assert np.abs(h[-4:, :3] - 1.0).max() < 1e-3  # the inflow corner is undisturbed
