@@ -421,9 +421,13 @@ def run_gpu(args, rank, world, local_rank):
             cores = host_cores()
             n = B  # the whole step: about 10-15 s of CPU work on 16 cores
             wall, refs = oracle_sample(first, n, nb, cores)
+            n1 = 4  # per-solve latency on one core: a few solves one after another in one process
+            wall1, _ = oracle_sample(first, n1, nb, 1)
             cpu = {"value": n / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"all {n} instances of the step, one solve per process (spawn pool), "
-                             f"{wall:.1f} s wall"}
+                             f"{wall:.1f} s wall",
+                   "latency_1core_ms": 1000.0 * wall1 / n1,
+                   "latency_1core_sample": f"the step's first {n1} instances solved one after another on one core"}
             errs = [float(np.abs(Us[k].cpu().numpy() - refs[k]).max() / np.abs(refs[k]).max()) for k in range(n)]
             parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "bound": MIXED_BOUND if mixed else 1e-10}
         out = {
