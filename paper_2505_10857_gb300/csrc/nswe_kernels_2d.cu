@@ -75,6 +75,12 @@ __device__ __forceinline__ Geo2 make_geo2(const ProbDev2 &P, int l) {
 #define NSWE_SOR_UNROLL 1
 #endif
 constexpr long kSorSplitF64 = NSWE_SOR_SPLIT_F64, kSorSplitF32 = NSWE_SOR_SPLIT_F32;
+// Largest number of (cell, block, component) items for which the Jacobian
+// takes one component per item.
+#ifndef NSWE_JAC_SPLIT_ITEMS
+#define NSWE_JAC_SPLIT_ITEMS 65536
+#endif
+constexpr long kJacSplitItems = NSWE_JAC_SPLIT_ITEMS;
 
 // Perturbation of one interior cell in one component (cp < 0: none).
 struct Pert {
@@ -386,17 +392,23 @@ __global__ void k2_finish(const double *partials, int nparts, int n, double *res
 
 // One item = (cell, stencil block k): three perturbed local residuals
 // (FROZEN: the frozen linearisation).
+// msplit: one item per (cell, block, component m) instead of per (cell,
+// block), for small grids where the kernel is bound by each thread's chain.
 template <typename TJ, bool FROZEN>
 __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int level, int st, const double *U,
-                                                        double eps, double alpha, const double *R, TJ *J) {
+                                                        double eps, double alpha, const double *R, TJ *J,
+                                                        int msplit) {
   const Geo2 G = make_geo2(*P, level);
   const int n = G.Nx * G.Ny, K = st_size(st), kc = st_center(st);
   const double ieps = 1.0 / eps;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n * K; it += gridDim.x * blockDim.x) {
-    const int c = it % n, k = it / n, i = c % G.Nx, j = c / G.Nx;
+  const int items = n * K * (msplit ? 3 : 1);
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+    const int c = it % n, kq = it / n, k = msplit ? kq % K : kq, i = c % G.Nx, j = c / G.Nx;
+    const int m0 = msplit ? kq / K : 0, m1 = msplit ? m0 + 1 : 3;
     const int pi = i + st_off(st, k, 0), pj = j + st_off(st, k, 1);
     if (pi < 0 || pi >= G.Nx || pj < 0 || pj >= G.Ny) {
-      for (int e = 0; e < 9; ++e) J[(size_t)(k * 9 + e) * n + c] = TJ(0.0);
+      for (int l = 0; l < 3; ++l)
+        for (int m = m0; m < m1; ++m) J[(size_t)(k * 9 + l * 3 + m) * n + c] = TJ(0.0);
       continue;
     }
     const double R0[3] = {R[c], R[n + c], R[2 * n + c]};
@@ -422,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
         double f[3], sv;
         dir_part2(G, dir, c, ifv, f, sv);
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
+        for (int m = 0; m < 3; ++m) {  // the same for every m (m0..m1-1 are read)
           fd[dir][m][0] = f[0];
           fd[dir][m][1] = f[1];
           fd[dir][m][2] = f[2];
@@ -431,7 +443,7 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
         continue;
       }
 #pragma unroll 1
-      for (int m = 0; m < 3; ++m) {
+      for (int m = m0; m < m1; ++m) {
         const Pert p{cp, m, eps};
 #pragma unroll 1
         for (int t = 0; t < 3; ++t)
@@ -439,8 +451,7 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
         dir_part2(G, dir, c, ifv, fd[dir][m], sd[dir][m]);
       }
     }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
+    for (int m = m0; m < m1; ++m) {
       const double S[3] = {0.0, sd[0][m], sd[1][m]};
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
@@ -971,11 +982,13 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
 template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
                              const double *R, TJ *J, bool frozen, cudaStream_t s) {
-  const int grid = grid2((long)n * (st == ST_J21 ? 21 : 9));
+  const long items = (long)n * (st == ST_J21 ? 21 : 9);
+  const int msplit = 3 * items <= kJacSplitItems ? 1 : 0;
+  const int grid = grid2(items * (msplit ? 3 : 1));
   if (frozen)
-    k2_jacobian<TJ, true><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
+    k2_jacobian<TJ, true><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, msplit);
   else
-    k2_jacobian<TJ, false><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J);
+    k2_jacobian<TJ, false><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, msplit);
   return cudaGetLastError();
 }
 
