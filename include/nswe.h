@@ -168,6 +168,16 @@ nswe_status nswe_params_default(nswe_params *p, int N, int levels);
  * caller, e.g. PyTorch's). Owns nothing the caller passes in. */
 nswe_status nswe_ctx_create(nswe_ctx *out, int device, void *stream);
 nswe_status nswe_ctx_set_stream(nswe_ctx ctx, void *stream);
+
+/* Storage of the 2D Jacobian in nested solves (a layout choice, not in the
+ * paper; results are the same bits either way): Newton levels of at least
+ * min_cells cells that are solved by V-cycles keep J9 and its diagonal
+ * inverses colour-major, each colour (i + j) mod 3 of the smoother one
+ * contiguous plane, so that a colour pass reads only its third of J.
+ * min_cells < 0: never. Default 131072 (512 x 256). The standalone calls
+ * (nswe_jacobian_*, nswe_mg_vcycle*) always use the cell-contiguous layout
+ * they document. */
+nswe_status nswe_ctx_set_colour_major_2d(nswe_ctx ctx, int min_cells);
 nswe_status nswe_ctx_destroy(nswe_ctx ctx);
 
 /* One-dimensional problem (Eq. 3-4) on [x0, x1] with N cells and `levels`

@@ -23,6 +23,7 @@ struct nswe_ctx_s {
   nswe_params *prms;     // device per-task parameters (nswe_newton_solve_batch_each)
   int cap;               // capacity of tasks / infos / prms
   int solve_shape[2];    // launch shape of the 1D solve kernel per precision
+  int cm2d_min_cells = 131072;  // 2D Newton levels of at least this many cells store J9 colour-major
 };
 
 struct nswe_prob_s {
@@ -98,7 +99,8 @@ size_t nswe::prob2d_arena_doubles(int Nx, int Ny, int levels) {
   size_t doubles = 0, nk = 0;
   for (int l = 0; l < levels; ++l) {
     const size_t n = (size_t)(Nx >> l) * (Ny >> l);
-    doubles += round_up(8 * n) + 3 * round_up(3 * n) + round_up(189 * n) + round_up(9 * n);
+    // Dinv: room for the colour-major stride (blk_stride <= n + 2 Ny)
+    doubles += round_up(8 * n) + 3 * round_up(3 * n) + round_up(189 * n) + round_up(9 * n + 27 * (size_t)(Ny >> l));
     nk += 2 * (size_t)((Nx >> l) + (Ny >> l));
   }
   const size_t N3 = 3 * (size_t)(Nx >> (levels - 1)) * (Ny >> (levels - 1));
@@ -199,12 +201,13 @@ template <typename T>
 struct Lev2 {
   int Nx, Ny;
   T *J, *Dinv, *R, *dU;
+  int cm;  // storage of J and Dinv (blk_pos)
 };
 
 template <typename T>
 Lev2<T> lev2_view(const Level2Dev &L) {
   return Lev2<T>{L.Nx, L.Ny, reinterpret_cast<T *>(L.J), reinterpret_cast<T *>(L.Dinv), reinterpret_cast<T *>(L.R),
-                 reinterpret_cast<T *>(L.dU)};
+                 reinterpret_cast<T *>(L.dU), 0};
 }
 
 template <typename T>
@@ -218,7 +221,7 @@ cudaError_t smooth2(const Lev2<T> &Lv, int st, int steps, double omega, int Kc, 
       for (int d = 0; d < 4; ++d)
         for (int q = 0; q < Kc; ++q) {
           const int mode = (d % 2) + 1, col = d < 2 ? q : Kc - 1 - q;
-          if ((e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, mode, Kc, col, 1, s)))
+          if ((e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, mode, Kc, col, 1, Lv.cm, s)))
             return e;
         }
     return e;
@@ -233,12 +236,12 @@ cudaError_t smooth2(const Lev2<T> &Lv, int st, int steps, double omega, int Kc, 
         continue;
       }
       if (prev >= 0 &&
-          (e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s)))
+          (e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, Lv.cm, s)))
         return e;
       prev = col;
       reps = 1;
     }
-  if (prev >= 0) e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, s);
+  if (prev >= 0) e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, Lv.cm, s);
   return e;
 }
 
@@ -251,8 +254,10 @@ struct MG2 {
   Lev2<T> lv[NSWE_MAX_LEVELS];
 };
 
+// cm0: the storage of level l0's J and Dinv (blk_pos); the coarser levels
+// are cell-contiguous.
 template <typename T>
-MG2<T> mg2_bind(const nswe_prob_s *p, int l0, int st0, const T *J, const T *R, T *dU) {
+MG2<T> mg2_bind(const nswe_prob_s *p, int l0, int st0, const T *J, const T *R, T *dU, int cm0) {
   MG2<T> m;
   m.l0 = l0;
   m.L = p->levels - 1;
@@ -263,6 +268,7 @@ MG2<T> mg2_bind(const nswe_prob_s *p, int l0, int st0, const T *J, const T *R, T
   m.lv[l0].J = const_cast<T *>(J);
   m.lv[l0].R = const_cast<T *>(R);
   m.lv[l0].dU = dU;
+  m.lv[l0].cm = cm0;
   return m;
 }
 
@@ -270,10 +276,11 @@ template <typename T>
 cudaError_t mg2_setup(nswe_prob_s *p, const MG2<T> &m, cudaStream_t s) {
   cudaError_t e;
   for (int l = m.l0 + 1; l <= m.L; ++l)
-    if ((e = launch2_coarse_op<T>(m.lv[l - 1].Nx, m.lv[l - 1].Ny, m.st[l - 1], m.lv[l - 1].J, m.lv[l].J, s)))
+    if ((e = launch2_coarse_op<T>(m.lv[l - 1].Nx, m.lv[l - 1].Ny, m.st[l - 1], m.lv[l - 1].J, m.lv[l].J,
+                                  m.lv[l - 1].cm, s)))
       return e;
   for (int l = m.l0; l < m.L; ++l)
-    if ((e = launch2_dinv<T>(m.lv[l].Nx * m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].Dinv, s))) return e;
+    if ((e = launch2_dinv<T>(m.lv[l].Nx, m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].Dinv, m.lv[l].cm, s))) return e;
   return launch2_dense_factor<T>(m.lv[m.L].Nx, m.lv[m.L].Ny, m.st[m.L], m.lv[m.L].J,
                                  reinterpret_cast<T *>(p->dense), p->piv, p->flag, s);
 }
@@ -292,7 +299,7 @@ cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2<T> &m, const nswe_params &prm, 
     }
     if ((e = smooth2<T>(m.lv[l], m.st[l], prm.nu1, prm.omega, prm.colours2d, s))) return e;
     if ((e = launch2_restrict<T>(m.lv[l].Nx, m.lv[l].Ny, m.st[l], m.lv[l].J, m.lv[l].R, m.lv[l].dU, m.lv[l + 1].R,
-                                 m.lv[l + 1].dU, s)))
+                                 m.lv[l + 1].dU, m.lv[l].cm, s)))
       return e;
   }
   Tail2<T> t;
@@ -348,17 +355,22 @@ nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_pa
     // and replayed; the host only waits for the residual and the flag.
     constexpr bool kMixed = std::is_same<T, float>::value;
     const int K = st0 == ST_J21 ? 21 : 9;
+    // Colour-major J9 and Dinv on large levels solved by V-cycles (not on
+    // the tail's levels, nor on the coarsest, whose J the dense LU reads).
+    const int minc = p->ctx->cm2d_min_cells;
+    const int cm = (l < L && st0 == ST_J9 && minc >= 0 && n >= minc && n > tail2_cells<T>()) ? 1 : 0;
     T *const J = reinterpret_cast<T *>(Lv.J);
     T *const dU = reinterpret_cast<T *>(Lv.dU);
-    T *const Rs = kMixed ? J + (size_t)K * 9 * n : reinterpret_cast<T *>(Lv.R);
+    T *const Rs = kMixed ? J + (size_t)K * 9 * blk_stride(cm, Lv.Nx, Lv.Ny) : reinterpret_cast<T *>(Lv.R);
     auto step = [&](cudaStream_t q) -> cudaError_t {
       cudaError_t e;
-      if ((e = launch2_jacobian<T>(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, J, frozen, q))) return e;
+      if ((e = launch2_jacobian<T>(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, J, frozen, cm, q)))
+        return e;
       if constexpr (kMixed) {
         if ((e = launch2_to_f32(3L * n, Lv.R, reinterpret_cast<float *>(Rs), q))) return e;
       }
       if ((e = cudaMemsetAsync(p->flag, 0, sizeof(int), q))) return e;
-      MG2<T> m = mg2_bind<T>(p, l, st0, J, Rs, dU);
+      MG2<T> m = mg2_bind<T>(p, l, st0, J, Rs, dU, cm);
       if (l == L) {
         if ((e = launch2_dense_factor<T>(Lv.Nx, Lv.Ny, st0, J, reinterpret_cast<T *>(p->dense), p->piv, p->flag, q)) ||
             (e = launch2_dense_solve<T>(n, reinterpret_cast<const T *>(p->dense), p->piv, Rs,
@@ -512,7 +524,7 @@ template <typename T>
 nswe_status vcycle2d_entry(nswe_ctx ctx, nswe_prob prob, int level, int nb, const T *J, const T *R, T *dU,
                            const nswe_params &prm) {
   if (nb != 9 && nb != 21) return NSWE_EINVAL;
-  MG2<T> m = mg2_bind<T>(prob, level, nb == 21 ? ST_J21 : ST_J9, J, R, dU);
+  MG2<T> m = mg2_bind<T>(prob, level, nb == 21 ? ST_J21 : ST_J9, J, R, dU, 0);
   cudaMemsetAsync(prob->flag, 0, sizeof(int), ctx->stream);
   if (level == prob->levels - 1) {
     const int n = nswe_prob_cells(prob, level);
@@ -581,6 +593,12 @@ nswe_status nswe_ctx_create(nswe_ctx *out, int device, void *stream) {
     return NSWE_ENOMEM;
   }
   *out = c;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_set_colour_major_2d(nswe_ctx ctx, int min_cells) {
+  if (!ctx) return NSWE_EINVAL;
+  ctx->cm2d_min_cells = min_cells;
   return NSWE_OK;
 }
 
@@ -811,7 +829,7 @@ nswe_status nswe_prob_create_2d(nswe_ctx ctx, nswe_prob *out, int Nx, int Ny, in
     Lv.J = a;
     a += round_up(189 * n);
     Lv.Dinv = a;
-    a += round_up(9 * n);
+    a += round_up(9 * n + 27 * (size_t)Lv.Ny);  // as prob2d_arena_doubles
   }
   p->dense = a;
   a += round_up(N3 * N3);
@@ -849,7 +867,7 @@ static nswe_status jacobian_common(nswe_ctx ctx, nswe_prob prob, int level, int 
   if (prob->dim == 2) {
     const int n = nswe_prob_cells(prob, level);
     if (launch2_residual(prob->dev2, level, n, U, R, res, ctx->partials, ctx->stream) ||
-        launch2_jacobian<double>(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, frozen,
+        launch2_jacobian<double>(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, frozen, 0,
                                  ctx->stream))
       return NSWE_ECUDA;
     return NSWE_OK;
@@ -886,7 +904,7 @@ nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, c
     if (nb != 9 && nb != 21) return NSWE_EINVAL;
     const int n = nswe_prob_cells(prob, level);
     return (launch2_residual(prob->dev2, level, n, U, R, res_l1, ctx->partials, ctx->stream) ||
-            launch2_jacobian<float>(prob->dev2, level, n, nb == 21 ? ST_J21 : ST_J9, U, eps, alpha, R, J, false,
+            launch2_jacobian<float>(prob->dev2, level, n, nb == 21 ? ST_J21 : ST_J9, U, eps, alpha, R, J, false, 0,
                                     ctx->stream))
                ? NSWE_ECUDA
                : NSWE_OK;

@@ -80,21 +80,35 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
                              double *partials, cudaStream_t s);
 // Multigrid launchers for T = double (FP64 path) and T = float (the multigrid
 // of a mixed-precision step); the Jacobian may be stored in either.
-// frozen: the frozen linearisation (weights and eigenvectors from U).
+// Storage of the 3x3 blocks (J, Dinv) of one level: cell-contiguous (cm = 0:
+// stride n, cell (i, j) at j Nx + i) or colour-major for the J9 colouring
+// (cm = 1): the cells of colour (i + j) mod 3 form one plane of Ny rows of
+// W3 = ceil(Nx / 3) slots, cell (i, j) at slot i / 3 of row j of its plane,
+// so that a colour pass reads one contiguous plane; stride 3 Ny W3 (at most
+// two unused slots per row of a plane).
+__host__ __device__ __forceinline__ size_t blk_stride(int cm, int Nx, int Ny) {
+  return cm ? 3 * (size_t)Ny * (size_t)((Nx + 2) / 3) : (size_t)Nx * (size_t)Ny;
+}
+__host__ __device__ __forceinline__ size_t blk_pos(int cm, int Nx, int Ny, int i, int j) {
+  return cm ? ((size_t)((i + j) % 3) * Ny + j) * (size_t)((Nx + 2) / 3) + (size_t)(i / 3) : (size_t)j * Nx + i;
+}
+
+// frozen: the frozen linearisation (weights and eigenvectors from U); cm:
+// the storage of J (blk_pos).
 template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, TJ *J, bool frozen, cudaStream_t s);
+                             const double *R, TJ *J, bool frozen, int cm, cudaStream_t s);
 template <typename T>
-cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, cudaStream_t s);
+cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, int cm, cudaStream_t s);
 template <typename T>
-cudaError_t launch2_dinv(int n, int st, const T *J, T *Dinv, cudaStream_t s);
+cudaError_t launch2_dinv(int Nx, int Ny, int st, const T *J, T *Dinv, int cm, cudaStream_t s);
 // mode 0: cells of colour col of the stencil's colouring; mode 1 / 2: of the
 // diagonal colourings (i + j) mod Kc / (j - i + Nx - 1) mod Kc.
 template <typename T>
 cudaError_t launch2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU, double omega, int mode,
-                        int Kc, int col, int reps, cudaStream_t s);
+                        int Kc, int col, int reps, int cm, cudaStream_t s);
 template <typename T>
-cudaError_t launch2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc,
+cudaError_t launch2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc, int cm,
                              cudaStream_t s);
 template <typename T>
 cudaError_t launch2_prolong(int Nx, int Ny, T *dU, const T *dUc, cudaStream_t s);

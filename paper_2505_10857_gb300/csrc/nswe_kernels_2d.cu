@@ -397,7 +397,7 @@ __global__ void k2_finish(const double *partials, int nparts, int n, double *res
 template <typename TJ, bool FROZEN>
 __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int level, int st, const double *U,
                                                         double eps, double alpha, const double *R, TJ *J,
-                                                        int msplit) {
+                                                        int msplit, int cm) {
   const Geo2 G = make_geo2(*P, level);
   const int n = G.Nx * G.Ny, K = st_size(st), kc = st_center(st);
   const double ieps = 1.0 / eps;
@@ -405,10 +405,11 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
     const int c = it % n, kq = it / n, k = msplit ? kq % K : kq, i = c % G.Nx, j = c / G.Nx;
     const int m0 = msplit ? kq / K : 0, m1 = msplit ? m0 + 1 : 3;
+    const size_t S = blk_stride(cm, G.Nx, G.Ny), pc = blk_pos(cm, G.Nx, G.Ny, i, j);
     const int pi = i + st_off(st, k, 0), pj = j + st_off(st, k, 1);
     if (pi < 0 || pi >= G.Nx || pj < 0 || pj >= G.Ny) {
       for (int l = 0; l < 3; ++l)
-        for (int m = m0; m < m1; ++m) J[(size_t)(k * 9 + l * 3 + m) * n + c] = TJ(0.0);
+        for (int m = m0; m < m1; ++m) J[(size_t)(k * 9 + l * 3 + m) * S + pc] = TJ(0.0);
       continue;
     }
     const double R0[3] = {R[c], R[n + c], R[2 * n + c]};
@@ -452,22 +453,22 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
       }
     }
     for (int m = m0; m < m1; ++m) {
-      const double S[3] = {0.0, sd[0][m], sd[1][m]};
+      const double Sm[3] = {0.0, sd[0][m], sd[1][m]};
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
-        const double Rp = fd[0][m][l] / G.dx + fd[1][m][l] / G.dy - S[l];
+        const double Rp = fd[0][m][l] / G.dx + fd[1][m][l] / G.dy - Sm[l];
         double v = (Rp - R0[l]) * ieps;
         if (l == m) v += reg;
-        J[(size_t)(k * 9 + l * 3 + m) * n + c] = TJ(v);
+        J[(size_t)(k * 9 + l * 3 + m) * S + pc] = TJ(v);
       }
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc) {
-  const int n = Nx * Ny, Ncx = Nx / 2, Ncy = Ny / 2, nc = Ncx * Ncy, K = st_size(st), cs = st_coarse(st),
-            Kc = st_size(cs);
+__global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, int cm) {
+  const int Ncx = Nx / 2, Ncy = Ny / 2, nc = Ncx * Ncy, K = st_size(st), cs = st_coarse(st), Kc = st_size(cs);
+  const size_t Sf = blk_stride(cm, Nx, Ny);
   for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += gridDim.x * blockDim.x) {
     const int I = cc % Ncx, Jy = cc / Ncx;
     T acc[9][9];
@@ -475,7 +476,8 @@ __global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st,
       for (int e = 0; e < 9; ++e) acc[t][e] = T(0.0);
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
-        const int xi = 2 * I + a, yi = 2 * Jy + b, c = yi * Nx + xi;
+        const int xi = 2 * I + a, yi = 2 * Jy + b;
+        const size_t c = blk_pos(cm, Nx, Ny, xi, yi);
         for (int k = 0; k < K; ++k) {
           const int ex = xi + st_off(st, k, 0), ey = yi + st_off(st, k, 1);
           if (ex < 0 || ex >= Nx || ey < 0 || ey >= Ny) continue;
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st,
           for (int t = 0; t < Kc; ++t)
             if (st_off(cs, t, 0) == ox && st_off(cs, t, 1) == oy) kk = t;
           if (kk < 0) continue;
-          for (int e = 0; e < 9; ++e) acc[kk][e] += Jf[(size_t)(k * 9 + e) * n + c];
+          for (int e = 0; e < 9; ++e) acc[kk][e] += Jf[(size_t)(k * 9 + e) * Sf + c];
         }
       }
     for (int t = 0; t < Kc; ++t)
@@ -493,9 +495,11 @@ __global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_dinv(int n, int st, const T *J, T *Dinv) {
-  const int kc = st_center(st);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(kThreads) k2_dinv(int Nx, int Ny, int st, const T *J, T *Dinv, int cm) {
+  const int kc = st_center(st), ncell = Nx * Ny;
+  const size_t n = blk_stride(cm, Nx, Ny);  // the stride of J and Dinv
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ncell; q += gridDim.x * blockDim.x) {
+    const size_t c = blk_pos(cm, Nx, Ny, q % Nx, q / Nx);
     T a[9];
     for (int e = 0; e < 9; ++e) a[e] = J[(size_t)(kc * 9 + e) * n + c];
     const T c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
@@ -516,9 +520,10 @@ __global__ void __launch_bounds__(kThreads) k2_dinv(int n, int st, const T *J, T
 // (consecutive visits of a colour see the same neighbours).
 template <typename T>
 __device__ __forceinline__ void sor_cell2(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU,
-                                          double omega_d, int reps, int i, int j) {
+                                          double omega_d, int reps, int i, int j, int cm) {
   const T omega = T(omega_d);
   const int n = Nx * Ny, K = st_size(st), kc = st_center(st), c = j * Nx + i;
+  const size_t S = blk_stride(cm, Nx, Ny), pc = blk_pos(cm, Nx, Ny, i, j);  // J, Dinv
   T r[3] = {R[c], R[n + c], R[2 * n + c]};
   for (int k = 0; k < K; ++k) {
     if (k == kc) continue;
@@ -528,14 +533,14 @@ __device__ __forceinline__ void sor_cell2(int Nx, int Ny, int st, const T *J, co
     const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
-              J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
+      r[l] += J[(size_t)(k * 9 + l * 3 + 0) * S + pc] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * S + pc] * x1 +
+              J[(size_t)(k * 9 + l * 3 + 2) * S + pc] * x2;
   }
   T t[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l)
-    t[l] = Dinv[(size_t)(l * 3 + 0) * n + c] * r[0] + Dinv[(size_t)(l * 3 + 1) * n + c] * r[1] +
-           Dinv[(size_t)(l * 3 + 2) * n + c] * r[2];
+    t[l] = Dinv[(size_t)(l * 3 + 0) * S + pc] * r[0] + Dinv[(size_t)(l * 3 + 1) * S + pc] * r[1] +
+           Dinv[(size_t)(l * 3 + 2) * S + pc] * r[2];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     T x = dU[l * n + c];
@@ -573,28 +578,28 @@ __device__ __forceinline__ void sor_items(int Nx, int Ny, int st, int &mode, int
 // block-wide stride).
 template <typename T>
 __device__ void sor_pass(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU, double omega,
-                         int mode, int Kc, int col, int reps, int first, int stride) {
+                         int mode, int Kc, int col, int reps, int first, int stride, int cm = 0) {
   int P, W, items;
   sor_items(Nx, Ny, st, mode, Kc, col, P, W, items);
   if (mode == 0) {
     const int a = col % P, b = col / P;
     for (int t = first; t < items; t += stride)
-      sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, a + (t % W) * P, b + (t / W) * P);
+      sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, a + (t % W) * P, b + (t / W) * P, cm);
     return;
   }
   for (int t = first; t < items; t += stride) {
     const int j = t / W, m = t % W;
     const int a = mode == 1 ? col - j : j + Nx - 1 - col;
     const int i = ((a % Kc) + Kc) % Kc + m * Kc;
-    if (i < Nx) sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, i, j);
+    if (i < Nx) sor_cell2(Nx, Ny, st, J, Dinv, R, dU, omega, reps, i, j, cm);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R,
-                                                   T *dU, double omega, int mode, int Kc, int col, int reps) {
+                                                   T *dU, double omega, int mode, int Kc, int col, int reps, int cm) {
   sor_pass<T>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, blockIdx.x * blockDim.x + threadIdx.x,
-              gridDim.x * blockDim.x);
+              gridDim.x * blockDim.x, cm);
 }
 
 // Cell (i, j) of item t of a colour pass (the enumeration of sor_pass);
@@ -624,7 +629,7 @@ __device__ __forceinline__ bool sor_item_cell(int Nx, int mode, int Kc, int col,
 template <typename T, int STC>
 __device__ __forceinline__ void sor_pass_split(int Nx, int Ny, int st_arg, const T *J, const T *Dinv, const T *R,
                                                T *dU, double omega_d, int mode, int Kc, int col, int reps,
-                                               int warp0, int warps) {
+                                               int warp0, int warps, int cm) {
   const int st = STC >= 0 ? STC : st_arg;
   int P, W, items;
   sor_items(Nx, Ny, st, mode, Kc, col, P, W, items);
@@ -636,6 +641,7 @@ __device__ __forceinline__ void sor_pass_split(int Nx, int Ny, int st_arg, const
     int i = 0, j = 0;
     const bool on = lane < 30 && t < items && sor_item_cell(Nx, mode, Kc, col, P, W, t, i, j);
     const int c = j * Nx + i;
+    const size_t S = blk_stride(cm, Nx, Ny), pc = blk_pos(cm, Nx, Ny, i, j);  // J, Dinv
     T r = on ? R[l * n + c] : T(0.0);
     if (on)
 #pragma unroll
@@ -645,15 +651,15 @@ __device__ __forceinline__ void sor_pass_split(int Nx, int Ny, int st_arg, const
         if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
         const int cp = q * Nx + p;
         const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
-        r += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
-             J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
+        r += J[(size_t)(k * 9 + l * 3 + 0) * S + pc] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * S + pc] * x1 +
+             J[(size_t)(k * 9 + l * 3 + 2) * S + pc] * x2;
       }
     const T r0 = __shfl_sync(0xffffffffu, r, min(src, 31));
     const T r1 = __shfl_sync(0xffffffffu, r, min(src + 1, 31));
     const T r2 = __shfl_sync(0xffffffffu, r, min(src + 2, 31));
     if (on) {
-      const T tl = Dinv[(size_t)(l * 3 + 0) * n + c] * r0 + Dinv[(size_t)(l * 3 + 1) * n + c] * r1 +
-                   Dinv[(size_t)(l * 3 + 2) * n + c] * r2;
+      const T tl = Dinv[(size_t)(l * 3 + 0) * S + pc] * r0 + Dinv[(size_t)(l * 3 + 1) * S + pc] * r1 +
+                   Dinv[(size_t)(l * 3 + 2) * S + pc] * r2;
       T x = dU[l * n + c];
       for (int s = 0; s < reps; ++s) x = (T(1.0) - omega) * x - omega * tl;
       dU[l * n + c] = x;
@@ -664,9 +670,9 @@ __device__ __forceinline__ void sor_pass_split(int Nx, int Ny, int st_arg, const
 template <typename T, int STC>
 __global__ void __launch_bounds__(kThreads) k2_sor_split(int Nx, int Ny, int st, const T *J, const T *Dinv,
                                                          const T *R, T *dU, double omega, int mode, int Kc, int col,
-                                                         int reps) {
+                                                         int reps, int cm) {
   sor_pass_split<T, STC>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps,
-                         (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+                         (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5, cm);
 }
 
 // A colour pass by the threads of one block (the tail kernel): in FP64 split
@@ -681,23 +687,25 @@ __device__ void sor_pass_block_split(int Nx, int Ny, int st, const T *J, const T
   }
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (st == ST_J9)
-    sor_pass_split<T, ST_J9>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw);
+    sor_pass_split<T, ST_J9>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw, 0);
   else if (st == ST_P5)
-    sor_pass_split<T, ST_P5>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw);
+    sor_pass_split<T, ST_P5>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw, 0);
   else
-    sor_pass_split<T, -1>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw);
+    sor_pass_split<T, -1>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, w, nw, 0);
 }
 
 template <typename T>
 __device__ void restrict_cells2(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc, int first,
-                                int stride) {
+                                int stride, int cm = 0) {
   const int n = Nx * Ny, Ncx = Nx / 2, nc = Ncx * (Ny / 2), K = st_size(st);
+  const size_t S = blk_stride(cm, Nx, Ny);  // J
   for (int cc = first; cc < nc; cc += stride) {
     const int I = cc % Ncx, Jy = cc / Ncx;
     T s[3] = {T(0.0), T(0.0), T(0.0)};
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         const int xi = 2 * I + a, yi = 2 * Jy + b, c = yi * Nx + xi;
+        const size_t pc = blk_pos(cm, Nx, Ny, xi, yi);
         T r[3] = {R[c], R[n + c], R[2 * n + c]};
         for (int k = 0; k < K; ++k) {
           const int p = xi + st_off(st, k, 0), q = yi + st_off(st, k, 1);
@@ -706,8 +714,8 @@ __device__ void restrict_cells2(int Nx, int Ny, int st, const T *J, const T *R, 
           const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
 #pragma unroll
           for (int l = 0; l < 3; ++l)
-            r[l] += J[(size_t)(k * 9 + l * 3 + 0) * n + c] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * n + c] * x1 +
-                    J[(size_t)(k * 9 + l * 3 + 2) * n + c] * x2;
+            r[l] += J[(size_t)(k * 9 + l * 3 + 0) * S + pc] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * S + pc] * x1 +
+                    J[(size_t)(k * 9 + l * 3 + 2) * S + pc] * x2;
         }
         s[0] += r[0];
         s[1] += r[1];
@@ -723,8 +731,9 @@ __device__ void restrict_cells2(int Nx, int Ny, int st, const T *J, const T *R, 
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU,
-                                                        T *Rc, T *dUc) {
-  restrict_cells2<T>(Nx, Ny, st, J, R, dU, Rc, dUc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+                                                        T *Rc, T *dUc, int cm) {
+  restrict_cells2<T>(Nx, Ny, st, J, R, dU, Rc, dUc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                     cm);
 }
 
 template <typename T>
@@ -981,32 +990,32 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
 
 template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, TJ *J, bool frozen, cudaStream_t s) {
+                             const double *R, TJ *J, bool frozen, int cm, cudaStream_t s) {
   const long items = (long)n * (st == ST_J21 ? 21 : 9);
   const int msplit = 3 * items <= kJacSplitItems ? 1 : 0;
   const int grid = grid2(items * (msplit ? 3 : 1));
   if (frozen)
-    k2_jacobian<TJ, true><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, msplit);
+    k2_jacobian<TJ, true><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, msplit, cm);
   else
-    k2_jacobian<TJ, false><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, msplit);
+    k2_jacobian<TJ, false><<<grid, kThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, msplit, cm);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, cudaStream_t s) {
-  k2_coarse_op<T><<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, Jf, Jc);
+cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, int cm, cudaStream_t s) {
+  k2_coarse_op<T><<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, Jf, Jc, cm);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch2_dinv(int n, int st, const T *J, T *Dinv, cudaStream_t s) {
-  k2_dinv<T><<<grid2(n), kThreads, 0, s>>>(n, st, J, Dinv);
+cudaError_t launch2_dinv(int Nx, int Ny, int st, const T *J, T *Dinv, int cm, cudaStream_t s) {
+  k2_dinv<T><<<grid2((long)Nx * Ny), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, cm);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const T *R, T *dU, double omega, int mode,
-                        int Kc, int col, int reps, cudaStream_t s) {
+                        int Kc, int col, int reps, int cm, cudaStream_t s) {
   // Items of the pass as the kernel enumerates them (see sor_items).
   long items;
   if (mode == 0 && (st == ST_J9 || st == ST_P5)) items = (long)((Nx + (st == ST_J9 ? 3 : 2) - 1) / (st == ST_J9 ? 3 : 2)) * Ny;
@@ -1019,21 +1028,21 @@ cudaError_t launch2_sor(int Nx, int Ny, int st, const T *J, const T *Dinv, const
     const int bs = warps <= 4L * 152 ? 32 : 128;
     const unsigned grid = (unsigned)((warps * 32 + bs - 1) / bs);
     if (NSWE_SOR_UNROLL && st == ST_J9)
-      k2_sor_split<T, ST_J9><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+      k2_sor_split<T, ST_J9><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, cm);
     else if (NSWE_SOR_UNROLL && st == ST_P5)
-      k2_sor_split<T, ST_P5><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+      k2_sor_split<T, ST_P5><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, cm);
     else
-      k2_sor_split<T, -1><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+      k2_sor_split<T, -1><<<grid, bs, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, cm);
   } else {
-    k2_sor<T><<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps);
+    k2_sor<T><<<grid2(items), kThreads, 0, s>>>(Nx, Ny, st, J, Dinv, R, dU, omega, mode, Kc, col, reps, cm);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc,
+cudaError_t launch2_restrict(int Nx, int Ny, int st, const T *J, const T *R, const T *dU, T *Rc, T *dUc, int cm,
                              cudaStream_t s) {
-  k2_restrict<T><<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, J, R, dU, Rc, dUc);
+  k2_restrict<T><<<grid2((long)(Nx / 2) * (Ny / 2)), kThreads, 0, s>>>(Nx, Ny, st, J, R, dU, Rc, dUc, cm);
   return cudaGetLastError();
 }
 
@@ -1077,12 +1086,12 @@ cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream
 
 #define NSWE_2D_INSTANTIATE(T)                                                                                    \
   template cudaError_t launch2_jacobian<T>(const ProbDev2 *, int, int, int, const double *, double, double,      \
-                                           const double *, T *, bool, cudaStream_t);                             \
-  template cudaError_t launch2_coarse_op<T>(int, int, int, const T *, T *, cudaStream_t);                        \
-  template cudaError_t launch2_dinv<T>(int, int, const T *, T *, cudaStream_t);                                  \
+                                           const double *, T *, bool, int, cudaStream_t);                        \
+  template cudaError_t launch2_coarse_op<T>(int, int, int, const T *, T *, int, cudaStream_t);                   \
+  template cudaError_t launch2_dinv<T>(int, int, int, const T *, T *, int, cudaStream_t);                        \
   template cudaError_t launch2_sor<T>(int, int, int, const T *, const T *, const T *, T *, double, int, int, int, \
-                                      int, cudaStream_t);                                                        \
-  template cudaError_t launch2_restrict<T>(int, int, int, const T *, const T *, const T *, T *, T *,             \
+                                      int, int, cudaStream_t);                                                   \
+  template cudaError_t launch2_restrict<T>(int, int, int, const T *, const T *, const T *, T *, T *, int,        \
                                            cudaStream_t);                                                        \
   template cudaError_t launch2_prolong<T>(int, int, T *, const T *, cudaStream_t);                               \
   template cudaError_t launch2_dense_factor<T>(int, int, int, const T *, T *, int *, int *, cudaStream_t);       \

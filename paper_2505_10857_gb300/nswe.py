@@ -108,6 +108,7 @@ EXPORTS = {
     "nswe_mg_vcycle": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
     "nswe_jacobian_f32": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_jacobian_frozen": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
+    "nswe_ctx_set_colour_major_2d": (_i, [_vp, _i]),
     "nswe_mg_vcycle_f32": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
     "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
@@ -353,6 +354,11 @@ def nswe_jacobian_simplified(ctx, prob, level, U, eps, alpha, R, J, res=None):
 def nswe_jacobian_full(ctx, prob, level, U, eps, alpha, R, J, res=None):
     _check("nswe_jacobian_full", lib().nswe_jacobian_full(
         ctx.h, prob.h, int(level), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
+
+
+def nswe_ctx_set_colour_major_2d(ctx, min_cells):
+    """2D Newton levels of at least min_cells cells keep J9 colour-major (<0: never)."""
+    _check("nswe_ctx_set_colour_major_2d", lib().nswe_ctx_set_colour_major_2d(ctx.h, int(min_cells)))
 
 
 def nswe_jacobian_frozen(ctx, prob, level, nb, U, eps, alpha, R, J, res=None):

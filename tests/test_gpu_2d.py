@@ -291,3 +291,33 @@ def test_guess_sized_for_another_level_is_refused(nswe, ctx):
     p1 = I.bump_channel_2d(0, 32, 16, 3, start_level=1)
     info = nswe.nswe_newton_solve(ctx, pr, dev(p1.U0_start), U, prm)
     assert info["status"] == 0 and info["res"][0] < 1e-10
+
+
+@pytest.mark.parametrize("case", ["wedge_fp64", "bump_mixed", "bump_fp64_directional"])
+def test_colour_major_storage_gives_the_same_bits(nswe, ctx, case):
+    """Nested solves with J9 and its diagonal inverses stored colour-major on
+    every level solved by V-cycles (forced down to the smallest levels) and
+    cell-contiguous: the same Newton counts and the same bits."""
+    if case == "wedge_fp64":
+        inp = I.wedge(64, 32, 4, start_level=2)
+        prm = nswe.params2d_from(I.Params2D(levels=4, nu1=[15], nu2=[15], tol=1e-11, n_max=400, nest_start=2,
+                                            omega=0.1, frozen=True))
+    else:
+        inp = I.bump_channel_2d(1, 128, 64, 5)
+        prm = nswe.params2d_from(I.Params2D(levels=5, nu1=[20], nu2=[20], tol=1e-10, n_max=400,
+                                            colours=5 if "directional" in case else 0))
+        prm.precision = nswe.PREC_MIXED if "mixed" in case else nswe.PREC_FP64
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    out = []
+    try:
+        for min_cells in (1, -1):
+            nswe.nswe_ctx_set_colour_major_2d(ctx, min_cells)
+            U = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
+            info = nswe.nswe_newton_solve(ctx, prob, dev(inp.U0_start), U, prm)
+            out.append((host(U), info))
+    finally:
+        nswe.nswe_ctx_set_colour_major_2d(ctx, 131072)
+    (Ua, ia), (Ub, ib) = out
+    assert ia["status"] == 0 == ib["status"], (ia, ib)
+    assert ia["iters"] == ib["iters"]
+    assert np.array_equal(Ua, Ub)
