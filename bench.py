@@ -312,8 +312,16 @@ def run_gpu(args, rank, world, local_rank):
     ctx = nswe.Context(local_rank)
     stream = torch.cuda.current_stream(dev)
     probs = [nswe.Problem1D.from_inputs(ctx, p) for p in inps]
-    U0s = [torch.from_numpy(p.U0_start).to(dev) for p in inps]
-    Us = [torch.zeros((2, p.N), dtype=torch.float64, device=dev) for p in inps]
+    # every problem's guess and result as a 256-byte-aligned view of one device
+    # buffer each, so that the end-to-end step moves them in one copy each way
+    u0_off = np.cumsum([0] + [-(-p.U0_start.size // 32) * 32 for p in inps])
+    u_off = np.cumsum([0] + [-(-2 * p.N // 32) * 32 for p in inps])
+    U0_all = torch.zeros(int(u0_off[-1]), dtype=torch.float64, device=dev)
+    U_all = torch.zeros(int(u_off[-1]), dtype=torch.float64, device=dev)
+    U0s = [U0_all[int(u0_off[k]):int(u0_off[k]) + p.U0_start.size].view(2, -1) for k, p in enumerate(inps)]
+    Us = [U_all[int(u_off[k]):int(u_off[k]) + 2 * p.N].view(2, -1) for k, p in enumerate(inps)]
+    for k, p in enumerate(inps):
+        U0s[k].copy_(torch.from_numpy(p.U0_start))
 
     def step(want_info=False):
         return nswe.nswe_newton_solve_batch(ctx, probs, U0s, Us, prm, want_info=want_info)
@@ -385,27 +393,25 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         single.append(e0.elapsed_time(e1))
 
-    # ---- end to end through the C ABI from pinned host buffers
-    pin = []
-    for p in inps:
-        sf = torch.from_numpy(p.sig_face).pin_memory()
-        gq = torch.from_numpy(p.gq_all()).pin_memory()
-        u0 = torch.from_numpy(p.U0_start).pin_memory()
-        pin.append((sf, gq, u0, torch.empty((2, p.N), dtype=torch.float64).pin_memory()))
-    h2d = sum(a.numel() * 8 for (sf, gq, u0, _) in pin for a in (sf, gq, u0))
-    d2h = sum(o.numel() * 8 for (_, _, _, o) in pin) + B * ctypes.sizeof(nswe.Info)
+    # ---- end to end through the C ABI from pinned host buffers: every step
+    # uploads all problems' geometry (one batched call) and guesses, solves,
+    # and reads the results back
+    pin_sf = [torch.from_numpy(p.sig_face).pin_memory().numpy() for p in inps]
+    pin_gq = [torch.from_numpy(p.gq_all()).pin_memory().numpy() for p in inps]
+    pin_u0 = U0_all.cpu().pin_memory()
+    pin_u = torch.empty_like(U_all, device="cpu").pin_memory()
+    bcl, bcr = [p.bcl for p in inps], [p.bcr for p in inps]
+    h2d = sum(a.nbytes for a in pin_sf + pin_gq) + pin_u0.numel() * 8  # the bytes copied, padding included
+    d2h = pin_u.numel() * 8 + B * ctypes.sizeof(nswe.Info)
     e2e_times = []
     for s in range(args.warmup + args.steps):
         barrier()
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        for k, p in enumerate(inps):
-            sf, gq, u0, _ = pin[k]
-            probs[k].set_geometry(sf.numpy(), gq.numpy(), p.bcl, p.bcr)
-            U0s[k].copy_(u0, non_blocking=True)
+        nswe.nswe_prob_set_geometry_batch_1d(ctx, probs, pin_sf, pin_gq, bcl, bcr)
+        U0_all.copy_(pin_u0, non_blocking=True)
         infos_e = step(want_info=True)  # synchronous: includes the D2H of the per-solve records
-        for k in range(B):
-            pin[k][3].copy_(Us[k], non_blocking=True)
+        pin_u.copy_(U_all, non_blocking=True)
         torch.cuda.synchronize()
         if s >= args.warmup:
             e2e_times.append(time.perf_counter() - w0)

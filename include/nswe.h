@@ -198,14 +198,27 @@ nswe_status nswe_prob_create_1d(nswe_ctx ctx, nswe_prob *out, int N, int levels,
                                 const double *gauss_geom,
                                 const nswe_bc1d *left, const nswe_bc1d *right);
 /* Re-uploads geometry and boundary data of an existing problem (same N and
- * levels) from HOST arrays, asynchronously on the context stream; the host
- * arrays must stay valid until the stream reaches this point (pinned memory
- * gives a true asynchronous copy). */
+ * levels) from HOST arrays. The arrays are checked and packed into the
+ * problem's pinned staging buffer before the call returns (the caller may
+ * reuse them at once); the copy to the device and the derived geometry then
+ * run asynchronously on the context stream. A later upload to the same
+ * problem first waits for that copy. EINVAL for non-finite data (nothing is
+ * uploaded). */
 nswe_status nswe_prob_set_geometry_1d(nswe_ctx ctx, nswe_prob prob,
                                       const double *sigma_face,
                                       const double *gauss_geom,
                                       const nswe_bc1d *left,
                                       const nswe_bc1d *right);
+
+/* The same for `count` distinct 1D problems (HOST arrays of count entries
+ * each): the packing and checks run in parallel on host threads, and no
+ * upload starts unless every problem's data is valid. */
+nswe_status nswe_prob_set_geometry_batch_1d(nswe_ctx ctx, int count,
+                                            const nswe_prob *probs,
+                                            const double *const *sigma_faces,
+                                            const double *const *gauss_geoms,
+                                            const nswe_bc1d *lefts,
+                                            const nswe_bc1d *rights);
 /* Two-dimensional problem (Eq. 1-2, Section 4) on [x0,x1] x [y0,y1] with
  * Nx x Ny cells and `levels` nested/multigrid levels (Nx, Ny divisible by
  * 2^(levels-1); every level at least 4 x 4 cells; coarsest level at most 512

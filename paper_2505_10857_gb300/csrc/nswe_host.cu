@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <thread>
@@ -35,6 +36,8 @@ struct nswe_prob_s {
   ProbDev *dev;          // device copy
   double *arena;
   size_t geo_doubles;    // geometry region at the front of the arena
+  double *stage;         // 1D: pinned staging of the geometry upload [geo_doubles]
+  cudaEvent_t staged;    // 1D: the last upload from `stage` has been copied
   // 2D
   int Nx, Ny;
   ProbDev2 host2;
@@ -157,24 +160,41 @@ nswe_status ensure_cap(nswe_ctx ctx, int count) {
   return NSWE_OK;
 }
 
-nswe_status upload_geometry(nswe_prob p, const double *sigma_face, const double *gauss_geom,
-                            const nswe_bc1d *left, const nswe_bc1d *right) {
-  std::vector<double> geo(p->geo_doubles, 0.0);
+// Geometry upload of a 1D problem in two phases. Pack: the per-level face
+// widths and Gauss-point geometry into the problem's pinned staging buffer
+// (after the previous upload from it has been copied), with the finiteness
+// check; host work only. Issue: the asynchronous copies of the staged
+// geometry and of the problem record, and the derived-geometry kernel, on
+// the context stream.
+nswe_status pack_geometry(nswe_prob p, const double *sigma_face, const double *gauss_geom) {
+  if (!p->stage) {
+    if (cudaMallocHost(&p->stage, sizeof(double) * p->geo_doubles) != cudaSuccess) return NSWE_ENOMEM;
+    if (cudaEventCreateWithFlags(&p->staged, cudaEventDisableTiming) != cudaSuccess) return NSWE_ECUDA;
+  } else if (cudaEventSynchronize(p->staged) != cudaSuccess) {
+    return NSWE_ECUDA;
+  }
+  double *geo = p->stage;
   size_t off = 0;
   for (int l = 0; l < p->levels; ++l) {
-    int Nl = p->N >> l;
+    const int Nl = p->N >> l;
     for (int f = 0; f <= Nl; ++f) geo[off + f] = sigma_face[(size_t)f << l];
+    for (size_t f = Nl + 1; f < round_up(Nl + 1); ++f) geo[off + f] = 0.0;
     off += round_up(Nl + 1);
   }
   size_t src = 0;
   for (int l = 0; l < p->levels; ++l) {
-    int Nl = p->N >> l;
+    const int Nl = p->N >> l;
     std::memcpy(&geo[off], gauss_geom + src, sizeof(double) * 6 * Nl);
+    for (size_t f = 6 * (size_t)Nl; f < round_up(6 * (size_t)Nl); ++f) geo[off + f] = 0.0;
     src += 6 * (size_t)Nl;
     off += round_up(6 * (size_t)Nl);
   }
   for (size_t i = 0; i < off; ++i)
     if (!std::isfinite(geo[i])) return NSWE_EINVAL;
+  return NSWE_OK;
+}
+
+nswe_status issue_geometry(nswe_prob p, const nswe_bc1d *left, const nswe_bc1d *right, bool derive = true) {
   p->host.bl = left->kind;
   p->host.br = right->kind;
   p->host.blh = left->h;
@@ -182,12 +202,20 @@ nswe_status upload_geometry(nswe_prob p, const double *sigma_face, const double 
   p->host.brh = right->h;
   p->host.brq = right->q;
   cudaStream_t s = p->ctx->stream;
-  if (cudaMemcpyAsync(p->arena, geo.data(), sizeof(double) * off, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (cudaMemcpyAsync(p->arena, p->stage, sizeof(double) * p->geo_doubles, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaEventRecord(p->staged, s) != cudaSuccess)
     return NSWE_ECUDA;
   if (cudaMemcpyAsync(p->dev, &p->host, sizeof(ProbDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return NSWE_ECUDA;
-  if (launch_geom_derive(p->dev, p->N, s) != cudaSuccess) return NSWE_ECUDA;
+  if (derive && launch_geom_derive(p->dev, p->N, s) != cudaSuccess) return NSWE_ECUDA;
   return NSWE_OK;
+}
+
+nswe_status upload_geometry(nswe_prob p, const double *sigma_face, const double *gauss_geom,
+                            const nswe_bc1d *left, const nswe_bc1d *right) {
+  nswe_status st = pack_geometry(p, sigma_face, gauss_geom);
+  return st != NSWE_OK ? st : issue_geometry(p, left, right);
 }
 
 // ---------------------------------------------------------------- 2D host side
@@ -714,10 +742,62 @@ nswe_status nswe_prob_set_geometry_1d(nswe_ctx ctx, nswe_prob prob, const double
   return upload_geometry(prob, sigma_face, gauss_geom, left, right);
 }
 
+nswe_status nswe_prob_set_geometry_batch_1d(nswe_ctx ctx, int count, const nswe_prob *probs,
+                                            const double *const *sigma_faces, const double *const *gauss_geoms,
+                                            const nswe_bc1d *lefts, const nswe_bc1d *rights) {
+  if (!ctx || count < 0 || (count > 0 && (!probs || !sigma_faces || !gauss_geoms || !lefts || !rights)))
+    return NSWE_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i] || probs[i]->ctx != ctx || probs[i]->dim != 1 || !sigma_faces[i] || !gauss_geoms[i] ||
+        !valid_bc(&lefts[i]) || !valid_bc(&rights[i]))
+      return NSWE_EINVAL;
+    for (int k = 0; k < i; ++k)
+      if (probs[k] == probs[i]) return NSWE_EINVAL;  // one staging buffer per problem
+  }
+  if (count == 0) return NSWE_OK;
+  DeviceGuard dg(ctx->device);
+  // Pack every problem (host work, in parallel), then issue the copies: no
+  // upload starts unless every problem's data is valid.
+  std::vector<nswe_status> st(count, NSWE_OK);
+  std::atomic<int> next{0};
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int workers = std::max(1, std::min(count, std::min(16, (int)(hw ? hw : 1))));
+  auto work = [&] {
+    cudaSetDevice(ctx->device);
+    for (int i = next++; i < count; i = next++) st[i] = pack_geometry(probs[i], sigma_faces[i], gauss_geoms[i]);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (st[i] != NSWE_OK) return st[i];
+  for (int i = 0; i < count; ++i) {
+    nswe_status e = issue_geometry(probs[i], &lefts[i], &rights[i], false);
+    if (e != NSWE_OK) return e;
+  }
+  // the derived geometry of all problems in one launch (the context's task
+  // array addresses them; later users of the array are ordered on the stream)
+  nswe_status e = ensure_cap(ctx, count);
+  if (e != NSWE_OK) return e;
+  std::vector<SolveTask> tasks(count);
+  for (int i = 0; i < count; ++i) {
+    std::memset(&tasks[i], 0, sizeof(SolveTask));
+    tasks[i].prob = probs[i]->dev;
+  }
+  if (cudaMemcpyAsync(ctx->tasks, tasks.data(), sizeof(SolveTask) * count, cudaMemcpyHostToDevice, ctx->stream) !=
+          cudaSuccess ||
+      launch_geom_derive_batch(ctx->tasks, count, ctx->stream) != cudaSuccess)
+    return NSWE_ECUDA;
+  return NSWE_OK;
+}
+
 nswe_status nswe_prob_destroy(nswe_prob prob) {
   if (!prob) return NSWE_EINVAL;
   DeviceGuard dg(prob->ctx->device);
   cudaStreamSynchronize(prob->ctx->stream);
+  if (prob->staged) cudaEventDestroy(prob->staged);
+  if (prob->stage) cudaFreeHost(prob->stage);
   cudaFree(prob->arena);
   cudaFree(prob->dev);
   cudaFree(prob->dev2);

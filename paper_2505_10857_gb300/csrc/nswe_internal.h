@@ -168,6 +168,8 @@ struct SolveTask {
 // Kernel launchers (stream-ordered, return cudaGetLastError()).
 // Fills every level's gd from its sf and gq (after each geometry upload).
 cudaError_t launch_geom_derive(const ProbDev *p, int finest_cells, cudaStream_t s);
+// The derived geometry of tasks[0..count).prob, one block each.
+cudaError_t launch_geom_derive_batch(const SolveTask *tasks, int count, cudaStream_t s);
 cudaError_t launch_residual(const ProbDev *p, int level, int N, const double *U, double *R, double *res,
                             double *partials, cudaStream_t s);
 cudaError_t launch_jacobian(const ProbDev *p, int level, int N, int nb, const double *U, double eps,

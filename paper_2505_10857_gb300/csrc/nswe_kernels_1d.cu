@@ -1089,6 +1089,12 @@ __global__ void __launch_bounds__(kThreads) k_geom_derive(const ProbDev *P) {
   geom_derive_items(*P, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+// The derived geometry of many problems in one launch: block b derives
+// tasks[b].prob.
+__global__ void __launch_bounds__(kThreads) k_geom_derive_batch(const SolveTask *tasks) {
+  geom_derive_items(*tasks[blockIdx.x].prob, threadIdx.x, blockDim.x);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jac_a(const ProbDev *P, int level, const double *U, double eps) {
   Geo G = make_geo(*P, level);
@@ -1296,6 +1302,12 @@ int grid_for(int items) {
 
 cudaError_t launch_geom_derive(const ProbDev *p, int finest_cells, cudaStream_t s) {
   k_geom_derive<<<grid_for(2 * finest_cells + 1), kThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geom_derive_batch(const SolveTask *tasks, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_geom_derive_batch<<<count, kThreads, 0, s>>>(tasks);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,8 @@ EXPORTS = {
     "nswe_jacobian_f32": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_jacobian_frozen": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_ctx_set_colour_major_2d": (_i, [_vp, _i]),
+    "nswe_prob_set_geometry_batch_1d": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                                             ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
     "nswe_mg_vcycle_f32": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
     "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
@@ -354,6 +356,18 @@ def nswe_jacobian_simplified(ctx, prob, level, U, eps, alpha, R, J, res=None):
 def nswe_jacobian_full(ctx, prob, level, U, eps, alpha, R, J, res=None):
     _check("nswe_jacobian_full", lib().nswe_jacobian_full(
         ctx.h, prob.h, int(level), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
+
+
+def nswe_prob_set_geometry_batch_1d(ctx, probs, sigma_faces, gauss_geoms, lefts, rights):
+    """Geometry re-upload of several 1D problems (host float64 arrays)."""
+    n = len(probs)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in list(sigma_faces) + list(gauss_geoms)]
+    ph = (_vp * n)(*[p.h.value for p in probs])
+    sf = (_dp * n)(*[a.ctypes.data for a in arrs[:n]])
+    gq = (_dp * n)(*[a.ctypes.data for a in arrs[n:]])
+    bl = (BC1D * n)(*[_bc(b) for b in lefts])
+    br = (BC1D * n)(*[_bc(b) for b in rights])
+    _check("nswe_prob_set_geometry_batch_1d", lib().nswe_prob_set_geometry_batch_1d(ctx.h, n, ph, sf, gq, bl, br))
 
 
 def nswe_ctx_set_colour_major_2d(ctx, min_cells):

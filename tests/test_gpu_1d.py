@@ -242,3 +242,24 @@ def test_negative_depth_reported_not_faulted(nswe, ctx):
     R = torch.zeros((2, 200), dtype=torch.float64, device="cuda")
     nswe.nswe_residual(ctx, prob, 0, dev(np.stack([np.full(200, 2.0), np.full(200, 4.42)])), R)
     assert np.isfinite(host(R)).all()
+
+
+def test_batched_geometry_upload_equals_single(nswe, ctx):
+    """nswe_prob_set_geometry_batch_1d leaves every problem as the single
+    upload does (the same solve, bit for bit); invalid data in one problem
+    refuses the whole batch before any upload."""
+    inps = [I.channel_small(k) for k in range(4)]
+    prm = nswe.params_from(I.Params1D.for_problem(inps[0], tol=1e-10, n_max=500))
+    probs = [nswe.Problem1D.from_inputs(ctx, I.channel_small(9)) for _ in inps]  # other geometry first
+    nswe.nswe_prob_set_geometry_batch_1d(ctx, probs, [p.sig_face for p in inps], [p.gq_all() for p in inps],
+                                         [p.bcl for p in inps], [p.bcr for p in inps])
+    for p, pr in zip(inps, probs):
+        U = torch.zeros((2, p.N), dtype=torch.float64, device="cuda")
+        info = nswe.nswe_newton_solve(ctx, pr, dev(p.U0_start), U, prm)
+        Uref, iref = _solve_gpu(nswe, ctx, p, I.Params1D.for_problem(inps[0], tol=1e-10, n_max=500))
+        assert info["status"] == 0 and np.array_equal(host(U), Uref)
+    bad = [p.gq_all().copy() for p in inps]
+    bad[2][5] = float("nan")
+    with pytest.raises(nswe.NsweError):
+        nswe.nswe_prob_set_geometry_batch_1d(ctx, probs, [p.sig_face for p in inps], bad,
+                                             [p.bcl for p in inps], [p.bcr for p in inps])
