@@ -52,7 +52,7 @@ class Grid1D(ctypes.Structure):
         ("gq", ctypes.POINTER(ctypes.c_double)),
         ("bcl_kind", ctypes.c_int), ("bcr_kind", ctypes.c_int),
         ("bcl_h", ctypes.c_double), ("bcl_q", ctypes.c_double),
-        ("bcr_h", ctypes.c_double), ("bcr_q", ctypes.c_double),
+        ("bcr_h", ctypes.c_double), ("bcr_q", ctypes.c_double), ("flux", ctypes.c_int),
     ]
 
 
@@ -112,6 +112,7 @@ def _lib_handle():
                 "or_weno3": (None, [dbl, dbl, dbl, _D, _D]),
                 "or_flux1d": (None, [dbl, dbl, dbl, dbl, _D]),
                 "or_hll1d": (None, [dbl, dbl, dbl, dbl, dbl, dbl, _D]),
+                "or_llf1d": (None, [dbl, dbl, dbl, dbl, dbl, dbl, _D]),
                 "or_cubic4": (dbl, [_D, dbl]),
                 "or_residual_cell1d": (None, [P(Grid1D), _D, _D, i32, _D]),
                 "or_residual1d": (dbl, [P(Grid1D), _D, _D, _D]),
@@ -181,14 +182,15 @@ class Problem1D:
     two Gauss points x_j -+ dx/(2 sqrt 3)); bc = (kind, h, q) per side.
     """
 
-    def __init__(self, N, x0, x1, g, sig_face, gq, bcl, bcr):
+    def __init__(self, N, x0, x1, g, sig_face, gq, bcl, bcr, flux=0):
         self.sig_face = _f64(sig_face).reshape(-1)
         self.gq = _f64(gq).reshape(-1)
         assert self.sig_face.size == N + 1 and self.gq.size == 6 * N
         self.N = int(N)
         self.s = Grid1D(int(N), float(x0), float(x1), (float(x1) - float(x0)) / N, float(g),
                         ptr(self.sig_face), ptr(self.gq),
-                        int(bcl[0]), int(bcr[0]), float(bcl[1]), float(bcl[2]), float(bcr[1]), float(bcr[2]))
+                        int(bcl[0]), int(bcr[0]), float(bcl[1]), float(bcl[2]), float(bcr[1]), float(bcr[2]),
+                        int(flux))
 
     def ref(self):
         return ctypes.byref(self.s)
@@ -203,6 +205,12 @@ def weno3(a, b, c):
 def hll1d(HL, QL, HR, QR, sig, g):
     F = np.zeros(2)
     lib().or_hll1d(HL, QL, HR, QR, sig, g, ptr(F))
+    return F
+
+
+def llf1d(HL, QL, HR, QR, sig, g):
+    F = np.zeros(2)
+    lib().or_llf1d(HL, QL, HR, QR, sig, g, ptr(F))
     return F
 
 
@@ -363,8 +371,8 @@ def newton1d(prob: Problem1D, U_init, nlev, eps, params: Params1D):
 
 def problem_levels(inp):
     """Oracle grids for every nested level of an inputs.Problem1DInputs."""
-    return [Problem1D(inp.N_level(l), inp.x0, inp.x1, inp.g, inp.sig_face_level(l), inp.gq[l], inp.bcl, inp.bcr)
-            for l in range(inp.levels)]
+    return [Problem1D(inp.N_level(l), inp.x0, inp.x1, inp.g, inp.sig_face_level(l), inp.gq[l], inp.bcl, inp.bcr,
+                      getattr(inp, "flux", 0)) for l in range(inp.levels)]
 
 
 def params_from(prm):

@@ -34,6 +34,7 @@ typedef struct {
   const double *gq;       /* [3][2][N]: sigma, sigma_x, b_x at the 2 Gauss pts */
   int bcl_kind, bcr_kind;
   double bcl_h, bcl_q, bcr_h, bcr_q;
+  int flux; /* numerical flux: 0 HLL (the paper's 1D choice), 1 LLF        */
 } or_grid1d;
 
 #endif

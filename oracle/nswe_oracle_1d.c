@@ -107,6 +107,21 @@ void or_hll1d(double HL, double QL, double HR, double QR, double sig, double g,
   }
 }
 
+/* LLF (Rusanov) numerical flux at a face of width sig (Section 3.1 names it
+ * beside HLL): the mean of the two physical fluxes minus a (U_R - U_L) / 2,
+ * with a the larger |u| + c of the two states, c = sqrt(g*h). */
+void or_llf1d(double HL, double QL, double HR, double QR, double sig, double g,
+              double F[2]) {
+  double FL[2], FR[2];
+  or_flux1d(HL, QL, sig, g, FL);
+  or_flux1d(HR, QR, sig, g, FR);
+  double uL = QL / HL, uR = QR / HR;
+  double cL = sqrt(g * (HL / sig)), cR = sqrt(g * (HR / sig));
+  double a = fmax(fabs(uL) + cL, fabs(uR) + cR);
+  F[0] = 0.5 * (FL[0] + FR[0]) - 0.5 * a * (HR - HL);
+  F[1] = 0.5 * (FL[1] + FR[1]) - 0.5 * a * (QR - QL);
+}
+
 /* Value at t (in units of dx from the cell centre) of the cubic through
  * (t_k, p_k), t_k = -3/2, -1/2, 1/2, 3/2, in Lagrange form (Eq. 9). */
 double or_cubic4(const double p[4], double t) {
@@ -140,9 +155,10 @@ void or_residual_cell1d(const or_grid1d *g, const double *H, const double *Q,
   }
   double Fr[2], Fl[2];
   /* face j+1/2 (face index j+1): left state from cell j, right from cell j+1 */
-  or_hll1d(umH[1], umQ[1], upH[2], upQ[2], g->sig_face[j + 1], g->g, Fr);
+  void (*flux)(double, double, double, double, double, double, double *) = g->flux == 1 ? or_llf1d : or_hll1d;
+  flux(umH[1], umQ[1], upH[2], upQ[2], g->sig_face[j + 1], g->g, Fr);
   /* face j-1/2 (face index j): left state from cell j-1, right from cell j */
-  or_hll1d(umH[0], umQ[0], upH[1], upQ[1], g->sig_face[j], g->g, Fl);
+  flux(umH[0], umQ[0], upH[1], upQ[1], g->sig_face[j], g->g, Fl);
   /* source: cubic through the four interface values of H */
   double pts[4] = {upH[0], upH[1], umH[1], umH[2]};
   int N = g->N;

@@ -131,6 +131,7 @@ class Problem1DInputs:
     b_fn: Callable = field(repr=False, default=None)
     sig_fn: Callable = field(repr=False, default=None)
     meta: dict = field(default_factory=dict)
+    flux: int = 0                   # numerical flux: 0 HLL (the paper's 1D choice), 1 LLF
 
     def N_level(self, l):
         return self.N >> l

@@ -613,3 +613,51 @@ def test_transcritical_flow_matches_the_exact_solution(orc, width):
     assert np.abs(h - he)[m].max() < 1e-2
     # constant discharge to discretisation accuracy
     assert np.abs(U[1] - 1.53)[m].max() < 2e-2
+
+
+# ---------------------------------------------------------------- LLF flux in 1D (a comparison of Section 5)
+
+def test_llf_is_hll_for_states_at_rest_and_consistent(orc):
+    """For states at rest the HLL wave speeds are -a and a with a = max(c_L,
+    c_R), and HLL reduces to the LLF flux with that speed: the two
+    implementations agree there; LLF(U, U) is the physical flux."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        HL, HR, s = rng.uniform(0.3, 3.0), rng.uniform(0.3, 3.0), rng.uniform(0.5, 2.0)
+        a, b = orc.llf1d(HL, 0.0, HR, 0.0, s, 9.81), orc.hll1d(HL, 0.0, HR, 0.0, s, 9.81)
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+        H, Q = rng.uniform(0.3, 3.0), rng.uniform(-4.0, 4.0)
+        assert np.array_equal(orc.llf1d(H, Q, H, Q, s, 9.81), orc.flux1d(H, Q, s, 9.81))
+    # a supercritical pair: HLL is the upwind flux, LLF adds dissipation
+    F_hll, F_llf = orc.hll1d(1.0, 8.0, 1.2, 8.0, 1.0, 9.81), orc.llf1d(1.0, 8.0, 1.2, 8.0, 1.0, 9.81)
+    assert np.array_equal(F_hll, orc.flux1d(1.0, 8.0, 1.0, 9.81)) and not np.allclose(F_hll, F_llf)
+
+
+@pytest.mark.parametrize("bc", [I.BC_STATE, I.BC_EXTRAP])
+def test_uniform_state_has_zero_residual_llf(orc, bc):
+    for h, q, s in [(2.0, 4.42, 1.0), (0.8, -1.3, 1.7)]:
+        p = I.uniform_flow(40, 1, h, q, sigma=s, bc=bc)
+        p.flux = 1
+        pr = orc.problem_levels(p)[0]
+        R, _ = orc.residual1d(pr, np.stack([np.full(40, s * h), np.full(40, q)]))
+        assert np.abs(R).max() <= 1e-14 * abs(orc.flux1d(s * h, q, s, p.g)).max()
+
+
+def test_smooth_subcritical_llf_third_order_and_more_dissipative(orc):
+    """Section 5.1.1 with the LLF flux: third order on the finer grids, larger
+    errors than HLL on every grid and more Newton steps on the finest, the
+    paper's reason for HLL in 1D."""
+    g = I.G_PAPER
+    err, its = {0: [], 1: []}, {0: [], 1: []}
+    for flux in (0, 1):
+        for lev, N in enumerate([96, 192, 384, 768]):
+            p = I.paper_smooth_subcritical(N, levels=lev + 1)
+            p.flux = flux
+            U, info = orc.solve_problem(p, I.Params1D.for_problem(p))
+            assert info["status"] == 0 and info["res"][0] < 1e-11
+            err[flux].append(np.abs(U[0] - _cell_avg(lambda x: 1.0 / _u_exact_eq27(x, g), -10, 10, N)).mean())
+            its[flux].append(info["iters"][0])
+    orders = [math.log2(err[1][i] / err[1][i + 1]) for i in range(3)]
+    assert orders[-1] > 2.8 and min(orders) > 2.0, orders
+    assert all(e1 > e0 for e0, e1 in zip(err[0], err[1])), err
+    assert its[1][-1] > its[0][-1], its
