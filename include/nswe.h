@@ -210,6 +210,16 @@ nswe_status nswe_prob_set_geometry_1d(nswe_ctx ctx, nswe_prob prob,
                                       const nswe_bc1d *left,
                                       const nswe_bc1d *right);
 
+/* Numerical flux of a 1D problem's residual (Section 3.1 names both): HLL,
+ * the paper's choice in 1D and the default, or LLF (the mean of the two
+ * physical fluxes minus a (U_R - U_L) / 2, a the larger |u| + c), kept for
+ * comparison. Applies to every later call on the problem; EINVAL for a 2D
+ * problem or another value. The problems of one batched solve share a flux
+ * (NSWE_EINVAL otherwise); LLF batches run in the default launch shape. */
+#define NSWE_FLUX_HLL 0
+#define NSWE_FLUX_LLF 1
+nswe_status nswe_prob_set_flux_1d(nswe_ctx ctx, nswe_prob prob, int flux);
+
 /* The same for `count` distinct 1D problems (HOST arrays of count entries
  * each): the packing and checks run in parallel on host threads, and no
  * upload starts unless every problem's data is valid. */

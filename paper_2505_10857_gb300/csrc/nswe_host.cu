@@ -742,6 +742,17 @@ nswe_status nswe_prob_set_geometry_1d(nswe_ctx ctx, nswe_prob prob, const double
   return upload_geometry(prob, sigma_face, gauss_geom, left, right);
 }
 
+nswe_status nswe_prob_set_flux_1d(nswe_ctx ctx, nswe_prob prob, int flux) {
+  if (!ctx || !prob || prob->ctx != ctx || prob->dim != 1 || (flux != NSWE_FLUX_HLL && flux != NSWE_FLUX_LLF))
+    return NSWE_EINVAL;
+  DeviceGuard dg(ctx->device);
+  prob->host.flux = flux;
+  return cudaMemcpyAsync(prob->dev, &prob->host, sizeof(ProbDev), cudaMemcpyHostToDevice, ctx->stream) ==
+                 cudaSuccess
+             ? NSWE_OK
+             : NSWE_ECUDA;
+}
+
 nswe_status nswe_prob_set_geometry_batch_1d(nswe_ctx ctx, int count, const nswe_prob *probs,
                                             const double *const *sigma_faces, const double *const *gauss_geoms,
                                             const nswe_bc1d *lefts, const nswe_bc1d *rights) {
@@ -1045,8 +1056,9 @@ static nswe_status solve_batch_common(nswe_ctx ctx, int count, const nswe_prob *
     int s0 = (q->nest_start >= 0 && q->nest_start < p->levels) ? q->nest_start : p->levels - 1;
     nswe_status st = check_params(q, p, s0);
     if (st != NSWE_OK) return st;
-    // one 1D launch computes in one arithmetic type
+    // one 1D launch computes in one arithmetic type, with one numerical flux
     if (q->precision != params[0].precision) return NSWE_EINVAL;
+    if (p->dim == 1 && p->host.flux != probs[0]->host.flux) return NSWE_EINVAL;
     if ((q->jacobian & ~NSWE_JAC_FROZEN) == NSWE_JAC_FULL) nb = 5;
   }
   DeviceGuard dg(ctx->device);
@@ -1078,7 +1090,8 @@ static nswe_status solve_batch_common(nswe_ctx ctx, int count, const nswe_prob *
       cudaSuccess)
     return NSWE_ECUDA;
   const int shape = ctx->solve_shape[params->precision == NSWE_PREC_MIXED ? 1 : 0];
-  if (launch_solve_sized(ctx->tasks, count, *params, max_coarse, nb, shape, s) != cudaSuccess) return NSWE_ECUDA;
+  if (launch_solve_sized(ctx->tasks, count, *params, max_coarse, nb, shape, s, probs[0]->host.flux) != cudaSuccess)
+    return NSWE_ECUDA;
   if (infos) {
     if (cudaMemcpyAsync(infos, ctx->infos, sizeof(nswe_info) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return NSWE_ECUDA;

@@ -43,6 +43,7 @@ struct ProbDev {
   double g;
   int bl, br;        // boundary kinds (nswe_bc_kind)
   double blh, blq, brh, brq;
+  int flux;          // numerical flux: NSWE_FLUX_HLL (0) or NSWE_FLUX_LLF
   double *jw;        // Jacobian workspace: 16*(N+2) + 18*(N+1) doubles, finest N
   LevelDev lev[NSWE_MAX_LEVELS];
 };
@@ -191,8 +192,10 @@ cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &p
 // The same with the coarsest band sized for max_nb (3 or 5) whatever prm
 // says (for batches whose tasks carry their own parameters), in launch shape
 // `shape` (0 .. kSolveShapes-1).
+// flux: the numerical flux of every task (NSWE_FLUX_HLL, or NSWE_FLUX_LLF,
+// which runs in the default shape).
 cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
-                               int max_nb, int shape, cudaStream_t s);
+                               int max_nb, int shape, cudaStream_t s, int flux = NSWE_FLUX_HLL);
 // Parameter checks shared by the entry points (eps of levels 0..first_level).
 nswe_status check_params_1d(const nswe_params *p, int levels, int first_level);
 // Parameter checks of a 2D solve (the frozen linearisation allowed).

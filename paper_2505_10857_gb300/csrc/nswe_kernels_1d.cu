@@ -37,6 +37,7 @@ struct Geo {
   const double *igq;  // [2][N] 1/sigma at the Gauss points
   int bl, br;
   double blh, blq, brh, brq;
+  int flux;  // NSWE_FLUX_HLL or NSWE_FLUX_LLF
 };
 
 __device__ __forceinline__ Geo make_geo(const ProbDev &P, int l) {
@@ -55,6 +56,7 @@ __device__ __forceinline__ Geo make_geo(const ProbDev &P, int l) {
   G.blq = P.blq;
   G.brh = P.brh;
   G.brq = P.brq;
+  G.flux = P.flux;
   return G;
 }
 
@@ -140,6 +142,21 @@ __device__ __forceinline__ void hll_states(const FState<T> &L, const FState<T> &
   }
 }
 
+// Numerical flux of two interface states: HLL, or LLF: the mean of the
+// physical fluxes minus a (U_R - U_L) / 2, a = max(|u_L| + c_L, |u_R| + c_R).
+// FLUX fixes the choice at compile time (NSWE_FLUX_HLL or NSWE_FLUX_LLF),
+// or -1 takes it from `flux` (the standalone kernels).
+template <int FLUX, typename T>
+__device__ __forceinline__ void num_flux(const FState<T> &L, const FState<T> &R, int flux, T &F0, T &F1) {
+  if (FLUX == NSWE_FLUX_LLF || (FLUX < 0 && flux == NSWE_FLUX_LLF)) {
+    const T a = fmax(fabs(L.u) + L.c, fabs(R.u) + R.c);
+    F0 = T(0.5) * (L.Q + R.Q) - T(0.5) * a * (R.H - L.H);
+    F1 = T(0.5) * (L.F1 + R.F1) - T(0.5) * a * (R.Q - L.Q);
+  } else {
+    hll_states(L, R, F0, F1);
+  }
+}
+
 // Five-cell window j-2..j+2 of one residual evaluation.
 struct Win {
   double H[5], Q[5];
@@ -212,10 +229,10 @@ __device__ __forceinline__ void local_residual(const Geo &G, int j, const Win &w
     weno3(w.Q[p], w.Q[p + 1], w.Q[p + 2], upQ[p], umQ[p]);
   }
   double Fr0, Fr1, Fl0, Fl1;
-  hll_states(fstate(umH[1], umQ[1], G.isf[j + 1], G.cgf[j + 1], G.g),
-             fstate(upH[2], upQ[2], G.isf[j + 1], G.cgf[j + 1], G.g), Fr0, Fr1);
-  hll_states(fstate(umH[0], umQ[0], G.isf[j], G.cgf[j], G.g), fstate(upH[1], upQ[1], G.isf[j], G.cgf[j], G.g),
-             Fl0, Fl1);
+  num_flux<-1>(fstate(umH[1], umQ[1], G.isf[j + 1], G.cgf[j + 1], G.g),
+               fstate(upH[2], upQ[2], G.isf[j + 1], G.cgf[j + 1], G.g), G.flux, Fr0, Fr1);
+  num_flux<-1>(fstate(umH[0], umQ[0], G.isf[j], G.cgf[j], G.g), fstate(upH[1], upQ[1], G.isf[j], G.cgf[j], G.g),
+               G.flux, Fl0, Fl1);
   double S = source_at(G, j, upH[0], upH[1], umH[1], umH[2]);
   R0 = Fr0 - Fl0;
   R1 = Fr1 - Fl1 - S;
@@ -344,7 +361,7 @@ __device__ __forceinline__ int rec_variant(int i, int kk) {
 // (perturbed for p = 0, 1, 2), the right state from cell f (p = 1, 2, 3);
 // the per-state HLL quantities of the base states serve all variants that do
 // not perturb that side.
-template <typename T>
+template <typename T, int FLUX>
 __device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) {
   const int N = G.N;
   const T g = T(G.g);
@@ -353,7 +370,7 @@ __device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) 
     const FState<T> Lb = fstate<T>(W.r(0, 0, 1, f - 1), W.r(1, 0, 1, f - 1), isg, cg, g);
     const FState<T> Rb = fstate<T>(W.r(0, 0, 0, f), W.r(1, 0, 0, f), isg, cg, g);
     T F0, F1;
-    hll_states(Lb, Rb, F0, F1);
+    num_flux<FLUX>(Lb, Rb, G.flux, F0, F1);
     W.f(0, 0, f) = F0;
     W.f(0, 1, f) = F1;
 #pragma unroll
@@ -366,7 +383,7 @@ __device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) 
         if (p <= 2)
           Ls = fstate<T>(W.r(0, m == 0 ? p + 1 : 0, 1, f - 1), W.r(1, m == 1 ? p + 1 : 0, 1, f - 1), isg, cg, g);
         if (p >= 1) Rs = fstate<T>(W.r(0, m == 0 ? p : 0, 0, f), W.r(1, m == 1 ? p : 0, 0, f), isg, cg, g);
-        hll_states(Ls, Rs, F0, F1);
+        num_flux<FLUX>(Ls, Rs, G.flux, F0, F1);
         const int w = 1 + 2 * p + m;
         W.f(w, 0, f) = F0;
         W.f(w, 1, f) = F1;
@@ -468,11 +485,12 @@ __device__ void res_pass_a(const Geo &G, const double *U, const RW &W, int first
   }
 }
 
+template <int FLUX>
 __device__ void res_pass_b(const Geo &G, const RW &W, int first, int stride) {
   for (int f = first; f <= G.N; f += stride) {
     double F0, F1;
-    hll_states(fstate(W.r(0, 1, f - 1), W.r(1, 1, f - 1), G.isf[f], G.cgf[f], G.g),
-               fstate(W.r(0, 0, f), W.r(1, 0, f), G.isf[f], G.cgf[f], G.g), F0, F1);
+    num_flux<FLUX>(fstate(W.r(0, 1, f - 1), W.r(1, 1, f - 1), G.isf[f], G.cgf[f], G.g),
+                   fstate(W.r(0, 0, f), W.r(1, 0, f), G.isf[f], G.cgf[f], G.g), G.flux, F0, F1);
     W.f(0, f) = F0;
     W.f(1, f) = F1;
   }
@@ -1104,7 +1122,7 @@ __global__ void __launch_bounds__(kThreads) k_jac_a(const ProbDev *P, int level,
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jac_b(const ProbDev *P, int level) {
   Geo G = make_geo(*P, level);
-  jac_pass_b<T>(G, jw_view<T>(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  jac_pass_b<T, -1>(G, jw_view<T>(P->jw, G.N), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 template <typename T>
@@ -1135,7 +1153,9 @@ __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level
 // whole step is FP64; with T = float the residual, the convergence test and
 // the update U += tau dU stay FP64 while the FD Jacobian (Eq. 12-13), the
 // coarse operators, the smoother and the coarsest LU run in FP32.
-template <typename T, int THREADS, int MINB>
+// FLUX: the numerical flux of every task of the launch (compile-time, so
+// that the HLL kernels carry no LLF code).
+template <typename T, int THREADS, int MINB, int FLUX>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_solve(const SolveTask *tasks, nswe_params launch_prm, int n_cap, int ldab_cap) {
   constexpr bool kMixed = std::is_same<T, float>::value;
@@ -1191,13 +1211,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
         const RW RWv = rw_view(P.jw, N);
         res_pass_a(G, Lv.U, RWv, threadIdx.x, blockDim.x);
         __syncthreads();
-        res_pass_b(G, RWv, threadIdx.x, blockDim.x);
+        res_pass_b<FLUX>(G, RWv, threadIdx.x, blockDim.x);
         __syncthreads();
         acc = res_pass_c(G, RWv, Lv.R, threadIdx.x, blockDim.x);
       } else {
         jac_pass_a<T>(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
         __syncthreads();
-        jac_pass_b<T>(G, W, threadIdx.x, blockDim.x);
+        jac_pass_b<T, FLUX>(G, W, threadIdx.x, blockDim.x);
         __syncthreads();
         acc = jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, nullptr, Lv.R, J, threadIdx.x, blockDim.x);
       }
@@ -1210,7 +1230,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         // FP32 Jacobian at the current state, regularised with the FP64 R.
         jac_pass_a<T>(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
         __syncthreads();
-        jac_pass_b<T>(G, W, threadIdx.x, blockDim.x);
+        jac_pass_b<T, FLUX>(G, W, threadIdx.x, blockDim.x);
         __syncthreads();
         jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, Lv.R, nullptr, J, threadIdx.x, blockDim.x);
         for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) Rs[t] = T(Lv.R[t]);
@@ -1367,19 +1387,25 @@ cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &p
 }
 
 namespace {
-template <int SHAPE>
+template <int SHAPE, int FLUX = NSWE_FLUX_HLL>
 void launch_shape(const SolveTask *tasks, int count, const nswe_params &prm, int n_cap, int ldab_cap, size_t smem,
                   cudaStream_t s) {
   constexpr int TH = kSolveShapeThreads[SHAPE], MB = kSolveShapeBlocks[SHAPE];
-  if (prm.precision == NSWE_PREC_MIXED) k_solve<float, TH, MB><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
-  else k_solve<double, TH, MB><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+  if (prm.precision == NSWE_PREC_MIXED)
+    k_solve<float, TH, MB, FLUX><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+  else
+    k_solve<double, TH, MB, FLUX><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
 }
 }  // namespace
 
 cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
-                               int max_nb, int shape, cudaStream_t s) {
+                               int max_nb, int shape, cudaStream_t s, int flux) {
   const int n_cap = 2 * max_coarse_cells, ldab_cap = 3 * (max_nb == 5 ? 5 : 3) + 1;
   const size_t smem = band_smem_bytes(n_cap, ldab_cap);
+  if (flux == NSWE_FLUX_LLF) {  // a comparison option: the default shape only
+    launch_shape<0, NSWE_FLUX_LLF>(tasks, count, prm, n_cap, ldab_cap, smem, s);
+    return cudaGetLastError();
+  }
   switch (shape) {
   case 1: launch_shape<1>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   case 2: launch_shape<2>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;

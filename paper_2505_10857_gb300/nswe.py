@@ -20,7 +20,8 @@ from . import build as _build
 
 MAX_LEVELS = 16
 JAC_SIMPLIFIED, JAC_FULL = 3, 5
-JAC_FROZEN = 0x100  # 2D: OR'd into the Jacobian choice, the frozen linearisation
+JAC_FROZEN = 0x100
+FLUX_HLL, FLUX_LLF = 0, 1  # 2D: OR'd into the Jacobian choice, the frozen linearisation
 PREC_FP64, PREC_MIXED = 0, 1
 BC_DISCHARGE, BC_DEPTH, BC_STATE, BC_EXTRAP = 1, 2, 3, 4
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENAN", 6: "ENEGDEPTH",
@@ -109,6 +110,7 @@ EXPORTS = {
     "nswe_jacobian_f32": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_jacobian_frozen": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_ctx_set_colour_major_2d": (_i, [_vp, _i]),
+    "nswe_prob_set_flux_1d": (_i, [_vp, _vp, _i]),
     "nswe_prob_set_geometry_batch_1d": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                              ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
     "nswe_mg_vcycle_f32": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
@@ -267,7 +269,14 @@ class Problem1D:
 
     @staticmethod
     def from_inputs(ctx: Context, inp) -> "Problem1D":
-        return Problem1D(ctx, inp.N, inp.levels, inp.x0, inp.x1, inp.g, inp.sig_face, inp.gq_all(), inp.bcl, inp.bcr)
+        p = Problem1D(ctx, inp.N, inp.levels, inp.x0, inp.x1, inp.g, inp.sig_face, inp.gq_all(), inp.bcl, inp.bcr)
+        if getattr(inp, "flux", 0):
+            p.set_flux(inp.flux)
+        return p
+
+    def set_flux(self, flux):
+        """FLUX_HLL (the default) or FLUX_LLF."""
+        _check("nswe_prob_set_flux_1d", lib().nswe_prob_set_flux_1d(self.ctx.h, self.h, int(flux)))
 
     def set_geometry(self, sigma_face, gauss_geom_all, bcl, bcr):
         """Arrays must stay alive until the stream has consumed them."""

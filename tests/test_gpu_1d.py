@@ -263,3 +263,55 @@ def test_batched_geometry_upload_equals_single(nswe, ctx):
     with pytest.raises(nswe.NsweError):
         nswe.nswe_prob_set_geometry_batch_1d(ctx, probs, [p.sig_face for p in inps], bad,
                                              [p.bcl for p in inps], [p.bcr for p in inps])
+
+
+@pytest.mark.parametrize("name", ["small", "irregular"])
+def test_llf_residual_and_jacobian_parity(nswe, ctx, orc, name):
+    """The LLF flux (nswe_prob_set_flux_1d) against the oracle's: residual,
+    J3 and J5, on every level of two problems."""
+    inp = problems()[name]
+    inp.flux = 1  # LLF
+    try:
+        prob = nswe.Problem1D.from_inputs(ctx, inp)
+        for level in sorted({0, inp.levels - 1}):
+            pr = orc.problem_levels(inp)[level]
+            U = state_for(inp, level, 40 + level)
+            sc = flux_scale(U, inp.g)
+            Rref, _ = orc.residual1d(pr, U)
+            dR = torch.zeros((2, pr.N), dtype=torch.float64, device="cuda")
+            nswe.nswe_residual(ctx, prob, level, dev(U), dR)
+            assert np.abs(host(dR) - Rref).max() <= 1e-12 * sc
+            for nb in (3, 5):
+                eps = I.eps_for_n(pr.N)
+                Jref, _, _ = orc.jacobian1d(pr, U, eps, 3.0, nb)
+                dJ = torch.full((nb, 4, pr.N), float("nan"), dtype=torch.float64, device="cuda")
+                f = nswe.nswe_jacobian_simplified if nb == 3 else nswe.nswe_jacobian_full
+                f(ctx, prob, level, dev(U), eps, 3.0, dR, dJ)
+                assert np.abs(host(dJ) - Jref).max() <= jac_tol(Jref, sc, eps)
+        # HLL differs from LLF on these states
+        Rllf = host(dR)
+        prob.set_flux(nswe.FLUX_HLL)
+        nswe.nswe_residual(ctx, prob, inp.levels - 1, dev(U), dR)
+        assert not np.allclose(host(dR), Rllf)
+    finally:
+        inp.flux = 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_llf_solve_parity(nswe, ctx, orc, precision):
+    """Nested solve of Eq. 26 (192 cells) with the LLF flux against the
+    oracle's: FP64 to 1e-10, mixed precision within its bound."""
+    inp = I.paper_smooth_subcritical(192, 2)
+    inp.flux = 1
+    prm = I.Params1D.for_problem(inp, tol=1e-11, n_max=500)
+    Uref, iref = orc.solve_problem(inp, prm)
+    prob = nswe.Problem1D.from_inputs(ctx, inp)
+    p = nswe.params_from(prm)
+    p.precision = precision
+    U = torch.zeros((2, inp.N), dtype=torch.float64, device="cuda")
+    info = nswe.nswe_newton_solve(ctx, prob, dev(inp.U0_start), U, p)
+    assert info["status"] == 0 == iref["status"], (info, iref)
+    err = np.abs(host(U) - Uref).max() / np.abs(Uref).max()
+    assert err <= (1e-10 if precision == 0 else 1e-8), err
+    if precision == 0:
+        assert abs(info["iters"][0] - iref["iters"][0]) <= 2

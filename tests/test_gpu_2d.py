@@ -321,3 +321,25 @@ def test_colour_major_storage_gives_the_same_bits(nswe, ctx, case):
     assert ia["status"] == 0 == ib["status"], (ia, ib)
     assert ia["iters"] == ib["iters"]
     assert np.array_equal(Ua, Ub)
+
+
+def test_negative_depth_reported_not_faulted_2d(nswe, ctx):
+    """A guess with a negative depth ends the 2D solve with ENAN or
+    ENEGDEPTH (no fault); the same problem then solves a valid guess, alone
+    and in a concurrent batch with another problem."""
+    inp = I.paper_parabolic_bump(32, 16, 3)
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    prm = nswe.params2d_from(I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=50))
+    U0 = inp.U0_start.copy()
+    U0[0, 5] = -1.0
+    U = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
+    info = nswe.nswe_newton_solve(ctx, prob, dev(U0), U, prm)
+    assert info["status"] in (5, 6), info  # ENAN or ENEGDEPTH
+    good = nswe.params2d_from(I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400))
+    info = nswe.nswe_newton_solve(ctx, prob, dev(inp.U0_start), U, good)
+    assert info["status"] == 0
+    other = I.paper_parabolic_bump(16, 8, 2)
+    p2 = nswe.Problem2D.from_inputs(ctx, other)
+    U2 = torch.zeros((3, other.Nx * other.Ny), dtype=torch.float64, device="cuda")
+    infos = nswe.nswe_newton_solve_batch_each(ctx, [prob, p2], [dev(U0), dev(other.U0_start)], [U, U2], [prm, good])
+    assert infos[0]["status"] in (5, 6) and infos[1]["status"] == 0, infos
