@@ -43,7 +43,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM G
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_solve launch of the default step
 # (608 channel solves, J3, shape 256x4), from a one-pass ncu capture of `bench.py --steps 1 --warmup 3
 # --no-cpu --no-autotune [--precision mixed]`; summarised in profiles/k_solve_channel_n4096_ncu_full.md.
-TRAFFIC_608 = {"fp64": 186.17e9 + 104.77e9, "mixed": 99.28e9 + 64.18e9}
+TRAFFIC_608 = {"fp64": 186.38e9 + 104.80e9, "mixed": 99.28e9 + 64.18e9}
 
 
 def workload_config(batch, nb, precision="fp64"):
