@@ -1409,6 +1409,7 @@ cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_par
   switch (shape) {
   case 1: launch_shape<1>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   case 2: launch_shape<2>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
+  case 3: launch_shape<3>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   default: launch_shape<0>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   }
   return cudaGetLastError();
