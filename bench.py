@@ -41,9 +41,10 @@ MIXED_BOUND = 1e-8  # solution distance of two solves that both reach res < TOL 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x FP64 FMA/clk/SM x 2 flop x max SM GHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM GHz
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_solve launch of the default step
-# (608 channel solves, J3, shape 256x4), from a one-pass ncu capture of `bench.py --steps 1 --warmup 3
-# --no-cpu --no-autotune [--precision mixed]`; summarised in profiles/k_solve_channel_n4096_ncu_full.md.
-TRAFFIC_608 = {"fp64": 186.38e9 + 104.80e9, "mixed": 99.28e9 + 64.18e9}
+# (608 channel solves, J3) per precision and launch shape, each from a one-pass ncu capture of
+# `bench.py --steps 1 --warmup 3 --no-cpu --shape S [--precision mixed]`; no entry: not captured.
+TRAFFIC_608 = {("fp64", "256x4"): 186.38e9 + 104.80e9, ("fp64", "128x4"): 216.09e9 + 104.06e9,
+               ("mixed", "256x4"): 99.28e9 + 64.18e9}
 
 
 def workload_config(batch, nb, precision="fp64"):
@@ -328,11 +329,17 @@ def run_gpu(args, rank, world, local_rank):
 
     # Launch-shape autotuning on this batch (before the warm-up; not timed).
     tune = None
-    if not args.no_autotune:
+    shape = 0
+    if args.shape is not None:
+        shape = args.shape
+        nswe.nswe_ctx_set_solve_shape(ctx, prm.precision, shape)
+    elif not args.no_autotune:
         ms_shapes, best = nswe.nswe_autotune_solve_batch(ctx, probs, U0s, Us, prm, reps=1)
         tune = {"shapes": ["%dx%d" % tb for tb in nswe.solve_shapes()], "ms_per_batch": ms_shapes,
                 "chosen": "%dx%d" % nswe.solve_shapes()[best],
                 "what": "threads per block x resident blocks per SM of k_solve, one timed batch each"}
+        shape = best
+    shape_name = "%dx%d" % nswe.solve_shapes()[shape]
 
     def barrier():
         if world > 1:
@@ -452,10 +459,10 @@ def run_gpu(args, rank, world, local_rank):
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1000.0,
                          "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1000.0),
-                         "traffic": TRAFFIC_608[args.precision] if (B == 608 and nb == 3) else None,
+                         "traffic": TRAFFIC_608.get((args.precision, shape_name)) if (B == 608 and nb == 3) else None,
                          "traffic_note": "DRAM bytes per launch from one ncu capture of this workload; "
                                          "8-16 % of the HBM copy rate over the launch, far from bound",
-                         "kernel": "k_solve (persistent nested NMGM, one block per instance)",
+                         "kernel": f"k_solve (persistent nested NMGM, one block per instance, shape {shape_name})",
                          "flops_per_launch": flops, "fp64_flops": f64, "fp32_flops": f32, "launch_ms": launch_ms,
                          "peak_note": "FP64 derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"
                                       + ("; FP32 flops counted at FP64/FP32 peak ratio (FP32 peak 152 x 128 lanes x "
@@ -875,6 +882,7 @@ def main():
     ap.add_argument("--nb", type=int, default=3, choices=[3, 5], help="3: simplified J3, 5: full J5")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of k_solve")
+    ap.add_argument("--shape", type=int, default=None, help="launch shape index of k_solve (no autotuning)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d",
