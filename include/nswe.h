@@ -348,7 +348,7 @@ nswe_status nswe_newton_solve_batch(nswe_ctx ctx, int count,
  * arithmetic type: all records must then share `precision` (NSWE_EINVAL
  * otherwise), while J3 and J5 tasks, relaxation factors, smoothing counts,
  * tolerances and nested start levels may differ. In 2D each record may also
- * choose its own Jacobian (J9, J21, | NSWE_JAC_FROZEN). */
+ * choose its own Jacobian (J9, J21, | NSWE_JAC_FROZEN) and precision. */
 nswe_status nswe_newton_solve_batch_each(nswe_ctx ctx, int count,
                                          const nswe_prob *probs,
                                          const double *const *U0s,

@@ -1057,8 +1057,8 @@ static nswe_status solve_batch_common(nswe_ctx ctx, int count, const nswe_prob *
     nswe_status st = check_params(q, p, s0);
     if (st != NSWE_OK) return st;
     // one 1D launch computes in one arithmetic type, with one numerical flux
-    if (q->precision != params[0].precision) return NSWE_EINVAL;
-    if (p->dim == 1 && p->host.flux != probs[0]->host.flux) return NSWE_EINVAL;
+    if (p->dim == 1 && (q->precision != params[0].precision || p->host.flux != probs[0]->host.flux))
+      return NSWE_EINVAL;
     if ((q->jacobian & ~NSWE_JAC_FROZEN) == NSWE_JAC_FULL) nb = 5;
   }
   DeviceGuard dg(ctx->device);

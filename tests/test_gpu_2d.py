@@ -255,6 +255,7 @@ def test_2d_batch_with_parameters_per_problem(nswe, ctx):
             I.Params2D(levels=2, nu1=[15], nu2=[15], tol=1e-10, n_max=400, nest_start=1, omega=0.1, frozen=True),
             I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-10, n_max=400, st=1)]
     cp = [nswe.params2d_from(q) for q in prms]
+    cp[3].precision = nswe.PREC_MIXED  # precision per problem, too
     probs = [nswe.Problem2D.from_inputs(ctx, p) for p in inps]
     U0s = [dev(p.U0_start) for p in inps]
     alone = []
