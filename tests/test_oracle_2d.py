@@ -553,3 +553,34 @@ def test_seeded_wedges_reach_their_oblique_jump(orc, k):
     h = U[0].reshape(16, 32)
     assert abs(h[0, -3:].mean() / ratio - 1.0) < 2e-3, (h[0, -3:], ratio)
     assert np.abs(h[-4:, :3] - 1.0).max() < 1e-3  # the inflow corner is undisturbed
+
+
+def _block_split(orc, inp, U):
+    """Entrywise l1 norms of the J21 blocks of in-grid neighbours, split into
+    the nine kept by J9 (the cross) and the twelve it drops."""
+    pr = orc.problem_levels2d(inp)[0]
+    J, _, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, orc.ST_J21)
+    cross = {(0, -2), (0, -1), (-2, 0), (-1, 0), (0, 0), (1, 0), (2, 0), (0, 1), (0, 2)}
+    kept, dropped = [], []
+    for c in range(inp.Nx * inp.Ny):
+        i, j = c % inp.Nx, c // inp.Nx
+        for k, (dx, dy) in enumerate(orc.stencil2d(orc.ST_J21)):
+            if 0 <= i + dx < inp.Nx and 0 <= j + dy < inp.Ny:
+                (kept if (dx, dy) in cross else dropped).append(np.abs(J[k, :, c]).sum())
+    return np.array(kept), np.array(dropped)
+
+
+def test_j9_keeps_the_large_blocks(orc):
+    """Section 4.1: on the 16 x 8 grid of Section 5.2.1, at its initial state
+    (Eq. 30), every block J9 keeps has l1-norm above 0.5, every block it drops
+    is below 0.5, and most dropped blocks are below 1e-6 (the paper reports
+    83 %); for the wedge of Section 5.2.2 at Eq. 31 every kept block exceeds 1
+    (the paper: 100 %)."""
+    b = I.paper_parabolic_bump(16, 8, 2)
+    kept, dropped = _block_split(orc, b, np.stack([np.ones(128), np.ones(128), np.zeros(128)]))
+    assert kept.min() > 0.5 and dropped.max() < 0.5, (kept.min(), dropped.max())
+    assert (dropped < 1e-6).mean() > 0.8
+    w = I.wedge(16, 8, 1)
+    s = w.bc_state[0]
+    kept, _ = _block_split(orc, w, np.stack([np.full(128, s[0]), np.full(128, s[1]), np.full(128, s[2])]))
+    assert kept.min() > 1.0
