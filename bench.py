@@ -872,6 +872,52 @@ def run_serve2d(args):
         "clocks": clk}), flush=True)
 
 
+def run_jac1d(args):
+    """1D Jacobian cost (not the default line): the residual and the FD
+    Jacobians J3 and J5 (Eq. 12-13) of one seeded channel of 2^20 cells,
+    CUDA events on the launching stream, FP64 and FP32 storage. Section 3.3
+    expects J3 to cost about 40 % less than J5."""
+    import numpy as np
+    import torch
+
+    from paper_2505_10857_gb300 import inputs as I
+    from paper_2505_10857_gb300 import nswe
+
+    N, levels = 1 << 20, 14  # coarsest level 128 cells
+    inp = I.channel_small(0, N=N, levels=levels)
+    ctx = nswe.Context(0)
+    prob = nswe.Problem1D.from_inputs(ctx, inp)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(7)
+    xc = (np.arange(N) + 0.5) * 25.0 / N
+    U = torch.tensor(np.stack([2.0 - 0.1 * np.exp(-((xc - 10.0) / 1.5) ** 2) + 1e-3 * rng.standard_normal(N),
+                               np.full(N, 4.42)]), dtype=torch.float64, device="cuda")
+    R, res = torch.zeros_like(U), torch.zeros(1, dtype=torch.float64, device="cuda")
+    J5 = torch.zeros((5, 4, N), dtype=torch.float64, device="cuda")
+    J5f = torch.zeros((5, 4, N), dtype=torch.float32, device="cuda")
+    eps = 0.05
+
+    def timed(f, reps=20):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            f()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t = {"residual_ms": timed(lambda: nswe.nswe_residual(ctx, prob, 0, U, R, res)),
+         "jacobian_j3_ms": timed(lambda: nswe.nswe_jacobian_simplified(ctx, prob, 0, U, eps, 3.0, R, J5[:3], res)),
+         "jacobian_j5_ms": timed(lambda: nswe.nswe_jacobian_full(ctx, prob, 0, U, eps, 3.0, R, J5, res)),
+         "jacobian_j3_f32_ms": timed(lambda: nswe.nswe_jacobian_f32(ctx, prob, 0, 3, U, eps, 3.0, R, J5f[:3], res)),
+         "jacobian_j5_f32_ms": timed(lambda: nswe.nswe_jacobian_f32(ctx, prob, 0, 5, U, eps, 3.0, R, J5f, res))}
+    t["j3_saving_vs_j5"] = 1.0 - t["jacobian_j3_ms"] / t["jacobian_j5_ms"]
+    print(json.dumps({"metric": "1D residual and Jacobian times at 2^20 cells (ms)", "cells": N, "phases": t}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -886,7 +932,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d",
-                    choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d"])
+                    choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d", "jac1d"])
     ap.add_argument("--batch2d", type=int, default=16, help="batch2d: 2D problems per batch")
     ap.add_argument("--rate2d", type=float, default=1.0, help="serve2d: Poisson arrival rate (requests/s)")
     ap.add_argument("--family2d", choices=["mix", "wedge", "bump"], default="mix",
@@ -913,6 +959,11 @@ def main():
         from paper_2505_10857_gb300 import build
         build.build()
         run_batch2d(args)
+        return
+    if args.workload == "jac1d":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        run_jac1d(args)
         return
     if args.workload == "serve2d":
         from paper_2505_10857_gb300 import build
