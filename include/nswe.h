@@ -178,6 +178,13 @@ nswe_status nswe_ctx_set_stream(nswe_ctx ctx, void *stream);
  * (nswe_jacobian_*, nswe_mg_vcycle*) always use the cell-contiguous layout
  * they document. */
 nswe_status nswe_ctx_set_colour_major_2d(nswe_ctx ctx, int min_cells);
+/* Work split of the 2D FD Jacobian (Eq. 12; results are the same bits either
+ * way): on levels of at least min_cells cells one thread takes a cell and
+ * builds its unperturbed reconstruction lines once for all stencil blocks;
+ * on smaller levels one thread takes one (cell, block) item. min_cells < 0:
+ * never per cell. Default 32768. Applies to nested solves and to the
+ * standalone Jacobian calls of this context. */
+nswe_status nswe_ctx_set_jacobian_cells_2d(nswe_ctx ctx, int min_cells);
 nswe_status nswe_ctx_destroy(nswe_ctx ctx);
 
 /* One-dimensional problem (Eq. 3-4) on [x0, x1] with N cells and `levels`

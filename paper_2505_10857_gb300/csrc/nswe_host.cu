@@ -25,6 +25,7 @@ struct nswe_ctx_s {
   int cap;               // capacity of tasks / infos / prms
   int solve_shape[2];    // launch shape of the 1D solve kernel per precision
   int cm2d_min_cells = 131072;  // 2D Newton levels of at least this many cells store J9 colour-major
+  int jac2d_cell_min = kJac2CellMinDefault;  // 2D levels from which the per-cell Jacobian kernel runs
 };
 
 struct nswe_prob_s {
@@ -392,7 +393,8 @@ nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_pa
     T *const Rs = kMixed ? J + (size_t)K * 9 * blk_stride(cm, Lv.Nx, Lv.Ny) : reinterpret_cast<T *>(Lv.R);
     auto step = [&](cudaStream_t q) -> cudaError_t {
       cudaError_t e;
-      if ((e = launch2_jacobian<T>(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, J, frozen, cm, q)))
+      if ((e = launch2_jacobian<T>(p->dev2, l, n, st0, Lv.U, prm.eps[l], prm.alpha, Lv.R, J, frozen, cm,
+                                   p->ctx->jac2d_cell_min, q)))
         return e;
       if constexpr (kMixed) {
         if ((e = launch2_to_f32(3L * n, Lv.R, reinterpret_cast<float *>(Rs), q))) return e;
@@ -627,6 +629,12 @@ nswe_status nswe_ctx_create(nswe_ctx *out, int device, void *stream) {
 nswe_status nswe_ctx_set_colour_major_2d(nswe_ctx ctx, int min_cells) {
   if (!ctx) return NSWE_EINVAL;
   ctx->cm2d_min_cells = min_cells;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_set_jacobian_cells_2d(nswe_ctx ctx, int min_cells) {
+  if (!ctx) return NSWE_EINVAL;
+  ctx->jac2d_cell_min = min_cells;
   return NSWE_OK;
 }
 
@@ -959,7 +967,7 @@ static nswe_status jacobian_common(nswe_ctx ctx, nswe_prob prob, int level, int 
     const int n = nswe_prob_cells(prob, level);
     if (launch2_residual(prob->dev2, level, n, U, R, res, ctx->partials, ctx->stream) ||
         launch2_jacobian<double>(prob->dev2, level, n, nb == 5 ? ST_J21 : ST_J9, U, eps, alpha, R, J, frozen, 0,
-                                 ctx->stream))
+                                 ctx->jac2d_cell_min, ctx->stream))
       return NSWE_ECUDA;
     return NSWE_OK;
   }
@@ -996,7 +1004,7 @@ nswe_status nswe_jacobian_f32(nswe_ctx ctx, nswe_prob prob, int level, int nb, c
     const int n = nswe_prob_cells(prob, level);
     return (launch2_residual(prob->dev2, level, n, U, R, res_l1, ctx->partials, ctx->stream) ||
             launch2_jacobian<float>(prob->dev2, level, n, nb == 21 ? ST_J21 : ST_J9, U, eps, alpha, R, J, false, 0,
-                                    ctx->stream))
+                                    ctx->jac2d_cell_min, ctx->stream))
                ? NSWE_ECUDA
                : NSWE_OK;
   }

@@ -95,10 +95,13 @@ __host__ __device__ __forceinline__ size_t blk_pos(int cm, int Nx, int Ny, int i
 }
 
 // frozen: the frozen linearisation (weights and eigenvectors from U); cm:
-// the storage of J (blk_pos).
+// the storage of J (blk_pos); levels of at least cell_min cells (>= 0) take
+// the one-cell-per-thread kernel, the others one (cell, block) item per
+// thread (the same bits either way).
+constexpr int kJac2CellMinDefault = 32768;
 template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, TJ *J, bool frozen, int cm, cudaStream_t s);
+                             const double *R, TJ *J, bool frozen, int cm, int cell_min, cudaStream_t s);
 template <typename T>
 cudaError_t launch2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, int cm, cudaStream_t s);
 template <typename T>

@@ -259,8 +259,10 @@ __device__ __forceinline__ void line_values2(const Geo2 &G, const double *U, int
 // lines (transverse positions r0-1, r0, r0+1): the edge fluxes at the two
 // Gauss points of the faces a-1/2, a+1/2 (flux = right minus left) and the
 // source component 1 + dir, -(1/4) sum g h b_dir (S / (dx dy)).
-__device__ __forceinline__ void dir_part2(const Geo2 &G, int dir, int c, const double ifv[3][4][2][3],
-                                          double flux[3], double &S) {
+__device__ __forceinline__ void dir_part2(const Geo2 &G, int dir, int c, const double (*l0)[2][3],
+                                          const double (*l1)[2][3], const double (*l2)[2][3], double flux[3],
+                                          double &S) {
+  const double(*ifv[3])[2][3] = {l0, l1, l2};
   const int n = G.Nx * G.Ny;
   double fl[2][3] = {{0, 0, 0}, {0, 0, 0}};
   double hq[2][4];
@@ -315,7 +317,7 @@ __device__ void local_residual2(const Geo2 &G, const double *U, int i, int j, co
     double ifv[3][4][2][3];
 #pragma unroll 1
     for (int t = 0; t < 3; ++t) line_values2<FROZEN>(G, U, dir, a, r0 - 1 + t, p, ifv[t]);
-    dir_part2(G, dir, c, ifv, flux[dir], S[1 + dir]);
+    dir_part2(G, dir, c, ifv[0], ifv[1], ifv[2], flux[dir], S[1 + dir]);
   }
 #pragma unroll
   for (int m = 0; m < 3; ++m) R[m] = flux[0][m] / G.dx + flux[1][m] / G.dy - S[m];
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
       }
       if (!reads) {
         double f[3], sv;
-        dir_part2(G, dir, c, ifv, f, sv);
+        dir_part2(G, dir, c, ifv[0], ifv[1], ifv[2], f, sv);
 #pragma unroll
         for (int m = 0; m < 3; ++m) {  // the same for every m (m0..m1-1 are read)
           fd[dir][m][0] = f[0];
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
 #pragma unroll 1
         for (int t = 0; t < 3; ++t)
           if (reads & (1 << t)) line_values2<FROZEN>(G, U, dir, a, r0 - 1 + t, p, ifv[t]);
-        dir_part2(G, dir, c, ifv, fd[dir][m], sd[dir][m]);
+        dir_part2(G, dir, c, ifv[0], ifv[1], ifv[2], fd[dir][m], sd[dir][m]);
       }
     }
     for (int m = m0; m < m1; ++m) {
@@ -988,9 +990,105 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
   return cudaGetLastError();
 }
 
+// The same Jacobian with one cell per thread (large grids): the six
+// unperturbed reconstruction lines of the cell and its two direction parts
+// are built once and serve all blocks and components; each perturbation
+// rebuilds only the lines that read the perturbed cell (for J9, 60 line
+// reconstructions per cell against 90 when each (cell, block) item builds
+// its own). The same expressions on the same inputs as k2_jacobian, so the
+// same bits. The lines live in local memory (about 1.9 KB a thread), which
+// costs less than the saved FP64 work from about 32,768 cells on; below
+// that the per-item kernel's nine- or 27-fold parallelism wins
+// (kJac2CellMinDefault).
+constexpr int kJacCellThreads = 128;
+template <typename TJ, bool FROZEN>
+__global__ void __launch_bounds__(kJacCellThreads) k2_jacobian_cell(const ProbDev2 *P, int level, int st,
+                                                                  const double *U, double eps, double alpha,
+                                                                  const double *R, TJ *J, int cm) {
+  const Geo2 G = make_geo2(*P, level);
+  const int n = G.Nx * G.Ny, K = st_size(st), kc = st_center(st);
+  const double ieps = 1.0 / eps;
+  const Pert none{-1, 0, 0.0};
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const int i = c % G.Nx, j = c / G.Nx;
+    const size_t S = blk_stride(cm, G.Nx, G.Ny), pc = blk_pos(cm, G.Nx, G.Ny, i, j);
+    const double R0[3] = {R[c], R[n + c], R[2 * n + c]};
+    double base[2][3][4][2][3], fb[2][3], sb[2];
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      const int a = dir == 0 ? i : j, r0 = dir == 0 ? j : i;
+#pragma unroll 1
+      for (int t = 0; t < 3; ++t) line_values2<FROZEN>(G, U, dir, a, r0 - 1 + t, none, base[dir][t]);
+      dir_part2(G, dir, c, base[dir][0], base[dir][1], base[dir][2], fb[dir], sb[dir]);
+    }
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+      const int pi = i + st_off(st, k, 0), pj = j + st_off(st, k, 1);
+      if (pi < 0 || pi >= G.Nx || pj < 0 || pj >= G.Ny) {
+        for (int e = 0; e < 9; ++e) J[(size_t)(k * 9 + e) * S + pc] = TJ(0.0);
+        continue;
+      }
+      const int cp = pj * G.Nx + pi;
+      const double reg = (k == kc) ? alpha * (fabs(R0[0]) + fabs(R0[1]) + fabs(R0[2])) : 0.0;
+      int reads[2];
+#pragma unroll 1
+      for (int dir = 0; dir < 2; ++dir) {
+        const int a = dir == 0 ? i : j, r0 = dir == 0 ? j : i;
+        reads[dir] = 0;
+        for (int t = 0; t < 3; ++t)
+          if (line_reads(G, dir, a, r0 - 1 + t, cp)) reads[dir] |= 1 << t;
+      }
+#pragma unroll 1
+      for (int m = 0; m < 3; ++m) {
+        const Pert p{cp, m, eps};
+        double fd[2][3], sdv[2];
+#pragma unroll 1
+        for (int dir = 0; dir < 2; ++dir) {
+          if (!reads[dir]) {
+            fd[dir][0] = fb[dir][0];
+            fd[dir][1] = fb[dir][1];
+            fd[dir][2] = fb[dir][2];
+            sdv[dir] = sb[dir];
+            continue;
+          }
+          const int a = dir == 0 ? i : j, r0 = dir == 0 ? j : i;
+          double tmp[3][4][2][3];
+          const double(*l[3])[2][3];
+#pragma unroll 1
+          for (int t = 0; t < 3; ++t) {
+            if (reads[dir] & (1 << t)) {
+              line_values2<FROZEN>(G, U, dir, a, r0 - 1 + t, p, tmp[t]);
+              l[t] = tmp[t];
+            } else {
+              l[t] = base[dir][t];
+            }
+          }
+          dir_part2(G, dir, c, l[0], l[1], l[2], fd[dir], sdv[dir]);
+        }
+        const double Sm[3] = {0.0, sdv[0], sdv[1]};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const double Rp = fd[0][q] / G.dx + fd[1][q] / G.dy - Sm[q];
+          double v = (Rp - R0[q]) * ieps;
+          if (q == m) v += reg;
+          J[(size_t)(k * 9 + q * 3 + m) * S + pc] = TJ(v);
+        }
+      }
+    }
+  }
+}
+
 template <typename TJ>
 cudaError_t launch2_jacobian(const ProbDev2 *p, int level, int n, int st, const double *U, double eps, double alpha,
-                             const double *R, TJ *J, bool frozen, int cm, cudaStream_t s) {
+                             const double *R, TJ *J, bool frozen, int cm, int cell_min, cudaStream_t s) {
+  if (cell_min >= 0 && n >= cell_min) {
+    const int grid = (int)((n + kJacCellThreads - 1) / kJacCellThreads);
+    if (frozen)
+      k2_jacobian_cell<TJ, true><<<grid, kJacCellThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, cm);
+    else
+      k2_jacobian_cell<TJ, false><<<grid, kJacCellThreads, 0, s>>>(p, level, st, U, eps, alpha, R, J, cm);
+    return cudaGetLastError();
+  }
   const long items = (long)n * (st == ST_J21 ? 21 : 9);
   const int msplit = 3 * items <= kJacSplitItems ? 1 : 0;
   const int grid = grid2(items * (msplit ? 3 : 1));
@@ -1086,7 +1184,7 @@ cudaError_t launch2_to_f32(long count, const double *src, float *dst, cudaStream
 
 #define NSWE_2D_INSTANTIATE(T)                                                                                    \
   template cudaError_t launch2_jacobian<T>(const ProbDev2 *, int, int, int, const double *, double, double,      \
-                                           const double *, T *, bool, int, cudaStream_t);                        \
+                                           const double *, T *, bool, int, int, cudaStream_t);                   \
   template cudaError_t launch2_coarse_op<T>(int, int, int, const T *, T *, int, cudaStream_t);                   \
   template cudaError_t launch2_dinv<T>(int, int, int, const T *, T *, int, cudaStream_t);                        \
   template cudaError_t launch2_sor<T>(int, int, int, const T *, const T *, const T *, T *, double, int, int, int, \

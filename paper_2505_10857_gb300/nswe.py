@@ -110,6 +110,7 @@ EXPORTS = {
     "nswe_jacobian_f32": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_jacobian_frozen": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_ctx_set_colour_major_2d": (_i, [_vp, _i]),
+    "nswe_ctx_set_jacobian_cells_2d": (_i, [_vp, _i]),
     "nswe_prob_set_flux_1d": (_i, [_vp, _vp, _i]),
     "nswe_prob_set_geometry_batch_1d": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                              ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
@@ -353,16 +354,45 @@ def _host_ptr(a) -> int:
 
 # ---------------------------------------------------------------- calls (same names as the C ABI)
 
+def _check_level_sizes(call, prob, level, nb=None, **arrays):
+    """The arrays of a call on one nested level must hold that level: U, R,
+    dU [comps][n_l] and J [nb][comps^2][n_l] (comps = 2 in 1D, 3 in 2D);
+    the C entry points take bare pointers and cannot check this. A level or
+    nb the call does not accept is left to the C entry point to refuse."""
+    if not 0 <= int(level) < prob.levels:
+        return
+    two_d = isinstance(prob, Problem2D)
+    comps = 3 if two_d else 2
+    n = prob.cells(int(level))
+    for name, t in arrays.items():
+        if t is None or isinstance(t, int):
+            continue
+        if name == "J" and int(nb) not in ((9, 21) if two_d else (3, 5)):
+            continue
+        need = (int(nb) * comps * comps if name == "J" else comps) * n
+        if t.numel() < need:
+            raise ValueError(f"{call}: {name} holds {t.numel()} values; level {level} needs {need}")
+
+
+def _nb_default(prob, full):
+    if isinstance(prob, Problem2D):
+        return 21 if full else 9
+    return 5 if full else 3
+
+
 def nswe_residual(ctx: Context, prob: Problem1D, level, U, R, res=None):
+    _check_level_sizes("nswe_residual", prob, level, U=U, R=R)
     _check("nswe_residual", lib().nswe_residual(ctx.h, prob.h, int(level), _ptr(U), _ptr(R), _ptr(res)))
 
 
 def nswe_jacobian_simplified(ctx, prob, level, U, eps, alpha, R, J, res=None):
+    _check_level_sizes("nswe_jacobian_simplified", prob, level, _nb_default(prob, False), U=U, R=R, J=J)
     _check("nswe_jacobian_simplified", lib().nswe_jacobian_simplified(
         ctx.h, prob.h, int(level), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
 
 
 def nswe_jacobian_full(ctx, prob, level, U, eps, alpha, R, J, res=None):
+    _check_level_sizes("nswe_jacobian_full", prob, level, _nb_default(prob, True), U=U, R=R, J=J)
     _check("nswe_jacobian_full", lib().nswe_jacobian_full(
         ctx.h, prob.h, int(level), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
 
@@ -384,24 +414,33 @@ def nswe_ctx_set_colour_major_2d(ctx, min_cells):
     _check("nswe_ctx_set_colour_major_2d", lib().nswe_ctx_set_colour_major_2d(ctx.h, int(min_cells)))
 
 
+def nswe_ctx_set_jacobian_cells_2d(ctx, min_cells):
+    """2D levels of at least min_cells cells take the per-cell Jacobian kernel (<0: never)."""
+    _check("nswe_ctx_set_jacobian_cells_2d", lib().nswe_ctx_set_jacobian_cells_2d(ctx.h, int(min_cells)))
+
+
 def nswe_jacobian_frozen(ctx, prob, level, nb, U, eps, alpha, R, J, res=None):
     """2D Jacobian (nb 9 or 21) under the frozen linearisation."""
+    _check_level_sizes("nswe_jacobian_frozen", prob, level, nb, U=U, R=R, J=J)
     _check("nswe_jacobian_frozen", lib().nswe_jacobian_frozen(
         ctx.h, prob.h, int(level), int(nb), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J), _ptr(res)))
 
 
 def nswe_mg_vcycle(ctx, prob, level, nb, J, R, dU, prm: Params):
+    _check_level_sizes("nswe_mg_vcycle", prob, level, nb, J=J, R=R, dU=dU)
     _check("nswe_mg_vcycle", lib().nswe_mg_vcycle(ctx.h, prob.h, int(level), int(nb), _ptr(J), _ptr(R), _ptr(dU),
                                                   ctypes.byref(prm)))
 
 
 def nswe_jacobian_f32(ctx, prob, level, nb, U, eps, alpha, R, J, res=None):
     """R (float64) and the FP32 Jacobian J (float32) of a mixed-precision step."""
+    _check_level_sizes("nswe_jacobian_f32", prob, level, nb, U=U, R=R, J=J)
     _check("nswe_jacobian_f32", lib().nswe_jacobian_f32(
         ctx.h, prob.h, int(level), int(nb), _ptr(U), float(eps), float(alpha), _ptr(R), _ptr(J, True), _ptr(res)))
 
 
 def nswe_mg_vcycle_f32(ctx, prob, level, nb, J, R, dU, prm: Params):
+    _check_level_sizes("nswe_mg_vcycle_f32", prob, level, nb, J=J, R=R, dU=dU)
     _check("nswe_mg_vcycle_f32", lib().nswe_mg_vcycle_f32(ctx.h, prob.h, int(level), int(nb), _ptr(J, True),
                                                           _ptr(R, True), _ptr(dU, True), ctypes.byref(prm)))
 

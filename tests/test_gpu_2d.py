@@ -294,6 +294,38 @@ def test_guess_sized_for_another_level_is_refused(nswe, ctx):
     assert info["status"] == 0 and info["res"][0] < 1e-10
 
 
+def test_level_arrays_sized_for_another_level_are_refused(nswe, ctx):
+    """The per-level calls (residual, Jacobians, V-cycles) refuse, before any
+    launch, arrays smaller than the level they name: a state held for the
+    coarsest grid, or a J9-sized array given to the J21 call. Arrays of the
+    right size pass."""
+    p = I.bump_channel_2d(0, 32, 16, 3)
+    pr = nswe.Problem2D.from_inputs(ctx, p)
+    n = p.Nx * p.Ny
+    z = lambda *shape, dt=torch.float64: torch.zeros(shape, dtype=dt, device="cuda")
+    coarse = dev(np.ones((3, (p.Nx >> 2) * (p.Ny >> 2))))
+    U, R = dev(np.ones((3, n))), z(3, n)
+    with pytest.raises(ValueError):
+        nswe.nswe_residual(ctx, pr, 0, coarse, R)
+    with pytest.raises(ValueError):
+        nswe.nswe_residual(ctx, pr, 0, U, z(3, n // 4))
+    with pytest.raises(ValueError):
+        nswe.nswe_jacobian_full(ctx, pr, 0, U, 1e-6, 3.0, R, z(9, 9, n))
+    with pytest.raises(ValueError):
+        nswe.nswe_jacobian_frozen(ctx, pr, 0, 21, U, 1e-6, 3.0, R, z(9, 9, n))
+    with pytest.raises(ValueError):
+        nswe.nswe_jacobian_f32(ctx, pr, 0, 9, U, 1e-6, 3.0, R, z(9, 9, n // 4, dt=torch.float32))
+    prm = nswe.params(96, 3, omega=1.0, nu1=2, nu2=2, nu3=1)
+    with pytest.raises(ValueError):
+        nswe.nswe_mg_vcycle(ctx, pr, 0, 9, z(9, 9, n), R, z(3, n // 4), prm)
+    # the level the arrays were made for is accepted
+    nswe.nswe_residual(ctx, pr, 2, coarse, z(3, coarse.shape[1]))
+    J = z(9, 9, n)
+    nswe.nswe_jacobian_simplified(ctx, pr, 0, U, 1e-6, 3.0, R, J)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(J).all())
+
+
 @pytest.mark.parametrize("case", ["wedge_fp64", "bump_mixed", "bump_fp64_directional"])
 def test_colour_major_storage_gives_the_same_bits(nswe, ctx, case):
     """Nested solves with J9 and its diagonal inverses stored colour-major on
@@ -322,6 +354,58 @@ def test_colour_major_storage_gives_the_same_bits(nswe, ctx, case):
     assert ia["status"] == 0 == ib["status"], (ia, ib)
     assert ia["iters"] == ib["iters"]
     assert np.array_equal(Ua, Ub)
+
+
+@pytest.mark.parametrize("frozen", [False, True])
+def test_per_cell_jacobian_gives_the_same_bits(nswe, ctx, frozen):
+    """The FD Jacobian of Eq. 12 built one cell per thread (unperturbed lines
+    shared by all blocks) and one (cell, block) item per thread: the same
+    bits for J9, J21 and the FP32-stored J9 on a ragged grid with walls,
+    inflow and outflow, and the same nested solve."""
+    inp = I.wedge(96, 40, 3, x1=40.0, y1=30.0, x_wall=8.0, theta_deg=10.0)
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    n = inp.Nx * inp.Ny
+    rng = np.random.default_rng(96)
+    base = np.repeat(np.asarray(inp.bc_state[0], dtype=np.float64)[:, None], n, axis=1)
+    U = dev(base * (1 + 0.05 * rng.standard_normal(base.shape)))
+    z = lambda *shape, dt=torch.float64: torch.zeros(shape, dtype=dt, device="cuda")
+    if frozen:  # the wedge needs the frozen linearisation to converge
+        solve = I.wedge(64, 32, 4, start_level=2)
+        prm = nswe.params2d_from(I.Params2D(levels=4, nu1=[15], nu2=[15], tol=1e-11, n_max=400, nest_start=2,
+                                            omega=0.1, frozen=True))
+    else:
+        solve = I.bump_channel_2d(1, 128, 64, 5)
+        prm = nswe.params2d_from(I.Params2D(levels=5, nu1=[20], nu2=[20], tol=1e-10, n_max=400))
+    sprob = nswe.Problem2D.from_inputs(ctx, solve)
+    out = []
+    try:
+        for min_cells in (0, -1):
+            nswe.nswe_ctx_set_jacobian_cells_2d(ctx, min_cells)
+            got = {}
+            for nb in (9, 21):
+                R, J = z(3, n), z(nb, 9, n)
+                if frozen:
+                    nswe.nswe_jacobian_frozen(ctx, prob, 0, nb, U, 1e-6, 3.0, R, J)
+                elif nb == 9:
+                    nswe.nswe_jacobian_simplified(ctx, prob, 0, U, 1e-6, 3.0, R, J)
+                else:
+                    nswe.nswe_jacobian_full(ctx, prob, 0, U, 1e-6, 3.0, R, J)
+                got[nb] = host(J)
+            J32 = z(9, 9, n, dt=torch.float32)
+            nswe.nswe_jacobian_f32(ctx, prob, 0, 9, U, 1e-6, 3.0, z(3, n), J32)
+            got["f32"] = J32.cpu().numpy()
+            Us = z(3, solve.Nx * solve.Ny)
+            got["info"] = nswe.nswe_newton_solve(ctx, sprob, dev(solve.U0_start), Us, prm)
+            got["U"] = host(Us)
+            out.append(got)
+    finally:
+        nswe.nswe_ctx_set_jacobian_cells_2d(ctx, 32768)
+    a, b = out
+    assert np.isfinite(a[9]).all() and np.abs(a[9]).max() > 0
+    for k in (9, 21, "f32", "U"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["info"]["status"] == 0 == b["info"]["status"]
+    assert a["info"]["iters"] == b["info"]["iters"]
 
 
 def test_negative_depth_reported_not_faulted_2d(nswe, ctx):
