@@ -78,3 +78,50 @@ def test_solve_shapes_listed():
     assert shapes[0] == (256, 4) and len(shapes) >= 2
     for t, b in shapes:
         assert t % 32 == 0 and t * b <= 2048 and t * b * 64 <= 65536 * 2
+
+
+def _fake_problem(cls, levels, dims):
+    """A binding problem object without a device-side problem: only the
+    sizes the host-side checks read."""
+    import ctypes as _ct
+    p = object.__new__(cls)
+    p.h = _ct.c_void_p()  # no handle: close() does nothing
+    p.levels = levels
+    if cls.__name__ == "Problem2D":
+        p.Nx, p.Ny = dims
+        p.cells = lambda l=0: (p.Nx >> l) * (p.Ny >> l)
+    else:
+        p.N = dims
+        p.cells = lambda l=0: p.N >> l
+    return p
+
+
+def test_binding_refuses_arrays_smaller_than_their_level():
+    """The per-level calls take bare pointers in C, so the binding checks the
+    sizes first: U, R, dU [comps][n_l] and J [nb][comps^2][n_l]. A level or
+    nb the C call does not accept is left to the C call to refuse."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    from paper_2505_10857_gb300 import nswe
+    chk = nswe._check_level_sizes
+    p2 = _fake_problem(nswe.Problem2D, 3, (32, 16))
+    n0, n2 = 32 * 16, 8 * 4
+    z = lambda *shape: torch.zeros(shape, dtype=torch.float64)
+    chk("call", p2, 0, 9, U=z(3, n0), R=z(3, n0), J=z(9, 9, n0))
+    chk("call", p2, 2, 21, U=z(3, n2), R=z(3, n2), J=z(21, 9, n2), dU=z(3, n2))
+    chk("call", p2, 0, 9, U=z(3, n0 * 2))  # larger is fine
+    for bad in (dict(U=z(3, n2)), dict(R=z(3, n0 - 1)), dict(dU=z(2, n0)), dict(J=z(9, 9, n0 // 4))):
+        with pytest.raises(ValueError):
+            chk("call", p2, 0, 9, **bad)
+    with pytest.raises(ValueError):
+        chk("call", p2, 0, 21, J=z(9, 9, n0))  # J9-sized array for J21
+    chk("call", p2, 3, 9, U=z(1))      # level outside 0..2: the C call refuses it
+    chk("call", p2, 0, 7, J=z(1))      # nb 7: the C call refuses it
+    chk("call", p2, 0, 9, U=None, R=12345)  # no array, or a raw pointer: not checked
+    p1 = _fake_problem(nswe.Problem1D, 4, 200)
+    chk("call", p1, 1, 3, U=z(2, 100), R=z(2, 100), J=z(3, 4, 100))
+    with pytest.raises(ValueError):
+        chk("call", p1, 0, 5, J=z(3, 4, 200))
+    with pytest.raises(ValueError):
+        chk("call", p1, 0, 3, U=z(3, 100))
+    chk("call", p1, 0, 9, J=z(1))      # a 2D nb on a 1D problem: the C call refuses it
