@@ -329,8 +329,9 @@ def test_level_arrays_sized_for_another_level_are_refused(nswe, ctx):
 @pytest.mark.parametrize("case", ["wedge_fp64", "bump_mixed", "bump_fp64_directional"])
 def test_colour_major_storage_gives_the_same_bits(nswe, ctx, case):
     """Nested solves with J9 and its diagonal inverses stored colour-major on
-    every level solved by V-cycles (forced down to the smallest levels) and
-    cell-contiguous: the same Newton counts and the same bits."""
+    every level solved by V-cycles (forced down to the smallest levels, with
+    the Jacobian built one cell per thread or one (cell, block) item per
+    thread) and cell-contiguous: the same Newton counts and the same bits."""
     if case == "wedge_fp64":
         inp = I.wedge(64, 32, 4, start_level=2)
         prm = nswe.params2d_from(I.Params2D(levels=4, nu1=[15], nu2=[15], tol=1e-11, n_max=400, nest_start=2,
@@ -343,17 +344,23 @@ def test_colour_major_storage_gives_the_same_bits(nswe, ctx, case):
     prob = nswe.Problem2D.from_inputs(ctx, inp)
     out = []
     try:
-        for min_cells in (1, -1):
-            nswe.nswe_ctx_set_colour_major_2d(ctx, min_cells)
+        # (colour-major from, per-cell Jacobian from): both forced down to the
+        # smallest levels, colour-major alone, neither
+        for cm_min, cell_min in ((1, 0), (1, -1), (-1, -1)):
+            nswe.nswe_ctx_set_colour_major_2d(ctx, cm_min)
+            nswe.nswe_ctx_set_jacobian_cells_2d(ctx, cell_min)
             U = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
             info = nswe.nswe_newton_solve(ctx, prob, dev(inp.U0_start), U, prm)
             out.append((host(U), info))
     finally:
         nswe.nswe_ctx_set_colour_major_2d(ctx, 131072)
-    (Ua, ia), (Ub, ib) = out
-    assert ia["status"] == 0 == ib["status"], (ia, ib)
-    assert ia["iters"] == ib["iters"]
-    assert np.array_equal(Ua, Ub)
+        nswe.nswe_ctx_set_jacobian_cells_2d(ctx, 32768)
+    (Ua, ia) = out[-1]
+    assert ia["status"] == 0, ia
+    for Ub, ib in out[:-1]:
+        assert ib["status"] == 0, ib
+        assert ia["iters"] == ib["iters"]
+        assert np.array_equal(Ua, Ub)
 
 
 @pytest.mark.parametrize("frozen", [False, True])
