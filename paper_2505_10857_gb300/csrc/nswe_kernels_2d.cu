@@ -39,9 +39,6 @@ __device__ __forceinline__ int st_off(int st, int k, int d) {
 }
 __device__ __forceinline__ int st_center(int st) { return st == ST_J9 ? 4 : st == ST_J21 ? 10 : st == ST_P5 ? 2 : 4; }
 __device__ __forceinline__ int st_coarse(int st) { return (st == ST_J9 || st == ST_P5) ? ST_P5 : ST_P9; }
-__device__ __forceinline__ int st_colour(int st, int i, int j) {
-  return st == ST_J9 ? (i + j) % 3 : st == ST_J21 ? (i % 3) + 3 * (j % 3) : st == ST_P5 ? (i + j) % 2 : (i % 2) + 2 * (j % 2);
-}
 
 struct Geo2 {
   int Nx, Ny;
