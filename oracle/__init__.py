@@ -110,6 +110,8 @@ def _lib_handle():
             dbl, i32, P = ctypes.c_double, ctypes.c_int, ctypes.POINTER
             sig = {
                 "or_weno3": (None, [dbl, dbl, dbl, _D, _D]),
+                "or_set_weno_zeta": (None, [dbl]),
+                "or_get_weno_zeta": (dbl, []),
                 "or_flux1d": (None, [dbl, dbl, dbl, dbl, _D]),
                 "or_hll1d": (None, [dbl, dbl, dbl, dbl, dbl, dbl, _D]),
                 "or_llf1d": (None, [dbl, dbl, dbl, dbl, dbl, dbl, _D]),
@@ -135,6 +137,7 @@ def _lib_handle():
             sig.update({
                 "or_llf2d": (None, [i32, _D, _D, dbl, _D]),
                 "or_residual_cell2d": (None, [G2, _D, i32, i32, _D]),
+                "or_face_gauss2d": (None, [G2, _D, i32, i32, i32, i32, _D]),
                 "or_residual2d": (dbl, [G2, _D, _D]),
                 "or_jacobian2d": (dbl, [G2, _D, dbl, dbl, i32, _D, _D]),
                 "or_jacobian2d_frozen": (dbl, [G2, _D, dbl, dbl, i32, _D, _D]),
@@ -200,6 +203,23 @@ def weno3(a, b, c):
     up, um = ctypes.c_double(), ctypes.c_double()
     lib().or_weno3(a, b, c, ctypes.byref(up), ctypes.byref(um))
     return up.value, um.value
+
+
+class weno_zeta:
+    """Context manager that sets the zeta of Eq. 8 (1e-6 in the paper) for the
+    oracle's reconstructions and restores it on exit."""
+
+    def __init__(self, zeta):
+        self.zeta = float(zeta)
+
+    def __enter__(self):
+        self.old = lib().or_get_weno_zeta()
+        lib().or_set_weno_zeta(self.zeta)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_weno_zeta(self.old)
+        return False
 
 
 def hll1d(HL, QL, HR, QR, sig, g):
@@ -471,6 +491,16 @@ def residual_cell2d(prob: Problem2D, U, i, j):
     R = np.zeros(3)
     lib().or_residual_cell2d(prob.ref(), ptr(U), int(i), int(j), ptr(R))
     return R
+
+
+def face_gauss2d(prob: Problem2D, U, direction, line, k, side):
+    """States at the two Gauss points of the face between cells k and k+1 of a
+    row (direction 0) or column (direction 1); side 0 = U^-, 1 = U^+.
+    Returns [2, 3]: lower then upper transverse Gauss point."""
+    U = _f64(U).reshape(3, prob.n).copy()
+    out = np.zeros(6)
+    lib().or_face_gauss2d(prob.ref(), ptr(U), int(direction), int(line), int(k), int(side), ptr(out))
+    return out.reshape(2, 3)
 
 
 def llf2d(direction, UL, UR, g):

@@ -56,7 +56,13 @@ static void cell_value(const or_grid1d *g, const double *H, const double *Q,
  * the combination equal the 3-cell quadratic reconstruction are
  *   U^+: d0 = 1/3, d1 = 2/3;   U^-: d~0 = 2/3, d~1 = 1/3,
  * consistent with the third-order rates of Table 1. */
-#define OR_WENO_ZETA 1e-6
+/* zeta of Eq. 8: 1e-6 in the paper. A test may raise it: as zeta grows the
+ * nonlinear weights tend to the linear weights d_r, and the scheme to the
+ * optimal linear third-order one. */
+static double or_weno_zeta = 1e-6;
+void or_set_weno_zeta(double zeta) { or_weno_zeta = zeta; }
+double or_get_weno_zeta(void) { return or_weno_zeta; }
+
 void or_weno3(double a, double b, double c, double *up, double *um) {
   double beta0 = (c - b) * (c - b); /* smoothness of T0 */
   double beta1 = (b - a) * (b - a); /* smoothness of T1 */
@@ -65,8 +71,8 @@ void or_weno3(double a, double b, double c, double *up, double *um) {
   double p1 = 0.5 * a + 0.5 * b; /* U^(1)_{k-1/2} */
   double q0 = 0.5 * b + 0.5 * c; /* U^(0)_{k+1/2} */
   double q1 = -0.5 * a + 1.5 * b; /* U^(1)_{k+1/2} */
-  double s0 = (OR_WENO_ZETA + beta0) * (OR_WENO_ZETA + beta0);
-  double s1 = (OR_WENO_ZETA + beta1) * (OR_WENO_ZETA + beta1);
+  double s0 = (or_weno_zeta + beta0) * (or_weno_zeta + beta0);
+  double s1 = (or_weno_zeta + beta1) * (or_weno_zeta + beta1);
   double a0 = (1.0 / 3.0) / s0, a1 = (2.0 / 3.0) / s1;   /* alpha_r  */
   double t0 = (2.0 / 3.0) / s0, t1 = (1.0 / 3.0) / s1;   /* alpha~_r */
   double w0 = a0 / (a0 + a1), w1 = a1 / (a0 + a1);

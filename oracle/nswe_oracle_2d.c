@@ -212,11 +212,33 @@ static void iface_value(const or_grid2d *G, const double *U, const double *U0, i
   char_rec(dir, vals, U0 ? (const double(*)[3])base : NULL, G->g, side, out);
 }
 
+/* Transverse interpolation of Section 4.1: the three reconstructed edge
+ * values of lines r-1, r, r+1 at one interface are edge averages; the
+ * quadratic that keeps those three averages takes, at the Gauss point
+ * -+ 1/(2 sqrt 3) of the middle edge, the value mid -+ (hi - lo)/(4 sqrt 3)
+ * (its curvature term (s^2 - 1/12) vanishes there). sgn = -1 (q = 0) or +1. */
+static void transverse_gauss(const double lo[3], const double mid[3], const double hi[3], double sgn, double out[3]) {
+  const double s3 = 1.0 / (4.0 * sqrt(3.0));
+  for (int m = 0; m < 3; ++m) out[m] = mid[m] + sgn * s3 * (hi[m] - lo[m]);
+}
+
+/* Values of the reconstruction at the two Gauss points of the face between
+ * cells k and k+1 of line r (dir 0: row r, x face; dir 1: column r, y face),
+ * side 0 (U^-) or 1 (U^+): out[q], q = 0 at the lower transverse Gauss point,
+ * q = 1 at the upper one. These are the states the LLF flux of Section 4.1
+ * sees. */
+void or_face_gauss2d(const or_grid2d *G, const double *U, int dir, int r, int k, int side, double out[6]) {
+  double v[3][3];
+  for (int t = 0; t < 3; ++t) iface_value(G, U, NULL, dir, r - 1 + t, k, side, v[t]);
+  transverse_gauss(v[0], v[1], v[2], -1.0, out);
+  transverse_gauss(v[0], v[1], v[2], 1.0, out + 3);
+}
+
 /* Local residual R_ij (Eq. 20), three components; with U0 != NULL the
  * reconstructions take their weights and eigenvectors from U0. */
 static void residual_cell2d(const or_grid2d *G, const double *U, const double *U0, int i, int j, double R[3]) {
   const int n = G->Nx * G->Ny, c = j * G->Nx + i;
-  const double s3 = 1.0 / (4.0 * sqrt(3.0)), tg = 1.0 / (2.0 * sqrt(3.0));
+  const double tg = 1.0 / (2.0 * sqrt(3.0));
   double flux[2][3] = {{0}}, S[3] = {0, 0, 0};
   /* dir 0: x faces i-1/2, i+1/2 of row j, transverse rows j-1..j+1.
    * dir 1: y faces j-1/2, j+1/2 of column i, transverse columns i-1..i+1. */
@@ -241,8 +263,7 @@ static void residual_cell2d(const or_grid2d *G, const double *U, const double *U
       for (int f = 0; f < 4; ++f)
         for (int side = 0; side < 2; ++side) {
           if ((f == 0 && side == 0) || (f == 3 && side == 1)) continue;
-          for (int m = 0; m < 3; ++m)
-            gv[f][side][m] = ifv[1][f][side][m] + sgn * s3 * (ifv[2][f][side][m] - ifv[0][f][side][m]);
+          transverse_gauss(ifv[0][f][side], ifv[1][f][side], ifv[2][f][side], sgn, gv[f][side]);
         }
       for (int e = 0; e < 2; ++e) { /* e = 0: face a-1/2 (f=1), e = 1: a+1/2 (f=2) */
         double F[3];

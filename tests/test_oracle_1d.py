@@ -205,27 +205,54 @@ def _cell_avg(f, x0, x1, N, nq=8):
     return sum(0.5 * wi * f(xc + 0.5 * dx * ti) for ti, wi in zip(t, w))
 
 
-@pytest.mark.slow
-def test_smooth_subcritical_third_order_and_table1(orc):
-    """Section 5.1.1: discrete steady states converge to the exact solution of
-    Eq. 27 at third order, with errors of the magnitude printed in Table 1."""
-    gold = json.load(open(os.path.join(GOLDEN, "table1_smooth_subcritical.json")))
+def _table1_errors(orc, gold):
+    """l1 errors (mean over the cells) of the discrete steady states of Eq. 26
+    with the weights of Eq. 8 (zeta = 1e-6) and with the linear weights. The
+    linear-weight steady state is reached by single-grid Newton steps with
+    direct linear solves from the nonlinear one (the nested solve from the
+    coarse lake-at-rest guess is not needed to define it)."""
     g = I.G_PAPER
-    eh, eq = [], []
+    out = {"h": [], "hu": [], "h_lin": [], "hu_lin": []}
     for lev, N in enumerate(gold["N"]):
         p = I.paper_smooth_subcritical(N, levels=lev + 1)
         prm = I.Params1D.for_problem(p)
         U, info = orc.solve_problem(p, prm)
         assert info["status"] == 0 and info["res"][0] < 1e-11
+        with orc.weno_zeta(1e30):
+            prm1 = I.Params1D(tau=1.0, levels=1, tol=1e-12, n_max=50, nb=5, eps=[1e-7])
+            Ul, il = orc.newton1d(orc.problem_levels(p)[0], U, 1, 1e-7, orc.params_from(prm1))
+        assert il["status"] == 0 and il["res"] < 1e-12, il
         h_ex = _cell_avg(lambda x: 1.0 / _u_exact_eq27(x, g), -10, 10, N)
         # Bernoulli + constant discharge: hu = 1 exactly for the exact solution
-        eh.append(np.abs(U[0] - h_ex).mean())
-        eq.append(np.abs(U[1] - 1.0).mean())
-    for e, ref in [(eh, gold["h_l1"]), (eq, gold["hu_l1"])]:
+        for key, V in (("", U), ("_lin", Ul)):
+            out["h" + key].append(np.abs(V[0] - h_ex).mean())
+            out["hu" + key].append(np.abs(V[1] - 1.0).mean())
+    return out
+
+
+@pytest.mark.slow
+def test_smooth_subcritical_third_order_and_table1(orc):
+    """Section 5.1.1: discrete steady states converge to the exact solution of
+    Eq. 27 at third order, and Table 1's printed errors lie between those of
+    the scheme's two limits.
+
+    With the weights of Eq. 8 at the paper's zeta = 1e-6 the errors are 1.9 to
+    2.9 times the printed ones; with the linear weights d_r (zeta -> infinity,
+    the optimal linear third-order scheme) they are 0.36 to 0.58 times the
+    printed ones and converge at order 3.00. No reading of the boundary data,
+    the HLL speeds (Einfeldt's give the same errors), a characteristic or a
+    primitive-variable reconstruction, or the l1 convention (dx * sum is 20
+    times the mean on [-10, 10]) brings the errors within 20 % of Table 1 on
+    all four grids; the gap lies in the nonlinear weights."""
+    gold = json.load(open(os.path.join(GOLDEN, "table1_smooth_subcritical.json")))
+    e = _table1_errors(orc, gold)
+    for e, lin, ref in [(e["h"], e["h_lin"], gold["h_l1"]), (e["hu"], e["hu_lin"], gold["hu_l1"])]:
         orders = [math.log2(e[i] / e[i + 1]) for i in range(3)]
         assert min(orders) > 2.3 and orders[-1] > 2.8, orders
-        for mine, paper in zip(e, ref):
-            assert paper / 3.0 < mine < paper * 3.0, (mine, paper)
+        lin_orders = [math.log2(lin[i] / lin[i + 1]) for i in range(3)]
+        assert all(2.9 < o < 3.1 for o in lin_orders), lin_orders
+        for mine, linear, paper in zip(e, lin, ref):
+            assert linear < paper < mine < 3.0 * paper, (linear, paper, mine)
 
 
 # ---------------------------------------------------------------- Jacobian (Eq. 12-13)
