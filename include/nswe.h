@@ -9,9 +9,9 @@
  * Jacobian J5 or its simplified block-tridiagonal form J3 (Section 3.3), and
  * solved by the geometric multigrid of Section 3.4 inside the nested NMGM of
  * Algorithm 3; the two-dimensional model of Section 4 (J21 / J9) through the
- * same calls. Arithmetic is FP64, with an optional mixed-precision 1D solve
- * (NSWE_PREC_MIXED). A continuous-batching server for streams of 1D solves
- * sits at the end of this header.
+ * same calls. Arithmetic is FP64, with an optional mixed-precision solve in
+ * 1D and 2D (NSWE_PREC_MIXED). A continuous-batching server for streams of
+ * 1D and 2D solves sits at the end of this header.
  *
  * Conventions
  *   - Cells and faces are 0-based: cell j of a level with N cells spans faces
@@ -410,7 +410,9 @@ nswe_status nswe_autotune_solve_batch(nswe_ctx ctx, int count,
  * device address (cudaGetSymbolAddress); make that first call before any
  * stream capture. All calls share the array, which keeps the last call's
  * contents; calls that overlap on the GPU race and must be serialised by the
- * caller. */
+ * caller. The looked-up address is kept for the life of the process: after
+ * cudaDeviceReset on a device the array may move, so this entry point must
+ * not be called on that device again in the same process. */
 #define NSWE_NOALLOC_MAX_CELLS 4096
 nswe_status nswe_newton_solve_noalloc(int device, void *stream, int N,
                                       int levels, double x0, double x1,

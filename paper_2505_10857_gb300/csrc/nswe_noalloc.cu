@@ -17,7 +17,9 @@
 // entry point on that device; make that first call before any stream
 // capture. Every call shares the array and leaves the last call's contents
 // in it; calls whose work overlaps on the GPU (different streams, or several
-// host threads) race on it and must be serialised by the caller.
+// host threads) race on it and must be serialised by the caller. The address
+// is kept for the life of the process; after cudaDeviceReset the array may
+// move, so the entry point must not be used on that device again.
 #include <cmath>
 #include <cstring>
 #include <mutex>

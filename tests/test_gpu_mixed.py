@@ -9,13 +9,19 @@ inputs, with bounds derived from FP32 rounding (u = 2^-24):
             plus 4u |J| for the regularisation rounded to FP32 (the cases
             here reach a third of it).
   V-cycle   the same system in FP32 and FP64 (J and R exactly representable
-            in both): the result agrees to a relative 2^-16 (64u), the
-            rounding of the smoothing sweeps amplified by the coarsest LU
-            (the cases here reach 3.5e-6).
+            in both): the result agrees to the stated 1e-5 relative bound for
+            the FP32 parts (the cases here reach 3.5e-6).
 The mixed Newton solve must reach the same FP64 stopping test (res < tol,
-checked again by the oracle's residual of the returned state) and so lands on
-the same discrete solution as the FP64 solve to within the distance that
-res < tol allows: 1e-8 relative (the cases here reach 2e-10).
+checked again by the oracle's residual of the returned state) and land on
+the FP64 discrete solution to 1e-10 relative. That solution is the oracle's
+solve converged to res < 1e-13. A solve stopped at res < 1e-10 is only
+within a few 1e-9 of it (Newton damped by tau = 0.6 contracts the error by
+0.4 per step, so the last step leaves it at about the size of the previous
+correction), whichever precision takes the steps; at res < 1e-12 the 1D
+channels here sit within 7.4e-11 of it (48 seeds of the 4096-cell channel on
+the oracle). The 1D mixed solves therefore stop at res < 1e-12; the 2D one,
+whose residual is divided by the cell area, stops at res < 1e-11 (8e-12 from
+the converged solution on the oracle).
 """
 import numpy as np
 import pytest
@@ -28,7 +34,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 EPS32 = 2.0 ** -24
-MIXED_BOUND = 1e-8
+MIXED_BOUND = 1e-10
+TOL_CONVERGED = 1e-13
+VCYCLE_F32_BOUND = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -122,7 +130,7 @@ def test_vcycle_f32_parity(nswe, ctx, orc, name, level, nb):
     nswe.nswe_mg_vcycle_f32(ctx, prob, level, nb, dev(J, torch.float32), dev(R, torch.float32), ddU, prm)
     got = host(ddU)
     err = np.abs(got - ref).max() / np.abs(ref).max()
-    assert err <= 2.0 ** -16, err
+    assert err <= VCYCLE_F32_BOUND, err
 
 
 CASES = {"small0": lambda: I.channel_small(0), "small1": lambda: I.channel_small(1),
@@ -133,10 +141,12 @@ CASES = {"small0": lambda: I.channel_small(0), "small1": lambda: I.channel_small
 @pytest.mark.parametrize("case", list(CASES))
 def test_mixed_newton_solve(nswe, ctx, orc, case):
     inp = CASES[case]()
-    prm = I.Params1D.for_problem(inp, tol=1e-10 if case != "eq26" else 1e-11, n_max=500,
-                                 nb=5 if case.endswith("j5") else 3)
-    Uref, iref = orc.solve_problem(inp, prm)
+    nb = 5 if case.endswith("j5") else 3
+    prm = I.Params1D.for_problem(inp, tol=1e-12, n_max=500, nb=nb)
+    _, iref = orc.solve_problem(inp, prm)
     assert iref["status"] == 0
+    Uref, iconv = orc.solve_problem(inp, I.Params1D.for_problem(inp, tol=TOL_CONVERGED, n_max=800, nb=nb))
+    assert iconv["status"] == 0
     prob = nswe.Problem1D.from_inputs(ctx, inp)
     p = nswe.params_from(prm)
     p.precision = nswe.PREC_MIXED
@@ -229,14 +239,16 @@ def test_vcycle_f32_parity_2d(nswe, ctx, orc, name, colours):
     ddU = dev(dU0, torch.float32)
     nswe.nswe_mg_vcycle_f32(ctx, prob, 0, 9, dev(J, torch.float32), dev(R, torch.float32), ddU, prm)
     err = np.abs(host(ddU) - ref).max() / np.abs(ref).max()
-    assert err <= 2.0 ** -16, err
+    assert err <= VCYCLE_F32_BOUND, err
 
 
 def test_mixed_newton_solve_2d(nswe, ctx, orc):
     inp = I.paper_parabolic_bump(32, 16, 3)
     prm = I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400)
-    Uref, iref = orc.solve_problem2d(inp, prm)
+    _, iref = orc.solve_problem2d(inp, prm)
     assert iref["status"] == 0
+    Uref, iconv = orc.solve_problem2d(inp, I.Params2D(levels=3, nu1=[15], nu2=[15], tol=TOL_CONVERGED, n_max=400))
+    assert iconv["status"] == 0
     prob = nswe.Problem2D.from_inputs(ctx, inp)
     p = nswe.params2d_from(prm)
     p.precision = nswe.PREC_MIXED
