@@ -36,31 +36,42 @@ if ROOT not in sys.path:
 
 METRIC = "steady solves/s and p99 latency at residual <=1e-10 vs plain FP64 Newton-MG"
 UNIT = "solves/s"
-TOL = 1e-10
-MIXED_BOUND = 1e-8  # solution distance of two solves that both reach res < TOL by different paths
+TOL = 1e-10  # the metric's residual threshold: the default FP64 line stops at res < TOL
+# Lines that compare precisions or execution forms at equal solution accuracy stop at res < TOL_SOLUTION
+# and are checked against the oracle's converged discrete solution (res < TOL_CONVERGED). Damped Newton
+# (tau = 0.6) leaves a solve stopped at res < 1e-10 a few 1e-9 from that solution whatever the precision
+# of its steps. On the oracle, res < 3e-13 puts the 4096-cell channels within 1.6e-11 of it (48 seeds)
+# and the serving requests within 4.9e-11 (the first 24; res < 1e-12 left one at 1.3e-10).
+TOL_SOLUTION = 3e-13
+TOL_CONVERGED = 3e-14
+MIXED_BOUND = 1e-10  # relative distance to the converged FP64 discrete solution
+# Derived FMA peaks (reported beside the measured ones of measure_fma_peaks, which the rooflines use)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x FP64 FMA/clk/SM x 2 flop x max SM GHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM GHz
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_solve launch of the default step
 # (608 channel solves, J3) per precision and launch shape, each from a one-pass ncu capture of
 # `bench.py --steps 1 --warmup 3 --no-cpu --shape S [--precision mixed]`; no entry: not captured.
+# DRAM bytes (read + write) of one colour pass of k2_sor_split<double, J9> at 512 x 256 with colour-major J9,
+# from one ncu capture of `bench.py --workload wedge2d --phases-only` (None: not captured for this kernel).
+SOR_PASS_TRAFFIC_512 = None
 TRAFFIC_608 = {("fp64", "256x4"): 186.38e9 + 104.80e9, ("fp64", "128x4"): 216.09e9 + 104.06e9,
                ("mixed", "256x4"): 99.28e9 + 64.18e9}
 
 
-def workload_config(batch, nb, precision="fp64"):
+def workload_config(batch, nb, precision="fp64", tol=TOL):
     prec = "FP64" if precision == "fp64" else "mixed FP64 residual/update + FP32 Jacobian/MG"
     return {"workload": "1D irregular channel, N=4096, 8-level MG, J%d, %s, subcritical" % (nb, prec),
             "precision": precision,
             "N": 4096, "levels": 8, "nest_start_cells": 256, "instances_per_step_per_gpu": batch,
-            "jacobian": "J3 (simplified)" if nb == 3 else "J5 (full)", "tol": TOL,
+            "jacobian": "J3 (simplified)" if nb == 3 else "J5 (full)", "tol": tol,
             "l2": "inputs + workspace per step (%.0f MB) exceed the 129 MB L2" % (batch * 2.4),
             "seeds": "numpy default_rng(2000 + k)"}
 
 
-def make_instances(first, count, nb):
+def make_instances(first, count, nb, tol=TOL):
     from paper_2505_10857_gb300 import inputs as I
     inps = [I.channel_irregular(k) for k in range(first, first + count)]
-    prms = [I.Params1D.for_problem(p, tol=TOL, n_max=500, nb=nb) for p in inps]
+    prms = [I.Params1D.for_problem(p, tol=tol, n_max=800, nb=nb) for p in inps]
     return inps, prms
 
 
@@ -153,6 +164,47 @@ def solve_flops(N, levels, start, iters, nb, nu1, nu2, nu3, mixed=False):
     return f64, f32
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json
+    at the repository root), else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+# ------------------------------------------------------------------------------------------------
+def measure_fma_peaks(device=0, reps=3):
+    """FP64 and FP32 FMA throughput of this GPU (TFLOP/s, best of `reps`
+    launches after one untimed), from the library's probe kernel: 8 resident
+    blocks of 256 threads per SM, 8 independent FMA chains per thread."""
+    import torch
+
+    from paper_2505_10857_gb300 import nswe
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    stream = torch.cuda.current_stream(device)
+    out = {"sms": sms, "blocks": blocks, "threads": threads}
+    for name, prec, dt, iters in (("fp64", nswe.PREC_FP64, torch.float64, 16384),
+                                  ("fp32", nswe.PREC_MIXED, torch.float32, 262144)):
+        sink = torch.zeros(blocks * threads, dtype=dt, device=f"cuda:{device}")
+        best = None
+        for r in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fl = nswe.nswe_probe_fma(stream.cuda_stream, prec, blocks, threads, iters, sink)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                t = fl / (a.elapsed_time(b) / 1000.0) / 1e12
+                best = t if best is None else max(best, t)
+        out[name + "_tflops"] = best
+        out[name + "_finite"] = bool(torch.isfinite(sink).all())
+    out["what"] = "nswe_probe_fma: best of %d timed launches (CUDA events) after one untimed" % reps
+    return out
+
+
 # ------------------------------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
@@ -210,9 +262,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------------
 def _oracle_worker(args):
-    first, count, nb = args
+    first, count, nb, tol = args
     import oracle
-    inps, prms = make_instances(first, count, nb)
+    inps, prms = make_instances(first, count, nb, tol)
     out = []
     for p, q in zip(inps, prms):
         U, info = oracle.solve_problem(p, q)
@@ -220,19 +272,24 @@ def _oracle_worker(args):
     return out
 
 
-def oracle_sample(first, count, nb, workers):
+def oracle_sample(first, count, nb, workers, tol=TOL):
     """Solves `count` instances with the CPU oracle on `workers` processes
     (spawn); returns (wall seconds, results)."""
     import oracle
     oracle.build()
-    chunks = [(first + i, 1, nb) for i in range(count)]
+    chunks = [(first + i, 1, nb, tol) for i in range(count)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        pool.map(_oracle_worker, [(first, 1, nb)] * workers)  # warm the workers
+        pool.map(_oracle_worker, [(first, 1, nb, tol)] * workers)  # warm the workers
         t0 = time.perf_counter()
         res = pool.map(_oracle_worker, chunks)
         wall = time.perf_counter() - t0
     return wall, [r[0][0] for r in res]
+
+
+def oracle_build_info():
+    import oracle
+    return oracle.compiler_info()
 
 
 def host_cores():
@@ -261,7 +318,7 @@ def run_reference(args, rank, world):
             "config": workload_config(args.batch, args.nb),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{sample} of the step's {args.batch} instances per timed step (seeds rotate), "
-                                       f"one solve per process (spawn pool)"},
+                                       f"one solve per process (spawn pool)", **oracle_build_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -303,8 +360,9 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     B, nb = args.batch, args.nb
     mixed = args.precision == "mixed"
+    tol = args.tol if args.tol is not None else (TOL_SOLUTION if mixed else TOL)
     first, _ = replica_instances(rank, world, B)
-    inps, prms = make_instances(first, B, nb)
+    inps, prms = make_instances(first, B, nb, tol)
     prm = nswe.params_from(prms[0])
     prm.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
     for q in prms[1:]:
@@ -384,9 +442,11 @@ def run_gpu(args, rank, world, local_rank):
           for k in range(B)]
     f64, f32 = sum(a for a, _ in fl), sum(b for _, b in fl)
     launch_ms = statistics.mean(per_launch)
+    peaks = measure_fma_peaks(local_rank)
+    p64, p32 = peaks["fp64_tflops"], peaks["fp32_tflops"]
     # FP64-equivalent rate: FP32 flops weighted by the FP64:FP32 peak ratio, so
     # that achieved / FP64 peak is the fraction of the time at both peaks.
-    flops = f64 + f32 * FP64_PEAK_GFLOPS / FP32_PEAK_GFLOPS
+    flops = f64 + f32 * p64 / p32
     achieved = flops / (launch_ms / 1000.0) / 1e12
 
     # ---- single-solve latency (one instance alone on the GPU)
@@ -433,21 +493,27 @@ def run_gpu(args, rank, world, local_rank):
         if world == 1 and not args.no_cpu:
             cores = host_cores()
             n = B  # the whole step: about 10-15 s of CPU work on 16 cores
-            wall, refs = oracle_sample(first, n, nb, cores)
+            wall, refs = oracle_sample(first, n, nb, cores, tol)
             n1 = 4  # per-solve latency on one core: a few solves one after another in one process
-            wall1, _ = oracle_sample(first, n1, nb, 1)
+            wall1, _ = oracle_sample(first, n1, nb, 1, tol)
             cpu = {"value": n / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"all {n} instances of the step, one solve per process (spawn pool), "
                              f"{wall:.1f} s wall",
                    "latency_1core_ms": 1000.0 * wall1 / n1,
-                   "latency_1core_sample": f"the step's first {n1} instances solved one after another on one core"}
+                   "latency_1core_sample": f"the step's first {n1} instances solved one after another on one core",
+                   **oracle_build_info()}
+            what = "the oracle's solve with the same stopping test"
+            if tol < TOL:  # equal-accuracy lines: against the converged discrete solution
+                _, refs = oracle_sample(first, n, nb, cores, TOL_CONVERGED)
+                what = f"the oracle's converged discrete solution (res < {TOL_CONVERGED:g})"
             errs = [float(np.abs(Us[k].cpu().numpy() - refs[k]).max() / np.abs(refs[k]).max()) for k in range(n)]
-            parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "bound": MIXED_BOUND if mixed else 1e-10}
+            parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "reference": what,
+                      "bound": MIXED_BOUND if tol < TOL else 1e-10}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-            "config": workload_config(B, nb, args.precision),
+            "config": workload_config(B, nb, args.precision, tol),
             "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
                            "what": "per-solve completion time from the start of its batch (device timer)",
                            "solve_p50": pct(dur, 50), "solve_p99": pct(dur, 99),
@@ -457,16 +523,17 @@ def run_gpu(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms},
             "gpu_launches": args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1000.0,
-                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1000.0),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": p64,
+                         "unit": "TFLOP/s", "frac": achieved / p64,
                          "traffic": TRAFFIC_608.get((args.precision, shape_name)) if (B == 608 and nb == 3) else None,
                          "traffic_note": "DRAM bytes per launch from one ncu capture of this workload; "
                                          "8-16 % of the HBM copy rate over the launch, far from bound",
                          "kernel": f"k_solve (persistent nested NMGM, one block per instance, shape {shape_name})",
                          "flops_per_launch": flops, "fp64_flops": f64, "fp32_flops": f32, "launch_ms": launch_ms,
-                         "peak_note": "FP64 derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"
-                                      + ("; FP32 flops counted at FP64/FP32 peak ratio (FP32 peak 152 x 128 lanes x "
-                                         "2 x 2.07 GHz)" if mixed else "")},
+                         "peak_note": "FP64 FMA peak measured in this run (nswe_probe_fma); derived "
+                                      "152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz = %.3f TFLOP/s" % (FP64_PEAK_GFLOPS / 1e3)
+                                      + ("; FP32 flops counted at the measured FP64/FP32 peak ratio" if mixed else ""),
+                         "peaks_measured": peaks},
             "clocks": clk,
         }
         if tune:
@@ -474,6 +541,8 @@ def run_gpu(args, rank, world, local_rank):
         if cpu:
             out["cpu_baseline"] = cpu
             out["parity"] = parity
+        if world == 1 and not args.no_serving:
+            out.update(serving_comparison(args, ctx))
         print(json.dumps(out), flush=True)
     return out
 
@@ -514,6 +583,33 @@ def run_wedge2d(args):
     J21 = torch.zeros((21, 9, n), dtype=torch.float64, device="cuda")
     dU = torch.zeros_like(U)
     prm = nswe.params(96, big.levels, omega=args.omega2d, nu1=20, nu2=20, nu3=3)
+    # The dominant kernel of the 2D solve: the multicolour block-SOR pass (Eq. 22) of the finest level,
+    # with J9 colour-major as the solve stores levels of 512 x 256 cells and more. Per-launch duration from
+    # two smoothing runs of different lengths (CUDA events on the launching stream): their difference holds
+    # colour passes only.
+    nswe.nswe_jacobian_simplified(ctx, pb, 0, U, 1e-6, 3.0, R, J9, res)
+    w3 = (big.Nx + 2) // 3
+    ii, jj = np.meshgrid(np.arange(big.Nx), np.arange(big.Ny))
+    pos = torch.from_numpy(((((ii + jj) % 3) * big.Ny + jj) * w3 + ii // 3).ravel()).cuda()
+    J9cm = torch.zeros((9, 9, 3 * big.Ny * w3), dtype=torch.float64, device="cuda")
+    J9cm[:, :, pos] = J9
+    sweeps = {}
+    for nu in (10, 30):
+        q = nswe.params(96, big.levels, omega=args.omega2d, nu1=nu, nu2=nu, nu3=3)
+        nl = nswe.nswe_mg_smooth(ctx, pb, 0, 9, J9cm, R, dU, q, colour_major=True)
+        sweeps[nu] = (timed(lambda: nswe.nswe_mg_smooth(ctx, pb, 0, 9, J9cm, R, dU, q, colour_major=True), 3), nl)
+    pass_ms = (sweeps[30][0] - sweeps[10][0]) / (sweeps[30][1] - sweeps[10][1])
+    # algorithmic bytes of one colour pass (n/3 cells): per cell J9 648 B, D^-1 72 B, R 24 B, own dU read and
+    # written 48 B; the other two colours' dU read once, 2n/3 x 24 B
+    pass_bytes = n / 3.0 * (648 + 72 + 24 + 48) + 2.0 * n / 3.0 * 24
+    peak, peak_src = hbm_peak_gbs()
+    achieved = pass_bytes / (pass_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": SOR_PASS_TRAFFIC_512, "peak_note": peak_src,
+            "kernel": "k2_sor_split<double, J9>: one colour pass of the 512x256 level, colour-major J9",
+            "bytes_per_launch": pass_bytes, "launch_us": 1000.0 * pass_ms,
+            "what": "algorithmic bytes per pass / per-pass time from nswe_mg_smooth with nu = 30 minus nu = 10 "
+                    "(%d vs %d colour passes)" % (sweeps[30][1], sweeps[10][1])}
     kern = {"residual_ms": timed(lambda: nswe.nswe_residual(ctx, pb, 0, U, R, res), 10),
             "jacobian_j9_ms": timed(lambda: nswe.nswe_jacobian_simplified(ctx, pb, 0, U, 1e-6, 3.0, R, J9, res), 3),
             "jacobian_j21_ms": timed(lambda: nswe.nswe_jacobian_full(ctx, pb, 0, U, 1e-6, 3.0, R, J21, res), 2),
@@ -528,8 +624,10 @@ def run_wedge2d(args):
     kern["jacobian_j9_f32_ms"] = timed(lambda: nswe.nswe_jacobian_f32(ctx, pb, 0, 9, U, 1e-6, 3.0, R, J32, res), 3)
     R32.copy_(R.float())
     kern["vcycle_j9_nu20_f32_ms"] = timed(lambda: nswe.nswe_mg_vcycle_f32(ctx, pb, 0, 9, J32, R32, dU32, prm), 2)
+    kern["sor_pass_colour_major_us"] = 1000.0 * pass_ms
     if args.phases_only:
-        print(json.dumps({"metric": "2D phase times at 512x256 (ms)", "kernels_512x256": kern}), flush=True)
+        print(json.dumps({"metric": "2D phase times at 512x256 (ms)", "kernels_512x256": kern, "roofline": roof}),
+              flush=True)
         return
     # nested from the 16 x 8 grid as in Section 5.2.2 (the V-cycles reach 8 x 4)
     frozen = args.jacobian2d == "frozen"
@@ -551,7 +649,8 @@ def run_wedge2d(args):
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1000.0 * statistics.mean(times)
-    print(json.dumps({
+    cpu = None if args.no_cpu else wedge2d_oracle_estimate(w, args, info["iters"], frozen)
+    line = {
         "metric": METRIC, "value": 1000.0 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
@@ -561,43 +660,98 @@ def run_wedge2d(args):
                                + ("mixed FP64/FP32" if mixed else "FP64"),
                    "theta_deg": big.meta["theta_deg"]},
         "converged": {"status": info["status"], "iters": info["iters"][:args.levels2d], "res": info["res"][0]},
-        "kernels_512x256": kern}), flush=True)
+        "kernels_512x256": kern, "roofline": roof}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
 
 
-def _serve_oracle_worker(k):
+def _wedge2d_step_worker(args):
+    """One oracle Newton step (Eq. 12-14 with the V-cycles of Algorithm 2) of
+    the wedge at nx x ny from its inflow guess; returns seconds."""
+    nx, ny, lev, theta, omega, frozen = args
+    import oracle
+    from paper_2505_10857_gb300 import inputs as I
+    w = I.wedge(nx, ny, lev, x1=40.0, y1=30.0, x_wall=8.0, theta_deg=theta, start_level=0)
+    prm = I.Params2D(levels=lev, nu1=[20], nu2=[20], omega=omega, tol=1e-30, n_max=1, nest_start=0, frozen=frozen)
+    t0 = time.perf_counter()
+    oracle.newton2d(oracle.problem_levels2d(w)[0], w.U0_start, lev, prm)
+    return time.perf_counter() - t0
+
+
+def wedge2d_oracle_estimate(w, args, iters, frozen):
+    """The oracle's time for the nested wedge solve, estimated: one Newton
+    step timed per nested level up to 256 x 128 cells (a process each, run
+    side by side), finer levels extrapolated in proportion to their cells
+    from the 256 x 128 step, times the GPU solve's Newton steps per level.
+    The oracle is single-threaded; one solve uses one core."""
+    import oracle
+    oracle.build()
+    s0 = args.levels2d - 2
+    levels = [l for l in range(s0, -1, -1)]
+    jobs, timed_l = [], []
+    for l in levels:
+        nx, ny = args.nx >> l, args.ny >> l
+        if nx * ny <= 256 * 128:
+            jobs.append((nx, ny, args.levels2d - l, w.meta["theta_deg"], args.omega2d, frozen))
+            timed_l.append(l)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(jobs)) as pool:
+        secs = pool.map(_wedge2d_step_worker, jobs)
+    t = dict(zip(timed_l, secs))
+    lmin = min(timed_l)
+    ref_cells = (args.nx >> lmin) * (args.ny >> lmin)
+    for l in levels:
+        if l not in t:
+            t[l] = t[lmin] * (args.nx >> l) * (args.ny >> l) / ref_cells
+    total = sum(iters[l] * t[l] for l in levels)
+    return {"value": 1.0 / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one Newton step per nested level up to 256x128 timed (one process each), the finer levels "
+                      "extrapolated in proportion to cells from the 256x128 step, times the GPU solve's Newton "
+                      "steps per level; one solve is single-threaded",
+            "step_s_per_level": {f"{args.nx >> l}x{args.ny >> l}": t[l] for l in levels},
+            "extrapolated_levels": [f"{args.nx >> l}x{args.ny >> l}" for l in levels if l not in timed_l],
+            "estimated_solve_s": total, **oracle_build_info()}
+
+
+def _serve_oracle_worker(args):
+    """Oracle solves of serving request k: at the line's stopping residual
+    (timed, the CPU baseline) and converged (the parity reference)."""
+    k, tol = args
     import oracle
     from paper_2505_10857_gb300 import inputs as I
     inp = I.serving_instance(k)
-    U, info = oracle.solve_problem(inp, I.Params1D.for_problem(inp, tol=TOL, n_max=500))
-    return U, info["status"]
+    t0 = time.perf_counter()
+    U, info = oracle.solve_problem(inp, I.Params1D.for_problem(inp, tol=tol, n_max=800))
+    dt = time.perf_counter() - t0
+    Uc, ic = oracle.solve_problem(inp, I.Params1D.for_problem(inp, tol=TOL_CONVERGED, n_max=800))
+    return U, info["status"], dt, Uc, ic["status"]
 
 
-def run_serve1d(args):
-    """Serving measurement (not the default line): `--requests` seeded 1D
-    requests (N log-uniform in [256, 16384], q ~ U[1, 6]) arriving as a
-    seeded Poisson process at `--rate` per second into the continuous-batching
-    server, mixed precision by default. Throughput counts the solves that
-    reached res < tol over the span from the first submission to the last
-    completion; latency is completion minus submission, host clock, per
-    request."""
-    import numpy as np
-    import torch
-
+def serving_requests(M, tol, mixed):
+    """The serving workload: M seeded 1D requests (N log-uniform in [256,
+    16384], q ~ U[1, 6]) and their parameters."""
     from paper_2505_10857_gb300 import inputs as I
     from paper_2505_10857_gb300 import nswe
-
-    mixed = args.precision != "fp64"
-    M = args.requests
     inps = [I.serving_instance(k) for k in range(M)]
     prms = []
     for p in inps:
-        q = nswe.params_from(I.Params1D.for_problem(p, tol=TOL, n_max=500))
+        q = nswe.params_from(I.Params1D.for_problem(p, tol=tol, n_max=800))
         q.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
         prms.append(q)
-    foot = [nswe.Server.footprint(p.N, p.levels, p.start_level) for p in inps]
-    torch.cuda.init()
-    sv = nswe.Server(0, device_bytes=args.serve_mem_gb << 30, host_bytes=1 << 30, streams=args.streams,
-                     max_batch=args.max_batch)
+    return inps, prms
+
+
+def serve1d_measure(inps, prms, rate, streams, max_batch, mem_gb, warm, seed=4999):
+    """One pass of the requests through a fresh continuous-batching server:
+    `warm` requests first (discarded), then all of them arriving as a seeded
+    Poisson process at `rate` per second (rate = inf: all at once). Returns
+    the results per request, the per-request host timestamps and the
+    server's launch count."""
+    import numpy as np
+    from paper_2505_10857_gb300 import nswe
+    M = len(inps)
+    sv = nswe.Server(0, device_bytes=mem_gb << 30, host_bytes=1 << 30, streams=streams, max_batch=max_batch)
     results = {}
 
     def drain(block_until=None):
@@ -608,18 +762,18 @@ def run_serve1d(args):
                 return
             sv.wait(1, 1.0)
 
-    # warm-up: a burst of the first requests, discarded
-    warm = min(M, 64 * max(1, args.warmup))
+    warm = min(M, warm)
     for k in range(warm):
         sv.submit(inps[k], prms[k])
     drain(warm)
     results.clear()
     st0 = sv.stats()
-    clocks = ClockSampler(0)
-    clocks.start()
-    rng = np.random.default_rng(4999)
-    gaps = rng.exponential(1.0 / args.rate, size=M)
-    arrive = np.cumsum(gaps) - gaps[0]
+    if math.isinf(rate):
+        arrive = np.zeros(M)
+    else:
+        rng = np.random.default_rng(seed)
+        gaps = rng.exponential(1.0 / rate, size=M)
+        arrive = np.cumsum(gaps) - gaps[0]
     tickets = []
     t0 = time.perf_counter()
     for k in range(M):
@@ -633,40 +787,166 @@ def run_serve1d(args):
             time.sleep(min(dt, 0.001))
         tickets.append(sv.submit(inps[k], prms[k]))
     drain(M)
-    clk = clocks.stop()
     st1 = sv.stats()
     sv.close()
     tim = [results[t][2] for t in tickets]
-    infos = [results[t][1] for t in tickets]
-    lat = sorted((x["t_done_ns"] - x["t_submit_ns"]) / 1e6 for x in tim)
-    queue = sorted((x["t_launch_ns"] - x["t_submit_ns"]) / 1e6 for x in tim)
-    span = (max(x["t_done_ns"] for x in tim) - min(x["t_submit_ns"] for x in tim)) / 1e9
-    ok = [k for k in range(M) if infos[k]["status"] == 0]
-    value = len(ok) / span  # solves that reached res < tol
+    out = {"U": [results[t][0] for t in tickets], "info": [results[t][1] for t in tickets],
+           "lat_ms": sorted((x["t_done_ns"] - x["t_submit_ns"]) / 1e6 for x in tim),
+           "queue_ms": sorted((x["t_launch_ns"] - x["t_submit_ns"]) / 1e6 for x in tim),
+           "span_s": (max(x["t_done_ns"] for x in tim) - min(x["t_submit_ns"] for x in tim)) / 1e9,
+           "launches": st1["launches"] - st0["launches"], "device_bytes_peak": st1["device_bytes_peak"]}
+    out["ok"] = [k for k in range(M) if out["info"][k]["status"] == 0]
+    out["value"] = len(out["ok"]) / out["span_s"]  # solves that reached res < tol
+    return out
 
-    def pct(a, q):
-        return a[min(len(a) - 1, int(math.ceil(q / 100.0 * len(a))) - 1)]
 
-    parity = None
+def pct(a, q):
+    return a[min(len(a) - 1, int(math.ceil(q / 100.0 * len(a))) - 1)]
+
+
+def serving_oracle(n, tol):
+    """The oracle on the host cores for the first n serving requests: timing
+    at the line's stopping residual, and the converged references."""
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_serve_oracle_worker, [(0, tol)] * cores)  # warm the workers
+        t0 = time.perf_counter()
+        refs = pool.map(_serve_oracle_worker, [(k, tol) for k in range(n)])
+        wall = time.perf_counter() - t0
+    cpu_seconds = sum(r[2] for r in refs)
+    return refs, {"value": n / cpu_seconds * cores, "unit": UNIT, "cores": cores, "kind": "oracle",
+                  "sample": f"the first {n} requests, one solve per process (spawn pool): their summed one-core "
+                            f"solve times at res < {tol:g}, scaled to {cores} cores ({cpu_seconds:.1f} core-s)",
+                  "latency_1core_ms_mean": 1000.0 * cpu_seconds / n, **oracle_build_info()}
+
+
+def _parity(Us, infos, refs, idx):
+    import numpy as np
+    errs = [float(np.abs(Us[k] - refs[k][3]).max() / np.abs(refs[k][3]).max())
+            for k in idx if infos[k]["status"] == 0 and refs[k][4] == 0]
+    return {"max_rel_err_vs_oracle": max(errs) if errs else None, "instances": len(errs),
+            "reference": f"the oracle's converged discrete solution (res < {TOL_CONVERGED:g})", "bound": MIXED_BOUND}
+
+
+def serving_comparison(args, ctx):
+    """The metric's comparison, measured beside the default line: the batched
+    mixed-precision serving form (the 1D serving workload through the
+    continuous-batching server) against the plain FP64 path solving one
+    instance at a time, both stopped at res < TOL_SOLUTION so that both land
+    within MIXED_BOUND of the converged FP64 discrete solution (checked on a
+    sample against the oracle)."""
+    import numpy as np
+    import torch
+
+    from paper_2505_10857_gb300 import nswe
+    M = args.requests
+    inps, prm_mixed = serving_requests(M, TOL_SOLUTION, True)
+    _, prm_fp64 = serving_requests(M, TOL_SOLUTION, False)
+    cfg = {"workload": f"1D serving: {M} requests, N log-uniform [256,16384] (mean "
+                       f"{np.mean([p.N for p in inps]):.0f} cells), q~U[1,6], sinusoidal width, Gaussian hump",
+           "tol": TOL_SOLUTION, "accuracy": f"res < {TOL_SOLUTION:g}: within {MIXED_BOUND:g} (relative) of the "
+                                            f"converged FP64 discrete solution", "seeds": "numpy default_rng(4000 + k)"}
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    sat = serve1d_measure(inps, prm_mixed, math.inf, args.streams, args.max_batch, args.serve_mem_gb, 64)
+    paced = serve1d_measure(inps, prm_mixed, args.rate, args.streams, args.max_batch, args.serve_mem_gb, 64)
+    sat64 = serve1d_measure(inps, prm_fp64, math.inf, args.streams, args.max_batch, args.serve_mem_gb, 64)
+    # the plain FP64 single-instance path: one request at a time, one solve per launch
+    K = args.single_requests
+    stream = torch.cuda.current_stream()
+    t_single, U_single, inf_single = [], [], []
+    for k in range(K):
+        pr = nswe.Problem1D.from_inputs(ctx, inps[k])
+        U0 = torch.from_numpy(inps[k].U0_start).cuda()
+        U = torch.zeros((2, inps[k].N), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = nswe.nswe_newton_solve(ctx, pr, U0, U, prm_fp64[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_single.append(e0.elapsed_time(e1))
+        U_single.append(U.cpu().numpy())
+        inf_single.append(info)
+        del pr
+    clk = clocks.stop()
+    ok_single = [k for k in range(K) if inf_single[k]["status"] == 0]
+    single_value = len(ok_single) / (sum(t_single) / 1000.0)
+    out = {
+        "serving": {"value": sat["value"], "unit": UNIT, "precision": "mixed FP64 residual/update + FP32 "
+                    "Jacobian/MG", "form": "continuous-batching server, all requests submitted at once",
+                    "config": dict(cfg, streams=args.streams, max_batch=args.max_batch),
+                    "converged": len(sat["ok"]), "of": M,
+                    "not_converged_seeds": [4000 + k for k in range(M) if sat["info"][k]["status"] != 0],
+                    "max_res": max(sat["info"][k]["res"][0] for k in sat["ok"]),
+                    "gpu_launches": sat["launches"], "span_s": sat["span_s"],
+                    "latency_ms_at_offered_rate": {"offered_rate": args.rate, "p50": pct(paced["lat_ms"], 50),
+                                                   "p99": pct(paced["lat_ms"], 99), "max": paced["lat_ms"][-1],
+                                                   "completed_per_s_over_run": paced["value"],
+                                                   "what": "completion minus submission per request (host clock), "
+                                                           "seeded Poisson arrivals"}},
+        "serving_fp64": {"value": sat64["value"], "unit": UNIT, "precision": "FP64",
+                         "form": "the same server and requests in FP64", "converged": len(sat64["ok"]), "of": M},
+        "plain_fp64_single": {"value": single_value, "unit": UNIT, "precision": "FP64",
+                              "form": "one request at a time through nswe_newton_solve (one solve per launch), "
+                                      "device-timed",
+                              "sample": f"the first {K} requests of the serving workload",
+                              "converged": len(ok_single), "of": K,
+                              "latency_ms_p50": pct(sorted(t_single), 50)},
+        "serving_over_plain_fp64_single": sat["value"] / single_value,
+        "serving_clocks": clk,
+    }
     if not args.no_cpu:
-        cores = host_cores()
-        n = min(M, 2 * cores)
-        ctx = mp.get_context("spawn")
-        with ctx.Pool(cores) as pool:
-            refs = pool.map(_serve_oracle_worker, range(n))
-        errs = [float(np.abs(results[tickets[k]][0] - refs[k][0]).max() / np.abs(refs[k][0]).max())
-                for k in range(n) if infos[k]["status"] == 0 and refs[k][1] == 0]
-        parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "bound": MIXED_BOUND if mixed else 1e-10}
+        n = min(K, 2 * host_cores())
+        refs, cpu = serving_oracle(n, TOL_SOLUTION)
+        out["serving"]["parity"] = _parity(sat["U"], sat["info"], refs, range(n))
+        out["serving"]["cpu_baseline"] = cpu
+        out["plain_fp64_single"]["parity"] = _parity(U_single, inf_single, refs, range(min(n, K)))
+    return out
+
+
+def run_serve1d(args):
+    """Serving measurement (not the default line): `--requests` seeded 1D
+    requests (N log-uniform in [256, 16384], q ~ U[1, 6]) arriving as a
+    seeded Poisson process at `--rate` per second into the continuous-batching
+    server, mixed precision by default, stopped at res < TOL_SOLUTION (or
+    --tol). Throughput counts the solves that reached res < tol over the span
+    from the first submission to the last completion; latency is completion
+    minus submission, host clock, per request."""
+    import numpy as np
+    import torch
+
+    from paper_2505_10857_gb300 import nswe
+
+    mixed = args.precision != "fp64"
+    tol = args.tol if args.tol is not None else TOL_SOLUTION
+    M = args.requests
+    inps, prms = serving_requests(M, tol, mixed)
+    foot = [nswe.Server.footprint(p.N, p.levels, p.start_level) for p in inps]
+    torch.cuda.init()
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = serve1d_measure(inps, prms, args.rate, args.streams, args.max_batch, args.serve_mem_gb,
+                        64 * max(1, args.warmup))
+    clk = clocks.stop()
+    lat, queue, ok, infos = r["lat_ms"], r["queue_ms"], r["ok"], r["info"]
+    line_parity, cpu = None, None
+    if not args.no_cpu:
+        n = min(M, 2 * host_cores())
+        refs, cpu = serving_oracle(n, tol)
+        line_parity = _parity(r["U"], infos, refs, range(n))
     h2d = sum(p.sig_face.nbytes + p.gq_all().nbytes + p.U0_start.nbytes for p in inps) / M
     d2h = sum(2 * p.N * 8 for p in inps) / M + ctypes.sizeof(nswe.Info)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * r["span_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
         "config": {"workload": f"1D serving: {M} requests, N log-uniform [256,16384] (mean {np.mean([p.N for p in inps]):.0f}"
                                f" cells), q~U[1,6], Poisson arrivals at {args.rate}/s, "
                                + ("mixed FP64/FP32" if mixed else "FP64"),
-                   "offered_rate": args.rate, "streams": args.streams, "max_batch": args.max_batch,
+                   "offered_rate": args.rate, "streams": args.streams, "max_batch": args.max_batch, "tol": tol,
                    "device_arena_gb": args.serve_mem_gb, "seeds": "numpy default_rng(4000 + k); arrivals 4999",
                    "l2": "resident workspace of the requests in flight exceeds the 129 MB L2"},
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": lat[-1],
@@ -676,16 +956,41 @@ def run_serve1d(args):
                       "not_converged_seeds": [4000 + k for k in range(M) if infos[k]["status"] != 0],
                       "max_res": max(infos[k]["res"][0] for k in ok),
                       "mean_newton_iters": statistics.mean(infos[k]["total_iters"] for k in ok)},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d * M, "d2h_bytes_per_step": d2h * M,
+        "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": h2d * M, "d2h_bytes_per_step": d2h * M,
                 "what": "the serving throughput is end to end: host arrays in, host results out"},
-        "gpu_launches": st1["launches"] - st0["launches"],
-        "serving": {"device_bytes_peak": st1["device_bytes_peak"], "mean_footprint_mb": float(np.mean(foot)) / 2**20,
-                    "launches": st1["launches"] - st0["launches"]},
+        "gpu_launches": r["launches"],
+        "serving": {"device_bytes_peak": r["device_bytes_peak"], "mean_footprint_mb": float(np.mean(foot)) / 2**20,
+                    "launches": r["launches"]},
         "clocks": clk,
     }
-    if parity:
-        line["parity"] = parity
+    if line_parity:
+        line["parity"] = line_parity
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
+
+
+CONFIG5_SIZES = [(128, 64, 5), (256, 128, 6), (512, 256, 7), (1024, 512, 8)]
+
+
+def config5_instances(B):
+    """The batched 2D serving workload at its stated sizes: B seeded channels,
+    grids 128 x 64 to 1024 x 512 (the four sizes in equal numbers, in the
+    order k mod 4), even k supercritical wedges (Froude 2-4, deflection 5-15
+    degrees, frozen linearisation, nested from 16 x 8), odd k subcritical
+    channels over a Gaussian bottom bump (Eq. 12, nested from 8 x 4); J9,
+    omega 0.1, nu1 = nu2 = 20, nu3 = 3, eps 1e-6."""
+    from paper_2505_10857_gb300 import inputs as I
+    inps, prms = [], []
+    for k in range(B):
+        Nx, Ny, lev = CONFIG5_SIZES[(k // 2) % 4]
+        if k % 2 == 0:
+            inps.append(I.wedge_serving_2d(k, Nx, Ny, lev))
+            prms.append(I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=TOL, n_max=400, nest_start=lev - 2,
+                                   omega=0.1, frozen=True))
+        else:
+            inps.append(I.gauss_bump_channel_2d(k, Nx, Ny, lev))
+            prms.append(I.Params2D(levels=lev, nu1=[20], nu2=[20], tol=TOL, n_max=400))
+    return inps, prms
 
 
 def batch2d_instances(B, family):
@@ -725,8 +1030,10 @@ def run_batch2d(args):
 
     mixed = args.precision != "fp64"
     B = args.batch2d
-    inps, prms_in = batch2d_instances(B, args.family2d)
+    inps, prms_in = config5_instances(B) if args.sizes2d == "config5" else batch2d_instances(B, args.family2d)
     ctx = nswe.Context(0)
+    lockstep = args.batch2d_mode == "lockstep"
+    nswe.nswe_ctx_set_batch_2d(ctx, nswe.BATCH2D_LOCKSTEP if lockstep else nswe.BATCH2D_CONCURRENT)
     probs = [nswe.Problem2D.from_inputs(ctx, p) for p in inps]
     U0s = [torch.from_numpy(p.U0_start).cuda() for p in inps]
     Us = [torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda") for p in inps]
@@ -752,11 +1059,13 @@ def run_batch2d(args):
         infos = batched()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    seq = one_by_one()
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
+    seq, t_seq = None, None
+    if not args.no_one_by_one:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seq = one_by_one()
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
     ms = 1000.0 * statistics.mean(times)
     ok = [k for k in range(B) if infos[k]["status"] == 0]
     # per-solve latency from the batch start, from the device timestamps of each solve
@@ -765,7 +1074,7 @@ def run_batch2d(args):
     pick = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
     kinds = {}
     for k, p in enumerate(inps):
-        key = f"{'wedge' if 'froude' in p.meta else 'bump'} {p.Nx}x{p.Ny}"
+        key = f"{'wedge' if 'froude' in p.meta else p.meta.get('case', 'bump')} {p.Nx}x{p.Ny}"
         kinds.setdefault(key, [0, 0])
         kinds[key][0] += 1
         kinds[key][1] += int(infos[k]["status"] == 0)
@@ -773,19 +1082,29 @@ def run_batch2d(args):
         "metric": METRIC, "value": len(ok) / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": f"2D batched: {B} seeded channels ({args.family2d}: wedges Froude 2-4, 5-15 deg, "
-                               "frozen linearisation; parabolic bumps, Eq. 12), 128x64 and 256x128, J9, nu 20, "
+        "config": {"workload": (f"2D batched serving sizes: {B} seeded channels (wedges Froude 2-4, 5-15 deg, "
+                                "frozen linearisation; Gaussian-bump channels, Eq. 12), 128x64, 256x128, 512x256 "
+                                "and 1024x512 in equal numbers, J9, nu 20, "
+                                if args.sizes2d == "config5" else
+                                f"2D batched: {B} seeded channels ({args.family2d}: wedges Froude 2-4, 5-15 deg, "
+                                "frozen linearisation; parabolic bumps, Eq. 12), 128x64 and 256x128, J9, nu 20, ")
                                + ("mixed FP64/FP32" if mixed else "FP64"),
-                   "seeds": "wedges default_rng(7000 + k), bumps default_rng(5000 + k)"},
+                   "batch_mode": args.batch2d_mode,
+                   "seeds": "wedges default_rng(7000 + k), bumps default_rng(%d + k)"
+                            % (6000 if args.sizes2d == "config5" else 5000)},
         "latency_ms": {"p50": pick(0.5), "p99": pick(0.99), "what": "per-solve completion from the batch start"},
         "converged": {"all_status_ok": len(ok) == B, "converged": len(ok), "of": B,
                       "by_kind": {k: {"n": v[0], "converged": v[1]} for k, v in kinds.items()},
                       "failed": [(inps[k].meta.get("seed"), infos[k]["status"], infos[k]["iters"][:inps[k].levels])
                                  for k in range(B) if infos[k]["status"] != 0][:8],
                       "max_res": max((infos[k]["res"][0] for k in ok), default=None),
-                      "one_by_one_equal_iters": all(seq[k]["iters"] == infos[k]["iters"] for k in range(B))},
-        "one_by_one": {"solves_per_s": sum(1 for i in seq if i["status"] == 0) / t_seq, "ms": 1000.0 * t_seq},
-        "what": "host-timed: the batched call runs the solves concurrently on worker streams"}), flush=True)
+                      "one_by_one_equal_iters": (all(seq[k]["iters"] == infos[k]["iters"] for k in range(B))
+                                                 if seq else None)},
+        "one_by_one": ({"solves_per_s": sum(1 for i in seq if i["status"] == 0) / t_seq, "ms": 1000.0 * t_seq}
+                       if seq else None),
+        "what": "host-timed: " + ("one launch per phase and colour pass over all problems (lockstep)" if lockstep
+                                  else "the batched call runs the solves concurrently on worker streams")}),
+          flush=True)
 
 
 def run_serve2d(args):
@@ -914,8 +1233,13 @@ def run_jac1d(args):
          "jacobian_j3_f32_ms": timed(lambda: nswe.nswe_jacobian_f32(ctx, prob, 0, 3, U, eps, 3.0, R, J5f[:3], res)),
          "jacobian_j5_f32_ms": timed(lambda: nswe.nswe_jacobian_f32(ctx, prob, 0, 5, U, eps, 3.0, R, J5f, res))}
     t["j3_saving_vs_j5"] = 1.0 - t["jacobian_j3_ms"] / t["jacobian_j5_ms"]
-    print(json.dumps({"metric": "1D residual and Jacobian times at 2^20 cells (ms)", "cells": N, "phases": t}),
-          flush=True)
+    # one V-cycle (Algorithm 2) on J3 of the same level, 14 levels down to 128 cells
+    nswe.nswe_jacobian_simplified(ctx, prob, 0, U, eps, 3.0, R, J5[:3], res)
+    dU = torch.zeros_like(U)
+    prm = nswe.params(N, levels, omega=inp.omega, nu1=2, nu2=2, nu3=1)
+    t["vcycle_j3_ms"] = timed(lambda: nswe.nswe_mg_vcycle(ctx, prob, 0, 3, J5[:3], R, dU, prm), 5)
+    print(json.dumps({"metric": "1D residual, Jacobian and V-cycle times at 2^20 cells (ms)", "cells": N,
+                      "phases": t}), flush=True)
 
 
 def main():
@@ -932,8 +1256,13 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d",
-                    choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d", "jac1d"])
+                    choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d", "jac1d", "peaks"])
     ap.add_argument("--batch2d", type=int, default=16, help="batch2d: 2D problems per batch")
+    ap.add_argument("--batch2d-mode", choices=["lockstep", "concurrent"], default="lockstep",
+                    help="batch2d: shared launches over all problems, or concurrent per-problem streams")
+    ap.add_argument("--sizes2d", choices=["small", "config5"], default="small",
+                    help="batch2d: 128x64/256x128, or the serving sizes 128x64 to 1024x512")
+    ap.add_argument("--no-one-by-one", action="store_true", help="batch2d: skip the one-by-one comparison")
     ap.add_argument("--rate2d", type=float, default=1.0, help="serve2d: Poisson arrival rate (requests/s)")
     ap.add_argument("--family2d", choices=["mix", "wedge", "bump"], default="mix",
                     help="batch2d: wedge and bump channels, or one family")
@@ -949,6 +1278,12 @@ def main():
                     help="wedge2d: the 2D Jacobian of the nested solve (Eq. 12 as printed, or frozen weights)")
     ap.add_argument("--omega2d", type=float, default=0.1)
     ap.add_argument("--phases-only", action="store_true", help="wedge2d: only the 512x256 phase times")
+    ap.add_argument("--tol", type=float, default=None,
+                    help="stopping residual (default: 1e-10 for the FP64 line, 3e-13 for mixed and serving lines)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default line: skip the serving / plain FP64 single-instance comparison")
+    ap.add_argument("--single-requests", type=int, default=24,
+                    help="default line: requests solved one at a time for the plain FP64 single-instance rate")
     args = ap.parse_args()
     if args.workload == "wedge2d":
         from paper_2505_10857_gb300 import build
@@ -959,6 +1294,13 @@ def main():
         from paper_2505_10857_gb300 import build
         build.build()
         run_batch2d(args)
+        return
+    if args.workload == "peaks":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        pk = measure_fma_peaks(0, reps=5)
+        pk.update({"derived_fp64_tflops": FP64_PEAK_GFLOPS / 1e3, "derived_fp32_tflops": FP32_PEAK_GFLOPS / 1e3})
+        print(json.dumps({"metric": "FP64 and FP32 FMA throughput (TFLOP/s)", "peaks": pk}), flush=True)
         return
     if args.workload == "jac1d":
         from paper_2505_10857_gb300 import build

@@ -185,6 +185,25 @@ nswe_status nswe_ctx_set_colour_major_2d(nswe_ctx ctx, int min_cells);
  * never per cell. Default 32768. Applies to nested solves and to the
  * standalone Jacobian calls of this context. */
 nswe_status nswe_ctx_set_jacobian_cells_2d(nswe_ctx ctx, int min_cells);
+/* How nswe_newton_solve_batch and nswe_newton_solve_batch_each run a batch
+ * of several 2D problems (the paper solves one problem; results are the same
+ * bits either way):
+ *   NSWE_BATCH2D_CONCURRENT (default): each problem's solve is sequenced on
+ *     its own stream by one of up to 8 host worker threads.
+ *   NSWE_BATCH2D_LOCKSTEP: problems with the same precision, Jacobian
+ *     stencil (J9 / J21) and smoothing schedule (nu1, nu2, nu3, omega,
+ *     colours2d) share launches: each phase of a Newton step (Eq. 12-14) and
+ *     each colour pass of its V-cycles (Algorithm 2) is one launch over all
+ *     of them, each problem owning a range of the launch's blocks. Nested
+ *     stage k runs Newton iterations on level s0 - k of every problem that
+ *     has it (s0 its start level); a problem that meets its stopping test
+ *     is masked off until the stage ends. A stage's Newton step is captured
+ *     once as a CUDA graph and replayed; the host reads every problem's res
+ *     and flag once per replay. Groups with different schedules run one
+ *     after another. Timestamps in nswe_info are host times. */
+#define NSWE_BATCH2D_CONCURRENT 0
+#define NSWE_BATCH2D_LOCKSTEP 1
+nswe_status nswe_ctx_set_batch_2d(nswe_ctx ctx, int mode);
 nswe_status nswe_ctx_destroy(nswe_ctx ctx);
 
 /* One-dimensional problem (Eq. 3-4) on [x0, x1] with N cells and `levels`
@@ -313,6 +332,28 @@ nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb,
                            const double *J, const double *R, double *dU,
                            const nswe_params *params);
 
+/* The smoother of Algorithm 2 alone on one 2D level: params->nu1 steps of
+ * the multicolour block SOR of Eq. 22 (relaxation params->omega, schedule
+ * params->colours2d as in a V-cycle: K = 0 two symmetric passes of the
+ * stencil colouring per step, K >= 3 the directional schedule), after the
+ * inverse diagonal blocks of J are formed in the problem's workspace. No
+ * coarse correction. 2D problems only (1D: NSWE_EINVAL).
+ *   nb            9 (J9) or 21 (J21).
+ *   J             DEVICE [nb][9][S]: cell-contiguous (colour_major = 0,
+ *                 S = n_l, cell (i, j) at j*Nx + i), or, for J9 only,
+ *                 colour-major (colour_major = 1) as the library stores large
+ *                 Newton levels: the cells of colour (i + j) mod 3 form one
+ *                 plane of Ny rows of W3 = ceil(Nx/3) slots, cell (i, j) at
+ *                 ((i + j) mod 3 * Ny + j) * W3 + i / 3, S = 3 * Ny * W3.
+ *   R             DEVICE [3][n_l] right-hand side of J dU = -R; dU DEVICE
+ *                 [3][n_l] in/out (cell-contiguous in both layouts).
+ *   launches      HOST, may be NULL: the number of colour-pass launches.
+ * Asynchronous on the context stream. */
+nswe_status nswe_mg_smooth(nswe_ctx ctx, nswe_prob prob, int level, int nb,
+                           const double *J, const double *R, double *dU,
+                           const nswe_params *params, int colour_major,
+                           int *launches);
+
 /* nswe_mg_vcycle in FP32, the linear solve of a NSWE_PREC_MIXED step: J, R
  * (float) in and dU (float) in/out in the layouts of nswe_mg_vcycle (nb = 3
  * or 5 in 1D, 9 or 21 in 2D). The coarse levels reuse the problem's
@@ -387,6 +428,19 @@ nswe_status nswe_autotune_solve_batch(nswe_ctx ctx, int count,
                                       double *const *Us,
                                       const nswe_params *params, int reps,
                                       double *ms, int *best);
+
+/* Throughput probe of the FMA pipes (the paper has no counterpart): the
+ * measured denominators of the arithmetic rooflines, since the FD Jacobian
+ * (Eq. 12) and the multigrid sweeps of this library are bound by FP64 issue.
+ * Launches `blocks` x `threads` threads on `stream` (cudaStream_t as void*),
+ * each running `iters` rounds of 8 independent fused multiply-add chains in
+ * FP64 (precision NSWE_PREC_FP64) or FP32 (NSWE_PREC_MIXED), and writes one
+ * value per thread to `sink` (DEVICE, blocks*threads doubles or floats).
+ * *flops (HOST, may be NULL) receives 2 * 8 * blocks * threads * iters; the
+ * caller times the launch with CUDA events on the stream. Asynchronous.
+ * threads must be a multiple of 32 in [32, 1024]; otherwise NSWE_EINVAL. */
+nswe_status nswe_probe_fma(void *stream, int precision, int blocks,
+                           int threads, int iters, void *sink, double *flops);
 
 /* Allocation-free nested solve. The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc, such as code running

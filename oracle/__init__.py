@@ -30,6 +30,18 @@ BC_REFLECT, BC_INFLOW, BC_OUTFLOW, BC2_DISCHARGE, BC2_DEPTH = 5, 6, 7, 8, 9
 ST_J9, ST_J21, ST_P5, ST_P9 = 0, 1, 2, 3
 
 
+CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off"]
+
+
+def compiler_info() -> dict:
+    """The compiler and flags the oracle is built with (for reports that time it)."""
+    try:
+        ver = subprocess.run(["gcc", "--version"], capture_output=True, text=True).stdout.splitlines()[0]
+    except (OSError, IndexError):
+        ver = "gcc (version unknown)"
+    return {"compiler": ver, "flags": " ".join(CFLAGS), "threads_per_solve": 1}
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (C11, -O2, no FP contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -38,7 +50,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    cmd = ["gcc"] + CFLAGS + ["-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

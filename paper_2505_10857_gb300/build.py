@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnswe_gb300.so")
-SOURCES = ["nswe_kernels_1d.cu", "nswe_kernels_2d.cu", "nswe_host.cu", "nswe_noalloc.cu", "nswe_server.cu"]
+SOURCES = ["nswe_kernels_1d.cu", "nswe_kernels_2d.cu", "nswe_host.cu", "nswe_noalloc.cu", "nswe_server.cu",
+           "nswe_probe.cu", "nswe_batch2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -14,47 +14,6 @@
 
 using namespace nswe;
 
-struct nswe_ctx_s {
-  int device;
-  cudaStream_t stream;
-  double *partials;      // [1024] per-block partial sums of res
-  int *status;           // device status word of standalone V-cycles
-  SolveTask *tasks;      // device task array
-  nswe_info *infos;      // device info records
-  nswe_params *prms;     // device per-task parameters (nswe_newton_solve_batch_each)
-  int cap;               // capacity of tasks / infos / prms
-  int solve_shape[2];    // launch shape of the 1D solve kernel per precision
-  int cm2d_min_cells = 131072;  // 2D Newton levels of at least this many cells store J9 colour-major
-  int jac2d_cell_min = kJac2CellMinDefault;  // 2D levels from which the per-cell Jacobian kernel runs
-};
-
-struct nswe_prob_s {
-  nswe_ctx ctx;
-  int dim;               // 1 or 2
-  int N, levels;         // 1D: cells of the finest level
-  double x0, x1, g;
-  ProbDev host;          // device pointers, host copy
-  ProbDev *dev;          // device copy
-  double *arena;
-  size_t geo_doubles;    // geometry region at the front of the arena
-  double *stage;         // 1D: pinned staging of the geometry upload [geo_doubles]
-  cudaEvent_t staged;    // 1D: the last upload from `stage` has been copied
-  // 2D
-  int Nx, Ny;
-  ProbDev2 host2;
-  ProbDev2 *dev2;
-  double *dense;         // coarsest dense LU factors [N3][N3]
-  int *piv;              // [N3]
-  double *xbuf;          // [N3]
-  int *flag;             // device flag (zero pivot / non-positive depth)
-  double *res_dev;       // device scalar
-  double *res_host;      // pinned host scalar
-  int *flag_host;        // pinned host flag
-  cudaStream_t cap;      // 2D: stream on which a Newton step is captured
-  double *partials2;     // 2D: [1024] per-block partial sums of res (per problem, so
-                         // that several 2D solves can run concurrently)
-};
-
 namespace {
 
 struct DeviceGuard {
@@ -239,8 +198,10 @@ Lev2<T> lev2_view(const Level2Dev &L) {
                  reinterpret_cast<T *>(L.dU), 0};
 }
 
+// launches (may be NULL): incremented once per colour-pass launch.
 template <typename T>
-cudaError_t smooth2(const Lev2<T> &Lv, int st, int steps, double omega, int Kc, cudaStream_t s) {
+cudaError_t smooth2(const Lev2<T> &Lv, int st, int steps, double omega, int Kc, cudaStream_t s,
+                    int *launches = nullptr) {
   cudaError_t e = cudaSuccess;
   if (Kc >= 3 && (st == ST_J9 || st == ST_P5)) {
     // Directional schedule (the multicolour analogue of D1-D4): diagonal
@@ -252,6 +213,7 @@ cudaError_t smooth2(const Lev2<T> &Lv, int st, int steps, double omega, int Kc, 
           const int mode = (d % 2) + 1, col = d < 2 ? q : Kc - 1 - q;
           if ((e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, mode, Kc, col, 1, Lv.cm, s)))
             return e;
+          if (launches) ++*launches;
         }
     return e;
   }
@@ -267,10 +229,14 @@ cudaError_t smooth2(const Lev2<T> &Lv, int st, int steps, double omega, int Kc, 
       if (prev >= 0 &&
           (e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, Lv.cm, s)))
         return e;
+      if (prev >= 0 && launches) ++*launches;
       prev = col;
       reps = 1;
     }
-  if (prev >= 0) e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, Lv.cm, s);
+  if (prev >= 0) {
+    e = launch2_sor<T>(Lv.Nx, Lv.Ny, st, Lv.J, Lv.Dinv, Lv.R, Lv.dU, omega, 0, 0, prev, reps, Lv.cm, s);
+    if (launches) ++*launches;
+  }
   return e;
 }
 
@@ -492,6 +458,7 @@ unsigned long long host_ns() {
 // prms[each ? i : 0] are problem i's parameters.
 nswe_status solve2d_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
                           double *const *Us, const nswe_params *prms, bool each, nswe_info *infos) {
+  if (count > 1 && ctx->batch2d_lockstep) return solve2d_lockstep(ctx, count, probs, U0s, Us, prms, each, infos);
   if (count == 1) {
     nswe_info inf;
     const unsigned long long t0 = host_ns();
@@ -629,6 +596,12 @@ nswe_status nswe_ctx_create(nswe_ctx *out, int device, void *stream) {
 nswe_status nswe_ctx_set_colour_major_2d(nswe_ctx ctx, int min_cells) {
   if (!ctx) return NSWE_EINVAL;
   ctx->cm2d_min_cells = min_cells;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_set_batch_2d(nswe_ctx ctx, int mode) {
+  if (!ctx || (mode != NSWE_BATCH2D_CONCURRENT && mode != NSWE_BATCH2D_LOCKSTEP)) return NSWE_EINVAL;
+  ctx->batch2d_lockstep = mode == NSWE_BATCH2D_LOCKSTEP ? 1 : 0;
   return NSWE_OK;
 }
 
@@ -1046,6 +1019,26 @@ nswe_status nswe_mg_vcycle(nswe_ctx ctx, nswe_prob prob, int level, int nb, cons
                  cudaSuccess
              ? NSWE_OK
              : NSWE_ECUDA;
+}
+
+nswe_status nswe_mg_smooth(nswe_ctx ctx, nswe_prob prob, int level, int nb, const double *J, const double *R,
+                           double *dU, const nswe_params *params, int colour_major, int *launches) {
+  if (!ctx || !prob || prob->ctx != ctx || !J || !R || !dU || level < 0 || level >= prob->levels) return NSWE_EINVAL;
+  if (prob->dim != 2 || (nb != 9 && nb != 21) || (colour_major != 0 && colour_major != 1) ||
+      (colour_major && nb != 9))
+    return NSWE_EINVAL;
+  nswe_status st = check_params(params, nullptr, 0);
+  if (st != NSWE_OK) return st;
+  DeviceGuard dg(ctx->device);
+  const Level2Dev &L = prob->host2.lev[level];
+  const int stc = nb == 21 ? ST_J21 : ST_J9;
+  Lev2<double> Lv{L.Nx, L.Ny, const_cast<double *>(J), L.Dinv, const_cast<double *>(R), dU, colour_major};
+  int count = 0;
+  if (launch2_dinv<double>(L.Nx, L.Ny, stc, J, L.Dinv, colour_major, ctx->stream) != cudaSuccess ||
+      smooth2<double>(Lv, stc, params->nu1, params->omega, params->colours2d, ctx->stream, &count) != cudaSuccess)
+    return NSWE_ECUDA;
+  if (launches) *launches = count;
+  return NSWE_OK;
 }
 
 // Batched Algorithm 3; params[each ? i : 0] are problem i's parameters.

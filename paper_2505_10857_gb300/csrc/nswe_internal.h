@@ -155,6 +155,77 @@ cudaError_t launch2_vcycle_tail(const Tail2<T> &t, int nu1, int nu2, double omeg
 cudaError_t launch2_interp(const ProbDev2 *p, int coarse_level, int nc, const double *Uc, double *Uf,
                            cudaStream_t s);
 
+// ---------------------------------------------------------------- batched 2D
+// Lockstep batches of 2D problems: every phase of a Newton step and every
+// colour pass of its V-cycles is one launch over all problems of the batch.
+// A problem owns the launch's blocks [b0, b0 + nb) (the instance -> tile
+// map); inside them the same device code as the single-problem kernels runs
+// on that problem's arrays, with the same per-problem block count where the
+// result depends on it (the residual's partial sums), so a batched solve is
+// the same bits as the problem solved alone. done[prob] != 0 (a problem that
+// has converged on its current nested level) skips the problem's blocks.
+template <typename T>
+struct BTask2 {
+  int b0, nb, prob;      // blocks [b0, b0 + nb) of the launch; the problem's index in the batch
+  int Nx, Ny, st, cm;    // the level: grid, stencil, storage of J and Dinv (blk_pos)
+  T *J, *Dinv, *R, *dU;  // its multigrid arrays (R: the right-hand side in T)
+  T *Jc, *Rc, *dUc;      // the next coarser level's: Galerkin operator, restriction, prolongation
+  const ProbDev2 *P;     // residual / Jacobian / update: the problem and its nested level
+  int level, frozen, msplit;
+  double *U, *R64;       // state and FP64 residual of the Newton level
+  double *partials;      // residual partial sums (nb of them)
+  float *R32;            // FP32 copy of R64 (mixed precision)
+  double eps, alpha, tau;
+  T *A, *x;              // dense coarsest system and its solve buffer
+  int *piv;
+};
+// Launchers: tasks is a DEVICE array of ntask tasks sorted by b0, blocks the
+// launch's grid (the sum of their nb), done / flags / res DEVICE arrays
+// indexed by the task's prob.
+template <typename T>
+struct Batch2Launch {
+  const BTask2<T> *tasks;
+  int ntask, blocks;
+};
+cudaError_t launchb2_residual(const Batch2Launch<double> &b, const int *done, double *res, cudaStream_t s);
+template <typename TJ>
+cudaError_t launchb2_jacobian(const Batch2Launch<TJ> &b, const int *done, int kind, bool frozen, cudaStream_t s);
+constexpr int kB2JacItems = 0, kB2JacCells = 1;  // launchb2_jacobian kinds
+int b2_jacobian_cell_threads();
+cudaError_t launchb2_to_f32(const Batch2Launch<float> &b, const int *done, cudaStream_t s);
+template <typename T>
+cudaError_t launchb2_zero_du(const Batch2Launch<T> &b, const int *done, cudaStream_t s);
+template <typename T>
+cudaError_t launchb2_coarse_op(const Batch2Launch<T> &b, const int *done, cudaStream_t s);
+template <typename T>
+cudaError_t launchb2_dinv(const Batch2Launch<T> &b, const int *done, cudaStream_t s);
+// one colour pass (mode, Kc, col, reps as launch2_sor) of every task; all
+// tasks of the launch share the stencil st
+template <typename T>
+cudaError_t launchb2_sor(const Batch2Launch<T> &b, const int *done, int st, double omega, int mode, int Kc, int col,
+                         int reps, cudaStream_t s);
+constexpr int kB2SorThreads = 128, kB2SorCellsPerBlock = 40;  // three lanes per cell, ten cells per warp
+template <typename T>
+cudaError_t launchb2_restrict(const Batch2Launch<T> &b, const int *done, cudaStream_t s);
+template <typename T>
+cudaError_t launchb2_prolong(const Batch2Launch<T> &b, const int *done, cudaStream_t s);
+// one block per task: the tail of each task's V-cycle (tails[i] for tasks[i])
+template <typename T>
+cudaError_t launchb2_vcycle_tail(const Tail2<T> *tails, const BTask2<T> *tasks, int ntask, const int *done, int nu1,
+                                 int nu2, double omega, int Kc, cudaStream_t s);
+template <typename T>
+cudaError_t launchb2_dense_factor(const Batch2Launch<T> &zero, const Batch2Launch<T> &scatter, const BTask2<T> *tasks,
+                                  int ntask, const int *done, int *flags, cudaStream_t s);
+template <typename T>
+cudaError_t launchb2_dense_solve(const BTask2<T> *tasks, int ntask, const int *done, cudaStream_t s);
+template <typename T>
+cudaError_t launchb2_update(const Batch2Launch<T> &b, const int *done, int *flags, cudaStream_t s);
+int b2_grid(long items);  // blocks of kThreads for `items` grid-stride items (as the single launches)
+// Lockstep batched 2D solves (nswe_batch2d.cu): problems grouped by precision,
+// Jacobian stencil and smoothing schedule; prms[each ? i : 0] are problem i's.
+nswe_status solve2d_lockstep(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
+                             double *const *Us, const nswe_params *prms, bool each, nswe_info *infos);
+
 // One solve of a batch.
 struct SolveTask {
   const ProbDev *prob;
@@ -208,3 +279,47 @@ size_t prob2d_arena_doubles(int Nx, int Ny, int levels);
 size_t prob2d_device_bytes(int Nx, int Ny, int levels);
 
 }  // namespace nswe
+
+// A context and a problem of the C ABI (include/nswe.h): host-side handles
+// of device resources, shared by the host translation units.
+struct nswe_ctx_s {
+  int device;
+  cudaStream_t stream;
+  double *partials;      // [1024] per-block partial sums of res
+  int *status;           // device status word of standalone V-cycles
+  nswe::SolveTask *tasks;      // device task array
+  nswe_info *infos;      // device info records
+  nswe_params *prms;     // device per-task parameters (nswe_newton_solve_batch_each)
+  int cap;               // capacity of tasks / infos / prms
+  int solve_shape[2];    // launch shape of the 1D solve kernel per precision
+  int batch2d_lockstep = 0;  // 2D batches: 0 concurrent per-problem solves, 1 lockstep batched launches
+  int cm2d_min_cells = 131072;  // 2D Newton levels of at least this many cells store J9 colour-major
+  int jac2d_cell_min = nswe::kJac2CellMinDefault;  // 2D levels from which the per-cell Jacobian kernel runs
+};
+
+struct nswe_prob_s {
+  nswe_ctx ctx;
+  int dim;               // 1 or 2
+  int N, levels;         // 1D: cells of the finest level
+  double x0, x1, g;
+  nswe::ProbDev host;          // device pointers, host copy
+  nswe::ProbDev *dev;          // device copy
+  double *arena;
+  size_t geo_doubles;    // geometry region at the front of the arena
+  double *stage;         // 1D: pinned staging of the geometry upload [geo_doubles]
+  cudaEvent_t staged;    // 1D: the last upload from `stage` has been copied
+  // 2D
+  int Nx, Ny;
+  nswe::ProbDev2 host2;
+  nswe::ProbDev2 *dev2;
+  double *dense;         // coarsest dense LU factors [N3][N3]
+  int *piv;              // [N3]
+  double *xbuf;          // [N3]
+  int *flag;             // device flag (zero pivot / non-positive depth)
+  double *res_dev;       // device scalar
+  double *res_host;      // pinned host scalar
+  int *flag_host;        // pinned host flag
+  cudaStream_t cap;      // 2D: stream on which a Newton step is captured
+  double *partials2;     // 2D: [1024] per-block partial sums of res (per problem, so
+                         // that several 2D solves can run concurrently)
+};

@@ -362,14 +362,16 @@ __device__ double block_sum2(double v, double *red) {
 
 // ---------------------------------------------------------------------------- kernels
 
-__global__ void __launch_bounds__(kThreads) k2_residual(const ProbDev2 *P, int level, const double *U, double *R,
-                                                        double *partials) {
+// The residual of Eq. 20 by block `bid` of `nblk` (grid-stride over cells),
+// its l1 partial sum stored in partials[bid].
+__device__ __forceinline__ void residual_blocks2(const ProbDev2 *P, int level, const double *U, double *R,
+                                                 double *partials, int bid, int nblk) {
   __shared__ double red[33];
   const Geo2 G = make_geo2(*P, level);
   const int n = G.Nx * G.Ny;
   const Pert np{-1, 0, 0.0};
   double acc = 0.0;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+  for (int c = bid * blockDim.x + threadIdx.x; c < n; c += nblk * blockDim.x) {
     double r[3];
     local_residual2<false>(G, U, c % G.Nx, c / G.Nx, np, r);
     R[c] = r[0];
@@ -378,7 +380,12 @@ __global__ void __launch_bounds__(kThreads) k2_residual(const ProbDev2 *P, int l
     acc += fabs(r[0]) + fabs(r[1]) + fabs(r[2]);
   }
   const double s = block_sum2(acc, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (threadIdx.x == 0) partials[bid] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k2_residual(const ProbDev2 *P, int level, const double *U, double *R,
+                                                        double *partials) {
+  residual_blocks2(P, level, U, R, partials, blockIdx.x, gridDim.x);
 }
 
 __global__ void k2_finish(const double *partials, int nparts, int n, double *res) {
@@ -394,14 +401,14 @@ __global__ void k2_finish(const double *partials, int nparts, int n, double *res
 // msplit: one item per (cell, block, component m) instead of per (cell,
 // block), for small grids where the kernel is bound by each thread's chain.
 template <typename TJ, bool FROZEN>
-__global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int level, int st, const double *U,
-                                                        double eps, double alpha, const double *R, TJ *J,
-                                                        int msplit, int cm) {
+__device__ __forceinline__ void jacobian_items2(const ProbDev2 *P, int level, int st, const double *U, double eps,
+                                                double alpha, const double *R, TJ *J, int msplit, int cm, int first,
+                                                int stride) {
   const Geo2 G = make_geo2(*P, level);
   const int n = G.Nx * G.Ny, K = st_size(st), kc = st_center(st);
   const double ieps = 1.0 / eps;
   const int items = n * K * (msplit ? 3 : 1);
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+  for (int it = first; it < items; it += stride) {
     const int c = it % n, kq = it / n, k = msplit ? kq % K : kq, i = c % G.Nx, j = c / G.Nx;
     const int m0 = msplit ? kq / K : 0, m1 = msplit ? m0 + 1 : 3;
     const size_t S = blk_stride(cm, G.Nx, G.Ny), pc = blk_pos(cm, G.Nx, G.Ny, i, j);
@@ -464,11 +471,20 @@ __global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int l
   }
 }
 
+template <typename TJ, bool FROZEN>
+__global__ void __launch_bounds__(kThreads) k2_jacobian(const ProbDev2 *P, int level, int st, const double *U,
+                                                        double eps, double alpha, const double *R, TJ *J,
+                                                        int msplit, int cm) {
+  jacobian_items2<TJ, FROZEN>(P, level, st, U, eps, alpha, R, J, msplit, cm, blockIdx.x * blockDim.x + threadIdx.x,
+                              gridDim.x * blockDim.x);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, int cm) {
+__device__ __forceinline__ void coarse_op_cells2(int Nx, int Ny, int st, const T *Jf, T *Jc, int cm, int first,
+                                                 int stride) {
   const int Ncx = Nx / 2, Ncy = Ny / 2, nc = Ncx * Ncy, K = st_size(st), cs = st_coarse(st), Kc = st_size(cs);
   const size_t Sf = blk_stride(cm, Nx, Ny);
-  for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += gridDim.x * blockDim.x) {
+  for (int cc = first; cc < nc; cc += stride) {
     const int I = cc % Ncx, Jy = cc / Ncx;
     T acc[9][9];
     for (int t = 0; t < Kc; ++t)
@@ -494,10 +510,16 @@ __global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_dinv(int Nx, int Ny, int st, const T *J, T *Dinv, int cm) {
+__global__ void __launch_bounds__(kThreads) k2_coarse_op(int Nx, int Ny, int st, const T *Jf, T *Jc, int cm) {
+  coarse_op_cells2<T>(Nx, Ny, st, Jf, Jc, cm, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void dinv_cells2(int Nx, int Ny, int st, const T *J, T *Dinv, int cm, int first,
+                                            int stride) {
   const int kc = st_center(st), ncell = Nx * Ny;
   const size_t n = blk_stride(cm, Nx, Ny);  // the stride of J and Dinv
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ncell; q += gridDim.x * blockDim.x) {
+  for (int q = first; q < ncell; q += stride) {
     const size_t c = blk_pos(cm, Nx, Ny, q % Nx, q / Nx);
     T a[9];
     for (int e = 0; e < 9; ++e) a[e] = J[(size_t)(kc * 9 + e) * n + c];
@@ -513,6 +535,11 @@ __global__ void __launch_bounds__(kThreads) k2_dinv(int Nx, int Ny, int st, cons
     Dinv[7 * (size_t)n + c] = (a[1] * a[6] - a[0] * a[7]) / det;
     Dinv[8 * (size_t)n + c] = (a[0] * a[4] - a[1] * a[3]) / det;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_dinv(int Nx, int Ny, int st, const T *J, T *Dinv, int cm) {
+  dinv_cells2<T>(Nx, Ny, st, J, Dinv, cm, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Block SOR update (Eq. 22) of cell (i, j), relaxation applied reps times
@@ -757,9 +784,9 @@ __global__ void __launch_bounds__(kThreads) k2_zero(long count, T *A) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_scatter(int Nx, int Ny, int st, const T *J, T *A) {
+__device__ __forceinline__ void scatter_items2(int Nx, int Ny, int st, const T *J, T *A, int first, int stride) {
   const int n = Nx * Ny, N3 = 3 * n, K = st_size(st);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * K; t += gridDim.x * blockDim.x) {
+  for (int t = first; t < n * K; t += stride) {
     const int c = t % n, k = t / n, i = c % Nx, j = c / Nx;
     const int p = i + st_off(st, k, 0), q = j + st_off(st, k, 1);
     if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
@@ -769,10 +796,16 @@ __global__ void __launch_bounds__(kThreads) k2_scatter(int Nx, int Ny, int st, c
   }
 }
 
-// LU with partial pivoting (ties to the lowest row) of A (n x n, global
-// memory), one thread block. piv[k] = pivot row; flag = 1 on an exact zero pivot.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_lu(int N3, T *A, int *piv, int *flag) {
+__global__ void __launch_bounds__(kThreads) k2_scatter(int Nx, int Ny, int st, const T *J, T *A) {
+  scatter_items2<T>(Nx, Ny, st, J, A, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// LU with partial pivoting (ties to the lowest row) of A (n x n, global
+// memory), by the calling thread block. piv[k] = pivot row; flag = 1 on an
+// exact zero pivot.
+template <typename T>
+__device__ void lu_block2(int N3, T *A, int *piv, int *flag) {
   __shared__ T sv[32];
   __shared__ int si[32];
   __shared__ int s_p;
@@ -832,6 +865,11 @@ __global__ void __launch_bounds__(kThreads) k2_lu(int N3, T *A, int *piv, int *f
     }
     __syncthreads();
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_lu(int N3, T *A, int *piv, int *flag) {
+  lu_block2<T>(N3, A, piv, flag);
 }
 
 // dU = -A^{-1} R with the factors (one warp; unknown 3c+m).
@@ -912,8 +950,7 @@ __device__ void smooth_block(const Tail2<T> &t, int l, int steps, double omega, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTail2Threads, 1) k2_vcycle_tail(Tail2<T> t, int nu1, int nu2, double omega,
-                                                                  int Kc) {
+__device__ void vcycle_tail_block2(const Tail2<T> &t, int nu1, int nu2, double omega, int Kc) {
   for (int l = t.ls; l < t.L; ++l) {
     smooth_block<T>(t, l, nu1, omega, Kc);
     restrict_cells2<T>(t.Nx[l], t.Ny[l], t.st[l], t.J[l], t.R[l], t.dU[l], t.R[l + 1], t.dU[l + 1], threadIdx.x,
@@ -929,20 +966,32 @@ __global__ void __launch_bounds__(kTail2Threads, 1) k2_vcycle_tail(Tail2<T> t, i
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kTail2Threads, 1) k2_vcycle_tail(Tail2<T> t, int nu1, int nu2, double omega,
+                                                                  int Kc) {
+  vcycle_tail_block2<T>(t, nu1, nu2, omega, Kc);
+}
+
 __global__ void __launch_bounds__(kThreads) k2_to_f32(long count, const double *src, float *dst) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x)
     dst[t] = float(src[t]);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k2_update(int n, double *U, const T *dU, double tau, int *flag) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void update_cells2(int n, double *U, const T *dU, double tau, int *flag, int first,
+                                              int stride) {
+  for (int c = first; c < n; c += stride) {
     const double h = U[c] + tau * double(dU[c]);
     U[c] = h;
     U[n + c] += tau * double(dU[n + c]);
     U[2 * n + c] += tau * double(dU[2 * n + c]);
     if (!(h > 0.0)) atomicOr(flag, 1);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k2_update(int n, double *U, const T *dU, double tau, int *flag) {
+  update_cells2<T>(n, U, dU, tau, flag, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(kThreads) k2_interp(const ProbDev2 *P, int coarse_level, const double *Uc,
@@ -999,14 +1048,14 @@ cudaError_t launch2_residual(const ProbDev2 *p, int level, int n, const double *
 // (kJac2CellMinDefault).
 constexpr int kJacCellThreads = 128;
 template <typename TJ, bool FROZEN>
-__global__ void __launch_bounds__(kJacCellThreads) k2_jacobian_cell(const ProbDev2 *P, int level, int st,
-                                                                  const double *U, double eps, double alpha,
-                                                                  const double *R, TJ *J, int cm) {
+__device__ __forceinline__ void jacobian_cells2(const ProbDev2 *P, int level, int st, const double *U, double eps,
+                                                double alpha, const double *R, TJ *J, int cm, int first,
+                                                int stride) {
   const Geo2 G = make_geo2(*P, level);
   const int n = G.Nx * G.Ny, K = st_size(st), kc = st_center(st);
   const double ieps = 1.0 / eps;
   const Pert none{-1, 0, 0.0};
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+  for (int c = first; c < n; c += stride) {
     const int i = c % G.Nx, j = c / G.Nx;
     const size_t S = blk_stride(cm, G.Nx, G.Ny), pc = blk_pos(cm, G.Nx, G.Ny, i, j);
     const double R0[3] = {R[c], R[n + c], R[2 * n + c]};
@@ -1073,6 +1122,14 @@ __global__ void __launch_bounds__(kJacCellThreads) k2_jacobian_cell(const ProbDe
       }
     }
   }
+}
+
+template <typename TJ, bool FROZEN>
+__global__ void __launch_bounds__(kJacCellThreads) k2_jacobian_cell(const ProbDev2 *P, int level, int st,
+                                                                  const double *U, double eps, double alpha,
+                                                                  const double *R, TJ *J, int cm) {
+  jacobian_cells2<TJ, FROZEN>(P, level, st, U, eps, alpha, R, J, cm, blockIdx.x * blockDim.x + threadIdx.x,
+                              gridDim.x * blockDim.x);
 }
 
 template <typename TJ>
@@ -1202,5 +1259,296 @@ cudaError_t launch2_interp(const ProbDev2 *p, int coarse_level, int nc, const do
   k2_interp<<<grid2(nc), kThreads, 0, s>>>(p, coarse_level, Uc, Uf);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------- batched (lockstep) kernels
+
+namespace {
+
+// The task owning this block (tasks sorted by b0) and the block's index in
+// it; null when the task's problem is masked off.
+template <typename T>
+__device__ __forceinline__ const BTask2<T> *btask2(const BTask2<T> *tasks, int ntask, const int *done, int &lb) {
+  int lo = 0, hi = ntask - 1;
+  const int b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].b0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const BTask2<T> *t = tasks + lo;
+  lb = b - t->b0;
+  return (done && done[t->prob]) ? nullptr : t;
+}
+
+__global__ void __launch_bounds__(kThreads) kb2_residual(const BTask2<double> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<double> *t = btask2(tasks, ntask, done, lb);
+  if (t) residual_blocks2(t->P, t->level, t->U, t->R64, t->partials, lb, t->nb);
+}
+
+// One task per block: res[prob] = (sum of its partials, in order) / cells (as k2_finish).
+__global__ void kb2_finish(const BTask2<double> *tasks, int ntask, const int *done, double *res) {
+  const BTask2<double> &t = tasks[blockIdx.x];
+  if ((done && done[t.prob]) || threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < t.nb; ++i) s += t.partials[i];
+  res[t.prob] = s / (t.Nx * t.Ny);
+}
+
+template <typename TJ, bool FROZEN>
+__global__ void __launch_bounds__(kThreads) kb2_jacobian(const BTask2<TJ> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<TJ> *t = btask2(tasks, ntask, done, lb);
+  if (t)
+    jacobian_items2<TJ, FROZEN>(t->P, t->level, t->st, t->U, t->eps, t->alpha, t->R64, t->J, t->msplit, t->cm,
+                                lb * blockDim.x + threadIdx.x, t->nb * blockDim.x);
+}
+
+template <typename TJ, bool FROZEN>
+__global__ void __launch_bounds__(kJacCellThreads) kb2_jacobian_cell(const BTask2<TJ> *tasks, int ntask,
+                                                                   const int *done) {
+  int lb;
+  const BTask2<TJ> *t = btask2(tasks, ntask, done, lb);
+  if (t)
+    jacobian_cells2<TJ, FROZEN>(t->P, t->level, t->st, t->U, t->eps, t->alpha, t->R64, t->J, t->cm,
+                                lb * blockDim.x + threadIdx.x, t->nb * blockDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads) kb2_to_f32(const BTask2<float> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<float> *t = btask2(tasks, ntask, done, lb);
+  if (!t) return;
+  const long count = 3L * t->Nx * t->Ny;
+  for (long c = lb * (long)blockDim.x + threadIdx.x; c < count; c += (long)t->nb * blockDim.x)
+    t->R32[c] = float(t->R64[c]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_zero_du(const BTask2<T> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (!t) return;
+  const long count = 3L * t->Nx * t->Ny;
+  for (long c = lb * (long)blockDim.x + threadIdx.x; c < count; c += (long)t->nb * blockDim.x) t->dU[c] = T(0.0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_coarse_op(const BTask2<T> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (t) coarse_op_cells2<T>(t->Nx, t->Ny, t->st, t->J, t->Jc, t->cm, lb * blockDim.x + threadIdx.x, t->nb * blockDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_dinv(const BTask2<T> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (t) dinv_cells2<T>(t->Nx, t->Ny, t->st, t->J, t->Dinv, t->cm, lb * blockDim.x + threadIdx.x, t->nb * blockDim.x);
+}
+
+template <typename T, int STC>
+__global__ void __launch_bounds__(kB2SorThreads) kb2_sor_split(const BTask2<T> *tasks, int ntask, const int *done,
+                                                               int st, double omega, int mode, int Kc, int col,
+                                                               int reps) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (t)
+    sor_pass_split<T, STC>(t->Nx, t->Ny, st, t->J, t->Dinv, t->R, t->dU, omega, mode, Kc, col, reps,
+                           (lb * blockDim.x + threadIdx.x) >> 5, (t->nb * blockDim.x) >> 5, t->cm);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_restrict(const BTask2<T> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (t)
+    restrict_cells2<T>(t->Nx, t->Ny, t->st, t->J, t->R, t->dU, t->Rc, t->dUc, lb * blockDim.x + threadIdx.x,
+                       t->nb * blockDim.x, t->cm);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_prolong(const BTask2<T> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (t) prolong_cells2<T>(t->Nx, t->Ny, t->dU, t->dUc, lb * blockDim.x + threadIdx.x, t->nb * blockDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTail2Threads, 1) kb2_vcycle_tail(const Tail2<T> *tails, const BTask2<T> *tasks,
+                                                                   const int *done, int nu1, int nu2, double omega,
+                                                                   int Kc) {
+  if (done && done[tasks[blockIdx.x].prob]) return;
+  vcycle_tail_block2<T>(tails[blockIdx.x], nu1, nu2, omega, Kc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_dense_zero(const BTask2<T> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (!t) return;
+  const long N3 = 3L * t->Nx * t->Ny, count = N3 * N3;
+  for (long c = lb * (long)blockDim.x + threadIdx.x; c < count; c += (long)t->nb * blockDim.x) t->A[c] = T(0.0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_scatter(const BTask2<T> *tasks, int ntask, const int *done) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (t) scatter_items2<T>(t->Nx, t->Ny, t->st, t->J, t->A, lb * blockDim.x + threadIdx.x, t->nb * blockDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_lu(const BTask2<T> *tasks, const int *done, int *flags) {
+  const BTask2<T> &t = tasks[blockIdx.x];
+  if (done && done[t.prob]) return;
+  lu_block2<T>(3 * t.Nx * t.Ny, t.A, t.piv, flags + t.prob);
+}
+
+template <typename T>
+__global__ void kb2_lu_solve(const BTask2<T> *tasks, const int *done) {
+  const BTask2<T> &t = tasks[blockIdx.x];
+  if ((done && done[t.prob]) || threadIdx.x >= 32) return;
+  lu_solve_warp<T>(t.Nx * t.Ny, t.A, t.piv, t.R, t.x, t.dU);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) kb2_update(const BTask2<T> *tasks, int ntask, const int *done,
+                                                       int *flags) {
+  int lb;
+  const BTask2<T> *t = btask2(tasks, ntask, done, lb);
+  if (t)
+    update_cells2<T>(t->Nx * t->Ny, t->U, t->dU, t->tau, flags + t->prob, lb * blockDim.x + threadIdx.x,
+                     t->nb * blockDim.x);
+}
+
+}  // namespace
+
+int b2_grid(long items) { return grid2(items); }
+int b2_jacobian_cell_threads() { return kJacCellThreads; }
+
+cudaError_t launchb2_residual(const Batch2Launch<double> &b, const int *done, double *res, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_residual<<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  kb2_finish<<<b.ntask, 32, 0, s>>>(b.tasks, b.ntask, done, res);
+  return cudaGetLastError();
+}
+
+template <typename TJ>
+cudaError_t launchb2_jacobian(const Batch2Launch<TJ> &b, const int *done, int kind, bool frozen, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  if (kind == kB2JacCells) {
+    if (frozen) kb2_jacobian_cell<TJ, true><<<b.blocks, kJacCellThreads, 0, s>>>(b.tasks, b.ntask, done);
+    else kb2_jacobian_cell<TJ, false><<<b.blocks, kJacCellThreads, 0, s>>>(b.tasks, b.ntask, done);
+  } else {
+    if (frozen) kb2_jacobian<TJ, true><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+    else kb2_jacobian<TJ, false><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launchb2_to_f32(const Batch2Launch<float> &b, const int *done, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_to_f32<<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_zero_du(const Batch2Launch<T> &b, const int *done, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_zero_du<T><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_coarse_op(const Batch2Launch<T> &b, const int *done, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_coarse_op<T><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_dinv(const Batch2Launch<T> &b, const int *done, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_dinv<T><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_sor(const Batch2Launch<T> &b, const int *done, int st, double omega, int mode, int Kc, int col,
+                         int reps, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  if (NSWE_SOR_UNROLL && st == ST_J9)
+    kb2_sor_split<T, ST_J9><<<b.blocks, kB2SorThreads, 0, s>>>(b.tasks, b.ntask, done, st, omega, mode, Kc, col, reps);
+  else if (NSWE_SOR_UNROLL && st == ST_P5)
+    kb2_sor_split<T, ST_P5><<<b.blocks, kB2SorThreads, 0, s>>>(b.tasks, b.ntask, done, st, omega, mode, Kc, col, reps);
+  else
+    kb2_sor_split<T, -1><<<b.blocks, kB2SorThreads, 0, s>>>(b.tasks, b.ntask, done, st, omega, mode, Kc, col, reps);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_restrict(const Batch2Launch<T> &b, const int *done, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_restrict<T><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_prolong(const Batch2Launch<T> &b, const int *done, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_prolong<T><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_vcycle_tail(const Tail2<T> *tails, const BTask2<T> *tasks, int ntask, const int *done, int nu1,
+                                 int nu2, double omega, int Kc, cudaStream_t s) {
+  if (ntask == 0) return cudaSuccess;
+  kb2_vcycle_tail<T><<<ntask, kTail2Threads, 0, s>>>(tails, tasks, done, nu1, nu2, omega, Kc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_dense_factor(const Batch2Launch<T> &zero, const Batch2Launch<T> &scatter, const BTask2<T> *tasks,
+                                  int ntask, const int *done, int *flags, cudaStream_t s) {
+  if (ntask == 0) return cudaSuccess;
+  kb2_dense_zero<T><<<zero.blocks, kThreads, 0, s>>>(zero.tasks, zero.ntask, done);
+  kb2_scatter<T><<<scatter.blocks, kThreads, 0, s>>>(scatter.tasks, scatter.ntask, done);
+  kb2_lu<T><<<ntask, kThreads, 0, s>>>(tasks, done, flags);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_dense_solve(const BTask2<T> *tasks, int ntask, const int *done, cudaStream_t s) {
+  if (ntask == 0) return cudaSuccess;
+  kb2_lu_solve<T><<<ntask, 32, 0, s>>>(tasks, done);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launchb2_update(const Batch2Launch<T> &b, const int *done, int *flags, cudaStream_t s) {
+  if (b.ntask == 0) return cudaSuccess;
+  kb2_update<T><<<b.blocks, kThreads, 0, s>>>(b.tasks, b.ntask, done, flags);
+  return cudaGetLastError();
+}
+
+#define NSWE_B2_INSTANTIATE(T)                                                                                     \
+  template cudaError_t launchb2_jacobian<T>(const Batch2Launch<T> &, const int *, int, bool, cudaStream_t);       \
+  template cudaError_t launchb2_zero_du<T>(const Batch2Launch<T> &, const int *, cudaStream_t);                   \
+  template cudaError_t launchb2_coarse_op<T>(const Batch2Launch<T> &, const int *, cudaStream_t);                 \
+  template cudaError_t launchb2_dinv<T>(const Batch2Launch<T> &, const int *, cudaStream_t);                      \
+  template cudaError_t launchb2_sor<T>(const Batch2Launch<T> &, const int *, int, double, int, int, int, int,     \
+                                       cudaStream_t);                                                             \
+  template cudaError_t launchb2_restrict<T>(const Batch2Launch<T> &, const int *, cudaStream_t);                  \
+  template cudaError_t launchb2_prolong<T>(const Batch2Launch<T> &, const int *, cudaStream_t);                   \
+  template cudaError_t launchb2_vcycle_tail<T>(const Tail2<T> *, const BTask2<T> *, int, const int *, int, int,   \
+                                               double, int, cudaStream_t);                                        \
+  template cudaError_t launchb2_dense_factor<T>(const Batch2Launch<T> &, const Batch2Launch<T> &,                 \
+                                                const BTask2<T> *, int, const int *, int *, cudaStream_t);        \
+  template cudaError_t launchb2_dense_solve<T>(const BTask2<T> *, int, const int *, cudaStream_t);                \
+  template cudaError_t launchb2_update<T>(const Batch2Launch<T> &, const int *, int *, cudaStream_t);
+NSWE_B2_INSTANTIATE(double)
+NSWE_B2_INSTANTIATE(float)
+#undef NSWE_B2_INSTANTIATE
 
 }  // namespace nswe

@@ -552,6 +552,25 @@ def bump_channel_2d(k, Nx=64, Ny=32, levels=4, start_level=-1):
                            meta={"case": "bump-channel", "seed": 5000 + k, "bump": (A, R, xc, yc), "q": q})
 
 
+def gauss_bump_channel_2d(k, Nx=128, Ny=64, levels=5, start_level=-1):
+    """Seeded subcritical 2D channel with a Gaussian bottom bump (seed
+    6000 + k), the bump family of the batched 2D serving workload: the
+    channel of Section 5.2.1, [-4, 4] x [0, 4], discharge hu ~U[0.75, 1.25]
+    at x = -4, depth 1 at x = 4, reflective side walls, with
+    b = A exp(-((x - xc)^2 + (y - yc)^2) / w^2), A ~U[0.1, 0.3],
+    w ~U[0.5, 1.0], centre ~U([-1.5, 1.5] x [1.5, 2.5]); guess h = 1,
+    hu = the discharge, hv = 0 (as Eq. 30) on start_level; g = 9.812."""
+    rng = np.random.default_rng(6000 + k)
+    A, w = float(rng.uniform(0.1, 0.3)), float(rng.uniform(0.5, 1.0))
+    xc, yc = float(rng.uniform(-1.5, 1.5)), float(rng.uniform(1.5, 2.5))
+    q = float(rng.uniform(0.75, 1.25))
+    st = np.array([[0.0, q, 0.0], [1.0, 0.0, 0.0], [0, 0, 0], [0, 0, 0]])
+    return make_problem_2d(Nx, Ny, levels, -4.0, 4.0, 0.0, 4.0, G_PAPER, bottom2d_gaussians([(A, xc, yc, w)]),
+                           (BC2_DISCHARGE, BC2_DEPTH, BC2_REFLECT, BC2_REFLECT), st,
+                           lambda X, Y: (1.0, q, 0.0), start_level=start_level,
+                           meta={"case": "gauss-bump-channel", "seed": 6000 + k, "bump": (A, xc, yc, w), "q": q})
+
+
 def wedge(Nx, Ny, levels, theta_deg=8.95, x1=5.0, y1=2.0, x_wall=1.0, speed=8.57, start_level=-1, meta=None):
     """Hydraulic jump over a wedge in the rotated frame of Section 5.2.2:
     inflow (h, u, v) = (1, speed cos(-theta), speed sin(-theta)) on the left

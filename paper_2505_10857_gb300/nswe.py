@@ -111,10 +111,12 @@ EXPORTS = {
     "nswe_jacobian_frozen": (_i, [_vp, _vp, _i, _i, _dp, _d, _d, _dp, _dp, _dp]),
     "nswe_ctx_set_colour_major_2d": (_i, [_vp, _i]),
     "nswe_ctx_set_jacobian_cells_2d": (_i, [_vp, _i]),
+    "nswe_ctx_set_batch_2d": (_i, [_vp, _i]),
     "nswe_prob_set_flux_1d": (_i, [_vp, _vp, _i]),
     "nswe_prob_set_geometry_batch_1d": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                              ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
     "nswe_mg_vcycle_f32": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params)]),
+    "nswe_mg_smooth": (_i, [_vp, _vp, _i, _i, _dp, _dp, _dp, ctypes.POINTER(Params), _i, ctypes.POINTER(_i)]),
     "nswe_newton_solve": (_i, [_vp, _vp, _dp, _dp, ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                      ctypes.POINTER(Params), ctypes.POINTER(Info)]),
@@ -122,6 +124,7 @@ EXPORTS = {
                                      ctypes.POINTER(Params), ctypes.POINTER(Info)]),
     "nswe_newton_solve_noalloc": (_i, [_i, _vp, _i, _i, _d, _d, _d, _dp, _dp, ctypes.POINTER(BC1D),
                                        ctypes.POINTER(BC1D), _dp, _dp, ctypes.POINTER(Params), _vp]),
+    "nswe_probe_fma": (_i, [_vp, _i, _i, _i, _i, _vp, ctypes.POINTER(_d)]),
     "nswe_solve_shape_count": (_i, []),
     "nswe_solve_shape_info": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nswe_ctx_set_solve_shape": (_i, [_vp, _i, _i]),
@@ -414,6 +417,15 @@ def nswe_ctx_set_colour_major_2d(ctx, min_cells):
     _check("nswe_ctx_set_colour_major_2d", lib().nswe_ctx_set_colour_major_2d(ctx.h, int(min_cells)))
 
 
+BATCH2D_CONCURRENT, BATCH2D_LOCKSTEP = 0, 1
+
+
+def nswe_ctx_set_batch_2d(ctx, mode):
+    """How batches of 2D problems run: BATCH2D_CONCURRENT (per-problem
+    streams) or BATCH2D_LOCKSTEP (shared launches); see include/nswe.h."""
+    _check("nswe_ctx_set_batch_2d", lib().nswe_ctx_set_batch_2d(ctx.h, int(mode)))
+
+
 def nswe_ctx_set_jacobian_cells_2d(ctx, min_cells):
     """2D levels of at least min_cells cells take the per-cell Jacobian kernel (<0: never)."""
     _check("nswe_ctx_set_jacobian_cells_2d", lib().nswe_ctx_set_jacobian_cells_2d(ctx.h, int(min_cells)))
@@ -430,6 +442,26 @@ def nswe_mg_vcycle(ctx, prob, level, nb, J, R, dU, prm: Params):
     _check_level_sizes("nswe_mg_vcycle", prob, level, nb, J=J, R=R, dU=dU)
     _check("nswe_mg_vcycle", lib().nswe_mg_vcycle(ctx.h, prob.h, int(level), int(nb), _ptr(J), _ptr(R), _ptr(dU),
                                                   ctypes.byref(prm)))
+
+
+def colour_major_size(Nx, Ny):
+    """Cells' slots of the colour-major block layout (see nswe_mg_smooth)."""
+    return 3 * Ny * ((Nx + 2) // 3)
+
+
+def nswe_mg_smooth(ctx, prob, level, nb, J, R, dU, prm: Params, colour_major=False):
+    """prm.nu1 steps of the 2D multicolour block SOR on one level (see
+    include/nswe.h); returns the number of colour-pass launches."""
+    _check_level_sizes("nswe_mg_smooth", prob, level, None, R=R, dU=dU)
+    if isinstance(prob, Problem2D) and 0 <= int(level) < prob.levels:
+        nx, ny = prob.Nx >> int(level), prob.Ny >> int(level)
+        slots = colour_major_size(nx, ny) if colour_major else nx * ny
+        if J.numel() < int(nb) * 9 * slots:
+            raise ValueError(f"nswe_mg_smooth: J holds {J.numel()} values; level {level} needs {int(nb) * 9 * slots}")
+    n = ctypes.c_int(0)
+    _check("nswe_mg_smooth", lib().nswe_mg_smooth(ctx.h, prob.h, int(level), int(nb), _ptr(J), _ptr(R), _ptr(dU),
+                                                  ctypes.byref(prm), int(bool(colour_major)), ctypes.byref(n)))
+    return n.value
 
 
 def nswe_jacobian_f32(ctx, prob, level, nb, U, eps, alpha, R, J, res=None):
@@ -546,6 +578,19 @@ def nswe_newton_solve_noalloc(device, stream, N, levels, x0, x1, g, sigma_face, 
     if rc:
         raise NsweError("nswe_newton_solve_noalloc", rc)
     return rc
+
+
+def nswe_probe_fma(stream, precision, blocks, threads, iters, sink) -> float:
+    """FMA throughput probe (see include/nswe.h): launches on `stream`
+    (a cudaStream_t handle) and returns the flops the launch performs; the
+    caller times it with CUDA events. `sink` is a device tensor of
+    blocks*threads float64 (FP64) or float32 (FP32) values."""
+    if sink.numel() < blocks * threads:
+        raise ValueError("sink holds fewer values than blocks * threads")
+    fl = ctypes.c_double()
+    _check("nswe_probe_fma", lib().nswe_probe_fma(_vp(stream), int(precision), int(blocks), int(threads), int(iters),
+                                                  _vp(sink.data_ptr()), ctypes.byref(fl)))
+    return fl.value
 
 
 def info_from_bytes(raw: bytes, levels=MAX_LEVELS) -> dict:

@@ -134,6 +134,46 @@ def test_vcycle_parity_2d(nswe, ctx, orc, name, level, full, colours):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
 
 
+def colour_major(J, nx, ny):
+    """J [K][9][n] cell-contiguous -> the colour-major layout of nswe_mg_smooth
+    (cell (i, j) at ((i + j) mod 3 * ny + j) * ceil(nx / 3) + i // 3)."""
+    w3 = (nx + 2) // 3
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny))
+    pos = (((i + j) % 3) * ny + j) * w3 + i // 3
+    out = np.zeros(J.shape[:2] + (3 * ny * w3,))
+    out[:, :, pos.ravel()] = J
+    return out
+
+
+@pytest.mark.parametrize("name,full,colours,cm,nu", [("bump", False, 0, False, 3), ("bump", False, 0, True, 3),
+                                                    ("wedge", False, 0, True, 4), ("bump", True, 0, False, 2),
+                                                    ("mixed", False, 5, False, 2), ("wedge", False, 3, True, 2)])
+def test_smoother_parity_2d(nswe, ctx, orc, name, full, colours, cm, nu):
+    """nswe_mg_smooth: nu multicolour block-SOR steps (Eq. 22) on the finest
+    level against the oracle's smoothing steps, with J given cell-contiguous
+    or colour-major, under both schedules."""
+    inp = problems()[name]
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    pr = orc.problem_levels2d(inp)[0]
+    U = state_for(inp, 0, 60)
+    st = orc.ST_J21 if full else orc.ST_J9
+    J, R, _ = orc.jacobian2d(pr, U, 1e-6, 3.0, st)
+    D = orc.block_inverse2d(J, st)
+    nx, ny = inp.dims(0)
+    rng = np.random.default_rng(61)
+    dU0 = 1e-3 * rng.standard_normal((3, nx * ny))
+    ref = dU0
+    for _ in range(nu):
+        ref = orc.sor_step2d(J, D, R, ref, nx, ny, st, 0.1, colours)
+    prm = nswe.params(96, inp.levels, omega=0.1, nu1=nu, nu2=nu, colours2d=colours)
+    ddU = dev(dU0)
+    launches = nswe.nswe_mg_smooth(ctx, prob, 0, J.shape[0], dev(colour_major(J, nx, ny) if cm else J), dev(R), ddU,
+                                   prm, colour_major=cm)
+    got = host(ddU)
+    assert launches > 0
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
 @pytest.mark.parametrize("case", ["bump_j9", "bump_j21", "wedge_direct", "bump_j9_directional", "wedge_frozen"])
 def test_newton_solve_parity_2d(nswe, ctx, orc, case):
     slack = 0
@@ -214,6 +254,68 @@ def test_full_size_residual_and_jacobian_sampled(nswe, ctx, orc):
                     assert abs(J[k, l * 3 + m, c] - col[l]) <= 1e-12 * abs(col[l]) + 8 * EPS64 * sc / eps
 
 
+@pytest.mark.parametrize("grid", [(96, 40), (256, 128)])
+@pytest.mark.parametrize("kind", ["j9", "j21", "j9_frozen"])
+def test_jacobian_parity_2d_large_grids(nswe, ctx, orc, grid, kind):
+    """Every cell and every block of J9, J21 and frozen J9 against the oracle
+    on the two large-grid branches of the CUDA Jacobian: 96 x 40 has more than
+    65,536 (cell, block, component) items, so each thread takes all three
+    components of one (cell, block); 256 x 128 has 32,768 cells, where one
+    thread takes one cell and reuses its unperturbed reconstruction lines."""
+    nx, ny = grid
+    levels = 3 if nx == 96 else 5  # coarsest grid within the library's 512 cells
+    inp = I.wedge(nx, ny, levels, x1=40.0, y1=30.0, x_wall=8.0, theta_deg=12.0)
+    assert nx * ny * 9 * 3 > 65536
+    prob = nswe.Problem2D.from_inputs(ctx, inp)
+    pr = orc.problem_levels2d(inp)[0]
+    U = state_for(inp, 0, 50)
+    st = orc.ST_J21 if kind == "j21" else orc.ST_J9
+    frozen = kind.endswith("frozen")
+    eps = 1e-6
+    Jref, Rref, _ = orc.jacobian2d(pr, U, eps, 3.0, st, frozen=frozen)
+    K = Jref.shape[0]
+    dR = torch.zeros((3, pr.n), dtype=torch.float64, device="cuda")
+    dJ = torch.full((K, 9, pr.n), float("nan"), dtype=torch.float64, device="cuda")
+    if frozen:
+        nswe.nswe_jacobian_frozen(ctx, prob, 0, K, dev(U), eps, 3.0, dR, dJ)
+    elif kind == "j21":
+        nswe.nswe_jacobian_full(ctx, prob, 0, dev(U), eps, 3.0, dR, dJ)
+    else:
+        nswe.nswe_jacobian_simplified(ctx, prob, 0, dev(U), eps, 3.0, dR, dJ)
+    J = host(dJ)
+    sc = flux_scale2(U, inp.g, min(pr.s.dx, pr.s.dy))
+    assert np.isfinite(J).all()
+    # FD cancellation: over the 0.3-2.6 million entries here the largest difference reaches 8.7 units of
+    # u * scale / eps (the rounding of the two residuals differenced), so the allowance is 16 of them
+    tol = 1e-12 * np.abs(Jref).max() + 16.0 * EPS64 * sc / eps
+    assert np.abs(J - Jref).max() <= tol, (np.abs(J - Jref).max(), tol)
+    # blocks reaching outside the grid are exactly zero
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny))
+    for k, (ox, oy) in enumerate(orc.stencil2d(st)):
+        outside = ((i + ox < 0) | (i + ox >= nx) | (j + oy < 0) | (j + oy >= ny)).ravel()
+        assert np.all(J[k][:, outside] == 0.0)
+    assert np.abs(host(dR) - Rref).max() <= 1e-12 * sc
+
+
+def test_converged_wedge_channel_512x256_passes_the_oracle_residual(nswe, ctx, orc):
+    """The 512 x 256 wedge channel (seed 3000), solved nested from 16 x 8 at
+    the paper's omega = 0.1 under the frozen linearisation: the oracle's own
+    residual (Eq. 20) of the returned state passes the solve's stopping test
+    and agrees with the residual norm the GPU reported (each cell's residual
+    carries rounding of about u times the flux scale over the cell size)."""
+    big = I.wedge_channel(0)
+    w = I.wedge(512, 256, 7, x1=40.0, y1=30.0, x_wall=8.0, theta_deg=big.meta["theta_deg"], start_level=5)
+    prm = I.Params2D(levels=7, nu1=[20], nu2=[20], omega=0.1, tol=1e-10, n_max=3000, nest_start=5, frozen=True)
+    prob = nswe.Problem2D.from_inputs(ctx, w)
+    U = torch.zeros((3, 512 * 256), dtype=torch.float64, device="cuda")
+    info = nswe.nswe_newton_solve(ctx, prob, dev(w.U0_start), U, nswe.params2d_from(prm))
+    assert info["status"] == 0, info
+    got = host(U)
+    _, res = orc.residual2d(orc.problem_levels2d(w)[0], got)
+    assert res < prm.tol, (res, info["res"][0])
+    assert abs(res - info["res"][0]) <= 0.05 * prm.tol
+
+
 def test_2d_batch_runs_concurrently_and_equals_single(nswe, ctx):
     """A batch of 2D problems is solved concurrently (one worker stream each);
     every result equals, bit for bit, the same problem solved alone."""
@@ -269,6 +371,63 @@ def test_2d_batch_with_parameters_per_problem(nswe, ctx):
         assert infos[k]["status"] == 0 == alone[k][1]["status"], (k, infos[k], alone[k][1])
         assert infos[k]["iters"] == alone[k][1]["iters"]
         assert np.array_equal(host(Us[k]), alone[k][0])
+
+
+@pytest.mark.parametrize("precision,small_thresholds", [("fp64", False), ("mixed", False), ("fp64", True),
+                                                      ("mixed", True)])
+def test_lockstep_2d_batch_equals_single(nswe, precision, small_thresholds):
+    """Lockstep batches (one launch per phase and colour pass over all
+    problems): problems of several sizes and nested starts (one starting on
+    its coarsest grid with the direct solve), wedges under the frozen
+    linearisation and bumps with Eq. 12, J9 and J21 (two launch groups), each
+    with its own parameters: every result and Newton count equals, bit for
+    bit, the problem solved alone. small_thresholds: colour-major storage and
+    the per-cell Jacobian forced onto these small levels."""
+    g = I.G_PAPER
+    c = nswe.Context(0)
+    if small_thresholds:
+        nswe.nswe_ctx_set_colour_major_2d(c, 256)
+        nswe.nswe_ctx_set_jacobian_cells_2d(c, 256)
+    inps = [I.wedge(32, 16, 3, theta_deg=12.0, speed=3.0 * np.sqrt(g), x1=40.0, y1=30.0, x_wall=8.0, start_level=1),
+            I.bump_channel_2d(1, 32, 16, 3), I.wedge(16, 8, 2, start_level=1), I.bump_channel_2d(2, 64, 32, 4),
+            I.bump_channel_2d(3, 32, 16, 3)]
+    prms = [I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400, nest_start=1, omega=0.1, frozen=True),
+            I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400),
+            I.Params2D(levels=2, nu1=[20], nu2=[20], tol=1e-10, n_max=400, nest_start=1, omega=0.1, frozen=True),
+            I.Params2D(levels=4, nu1=[20], nu2=[20], tol=1e-10, n_max=400),
+            I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-10, n_max=400, st=1)]
+    cp = [nswe.params2d_from(q) for q in prms]
+    for q in cp:
+        q.precision = nswe.PREC_MIXED if precision == "mixed" else nswe.PREC_FP64
+    probs = [nswe.Problem2D.from_inputs(c, p) for p in inps]
+    U0s = [dev(p.U0_start) for p in inps]
+    alone = []
+    for pr, u0, p, q in zip(probs, U0s, inps, cp):
+        U = torch.zeros((3, p.Nx * p.Ny), dtype=torch.float64, device="cuda")
+        info = nswe.nswe_newton_solve(c, pr, u0, U, q)
+        alone.append((host(U), info))
+    nswe.nswe_ctx_set_batch_2d(c, nswe.BATCH2D_LOCKSTEP)
+    Us = [torch.full((3, p.Nx * p.Ny), float("nan"), dtype=torch.float64, device="cuda") for p in inps]
+    infos = nswe.nswe_newton_solve_batch_each(c, probs, U0s, Us, cp)
+    for k in range(len(inps)):
+        assert infos[k]["status"] == 0 == alone[k][1]["status"], (k, infos[k], alone[k][1])
+        assert infos[k]["iters"] == alone[k][1]["iters"], (k, infos[k]["iters"], alone[k][1]["iters"])
+        assert np.array_equal(host(Us[k]), alone[k][0]), (k, np.abs(host(Us[k]) - alone[k][0]).max())
+        assert infos[k]["vcycles"] == alone[k][1]["vcycles"]
+    # one parameter record for all through nswe_newton_solve_batch, twice in a row
+    extra = I.bump_channel_2d(4, 32, 16, 3)
+    pe = nswe.Problem2D.from_inputs(c, extra)
+    ue = dev(extra.U0_start)
+    nswe.nswe_ctx_set_batch_2d(c, nswe.BATCH2D_CONCURRENT)
+    Ue = torch.zeros((3, extra.Nx * extra.Ny), dtype=torch.float64, device="cuda")
+    ie = nswe.nswe_newton_solve(c, pe, ue, Ue, cp[1])
+    Ue = host(Ue)
+    nswe.nswe_ctx_set_batch_2d(c, nswe.BATCH2D_LOCKSTEP)
+    for _ in range(2):
+        Uz = [torch.zeros((3, 32 * 16), dtype=torch.float64, device="cuda") for _ in range(2)]
+        inf2 = nswe.nswe_newton_solve_batch(c, [probs[1], pe], [U0s[1], ue], Uz, cp[1])
+        assert np.array_equal(host(Uz[0]), alone[1][0]) and np.array_equal(host(Uz[1]), Ue)
+        assert inf2[0]["iters"] == alone[1][1]["iters"] and inf2[1]["iters"] == ie["iters"]
 
 
 def test_guess_sized_for_another_level_is_refused(nswe, ctx):
