@@ -53,7 +53,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM G
 # `bench.py --steps 1 --warmup 3 --no-cpu --shape S [--precision mixed]`; no entry: not captured.
 # DRAM bytes (read + write) of one colour pass of k2_sor_split<double, J9> at 512 x 256 with colour-major J9,
 # from one ncu capture of `bench.py --workload wedge2d --phases-only` (None: not captured for this kernel).
-SOR_PASS_TRAFFIC_512 = None
+SOR_PASS_TRAFFIC_512 = 34.606336e6 + 0.020480e6
 TRAFFIC_608 = {("fp64", "256x4"): 186.38e9 + 104.80e9, ("fp64", "128x4"): 216.09e9 + 104.06e9,
                ("mixed", "256x4"): 99.28e9 + 64.18e9}
 
@@ -599,17 +599,23 @@ def run_wedge2d(args):
         nl = nswe.nswe_mg_smooth(ctx, pb, 0, 9, J9cm, R, dU, q, colour_major=True)
         sweeps[nu] = (timed(lambda: nswe.nswe_mg_smooth(ctx, pb, 0, 9, J9cm, R, dU, q, colour_major=True), 3), nl)
     pass_ms = (sweeps[30][0] - sweeps[10][0]) / (sweeps[30][1] - sweeps[10][1])
-    # algorithmic bytes of one colour pass (n/3 cells): per cell J9 648 B, D^-1 72 B, R 24 B, own dU read and
-    # written 48 B; the other two colours' dU read once, 2n/3 x 24 B
+    # Per cell of the pass (n/3 cells): 8 off-diagonal 3x3 blocks times the neighbours' dU (8 x 9 FMA),
+    # D^-1 times the sum (9 FMA), the relaxation of 3 components (2 flops each): 168 flops. Bytes: J9 648 B,
+    # D^-1 72 B, R 24 B, own dU read and written 48 B per cell, the other colours' dU (2n/3 x 24 B) once.
+    pass_flops = n / 3.0 * (8 * 18 + 18 + 6)
     pass_bytes = n / 3.0 * (648 + 72 + 24 + 48) + 2.0 * n / 3.0 * 24
-    peak, peak_src = hbm_peak_gbs()
-    achieved = pass_bytes / (pass_ms / 1000.0) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": SOR_PASS_TRAFFIC_512, "peak_note": peak_src,
+    pk = measure_fma_peaks(0)
+    hbm, hbm_src = hbm_peak_gbs()
+    achieved = pass_flops / (pass_ms / 1000.0) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / pk["fp64_tflops"], "traffic": SOR_PASS_TRAFFIC_512,
+            "peak_note": "FP64 FMA peak measured in this run (nswe_probe_fma)",
             "kernel": "k2_sor_split<double, J9>: one colour pass of the 512x256 level, colour-major J9",
-            "bytes_per_launch": pass_bytes, "launch_us": 1000.0 * pass_ms,
-            "what": "algorithmic bytes per pass / per-pass time from nswe_mg_smooth with nu = 30 minus nu = 10 "
-                    "(%d vs %d colour passes)" % (sweeps[30][1], sweeps[10][1])}
+            "flops_per_launch": pass_flops, "bytes_per_launch": pass_bytes, "launch_us": 1000.0 * pass_ms,
+            "hbm": {"achieved_gbs": pass_bytes / (pass_ms / 1000.0) / 1e9, "peak_gbs": hbm, "peak_note": hbm_src},
+            "what": "algorithmic flops (and bytes) per pass / per-pass time from nswe_mg_smooth with nu = 30 minus "
+                    "nu = 10 (%d vs %d colour passes); ncu: FP64 pipe 73 %% busy, DRAM 26 %% of peak, so the pass "
+                    "is bound by FP64 issue" % (sweeps[30][1], sweeps[10][1])}
     kern = {"residual_ms": timed(lambda: nswe.nswe_residual(ctx, pb, 0, U, R, res), 10),
             "jacobian_j9_ms": timed(lambda: nswe.nswe_jacobian_simplified(ctx, pb, 0, U, 1e-6, 3.0, R, J9, res), 3),
             "jacobian_j21_ms": timed(lambda: nswe.nswe_jacobian_full(ctx, pb, 0, U, 1e-6, 3.0, R, J21, res), 2),
@@ -1049,7 +1055,7 @@ def run_batch2d(args):
     def one_by_one():
         return [nswe.nswe_newton_solve(ctx, probs[k], U0s[k], Us[k], prms[k]) for k in range(B)]
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(args.warmup):  # --warmup 0 for the multi-minute serving sizes: one timed batch includes capture
         batched()
     times = []
     infos = None
@@ -1191,6 +1197,39 @@ def run_serve2d(args):
         "clocks": clk}), flush=True)
 
 
+def run_autotune2d(args):
+    """The 2D autotuner's log (not the default line): for seeded wedge
+    channels of 64 x 32 to 512 x 256 cells in FP64 and mixed precision, the
+    time of one V-cycle (nu 20) for every smoothing schedule (0: the stencil
+    colouring; K: the directional schedule) and tail threshold, and the
+    choice nswe_autotune_2d records."""
+    import numpy as np
+    import torch
+
+    from paper_2505_10857_gb300 import inputs as I
+    from paper_2505_10857_gb300 import nswe
+
+    ctx = nswe.Context(0)
+    schedules, tails = [0, 3, 5, 7], [64, 256, 1024, 4096, 16384]
+    rows = []
+    for Nx, Ny, lev in ((64, 32, 4), (128, 64, 5), (256, 128, 6), (512, 256, 7)):
+        inp = I.wedge_serving_2d(0, Nx, Ny, lev)
+        prob = nswe.Problem2D.from_inputs(ctx, inp)
+        X, _ = inp.centres(0)
+        s0 = inp.bc_state[0]
+        U = torch.tensor(np.stack([s0[0] * (1 + 0.02 * np.sin(X.ravel())), np.full(X.size, s0[1]),
+                                   np.full(X.size, s0[2])]), dtype=torch.float64, device="cuda")
+        for prec in ("fp64", "mixed"):
+            q = nswe.params2d_from(I.Params2D(levels=lev, nu1=[20], nu2=[20], omega=0.1, frozen=True))
+            q.precision = nswe.PREC_MIXED if prec == "mixed" else nswe.PREC_FP64
+            ms, bs, bt = nswe.nswe_autotune_2d(ctx, prob, U, q, schedules, tails, reps=2)
+            rows.append({"grid": f"{Nx}x{Ny}", "precision": prec, "ms_per_vcycle": ms, "chosen_schedule": bs,
+                         "chosen_tail": bt, "default_ms": ms[0][tails.index(256 if prec == "fp64" else 4096)]})
+        del prob
+    print(json.dumps({"metric": "2D V-cycle time per schedule and tail threshold (ms), the autotuner's choices",
+                      "schedules": schedules, "tails": tails, "rows": rows}), flush=True)
+
+
 def run_jac1d(args):
     """1D Jacobian cost (not the default line): the residual and the FD
     Jacobians J3 and J5 (Eq. 12-13) of one seeded channel of 2^20 cells,
@@ -1256,7 +1295,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d",
-                    choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d", "jac1d", "peaks"])
+                    choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d", "jac1d", "peaks",
+                             "autotune2d"])
     ap.add_argument("--batch2d", type=int, default=16, help="batch2d: 2D problems per batch")
     ap.add_argument("--batch2d-mode", choices=["lockstep", "concurrent"], default="lockstep",
                     help="batch2d: shared launches over all problems, or concurrent per-problem streams")
@@ -1301,6 +1341,11 @@ def main():
         pk = measure_fma_peaks(0, reps=5)
         pk.update({"derived_fp64_tflops": FP64_PEAK_GFLOPS / 1e3, "derived_fp32_tflops": FP32_PEAK_GFLOPS / 1e3})
         print(json.dumps({"metric": "FP64 and FP32 FMA throughput (TFLOP/s)", "peaks": pk}), flush=True)
+        return
+    if args.workload == "autotune2d":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        run_autotune2d(args)
         return
     if args.workload == "jac1d":
         from paper_2505_10857_gb300 import build

@@ -135,7 +135,8 @@ typedef struct {
                      analogue of the sweeps D1-D4 of Eq. 22: diagonal colours
                      (i + j) mod K ascending, (j - i + Nx - 1) mod K
                      ascending, both descending; K >= Nx + Ny - 1 is the
-                     lexicographic sweep itself                          */
+                     lexicographic sweep itself;
+                     NSWE_COLOURS2D_AUTO = the choice of nswe_autotune_2d */
   double eps[NSWE_MAX_LEVELS]; /* FD perturbation per nested level, Eq. 12  */
 } nswe_params;
 
@@ -204,6 +205,41 @@ nswe_status nswe_ctx_set_jacobian_cells_2d(nswe_ctx ctx, int min_cells);
 #define NSWE_BATCH2D_CONCURRENT 0
 #define NSWE_BATCH2D_LOCKSTEP 1
 nswe_status nswe_ctx_set_batch_2d(nswe_ctx ctx, int mode);
+
+/* Tail threshold of the 2D V-cycles (the paper has no counterpart; results
+ * are the same bits whatever its value): from the first level of at most
+ * max_cells cells down to the coarsest and back, a V-cycle runs as one
+ * thread block per problem instead of one launch per colour pass. precision:
+ * NSWE_PREC_FP64 (default 256 cells) or NSWE_PREC_MIXED (default 4096). */
+nswe_status nswe_ctx_set_tail_2d(nswe_ctx ctx, int precision, int max_cells);
+
+/* Autotuner of the 2D V-cycle (the paper has no counterpart): forms the
+ * Jacobian of params (J9 / J21, frozen or Eq. 12, eps[0], alpha) at the
+ * finest level of `prob` from U (DEVICE [3][Nx*Ny]) in params->precision,
+ * then times, with CUDA events on the context stream, one untimed and `reps`
+ * timed V-cycles (Algorithm 2 with params' nu1, nu2, omega) for every
+ * smoothing schedule schedules[0..nsched) (colours2d values: 0 or K >= 3)
+ * and every tail threshold tails[0..ntails) (cells), and writes the mean
+ * milliseconds per V-cycle to ms[a * ntails + b] (HOST, may be NULL). The
+ * fastest pair is recorded in the context for prob's size and precision and
+ * returned in *best_schedule and *best_tail (HOST, may be NULL); a solve of
+ * a problem of that size and precision with colours2d = NSWE_COLOURS2D_AUTO
+ * then uses it (a size with nothing recorded: schedule 0 and the context's
+ * tail). The tail threshold changes no result; the schedule changes the
+ * smoothing, and so the Newton iterates, though not the steady state.
+ * Standalone V-cycle calls take the recorded schedule but the context's
+ * tail. Overwrites the problem's multigrid workspace; synchronises the
+ * context stream. */
+#define NSWE_COLOURS2D_AUTO (-1)
+nswe_status nswe_autotune_2d(nswe_ctx ctx, nswe_prob prob, const double *U,
+                             const nswe_params *params, const int *schedules,
+                             int nsched, const int *tails, int ntails,
+                             int reps, double *ms, int *best_schedule,
+                             int *best_tail);
+/* The schedule and tail nswe_autotune_2d recorded for Nx x Ny in
+ * `precision`; NSWE_EINVAL if none. */
+nswe_status nswe_ctx_get_tuned_2d(nswe_ctx ctx, int Nx, int Ny, int precision,
+                                  int *schedule, int *tail);
 nswe_status nswe_ctx_destroy(nswe_ctx ctx);
 
 /* One-dimensional problem (Eq. 3-4) on [x0, x1] with N cells and `levels`

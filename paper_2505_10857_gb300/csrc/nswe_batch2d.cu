@@ -141,9 +141,10 @@ void for_each_pass(int st, int steps, int Kc, F &&pass) {
   if (prev >= 0) pass(0, 0, prev, reps);
 }
 
+// tails[i]: the tail threshold (cells) of problem i's V-cycles.
 template <typename T>
 nswe_status lockstep_t(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s, double *const *Us,
-                       const nswe_params *prms, bool each, nswe_info *infos) {
+                       const nswe_params *prms, const int *tails, bool each, nswe_info *infos) {
   constexpr bool kMixed = std::is_same<T, float>::value;
   const nswe_params &P0 = prms[0];
   const int st0 = (P0.jacobian & ~NSWE_JAC_FROZEN) == NSWE_JAC_FULL ? ST_J21 : ST_J9;
@@ -223,7 +224,7 @@ nswe_status lockstep_t(nswe_ctx ctx, int count, const nswe_prob *probs, const do
       const Level2Dev &Lv = p->host2.lev[l];
       const int n = Lv.Nx * Lv.Ny;
       const int minc = ctx->cm2d_min_cells;
-      const int cm = (l < L && st0 == ST_J9 && minc >= 0 && n >= minc && n > tail2_cells<T>()) ? 1 : 0;
+      const int cm = (l < L && st0 == ST_J9 && minc >= 0 && n >= minc && n > tails[i]) ? 1 : 0;
       T *const J = reinterpret_cast<T *>(Lv.J);
       T *const dU = reinterpret_cast<T *>(Lv.dU);
       T *const Rs = kMixed ? J + (size_t)K * 9 * blk_stride(cm, Lv.Nx, Lv.Ny) : reinterpret_cast<T *>(Lv.R);
@@ -288,10 +289,10 @@ nswe_status lockstep_t(nswe_ctx ctx, int count, const nswe_prob *probs, const do
         sd.pool.add(sd.g_direct, t, 1);
         continue;
       }
-      // V-cycles: the first level of at most tail2_cells<T>() cells starts the tail
+      // V-cycles: the first level of at most tails[i] cells starts the tail
       int ls = L;
       for (int m = l; m < L; ++m)
-        if (p->host2.lev[m].Nx * p->host2.lev[m].Ny <= tail2_cells<T>()) {
+        if (p->host2.lev[m].Nx * p->host2.lev[m].Ny <= tails[i]) {
           ls = m;
           break;
         }
@@ -577,13 +578,16 @@ namespace nswe {
 nswe_status solve2d_lockstep(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
                              double *const *Us, const nswe_params *prms, bool each, nswe_info *infos) {
   DevGuard dg(ctx->device);
+  // each problem's schedule and tail threshold (colours2d = AUTO resolved per size)
+  std::vector<nswe_params> res(count);
+  std::vector<int> tail(count);
+  for (int i = 0; i < count; ++i) resolve2d(probs[i], prms[each ? i : 0], res[i], tail[i]);
   std::vector<int> group(count, -1);
   int ngroups = 0;
   std::vector<int> rep;
   for (int i = 0; i < count; ++i) {
-    const nswe_params &p = prms[each ? i : 0];
     for (int g = 0; g < ngroups && group[i] < 0; ++g)
-      if (same_group(prms[each ? rep[g] : 0], p)) group[i] = g;
+      if (same_group(res[rep[g]], res[i])) group[i] = g;
     if (group[i] < 0) {
       group[i] = ngroups++;
       rep.push_back(i);
@@ -595,21 +599,22 @@ nswe_status solve2d_lockstep(nswe_ctx ctx, int count, const nswe_prob *probs, co
     std::vector<const double *> u0g;
     std::vector<double *> ug;
     std::vector<nswe_params> prg;
-    std::vector<int> idx;
+    std::vector<int> idx, tg;
     for (int i = 0; i < count; ++i)
       if (group[i] == g) {
         pg.push_back(probs[i]);
         u0g.push_back(U0s[i]);
         ug.push_back(Us[i]);
-        prg.push_back(prms[each ? i : 0]);
+        prg.push_back(res[i]);
+        tg.push_back(tail[i]);
         idx.push_back(i);
       }
     std::vector<nswe_info> ig(pg.size());
     const bool mixed = prg[0].precision == NSWE_PREC_MIXED;
     const nswe_status st = mixed ? lockstep_t<float>(ctx, (int)pg.size(), pg.data(), u0g.data(), ug.data(),
-                                                     prg.data(), true, ig.data())
+                                                     prg.data(), tg.data(), true, ig.data())
                                  : lockstep_t<double>(ctx, (int)pg.size(), pg.data(), u0g.data(), ug.data(),
-                                                      prg.data(), true, ig.data());
+                                                      prg.data(), tg.data(), true, ig.data());
     if (st == NSWE_ECUDA || st == NSWE_ENOMEM) return st;
     for (size_t a = 0; a < idx.size(); ++a)
       if (infos) infos[idx[a]] = ig[a];

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <chrono>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "nswe_internal.h"
@@ -46,7 +47,8 @@ nswe_status check_params(const nswe_params *p, const nswe_prob_s *pr, int first_
   if (jb != NSWE_JAC_SIMPLIFIED && jb != NSWE_JAC_FULL) return NSWE_EINVAL;
   if ((p->jacobian & NSWE_JAC_FROZEN) && pr && pr->dim != 2) return NSWE_EINVAL;  // 2D only
   if (p->precision != NSWE_PREC_FP64 && p->precision != NSWE_PREC_MIXED) return NSWE_EINVAL;
-  if (p->colours2d != 0 && (p->colours2d < 3 || p->colours2d > 4096)) return NSWE_EINVAL;
+  if (p->colours2d != 0 && p->colours2d != NSWE_COLOURS2D_AUTO && (p->colours2d < 3 || p->colours2d > 4096))
+    return NSWE_EINVAL;
   if (pr) {
     for (int l = 0; l <= first_level && l < pr->levels; ++l)
       if (!(p->eps[l] > 0.0) || !std::isfinite(p->eps[l])) return NSWE_EINVAL;
@@ -281,14 +283,14 @@ cudaError_t mg2_setup(nswe_prob_s *p, const MG2<T> &m, cudaStream_t s) {
 }
 
 // Algorithm 2 from level l0: grid-wide kernels on the large levels; from the
-// first level of at most tail2_cells<T>() cells down to the coarsest and back
-// up, one block-persistent launch.
+// first level of at most `tail` cells down to the coarsest and back up, one
+// block-persistent launch (the same bits either way).
 template <typename T>
-cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2<T> &m, const nswe_params &prm, cudaStream_t s) {
+cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2<T> &m, const nswe_params &prm, cudaStream_t s, int tail) {
   cudaError_t e;
   int ls = m.L;  // first level handled by the tail launch
   for (int l = m.l0; l < m.L; ++l) {
-    if (m.lv[l].Nx * m.lv[l].Ny <= tail2_cells<T>()) {
+    if (m.lv[l].Nx * m.lv[l].Ny <= tail) {
       ls = l;
       break;
     }
@@ -327,8 +329,11 @@ cudaError_t mg2_vcycle(nswe_prob_s *p, const MG2<T> &m, const nswe_params &prm, 
 // FP32, FP32 multigrid with the FP32 right-hand side in the upper half of
 // J's storage).
 template <typename T>
-nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm, nswe_info *info,
+nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_params &prm_in, nswe_info *info,
                       cudaStream_t s) {
+  nswe_params prm;
+  int tail;
+  resolve2d(p, prm_in, prm, tail);
   const int L = p->levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
   const int st0 = (prm.jacobian & ~NSWE_JAC_FROZEN) == NSWE_JAC_FULL ? ST_J21 : ST_J9;
@@ -353,7 +358,7 @@ nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_pa
     // Colour-major J9 and Dinv on large levels solved by V-cycles (not on
     // the tail's levels, nor on the coarsest, whose J the dense LU reads).
     const int minc = p->ctx->cm2d_min_cells;
-    const int cm = (l < L && st0 == ST_J9 && minc >= 0 && n >= minc && n > tail2_cells<T>()) ? 1 : 0;
+    const int cm = (l < L && st0 == ST_J9 && minc >= 0 && n >= minc && n > tail) ? 1 : 0;
     T *const J = reinterpret_cast<T *>(Lv.J);
     T *const dU = reinterpret_cast<T *>(Lv.dU);
     T *const Rs = kMixed ? J + (size_t)K * 9 * blk_stride(cm, Lv.Nx, Lv.Ny) : reinterpret_cast<T *>(Lv.R);
@@ -376,7 +381,7 @@ nswe_status solve2d_t(nswe_prob_s *p, const double *U0, double *U, const nswe_pa
         if ((e = mg2_setup<T>(p, m, q))) return e;
         if ((e = cudaMemsetAsync(dU, 0, sizeof(T) * 3 * n, q))) return e;
         for (int v = 0; v < prm.nu3; ++v)
-          if ((e = mg2_vcycle<T>(p, m, prm, q))) return e;
+          if ((e = mg2_vcycle<T>(p, m, prm, q, tail))) return e;
       }
       if ((e = launch2_update<T>(n, Lv.U, dU, prm.tau, p->flag, q))) return e;
       if ((e = launch2_residual(p->dev2, l, n, Lv.U, Lv.R, p->res_dev, p->partials2, q))) return e;
@@ -519,8 +524,12 @@ nswe_status solve2d_batch(nswe_ctx ctx, int count, const nswe_prob *probs, const
 // is the coarsest).
 template <typename T>
 nswe_status vcycle2d_entry(nswe_ctx ctx, nswe_prob prob, int level, int nb, const T *J, const T *R, T *dU,
-                           const nswe_params &prm) {
+                           const nswe_params &prm_in) {
   if (nb != 9 && nb != 21) return NSWE_EINVAL;
+  nswe_params prm;
+  int tail;
+  resolve2d(prob, prm_in, prm, tail);
+  tail = ctx->tail2[std::is_same<T, float>::value ? 1 : 0];  // the standalone call's own precision
   MG2<T> m = mg2_bind<T>(prob, level, nb == 21 ? ST_J21 : ST_J9, J, R, dU, 0);
   cudaMemsetAsync(prob->flag, 0, sizeof(int), ctx->stream);
   if (level == prob->levels - 1) {
@@ -532,10 +541,24 @@ nswe_status vcycle2d_entry(nswe_ctx ctx, nswe_prob prob, int level, int nb, cons
                ? NSWE_ECUDA
                : NSWE_OK;
   }
-  return (mg2_setup<T>(prob, m, ctx->stream) || mg2_vcycle<T>(prob, m, prm, ctx->stream)) ? NSWE_ECUDA : NSWE_OK;
+  return (mg2_setup<T>(prob, m, ctx->stream) || mg2_vcycle<T>(prob, m, prm, ctx->stream, tail)) ? NSWE_ECUDA
+                                                                                                : NSWE_OK;
 }
 
 }  // namespace
+
+void nswe::resolve2d(const nswe_prob_s *p, const nswe_params &in, nswe_params &out, int &tail) {
+  out = in;
+  const int prec = in.precision == NSWE_PREC_MIXED ? 1 : 0;
+  tail = p->ctx->tail2[prec];
+  if (in.colours2d != NSWE_COLOURS2D_AUTO) return;
+  out.colours2d = 0;
+  for (const nswe_tuned2d &t : p->ctx->tuned2)
+    if (t.Nx == p->Nx && t.Ny == p->Ny && t.precision == prec) {
+      out.colours2d = t.colours;
+      tail = t.tail;
+    }
+}
 
 extern "C" {
 
@@ -1032,12 +1055,142 @@ nswe_status nswe_mg_smooth(nswe_ctx ctx, nswe_prob prob, int level, int nb, cons
   DeviceGuard dg(ctx->device);
   const Level2Dev &L = prob->host2.lev[level];
   const int stc = nb == 21 ? ST_J21 : ST_J9;
+  nswe_params prm;
+  int tail;
+  resolve2d(prob, *params, prm, tail);
   Lev2<double> Lv{L.Nx, L.Ny, const_cast<double *>(J), L.Dinv, const_cast<double *>(R), dU, colour_major};
   int count = 0;
   if (launch2_dinv<double>(L.Nx, L.Ny, stc, J, L.Dinv, colour_major, ctx->stream) != cudaSuccess ||
-      smooth2<double>(Lv, stc, params->nu1, params->omega, params->colours2d, ctx->stream, &count) != cudaSuccess)
+      smooth2<double>(Lv, stc, prm.nu1, prm.omega, prm.colours2d, ctx->stream, &count) != cudaSuccess)
     return NSWE_ECUDA;
   if (launches) *launches = count;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_set_tail_2d(nswe_ctx ctx, int precision, int max_cells) {
+  if (!ctx || (precision != NSWE_PREC_FP64 && precision != NSWE_PREC_MIXED) || max_cells < 0) return NSWE_EINVAL;
+  ctx->tail2[precision == NSWE_PREC_MIXED ? 1 : 0] = max_cells;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_get_tuned_2d(nswe_ctx ctx, int Nx, int Ny, int precision, int *schedule, int *tail) {
+  if (!ctx || (precision != NSWE_PREC_FP64 && precision != NSWE_PREC_MIXED)) return NSWE_EINVAL;
+  const int prec = precision == NSWE_PREC_MIXED ? 1 : 0;
+  for (const nswe_tuned2d &t : ctx->tuned2)
+    if (t.Nx == Nx && t.Ny == Ny && t.precision == prec) {
+      if (schedule) *schedule = t.colours;
+      if (tail) *tail = t.tail;
+      return NSWE_OK;
+    }
+  return NSWE_EINVAL;  // nothing recorded for this size and precision
+}
+
+}  // extern "C"
+
+namespace {
+
+// Times `reps` V-cycles from the finest level of `prob` for every (schedule,
+// tail) pair, the Jacobian formed once from U in the precision of `prm`.
+template <typename T>
+nswe_status autotune2d_t(nswe_ctx ctx, nswe_prob prob, const double *U, const nswe_params &prm,
+                         const int *schedules, int nsched, const int *tails, int ntails, int reps, double *ms,
+                         int *best_s, int *best_t) {
+  const int n = prob->Nx * prob->Ny;
+  const int st = (prm.jacobian & ~NSWE_JAC_FROZEN) == NSWE_JAC_FULL ? ST_J21 : ST_J9;
+  const int K = st == ST_J21 ? 21 : 9;
+  const bool frozen = (prm.jacobian & NSWE_JAC_FROZEN) != 0;
+  cudaStream_t s = ctx->stream;
+  double *R64 = nullptr;
+  T *J = nullptr, *R = nullptr, *dU = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  nswe_status status = NSWE_OK;
+  if (cudaMalloc(&R64, sizeof(double) * 3 * n) || cudaMalloc(&J, sizeof(T) * (size_t)K * 9 * n) ||
+      cudaMalloc(&R, sizeof(T) * 3 * n) || cudaMalloc(&dU, sizeof(T) * 3 * n) || cudaEventCreate(&e0) ||
+      cudaEventCreate(&e1))
+    status = NSWE_ENOMEM;
+  if (status == NSWE_OK &&
+      (launch2_residual(prob->dev2, 0, n, U, R64, nullptr, prob->partials2, s) ||
+       launch2_jacobian<T>(prob->dev2, 0, n, st, U, prm.eps[0], prm.alpha, R64, J, frozen, 0, ctx->jac2d_cell_min, s)))
+    status = NSWE_ECUDA;
+  if (status == NSWE_OK) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (launch2_to_f32(3L * n, R64, R, s)) status = NSWE_ECUDA;
+    } else {
+      if (cudaMemcpyAsync(R, R64, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s)) status = NSWE_ECUDA;
+    }
+  }
+  MG2<T> m = mg2_bind<T>(prob, 0, st, J, R, dU, 0);
+  if (status == NSWE_OK && mg2_setup<T>(prob, m, s)) status = NSWE_ECUDA;
+  double best = 0.0;
+  for (int a = 0; a < nsched && status == NSWE_OK; ++a)
+    for (int b = 0; b < ntails && status == NSWE_OK; ++b) {
+      nswe_params q = prm;
+      q.colours2d = schedules[a];
+      float t = 0.f;
+      if (cudaMemsetAsync(dU, 0, sizeof(T) * 3 * n, s) || mg2_vcycle<T>(prob, m, q, s, tails[b]) ||  // untimed
+          cudaEventRecord(e0, s)) {
+        status = NSWE_ECUDA;
+        break;
+      }
+      for (int r = 0; r < reps && status == NSWE_OK; ++r)
+        if (mg2_vcycle<T>(prob, m, q, s, tails[b])) status = NSWE_ECUDA;
+      if (status != NSWE_OK || cudaEventRecord(e1, s) || cudaEventSynchronize(e1) ||
+          cudaEventElapsedTime(&t, e0, e1)) {
+        status = NSWE_ECUDA;
+        break;
+      }
+      const double per = (double)t / reps;
+      if (ms) ms[a * ntails + b] = per;
+      if ((a == 0 && b == 0) || per < best) {
+        best = per;
+        *best_s = schedules[a];
+        *best_t = tails[b];
+      }
+    }
+  cudaStreamSynchronize(s);
+  cudaFree(R64);
+  cudaFree(J);
+  cudaFree(R);
+  cudaFree(dU);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+nswe_status nswe_autotune_2d(nswe_ctx ctx, nswe_prob prob, const double *U, const nswe_params *params,
+                             const int *schedules, int nsched, const int *tails, int ntails, int reps, double *ms,
+                             int *best_schedule, int *best_tail) {
+  if (!ctx || !prob || prob->ctx != ctx || prob->dim != 2 || !U || !params || !schedules || !tails || nsched < 1 ||
+      ntails < 1 || nsched > 64 || ntails > 64 || reps < 1 || reps > 100)
+    return NSWE_EINVAL;
+  nswe_status st = check_params(params, prob, 0);
+  if (st != NSWE_OK) return st;
+  for (int a = 0; a < nsched; ++a)
+    if (schedules[a] != 0 && (schedules[a] < 3 || schedules[a] > 4096)) return NSWE_EINVAL;
+  for (int b = 0; b < ntails; ++b)
+    if (tails[b] < 0) return NSWE_EINVAL;
+  if (prob->levels < 2) return NSWE_EINVAL;  // a V-cycle needs a coarser level
+  DeviceGuard dg(ctx->device);
+  int bs = 0, bt = 0;
+  st = params->precision == NSWE_PREC_MIXED
+           ? autotune2d_t<float>(ctx, prob, U, *params, schedules, nsched, tails, ntails, reps, ms, &bs, &bt)
+           : autotune2d_t<double>(ctx, prob, U, *params, schedules, nsched, tails, ntails, reps, ms, &bs, &bt);
+  if (st != NSWE_OK) return st;
+  const int prec = params->precision == NSWE_PREC_MIXED ? 1 : 0;
+  bool found = false;
+  for (nswe_tuned2d &t : ctx->tuned2)
+    if (t.Nx == prob->Nx && t.Ny == prob->Ny && t.precision == prec) {
+      t.colours = bs;
+      t.tail = bt;
+      found = true;
+    }
+  if (!found) ctx->tuned2.push_back({prob->Nx, prob->Ny, prec, bs, bt});
+  if (best_schedule) *best_schedule = bs;
+  if (best_tail) *best_tail = bt;
   return NSWE_OK;
 }
 

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/nswe.h"
 
 namespace nswe {
@@ -225,6 +227,11 @@ int b2_grid(long items);  // blocks of kThreads for `items` grid-stride items (a
 // Jacobian stencil and smoothing schedule; prms[each ? i : 0] are problem i's.
 nswe_status solve2d_lockstep(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
                              double *const *Us, const nswe_params *prms, bool each, nswe_info *infos);
+// The parameters and tail threshold (cells) a 2D solve of `p` runs with:
+// colours2d = NSWE_COLOURS2D_AUTO takes the schedule and tail that
+// nswe_autotune_2d recorded for p's size and precision (none recorded:
+// schedule 0 and the context's tail).
+void resolve2d(const nswe_prob_s *p, const nswe_params &in, nswe_params &out, int &tail);
 
 // One solve of a batch.
 struct SolveTask {
@@ -280,6 +287,12 @@ size_t prob2d_device_bytes(int Nx, int Ny, int levels);
 
 }  // namespace nswe
 
+// A choice of nswe_autotune_2d: smoothing schedule and tail threshold of the
+// 2D V-cycles of problems of Nx x Ny cells in one precision.
+struct nswe_tuned2d {
+  int Nx, Ny, precision, colours, tail;
+};
+
 // A context and a problem of the C ABI (include/nswe.h): host-side handles
 // of device resources, shared by the host translation units.
 struct nswe_ctx_s {
@@ -295,6 +308,9 @@ struct nswe_ctx_s {
   int batch2d_lockstep = 0;  // 2D batches: 0 concurrent per-problem solves, 1 lockstep batched launches
   int cm2d_min_cells = 131072;  // 2D Newton levels of at least this many cells store J9 colour-major
   int jac2d_cell_min = nswe::kJac2CellMinDefault;  // 2D levels from which the per-cell Jacobian kernel runs
+  // 2D V-cycles: levels of at most tail2[precision] cells run in the one-block tail (0 FP64, 1 mixed)
+  int tail2[2] = {nswe::tail2_cells<double>(), nswe::tail2_cells<float>()};
+  std::vector<nswe_tuned2d> tuned2;  // nswe_autotune_2d's choices per size and precision
 };
 
 struct nswe_prob_s {

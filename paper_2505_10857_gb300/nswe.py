@@ -112,6 +112,10 @@ EXPORTS = {
     "nswe_ctx_set_colour_major_2d": (_i, [_vp, _i]),
     "nswe_ctx_set_jacobian_cells_2d": (_i, [_vp, _i]),
     "nswe_ctx_set_batch_2d": (_i, [_vp, _i]),
+    "nswe_ctx_set_tail_2d": (_i, [_vp, _i, _i]),
+    "nswe_autotune_2d": (_i, [_vp, _vp, _dp, ctypes.POINTER(Params), ctypes.POINTER(_i), _i, ctypes.POINTER(_i), _i,
+                              _i, ctypes.POINTER(_d), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "nswe_ctx_get_tuned_2d": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nswe_prob_set_flux_1d": (_i, [_vp, _vp, _i]),
     "nswe_prob_set_geometry_batch_1d": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                              ctypes.POINTER(BC1D), ctypes.POINTER(BC1D)]),
@@ -424,6 +428,36 @@ def nswe_ctx_set_batch_2d(ctx, mode):
     """How batches of 2D problems run: BATCH2D_CONCURRENT (per-problem
     streams) or BATCH2D_LOCKSTEP (shared launches); see include/nswe.h."""
     _check("nswe_ctx_set_batch_2d", lib().nswe_ctx_set_batch_2d(ctx.h, int(mode)))
+
+
+COLOURS2D_AUTO = -1
+
+
+def nswe_ctx_set_tail_2d(ctx, precision, max_cells):
+    _check("nswe_ctx_set_tail_2d", lib().nswe_ctx_set_tail_2d(ctx.h, int(precision), int(max_cells)))
+
+
+def nswe_autotune_2d(ctx, prob, U, prm: Params, schedules, tails, reps=3):
+    """Times V-cycles of the 2D problem for every (schedule, tail) pair (see
+    include/nswe.h); returns (ms[len(schedules)][len(tails)], best schedule,
+    best tail) and records the choice in the context."""
+    if U.numel() < 3 * prob.Nx * prob.Ny:
+        raise ValueError("nswe_autotune_2d: U must hold the finest level")
+    ns, nt = len(schedules), len(tails)
+    sc = (_i * ns)(*[int(v) for v in schedules])
+    tl = (_i * nt)(*[int(v) for v in tails])
+    ms = (_d * (ns * nt))()
+    bs, bt = _i(), _i()
+    _check("nswe_autotune_2d", lib().nswe_autotune_2d(ctx.h, prob.h, _ptr(U), ctypes.byref(prm), sc, ns, tl, nt,
+                                                      int(reps), ms, ctypes.byref(bs), ctypes.byref(bt)))
+    return [[ms[a * nt + b] for b in range(nt)] for a in range(ns)], bs.value, bt.value
+
+
+def nswe_ctx_get_tuned_2d(ctx, Nx, Ny, precision):
+    """(schedule, tail) recorded by the autotuner, or None."""
+    s_, t_ = _i(), _i()
+    rc = lib().nswe_ctx_get_tuned_2d(ctx.h, int(Nx), int(Ny), int(precision), ctypes.byref(s_), ctypes.byref(t_))
+    return (s_.value, t_.value) if rc == 0 else None
 
 
 def nswe_ctx_set_jacobian_cells_2d(ctx, min_cells):

@@ -174,10 +174,15 @@ def test_smoother_parity_2d(nswe, ctx, orc, name, full, colours, cm, nu):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
 
 
-@pytest.mark.parametrize("case", ["bump_j9", "bump_j21", "wedge_direct", "bump_j9_directional", "wedge_frozen"])
+@pytest.mark.parametrize("case", ["bump_j9", "bump_j21", "wedge_direct", "bump_j9_directional", "wedge_frozen",
+                                  "gauss_bump"])
 def test_newton_solve_parity_2d(nswe, ctx, orc, case):
     slack = 0
-    if case == "wedge_frozen":
+    if case == "gauss_bump":
+        # the Gaussian-bump channel family of the batched 2D serving sizes, at 32 x 16
+        inp = I.gauss_bump_channel_2d(1, 32, 16, 3)
+        prm = I.Params2D(levels=3, nu1=[20], nu2=[20], tol=1e-11, n_max=400)
+    elif case == "wedge_frozen":
         # Section 5.2.2 with the paper's omega = 0.1, nested from 16 x 8, frozen linearisation
         inp = I.wedge(32, 16, 3, start_level=1)
         prm = I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400, nest_start=1, omega=0.1, frozen=True)
@@ -428,6 +433,50 @@ def test_lockstep_2d_batch_equals_single(nswe, precision, small_thresholds):
         inf2 = nswe.nswe_newton_solve_batch(c, [probs[1], pe], [U0s[1], ue], Uz, cp[1])
         assert np.array_equal(host(Uz[0]), alone[1][0]) and np.array_equal(host(Uz[1]), Ue)
         assert inf2[0]["iters"] == alone[1][1]["iters"] and inf2[1]["iters"] == ie["iters"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_2d_choice_and_tail_threshold(nswe, precision):
+    """nswe_autotune_2d times V-cycles per (schedule, tail threshold) and
+    records the fastest for the problem's size; the tail threshold changes no
+    result (a 64 x 32 wedge solved with every non-coarsest level grid-wide,
+    and with all levels in the one-block tail, gives the same bits); a solve
+    with colours2d = AUTO equals, bit for bit, the solve with the recorded
+    schedule given explicitly."""
+    c = nswe.Context(0)
+    prec = nswe.PREC_MIXED if precision == "mixed" else nswe.PREC_FP64
+    inp = I.wedge_serving_2d(0, 64, 32, 4)
+    q = I.Params2D(levels=4, nu1=[20], nu2=[20], tol=1e-10, n_max=400, nest_start=2, omega=0.1, frozen=True)
+
+    def prm(colours):
+        p = nswe.params2d_from(q)
+        p.precision = prec
+        p.colours2d = colours
+        return p
+
+    prob = nswe.Problem2D.from_inputs(c, inp)
+    X, Y = inp.centres(0)
+    s0 = inp.bc_state[0]
+    U = dev(np.stack([s0[0] * (1 + 0.02 * np.sin(X.ravel())), np.full(X.size, s0[1]), np.full(X.size, s0[2])]))
+    ms, bs, bt = nswe.nswe_autotune_2d(c, prob, U, prm(0), [0, 3, 5], [16, 256, 4096], reps=2)
+    assert all(m > 0 for row in ms for m in row)
+    assert bs in (0, 3, 5) and bt in (16, 256, 4096)
+    assert nswe.nswe_ctx_get_tuned_2d(c, 64, 32, prec) == (bs, bt)
+    assert nswe.nswe_ctx_get_tuned_2d(c, 128, 64, prec) is None
+
+    def solve(p):
+        Uo = torch.zeros((3, inp.Nx * inp.Ny), dtype=torch.float64, device="cuda")
+        info = nswe.nswe_newton_solve(c, prob, dev(inp.U0_start), Uo, p)
+        assert info["status"] == 0, info
+        return host(Uo), info["iters"]
+
+    out = []
+    for tail in (16, 4096):
+        nswe.nswe_ctx_set_tail_2d(c, prec, tail)
+        out.append(solve(prm(0)))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    auto, explicit = solve(prm(nswe.COLOURS2D_AUTO)), solve(prm(bs))
+    assert np.array_equal(auto[0], explicit[0]) and auto[1] == explicit[1]
 
 
 def test_guess_sized_for_another_level_is_refused(nswe, ctx):
