@@ -58,19 +58,31 @@ TRAFFIC_608 = {("fp64", "256x4"): 186.38e9 + 104.80e9, ("fp64", "128x4"): 216.09
                ("mixed", "256x4"): 99.28e9 + 64.18e9}
 
 
-def workload_config(batch, nb, precision="fp64", tol=TOL):
+# The 1D workloads of the default line: the irregular channel (N = 4096, the metric's configuration)
+# and the small smooth channel (N = 200): cells, levels, nested start (cells), description, seeds.
+CONFIG1D = {"irregular": (4096, 8, 256, "1D irregular channel, N=4096, 8-level MG", "numpy default_rng(2000 + k)"),
+            "small": (200, 4, 25, "1D smooth subcritical channel, N=200, 4-level MG, omega 1.2",
+                      "numpy default_rng(1000 + k)")}
+
+
+def workload_config(batch, nb, precision="fp64", tol=TOL, kind="irregular"):
     prec = "FP64" if precision == "fp64" else "mixed FP64 residual/update + FP32 Jacobian/MG"
-    return {"workload": "1D irregular channel, N=4096, 8-level MG, J%d, %s, subcritical" % (nb, prec),
+    N, levels, start, desc, seeds = CONFIG1D[kind]
+    return {"workload": "%s, J%d, %s, subcritical" % (desc, nb, prec),
             "precision": precision,
-            "N": 4096, "levels": 8, "nest_start_cells": 256, "instances_per_step_per_gpu": batch,
+            "N": N, "levels": levels, "nest_start_cells": start, "instances_per_step_per_gpu": batch,
             "jacobian": "J3 (simplified)" if nb == 3 else "J5 (full)", "tol": tol,
-            "l2": "inputs + workspace per step (%.0f MB) exceed the 129 MB L2" % (batch * 2.4),
-            "seeds": "numpy default_rng(2000 + k)"}
+            "l2": ("inputs + workspace per step (%.0f MB) exceed the 129 MB L2" % (batch * N * 0.95e-3)
+                   if batch * N * 0.95e3 >= 2 * 129e6 else
+                   "inputs + workspace per step (%.0f MB) fit in L2: 256 MB written between timed steps, each "
+                   "step timed on its own" % (batch * N * 0.95e-3)),
+            "seeds": seeds}
 
 
-def make_instances(first, count, nb, tol=TOL):
+def make_instances(first, count, nb, tol=TOL, kind="irregular"):
     from paper_2505_10857_gb300 import inputs as I
-    inps = [I.channel_irregular(k) for k in range(first, first + count)]
+    make = I.channel_irregular if kind == "irregular" else I.channel_small
+    inps = [make(k) for k in range(first, first + count)]
     prms = [I.Params1D.for_problem(p, tol=tol, n_max=800, nb=nb) for p in inps]
     return inps, prms
 
@@ -262,9 +274,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------------
 def _oracle_worker(args):
-    first, count, nb, tol = args
+    first, count, nb, tol, kind = args
     import oracle
-    inps, prms = make_instances(first, count, nb, tol)
+    inps, prms = make_instances(first, count, nb, tol, kind)
     out = []
     for p, q in zip(inps, prms):
         U, info = oracle.solve_problem(p, q)
@@ -272,15 +284,15 @@ def _oracle_worker(args):
     return out
 
 
-def oracle_sample(first, count, nb, workers, tol=TOL):
+def oracle_sample(first, count, nb, workers, tol=TOL, kind="irregular"):
     """Solves `count` instances with the CPU oracle on `workers` processes
     (spawn); returns (wall seconds, results)."""
     import oracle
     oracle.build()
-    chunks = [(first + i, 1, nb, tol) for i in range(count)]
+    chunks = [(first + i, 1, nb, tol, kind) for i in range(count)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        pool.map(_oracle_worker, [(first, 1, nb, tol)] * workers)  # warm the workers
+        pool.map(_oracle_worker, [(first, 1, nb, tol, kind)] * workers)  # warm the workers
         t0 = time.perf_counter()
         res = pool.map(_oracle_worker, chunks)
         wall = time.perf_counter() - t0
@@ -307,7 +319,7 @@ def run_reference(args, rank, world):
     sample = cores
     times = []
     for s in range(args.warmup + args.steps):
-        wall, _ = oracle_sample((s * sample) % args.batch, sample, args.nb, cores)
+        wall, _ = oracle_sample((s * sample) % args.batch, sample, args.nb, cores, TOL, args.config1d)
         if s >= args.warmup:
             times.append(wall)
     ms = 1000.0 * sum(times) / len(times)
@@ -315,7 +327,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.batch, args.nb),
+            "config": workload_config(args.batch, args.nb, kind=args.config1d),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{sample} of the step's {args.batch} instances per timed step (seeds rotate), "
                                        f"one solve per process (spawn pool)", **oracle_build_info()},
@@ -362,7 +374,10 @@ def run_gpu(args, rank, world, local_rank):
     mixed = args.precision == "mixed"
     tol = args.tol if args.tol is not None else (TOL_SOLUTION if mixed else TOL)
     first, _ = replica_instances(rank, world, B)
-    inps, prms = make_instances(first, B, nb, tol)
+    kind = args.config1d
+    inps, prms = make_instances(first, B, nb, tol, kind)
+    # about 0.95 KB of arena per finest cell: flush L2 between timed steps when a step's data fits in it
+    l2_flush = B * inps[0].N * 0.95e3 < 2 * 129e6
     prm = nswe.params_from(prms[0])
     prm.precision = nswe.PREC_MIXED if mixed else nswe.PREC_FP64
     for q in prms[1:]:
@@ -413,16 +428,31 @@ def run_gpu(args, rank, world, local_rank):
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev[0].record(stream)
-    for s in range(args.steps):
-        step()
-        ev[s + 1].record(stream)
-    torch.cuda.synchronize()
+    if l2_flush:
+        # the step's data fits in L2: each step timed on its own, a 256 MB write between steps
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+        ea = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        eb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ea[s].record(stream)
+            step()
+            eb[s].record(stream)
+        torch.cuda.synchronize()
+        per_launch = [ea[s].elapsed_time(eb[s]) for s in range(args.steps)]
+        ms = sum(per_launch) / args.steps
+        del flush
+    else:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for s in range(args.steps):
+            step()
+            ev[s + 1].record(stream)
+        torch.cuda.synchronize()
+        per_launch = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+        ms = ev[0].elapsed_time(ev[-1]) / args.steps
     barrier()
     clk = clocks.stop()
-    per_launch = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
-    ms = ev[0].elapsed_time(ev[-1]) / args.steps
     ms_max = max_over_ranks(ms, world, dev)
     value = whole_job_rate(world, B, ms_max)
 
@@ -438,7 +468,8 @@ def run_gpu(args, rank, world, local_rank):
     def pct(a, p):
         return a[min(len(a) - 1, int(math.ceil(p / 100.0 * len(a))) - 1)]
 
-    fl = [solve_flops(4096, 8, inps[k].start_level, infos[k]["iters"], nb, prm.nu1, prm.nu2, prm.nu3, mixed)
+    fl = [solve_flops(inps[k].N, inps[k].levels, inps[k].start_level, infos[k]["iters"], nb, prm.nu1, prm.nu2,
+                      prm.nu3, mixed)
           for k in range(B)]
     f64, f32 = sum(a for a, _ in fl), sum(b for _, b in fl)
     launch_ms = statistics.mean(per_launch)
@@ -493,9 +524,9 @@ def run_gpu(args, rank, world, local_rank):
         if world == 1 and not args.no_cpu:
             cores = host_cores()
             n = B  # the whole step: about 10-15 s of CPU work on 16 cores
-            wall, refs = oracle_sample(first, n, nb, cores, tol)
+            wall, refs = oracle_sample(first, n, nb, cores, tol, kind)
             n1 = 4  # per-solve latency on one core: a few solves one after another in one process
-            wall1, _ = oracle_sample(first, n1, nb, 1, tol)
+            wall1, _ = oracle_sample(first, n1, nb, 1, tol, kind)
             cpu = {"value": n / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"all {n} instances of the step, one solve per process (spawn pool), "
                              f"{wall:.1f} s wall",
@@ -504,7 +535,7 @@ def run_gpu(args, rank, world, local_rank):
                    **oracle_build_info()}
             what = "the oracle's solve with the same stopping test"
             if tol < TOL:  # equal-accuracy lines: against the converged discrete solution
-                _, refs = oracle_sample(first, n, nb, cores, TOL_CONVERGED)
+                _, refs = oracle_sample(first, n, nb, cores, TOL_CONVERGED, kind)
                 what = f"the oracle's converged discrete solution (res < {TOL_CONVERGED:g})"
             errs = [float(np.abs(Us[k].cpu().numpy() - refs[k]).max() / np.abs(refs[k]).max()) for k in range(n)]
             parity = {"max_rel_err_vs_oracle": max(errs), "instances": n, "reference": what,
@@ -513,7 +544,7 @@ def run_gpu(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-            "config": workload_config(B, nb, args.precision, tol),
+            "config": workload_config(B, nb, args.precision, tol, kind),
             "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
                            "what": "per-solve completion time from the start of its batch (device timer)",
                            "solve_p50": pct(dur, 50), "solve_p99": pct(dur, 99),
@@ -525,7 +556,8 @@ def run_gpu(args, rank, world, local_rank):
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": p64,
                          "unit": "TFLOP/s", "frac": achieved / p64,
-                         "traffic": TRAFFIC_608.get((args.precision, shape_name)) if (B == 608 and nb == 3) else None,
+                         "traffic": (TRAFFIC_608.get((args.precision, shape_name))
+                                     if (B == 608 and nb == 3 and kind == "irregular") else None),
                          "traffic_note": "DRAM bytes per launch from one ncu capture of this workload; "
                                          "8-16 % of the HBM copy rate over the launch, far from bound",
                          "kernel": f"k_solve (persistent nested NMGM, one block per instance, shape {shape_name})",
@@ -1288,6 +1320,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--batch", type=int, default=608, help="instances per GPU per step")
+    ap.add_argument("--config1d", choices=["irregular", "small"], default="irregular",
+                    help="the 1D workload: the irregular channel N=4096 (default) or the smooth channel N=200")
     ap.add_argument("--nb", type=int, default=3, choices=[3, 5], help="3: simplified J3, 5: full J5")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape of k_solve")
@@ -1325,6 +1359,8 @@ def main():
     ap.add_argument("--single-requests", type=int, default=24,
                     help="default line: requests solved one at a time for the plain FP64 single-instance rate")
     args = ap.parse_args()
+    if args.config1d == "small" and "--batch" not in sys.argv:
+        args.batch = 256  # the 256 seeded instances of the N = 200 configuration
     if args.workload == "wedge2d":
         from paper_2505_10857_gb300 import build
         build.build()

@@ -275,6 +275,44 @@ __device__ double residual_cells(const Geo &G, const double *U, double *R, int f
   return acc;
 }
 
+// The same residual with each block's five-cell windows staged in shared
+// memory: the block reads cells t0-2 .. t0+B+1 of a tile of B = blockDim.x
+// cells once, coalesced, and every thread builds its window from the tile.
+// Thread tid of block bid takes cells bid*B + tid + k*nblk*B, the cells and
+// the order of residual_cells with first = bid*B + tid, stride = nblk*B, so
+// the partial sums are the same bits. sH, sQ: B + 4 doubles each.
+__device__ double residual_cells_staged(const Geo &G, const double *U, double *R, int bid, int nblk, double *sH,
+                                        double *sQ) {
+  const int B = blockDim.x, N = G.N;
+  const double *H = U, *Q = U + N;
+  double acc = 0.0;
+  for (int t0 = bid * B; t0 < N; t0 += nblk * B) {  // block-uniform
+    __syncthreads();                                // the previous tile's windows are read
+    for (int i = threadIdx.x; i < B + 4; i += B) {
+      const int k = min(max(t0 - 2 + i, 0), N - 1);  // clamped as load_win: ghosts are filled later
+      sH[i] = H[k];
+      sQ[i] = Q[k];
+    }
+    __syncthreads();
+    const int j = t0 + threadIdx.x;
+    if (j < N) {
+      Win w;
+#pragma unroll
+      for (int p = 0; p < 5; ++p) {
+        w.H[p] = sH[threadIdx.x + p];
+        w.Q[p] = sQ[threadIdx.x + p];
+      }
+      fill_ghosts(G, j, w);
+      double R0, R1;
+      local_residual(G, j, w, R0, R1);
+      R[j] = R0;
+      R[N + j] = R1;
+      acc += fabs(R0) + fabs(R1);
+    }
+  }
+  return acc;
+}
+
 // ----------------------------------------------------------------------------
 // Regularized FD Jacobian (Eq. 12-13) in three passes that share work between
 // neighbouring cells. Perturbing U_i in component m changes only the
@@ -1086,11 +1124,22 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// NSWE_RESIDUAL_SMEM (default 1): the standalone residual stages its WENO
+// windows in shared memory (residual_cells_staged); 0 reads them through L1.
+#ifndef NSWE_RESIDUAL_SMEM
+#define NSWE_RESIDUAL_SMEM 1
+#endif
+
 __global__ void __launch_bounds__(kThreads) k_residual(const ProbDev *P, int level, const double *U, double *R,
                                                        double *partials) {
   __shared__ double red[33];
   Geo G = make_geo(*P, level);
+#if NSWE_RESIDUAL_SMEM
+  __shared__ double sH[kThreads + 4], sQ[kThreads + 4];
+  double acc = residual_cells_staged(G, U, R, blockIdx.x, gridDim.x, sH, sQ);
+#else
   double acc = residual_cells(G, U, R, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+#endif
   double s = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
