@@ -696,7 +696,7 @@ def run_wedge2d(args):
                                + (" (frozen linearisation)" if frozen else "") + f", {args.levels2d} levels, "
                                f"nested from 16x8, omega {args.omega2d}, nu 20, nu3 3, eps 1e-6, "
                                + ("mixed FP64/FP32" if mixed else "FP64"),
-                   "theta_deg": big.meta["theta_deg"]},
+                   "theta_deg": big.meta["theta_deg"], "launch_overlap": not args.no_launch_overlap},
         "converged": {"status": info["status"], "iters": info["iters"][:args.levels2d], "res": info["res"][0]},
         "kernels_512x256": kern, "roofline": roof}
     if cpu:
@@ -1127,7 +1127,7 @@ def run_batch2d(args):
                                 f"2D batched: {B} seeded channels ({args.family2d}: wedges Froude 2-4, 5-15 deg, "
                                 "frozen linearisation; parabolic bumps, Eq. 12), 128x64 and 256x128, J9, nu 20, ")
                                + ("mixed FP64/FP32" if mixed else "FP64"),
-                   "batch_mode": args.batch2d_mode,
+                   "batch_mode": args.batch2d_mode, "launch_overlap": not args.no_launch_overlap,
                    "seeds": "wedges default_rng(7000 + k), bumps default_rng(%d + k)"
                             % (6000 if args.sizes2d == "config5" else 5000)},
         "latency_ms": {"p50": pick(0.5), "p99": pick(0.99), "what": "per-solve completion from the batch start"},
@@ -1160,7 +1160,8 @@ def run_serve2d(args):
 
     mixed = args.precision != "fp64"
     B = args.batch2d
-    inps, prms_in = batch2d_instances(B, args.family2d)
+    c5 = args.sizes2d == "config5"
+    inps, prms_in = config5_instances(B) if c5 else batch2d_instances(B, args.family2d)
     prms = []
     for q in prms_in:
         c = nswe.params2d_from(q)
@@ -1217,11 +1218,15 @@ def run_serve2d(args):
         "metric": METRIC, "value": len(ok) / span, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
         "ms_per_step": 1000.0 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": f"2D serving: {B} requests ({args.family2d}: wedges Froude 2-4, 5-15 deg, frozen "
-                               "linearisation; parabolic bumps, Eq. 12), 128x64 and 256x128, J9, nu 20, Poisson "
-                               f"arrivals at {args.rate2d}/s, " + ("mixed FP64/FP32" if mixed else "FP64"),
+        "config": {"workload": (f"2D serving: {B} requests (wedges Froude 2-4, 5-15 deg, frozen linearisation; "
+                                "Gaussian-bump channels, Eq. 12), 128x64, 256x128, 512x256 and 1024x512 in equal "
+                                "numbers, J9, nu 20, " if c5 else
+                                f"2D serving: {B} requests ({args.family2d}: wedges Froude 2-4, 5-15 deg, frozen "
+                                "linearisation; parabolic bumps, Eq. 12), 128x64 and 256x128, J9, nu 20, ")
+                               + f"Poisson arrivals at {args.rate2d}/s, " + ("mixed FP64/FP32" if mixed else "FP64"),
                    "offered_rate": args.rate2d, "workers": args.streams, "device_budget_2d_gb": args.serve_mem_gb,
-                   "seeds": "wedges default_rng(7000 + k), bumps default_rng(5000 + k); arrivals 6999"},
+                   "seeds": "wedges default_rng(7000 + k), bumps default_rng(%d + k); arrivals 6999"
+                            % (6000 if c5 else 5000)},
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "queue_p50": pct(queue, 50),
                        "queue_p99": pct(queue, 99), "what": "completion minus submission per request (host clock)"},
         "converged": {"converged": len(ok), "of": B, "max_res": max((infos[k]["res"][0] for k in ok), default=None)},
@@ -1337,6 +1342,8 @@ def main():
     ap.add_argument("--sizes2d", choices=["small", "config5"], default="small",
                     help="batch2d: 128x64/256x128, or the serving sizes 128x64 to 1024x512")
     ap.add_argument("--no-one-by-one", action="store_true", help="batch2d: skip the one-by-one comparison")
+    ap.add_argument("--no-launch-overlap", action="store_true",
+                    help="2D workloads: launch the 2D kernels without programmatic dependent launch")
     ap.add_argument("--rate2d", type=float, default=1.0, help="serve2d: Poisson arrival rate (requests/s)")
     ap.add_argument("--family2d", choices=["mix", "wedge", "bump"], default="mix",
                     help="batch2d: wedge and bump channels, or one family")
@@ -1359,6 +1366,11 @@ def main():
     ap.add_argument("--single-requests", type=int, default=24,
                     help="default line: requests solved one at a time for the plain FP64 single-instance rate")
     args = ap.parse_args()
+    if args.no_launch_overlap:
+        from paper_2505_10857_gb300 import build
+        build.build()
+        from paper_2505_10857_gb300 import nswe
+        nswe.nswe_set_launch_overlap_2d(0)
     if args.config1d == "small" and "--batch" not in sys.argv:
         args.batch = 256  # the 256 seeded instances of the N = 200 configuration
     if args.workload == "wedge2d":

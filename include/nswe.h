@@ -189,9 +189,9 @@ nswe_status nswe_ctx_set_jacobian_cells_2d(nswe_ctx ctx, int min_cells);
 /* How nswe_newton_solve_batch and nswe_newton_solve_batch_each run a batch
  * of several 2D problems (the paper solves one problem; results are the same
  * bits either way):
- *   NSWE_BATCH2D_CONCURRENT (default): each problem's solve is sequenced on
- *     its own stream by one of up to 8 host worker threads.
- *   NSWE_BATCH2D_LOCKSTEP: problems with the same precision, Jacobian
+ *   NSWE_BATCH2D_CONCURRENT: each problem's solve is sequenced on its own
+ *     stream by one of up to 8 host worker threads.
+ *   NSWE_BATCH2D_LOCKSTEP (default): problems with the same precision, Jacobian
  *     stencil (J9 / J21) and smoothing schedule (nu1, nu2, nu3, omega,
  *     colours2d) share launches: each phase of a Newton step (Eq. 12-14) and
  *     each colour pass of its V-cycles (Algorithm 2) is one launch over all
@@ -205,6 +205,17 @@ nswe_status nswe_ctx_set_jacobian_cells_2d(nswe_ctx ctx, int min_cells);
 #define NSWE_BATCH2D_CONCURRENT 0
 #define NSWE_BATCH2D_LOCKSTEP 1
 nswe_status nswe_ctx_set_batch_2d(nswe_ctx ctx, int mode);
+
+/* Programmatic dependent launch of the 2D kernels (the paper has no
+ * counterpart; results are the same bits either way), process-wide, on by
+ * default: each 2D kernel launched from the host (the standalone calls,
+ * nswe_mg_vcycle, nswe_mg_smooth, the autotuner) carries programmatic
+ * stream serialization, so that it may begin launching while the kernel
+ * before it on the stream still runs, and waits for that kernel's
+ * completion on the device before it reads anything. Launches captured into
+ * the CUDA graphs of the nested solves keep ordinary stream order.
+ * enable: 1 on, 0 off; other values NSWE_EINVAL. */
+nswe_status nswe_set_launch_overlap_2d(int enable);
 
 /* Tail threshold of the 2D V-cycles (the paper has no counterpart; results
  * are the same bits whatever its value): from the first level of at most

@@ -1067,6 +1067,12 @@ nswe_status nswe_mg_smooth(nswe_ctx ctx, nswe_prob prob, int level, int nb, cons
   return NSWE_OK;
 }
 
+nswe_status nswe_set_launch_overlap_2d(int enable) {
+  if (enable != 0 && enable != 1) return NSWE_EINVAL;
+  set_pdl_2d(enable);
+  return NSWE_OK;
+}
+
 nswe_status nswe_ctx_set_tail_2d(nswe_ctx ctx, int precision, int max_cells) {
   if (!ctx || (precision != NSWE_PREC_FP64 && precision != NSWE_PREC_MIXED) || max_cells < 0) return NSWE_EINVAL;
   ctx->tail2[precision == NSWE_PREC_MIXED ? 1 : 0] = max_cells;

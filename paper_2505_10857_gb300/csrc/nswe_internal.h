@@ -223,6 +223,9 @@ cudaError_t launchb2_dense_solve(const BTask2<T> *tasks, int ntask, const int *d
 template <typename T>
 cudaError_t launchb2_update(const Batch2Launch<T> &b, const int *done, int *flags, cudaStream_t s);
 int b2_grid(long items);  // blocks of kThreads for `items` grid-stride items (as the single launches)
+// Programmatic dependent launch of the 2D kernels (process-wide; on by default).
+void set_pdl_2d(int on);
+int get_pdl_2d();
 // Lockstep batched 2D solves (nswe_batch2d.cu): problems grouped by precision,
 // Jacobian stencil and smoothing schedule; prms[each ? i : 0] are problem i's.
 nswe_status solve2d_lockstep(nswe_ctx ctx, int count, const nswe_prob *probs, const double *const *U0s,
@@ -305,7 +308,7 @@ struct nswe_ctx_s {
   nswe_params *prms;     // device per-task parameters (nswe_newton_solve_batch_each)
   int cap;               // capacity of tasks / infos / prms
   int solve_shape[2];    // launch shape of the 1D solve kernel per precision
-  int batch2d_lockstep = 0;  // 2D batches: 0 concurrent per-problem solves, 1 lockstep batched launches
+  int batch2d_lockstep = 1;  // 2D batches: 1 lockstep batched launches (default), 0 concurrent solves
   int cm2d_min_cells = 131072;  // 2D Newton levels of at least this many cells store J9 colour-major
   int jac2d_cell_min = nswe::kJac2CellMinDefault;  // 2D levels from which the per-cell Jacobian kernel runs
   // 2D V-cycles: levels of at most tail2[precision] cells run in the one-block tail (0 FP64, 1 mixed)

@@ -113,6 +113,7 @@ EXPORTS = {
     "nswe_ctx_set_jacobian_cells_2d": (_i, [_vp, _i]),
     "nswe_ctx_set_batch_2d": (_i, [_vp, _i]),
     "nswe_ctx_set_tail_2d": (_i, [_vp, _i, _i]),
+    "nswe_set_launch_overlap_2d": (_i, [_i]),
     "nswe_autotune_2d": (_i, [_vp, _vp, _dp, ctypes.POINTER(Params), ctypes.POINTER(_i), _i, ctypes.POINTER(_i), _i,
                               _i, ctypes.POINTER(_d), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nswe_ctx_get_tuned_2d": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -431,6 +432,11 @@ def nswe_ctx_set_batch_2d(ctx, mode):
 
 
 COLOURS2D_AUTO = -1
+
+
+def nswe_set_launch_overlap_2d(enable):
+    """Programmatic dependent launch of the 2D kernels (process-wide, on by default)."""
+    _check("nswe_set_launch_overlap_2d", lib().nswe_set_launch_overlap_2d(int(bool(enable))))
 
 
 def nswe_ctx_set_tail_2d(ctx, precision, max_cells):

@@ -321,9 +321,12 @@ def test_converged_wedge_channel_512x256_passes_the_oracle_residual(nswe, ctx, o
     assert abs(res - info["res"][0]) <= 0.05 * prm.tol
 
 
-def test_2d_batch_runs_concurrently_and_equals_single(nswe, ctx):
-    """A batch of 2D problems is solved concurrently (one worker stream each);
-    every result equals, bit for bit, the same problem solved alone."""
+@pytest.mark.parametrize("mode", ["concurrent", "lockstep"])
+def test_2d_batch_runs_concurrently_and_equals_single(nswe, ctx, mode):
+    """A batch of 2D problems solved concurrently (one worker stream each) or
+    in lockstep (shared launches, the default): every result equals, bit for
+    bit, the same problem solved alone."""
+    nswe.nswe_ctx_set_batch_2d(ctx, nswe.BATCH2D_CONCURRENT if mode == "concurrent" else nswe.BATCH2D_LOCKSTEP)
     inps = [I.paper_parabolic_bump(32, 16, 3), I.wedge(16, 8, 1), I.paper_parabolic_bump(16, 8, 2),
             I.make_problem_2d(12, 8, 2, 0.0, 3.0, 0.0, 2.0, 9.81, I.bottom2d_linear(0.0, 0.01, 0.0),
                               (I.BC2_INFLOW, I.BC2_OUTFLOW, I.BC2_REFLECT, I.BC2_REFLECT),
@@ -477,6 +480,57 @@ def test_autotune_2d_choice_and_tail_threshold(nswe, precision):
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
     auto, explicit = solve(prm(nswe.COLOURS2D_AUTO)), solve(prm(bs))
     assert np.array_equal(auto[0], explicit[0]) and auto[1] == explicit[1]
+
+
+def test_launch_overlap_changes_no_result(nswe):
+    """Programmatic dependent launch of the 2D kernels (on by default) only
+    changes when a kernel may begin launching: a nested wedge solve and a
+    lockstep batch give the same bits with it on and off."""
+    c = nswe.Context(0)
+    inps = [I.wedge(32, 16, 3, start_level=1), I.bump_channel_2d(1, 32, 16, 3)]
+    prms = [I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400, nest_start=1, omega=0.1, frozen=True),
+            I.Params2D(levels=3, nu1=[15], nu2=[15], tol=1e-11, n_max=400, omega=0.1)]
+    probs = [nswe.Problem2D.from_inputs(c, p) for p in inps]
+    cp = [nswe.params2d_from(q) for q in prms]
+    out = {}
+    try:
+        for on in (1, 0):
+            nswe.nswe_set_launch_overlap_2d(on)
+            U = torch.zeros((3, 32 * 16), dtype=torch.float64, device="cuda")
+            info = nswe.nswe_newton_solve(c, probs[0], dev(inps[0].U0_start), U, cp[0])
+            assert info["status"] == 0, info
+            nswe.nswe_ctx_set_batch_2d(c, nswe.BATCH2D_LOCKSTEP)
+            Us = [torch.zeros((3, 32 * 16), dtype=torch.float64, device="cuda") for _ in inps]
+            infos = nswe.nswe_newton_solve_batch_each(c, probs, [dev(p.U0_start) for p in inps], Us, cp)
+            nswe.nswe_ctx_set_batch_2d(c, nswe.BATCH2D_CONCURRENT)
+            out[on] = (host(U), info["iters"], [host(u) for u in Us], [i["iters"] for i in infos])
+    finally:
+        nswe.nswe_set_launch_overlap_2d(1)
+    assert np.array_equal(out[1][0], out[0][0]) and out[1][1] == out[0][1]
+    for a, b in zip(out[1][2], out[0][2]):
+        assert np.array_equal(a, b)
+    assert out[1][3] == out[0][3]
+    # host-launched V-cycles (where the programmatic launches apply), both precisions
+    inp = I.bump_channel_2d(2, 64, 32, 4)
+    pb = nswe.Problem2D.from_inputs(c, inp)
+    U = dev(state_for(inp, 0, 70))
+    R = torch.zeros((3, 64 * 32), dtype=torch.float64, device="cuda")
+    J = torch.zeros((9, 9, 64 * 32), dtype=torch.float64, device="cuda")
+    nswe.nswe_jacobian_simplified(c, pb, 0, U, 1e-6, 3.0, R, J)
+    prm = nswe.params(96, 4, omega=0.1, nu1=5, nu2=5, nu3=1)
+    got = {}
+    try:
+        for on in (1, 0):
+            nswe.nswe_set_launch_overlap_2d(on)
+            d64 = torch.zeros_like(R)
+            nswe.nswe_mg_vcycle(c, pb, 0, 9, J, R, d64, prm)
+            d32 = torch.zeros_like(R, dtype=torch.float32)
+            nswe.nswe_mg_vcycle_f32(c, pb, 0, 9, J.float(), R.float(), d32, prm)
+            got[on] = (host(d64), host(d32))
+    finally:
+        nswe.nswe_set_launch_overlap_2d(1)
+    assert np.array_equal(got[1][0], got[0][0]) and np.array_equal(got[1][1], got[0][1])
+    assert np.abs(got[1][0]).max() > 0
 
 
 def test_guess_sized_for_another_level_is_refused(nswe, ctx):
