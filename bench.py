@@ -48,14 +48,15 @@ MIXED_BOUND = 1e-10  # relative distance to the converged FP64 discrete solution
 # Derived FMA peaks (reported beside the measured ones of measure_fma_peaks, which the rooflines use)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x FP64 FMA/clk/SM x 2 flop x max SM GHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM GHz
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_solve launch of the default step
-# (608 channel solves, J3) per precision and launch shape, each from a one-pass ncu capture of
-# `bench.py --steps 1 --warmup 3 --no-cpu --shape S [--precision mixed]`; no entry: not captured.
 # DRAM bytes (read + write) of one colour pass of k2_sor_split<double, J9> at 512 x 256 with colour-major J9,
 # from one ncu capture of `bench.py --workload wedge2d --phases-only` (None: not captured for this kernel).
 SOR_PASS_TRAFFIC_512 = 34.606336e6 + 0.020480e6
-TRAFFIC_608 = {("fp64", "256x4"): 186.38e9 + 104.80e9, ("fp64", "128x4"): 216.09e9 + 104.06e9,
-               ("mixed", "256x4"): 99.28e9 + 64.18e9}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_solve launch of the 608-channel J3 step
+# per (precision, launch shape, stopping tolerance), each from a one-pass ncu capture of
+# `bench.py --steps 1 --warmup 3 --no-cpu --shape S [--precision mixed] --tol T`; no entry: not captured
+# (the bytes grow with the Newton steps, so a capture stands only for its own tolerance).
+TRAFFIC_608 = {("fp64", "256x4", 1e-10): 186.38e9 + 104.80e9, ("fp64", "128x4", 1e-10): 216.09e9 + 104.06e9,
+               ("mixed", "256x4", 1e-10): 99.28e9 + 64.18e9}
 
 
 # The 1D workloads of the default line: the irregular channel (N = 4096, the metric's configuration)
@@ -556,7 +557,7 @@ def run_gpu(args, rank, world, local_rank):
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": p64,
                          "unit": "TFLOP/s", "frac": achieved / p64,
-                         "traffic": (TRAFFIC_608.get((args.precision, shape_name))
+                         "traffic": (TRAFFIC_608.get((args.precision, shape_name, tol))
                                      if (B == 608 and nb == 3 and kind == "irregular") else None),
                          "traffic_note": "DRAM bytes per launch from one ncu capture of this workload; "
                                          "8-16 % of the HBM copy rate over the launch, far from bound",
