@@ -93,6 +93,7 @@ def make_instances(first, count, nb, tol=TOL, kind="irregular"):
 # square root = 1), following the steps the kernels execute; per cell unless noted.
 F_WENO = 38          # one component of one cell: smoothness, candidates, one reciprocal, two weights
 F_STATE = 10         # HLL quantities of one interface state (1/H, u, h, c, physical flux)
+F_STATE_Q = 3        # the same for a state that differs from a computed one only in Q (u, flux)
 F_HLL = 20           # HLL combination of two states
 F_SOURCE = 36        # two-point Gauss source of one cell (Eq. 9)
 F_UPDATE = 4         # damped Newton update of H and Q
@@ -108,12 +109,16 @@ def f_res():
 
 
 def f_res_jac(nb):
-    """Residual + FD Jacobian per cell: 8 WENO variants (+6 perturbations),
-    per face 1 reciprocal + 14 states + 9 HLL combinations, per block two
-    sources, differences and scaling (+6 for the diagonal)."""
+    """Residual + FD Jacobian per cell: 8 WENO variants (+6 perturbations);
+    per face 8 full interface states (the two base states and the six with H
+    perturbed), 6 states with only Q perturbed (u and the flux from the base
+    state's 1/H and pressure term: F_STATE_Q) and 9 HLL combinations; per cell
+    the base source and one source per block (an H perturbation; a Q
+    perturbation leaves the source), and per block the differences and
+    scaling (+6 for the diagonal)."""
     pass_a = 8 * F_WENO + 6
-    pass_b = 1 + 14 * F_STATE + 9 * F_HLL
-    pass_c = nb * (2 * F_SOURCE + 18) + 6
+    pass_b = 8 * F_STATE + 6 * F_STATE_Q + 9 * F_HLL
+    pass_c = (nb + 1) * F_SOURCE + 18 * nb + 6
     return pass_a + pass_b + pass_c
 
 

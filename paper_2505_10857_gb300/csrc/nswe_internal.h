@@ -18,9 +18,9 @@ constexpr int kThreads = NSWE_THREADS;
 // Launch shapes of the persistent solve kernel, (threads per block, resident
 // blocks per SM it is built for): the register budget per thread follows
 // from the pair (65536 registers per SM). Shape 0 is the default.
-constexpr int kSolveShapes = 4;
-constexpr int kSolveShapeThreads[kSolveShapes] = {256, 128, 256, 128};
-constexpr int kSolveShapeBlocks[kSolveShapes] = {4, 8, 2, 4};
+constexpr int kSolveShapes = 6;
+constexpr int kSolveShapeThreads[kSolveShapes] = {256, 128, 256, 128, 160, 192};
+constexpr int kSolveShapeBlocks[kSolveShapes] = {4, 8, 2, 4, 4, 4};
 constexpr int kMaxCoarse = 128;    // max cells of the coarsest level (direct solve)
 
 // One nested / multigrid level of a 1D problem. Geometry is read-only input;

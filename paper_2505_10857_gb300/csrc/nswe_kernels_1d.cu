@@ -103,10 +103,13 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // sigma: velocity u = Q/H, celerity c = sqrt(g H/sigma) and physical flux
 // F = (Q, Q^2/H + g H^2/(2 sigma)) (Eq. 4). One reciprocal square root
 // r = H^(-1/2) gives both 1/H = r^2 and c = sqrt(g/sigma) H r; isg = 1/sigma
-// and cg = sqrt(g/sigma) are per-face geometry.
+// and cg = sqrt(g/sigma) are per-face geometry. r2 = 1/H and the pressure
+// term P = g H^2/(2 sigma) are kept, so that a state differing only in Q
+// (fstate_q) costs one multiply and one fused multiply-add, with the same
+// bits as a full evaluation.
 template <typename T>
 struct FState {
-  T H, Q, u, c, F1;
+  T H, Q, u, c, F1, r2, P;
 };
 
 template <typename T>
@@ -115,24 +118,53 @@ __device__ __forceinline__ FState<T> fstate(T H, T Q, T isg, T cg, T g) {
   s.H = H;
   s.Q = Q;
   const T r = rsq(H);
-  s.u = Q * (r * r);
+  s.r2 = r * r;
+  s.u = Q * s.r2;
   const T h = H * isg;
   s.c = cg * (H * r);
-  s.F1 = Q * s.u + T(0.5) * g * H * h;
+  s.P = (T(0.5) * g * H) * h;
+  s.F1 = fma(Q, s.u, s.P);
   return s;
 }
+
+// The state of `b` with its discharge replaced by Q.
+template <typename T>
+__device__ __forceinline__ FState<T> fstate_q(const FState<T> &b, T Q) {
+  FState<T> s = b;
+  s.Q = Q;
+  s.u = Q * b.r2;
+  s.F1 = fma(Q, s.u, b.P);
+  return s;
+}
+
+// Ordering keys of FP64 values on the integer pipe (the FP64 pipe is the
+// narrow one): for finite x, key(x) orders as x, with key(-0) = -1 just
+// below key(+0) = 0. Selecting by key gives fmin / fmax of two finite values
+// (either zero for a pair of zeros), and x >= 0 is key(x) >= -1.
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double kmin(double a, double b) { return okey(a) <= okey(b) ? a : b; }
+__device__ __forceinline__ double kmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
+__device__ __forceinline__ bool knonneg(double a) { return okey(a) >= -1LL; }
+__device__ __forceinline__ bool knonpos(double a) { return okey(a) <= 0LL; }
+__device__ __forceinline__ float kmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float kmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ bool knonneg(float a) { return a >= 0.0f; }
+__device__ __forceinline__ bool knonpos(float a) { return a <= 0.0f; }
 
 // HLL flux of two interface states: S_L = min(u_L - c_L, u_R - c_R),
 // S_R = max(u_L + c_L, u_R + c_R), upwind fluxes outside the fan, the HLL
 // average inside.
 template <typename T>
 __device__ __forceinline__ void hll_states(const FState<T> &L, const FState<T> &R, T &F0, T &F1) {
-  T SL = fmin(L.u - L.c, R.u - R.c);
-  T SR = fmax(L.u + L.c, R.u + R.c);
-  if (SL >= T(0.0)) {
+  T SL = kmin(L.u - L.c, R.u - R.c);
+  T SR = kmax(L.u + L.c, R.u + R.c);
+  if (knonneg(SL)) {
     F0 = L.Q;
     F1 = L.F1;
-  } else if (SR <= T(0.0)) {
+  } else if (knonpos(SR)) {
     F0 = R.Q;
     F1 = R.F1;
   } else {
@@ -417,10 +449,14 @@ __device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) 
       if (i < 0 || i >= N) continue;
 #pragma unroll
       for (int m = 0; m < 2; ++m) {
+        // a Q perturbation (m = 1) leaves H, 1/H, c and the pressure term of
+        // the base state
         FState<T> Ls = Lb, Rs = Rb;
         if (p <= 2)
-          Ls = fstate<T>(W.r(0, m == 0 ? p + 1 : 0, 1, f - 1), W.r(1, m == 1 ? p + 1 : 0, 1, f - 1), isg, cg, g);
-        if (p >= 1) Rs = fstate<T>(W.r(0, m == 0 ? p : 0, 0, f), W.r(1, m == 1 ? p : 0, 0, f), isg, cg, g);
+          Ls = m == 0 ? fstate<T>(W.r(0, p + 1, 1, f - 1), W.r(1, 0, 1, f - 1), isg, cg, g)
+                      : fstate_q<T>(Lb, W.r(1, p + 1, 1, f - 1));
+        if (p >= 1)
+          Rs = m == 0 ? fstate<T>(W.r(0, p, 0, f), W.r(1, 0, 0, f), isg, cg, g) : fstate_q<T>(Rb, W.r(1, p, 0, f));
         num_flux<FLUX>(Ls, Rs, G.flux, F0, F1);
         const int w = 1 + 2 * p + m;
         W.f(w, 0, f) = F0;
@@ -582,10 +618,25 @@ __device__ void dinv_cells(int N, int nb, const T *J, T *Dinv, int first, int st
 }
 
 // Galerkin coarse operator (Eq. 17): sums of fine blocks over aggregate pairs.
+// An interior aggregate (2j, 2j+1) of a three-block fine level has the
+// coarse blocks J_-1(2j), J_0(2j) + J_+1(2j) + J_-1(2j+1) + J_0(2j+1) and
+// J_+1(2j+1), summed in the order of the general loop below.
 template <typename T>
 __device__ void coarse_op_cells(int Nf, int nbf, const T *Jf, int Nc, T *Jc, int first, int stride) {
   const int hf = (nbf - 1) / 2;
   for (int j = first; j < Nc; j += stride) {
+    if (nbf == 3 && j > 0 && 2 * j + 2 < Nf) {
+      const int x0 = 2 * j, x1 = 2 * j + 1;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        Jc[(0 * 4 + e) * Nc + j] = Jf[(0 * 4 + e) * Nf + x0];
+        Jc[(1 * 4 + e) * Nc + j] =
+            ((Jf[(1 * 4 + e) * Nf + x0] + Jf[(2 * 4 + e) * Nf + x0]) + Jf[(0 * 4 + e) * Nf + x1]) +
+            Jf[(1 * 4 + e) * Nf + x1];
+        Jc[(2 * 4 + e) * Nc + j] = Jf[(2 * 4 + e) * Nf + x1];
+      }
+      continue;
+    }
     T a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};
     for (int a = 0; a < 2; ++a) {
       int xi = 2 * j + a;
@@ -616,7 +667,9 @@ __device__ void coarse_op_cells(int Nf, int nbf, const T *Jf, int Nc, T *Jc, int
 // applied `reps` times in a row. Cells of one colour do not couple, so a
 // repeated visit of the same colour sees the same neighbour values: the
 // correction t is computed once and the relaxation applied reps times, which
-// is exactly the sequence of reps separate passes.
+// is exactly the sequence of reps separate passes. The neighbour sum is a
+// chain of fused multiply-adds (two per product pair instead of a multiply,
+// a fused multiply-add and an add).
 template <typename T>
 __device__ void sor_colour(int N, int nb, const T *J, const T *Dinv, const T *R, T *dU, double omega_d, int C,
                            int col, int reps, int first, int stride) {
@@ -628,8 +681,10 @@ __device__ void sor_colour(int N, int nb, const T *J, const T *Dinv, const T *R,
       int i = j + k - hw;
       if (k == hw || i < 0 || i >= N) continue;
       T x0 = dU[i], x1 = dU[N + i];
-      r0 += J[(k * 4 + 0) * N + j] * x0 + J[(k * 4 + 1) * N + j] * x1;
-      r1 += J[(k * 4 + 2) * N + j] * x0 + J[(k * 4 + 3) * N + j] * x1;
+      r0 = fma(J[(k * 4 + 0) * N + j], x0, r0);
+      r0 = fma(J[(k * 4 + 1) * N + j], x1, r0);
+      r1 = fma(J[(k * 4 + 2) * N + j], x0, r1);
+      r1 = fma(J[(k * 4 + 3) * N + j], x1, r1);
     }
     T t0 = Dinv[0 * N + j] * r0 + Dinv[1 * N + j] * r1;
     T t1 = Dinv[2 * N + j] * r0 + Dinv[3 * N + j] * r1;
@@ -658,8 +713,10 @@ __device__ void restrict_cells(int Nf, int nb, const T *J, const T *R, const T *
         int eta = xi + k - hw;
         if (eta < 0 || eta >= Nf) continue;
         T x0 = dU[eta], x1 = dU[Nf + eta];
-        r0 += J[(k * 4 + 0) * Nf + xi] * x0 + J[(k * 4 + 1) * Nf + xi] * x1;
-        r1 += J[(k * 4 + 2) * Nf + xi] * x0 + J[(k * 4 + 3) * Nf + xi] * x1;
+        r0 = fma(J[(k * 4 + 0) * Nf + xi], x0, r0);
+        r0 = fma(J[(k * 4 + 1) * Nf + xi], x1, r0);
+        r1 = fma(J[(k * 4 + 2) * Nf + xi], x0, r1);
+        r1 = fma(J[(k * 4 + 3) * Nf + xi], x1, r1);
       }
       s0 += r0;
       s1 += r1;
@@ -1459,6 +1516,8 @@ cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_par
   case 1: launch_shape<1>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   case 2: launch_shape<2>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   case 3: launch_shape<3>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
+  case 4: launch_shape<4>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
+  case 5: launch_shape<5>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   default: launch_shape<0>(tasks, count, prm, n_cap, ldab_cap, smem, s); break;
   }
   return cudaGetLastError();
