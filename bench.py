@@ -53,10 +53,11 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM G
 SOR_PASS_TRAFFIC_512 = 34.606336e6 + 0.020480e6
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_solve launch of the 608-channel J3 step
 # per (precision, launch shape, stopping tolerance), each from a one-pass ncu capture of
-# `bench.py --steps 1 --warmup 3 --no-cpu --shape S [--precision mixed] --tol T`; no entry: not captured
+# `bench.py --steps 1 --warmup 3 --no-cpu --no-serving --shape S [--precision mixed]`; no entry: not captured
 # (the bytes grow with the Newton steps, so a capture stands only for its own tolerance).
-TRAFFIC_608 = {("fp64", "256x4", 1e-10): 186.38e9 + 104.80e9, ("fp64", "128x4", 1e-10): 216.09e9 + 104.06e9,
-               ("mixed", "256x4", 1e-10): 99.28e9 + 64.18e9}
+TRAFFIC_608 = {("fp64", "128x4", 1e-10): 209567876096 + 103480428800,
+               ("mixed", "256x4", 3e-13): 153810537216 + 96052265472,
+               ("mixed", "192x4", 3e-13): 144785353728 + 91365382400}
 
 
 # The 1D workloads of the default line: the irregular channel (N = 4096, the metric's configuration)
