@@ -48,6 +48,14 @@ MIXED_BOUND = 1e-10  # relative distance to the converged FP64 discrete solution
 # Derived FMA peaks (reported beside the measured ones of measure_fma_peaks, which the rooflines use)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x FP64 FMA/clk/SM x 2 flop x max SM GHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max SM GHz
+# The latency form of the 1D solve timed beside the block form: cluster sizes and the smallest
+# multigrid level (cells) run on every CTA of the cluster.
+CLUSTER_CTAS = (8, 16)
+CLUSTER_TEAM_CELLS = 1024
+# Light-load serving latency: the first LIGHT_REQUESTS serving requests arriving at LIGHT_RATE per second,
+# through the server in the block form and with its cluster form (LIGHT_CTAS CTAs per problem while at most
+# LIGHT_MAX_IN_FLIGHT solves are in flight: 16 x 9 = 144 of the 152 SMs).
+LIGHT_REQUESTS, LIGHT_RATE, LIGHT_CTAS, LIGHT_MAX_IN_FLIGHT = 128, 25.0, 16, 9
 # DRAM bytes (read + write) of one colour pass of k2_sor_split<double, J9> at 512 x 256 with colour-major J9,
 # from one ncu capture of `bench.py --workload wedge2d --phases-only` (None: not captured for this kernel).
 SOR_PASS_TRAFFIC_512 = 34.606336e6 + 0.020480e6
@@ -497,6 +505,25 @@ def run_gpu(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         single.append(e0.elapsed_time(e1))
+    # the latency form: the same solves, each alone on a thread-block cluster
+    single_cluster = {}
+    for ctas in CLUSTER_CTAS:
+        try:
+            nswe.nswe_ctx_set_solve_cluster(ctx, ctas, CLUSTER_TEAM_CELLS)
+            t = []
+            for s in range(3):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                nswe.nswe_newton_solve(ctx, probs[s], U0s[s], Us[s], prm, want_info=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t.append(e0.elapsed_time(e1))
+            single_cluster[str(ctas)] = statistics.median(t)
+        except nswe.NsweError as e:
+            single_cluster[str(ctas)] = f"unavailable: {e}"
+        finally:
+            nswe.nswe_ctx_set_solve_cluster(ctx, 1, CLUSTER_TEAM_CELLS)
 
     # ---- end to end through the C ABI from pinned host buffers: every step
     # uploads all problems' geometry (one batched call) and guesses, solves,
@@ -555,7 +582,11 @@ def run_gpu(args, rank, world, local_rank):
             "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99),
                            "what": "per-solve completion time from the start of its batch (device timer)",
                            "solve_p50": pct(dur, 50), "solve_p99": pct(dur, 99),
-                           "single_solve_alone": statistics.median(single)},
+                           "single_solve_alone": statistics.median(single),
+                           "single_solve_cluster": single_cluster,
+                           "single_solve_cluster_what": "the same solve alone on a thread-block cluster of that "
+                                                        "many CTAs (nswe_ctx_set_solve_cluster; multigrid levels "
+                                                        f"of >= {CLUSTER_TEAM_CELLS} cells on every CTA)"},
             "converged": {"all_status_ok": all(s == 0 for s in status), "max_res": max(res0),
                           "mean_newton_iters": statistics.mean(i["total_iters"] for i in infos)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -787,16 +818,19 @@ def serving_requests(M, tol, mixed):
     return inps, prms
 
 
-def serve1d_measure(inps, prms, rate, streams, max_batch, mem_gb, warm, seed=4999):
+def serve1d_measure(inps, prms, rate, streams, max_batch, mem_gb, warm, seed=4999, cluster=None):
     """One pass of the requests through a fresh continuous-batching server:
     `warm` requests first (discarded), then all of them arriving as a seeded
-    Poisson process at `rate` per second (rate = inf: all at once). Returns
-    the results per request, the per-request host timestamps and the
+    Poisson process at `rate` per second (rate = inf: all at once). cluster:
+    None, or (ctas, max_in_flight) for the server's light-load cluster form.
+    Returns the results per request, the per-request host timestamps and the
     server's launch count."""
     import numpy as np
     from paper_2505_10857_gb300 import nswe
     M = len(inps)
     sv = nswe.Server(0, device_bytes=mem_gb << 30, host_bytes=1 << 30, streams=streams, max_batch=max_batch)
+    if cluster:
+        sv.set_cluster(cluster[0], cluster[1], CLUSTER_TEAM_CELLS)
     results = {}
 
     def drain(block_until=None):
@@ -874,6 +908,54 @@ def _parity(Us, infos, refs, idx):
             "reference": f"the oracle's converged discrete solution (res < {TOL_CONVERGED:g})", "bound": MIXED_BOUND}
 
 
+def run_latency1d(args):
+    """Single-solve latency of the 1D channel workload (N = 4096, 8 levels, J3)
+    in the block form and in the cluster form over cluster sizes and the
+    smallest multigrid level run on every CTA (team_cells): each of the first
+    three instances solved alone, the median of the three (CUDA events). FP64
+    at res < TOL and mixed precision at res < TOL_SOLUTION. Prints one JSON
+    line."""
+    import statistics
+
+    import torch
+
+    from paper_2505_10857_gb300 import nswe
+    inps, _ = make_instances(0, 3, 3)
+    ctx = nswe.Context(0)
+    probs = [nswe.Problem1D.from_inputs(ctx, p) for p in inps]
+    U0s = [torch.from_numpy(p.U0_start).cuda() for p in inps]
+    Us = [torch.zeros(2, p.N, dtype=torch.float64, device="cuda") for p in inps]
+    stream = torch.cuda.current_stream()
+    rows = []
+    for prec, tol in ((nswe.PREC_FP64, TOL), (nswe.PREC_MIXED, TOL_SOLUTION)):
+        from paper_2505_10857_gb300 import inputs as I
+        prm = nswe.params_from(I.Params1D.for_problem(inps[0], tol=tol, n_max=800))
+        prm.precision = prec
+        nswe.nswe_ctx_set_solve_shape(ctx, prec, 3)  # 128 x 4: no spills, the best single-block shape
+        configs = [(1, CLUSTER_TEAM_CELLS)] + [(c, t) for c in (2, 4, 8, 16)
+                                               for t in (256, 512, 1024, 2048, 4096, 1 << 30)]
+        for ctas, cells in configs:
+            nswe.nswe_ctx_set_solve_cluster(ctx, ctas, cells)
+            ms, its = [], []
+            for k in range(3):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = nswe.nswe_newton_solve(ctx, probs[k], U0s[k], Us[k], prm)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                its.append(info["total_iters"])
+            rows.append({"precision": "mixed" if prec == nswe.PREC_MIXED else "fp64", "ctas": ctas,
+                         "team_cells": cells, "ms_median": statistics.median(ms), "newton_steps": its})
+        nswe.nswe_ctx_set_solve_cluster(ctx, 1, CLUSTER_TEAM_CELLS)
+    print(json.dumps({"metric": "single-solve latency (ms), 1D irregular channel N=4096, 8-level MG, J3",
+                      "config": {"workload": "1D irregular channel, N=4096, 8-level MG, J3, seeds 2000-2002",
+                                 "what": "each instance alone, CUDA events, median of three; ctas 1: one block "
+                                         "of 128 threads"},
+                      "rows": rows}), flush=True)
+
+
 def serving_comparison(args, ctx):
     """The metric's comparison, measured beside the default line: the batched
     mixed-precision serving form (the 1D serving workload through the
@@ -898,6 +980,19 @@ def serving_comparison(args, ctx):
     sat = serve1d_measure(inps, prm_mixed, math.inf, args.streams, args.max_batch, args.serve_mem_gb, 64)
     paced = serve1d_measure(inps, prm_mixed, args.rate, args.streams, args.max_batch, args.serve_mem_gb, 64)
     sat64 = serve1d_measure(inps, prm_fp64, math.inf, args.streams, args.max_batch, args.serve_mem_gb, 64)
+    # light load, where a request's latency is its own solve time: block form against the cluster form
+    nl = min(M, LIGHT_REQUESTS)
+    light = {}
+    for form, cl in (("block_form", None), ("cluster_form", (LIGHT_CTAS, LIGHT_MAX_IN_FLIGHT))):
+        r = serve1d_measure(inps[:nl], prm_mixed[:nl], LIGHT_RATE, args.streams, args.max_batch, args.serve_mem_gb, 8,
+                            cluster=cl)
+        light[form] = {"p50": pct(r["lat_ms"], 50), "p99": pct(r["lat_ms"], 99), "max": r["lat_ms"][-1],
+                       "converged": len(r["ok"]), "of": nl}
+    light["cluster_form"].update({"ctas": LIGHT_CTAS, "max_in_flight": LIGHT_MAX_IN_FLIGHT})
+    light.update({"offered_rate": LIGHT_RATE, "requests": nl,
+                  "what": "completion minus submission per request (host clock), seeded Poisson arrivals, mixed "
+                          "precision; the cluster form runs a launch's problems on thread-block clusters while "
+                          "at most max_in_flight 1D solves are in flight"})
     # the plain FP64 single-instance path: one request at a time, one solve per launch
     K = args.single_requests
     stream = torch.cuda.current_stream()
@@ -931,7 +1026,8 @@ def serving_comparison(args, ctx):
                                                    "p99": pct(paced["lat_ms"], 99), "max": paced["lat_ms"][-1],
                                                    "completed_per_s_over_run": paced["value"],
                                                    "what": "completion minus submission per request (host clock), "
-                                                           "seeded Poisson arrivals"}},
+                                                           "seeded Poisson arrivals"},
+                    "latency_ms_light_load": light},
         "serving_fp64": {"value": sat64["value"], "unit": UNIT, "precision": "FP64",
                          "form": "the same server and requests in FP64", "converged": len(sat64["ok"]), "of": M},
         "plain_fp64_single": {"value": single_value, "unit": UNIT, "precision": "FP64",
@@ -1342,7 +1438,7 @@ def main():
                     help="fp64: every step in FP64; mixed: FP32 Jacobian and multigrid, FP64 residual and update")
     ap.add_argument("--workload", default="channel1d",
                     choices=["channel1d", "wedge2d", "serve1d", "batch2d", "serve2d", "jac1d", "peaks",
-                             "autotune2d"])
+                             "autotune2d", "latency1d"])
     ap.add_argument("--batch2d", type=int, default=16, help="batch2d: 2D problems per batch")
     ap.add_argument("--batch2d-mode", choices=["lockstep", "concurrent"], default="lockstep",
                     help="batch2d: shared launches over all problems, or concurrent per-problem streams")
@@ -1406,6 +1502,11 @@ def main():
         from paper_2505_10857_gb300 import build
         build.build()
         run_jac1d(args)
+        return
+    if args.workload == "latency1d":
+        from paper_2505_10857_gb300 import build
+        build.build()
+        run_latency1d(args)
         return
     if args.workload == "serve2d":
         from paper_2505_10857_gb300 import build

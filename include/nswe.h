@@ -10,7 +10,9 @@
  * solved by the geometric multigrid of Section 3.4 inside the nested NMGM of
  * Algorithm 3; the two-dimensional model of Section 4 (J21 / J9) through the
  * same calls. Arithmetic is FP64, with an optional mixed-precision solve in
- * 1D and 2D (NSWE_PREC_MIXED). A continuous-batching server for streams of
+ * 1D and 2D (NSWE_PREC_MIXED). A 1D solve runs on one thread block (many
+ * problems per launch) or, for latency, on a thread-block cluster
+ * (nswe_ctx_set_solve_cluster). A continuous-batching server for streams of
  * 1D and 2D solves sits at the end of this header.
  *
  * Conventions
@@ -462,6 +464,25 @@ nswe_status nswe_solve_shape_info(int shape, int *threads, int *blocks_per_sm);
 nswe_status nswe_ctx_set_solve_shape(nswe_ctx ctx, int precision, int shape);
 nswe_status nswe_ctx_get_solve_shape(nswe_ctx ctx, int precision, int *shape);
 
+/* Latency form of the 1D solve (the paper has no counterpart; Algorithm 3
+ * itself is unchanged): with ctas >= 2, nswe_newton_solve and
+ * nswe_newton_solve_batch give each 1D problem a thread-block cluster of
+ * `ctas` CTAs (128 threads each) on as many SMs instead of one thread block.
+ * The residual, Jacobian, update and the multigrid levels of at least
+ * team_cells cells run on all CTAs of the cluster, with cluster barriers
+ * between phases; the coarser levels and the coarsest LU run on its first
+ * CTA. Every cell sees the same arithmetic as in the block form; the sum
+ * that forms res is taken in another order, so res (and in rare cases the
+ * Newton step at which it crosses tol) may differ in the last bits.
+ * Worthwhile for few problems at a time (one solve's latency); a full batch
+ * runs faster in the block form. ctas = 1 restores the block form (the
+ * default); 2..16 (sizes above 8 need the GPU's non-portable cluster sizes);
+ * team_cells >= 1; NSWE_EINVAL otherwise. LLF problems always run in the
+ * block form. nswe_ctx_get_solve_cluster reads both settings (either
+ * pointer may be NULL). */
+nswe_status nswe_ctx_set_solve_cluster(nswe_ctx ctx, int ctas, int team_cells);
+nswe_status nswe_ctx_get_solve_cluster(nswe_ctx ctx, int *ctas, int *team_cells);
+
 /* Autotuner of the launch shape (the paper has no counterpart): solves the
  * given 1D batch once untimed and `reps` times timed (CUDA events on the
  * context stream) in every shape, records the fastest for params->precision
@@ -632,6 +653,16 @@ nswe_status nswe_server_take(nswe_server s, unsigned long long ticket,
                              nswe_server_times *times);
 
 nswe_status nswe_server_query(nswe_server s, nswe_server_stats *out);
+
+/* Latency form for light load (see nswe_ctx_set_solve_cluster): a 1D launch
+ * runs each of its problems on a thread-block cluster of `ctas` CTAs when the
+ * 1D solves in flight, the launch's own included, are at most
+ * max_in_flight; otherwise, and always with ctas = 1 (the default), one
+ * thread block per problem. team_cells as in nswe_ctx_set_solve_cluster.
+ * May be called at any time; applies from the next launch. EINVAL for ctas
+ * outside 1..16, max_in_flight < 0 or team_cells < 1. */
+nswe_status nswe_server_set_cluster(nswe_server s, int ctas, int max_in_flight,
+                                    int team_cells);
 
 /* Stops the scheduler after the launched work finishes, frees everything;
  * requests not yet launched are dropped. */

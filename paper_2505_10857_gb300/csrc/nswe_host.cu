@@ -1250,8 +1250,11 @@ static nswe_status solve_batch_common(nswe_ctx ctx, int count, const nswe_prob *
       cudaSuccess)
     return NSWE_ECUDA;
   const int shape = ctx->solve_shape[params->precision == NSWE_PREC_MIXED ? 1 : 0];
-  if (launch_solve_sized(ctx->tasks, count, *params, max_coarse, nb, shape, s, probs[0]->host.flux) != cudaSuccess)
-    return NSWE_ECUDA;
+  const cudaError_t le =
+      (ctx->solve_ctas > 1 && probs[0]->host.flux == NSWE_FLUX_HLL)
+          ? launch_solve_cluster(ctx->tasks, count, *params, max_coarse, nb, ctx->solve_ctas, ctx->team_cells, s)
+          : launch_solve_sized(ctx->tasks, count, *params, max_coarse, nb, shape, s, probs[0]->host.flux);
+  if (le != cudaSuccess) return NSWE_ECUDA;
   if (infos) {
     if (cudaMemcpyAsync(infos, ctx->infos, sizeof(nswe_info) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return NSWE_ECUDA;
@@ -1292,6 +1295,20 @@ nswe_status nswe_ctx_set_solve_shape(nswe_ctx ctx, int precision, int shape) {
   if (!ctx || (precision != NSWE_PREC_FP64 && precision != NSWE_PREC_MIXED) || shape < 0 || shape >= kSolveShapes)
     return NSWE_EINVAL;
   ctx->solve_shape[precision == NSWE_PREC_MIXED ? 1 : 0] = shape;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_set_solve_cluster(nswe_ctx ctx, int ctas, int team_cells) {
+  if (!ctx || ctas < 1 || ctas > kMaxClusterCtas || team_cells < 1) return NSWE_EINVAL;
+  ctx->solve_ctas = ctas;
+  ctx->team_cells = team_cells;
+  return NSWE_OK;
+}
+
+nswe_status nswe_ctx_get_solve_cluster(nswe_ctx ctx, int *ctas, int *team_cells) {
+  if (!ctx) return NSWE_EINVAL;
+  if (ctas) *ctas = ctx->solve_ctas;
+  if (team_cells) *team_cells = ctx->team_cells;
   return NSWE_OK;
 }
 

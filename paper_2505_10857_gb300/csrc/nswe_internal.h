@@ -22,6 +22,10 @@ constexpr int kSolveShapes = 6;
 constexpr int kSolveShapeThreads[kSolveShapes] = {256, 128, 256, 128, 160, 192};
 constexpr int kSolveShapeBlocks[kSolveShapes] = {4, 8, 2, 4, 4, 4};
 constexpr int kMaxCoarse = 128;    // max cells of the coarsest level (direct solve)
+// The latency form of the solve kernel: one problem per thread-block cluster
+// of up to kMaxClusterCtas CTAs of kClusterThreads threads.
+constexpr int kClusterThreads = 128;
+constexpr int kMaxClusterCtas = 16;
 
 // One nested / multigrid level of a 1D problem. Geometry is read-only input;
 // the rest is solver workspace owned by the problem.
@@ -280,6 +284,10 @@ cudaError_t launch_solve(const SolveTask *tasks, int count, const nswe_params &p
 // which runs in the default shape).
 cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                                int max_nb, int shape, cudaStream_t s, int flux = NSWE_FLUX_HLL);
+// One problem per cluster of `ctas` CTAs (2..kMaxClusterCtas, HLL flux):
+// multigrid levels with at least team_cells cells run on the whole cluster.
+cudaError_t launch_solve_cluster(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
+                                 int max_nb, int ctas, int team_cells, cudaStream_t s);
 // Parameter checks shared by the entry points (eps of levels 0..first_level).
 nswe_status check_params_1d(const nswe_params *p, int levels, int first_level);
 // Parameter checks of a 2D solve (the frozen linearisation allowed).
@@ -308,6 +316,8 @@ struct nswe_ctx_s {
   nswe_params *prms;     // device per-task parameters (nswe_newton_solve_batch_each)
   int cap;               // capacity of tasks / infos / prms
   int solve_shape[2];    // launch shape of the 1D solve kernel per precision
+  int solve_ctas = 1;    // 1D solves: CTAs per problem (1: a block per problem; 2..16: a cluster)
+  int team_cells = 1024; // cluster form: multigrid levels with at least this many cells on every CTA
   int batch2d_lockstep = 1;  // 2D batches: 1 lockstep batched launches (default), 0 concurrent solves
   int cm2d_min_cells = 131072;  // 2D Newton levels of at least this many cells store J9 colour-major
   int jac2d_cell_min = nswe::kJac2CellMinDefault;  // 2D levels from which the per-cell Jacobian kernel runs

@@ -9,6 +9,8 @@
 // solve of one problem with __syncthreads() between phases and no host
 // round trip. Problem data and workspace stay in device memory (L2 resident
 // for the 1D sizes); the coarsest factorisation lives in shared memory.
+#include <cooperative_groups.h>
+
 #include <cmath>
 #include <type_traits>
 
@@ -289,6 +291,68 @@ __device__ double block_sum(double v, double *red) {
   __syncthreads();
   return s;
 }
+
+// ----------------------------------------------------------------------------
+// Teams: the threads that share one problem's phases. BlockTeam is one
+// thread block (the batched form: one problem per block). ClusterTeam is a
+// thread-block cluster of up to 16 CTAs on as many SMs (the latency form:
+// one problem per cluster): the per-cell loops of a phase are strided over
+// all its threads, phases are separated by cluster barriers (release /
+// acquire at cluster scope, so the global writes of one phase are visible to
+// every CTA in the next), and the coarse levels and the coarsest LU run on
+// the leader CTA alone with block barriers. Every cluster barrier is reached
+// by all threads of the cluster: the branches around them depend only on
+// values that are the same in every CTA (sizes, and res, flags and counters
+// reduced over the cluster).
+struct BlockTeam {
+  __device__ __forceinline__ int tid() const { return threadIdx.x; }
+  __device__ __forceinline__ int size() const { return blockDim.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ bool lead() const { return true; }
+  static constexpr bool kMulti = false;
+  // the same sum in every thread (fixed order)
+  __device__ __forceinline__ double sum(double v, double *red) const { return block_sum(v, red); }
+  __device__ __forceinline__ bool any(bool b) const { return __syncthreads_or(b) != 0; }
+  // the leader's value of a flag in every thread (after the leader wrote it)
+  __device__ __forceinline__ int lead_value(const int *flag) const { return *flag; }
+};
+
+struct ClusterTeam {
+  int rank, n;
+  __device__ __forceinline__ int tid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+  __device__ __forceinline__ int size() const { return n * (int)blockDim.x; }
+  __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+  __device__ __forceinline__ bool lead() const { return rank == 0; }
+  static constexpr bool kMulti = true;
+  // CTA partials in rank order: every thread adds the same values in the same
+  // order. red[33] holds this CTA's partial until all CTAs have read it.
+  __device__ double sum(double v, double *red) const {
+    const double part = block_sum(v, red);
+    if (threadIdx.x == 0) red[33] = part;
+    sync();
+    auto cl = cooperative_groups::this_cluster();
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) s += *cl.map_shared_rank(red + 33, r);
+    sync();
+    return s;
+  }
+  __device__ bool any(bool b) const {
+    __shared__ int s_any;
+    const int mine = __syncthreads_or(b);
+    if (threadIdx.x == 0) s_any = mine;
+    sync();
+    auto cl = cooperative_groups::this_cluster();
+    int a = 0;
+    for (int r = 0; r < n; ++r) a |= *cl.map_shared_rank(&s_any, r);
+    sync();
+    return a != 0;
+  }
+  __device__ int lead_value(const int *flag) const {
+    const int v = *cooperative_groups::this_cluster().map_shared_rank(const_cast<int *>(flag), 0);
+    sync();
+    return v;
+  }
+};
 
 // Residual of cells [first, N) with stride; returns sum_j ||R_j||_1.
 __device__ double residual_cells(const Geo &G, const double *U, double *R, int first, int stride) {
@@ -1023,6 +1087,8 @@ __device__ void band_lu_solve_serial(const Band<T> &B) {
 // Assemble the band matrix from J (all threads), then factor (warp 0 in
 // FP64, thread 0 in FP32). Returns true if a pivot was exactly zero (all
 // threads).
+__shared__ int s_sing;
+
 template <typename T>
 __device__ bool band_factor(Band<T> &B, int N, int nb, const T *J) {
   const int hw = (nb - 1) / 2;
@@ -1039,7 +1105,6 @@ __device__ bool band_factor(Band<T> &B, int N, int nb, const T *J) {
     B.A(2 * j + l, 2 * i + m) = J[(k * 4 + e) * N + j];
   }
   __syncthreads();
-  __shared__ int s_sing;
   if constexpr (std::is_same<T, double>::value) {
     if (threadIdx.x < 32) {
       const bool sing = band_lu_warp<T>(B);
@@ -1101,22 +1166,50 @@ __device__ void mg_bind(MG<T> &mg, const ProbDev &P, int l0, int nb0, const T *J
   }
 }
 
+// First multigrid level run by the leader CTA alone: a cluster team runs
+// the levels with at least team_cells cells (from l0 down) on all its CTAs
+// and the coarser ones, with the coarsest solve, on the leader; a block team
+// runs every level (the coarsest solve is level L).
+template <typename T, class TM>
+__device__ __forceinline__ int team_split(const MG<T> &mg, int team_cells) {
+  if constexpr (!TM::kMulti) return mg.L;
+  int lt = mg.l0;
+  while (lt < mg.L && mg.N[lt] >= team_cells) ++lt;
+  return lt;
+}
+
 // Coarse operators, diagonal inverses and the coarsest factorisation; done
-// once per Newton step since J is fixed during its V-cycles.
-template <typename T>
-__device__ bool mg_setup(const MG<T> &mg, Band<T> &B) {
-  for (int l = mg.l0 + 1; l <= mg.L; ++l) {
-    coarse_op_cells(mg.N[l - 1], mg.nb[l - 1], mg.J[l - 1], mg.N[l], mg.J[l], threadIdx.x, blockDim.x);
-    __syncthreads();
+// once per Newton step since J is fixed during its V-cycles. Returns whether
+// a pivot was exactly zero, in every thread of the team.
+template <typename T, class TM = BlockTeam>
+__device__ bool mg_setup(const MG<T> &mg, Band<T> &B, const TM &team = TM(), int team_cells = 0) {
+  const int lt = team_split<T, TM>(mg, team_cells);
+  for (int l = mg.l0 + 1; l < lt; ++l) {
+    coarse_op_cells(mg.N[l - 1], mg.nb[l - 1], mg.J[l - 1], mg.N[l], mg.J[l], team.tid(), team.size());
+    team.sync();
   }
-  for (int l = mg.l0; l < mg.L; ++l) dinv_cells(mg.N[l], mg.nb[l], mg.J[l], mg.Dinv[l], threadIdx.x, blockDim.x);
-  return band_factor(B, mg.N[mg.L], mg.nb[mg.L], mg.J[mg.L]);
+  if (team.lead())
+    for (int l = max(mg.l0 + 1, lt); l <= mg.L; ++l) {
+      coarse_op_cells(mg.N[l - 1], mg.nb[l - 1], mg.J[l - 1], mg.N[l], mg.J[l], threadIdx.x, blockDim.x);
+      __syncthreads();
+    }
+  for (int l = mg.l0; l < lt; ++l) dinv_cells(mg.N[l], mg.nb[l], mg.J[l], mg.Dinv[l], team.tid(), team.size());
+  bool sing = false;
+  if (team.lead()) {
+    for (int l = lt; l < mg.L; ++l) dinv_cells(mg.N[l], mg.nb[l], mg.J[l], mg.Dinv[l], threadIdx.x, blockDim.x);
+    sing = band_factor(B, mg.N[mg.L], mg.nb[mg.L], mg.J[mg.L]);
+  }
+  if constexpr (TM::kMulti) {
+    team.sync();  // the team's inverses and the leader's factors and flag are done
+    sing = team.lead_value(&s_sing) != 0;
+  }
+  return sing;
 }
 
 // `steps` symmetric multicolour SOR steps (colours 0..C-1 then C-1..0 each);
 // consecutive visits of one colour run as one pass.
-template <typename T>
-__device__ void sor_smooth(const MG<T> &mg, int l, int steps, double omega) {
+template <typename T, class TM = BlockTeam>
+__device__ void sor_smooth(const MG<T> &mg, int l, int steps, double omega, const TM &team = TM()) {
   const int nb = mg.nb[l], C = (nb - 1) / 2 + 1;
   int prev = -1, reps = 0;
   for (int s = 0; s < steps; ++s)
@@ -1127,33 +1220,51 @@ __device__ void sor_smooth(const MG<T> &mg, int l, int steps, double omega) {
         continue;
       }
       if (prev >= 0) {
-        sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, prev, reps, threadIdx.x,
-                   blockDim.x);
-        __syncthreads();
+        sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, prev, reps, team.tid(),
+                   team.size());
+        team.sync();
       }
       prev = col;
       reps = 1;
     }
   if (prev >= 0) {
-    sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, prev, reps, threadIdx.x, blockDim.x);
-    __syncthreads();
+    sor_colour(mg.N[l], nb, mg.J[l], mg.Dinv[l], mg.R[l], mg.dU[l], omega, C, prev, reps, team.tid(), team.size());
+    team.sync();
   }
 }
 
-// Algorithm 2 from level l0, unrolled over levels.
-template <typename T>
-__device__ void mg_vcycle(const MG<T> &mg, const Band<T> &B, const nswe_params &prm) {
-  for (int l = mg.l0; l < mg.L; ++l) {
-    sor_smooth(mg, l, prm.nu1, prm.omega);
+// Algorithm 2 from level l0, unrolled over levels. A cluster team smooths,
+// restricts and prolongs the levels l0..lt-1; the leader CTA runs the
+// V-cycle below them (levels lt..L) between two cluster barriers.
+template <typename T, class TM = BlockTeam>
+__device__ void mg_vcycle(const MG<T> &mg, const Band<T> &B, const nswe_params &prm, const TM &team = TM(),
+                          int team_cells = 0) {
+  const int lt = team_split<T, TM>(mg, team_cells);
+  for (int l = mg.l0; l < lt; ++l) {
+    sor_smooth(mg, l, prm.nu1, prm.omega, team);
     restrict_cells(mg.N[l], mg.nb[l], mg.J[l], mg.R[l], mg.dU[l], mg.N[l + 1], mg.R[l + 1], mg.dU[l + 1],
-                   threadIdx.x, blockDim.x);
-    __syncthreads();
+                   team.tid(), team.size());
+    team.sync();
   }
-  band_solve(B, mg.N[mg.L], mg.R[mg.L], mg.dU[mg.L]);
-  for (int l = mg.L - 1; l >= mg.l0; --l) {
-    prolong_cells(mg.N[l], mg.dU[l], mg.N[l + 1], mg.dU[l + 1], threadIdx.x, blockDim.x);
-    __syncthreads();
-    sor_smooth(mg, l, prm.nu2, prm.omega);
+  if (team.lead()) {
+    for (int l = lt; l < mg.L; ++l) {
+      sor_smooth(mg, l, prm.nu1, prm.omega);
+      restrict_cells(mg.N[l], mg.nb[l], mg.J[l], mg.R[l], mg.dU[l], mg.N[l + 1], mg.R[l + 1], mg.dU[l + 1],
+                     threadIdx.x, blockDim.x);
+      __syncthreads();
+    }
+    band_solve(B, mg.N[mg.L], mg.R[mg.L], mg.dU[mg.L]);
+    for (int l = mg.L - 1; l >= lt; --l) {
+      prolong_cells(mg.N[l], mg.dU[l], mg.N[l + 1], mg.dU[l + 1], threadIdx.x, blockDim.x);
+      __syncthreads();
+      sor_smooth(mg, l, prm.nu2, prm.omega);
+    }
+  }
+  if constexpr (TM::kMulti) team.sync();
+  for (int l = lt - 1; l >= mg.l0; --l) {
+    prolong_cells(mg.N[l], mg.dU[l], mg.N[l + 1], mg.dU[l + 1], team.tid(), team.size());
+    team.sync();
+    sor_smooth(mg, l, prm.nu2, prm.omega, team);
   }
 }
 
@@ -1254,25 +1365,46 @@ __global__ void __launch_bounds__(kThreads) k_vcycle(const ProbDev *P, int level
   if (threadIdx.x == 0) *status = sing ? NSWE_ESINGULAR : NSWE_OK;
 }
 
-// Algorithm 3 for one problem per thread block. T is the precision of the
-// Jacobian and the multigrid solve of each Newton step: with T = double the
-// whole step is FP64; with T = float the residual, the convergence test and
-// the update U += tau dU stay FP64 while the FD Jacobian (Eq. 12-13), the
-// coarse operators, the smoother and the coarsest LU run in FP32.
-// FLUX: the numerical flux of every task of the launch (compile-time, so
-// that the HLL kernels carry no LLF code).
-template <typename T, int THREADS, int MINB, int FLUX>
+// The team of the calling thread and the index of its problem: a block per
+// problem, or a cluster per problem (clusters tile the grid along x).
+template <class TM>
+__device__ __forceinline__ TM make_team(int &task_index);
+template <>
+__device__ __forceinline__ BlockTeam make_team<BlockTeam>(int &task_index) {
+  task_index = blockIdx.x;
+  return BlockTeam{};
+}
+template <>
+__device__ __forceinline__ ClusterTeam make_team<ClusterTeam>(int &task_index) {
+  const auto cl = cooperative_groups::this_cluster();
+  ClusterTeam t{(int)cl.block_rank(), (int)cl.num_blocks()};
+  task_index = blockIdx.x / t.n;
+  return t;
+}
+
+// Algorithm 3 for one problem per team (a thread block, or a cluster of
+// blocks: TM). T is the precision of the Jacobian and the multigrid solve of
+// each Newton step: with T = double the whole step is FP64; with T = float
+// the residual, the convergence test and the update U += tau dU stay FP64
+// while the FD Jacobian (Eq. 12-13), the coarse operators, the smoother and
+// the coarsest LU run in FP32. FLUX: the numerical flux of every task of the
+// launch (compile-time, so that the HLL kernels carry no LLF code).
+// team_cells: a cluster team runs the multigrid levels with at least that
+// many cells on all its CTAs, the others on the leader CTA.
+template <typename T, int THREADS, int MINB, int FLUX, class TM = BlockTeam>
 __global__ void __launch_bounds__(THREADS, MINB)
-    k_solve(const SolveTask *tasks, nswe_params launch_prm, int n_cap, int ldab_cap) {
+    k_solve(const SolveTask *tasks, nswe_params launch_prm, int n_cap, int ldab_cap, int team_cells) {
   constexpr bool kMixed = std::is_same<T, float>::value;
-  __shared__ double red[33];
+  __shared__ double red[34];
   __shared__ nswe_params s_prm;
   const unsigned long long t_start = global_ns();
-  const SolveTask task = tasks[blockIdx.x];
+  int ti;
+  const TM team = make_team<TM>(ti);
+  const SolveTask task = tasks[ti];
   const ProbDev &P = *task.prob;
   if (threadIdx.x == 0) s_prm = task.prm ? *task.prm : launch_prm;
-  if (task.derive) geom_derive_items(P, threadIdx.x, blockDim.x);
-  __syncthreads();
+  if (task.derive) geom_derive_items(P, team.tid(), team.size());
+  team.sync();  // (a cluster team: also every CTA has started before any shared-memory access across CTAs)
   const nswe_params &prm = s_prm;
   const int L = P.levels - 1;
   const int s0 = (prm.nest_start < 0 || prm.nest_start > L) ? L : prm.nest_start;
@@ -1290,8 +1422,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
 
   {
     const int Ns = P.lev[s0].N;
-    for (int t = threadIdx.x; t < 2 * Ns; t += blockDim.x) P.lev[s0].U[t] = task.U0[t];
-    __syncthreads();
+    for (int t = team.tid(); t < 2 * Ns; t += team.size()) P.lev[s0].U[t] = task.U0[t];
+    team.sync();
   }
 
   for (int l = s0; l >= 0 && !fatal; --l) {
@@ -1299,8 +1431,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
     const Geo G = make_geo(P, l);
     const int N = G.N;
     if (l < s0) {
-      interp_cells(make_geo(P, l + 1), P.lev[l + 1].U, Lv.U, threadIdx.x, blockDim.x);
-      __syncthreads();
+      interp_cells(make_geo(P, l + 1), P.lev[l + 1].U, Lv.U, team.tid(), team.size());
+      team.sync();
     }
     const JW<T> W = jw_view<T>(P.jw, N);
     T *const J = reinterpret_cast<T *>(Lv.J);
@@ -1315,59 +1447,60 @@ __global__ void __launch_bounds__(THREADS, MINB)
       double acc;
       if constexpr (kMixed) {
         const RW RWv = rw_view(P.jw, N);
-        res_pass_a(G, Lv.U, RWv, threadIdx.x, blockDim.x);
-        __syncthreads();
-        res_pass_b<FLUX>(G, RWv, threadIdx.x, blockDim.x);
-        __syncthreads();
-        acc = res_pass_c(G, RWv, Lv.R, threadIdx.x, blockDim.x);
+        res_pass_a(G, Lv.U, RWv, team.tid(), team.size());
+        team.sync();
+        res_pass_b<FLUX>(G, RWv, team.tid(), team.size());
+        team.sync();
+        acc = res_pass_c(G, RWv, Lv.R, team.tid(), team.size());
       } else {
-        jac_pass_a<T>(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
-        __syncthreads();
-        jac_pass_b<T, FLUX>(G, W, threadIdx.x, blockDim.x);
-        __syncthreads();
-        acc = jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, nullptr, Lv.R, J, threadIdx.x, blockDim.x);
+        jac_pass_a<T>(G, Lv.U, prm.eps[l], W, team.tid(), team.size());
+        team.sync();
+        jac_pass_b<T, FLUX>(G, W, team.tid(), team.size());
+        team.sync();
+        acc = jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, nullptr, Lv.R, J, team.tid(), team.size());
       }
-      return block_sum(acc, red) / N;
+      return team.sum(acc, red) / N;
     };
     double res = residual_step();
     int n = 0, st = NSWE_OK;
     while (true) {
       if constexpr (kMixed) {
         // FP32 Jacobian at the current state, regularised with the FP64 R.
-        jac_pass_a<T>(G, Lv.U, prm.eps[l], W, threadIdx.x, blockDim.x);
-        __syncthreads();
-        jac_pass_b<T, FLUX>(G, W, threadIdx.x, blockDim.x);
-        __syncthreads();
-        jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, Lv.R, nullptr, J, threadIdx.x, blockDim.x);
-        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) Rs[t] = T(Lv.R[t]);
-        __syncthreads();
+        jac_pass_a<T>(G, Lv.U, prm.eps[l], W, team.tid(), team.size());
+        team.sync();
+        jac_pass_b<T, FLUX>(G, W, team.tid(), team.size());
+        team.sync();
+        jac_pass_c<T>(G, nb, prm.eps[l], prm.alpha, W, Lv.R, nullptr, J, team.tid(), team.size());
+        for (int t = team.tid(); t < 2 * N; t += team.size()) Rs[t] = T(Lv.R[t]);
+        team.sync();
       }
       MG<T> mg;
       mg_bind<T>(mg, P, l, nb, J, Rs, dU);
-      bool sing = mg_setup<T>(mg, B);
-      __syncthreads();
+      bool sing = mg_setup<T, TM>(mg, B, team, team_cells);
+      team.sync();
       if (sing) {
         st = NSWE_ESINGULAR;
         break;
       }
       if (l == L) {
-        band_solve<T>(B, N, Rs, dU);
+        if (team.lead()) band_solve<T>(B, N, Rs, dU);
+        if constexpr (TM::kMulti) team.sync();
       } else {
-        for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) dU[t] = T(0.0);
-        __syncthreads();
+        for (int t = team.tid(); t < 2 * N; t += team.size()) dU[t] = T(0.0);
+        team.sync();
         for (int m = 0; m < prm.nu3; ++m) {
-          mg_vcycle<T>(mg, B, prm);
+          mg_vcycle<T, TM>(mg, B, prm, team, team_cells);
           ++vcycles;
         }
       }
       bool bad = false;
-      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      for (int j = team.tid(); j < N; j += team.size()) {
         double h = Lv.U[j] + prm.tau * double(dU[j]);
         Lv.U[j] = h;
         Lv.U[N + j] += prm.tau * double(dU[N + j]);
         if (!(h > 0.0)) bad = true;
       }
-      bad = __syncthreads_or(bad);
+      bad = team.any(bad);
       ++n;
       if (bad) {
         st = NSWE_ENEGDEPTH;
@@ -1395,9 +1528,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
 
   if (!fatal) {
     const int N0 = P.lev[0].N;
-    for (int t = threadIdx.x; t < 2 * N0; t += blockDim.x) task.U[t] = P.lev[0].U[t];
+    for (int t = team.tid(); t < 2 * N0; t += team.size()) task.U[t] = P.lev[0].U[t];
   }
-  if (threadIdx.x == 0 && task.info) {
+  if (threadIdx.x == 0 && team.lead() && task.info) {
     nswe_info inf;
     for (int l = 0; l < NSWE_MAX_LEVELS; ++l) {
       inf.iters[l] = iters[l];
@@ -1414,9 +1547,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
   if (task.done) {
     // Every thread's result writes are visible system-wide before the flag.
     __threadfence_system();
-    __syncthreads();
-    if (threadIdx.x == 0) *reinterpret_cast<volatile int *>(task.done) = 1;
+    team.sync();
+    if (threadIdx.x == 0 && team.lead()) *reinterpret_cast<volatile int *>(task.done) = 1;
   }
+  if constexpr (TM::kMulti) team.sync();  // no CTA leaves while another may read its shared memory
 }
 
 int grid_for(int items) {
@@ -1498,11 +1632,46 @@ void launch_shape(const SolveTask *tasks, int count, const nswe_params &prm, int
                   cudaStream_t s) {
   constexpr int TH = kSolveShapeThreads[SHAPE], MB = kSolveShapeBlocks[SHAPE];
   if (prm.precision == NSWE_PREC_MIXED)
-    k_solve<float, TH, MB, FLUX><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+    k_solve<float, TH, MB, FLUX><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap, 0);
   else
-    k_solve<double, TH, MB, FLUX><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap);
+    k_solve<double, TH, MB, FLUX><<<count, TH, smem, s>>>(tasks, prm, n_cap, ldab_cap, 0);
 }
 }  // namespace
+
+namespace {
+template <typename T>
+cudaError_t launch_cluster_t(const SolveTask *tasks, int count, const nswe_params &prm, int n_cap, int ldab_cap,
+                             size_t smem, int ctas, int team_cells, cudaStream_t s) {
+  auto kern = k_solve<T, kClusterThreads, 1, NSWE_FLUX_HLL, ClusterTeam>;
+  if (ctas > 8) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)count * (unsigned)ctas, 1, 1);
+  cfg.blockDim = dim3(kClusterThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, tasks, prm, n_cap, ldab_cap, team_cells);
+}
+}  // namespace
+
+cudaError_t launch_solve_cluster(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
+                                 int max_nb, int ctas, int team_cells, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int n_cap = 2 * max_coarse_cells, ldab_cap = 3 * (max_nb == 5 ? 5 : 3) + 1;
+  const size_t smem = band_smem_bytes(n_cap, ldab_cap);
+  if (prm.precision == NSWE_PREC_MIXED)
+    return launch_cluster_t<float>(tasks, count, prm, n_cap, ldab_cap, smem, ctas, team_cells, s);
+  return launch_cluster_t<double>(tasks, count, prm, n_cap, ldab_cap, smem, ctas, team_cells, s);
+}
 
 cudaError_t launch_solve_sized(const SolveTask *tasks, int count, const nswe_params &prm, int max_coarse_cells,
                                int max_nb, int shape, cudaStream_t s, int flux) {

@@ -184,6 +184,10 @@ struct Batch {
 struct nswe_server_s {
   int device = 0;
   nswe_server_config cfg{};
+  // latency form (nswe_server_set_cluster): a 1D launch runs one problem per
+  // cluster of cl_ctas CTAs when the 1D solves in flight, its own included,
+  // are at most cl_max (cl_ctas 1: never)
+  std::atomic<int> cl_ctas{1}, cl_max{0}, cl_team_cells{1024};
   char *dev_base = nullptr;
   char *host_base = nullptr;      // pinned, mapped
   char *host_base_dev = nullptr;  // its device address
@@ -356,9 +360,12 @@ bool nswe_server_s::admit_and_launch(int s) {
   const int n = (int)take.size();
   nswe_params launch = take[0]->prm;
   const uint64_t tl = now_ns();
+  const int ctas = cl_ctas.load();
+  const bool cluster = ctas > 1 && (int)(running.size() + take.size()) <= cl_max.load();
   if (cudaMemcpyAsync(task_dev[s], task_host[s], sizeof(SolveTask) * n, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
-      launch_solve_sized(task_dev[s], n, launch, max_coarse, max_nb, 0, st) != cudaSuccess) {
+      (cluster ? launch_solve_cluster(task_dev[s], n, launch, max_coarse, max_nb, ctas, cl_team_cells.load(), st)
+               : launch_solve_sized(task_dev[s], n, launch, max_coarse, max_nb, 0, st)) != cudaSuccess) {
     error = NSWE_ECUDA;
     return false;
   }
@@ -809,6 +816,14 @@ nswe_status nswe_server_take(nswe_server sv, unsigned long long ticket, double *
   if (info) *info = r->info;
   if (times) *times = r->times;
   delete r;
+  return NSWE_OK;
+}
+
+nswe_status nswe_server_set_cluster(nswe_server sv, int ctas, int max_in_flight, int team_cells) {
+  if (!sv || ctas < 1 || ctas > kMaxClusterCtas || max_in_flight < 0 || team_cells < 1) return NSWE_EINVAL;
+  sv->cl_team_cells = team_cells;
+  sv->cl_max = max_in_flight;
+  sv->cl_ctas = ctas;
   return NSWE_OK;
 }
 

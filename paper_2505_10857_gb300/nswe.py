@@ -134,6 +134,9 @@ EXPORTS = {
     "nswe_solve_shape_info": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nswe_ctx_set_solve_shape": (_i, [_vp, _i, _i]),
     "nswe_ctx_get_solve_shape": (_i, [_vp, _i, ctypes.POINTER(_i)]),
+    "nswe_ctx_set_solve_cluster": (_i, [_vp, _i, _i]),
+    "nswe_server_set_cluster": (_i, [_vp, _i, _i, _i]),
+    "nswe_ctx_get_solve_cluster": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nswe_autotune_solve_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_dp), ctypes.POINTER(_dp),
                                        ctypes.POINTER(Params), _i, ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "nswe_server_footprint_1d": (ctypes.c_size_t, [_i, _i, _i]),
@@ -586,6 +589,18 @@ def nswe_ctx_set_solve_shape(ctx, precision, shape):
     _check("nswe_ctx_set_solve_shape", lib().nswe_ctx_set_solve_shape(ctx.h, int(precision), int(shape)))
 
 
+def nswe_ctx_set_solve_cluster(ctx, ctas, team_cells=1024):
+    """1D solves on a cluster of `ctas` CTAs per problem (1: a block per problem)."""
+    _check("nswe_ctx_set_solve_cluster", lib().nswe_ctx_set_solve_cluster(ctx.h, int(ctas), int(team_cells)))
+
+
+def nswe_ctx_get_solve_cluster(ctx):
+    """(ctas, team_cells) of the context."""
+    a, b = _i(), _i()
+    _check("nswe_ctx_get_solve_cluster", lib().nswe_ctx_get_solve_cluster(ctx.h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def nswe_ctx_get_solve_shape(ctx, precision):
     v = _i()
     _check("nswe_ctx_get_solve_shape", lib().nswe_ctx_get_solve_shape(ctx.h, int(precision), ctypes.byref(v)))
@@ -654,6 +669,12 @@ class Server:
         _check("nswe_server_create", lib().nswe_server_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)))
         self.N = {}
         _live["server"].add(self)
+
+    def set_cluster(self, ctas, max_in_flight, team_cells=1024):
+        """Light-load latency form: launches with at most max_in_flight 1D solves in
+        flight run each problem on a cluster of `ctas` CTAs (ctas 1: off)."""
+        _check("nswe_server_set_cluster",
+               lib().nswe_server_set_cluster(self.h, int(ctas), int(max_in_flight), int(team_cells)))
 
     @staticmethod
     def footprint(N, levels, nest_start=-1) -> int:

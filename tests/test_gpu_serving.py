@@ -201,3 +201,39 @@ def test_2d_requests_refused(nswe):
     with pytest.raises(nswe.NsweError):  # can never fit
         sv.submit2d(inp, p)
     sv.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_light_load_cluster_form_matches_the_solve_alone(nswe, precision):
+    """nswe_server_set_cluster: requests submitted one at a time (one solve
+    in flight) run on 8-CTA clusters, the same requests submitted together
+    (the form then depends on how many are in flight); every result agrees with
+    the block-form solve alone: FP64 to a few ulps with the same Newton
+    counts (or within the Newton step that res crossing tol may move),
+    mixed within its bound."""
+    ctx = nswe.Context(0)
+    inps = [I.serving_instance(k) for k in KS[:5]]
+    prms = [params(nswe, p, precision) for p in inps]
+    ref = [alone(nswe, ctx, p, q) for p, q in zip(inps, prms)]
+    sv = nswe.Server(0, device_bytes=256 << 20, host_bytes=64 << 20, streams=2, max_batch=8)
+    try:
+        sv.set_cluster(8, 2)
+        got = []
+        for p, q in zip(inps, prms):  # light load: one in flight
+            t = sv.submit(p, q)
+            got.append(collect(sv, 1)[t])
+        tickets = [sv.submit(p, q) for p, q in zip(inps, prms)]  # five at once: the block form
+        together = collect(sv, len(tickets))
+        got += [together[t] for t in tickets]
+        with pytest.raises(nswe.NsweError):
+            sv.set_cluster(17, 2)
+        sv.set_cluster(1, 0)
+    finally:
+        sv.close()
+    bound = 1e-13 if precision == 0 else 1e-8
+    for k, (U, info, _) in enumerate(got):
+        Ur, infr = ref[k % len(inps)]
+        assert info["status"] == 0, (k, info["status"])
+        same = list(info["iters"]) == list(infr["iters"])
+        err = np.abs(U - Ur).max() / np.abs(Ur).max()
+        assert err <= (bound if same else 1e-9), (k, err, info["iters"], infr["iters"])
