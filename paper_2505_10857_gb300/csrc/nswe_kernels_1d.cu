@@ -40,10 +40,22 @@ struct Geo {
   int bl, br;
   double blh, blq, brh, brq;
   int flux;  // NSWE_FLUX_HLL or NSWE_FLUX_LLF
+  // FP32 copies of the level's state and geometry, read by the FP32 Jacobian
+  // passes instead of converting the FP64 values at every use (a conversion
+  // from FP64 occupies the narrow FP64 pipe); nullptr: convert at use. The
+  // copies hold exactly the converted values, so both give the same bits.
+  const float *U32;    // [2][N]
+  const float *isf32;  // [N+1]
+  const float *cgf32;  // [N+1]
+  const float *igq32;  // [2][N]
+  const float *gq32;   // [2: sigma_x, b_x][2][N]
+  float g32, hdx32;    // float(g), 0.5f * float(dx)
 };
 
 __device__ __forceinline__ Geo make_geo(const ProbDev &P, int l) {
   Geo G;
+  G.U32 = G.isf32 = G.cgf32 = G.igq32 = G.gq32 = nullptr;
+  G.g32 = G.hdx32 = 0.0f;
   G.N = P.lev[l].N;
   G.dx = P.lev[l].dx;
   G.g = P.g;
@@ -234,6 +246,36 @@ __device__ __forceinline__ void fill_ghosts(const Geo &G, int j, Win &w) {
   }
 }
 
+// Level data in the precision T of a pass: FP64 values as stored; FP32
+// values from the copies when the level has them, else converted at use.
+template <typename T> struct GeoT;
+template <> struct GeoT<double> {
+  static __device__ __forceinline__ double u(const Geo &G, const double *U, int i) { return U[i]; }
+  static __device__ __forceinline__ double isf(const Geo &G, int f) { return G.isf[f]; }
+  static __device__ __forceinline__ double cgf(const Geo &G, int f) { return G.cgf[f]; }
+  static __device__ __forceinline__ double igq(const Geo &G, int i) { return G.igq[i]; }
+  static __device__ __forceinline__ double sigx(const Geo &G, int i) { return G.gq[2 * G.N + i]; }
+  static __device__ __forceinline__ double bx(const Geo &G, int i) { return G.gq[4 * G.N + i]; }
+  static __device__ __forceinline__ double g(const Geo &G) { return G.g; }
+  static __device__ __forceinline__ double hdx(const Geo &G) { return 0.5 * G.dx; }
+};
+template <> struct GeoT<float> {
+  static __device__ __forceinline__ float u(const Geo &G, const double *U, int i) {
+    return G.U32 ? G.U32[i] : float(U[i]);
+  }
+  static __device__ __forceinline__ float isf(const Geo &G, int f) { return G.isf32 ? G.isf32[f] : float(G.isf[f]); }
+  static __device__ __forceinline__ float cgf(const Geo &G, int f) { return G.cgf32 ? G.cgf32[f] : float(G.cgf[f]); }
+  static __device__ __forceinline__ float igq(const Geo &G, int i) { return G.igq32 ? G.igq32[i] : float(G.igq[i]); }
+  static __device__ __forceinline__ float sigx(const Geo &G, int i) {
+    return G.gq32 ? G.gq32[i] : float(G.gq[2 * G.N + i]);
+  }
+  static __device__ __forceinline__ float bx(const Geo &G, int i) {
+    return G.gq32 ? G.gq32[2 * G.N + i] : float(G.gq[4 * G.N + i]);
+  }
+  static __device__ __forceinline__ float g(const Geo &G) { return G.isf32 ? G.g32 : float(G.g); }
+  static __device__ __forceinline__ float hdx(const Geo &G) { return G.isf32 ? G.hdx32 : 0.5f * float(G.dx); }
+};
+
 // Two-point Gauss source of cell j (Eq. 9): S = (dx/2) sum_q [g h^2 sigma_x/2
 // - g sigma h b_x] at the Gauss points, h = H_h/sigma, H_h the cubic through
 // the interface values p0..p3 of H at t = -3/2, -1/2, 1/2, 3/2.
@@ -242,16 +284,16 @@ __device__ __forceinline__ void fill_ghosts(const Geo &G, int j, Win &w) {
 template <typename T>
 __device__ __forceinline__ T source_at(const Geo &G, int j, T p0, T p1, T p2, T p3) {
   T S = T(0.0);
-  const T g = T(G.g);
+  const T g = GeoT<T>::g(G);
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     T Hh = T(kLag[q][0]) * p0 + T(kLag[q][1]) * p1 + T(kLag[q][2]) * p2 + T(kLag[q][3]) * p3;
-    T sigx = T(G.gq[(1 * 2 + q) * G.N + j]);
-    T bx = T(G.gq[(2 * 2 + q) * G.N + j]);
-    T h = Hh * T(G.igq[q * G.N + j]);
+    T sigx = GeoT<T>::sigx(G, q * G.N + j);
+    T bx = GeoT<T>::bx(G, q * G.N + j);
+    T h = Hh * GeoT<T>::igq(G, q * G.N + j);
     S += T(0.5) * g * h * h * sigx - g * Hh * bx;
   }
-  return S * (T(0.5) * T(G.dx));
+  return S * GeoT<T>::hdx(G);
 }
 
 // Local residual R_j (Eq. 10) from a filled window.
@@ -448,11 +490,11 @@ __device__ __forceinline__ JW<T> jw_view(double *base, int N) {
 // Component m of cell kk (ghosts included) of the state with interior cell
 // ip perturbed by eps in component m (ip = -1: no perturbation).
 template <typename T>
-__device__ __forceinline__ T pval(const Geo &G, const double *U, int m, int kk, int ip, double eps) {
+__device__ __forceinline__ T pval(const Geo &G, const double *U, int m, int kk, int ip, double eps, T eps_t) {
   const int N = G.N;
   if (kk >= 0 && kk < N) {
-    T x = T(U[m * N + kk]);
-    return kk == ip ? x + T(eps) : x;
+    T x = GeoT<T>::u(G, U, m * N + kk);
+    return kk == ip ? x + eps_t : x;
   }
   const int e = kk < 0 ? 0 : N - 1;
   double He = U[e], Qe = U[N + e];
@@ -470,6 +512,7 @@ __device__ __forceinline__ T pval(const Geo &G, const double *U, int m, int kk, 
 template <typename T>
 __device__ void jac_pass_a(const Geo &G, const double *U, double eps, const JW<T> &W, int first, int stride) {
   const int N = G.N, items = (N + 2) * 8;
+  const T eps_t = T(eps);
   for (int it = first; it < items; it += stride) {
     const int k = it % (N + 2) - 1, mv = it / (N + 2), m = mv >> 2, v = mv & 3;
     int ip = -1;
@@ -478,7 +521,8 @@ __device__ void jac_pass_a(const Geo &G, const double *U, double eps, const JW<T
       if (ip < 0 || ip >= N) continue;
     }
     T up, um;
-    weno3<T>(pval<T>(G, U, m, k - 1, ip, eps), pval<T>(G, U, m, k, ip, eps), pval<T>(G, U, m, k + 1, ip, eps), up, um);
+    weno3<T>(pval<T>(G, U, m, k - 1, ip, eps, eps_t), pval<T>(G, U, m, k, ip, eps, eps_t),
+             pval<T>(G, U, m, k + 1, ip, eps, eps_t), up, um);
     W.r(m, v, 0, k) = up;
     W.r(m, v, 1, k) = um;
   }
@@ -498,9 +542,9 @@ __device__ __forceinline__ int rec_variant(int i, int kk) {
 template <typename T, int FLUX>
 __device__ void jac_pass_b(const Geo &G, const JW<T> &W, int first, int stride) {
   const int N = G.N;
-  const T g = T(G.g);
+  const T g = GeoT<T>::g(G);
   for (int f = first; f <= N; f += stride) {
-    const T isg = T(G.isf[f]), cg = T(G.cgf[f]);
+    const T isg = GeoT<T>::isf(G, f), cg = GeoT<T>::cgf(G, f);
     const FState<T> Lb = fstate<T>(W.r(0, 0, 1, f - 1), W.r(1, 0, 1, f - 1), isg, cg, g);
     const FState<T> Rb = fstate<T>(W.r(0, 0, 0, f), W.r(1, 0, 0, f), isg, cg, g);
     T F0, F1;
@@ -602,6 +646,45 @@ struct RW {
   __device__ __forceinline__ double &f(int l, int face) const { return flx[l * (N + 1) + face]; }
 };
 
+// FP32 copies of a mixed-precision level (Geo::U32 and the geometry): 10 N + 2
+// floats placed after the FP64 residual's workspace, within jw_doubles(N).
+__host__ __device__ inline size_t f32_area_offset(size_t N) {
+  const size_t rw = (jw_doubles(N) / 2 + 2) / 2 * 2;
+  return (rw + 4 * (N + 2) + 2 * (N + 1) + 3) / 4 * 4;
+}
+
+// Points G's FP32 copies at their place in the Jacobian workspace jw.
+__device__ __forceinline__ float *attach_f32(Geo &G, double *jw) {
+  float *A = reinterpret_cast<float *>(jw + f32_area_offset((size_t)G.N));
+  const int N = G.N;
+  G.U32 = A;
+  G.isf32 = A + 2 * N;
+  G.cgf32 = G.isf32 + N + 1;
+  G.igq32 = G.cgf32 + N + 1;
+  G.gq32 = G.igq32 + 2 * N;
+  G.g32 = float(G.g);
+  G.hdx32 = 0.5f * float(G.dx);
+  return A;
+}
+
+// Writes the FP32 copies of state U and of G's geometry into A (attach_f32's
+// layout), items strided.
+__device__ void fill_f32(const Geo &G, const double *U, float *A, int first, int stride) {
+  const int N = G.N;
+  float *U32 = A, *isf = A + 2 * N, *cgf = isf + N + 1, *igq = cgf + N + 1, *gq = igq + 2 * N;
+  for (int t = first; t < 4 * N; t += stride) {
+    if (t < 2 * N) {
+      U32[t] = float(U[t]);
+      igq[t] = float(G.igq[t]);
+    }
+    if (t <= N) {
+      isf[t] = float(G.isf[t]);
+      cgf[t] = float(G.cgf[t]);
+    }
+    gq[t] = float(G.gq[2 * N + t]);  // sigma_x and b_x planes
+  }
+}
+
 // Placed after the FP32 Jacobian workspace of the same level.
 __device__ __forceinline__ RW rw_view(double *jw, int N) {
   RW W;
@@ -616,8 +699,8 @@ __device__ void res_pass_a(const Geo &G, const double *U, const RW &W, int first
   for (int it = first; it < items; it += stride) {
     const int k = it % (N + 2) - 1, m = it / (N + 2);
     double up, um;
-    weno3<double>(pval<double>(G, U, m, k - 1, -1, 0.0), pval<double>(G, U, m, k, -1, 0.0),
-                  pval<double>(G, U, m, k + 1, -1, 0.0), up, um);
+    weno3<double>(pval<double>(G, U, m, k - 1, -1, 0.0, 0.0), pval<double>(G, U, m, k, -1, 0.0, 0.0),
+                  pval<double>(G, U, m, k + 1, -1, 0.0, 0.0), up, um);
     W.r(m, 0, k) = up;
     W.r(m, 1, k) = um;
   }
@@ -1428,10 +1511,18 @@ __global__ void __launch_bounds__(THREADS, MINB)
 
   for (int l = s0; l >= 0 && !fatal; --l) {
     const LevelDev &Lv = P.lev[l];
-    const Geo G = make_geo(P, l);
+    Geo G = make_geo(P, l);
     const int N = G.N;
     if (l < s0) {
       interp_cells(make_geo(P, l + 1), P.lev[l + 1].U, Lv.U, team.tid(), team.size());
+      team.sync();
+    }
+    // Mixed path: the FP32 Jacobian reads FP32 copies of the state (kept up
+    // to date by the update) and of the level's geometry.
+    float *U32 = nullptr;
+    if constexpr (kMixed) {
+      U32 = attach_f32(G, P.jw);
+      fill_f32(G, Lv.U, U32, team.tid(), team.size());
       team.sync();
     }
     const JW<T> W = jw_view<T>(P.jw, N);
@@ -1498,6 +1589,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
         double h = Lv.U[j] + prm.tau * double(dU[j]);
         Lv.U[j] = h;
         Lv.U[N + j] += prm.tau * double(dU[N + j]);
+        if constexpr (kMixed) {
+          U32[j] = float(h);
+          U32[N + j] = float(Lv.U[N + j]);
+        }
         if (!(h > 0.0)) bad = true;
       }
       bad = team.any(bad);
