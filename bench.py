@@ -415,6 +415,23 @@ def run_gpu(args, rank, world, local_rank):
     def step(want_info=False):
         return nswe.nswe_newton_solve_batch(ctx, probs, U0s, Us, prm, want_info=want_info)
 
+    # Steady throughput: consecutive steps alternate between two independent copies of the batch,
+    # each with its own context and stream, so that one step's launch starts on the SMs that the
+    # previous step's slowest problems leave idle. Every step still solves all B problems.
+    pipelined = not l2_flush and not args.sequential_steps
+    if pipelined:
+        stream_b = torch.cuda.Stream(dev)
+        ctx_b = nswe.Context(local_rank, stream=stream_b.cuda_stream)
+        probs_b = [nswe.Problem1D.from_inputs(ctx_b, p) for p in inps]
+        U0_all_b, U_all_b = torch.zeros_like(U0_all), torch.zeros_like(U_all)
+        U0s_b = [U0_all_b[int(u0_off[k]):int(u0_off[k]) + p.U0_start.size].view(2, -1) for k, p in enumerate(inps)]
+        Us_b = [U_all_b[int(u_off[k]):int(u_off[k]) + 2 * p.N].view(2, -1) for k, p in enumerate(inps)]
+        U0_all_b.copy_(U0_all)
+        torch.cuda.synchronize()
+
+        def step_b():
+            nswe.nswe_newton_solve_batch(ctx_b, probs_b, U0s_b, Us_b, prm, want_info=False)
+
     # Launch-shape autotuning on this batch (before the warm-up; not timed).
     tune = None
     shape = 0
@@ -428,13 +445,15 @@ def run_gpu(args, rank, world, local_rank):
                 "what": "threads per block x resident blocks per SM of k_solve, one timed batch each"}
         shape = best
     shape_name = "%dx%d" % nswe.solve_shapes()[shape]
+    if pipelined:
+        nswe.nswe_ctx_set_solve_shape(ctx_b, prm.precision, shape)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
+    for w in range(args.warmup):
+        step_b() if (pipelined and w % 2) else step()
     torch.cuda.synchronize()
 
     # ---- device-timed throughput (inputs resident in HBM)
@@ -458,6 +477,8 @@ def run_gpu(args, rank, world, local_rank):
         ms = sum(per_launch) / args.steps
         del flush
     else:
+        # one step at a time on one stream (reported beside the steady figure, and the roofline's
+        # per-launch duration)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev[0].record(stream)
         for s in range(args.steps):
@@ -466,6 +487,21 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         per_launch = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
         ms = ev[0].elapsed_time(ev[-1]) / args.steps
+        ms_sequential = ms
+        if pipelined:
+            # steady throughput: the same K steps alternating between the two streams
+            barrier()
+            torch.cuda.synchronize()
+            e0, e1, eb_end = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            stream_b.wait_event(e0)
+            for s in range(args.steps):
+                step_b() if s % 2 else step()
+            eb_end.record(stream_b)
+            stream.wait_event(eb_end)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
     barrier()
     clk = clocks.stop()
     ms_max = max_over_ranks(ms, world, dev)
@@ -488,12 +524,15 @@ def run_gpu(args, rank, world, local_rank):
           for k in range(B)]
     f64, f32 = sum(a for a, _ in fl), sum(b for _, b in fl)
     launch_ms = statistics.mean(per_launch)
+    # the roofline of the steady form: each launch's flops over the timed region per launch
+    launch_ms_steady = ms if pipelined else launch_ms
     peaks = measure_fma_peaks(local_rank)
     p64, p32 = peaks["fp64_tflops"], peaks["fp32_tflops"]
     # FP64-equivalent rate: FP32 flops weighted by the FP64:FP32 peak ratio, so
     # that achieved / FP64 peak is the fraction of the time at both peaks.
     flops = f64 + f32 * p64 / p32
-    achieved = flops / (launch_ms / 1000.0) / 1e12
+    achieved = flops / (launch_ms_steady / 1000.0) / 1e12
+    achieved_one = flops / (launch_ms / 1000.0) / 1e12
 
     # ---- single-solve latency (one instance alone on the GPU)
     single = []
@@ -534,21 +573,50 @@ def run_gpu(args, rank, world, local_rank):
     pin_u = torch.empty_like(U_all, device="cpu").pin_memory()
     bcl, bcr = [p.bcl for p in inps], [p.bcr for p in inps]
     h2d = sum(a.nbytes for a in pin_sf + pin_gq) + pin_u0.numel() * 8  # the bytes copied, padding included
-    d2h = pin_u.numel() * 8 + B * ctypes.sizeof(nswe.Info)
-    e2e_times = []
-    for s in range(args.warmup + args.steps):
+    if pipelined:
+        # steady form: the steps alternate between the two batches and streams; each step uploads its
+        # geometry and guesses, solves and copies its results back, asynchronously on its own stream,
+        # so one step's uploads overlap the other's solve; every step's copies lie in the timed region
+        pin_u_b = torch.empty_like(U_all_b, device="cpu").pin_memory()
+        d2h = pin_u.numel() * 8
+        sets = [(ctx, probs, U0_all, U0s, U_all, Us, pin_u, stream),
+                (ctx_b, probs_b, U0_all_b, U0s_b, U_all_b, Us_b, pin_u_b, stream_b)]
+
+        def e2e_step(s):
+            c_ctx, c_probs, c_u0_all, c_u0s, c_u_all, c_us, c_pin_u, c_stream = sets[s % 2]
+            nswe.nswe_prob_set_geometry_batch_1d(c_ctx, c_probs, pin_sf, pin_gq, bcl, bcr)
+            with torch.cuda.stream(c_stream):
+                c_u0_all.copy_(pin_u0, non_blocking=True)
+            nswe.nswe_newton_solve_batch(c_ctx, c_probs, c_u0s, c_us, prm, want_info=False)
+            with torch.cuda.stream(c_stream):
+                c_pin_u.copy_(c_u_all, non_blocking=True)
+
+        for s in range(args.warmup):
+            e2e_step(s)
         barrier()
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        nswe.nswe_prob_set_geometry_batch_1d(ctx, probs, pin_sf, pin_gq, bcl, bcr)
-        U0_all.copy_(pin_u0, non_blocking=True)
-        infos_e = step(want_info=True)  # synchronous: includes the D2H of the per-solve records
-        pin_u.copy_(U_all, non_blocking=True)
+        for s in range(args.steps):
+            e2e_step(s)
         torch.cuda.synchronize()
-        if s >= args.warmup:
-            e2e_times.append(time.perf_counter() - w0)
-        assert all(i["status"] == 0 for i in infos_e)
-    e2e_ms = max_over_ranks(1000.0 * statistics.mean(e2e_times), world, dev)
+        e2e_ms = max_over_ranks(1000.0 * (time.perf_counter() - w0) / args.steps, world, dev)
+        assert np.array_equal(pin_u.numpy(), U_all.cpu().numpy())  # the results copied back are the solves'
+    else:
+        d2h = pin_u.numel() * 8 + B * ctypes.sizeof(nswe.Info)
+        e2e_times = []
+        for s in range(args.warmup + args.steps):
+            barrier()
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            nswe.nswe_prob_set_geometry_batch_1d(ctx, probs, pin_sf, pin_gq, bcl, bcr)
+            U0_all.copy_(pin_u0, non_blocking=True)
+            infos_e = step(want_info=True)  # synchronous: includes the D2H of the per-solve records
+            pin_u.copy_(U_all, non_blocking=True)
+            torch.cuda.synchronize()
+            if s >= args.warmup:
+                e2e_times.append(time.perf_counter() - w0)
+            assert all(i["status"] == 0 for i in infos_e)
+        e2e_ms = max_over_ranks(1000.0 * statistics.mean(e2e_times), world, dev)
     e2e_value = whole_job_rate(world, B, e2e_ms)
 
     out = None
@@ -590,7 +658,16 @@ def run_gpu(args, rank, world, local_rank):
             "converged": {"all_status_ok": all(s == 0 for s in status), "max_res": max(res0),
                           "mean_newton_iters": statistics.mean(i["total_iters"] for i in infos)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": e2e_ms},
+                    "ms_per_step": e2e_ms,
+                    "form": ("steps alternating between two batches and streams, copies and solves asynchronous"
+                             if pipelined else "one step at a time, synchronous")},
+            "steps_form": ({"form": "steady: consecutive steps alternate between two independent copies of the "
+                                    "batch, each with its own context and stream, so that a step's launch starts "
+                                    "on the SMs the previous step's slowest problems leave idle; every step "
+                                    "solves all instances; ms_per_step = timed region / steps",
+                            "one_step_at_a_time": {"ms_per_step": ms_sequential,
+                                                   "value": whole_job_rate(world, B, ms_sequential)}}
+                           if pipelined else {"form": "one step at a time on one stream"}),
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": p64,
                          "unit": "TFLOP/s", "frac": achieved / p64,
@@ -599,7 +676,12 @@ def run_gpu(args, rank, world, local_rank):
                          "traffic_note": "DRAM bytes per launch from one ncu capture of this workload; "
                                          "8-16 % of the HBM copy rate over the launch, far from bound",
                          "kernel": f"k_solve (persistent nested NMGM, one block per instance, shape {shape_name})",
-                         "flops_per_launch": flops, "fp64_flops": f64, "fp32_flops": f32, "launch_ms": launch_ms,
+                         "flops_per_launch": flops, "fp64_flops": f64, "fp32_flops": f32,
+                         "launch_ms": launch_ms_steady,
+                         "launch_ms_note": ("timed region per launch, two launches in flight (steady form); one "
+                                            f"launch alone takes {launch_ms:.1f} ms, frac "
+                                            f"{achieved_one / p64:.3f} of the peak" if pipelined
+                                            else "mean launch duration (CUDA events on the launching stream)"),
                          "peak_note": "FP64 FMA peak measured in this run (nswe_probe_fma); derived "
                                       "152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz = %.3f TFLOP/s" % (FP64_PEAK_GFLOPS / 1e3)
                                       + ("; FP32 flops counted at the measured FP64/FP32 peak ratio" if mixed else ""),
@@ -1464,6 +1546,8 @@ def main():
     ap.add_argument("--phases-only", action="store_true", help="wedge2d: only the 512x256 phase times")
     ap.add_argument("--tol", type=float, default=None,
                     help="stopping residual (default: 1e-10 for the FP64 line, 3e-13 for mixed and serving lines)")
+    ap.add_argument("--sequential-steps", action="store_true",
+                    help="time the 1D steps one at a time on one stream only (no steady two-stream form)")
     ap.add_argument("--no-serving", action="store_true",
                     help="default line: skip the serving / plain FP64 single-instance comparison")
     ap.add_argument("--single-requests", type=int, default=24,
