@@ -581,9 +581,11 @@ __device__ __forceinline__ void sor_cell2(int Nx, int Ny, int st, const T *J, co
     const int cp = q * Nx + p;
     const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
-      r[l] += J[(size_t)(k * 9 + l * 3 + 0) * S + pc] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * S + pc] * x1 +
-              J[(size_t)(k * 9 + l * 3 + 2) * S + pc] * x2;
+    for (int l = 0; l < 3; ++l) {  // a chain of fused multiply-adds (the order of sor_pass_split)
+      r[l] = fma(J[(size_t)(k * 9 + l * 3 + 0) * S + pc], x0, r[l]);
+      r[l] = fma(J[(size_t)(k * 9 + l * 3 + 1) * S + pc], x1, r[l]);
+      r[l] = fma(J[(size_t)(k * 9 + l * 3 + 2) * S + pc], x2, r[l]);
+    }
   }
   T t[3];
 #pragma unroll
@@ -701,8 +703,9 @@ __device__ __forceinline__ void sor_pass_split(int Nx, int Ny, int st_arg, const
         if (p < 0 || p >= Nx || q < 0 || q >= Ny) continue;
         const int cp = q * Nx + p;
         const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
-        r += J[(size_t)(k * 9 + l * 3 + 0) * S + pc] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * S + pc] * x1 +
-             J[(size_t)(k * 9 + l * 3 + 2) * S + pc] * x2;
+        r = fma(J[(size_t)(k * 9 + l * 3 + 0) * S + pc], x0, r);
+        r = fma(J[(size_t)(k * 9 + l * 3 + 1) * S + pc], x1, r);
+        r = fma(J[(size_t)(k * 9 + l * 3 + 2) * S + pc], x2, r);
       }
     const T r0 = __shfl_sync(0xffffffffu, r, min(src, 31));
     const T r1 = __shfl_sync(0xffffffffu, r, min(src + 1, 31));
@@ -764,9 +767,11 @@ __device__ void restrict_cells2(int Nx, int Ny, int st, const T *J, const T *R, 
           const int cp = q * Nx + p;
           const T x0 = dU[cp], x1 = dU[n + cp], x2 = dU[2 * n + cp];
 #pragma unroll
-          for (int l = 0; l < 3; ++l)
-            r[l] += J[(size_t)(k * 9 + l * 3 + 0) * S + pc] * x0 + J[(size_t)(k * 9 + l * 3 + 1) * S + pc] * x1 +
-                    J[(size_t)(k * 9 + l * 3 + 2) * S + pc] * x2;
+          for (int l = 0; l < 3; ++l) {
+            r[l] = fma(J[(size_t)(k * 9 + l * 3 + 0) * S + pc], x0, r[l]);
+            r[l] = fma(J[(size_t)(k * 9 + l * 3 + 1) * S + pc], x1, r[l]);
+            r[l] = fma(J[(size_t)(k * 9 + l * 3 + 2) * S + pc], x2, r[l]);
+          }
         }
         s[0] += r[0];
         s[1] += r[1];
