@@ -604,7 +604,10 @@ size_t nswe_server_footprint_1d(int N, int levels, int nest_start);
 size_t nswe_server_footprint_2d(int Nx, int Ny, int levels, int nest_start);
 
 /* Allocates the arenas, streams and the scheduler thread on `device`.
- * EINVAL for a bad config, ENOMEM if an arena cannot be allocated. */
+ * EINVAL for a bad config, ENOMEM if an arena cannot be allocated. A 1D
+ * launch gives each request one thread block of 128 threads (FP64; the
+ * launch shape 128 x 4 of nswe_solve_shape_info) or 256 threads (mixed
+ * precision; 256 x 4), or a cluster (nswe_server_set_cluster). */
 nswe_status nswe_server_create(nswe_server *out, int device,
                                const nswe_server_config *cfg);
 

@@ -22,6 +22,15 @@ constexpr int kSolveShapes = 6;
 constexpr int kSolveShapeThreads[kSolveShapes] = {256, 128, 256, 128, 160, 192};
 constexpr int kSolveShapeBlocks[kSolveShapes] = {4, 8, 2, 4, 4, 4};
 constexpr int kMaxCoarse = 128;    // max cells of the coarsest level (direct solve)
+// Launch shapes of the serving server's 1D block launches, per precision:
+// 128 x 4 in FP64 (128 registers a thread, no spills), 256 x 4 in mixed
+// precision (the faster of the two there).
+constexpr int kServerShapeFp64 = 3;
+constexpr int kServerShapeMixed = 0;
+static_assert(kSolveShapeThreads[kServerShapeFp64] == 128 && kSolveShapeBlocks[kServerShapeFp64] == 4,
+              "FP64 server shape is 128 x 4");
+static_assert(kSolveShapeThreads[kServerShapeMixed] == 256 && kSolveShapeBlocks[kServerShapeMixed] == 4,
+              "mixed server shape is 256 x 4");
 // The latency form of the solve kernel: one problem per thread-block cluster
 // of up to kMaxClusterCtas CTAs of kClusterThreads threads.
 constexpr int kClusterThreads = 128;

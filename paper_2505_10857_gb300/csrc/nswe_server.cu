@@ -365,7 +365,9 @@ bool nswe_server_s::admit_and_launch(int s) {
   if (cudaMemcpyAsync(task_dev[s], task_host[s], sizeof(SolveTask) * n, cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
       (cluster ? launch_solve_cluster(task_dev[s], n, launch, max_coarse, max_nb, ctas, cl_team_cells.load(), st)
-               : launch_solve_sized(task_dev[s], n, launch, max_coarse, max_nb, 0, st)) != cudaSuccess) {
+               : launch_solve_sized(task_dev[s], n, launch, max_coarse, max_nb,
+                                    launch.precision == NSWE_PREC_MIXED ? kServerShapeMixed : kServerShapeFp64,
+                                    st)) != cudaSuccess) {
     error = NSWE_ECUDA;
     return false;
   }

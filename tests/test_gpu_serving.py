@@ -33,6 +33,16 @@ def alone(nswe, ctx, inp, prm):
     return U.cpu().numpy(), info
 
 
+def server_ctx(nswe):
+    """A context whose 1D launch shapes are the server's (128 x 4 threads x
+    blocks in FP64, 256 x 4 in mixed precision), so that a solve alone runs the
+    kernel instantiation of the server's launches: the same bits."""
+    ctx = nswe.Context(0)
+    nswe.nswe_ctx_set_solve_shape(ctx, 0, nswe.solve_shapes().index((128, 4)))
+    nswe.nswe_ctx_set_solve_shape(ctx, 1, nswe.solve_shapes().index((256, 4)))
+    return ctx
+
+
 def params(nswe, inp, precision):
     p = nswe.params_from(I.Params1D.for_problem(inp, tol=1e-10, n_max=500))
     p.precision = precision
@@ -51,7 +61,7 @@ def collect(sv, n, timeout=120.0):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_mix_equals_alone(nswe, precision):
-    ctx = nswe.Context(0)
+    ctx = server_ctx(nswe)
     inps = [I.serving_instance(k) for k in KS]
     prms = [params(nswe, p, precision) for p in inps]
     ref = [alone(nswe, ctx, p, q) for p, q in zip(inps, prms)]
@@ -148,7 +158,7 @@ def requests2d(nswe):
 def test_2d_requests_equal_alone_beside_1d(nswe):
     """2D requests served by the worker pool, interleaved with 1D requests on
     the same server: every result equals, bit for bit, its solve alone."""
-    ctx = nswe.Context(0)
+    ctx = server_ctx(nswe)
     reqs = requests2d(nswe)
     ref2 = [alone2d(nswe, ctx, inp, p) for inp, p in reqs]
     one = [I.serving_instance(k) for k in (11, 9)]
@@ -211,7 +221,7 @@ def test_light_load_cluster_form_matches_the_solve_alone(nswe, precision):
     the block-form solve alone: FP64 to a few ulps with the same Newton
     counts (or within the Newton step that res crossing tol may move),
     mixed within its bound."""
-    ctx = nswe.Context(0)
+    ctx = server_ctx(nswe)
     inps = [I.serving_instance(k) for k in KS[:5]]
     prms = [params(nswe, p, precision) for p in inps]
     ref = [alone(nswe, ctx, p, q) for p, q in zip(inps, prms)]
