@@ -1151,8 +1151,9 @@ def run_serve1d(args):
     torch.cuda.init()
     clocks = ClockSampler(0)
     clocks.start()
+    cluster = (args.cluster_ctas, LIGHT_MAX_IN_FLIGHT) if args.cluster_ctas > 1 else None
     r = serve1d_measure(inps, prms, args.rate, args.streams, args.max_batch, args.serve_mem_gb,
-                        64 * max(1, args.warmup))
+                        64 * max(1, args.warmup), cluster=cluster)
     clk = clocks.stop()
     lat, queue, ok, infos = r["lat_ms"], r["queue_ms"], r["ok"], r["info"]
     line_parity, cpu = None, None
@@ -1171,6 +1172,8 @@ def run_serve1d(args):
                                + ("mixed FP64/FP32" if mixed else "FP64"),
                    "offered_rate": args.rate, "streams": args.streams, "max_batch": args.max_batch, "tol": tol,
                    "device_arena_gb": args.serve_mem_gb, "seeds": "numpy default_rng(4000 + k); arrivals 4999",
+                   "cluster_form": ({"ctas": args.cluster_ctas, "max_in_flight": LIGHT_MAX_IN_FLIGHT}
+                                    if cluster else None),
                    "l2": "resident workspace of the requests in flight exceeds the 129 MB L2"},
         "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": lat[-1],
                        "what": "completion minus submission per request (host clock)",
@@ -1546,6 +1549,8 @@ def main():
     ap.add_argument("--phases-only", action="store_true", help="wedge2d: only the 512x256 phase times")
     ap.add_argument("--tol", type=float, default=None,
                     help="stopping residual (default: 1e-10 for the FP64 line, 3e-13 for mixed and serving lines)")
+    ap.add_argument("--cluster-ctas", type=int, default=1,
+                    help="serve1d: the server's light-load cluster form with that many CTAs per request (1: off)")
     ap.add_argument("--sequential-steps", action="store_true",
                     help="time the 1D steps one at a time on one stream only (no steady two-stream form)")
     ap.add_argument("--no-serving", action="store_true",
