@@ -81,3 +81,37 @@ def test_autotuner_picks_and_records_a_shape(nswe, ctx):
     finally:
         nswe.nswe_ctx_set_solve_shape(ctx, 0, 0)
         b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_contexts_on_two_streams_solve_concurrently_with_the_same_bits(nswe, precision):
+    """Two contexts, each with its own stream and its own copy of a batch,
+    launched back to back so that their solves overlap on the GPU (the steady
+    form of the benchmark): every solution equals, bit for bit, the same batch
+    solved alone on one context."""
+    inps = [I.channel_irregular(k, N=1024, levels=6, start_level=2) for k in range(6)]
+    prm = nswe.params_from(I.Params1D.for_problem(inps[0], tol=1e-10, n_max=500))
+    prm.precision = precision
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ctxs = [nswe.Context(0, stream=s.cuda_stream) for s in streams]
+    batches = [Batch(nswe, c, inps) for c in ctxs]
+    try:
+        torch.cuda.synchronize()
+        nswe.nswe_newton_solve_batch(ctxs[0], batches[0].probs, batches[0].U0s, batches[0].Us, prm)
+        torch.cuda.synchronize()
+        alone = [u.cpu().numpy() for u in batches[0].Us]
+        for b in batches:
+            for u in b.Us:
+                u.zero_()
+        torch.cuda.synchronize()
+        for c, b in zip(ctxs, batches):  # asynchronous: the second launch overlaps the first
+            nswe.nswe_newton_solve_batch(c, b.probs, b.U0s, b.Us, prm, want_info=False)
+        torch.cuda.synchronize()
+        for b in batches:
+            for k, u in enumerate(b.Us):
+                assert np.array_equal(u.cpu().numpy(), alone[k]), k
+    finally:
+        for b in batches:
+            b.close()
+        for c in ctxs:
+            c.close()
