@@ -108,3 +108,41 @@ def test_cluster_settings(nswe, ctx):
             nswe.nswe_ctx_set_solve_cluster(ctx, ctas, cells)
     assert nswe.nswe_ctx_get_solve_cluster(ctx) == (4, 2048)
     nswe.nswe_ctx_set_solve_cluster(ctx, 1, 1024)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cluster_solve_with_the_full_jacobian_agrees(nswe, ctx, precision):
+    """J5 (nb = 5, Section 3.3's full Jacobian): the coarsest nested level is
+    solved directly with the five-block band, on the leader CTA."""
+    inps = [I.channel_irregular(k, N=1024, levels=6, start_level=2) for k in range(2)]
+    prm = nswe.params_from(I.Params1D.for_problem(inps[0], tol=1e-10, n_max=500, nb=5))
+    prm.precision = precision
+    b = Batch(nswe, ctx, inps)
+    try:
+        U_ref, infos_ref = b.solve(nswe, ctx, prm)
+        nswe.nswe_ctx_set_solve_cluster(ctx, 8, 512)
+        U, infos = b.solve(nswe, ctx, prm)
+    finally:
+        nswe.nswe_ctx_set_solve_cluster(ctx, 1, 1024)
+        b.close()
+    _agree(U, infos, U_ref, infos_ref, precision)
+
+
+def test_llf_problems_keep_the_block_form_under_the_cluster_setting(nswe, ctx):
+    """The cluster form is built for the HLL flux; LLF problems (Section 3.1's
+    alternative) run in the block form whatever the setting: the same bits as
+    with the setting off."""
+    inps = [I.channel_irregular(k, N=1024, levels=6, start_level=2) for k in range(2)]
+    for p in inps:
+        p.flux = nswe.FLUX_LLF
+    prm = nswe.params_from(I.Params1D.for_problem(inps[0], tol=1e-10, n_max=500))
+    b = Batch(nswe, ctx, inps)
+    try:
+        U_ref, infos_ref = b.solve(nswe, ctx, prm)
+        nswe.nswe_ctx_set_solve_cluster(ctx, 8, 512)
+        U, infos = b.solve(nswe, ctx, prm)
+    finally:
+        nswe.nswe_ctx_set_solve_cluster(ctx, 1, 1024)
+        b.close()
+    for k in range(len(inps)):
+        assert infos[k]["status"] == 0 and np.array_equal(U[k], U_ref[k]), k
